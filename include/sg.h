@@ -1,0 +1,138 @@
+/*
+ * libsg -- stochastic Galerkin (SG) solver for the linear stochastic Poisson
+ * problem  -div(c(x, xi) grad u) = 1  on the unit square, u = 0 on the
+ * boundary, with a lognormal coefficient c = exp(g), g a Gaussian field with
+ * the separable exponential covariance of Sec. 2.1 (Eqs. KLE, CovarKer2DNLP),
+ * expanded in a Hermite polynomial chaos (Eqs. inputpc, inputlogn, outpc) and
+ * projected onto the chaos (Eq. Galerkin_L_exp).  The coupled system
+ *
+ *        sum_k  A_k X G_k^T = F,      G_k[a][b] = <psi_k psi_a psi_b>,
+ *
+ * is solved by flexible GMRES preconditioned by the two-level restricted
+ * additive Schwarz cycle of Sec. 3 (Eqs. RASsto, coarse, RAS_2L).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Chaos basis: orthonormal probabilists' Hermite polynomials
+ *   psi_alpha = prod_i He_{alpha_i}(xi_i) / sqrt(alpha_i!).  The paper's
+ *   coefficient u_bar_a equals X[:, a] / sqrt(alpha_a!).
+ * - Multi-index order: total degree ascending, then lexicographically
+ *   descending in (alpha_1, ..., alpha_L).
+ * - Mesh: N x N cells of size h = 1/N, each split by the "/" diagonal into
+ *   two right triangles, P1 elements, coefficient constant per triangle
+ *   (evaluated at its centroid).  Interior node (i, j), 1 <= i, j <= N-1, has
+ *   number r = (j-1)(N-1) + (i-1); n = (N-1)^2.
+ * - Blocks of PCE coefficients (X, Y, F) are MODE-MAJOR device arrays:
+ *   entry (node r, mode a) lives at X[a * ld + r], ld >= n.
+ * - Device pointers belong to the caller; the library never frees them.
+ *   The handle owns every buffer it allocates (in sg_setup and
+ *   sg_precond_setup) and frees them in sg_destroy.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued on it; calls return without waiting unless
+ *   stated otherwise.
+ * - Errors are returned as sg_status codes; no exception crosses the ABI.
+ *   sg_last_error() returns a thread-local message for the last failure.
+ *   A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef SG_H_
+#define SG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_problem sg_problem;
+
+typedef enum {
+  SG_OK = 0,
+  SG_NOT_CONVERGED = 1,     /* solver hit max_it; best iterate written  */
+  SG_ERR_ARG = -1,          /* bad argument (NULL, size, ld, order ...) */
+  SG_ERR_CUDA = -2,         /* a CUDA runtime call failed               */
+  SG_ERR_NOMEM = -3,        /* device or host allocation failed         */
+  SG_ERR_BREAKDOWN = -4,    /* non-finite value inside the solver       */
+  SG_ERR_TIMEOUT = -5,      /* a bounded device wait ran out            */
+  SG_ERR_UNSUPPORTED = -6   /* feature not available in this build      */
+} sg_status;
+
+typedef enum { SG_F64 = 0, SG_F32 = 1 } sg_dtype;
+
+/* Structured unit-square mesh: N cells per side (N >= 2, even when a
+ * preconditioner with a coarse grid is set up). */
+typedef struct {
+  int N;
+} sg_mesh_desc;
+
+/* Gaussian field g = g0 + sum_{i<L} g_i xi_i (Sec. 2.1, Eq. KLE).
+ * Analytic KL modes of sigma2 * exp(-|dx|/bx - |dy|/by) are used unless
+ * user_modes is given: then it holds L x (2 N^2) values g_i(e) per triangle e
+ * (element id 2 (j N + i) for the lower and 2 (j N + i) + 1 for the upper
+ * triangle of cell (i, j)), sqrt(lambda_i) included; it is copied. */
+typedef struct {
+  double sigma2, bx, by, g0;
+  int L;
+  const double* user_modes;
+} sg_kl_desc;
+
+/* Build the SG system (Sec. 2.1): KL modes at triangle centroids, output
+ * multi-indices of degree <= p_out (P terms), input multi-indices of degree
+ * <= q_in (K terms), the nonzero triple products, the lognormal input
+ * coefficients, and the K stiffness matrices A_k on one shared CSR pattern
+ * (the pattern of A_0 with exact zeros dropped; every A_k is stored on it).
+ * The matrices are assembled on the current CUDA device in FP64 and FP32.
+ * Errors: SG_ERR_ARG for N < 2, L < 0, p_out < 0, q_in < 0 or NULL pointers;
+ * SG_ERR_NOMEM / SG_ERR_CUDA on allocation or launch failure. */
+sg_status sg_setup(const sg_mesh_desc* mesh, const sg_kl_desc* kl, int p_out, int q_in,
+                   sg_problem** out);
+
+/* Frees every buffer the handle owns.  NULL is accepted. */
+sg_status sg_destroy(sg_problem* prob);
+
+/* Sizes: n interior nodes, P output terms, K input terms, nnzA entries of
+ * the shared pattern, T nonzero triple products.  Any pointer may be NULL. */
+sg_status sg_get_sizes(const sg_problem* prob, int64_t* n, int* P, int* K, int64_t* nnzA,
+                       int64_t* T);
+
+/* Multi-index table, row-major: which = 0 gives the P x L output set,
+ * which = 1 the K x L input set.  `out` is host memory of that size. */
+sg_status sg_get_multi_indices(const sg_problem* prob, int32_t* out, int which);
+
+/* Triple products <psi_k psi_a psi_b> != 0 ordered by k, a, b
+ * (Eq. Galerkin_L_exp): kab is host T x 3, num is host T (unnormalised
+ * integer prod_i <He_{k_i} He_{a_i} He_{b_i}>), g is host T (orthonormal
+ * value num / sqrt(k! a! b!)).  num or g may be NULL. */
+sg_status sg_get_triples(const sg_problem* prob, int32_t* kab, int64_t* num, double* g);
+
+/* Shared CSR pattern on the host: rowptr n+1, colidx nnzA, columns ascending. */
+sg_status sg_get_csr(const sg_problem* prob, int32_t* rowptr, int32_t* colidx);
+
+/* Values of A_k on the shared pattern (FP64, host array K x nnzA, CSR order),
+ * copied back from the device; for tests and small problems. */
+sg_status sg_get_values(const sg_problem* prob, double* vals);
+
+/* Load vector F = b e_0^T (b_r = integral of the hat function, f = 1,
+ * Eq. Galerkin_L_exp with <psi_k> = delta_k0), written as a mode-major
+ * FP64 device block with leading dimension ld (all modes a >= 1 zeroed). */
+sg_status sg_get_rhs(const sg_problem* prob, double* F_dev, int64_t ld, void* stream);
+
+/* Galerkin operator apply (Eq. Galerkin_L_exp in Kronecker form):
+ *     Y = sum_k A_k X G_k^T,   y_r[a] = sum_{c} sum_{(k,a,b)} v_k^{rc} g_kab x_c[b].
+ * dtype selects FP64 (double X, Y, FP64 values) or FP32 (float X, Y, FP32
+ * values, FP32 accumulation).  X and Y are mode-major device blocks with
+ * leading dimensions ldx, ldy >= n; X and Y must not overlap.
+ * Errors: SG_ERR_ARG (NULL, ld < n, overlap), SG_ERR_CUDA (launch). */
+sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t ldx, void* Y_dev,
+                   int64_t ldy, void* stream);
+
+/* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
+ * sg_apply (F may equal R for an in-place update). */
+sg_status sg_residual(sg_problem* prob, sg_dtype dtype, const void* F_dev, int64_t ldf,
+                      const void* X_dev, int64_t ldx, void* R_dev, int64_t ldr, void* stream);
+
+const char* sg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H_ */

@@ -1,0 +1,126 @@
+"""GB300 (sm_103a) stochastic Galerkin solver of arXiv 2310.14649.
+
+Python face of the C ABI in include/sg.h.  Function names follow the C
+entry points; each call only marshals arguments and checks the status code.
+Device blocks are torch CUDA tensors [P, ld] (mode-major).
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import SG_F32, SG_F64, SgError, call, dev_ptr, stream_handle
+
+__all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_indices",
+           "sg_get_triples", "sg_get_csr", "sg_get_values", "sg_get_rhs", "sg_apply",
+           "sg_residual", "SgError", "SG_F32", "SG_F64"]
+
+
+class Problem:
+    """Owning wrapper of an sg_problem handle."""
+
+    def __init__(self, handle, L):
+        self.handle = handle
+        self.L = L
+        n, P, K, nnz, T = sg_get_sizes(self)
+        self.n, self.P, self.K, self.nnzA, self.T = n, P, K, nnz, T
+
+    def close(self):
+        if self.handle:
+            sg_destroy(self)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sg_setup(N, L, p_out, q_in, sigma2=0.3, bx=0.5, by=0.5, g0=0.0, user_modes=None):
+    mesh = _lib.MeshDesc(N)
+    um = None
+    if user_modes is not None:
+        um = np.ascontiguousarray(user_modes, dtype=np.float64)
+    kl = _lib.KlDesc(sigma2, bx, by, g0, L,
+                     um.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if um is not None else None)
+    h = ctypes.c_void_p()
+    call("sg_setup", ctypes.byref(mesh), ctypes.byref(kl), p_out, q_in, ctypes.byref(h))
+    return Problem(h, L)
+
+
+def sg_destroy(prob):
+    call("sg_destroy", prob.handle)
+
+
+def sg_get_sizes(prob):
+    n, nnz, T = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    P, K = ctypes.c_int(), ctypes.c_int()
+    call("sg_get_sizes", prob.handle, ctypes.byref(n), ctypes.byref(P), ctypes.byref(K),
+         ctypes.byref(nnz), ctypes.byref(T))
+    return n.value, P.value, K.value, nnz.value, T.value
+
+
+def sg_get_multi_indices(prob, which):
+    rows = prob.P if which == 0 else prob.K
+    L = prob.L
+    out = np.zeros((rows, max(L, 0)), dtype=np.int32)
+    if L > 0:
+        call("sg_get_multi_indices", prob.handle, _lib.ptr(out, ctypes.c_int32), which)
+    return out
+
+
+def sg_get_triples(prob):
+    kab = np.zeros((prob.T, 3), dtype=np.int32)
+    num = np.zeros(prob.T, dtype=np.int64)
+    g = np.zeros(prob.T, dtype=np.float64)
+    call("sg_get_triples", prob.handle, _lib.ptr(kab, ctypes.c_int32), _lib.ptr(num, ctypes.c_int64),
+         _lib.ptr(g, ctypes.c_double))
+    return kab, num, g
+
+
+def sg_get_csr(prob):
+    rowptr = np.zeros(prob.n + 1, dtype=np.int32)
+    colidx = np.zeros(prob.nnzA, dtype=np.int32)
+    call("sg_get_csr", prob.handle, _lib.ptr(rowptr, ctypes.c_int32), _lib.ptr(colidx, ctypes.c_int32))
+    return rowptr, colidx
+
+
+def sg_get_values(prob):
+    vals = np.zeros((prob.K, prob.nnzA), dtype=np.float64)
+    call("sg_get_values", prob.handle, _lib.ptr(vals, ctypes.c_double))
+    return vals
+
+
+def sg_get_rhs(prob, F, stream=None):
+    call("sg_get_rhs", prob.handle, dev_ptr(F), F.stride(0), stream_handle(stream))
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return SG_F64
+    if t.dtype == torch.float32:
+        return SG_F32
+    raise TypeError("blocks must be float32 or float64 CUDA tensors")
+
+
+def _check_block(prob, t, name):
+    if not t.is_cuda or t.dim() != 2 or t.shape[0] != prob.P or t.stride(1) != 1 or t.shape[1] < prob.n:
+        raise ValueError("%s must be a CUDA tensor [P, ld >= n] with unit column stride" % name)
+
+
+def sg_apply(prob, X, Y, stream=None):
+    """Y = sum_k A_k X G_k^T (X, Y: [P, ld] CUDA tensors, same dtype)."""
+    _check_block(prob, X, "X")
+    _check_block(prob, Y, "Y")
+    call("sg_apply", prob.handle, _dtype_code(X), dev_ptr(X), X.stride(0), dev_ptr(Y), Y.stride(0),
+         stream_handle(stream))
+
+
+def sg_residual(prob, F, X, R, stream=None):
+    """R = F - sum_k A_k X G_k^T."""
+    for t, nm in ((F, "F"), (X, "X"), (R, "R")):
+        _check_block(prob, t, nm)
+    call("sg_residual", prob.handle, _dtype_code(X), dev_ptr(F), F.stride(0), dev_ptr(X), X.stride(0),
+         dev_ptr(R), R.stride(0), stream_handle(stream))

@@ -1,0 +1,98 @@
+"""ctypes binding of libsg (C ABI declared in include/sg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Device blocks are torch CUDA tensors of shape [P, ld] (mode-major,
+row a = PCE mode a, contiguous), passed by data pointer with the current
+torch stream.  If libsg.so is missing the calls raise; there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsg.so")
+
+SG_OK, SG_NOT_CONVERGED = 0, 1
+STATUS_NAMES = {0: "SG_OK", 1: "SG_NOT_CONVERGED", -1: "SG_ERR_ARG", -2: "SG_ERR_CUDA",
+                -3: "SG_ERR_NOMEM", -4: "SG_ERR_BREAKDOWN", -5: "SG_ERR_TIMEOUT",
+                -6: "SG_ERR_UNSUPPORTED"}
+SG_F64, SG_F32 = 0, 1
+
+
+class SgError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__("%s -> %s: %s" % (fn, STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int)]
+
+
+class KlDesc(ctypes.Structure):
+    _fields_ = [("sigma2", ctypes.c_double), ("bx", ctypes.c_double), ("by", ctypes.c_double),
+                ("g0", ctypes.c_double), ("L", ctypes.c_int),
+                ("user_modes", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+P_i32, P_i64, P_f64 = ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(f64)
+
+# name -> argtypes (restype is always int = sg_status, except sg_last_error)
+SIGNATURES = {
+    "sg_setup": [ctypes.POINTER(MeshDesc), ctypes.POINTER(KlDesc), ctypes.c_int, ctypes.c_int,
+                 ctypes.POINTER(vp)],
+    "sg_destroy": [vp],
+    "sg_get_sizes": [vp, P_i64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), P_i64, P_i64],
+    "sg_get_multi_indices": [vp, P_i32, ctypes.c_int],
+    "sg_get_triples": [vp, P_i32, P_i64, P_f64],
+    "sg_get_csr": [vp, P_i32, P_i32],
+    "sg_get_values": [vp, P_f64],
+    "sg_get_rhs": [vp, vp, i64, vp],
+    "sg_apply": [vp, ctypes.c_int, vp, i64, vp, i64, vp],
+    "sg_residual": [vp, ctypes.c_int, vp, i64, vp, i64, vp, i64, vp],
+}
+
+
+def lib():
+    """Load libsg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsg.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.sg_last_error.argtypes = []
+        L.sg_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(fn, status, allow=(SG_OK,)):
+    if status not in allow:
+        raise SgError(fn, status, lib().sg_last_error().decode(errors="replace"))
+    return status
+
+
+def call(name, *args, allow=(SG_OK,)):
+    return check(name, getattr(lib(), name)(*args), allow)
+
+
+def ptr(arr, ctype):
+    return arr.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def stream_handle(stream=None):
+    """cudaStream_t of a torch stream (current stream by default)."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def dev_ptr(t):
+    return ctypes.c_void_p(t.data_ptr())

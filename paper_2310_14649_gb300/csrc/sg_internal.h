@@ -1,0 +1,102 @@
+// Internal declarations of libsg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sg.h"
+
+namespace sg {
+
+void set_error(const std::string& msg);
+
+#define SG_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      ::sg::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));               \
+      return SG_ERR_CUDA;                                                                \
+    }                                                                                    \
+  } while (0)
+
+#define SG_TRY(call)                    \
+  do {                                  \
+    sg_status s_ = (call);              \
+    if (s_ != SG_OK) return s_;         \
+  } while (0)
+
+#define SG_ARG(cond, msg)               \
+  do {                                  \
+    if (!(cond)) {                      \
+      ::sg::set_error(msg);             \
+      return SG_ERR_ARG;                \
+    }                                   \
+  } while (0)
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Device buffer owned by a handle.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  sg_status alloc(size_t nbytes);
+  void free_();
+  template <typename T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// ELL ("sliced by slot") storage of a family of K matrices sharing one
+// pattern with at most S entries per row: col[s * ldr + r] and
+// val[(k * S + s) * ldr + r].  Padding entries carry col = r, value 0.
+struct Ell {
+  int S = 0;
+  int64_t n = 0, ldr = 0;
+  DevBuf col;      // int32 S x ldr
+  DevBuf v64;      // double K x S x ldr
+  DevBuf v32;      // float  K x S x ldr
+};
+
+// Triple products re-ordered by output mode a, then k, then b, split into
+// chunks of input terms [c*kc, (c+1)*kc) for the shared-memory apply.
+struct TripleTables {
+  int kc = 0, nchunk = 0;
+  DevBuf tk, tb;   // int32 T
+  DevBuf g64, g32; // T
+  DevBuf off;      // int32 P x (nchunk + 1)
+};
+
+}  // namespace sg
+
+struct sg_problem {
+  int device = 0;
+  int N = 0, L = 0, p = 0, q = 0, P = 0, K = 0;
+  int64_t n = 0, nnzA = 0, T = 0, E = 0;
+  double sigma2 = 0, bx = 0, by = 0, g0 = 0;
+  std::vector<int32_t> mi_out, mi_in;  // P x L, K x L
+  std::vector<int32_t> kab;            // T x 3, ordered k, a, b
+  std::vector<int64_t> num;            // T
+  std::vector<double> g;               // T
+  std::vector<double> gfield;          // L x E
+  std::vector<int32_t> rowptr, colidx; // shared CSR pattern
+  std::vector<double> b;               // load vector (n)
+  std::vector<double> a0;              // A_0 values on the CSR pattern (host)
+
+  sg::Ell fine;                        // A_k on the device
+  sg::TripleTables tri;
+  int64_t ld = 0;                      // internal leading dimension of blocks
+};
+
+namespace sg {
+// setup helpers (sg_setup.cpp)
+std::vector<int32_t> multi_indices(int L, int p);
+sg_status build_host(sg_problem* pr, const sg_kl_desc* kl);
+// device assembly (sg_assemble.cu)
+sg_status assemble_fine(sg_problem* pr);
+sg_status build_triple_tables(sg_problem* pr, TripleTables& t, int S);
+// apply (sg_apply.cu)
+template <typename T>
+sg_status apply_ell(const Ell& A, const TripleTables& tri, int P, int K, const T* X, int64_t ldx,
+                    const T* F, int64_t ldf, T* Y, int64_t ldy, cudaStream_t st);
+}  // namespace sg

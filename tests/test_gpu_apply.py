@@ -1,0 +1,165 @@
+"""Setup artefacts and the Galerkin operator apply through the C ABI versus
+the FP64 oracle (GPU)."""
+import numpy as np
+import pytest
+
+from oracle import galerkin, pce
+from sg_inputs import CONFIGS, random_block
+
+pytestmark = pytest.mark.gpu
+
+
+def setup_pair(N, L, p, q, sigma2=0.3, b=0.5, user_modes=None):
+    import paper_2310_14649_gb300 as sg
+    prob = sg.sg_setup(N, L, p, q, sigma2=sigma2, bx=b, by=b, user_modes=user_modes)
+    ref = galerkin.build(N, L, p, q, sigma2=sigma2, bx=b, by=b, user_modes=user_modes)
+    return prob, ref
+
+
+def to_dev(X, dtype, ld=None):
+    import torch
+    n, P = X.shape
+    ld = ld or n
+    out = torch.zeros((P, ld), dtype=dtype, device="cuda")
+    out[:, :n] = torch.from_numpy(np.ascontiguousarray(X.T)).to(dtype)
+    return out
+
+
+def from_dev(Y, n):
+    return Y[:, :n].double().cpu().numpy().T
+
+
+def bound_and_terms(ref, X):
+    """|A||X| elementwise (the oracle applied to absolute values) and the
+    largest number of products summed into one output entry."""
+    absprob = galerkin.Problem(**{**ref.__dict__, "vals": np.abs(ref.vals), "g": np.abs(ref.g)})
+    Yb = galerkin.apply(absprob, np.abs(X))
+    per_a = np.bincount(ref.kab[:, 1], minlength=ref.P).max()
+    row_len = np.diff(ref.rowptr).max()
+    return Yb, int(per_a * row_len)
+
+
+def gamma(m, u):
+    """Deterministic rounding bound gamma_m = m u / (1 - m u) for a sum of m
+    products whose factors carry at most 3 extra roundings (value, g, x)."""
+    m = m + 3
+    return m * u / (1 - m * u)
+
+
+U64, U32 = 2.0 ** -53, 2.0 ** -24
+
+
+# integer artefacts must match the oracle bit for bit
+@pytest.mark.parametrize("N,L,p,q", [(32, 2, 2, 4), (20, 3, 2, 4), (17, 1, 3, 6), (64, 4, 3, 6)])
+def test_integer_artefacts_bit_exact(gpu, N, L, p, q):
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(N, L, p, q)
+    assert (prob.n, prob.P, prob.K, prob.nnzA, prob.T) == (ref.n, ref.P, ref.K, len(ref.colidx), len(ref.g))
+    assert np.array_equal(sg.sg_get_multi_indices(prob, 0), pce.multi_indices(L, p))
+    assert np.array_equal(sg.sg_get_multi_indices(prob, 1), pce.multi_indices(L, q))
+    kab, num, g = sg.sg_get_triples(prob)
+    assert np.array_equal(kab, ref.kab) and np.array_equal(num, ref.num)
+    assert np.max(np.abs(g - ref.g) / np.abs(ref.g)) < 4 * U64
+    rowptr, colidx = sg.sg_get_csr(prob)
+    assert np.array_equal(rowptr, ref.rowptr) and np.array_equal(colidx, ref.colidx)
+
+
+@pytest.mark.parametrize("N,L,p,q,s2,b", [(32, 2, 2, 4, 0.3, 0.5), (24, 3, 2, 4, 0.5, 0.2)])
+def test_stiffness_values(gpu, N, L, p, q, s2, b):
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(N, L, p, q, s2, b)
+    vals = sg.sg_get_values(prob)
+    scale = np.abs(ref.vals[0]).max()
+    assert np.max(np.abs(vals - ref.vals)) < 1e-13 * scale
+
+
+def check_apply(prob, ref, X, dtype, ld=None):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    Xd = to_dev(X, dtype, ld)
+    Yd = torch.full_like(Xd, float("nan"))
+    sg.sg_apply(prob, Xd, Yd)
+    torch.cuda.synchronize()
+    Xq = from_dev(Xd, ref.n)           # the inputs the kernel actually saw
+    Yref = galerkin.apply(ref, Xq)
+    Yb, m = bound_and_terms(ref, Xq)
+    u = U64 if dtype == torch.float64 else U32
+    err = np.abs(from_dev(Yd, ref.n) - Yref)
+    assert np.all(err <= gamma(m, u) * Yb + 1e-300), (err / np.maximum(Yb, 1e-300)).max()
+    return Yd
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("N,L,p,q", [(32, 2, 2, 4), (33, 3, 3, 6), (2, 2, 1, 2), (9, 0, 0, 0), (40, 1, 5, 10)])
+def test_apply_vs_oracle(gpu, dt, N, L, p, q):
+    import torch
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    prob, ref = setup_pair(N, L, p, q)
+    X = random_block(ref.n, ref.P, seed=3)
+    check_apply(prob, ref, X, dtype)
+    # ragged leading dimension and a second, different input
+    check_apply(prob, ref, random_block(ref.n, ref.P, seed=4), dtype, ld=ref.n + 37)
+
+
+def test_residual_in_place(gpu):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(32, 2, 2, 4)
+    X = random_block(ref.n, ref.P, seed=8)
+    F = random_block(ref.n, ref.P, seed=9)
+    Xd, Fd = to_dev(X, torch.float64), to_dev(F, torch.float64)
+    sg.sg_residual(prob, Fd, Xd, Fd)
+    torch.cuda.synchronize()
+    R = from_dev(Fd, ref.n)
+    Rref = F - galerkin.apply(ref, X)
+    Yb, m = bound_and_terms(ref, X)
+    assert np.all(np.abs(R - Rref) <= gamma(m + 1, U64) * (Yb + np.abs(F)))
+
+
+def test_rhs(gpu):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(16, 2, 2, 4)
+    F = torch.full((ref.P, ref.n + 5), 7.0, dtype=torch.float64, device="cuda")
+    sg.sg_get_rhs(prob, F)
+    Fh = F.cpu().numpy()
+    assert np.max(np.abs(Fh[0, :ref.n] - ref.b)) <= 4 * U64 * ref.b.max()
+    assert np.all(Fh[1:] == 0) and np.all(Fh[0, ref.n:] == 0)
+
+
+def test_apply_full_size_sampled_rows(gpu):
+    """256x256 mesh, L=4, p=3 (P=35), q=6 (K=210): sampled output rows
+    against the entrywise oracle definition, FP64 and FP32."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    c = CONFIGS["poisson256_L4_p3"]
+    prob, ref = setup_pair(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"])
+    rows = np.unique(np.concatenate([[0, 1, ref.n - 1, ref.n // 2],
+                                     np.random.default_rng(0).integers(0, ref.n, 60)]))
+    X = random_block(ref.n, ref.P, seed=21)
+    for dtype, u in ((torch.float64, U64), (torch.float32, U32)):
+        Xd = to_dev(X, dtype)
+        Yd = torch.empty_like(Xd)
+        sg.sg_apply(prob, Xd, Yd)
+        torch.cuda.synchronize()
+        Xq = from_dev(Xd, ref.n)
+        Y = from_dev(Yd, ref.n)[rows]
+        Yref = galerkin.apply_rows(ref, Xq, rows)
+        absref = galerkin.Problem(**{**ref.__dict__, "vals": np.abs(ref.vals), "g": np.abs(ref.g)})
+        Yb = galerkin.apply_rows(absref, np.abs(Xq), rows)
+        m = int(np.bincount(ref.kab[:, 1]).max() * 5)
+        assert np.all(np.abs(Y - Yref) <= gamma(m, u) * Yb)
+
+
+def test_bad_arguments(gpu):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(8, 1, 1, 2)
+    X = torch.zeros((ref.P, ref.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_apply(prob, X, X)          # aliasing input and output
+    assert e.value.status == -1
+    from paper_2310_14649_gb300 import _lib
+    Y = torch.zeros_like(X)
+    st = _lib.lib().sg_apply(prob.handle, 0, _lib.dev_ptr(X), ref.n - 1, _lib.dev_ptr(Y), ref.n, None)
+    assert st == -1
