@@ -130,6 +130,100 @@ sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t 
 sg_status sg_residual(sg_problem* prob, sg_dtype dtype, const void* F_dev, int64_t ldf,
                       const void* X_dev, int64_t ldx, void* R_dev, int64_t ldr, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Two-level preconditioner (Sec. 3, Eqs. RASsto, coarse, RAS_2L; variant
+ * 2GV3: the coarse problem is solved by an inner GMRES preconditioned by
+ * AMG).  The cycle applied to a residual r is
+ *     z  = S r,   z += Q (r - A z),   z += S (r - A z),
+ * with Q = R_0^T A_c^{-1} R_0 (R_0^T: P1 interpolation from the nested 2h
+ * mesh, A_c = sum_k (R_0 A_k R_0^T) (x) G_k solved by GMRES + AMG to
+ * inner_rtol) and the restricted additive Schwarz smoother
+ *     S r = omega (G~^{-1} (x) I) sum_i R_i^T D_i (I (x) A_{0,i})^{-1} R_i r,
+ * where boxes are sx x sy blocks of the interior grid grown by `overlap`
+ * layers of the A_0 graph, D_i keeps owned nodes, A_{0,i} is the local mean
+ * block, G~ = sum_k (<A_k, A_0>_F / <A_0, A_0>_F) G_k is the stochastic
+ * Kronecker factor, and omega = 1 / rho(S A) (power iteration) unless given.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int sx, sy;          /* subdomain boxes per direction (>= 1)          */
+  int overlap;         /* overlap layers (0..8)                         */
+  double omega;        /* smoother damping; <= 0 = estimate             */
+  double inner_rtol;   /* coarse GMRES tolerance; <= 0 = 1e-5           */
+  int inner_max;       /* coarse GMRES iteration cap; <= 0 = 100        */
+  int smoother;        /* 0 = RAS (only value accepted)                 */
+} sg_precond_opts;
+
+/* Builds partitions, local factors, the coarse space, the AMG hierarchy,
+ * the Kronecker factor and omega.  Needs an even N >= 4.  Replaces a
+ * previous preconditioner.  Synchronous.
+ * Errors: SG_ERR_ARG (ranges), SG_ERR_NOMEM, SG_ERR_CUDA, SG_ERR_BREAKDOWN
+ * (omega estimate or Kronecker factor not finite). */
+sg_status sg_precond_setup(sg_problem* prob, const sg_precond_opts* opts, void* stream);
+
+/* omega, number of AMG levels, coarse unknowns per mode, iterations of the
+ * last inner coarse solve.  Any pointer may be NULL. */
+sg_status sg_precond_info(const sg_problem* prob, double* omega, int* amg_levels, int64_t* nc,
+                          int* inner_its_last);
+
+/* Overlapped node set of box `sub` (ascending global indices) and its owned
+ * flags (D_i).  Call with idx = owned = NULL to get the count first. */
+sg_status sg_get_partition(const sg_problem* prob, int sub, int32_t* idx, int64_t* count,
+                           int32_t* owned);
+
+/* Pattern of the coarse matrices R_0 A_k R_0^T (symbolic product). */
+sg_status sg_get_coarse_csr(const sg_problem* prob, int64_t* nc, int64_t* nnz, int32_t* rowptr,
+                            int32_t* colidx);
+
+/* Size of AMG level `level` and, for every level but the last, the
+ * aggregate id of each of its unknowns (host array of n entries). */
+sg_status sg_get_amg_level(const sg_problem* prob, int level, int64_t* n, int32_t* agg);
+
+/* Applies one piece of the preconditioner to a mode-major device block
+ * (for tests and for users composing their own solver):
+ *   0 two-level cycle z = B r        (fine -> fine)
+ *   1 smoother S r                    (fine -> fine)
+ *   2 coarse correction Q r           (fine -> fine)
+ *   3 one AMG V-cycle per mode        (coarse -> coarse)
+ *   4 coarse operator A_c x           (coarse -> coarse)
+ *   5 restriction R_0 r               (fine -> coarse)
+ *   6 interpolation R_0^T e           (coarse -> fine)
+ *   7 RAS local mean solves only      (fine -> fine)
+ * Coarse blocks have nc rows (sg_precond_info).  R and Z must not overlap. */
+sg_status sg_precond_apply(sg_problem* prob, sg_dtype dtype, int which, const void* R, int64_t ldr,
+                           void* Z, int64_t ldz, void* stream);
+
+typedef struct {
+  double rtol;        /* stop when ||F - A X|| <= rtol ||F|| (true FP64 residual) */
+  int max_it;         /* cap on outer (F)GMRES iterations in total             */
+  int restart;        /* FGMRES restart length (<= 31; <= 0 = 30)              */
+  int mode;           /* 0: FP64 FGMRES with FP64 preconditioner;
+                         1: FP32 FGMRES + FP32 preconditioner inside FP64
+                            iterative refinement (FP64 residuals)              */
+  double inner_rtol;  /* mode 1: tolerance of each FP32 solve; <= 0 = 1e-4      */
+  int max_ir;         /* mode 1: refinement steps cap; <= 0 = 20               */
+  double* hist_host;  /* optional host buffer for the residual history         */
+  int hist_cap;
+} sg_solve_opts;
+
+typedef struct {
+  int outer_it;       /* (F)GMRES iterations (all refinement steps)  */
+  int inner_it;       /* coarse GMRES iterations, summed              */
+  int ir_steps;       /* refinement corrections applied (mode 1)      */
+  int fallback_used;  /* learned smoother replaced by RAS (0 here)    */
+  int hist_len;       /* entries written to hist_host                 */
+  double relres;      /* ||F - A X|| / ||F|| in FP64 at return       */
+  double t_setup, t_solve; /* seconds (t_setup unused here)          */
+} sg_solve_info;
+
+/* Solves sum_k A_k X G_k^T = F.  F = NULL uses the load vector of
+ * sg_get_rhs.  X holds the initial guess on entry and the solution on
+ * return (FP64 device blocks).  Needs sg_precond_setup.  Synchronises the
+ * stream once per iteration to test convergence.
+ * Returns SG_OK when relres <= rtol, SG_NOT_CONVERGED (X = last iterate)
+ * when max_it is reached first, SG_ERR_BREAKDOWN on non-finite values. */
+sg_status sg_solve(sg_problem* prob, const double* F_dev, int64_t ldf, double* X_dev, int64_t ldx,
+                   const sg_solve_opts* opts, sg_solve_info* info, void* stream);
+
 const char* sg_last_error(void);
 
 #ifdef __cplusplus

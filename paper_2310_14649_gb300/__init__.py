@@ -13,7 +13,14 @@ from ._lib import SG_F32, SG_F64, SgError, call, dev_ptr, stream_handle
 
 __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_indices",
            "sg_get_triples", "sg_get_csr", "sg_get_values", "sg_get_rhs", "sg_apply",
-           "sg_residual", "SgError", "SG_F32", "SG_F64"]
+           "sg_residual", "sg_precond_setup", "sg_precond_info", "sg_get_partition",
+           "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
+           "SgError", "SG_F32", "SG_F64", "PC_TWOLEVEL", "PC_SMOOTH", "PC_COARSE", "PC_AMG",
+           "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL"]
+
+# operators of sg_precond_apply
+(PC_TWOLEVEL, PC_SMOOTH, PC_COARSE, PC_AMG, PC_COARSE_APPLY, PC_RESTRICT, PC_INTERP,
+ PC_RAS_LOCAL) = range(8)
 
 
 class Problem:
@@ -124,3 +131,75 @@ def sg_residual(prob, F, X, R, stream=None):
         _check_block(prob, t, nm)
     call("sg_residual", prob.handle, _dtype_code(X), dev_ptr(F), F.stride(0), dev_ptr(X), X.stride(0),
          dev_ptr(R), R.stride(0), stream_handle(stream))
+
+
+def sg_precond_setup(prob, sx, sy, overlap, omega=0.0, inner_rtol=0.0, inner_max=0, smoother=0,
+                     stream=None):
+    opts = _lib.PrecondOpts(sx, sy, overlap, omega, inner_rtol, inner_max, smoother)
+    call("sg_precond_setup", prob.handle, ctypes.byref(opts), stream_handle(stream))
+    prob.nc = sg_precond_info(prob)[2]
+
+
+def sg_precond_info(prob):
+    om, lev, nc, inner = ctypes.c_double(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+    call("sg_precond_info", prob.handle, ctypes.byref(om), ctypes.byref(lev), ctypes.byref(nc),
+         ctypes.byref(inner))
+    return om.value, lev.value, nc.value, inner.value
+
+
+def sg_get_partition(prob, sub):
+    cnt = ctypes.c_int64()
+    call("sg_get_partition", prob.handle, sub, None, ctypes.byref(cnt), None)
+    idx = np.zeros(cnt.value, dtype=np.int32)
+    own = np.zeros(cnt.value, dtype=np.int32)
+    call("sg_get_partition", prob.handle, sub, _lib.ptr(idx, ctypes.c_int32), ctypes.byref(cnt),
+         _lib.ptr(own, ctypes.c_int32))
+    return idx, own
+
+
+def sg_get_coarse_csr(prob):
+    nc, nnz = ctypes.c_int64(), ctypes.c_int64()
+    call("sg_get_coarse_csr", prob.handle, ctypes.byref(nc), ctypes.byref(nnz), None, None)
+    rp = np.zeros(nc.value + 1, dtype=np.int32)
+    ci = np.zeros(nnz.value, dtype=np.int32)
+    call("sg_get_coarse_csr", prob.handle, None, None, _lib.ptr(rp, ctypes.c_int32), _lib.ptr(ci, ctypes.c_int32))
+    return rp, ci
+
+
+def sg_get_amg_level(prob, level):
+    n = ctypes.c_int64()
+    call("sg_get_amg_level", prob.handle, level, ctypes.byref(n), None)
+    agg = np.full(n.value, -1, dtype=np.int32)
+    call("sg_get_amg_level", prob.handle, level, ctypes.byref(n), _lib.ptr(agg, ctypes.c_int32))
+    return n.value, agg
+
+
+def sg_precond_apply(prob, which, R, Z, stream=None):
+    """Z = op(R) for one piece of the two-level preconditioner (PC_*)."""
+    if not (R.is_cuda and Z.is_cuda and R.dtype == Z.dtype and R.stride(1) == 1 and Z.stride(1) == 1):
+        raise ValueError("R and Z must be CUDA tensors [P, ld] of one dtype")
+    call("sg_precond_apply", prob.handle, _dtype_code(R), which, dev_ptr(R), R.stride(0), dev_ptr(Z),
+         Z.stride(0), stream_handle(stream))
+
+
+def sg_solve(prob, X, F=None, rtol=1e-8, max_it=500, restart=30, mode=0, inner_rtol=0.0, max_ir=0,
+             hist_cap=256, stream=None, allow_not_converged=False):
+    """Solve sum_k A_k X G_k^T = F (F None: the load vector).  X (FP64, [P, ld])
+    holds the initial guess and receives the solution.  Returns a dict of
+    the solve info (and the residual history)."""
+    import torch
+    _check_block(prob, X, "X")
+    if X.dtype != torch.float64 or (F is not None and F.dtype != torch.float64):
+        raise TypeError("sg_solve works on FP64 blocks")
+    hist = np.zeros(max(hist_cap, 1), dtype=np.float64)
+    opts = _lib.SolveOpts(rtol, max_it, restart, mode, inner_rtol, max_ir,
+                          hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), hist_cap)
+    info = _lib.SolveInfo()
+    allow = (0, 1) if allow_not_converged else (0,)
+    st = call("sg_solve", prob.handle, dev_ptr(F) if F is not None else None,
+              F.stride(0) if F is not None else 0, dev_ptr(X), X.stride(0), ctypes.byref(opts),
+              ctypes.byref(info), stream_handle(stream), allow=allow)
+    out = {f: getattr(info, f) for f, _ in _lib.SolveInfo._fields_}
+    out["hist"] = hist[:info.hist_len].copy()
+    out["status"] = st
+    return out

@@ -36,6 +36,24 @@ class KlDesc(ctypes.Structure):
                 ("user_modes", ctypes.POINTER(ctypes.c_double))]
 
 
+class PrecondOpts(ctypes.Structure):
+    _fields_ = [("sx", ctypes.c_int), ("sy", ctypes.c_int), ("overlap", ctypes.c_int),
+                ("omega", ctypes.c_double), ("inner_rtol", ctypes.c_double),
+                ("inner_max", ctypes.c_int), ("smoother", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("restart", ctypes.c_int),
+                ("mode", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_ir", ctypes.c_int),
+                ("hist_host", ctypes.POINTER(ctypes.c_double)), ("hist_cap", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("outer_it", ctypes.c_int), ("inner_it", ctypes.c_int), ("ir_steps", ctypes.c_int),
+                ("fallback_used", ctypes.c_int), ("hist_len", ctypes.c_int),
+                ("relres", ctypes.c_double), ("t_setup", ctypes.c_double), ("t_solve", ctypes.c_double)]
+
+
 _lib = None
 vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 P_i32, P_i64, P_f64 = ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(f64)
@@ -53,6 +71,13 @@ SIGNATURES = {
     "sg_get_rhs": [vp, vp, i64, vp],
     "sg_apply": [vp, ctypes.c_int, vp, i64, vp, i64, vp],
     "sg_residual": [vp, ctypes.c_int, vp, i64, vp, i64, vp, i64, vp],
+    "sg_precond_setup": [vp, ctypes.POINTER(PrecondOpts), vp],
+    "sg_precond_info": [vp, P_f64, ctypes.POINTER(ctypes.c_int), P_i64, ctypes.POINTER(ctypes.c_int)],
+    "sg_get_partition": [vp, ctypes.c_int, P_i32, P_i64, P_i32],
+    "sg_get_coarse_csr": [vp, P_i64, P_i64, P_i32, P_i32],
+    "sg_get_amg_level": [vp, ctypes.c_int, P_i64, P_i32],
+    "sg_precond_apply": [vp, ctypes.c_int, ctypes.c_int, vp, i64, vp, i64, vp],
+    "sg_solve": [vp, vp, i64, vp, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
 }
 
 

@@ -54,6 +54,7 @@ sg_status sg_setup(const sg_mesh_desc* mesh, const sg_kl_desc* kl, int p_out, in
 
 sg_status sg_destroy(sg_problem* pr) {
   if (!pr) return SG_OK;
+  solver_free(pr);
   pr->fine.col.free_();
   pr->fine.v64.free_();
   pr->fine.v32.free_();

@@ -47,6 +47,8 @@ struct DevBuf {
   template <typename T> T* as() const { return static_cast<T*>(ptr); }
 };
 
+template <typename T> inline T* dp(const DevBuf& b) { return static_cast<T*>(b.ptr); }
+
 // ELL ("sliced by slot") storage of a family of K matrices sharing one
 // pattern with at most S entries per row: col[s * ldr + r] and
 // val[(k * S + s) * ldr + r].  Padding entries carry col = r, value 0.
@@ -57,6 +59,9 @@ struct Ell {
   DevBuf v64;      // double K x S x ldr
   DevBuf v32;      // float  K x S x ldr
 };
+
+struct SolverState;
+void solver_free(sg_problem* pr);
 
 // Triple products re-ordered by output mode a, then k, then b, split into
 // chunks of input terms [c*kc, (c+1)*kc) for the shared-memory apply.
@@ -86,6 +91,7 @@ struct sg_problem {
   sg::Ell fine;                        // A_k on the device
   sg::TripleTables tri;
   int64_t ld = 0;                      // internal leading dimension of blocks
+  sg::SolverState* solver = nullptr;   // preconditioner + solver workspaces
 };
 
 namespace sg {

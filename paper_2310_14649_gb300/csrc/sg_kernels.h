@@ -1,0 +1,68 @@
+// Launch wrappers shared between the translation units of libsg.
+#pragma once
+
+#include <functional>
+
+#include "sg_solver.h"
+
+namespace sg {
+
+// AMG level work buffers ([P][ld_l] blocks per level).
+template <typename T>
+struct AmgWork {
+  std::vector<T*> b, x, t;
+};
+
+template <typename T>
+sg_status spmm(const DevCsr& A, const T* X, int64_t ldx, const T* B, int64_t ldb, T* Y, int64_t ldy, int P,
+               int op, cudaStream_t st);
+template <typename T>
+sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld, T* Z, cudaStream_t st,
+                    bool transform);
+template <typename T>
+sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st);
+template <typename T>
+sg_status amg_vcycle(const Precond& pc, AmgWork<T>& w, int P, cudaStream_t st);
+sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w);
+
+// ---- vector kernels (sg_krylov.cu) ----
+// Device-resident scalar state of one (F)GMRES cycle.
+struct GmresState {
+  double* H;      // (m+1) x m, column-major; upper triangle R after rotations
+  double* cs;     // m
+  double* sn;     // m
+  double* g;      // m+1
+  double* y;      // m
+  double* hsum;   // 2 (m+1): CGS2 coefficients of the two passes
+  double* scal;   // [0] norm^2 of w, [1] h_{j+1,j}, [2] estimate |g_{j+1}|, [3] beta, [4] flags
+};
+
+template <typename T>
+sg_status vec_norm2(const T* x, int64_t len, double* out, double* partial, unsigned* counter, cudaStream_t st);
+template <typename T>
+sg_status vec_mdot(const T* V, int64_t stride, int nv, const T* w, int64_t len, double* out, double* partial,
+                   unsigned* counter, cudaStream_t st);
+template <typename T>
+sg_status vec_maxpy_mdot(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
+                         double* partial, unsigned* counter, cudaStream_t st);
+template <typename T>
+sg_status vec_maxpy_norm(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
+                         double* partial, unsigned* counter, cudaStream_t st);
+// y = x * (1 / *den) (den on the device; sqrt taken when take_sqrt)
+template <typename T>
+sg_status vec_scale_by(const T* x, T* y, int64_t len, const double* den, bool take_sqrt, cudaStream_t st);
+// x += sum_i coef[i] * V_i
+template <typename T>
+sg_status vec_axpy_multi(const T* V, int64_t stride, int nv, const double* coef, T* x, int64_t len,
+                         cudaStream_t st);
+// y = x (with type conversion) and y = alpha * x
+template <typename Ti, typename To>
+sg_status vec_convert(const Ti* x, To* y, int64_t len, const double* scale_num, const double* scale_den,
+                      cudaStream_t st);
+// x64 += s * double(d)   (s on the device)
+sg_status vec_add_scaled_f32(double* x, const float* d, int64_t len, const double* s, cudaStream_t st);
+sg_status gmres_init(GmresState s, int m, const double* beta, cudaStream_t st);
+sg_status gmres_givens(GmresState s, int m, int j, double* host_est, cudaStream_t st);
+sg_status gmres_backsolve(GmresState s, int m, int k, cudaStream_t st);
+
+}  // namespace sg

@@ -1,0 +1,318 @@
+// Krylov building blocks (Sec. 3: FGMRES outer solver, inner GMRES on the
+// coarse problem): fused multi-vector dot products and updates for
+// classical Gram-Schmidt with one re-orthogonalisation (CGS2), the Givens
+// update of the Hessenberg column and the triangular solve, all on the
+// device.  Dot products accumulate in FP64 across threads; for FP32 vectors
+// each thread first sums its few products in FP32.
+#include <cmath>
+
+#include "sg_kernels.h"
+
+namespace sg {
+
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 2 * 152;
+constexpr int kMaxV = 32;  // vectors per fused pass
+
+template <typename T> struct Acc;
+template <> struct Acc<double> { using type = double; };
+template <> struct Acc<float> { using type = float; };
+
+// block-reduce nv values (in registers) into partial[blockIdx * nv + i];
+// the last block to finish sums the partials into out[i] and resets the
+// counter (threadfence reduction).
+template <int NV>
+__device__ void block_reduce_finish(double (&v)[NV], int nv, double* __restrict__ partial,
+                                    unsigned* __restrict__ counter, double* __restrict__ out) {
+  __shared__ double red[kRedThreads / 32][kMaxV];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    if (i >= nv) break;
+    double x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[wid][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double x = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) x += red[w][threadIdx.x];
+    partial[blockIdx.x * nv + threadIdx.x] = x;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    for (int i = wid; i < nv; i += kRedThreads / 32) {
+      double x = 0.0;
+      for (int b = lane; b < gridDim.x; b += 32) x += partial[b * nv + i];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) out[i] = x;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// mode 0: out = V^T w
+// mode 1: w -= V h; out = V^T w
+// mode 2: w -= V h; out[0] = w^T w
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_multi(const T* __restrict__ V, int64_t stride, int nv,
+                                                       const double* __restrict__ h, T* __restrict__ w, int64_t len,
+                                                       int mode, double* __restrict__ partial,
+                                                       unsigned* __restrict__ counter, double* __restrict__ out) {
+  using A = typename Acc<T>::type;
+  double tot[kMaxV];
+  A loc[kMaxV];
+  T hc[kMaxV];
+#pragma unroll
+  for (int i = 0; i < kMaxV; ++i) {
+    tot[i] = 0.0;
+    loc[i] = A(0);
+    hc[i] = (mode > 0 && i < nv) ? T(h[i]) : T(0);
+  }
+  int cnt = 0;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x) {
+    T we = w[e];
+    if (mode > 0) {
+#pragma unroll
+      for (int i = 0; i < kMaxV; ++i)
+        if (i < nv) we -= hc[i] * V[int64_t(i) * stride + e];
+      w[e] = we;
+    }
+    if (mode == 2) {
+      loc[0] += A(we) * A(we);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kMaxV; ++i)
+        if (i < nv) loc[i] += A(V[int64_t(i) * stride + e]) * A(we);
+    }
+    if (++cnt == 8) {  // flush the short FP32 partial sums into FP64
+#pragma unroll
+      for (int i = 0; i < kMaxV; ++i) {
+        tot[i] += double(loc[i]);
+        loc[i] = A(0);
+      }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kMaxV; ++i) tot[i] += double(loc[i]);
+  block_reduce_finish<kMaxV>(tot, mode == 2 ? 1 : nv, partial, counter, out);
+}
+
+template <typename T>
+__global__ void k_scale_by(const T* __restrict__ x, T* __restrict__ y, int64_t len, const double* __restrict__ den,
+                           bool take_sqrt) {
+  double d = *den;
+  if (take_sqrt) d = sqrt(d);
+  const T s = T(d != 0.0 ? 1.0 / d : 0.0);
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x)
+    y[e] = x[e] * s;
+}
+
+template <typename T>
+__global__ void k_axpy_multi(const T* __restrict__ V, int64_t stride, int nv, const double* __restrict__ coef,
+                             T* __restrict__ x, int64_t len) {
+  T c[kMaxV];
+#pragma unroll
+  for (int i = 0; i < kMaxV; ++i) c[i] = i < nv ? T(coef[i]) : T(0);
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x) {
+    T acc = x[e];
+#pragma unroll
+    for (int i = 0; i < kMaxV; ++i)
+      if (i < nv) acc += c[i] * V[int64_t(i) * stride + e];
+    x[e] = acc;
+  }
+}
+
+template <typename Ti, typename To>
+__global__ void k_convert(const Ti* __restrict__ x, To* __restrict__ y, int64_t len, const double* __restrict__ num,
+                          const double* __restrict__ den) {
+  double s = 1.0;
+  if (num) s *= *num;
+  if (den) s /= sqrt(*den);
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x)
+    y[e] = To(double(x[e]) * s);
+}
+
+__global__ void k_add_scaled_f32(double* __restrict__ x, const float* __restrict__ d, int64_t len,
+                                 const double* __restrict__ s2) {
+  const double s = sqrt(*s2);
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x)
+    x[e] += s * double(d[e]);
+}
+
+__global__ void k_gmres_init(GmresState s, int m, const double* beta2) {
+  const double beta = sqrt(*beta2);
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) s.g[i] = i == 0 ? beta : 0.0;
+  if (threadIdx.x == 0) {
+    s.scal[2] = beta;
+    s.scal[3] = beta;
+    s.scal[4] = 0.0;
+  }
+}
+
+// Column j of the Hessenberg matrix from the two CGS passes, previous
+// rotations, new rotation, residual estimate |g_{j+1}|.
+__global__ void k_gmres_givens(GmresState s, int m, int j, double* host_est) {
+  if (threadIdx.x != 0) return;
+  double* col = s.H + int64_t(j) * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = s.hsum[i] + s.hsum[(m + 1) + i];
+  const double hn = sqrt(s.scal[0]);
+  col[j + 1] = hn;
+  s.scal[1] = hn;
+  for (int i = 0; i < j; ++i) {
+    double t = s.cs[i] * col[i] + s.sn[i] * col[i + 1];
+    col[i + 1] = -s.sn[i] * col[i] + s.cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  double den = hypot(col[j], col[j + 1]);
+  double c = den != 0.0 ? col[j] / den : 1.0, sn = den != 0.0 ? col[j + 1] / den : 0.0;
+  s.cs[j] = c;
+  s.sn[j] = sn;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  s.g[j + 1] = -sn * s.g[j];
+  s.g[j] = c * s.g[j];
+  const double est = fabs(s.g[j + 1]);
+  s.scal[2] = est;
+  bool bad = !isfinite(est) || !isfinite(hn) || !isfinite(den);
+  s.scal[4] = bad ? 1.0 : 0.0;
+  if (host_est) {
+    host_est[0] = est;
+    host_est[1] = hn;
+    host_est[2] = bad ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_gmres_backsolve(GmresState s, int m, int k) {
+  if (threadIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = s.g[i];
+    for (int c = i + 1; c < k; ++c) acc -= s.H[int64_t(c) * (m + 1) + i] * s.y[c];
+    double d = s.H[int64_t(i) * (m + 1) + i];
+    s.y[i] = d != 0.0 ? acc / d : 0.0;
+  }
+}
+
+inline unsigned grid_for(int64_t len) {
+  int64_t b = (len + 255) / 256;
+  return unsigned(b < 4 * 152 ? (b > 0 ? b : 1) : 4 * 152);
+}
+
+}  // namespace
+
+template <typename T>
+sg_status vec_mdot(const T* V, int64_t stride, int nv, const T* w, int64_t len, double* out, double* partial,
+                   unsigned* counter, cudaStream_t st) {
+  if (nv > kMaxV) {
+    set_error("vec_mdot: too many vectors");
+    return SG_ERR_ARG;
+  }
+  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, nullptr, const_cast<T*>(w), len, 0, partial, counter,
+                                                 out);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status vec_maxpy_mdot(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
+                         double* partial, unsigned* counter, cudaStream_t st) {
+  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, h, w, len, 1, partial, counter, out);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status vec_maxpy_norm(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
+                         double* partial, unsigned* counter, cudaStream_t st) {
+  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, h, w, len, 2, partial, counter, out);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status vec_norm2(const T* x, int64_t len, double* out, double* partial, unsigned* counter, cudaStream_t st) {
+  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, 0, 0, nullptr, const_cast<T*>(x), len, 2, partial, counter, out);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status vec_scale_by(const T* x, T* y, int64_t len, const double* den, bool take_sqrt, cudaStream_t st) {
+  k_scale_by<T><<<grid_for(len), 256, 0, st>>>(x, y, len, den, take_sqrt);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status vec_axpy_multi(const T* V, int64_t stride, int nv, const double* coef, T* x, int64_t len,
+                         cudaStream_t st) {
+  for (int i0 = 0; i0 < nv; i0 += kMaxV) {
+    int cnt = nv - i0 < kMaxV ? nv - i0 : kMaxV;
+    k_axpy_multi<T><<<grid_for(len), 256, 0, st>>>(V + int64_t(i0) * stride, stride, cnt, coef + i0, x, len);
+    SG_CUDA(cudaGetLastError());
+  }
+  return SG_OK;
+}
+
+template <typename Ti, typename To>
+sg_status vec_convert(const Ti* x, To* y, int64_t len, const double* num, const double* den, cudaStream_t st) {
+  k_convert<Ti, To><<<grid_for(len), 256, 0, st>>>(x, y, len, num, den);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+sg_status vec_add_scaled_f32(double* x, const float* d, int64_t len, const double* s2, cudaStream_t st) {
+  k_add_scaled_f32<<<grid_for(len), 256, 0, st>>>(x, d, len, s2);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+sg_status gmres_init(GmresState s, int m, const double* beta2, cudaStream_t st) {
+  k_gmres_init<<<1, 64, 0, st>>>(s, m, beta2);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+sg_status gmres_givens(GmresState s, int m, int j, double* host_est, cudaStream_t st) {
+  k_gmres_givens<<<1, 32, 0, st>>>(s, m, j, host_est);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+sg_status gmres_backsolve(GmresState s, int m, int k, cudaStream_t st) {
+  k_gmres_backsolve<<<1, 32, 0, st>>>(s, m, k);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+#define INST(T)                                                                                                   \
+  template sg_status vec_mdot<T>(const T*, int64_t, int, const T*, int64_t, double*, double*, unsigned*,         \
+                                 cudaStream_t);                                                                   \
+  template sg_status vec_maxpy_mdot<T>(const T*, int64_t, int, const double*, T*, int64_t, double*, double*,     \
+                                       unsigned*, cudaStream_t);                                                  \
+  template sg_status vec_maxpy_norm<T>(const T*, int64_t, int, const double*, T*, int64_t, double*, double*,     \
+                                       unsigned*, cudaStream_t);                                                  \
+  template sg_status vec_norm2<T>(const T*, int64_t, double*, double*, unsigned*, cudaStream_t);                 \
+  template sg_status vec_scale_by<T>(const T*, T*, int64_t, const double*, bool, cudaStream_t);                  \
+  template sg_status vec_axpy_multi<T>(const T*, int64_t, int, const double*, T*, int64_t, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+template sg_status vec_convert<double, float>(const double*, float*, int64_t, const double*, const double*,
+                                              cudaStream_t);
+template sg_status vec_convert<float, double>(const float*, double*, int64_t, const double*, const double*,
+                                              cudaStream_t);
+template sg_status vec_convert<double, double>(const double*, double*, int64_t, const double*, const double*,
+                                               cudaStream_t);
+template sg_status vec_convert<float, float>(const float*, float*, int64_t, const double*, const double*,
+                                             cudaStream_t);
+
+}  // namespace sg

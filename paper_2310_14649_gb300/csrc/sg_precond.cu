@@ -1,0 +1,337 @@
+// Device side of the two-grid preconditioner (Sec. 3, Eqs. RASsto, coarse,
+// RAS_2L): restricted additive Schwarz local solves, the Kronecker
+// stochastic factor, 2h transfer, Galerkin coarse values, AMG V-cycle.
+#include <algorithm>
+#include <cmath>
+
+#include "sg_kernels.h"
+#include "sg_solver.h"
+
+namespace sg {
+
+namespace {
+
+constexpr int kOwnedBit = 1 << 30;
+constexpr int kIdxMask = kOwnedBit - 1;
+
+// ---------------------------------------------------------------------------
+// RAS local solve: z_owned = (A_{0,i}^{-1} R_i r)_owned for every box i and
+// every PCE mode, with the block-tridiagonal Cholesky factor of A_{0,i}:
+//   forward  y_j = Linv_j (r_j - Loff_j y_{j-1})
+//   backward x_j = Linv_j^T (y_j - Loff_{j+1}^T x_{j+1})
+// One CTA per (box, chunk of MC modes); the local block lives in shared
+// memory as y[line][slot][mode] with a padded mode stride (MC + 1).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__ Z, int P, int MC,
+                            int W, int Lm, const int* __restrict__ nlines, const int* __restrict__ gidx,
+                            const T* __restrict__ linv, const T* __restrict__ loff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int MS = MC + 1;
+  T* y = reinterpret_cast<T*>(smem_raw);  // [Lm * W][MS]
+  T* s = y + size_t(Lm) * W * MS;         // [W][MS]
+  const int box = blockIdx.x, a0 = blockIdx.y * MC;
+  const int nl = nlines[box];
+  const int* gbox = gidx + size_t(box) * Lm * W;
+  const T* Li = linv + size_t(box) * Lm * W * W;
+  const T* Lo = loff + size_t(box) * Lm * W * W;
+  const int nthr = blockDim.x;
+  // gather (nodes fastest across threads)
+  const int nslot = nl * W;
+  for (int e = threadIdx.x; e < nslot * MC; e += nthr) {
+    int a = e / nslot, q = e - a * nslot;
+    int g = gbox[q];
+    T v = T(0);
+    if (g >= 0 && a0 + a < P) v = R[int64_t(a0 + a) * ld + (g & kIdxMask)];
+    y[q * MS + a] = v;
+  }
+  __syncthreads();
+  const int a = threadIdx.x % MC, grp = threadIdx.x / MC, ngrp = nthr / MC;
+  const bool act = grp < ngrp;
+  // forward sweep
+  for (int j = 0; j < nl; ++j) {
+    if (act) {
+      const T* Lof = Lo + size_t(j) * W * W;
+      for (int t = grp; t < W; t += ngrp) {
+        T acc = y[(j * W + t) * MS + a];
+        if (j > 0)
+          for (int u = 0; u < W; ++u) acc -= Lof[t * W + u] * y[((j - 1) * W + u) * MS + a];
+        s[t * MS + a] = acc;
+      }
+    }
+    __syncthreads();
+    if (act) {
+      const T* Lin = Li + size_t(j) * W * W;
+      for (int t = grp; t < W; t += ngrp) {
+        T acc = T(0);
+        for (int u = 0; u <= t; ++u) acc += Lin[t * W + u] * s[u * MS + a];
+        y[(j * W + t) * MS + a] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  // backward sweep
+  for (int j = nl - 1; j >= 0; --j) {
+    if (act) {
+      const T* Lof = Lo + size_t(j + 1) * W * W;
+      for (int t = grp; t < W; t += ngrp) {
+        T acc = y[(j * W + t) * MS + a];
+        if (j + 1 < nl)
+          for (int u = 0; u < W; ++u) acc -= Lof[u * W + t] * y[((j + 1) * W + u) * MS + a];
+        s[t * MS + a] = acc;
+      }
+    }
+    __syncthreads();
+    if (act) {
+      const T* Lin = Li + size_t(j) * W * W;
+      for (int t = grp; t < W; t += ngrp) {
+        T acc = T(0);
+        for (int u = t; u < W; ++u) acc += Lin[u * W + t] * s[u * MS + a];
+        y[(j * W + t) * MS + a] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  // scatter owned nodes
+  for (int e = threadIdx.x; e < nslot * MC; e += nthr) {
+    int aa = e / nslot, q = e - aa * nslot;
+    int g = gbox[q];
+    if (g >= 0 && (g & kOwnedBit) && a0 + aa < P) Z[int64_t(a0 + aa) * ld + (g & kIdxMask)] = y[q * MS + aa];
+  }
+}
+
+// In-place per-node transform z_r <- M z_r with a P x P matrix M (the
+// stochastic factor omega G~^{-1}).  128 nodes per CTA staged in shared memory.
+template <typename T>
+__global__ void k_node_transform(T* __restrict__ Z, int64_t ld, int64_t n, int P, const T* __restrict__ M) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ms = reinterpret_cast<T*>(smem_raw);  // P x P
+  T* zs = Ms + size_t(P) * P;               // P x 128
+  for (int e = threadIdx.x; e < P * P; e += blockDim.x) Ms[e] = M[e];
+  const int64_t r = int64_t(blockIdx.x) * 128 + threadIdx.x;
+  const bool valid = r < n;
+  for (int b = 0; b < P; ++b) zs[b * 128 + threadIdx.x] = valid ? Z[int64_t(b) * ld + r] : T(0);
+  __syncthreads();
+  if (!valid) return;
+  for (int a = 0; a < P; ++a) {
+    T acc = T(0);
+    for (int b = 0; b < P; ++b) acc += Ms[a * P + b] * zs[b * 128 + threadIdx.x];
+    Z[int64_t(a) * ld + r] = acc;
+  }
+}
+
+// Coarse ELL values of all K terms from the fine ELL values by the RAP plan.
+__global__ void k_coarse_values(const double* __restrict__ fine, int64_t fine_kstride, const int* __restrict__ rp,
+                                const int64_t* __restrict__ src, const double* __restrict__ w, int64_t npos,
+                                int K, double* __restrict__ v64, float* __restrict__ v32) {
+  int64_t total = npos * K;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    int k = int(t / npos);
+    int64_t q = t - int64_t(k) * npos;
+    const double* fk = fine + int64_t(k) * fine_kstride;
+    double acc = 0.0;
+    for (int u = rp[q]; u < rp[q + 1]; ++u) acc += w[u] * fk[src[u]];
+    v64[t] = acc;
+    v32[t] = float(acc);
+  }
+}
+
+// Frobenius products <A_k, A_0> over the ELL values (one CTA per k).
+__global__ void k_frob(const double* __restrict__ V, int64_t kstride, int K, double* __restrict__ out) {
+  __shared__ double red[32];
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < kstride; e += blockDim.x) acc += V[int64_t(k) * kstride + e] * V[e];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[k] = acc;
+  }
+}
+
+// CSR SpMM over P columns (mode-major blocks):
+//   op 0: Y = A X;  op 1: Y += A X;  op 2: Y = B - A X
+template <typename T>
+__global__ void k_spmm(int64_t nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                       const T* __restrict__ v, const T* __restrict__ X, int64_t ldx, const T* __restrict__ B,
+                       int64_t ldb, T* __restrict__ Y, int64_t ldy, int op) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int a = blockIdx.y;
+  if (i >= nrows) return;
+  const T* x = X + int64_t(a) * ldx;
+  T acc = T(0);
+  for (int t = rp[i]; t < rp[i + 1]; ++t) acc += v[t] * x[ci[t]];
+  T* y = Y + int64_t(a) * ldy + i;
+  if (op == 0)
+    *y = acc;
+  else if (op == 1)
+    *y += acc;
+  else
+    *y = B[int64_t(a) * ldb + i] - acc;
+}
+
+// Y = diag(d) X  (op 0)   or   Y += diag(d) X  (op 1)
+template <typename T>
+__global__ void k_diag(int64_t n, const T* __restrict__ d, const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
+                       int64_t ldy, int op) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int a = blockIdx.y;
+  if (i >= n) return;
+  T v = d[i] * X[int64_t(a) * ldx + i];
+  if (op == 0)
+    Y[int64_t(a) * ldy + i] = v;
+  else
+    Y[int64_t(a) * ldy + i] += v;
+}
+
+// Coarsest AMG level: X = A^{-1} B with the explicit FP64 inverse.
+template <typename T>
+__global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ B, int64_t ldb,
+                              T* __restrict__ X, int64_t ldx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = 0; j < n; ++j) acc += Ainv[int64_t(i) * n + j] * double(B[int64_t(a) * ldb + j]);
+  X[int64_t(a) * ldx + i] = T(acc);
+}
+
+template <typename T> const T* dv(const DevBuf& b64, const DevBuf& b32);
+template <> const double* dv<double>(const DevBuf& b64, const DevBuf&) { return b64.as<double>(); }
+template <> const float* dv<float>(const DevBuf&, const DevBuf& b32) { return b32.as<float>(); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+template <typename T>
+sg_status spmm(const DevCsr& A, const T* X, int64_t ldx, const T* B, int64_t ldb, T* Y, int64_t ldy, int P,
+               int op, cudaStream_t st) {
+  if (A.n == 0) return SG_OK;
+  dim3 grid(unsigned((A.n + 127) / 128), unsigned(P));
+  k_spmm<T><<<grid, 128, 0, st>>>(A.n, A.rowptr.as<int>(), A.col.as<int>(), dv<T>(A.v64, A.v32), X, ldx, B, ldb, Y,
+                                  ldy, op);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld, T* Z, cudaStream_t st,
+                    bool transform) {
+  const RasData& D = pc.ras;
+  const int maxmc = sizeof(T) == 8 ? 16 : 32;
+  const int nchunk = (P + maxmc - 1) / maxmc;
+  const int MC = (P + nchunk - 1) / nchunk;
+  const int ngrp = std::max(1, 256 / MC);
+  const int threads = ngrp * MC;
+  const size_t smem = (size_t(D.lmax) * D.wmax + D.wmax) * (MC + 1) * sizeof(T);
+  static bool attr[2] = {false, false};
+  if (!attr[sizeof(T) == 8]) {
+    SG_CUDA(cudaFuncSetAttribute(k_ras_local<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr[sizeof(T) == 8] = true;
+  }
+  if (smem > 227 * 1024) {
+    set_error("RAS: overlapped box too large for the shared-memory local solve");
+    return SG_ERR_UNSUPPORTED;
+  }
+  dim3 grid(unsigned(D.nbox), unsigned(nchunk));
+  k_ras_local<T><<<grid, threads, smem, st>>>(R, ld, Z, P, MC, D.wmax, D.lmax, D.d_nlines.as<int>(),
+                                              D.d_gidx.as<int>(), dv<T>(D.linv64, D.linv32),
+                                              dv<T>(D.loff64, D.loff32));
+  SG_CUDA(cudaGetLastError());
+  if (transform) SG_TRY(node_transform<T>(Z, ld, n, P, dv<T>(pc.gtinv64, pc.gtinv32), st));
+  return SG_OK;
+}
+
+template <typename T>
+sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st) {
+  const size_t smem = (size_t(P) * P + size_t(P) * 128) * sizeof(T);
+  static bool attr[2] = {false, false};
+  if (!attr[sizeof(T) == 8]) {
+    SG_CUDA(cudaFuncSetAttribute(k_node_transform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr[sizeof(T) == 8] = true;
+  }
+  k_node_transform<T><<<unsigned((n + 127) / 128), 128, smem, st>>>(Z, ld, n, P, M);
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+// One V(1,1) cycle with l1-Jacobi on every column, from a zero guess.
+// Level buffers: b (rhs), x (solution), t (temporary), each [P][ld_l].
+template <typename T>
+sg_status amg_vcycle(const Precond& pc, AmgWork<T>& w, int P, cudaStream_t st) {
+  const int nl = int(pc.amg.size());
+  for (int l = 0; l < nl - 1; ++l) {
+    const AmgLevel& L = pc.amg[l];
+    dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
+    k_diag<T><<<g, 128, 0, st>>>(L.n, dv<T>(L.dinv64, L.dinv32), w.b[l], L.ld, w.x[l], L.ld, 0);
+    SG_CUDA(cudaGetLastError());
+    SG_TRY(spmm<T>(L.A, w.x[l], L.ld, w.b[l], L.ld, w.t[l], L.ld, P, 2, st));
+    SG_TRY(spmm<T>(L.R, w.t[l], L.ld, nullptr, 0, w.b[l + 1], pc.amg[l + 1].ld, P, 0, st));
+  }
+  {
+    const AmgLevel& L = pc.amg[nl - 1];
+    dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
+    k_dense_solve<T><<<g, 128, 0, st>>>(int(L.n), pc.coarsest_inv64.as<double>(), w.b[nl - 1], L.ld, w.x[nl - 1],
+                                        L.ld);
+    SG_CUDA(cudaGetLastError());
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    const AmgLevel& L = pc.amg[l];
+    dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
+    SG_TRY(spmm<T>(L.Pm, w.x[l + 1], pc.amg[l + 1].ld, nullptr, 0, w.x[l], L.ld, P, 1, st));
+    SG_TRY(spmm<T>(L.A, w.x[l], L.ld, w.b[l], L.ld, w.t[l], L.ld, P, 2, st));
+    k_diag<T><<<g, 128, 0, st>>>(L.n, dv<T>(L.dinv64, L.dinv32), w.t[l], L.ld, w.x[l], L.ld, 1);
+    SG_CUDA(cudaGetLastError());
+  }
+  return SG_OK;
+}
+
+sg_status precond_setup_coarse_plan(sg_problem* pr, Precond& pc, const CoarsePlan& plan) {
+  CoarseData& C = pc.co;
+  const int K = pr->K, S = C.ell.S;
+  const int64_t npos = int64_t(S) * C.ldc;
+  DevBuf rp, src, w;
+  SG_TRY(rp.alloc(plan.rp.size() * 4));
+  SG_TRY(src.alloc(std::max<size_t>(1, plan.src.size()) * 8));
+  SG_TRY(w.alloc(std::max<size_t>(1, plan.w.size()) * 8));
+  SG_CUDA(cudaMemcpy(rp.ptr, plan.rp.data(), plan.rp.size() * 4, cudaMemcpyHostToDevice));
+  if (!plan.src.empty()) {
+    SG_CUDA(cudaMemcpy(src.ptr, plan.src.data(), plan.src.size() * 8, cudaMemcpyHostToDevice));
+    SG_CUDA(cudaMemcpy(w.ptr, plan.w.data(), plan.w.size() * 8, cudaMemcpyHostToDevice));
+  }
+  SG_TRY(C.ell.v64.alloc(size_t(K) * npos * 8));
+  SG_TRY(C.ell.v32.alloc(size_t(K) * npos * 4));
+  k_coarse_values<<<4 * 152, 256>>>(pr->fine.v64.as<double>(), int64_t(pr->fine.S) * pr->fine.ldr, rp.as<int>(),
+                                    src.as<int64_t>(), w.as<double>(), npos, K, C.ell.v64.as<double>(),
+                                    C.ell.v32.as<float>());
+  SG_CUDA(cudaGetLastError());
+  SG_CUDA(cudaDeviceSynchronize());
+  SG_TRY(build_triple_tables(pr, C.tri, S));
+  return SG_OK;
+}
+
+sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w) {
+  DevBuf out;
+  SG_TRY(out.alloc(size_t(pr->K) * 8));
+  const int64_t kstride = int64_t(pr->fine.S) * pr->fine.ldr;
+  k_frob<<<pr->K, 256>>>(pr->fine.v64.as<double>(), kstride, pr->K, out.as<double>());
+  SG_CUDA(cudaGetLastError());
+  w.resize(pr->K);
+  SG_CUDA(cudaMemcpy(w.data(), out.ptr, size_t(pr->K) * 8, cudaMemcpyDeviceToHost));
+  return SG_OK;
+}
+
+#define INST(T)                                                                                           \
+  template sg_status spmm<T>(const DevCsr&, const T*, int64_t, const T*, int64_t, T*, int64_t, int, int,  \
+                             cudaStream_t);                                                               \
+  template sg_status ras_apply<T>(const Precond&, int64_t, int, const T*, int64_t, T*, cudaStream_t, bool);        \
+  template sg_status node_transform<T>(T*, int64_t, int64_t, int, const T*, cudaStream_t);                \
+  template sg_status amg_vcycle<T>(const Precond&, AmgWork<T>&, int, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace sg

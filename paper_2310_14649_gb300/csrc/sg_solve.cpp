@@ -1,0 +1,655 @@
+// Solver orchestration: the two-level preconditioner of Sec. 3 (Eq. RAS_2L),
+// flexible GMRES on the fine Galerkin system, GMRES + AMG on the coarse
+// system (the 2GV3 variant), and mixed-precision iterative refinement
+// (FP32 inner FGMRES inside an FP64 residual loop).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <memory>
+
+#include "sg_kernels.h"
+
+namespace sg {
+
+// --------------------------------------------------------------------------
+// (F)GMRES workspace and driver
+// --------------------------------------------------------------------------
+template <typename T>
+struct KrylovWork {
+  int64_t len = 0;
+  int m = 0;
+  bool flexible = false;
+  DevBuf V, Z, w, tmp, tmp2, state, partial, counter;
+  GmresState s{};
+  double* host = nullptr;  // pinned: [0] est, [1] h_{j+1,j}, [2] bad, [4..] scalars
+
+  sg_status init(int64_t len_, int m_, bool flexible_) {
+    len = len_;
+    m = m_;
+    flexible = flexible_;
+    SG_TRY(V.alloc(size_t(m + 1) * len * sizeof(T)));
+    if (flexible) SG_TRY(Z.alloc(size_t(m) * len * sizeof(T)));
+    SG_TRY(w.alloc(size_t(len) * sizeof(T)));
+    SG_TRY(tmp.alloc(size_t(len) * sizeof(T)));
+    SG_TRY(tmp2.alloc(size_t(len) * sizeof(T)));
+    const size_t nst = size_t(m + 1) * m + 2 * m + (m + 1) + m + 2 * (m + 1) + 8;
+    SG_TRY(state.alloc(nst * sizeof(double)));
+    SG_TRY(partial.alloc(size_t(2 * 152) * 32 * sizeof(double)));
+    SG_TRY(counter.alloc(64));
+    double* p = dp<double>(state);
+    s.H = p;
+    p += size_t(m + 1) * m;
+    s.cs = p;
+    p += m;
+    s.sn = p;
+    p += m;
+    s.g = p;
+    p += m + 1;
+    s.y = p;
+    p += m;
+    s.hsum = p;
+    p += 2 * (m + 1);
+    s.scal = p;
+    SG_CUDA(cudaHostAlloc(&host, 16 * sizeof(double), cudaHostAllocMapped));
+    std::memset(host, 0, 16 * sizeof(double));
+    return SG_OK;
+  }
+  ~KrylovWork() {
+    if (host) cudaFreeHost(host);
+  }
+  T* Vj(int j) { return dp<T>(V) + int64_t(j) * len; }
+  T* Zj(int j) { return dp<T>(Z) + int64_t(j) * len; }
+};
+
+template <typename T>
+using Op = std::function<sg_status(const T*, T*)>;
+
+// y = a - b (elementwise), used for r = F - A x
+template <typename T>
+static sg_status sub_into(const T* a, const T* b, T* y, int64_t len, KrylovWork<T>& W, cudaStream_t st) {
+  // y = a; y -= 1 * b  (axpy with a device coefficient -1)
+  SG_CUDA(cudaMemcpyAsync(y, a, len * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  static thread_local double* minus_one = nullptr;
+  if (!minus_one) {
+    SG_CUDA(cudaMalloc(&minus_one, sizeof(double)));
+    const double v = -1.0;
+    SG_CUDA(cudaMemcpy(minus_one, &v, sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return vec_axpy_multi<T>(b, 0, 1, minus_one, y, len, st);
+}
+
+struct GmresResult {
+  int its = 0;
+  double est = 0.0;     // last residual estimate (absolute)
+  bool converged = false;
+};
+
+// Right-preconditioned restarted GMRES (flexible when W.flexible: the
+// preconditioned vectors are kept and x += Z y).  Stops when the residual
+// estimate drops below tol_abs; at each restart the true residual is used.
+template <typename T>
+static sg_status gmres_run(KrylovWork<T>& W, const Op<T>& A, const Op<T>& M, const T* F, T* x, bool x_zero,
+                           double tol_abs, int max_it, GmresResult& res, std::vector<double>* hist, double hist_scale,
+                           cudaStream_t st) {
+  const int64_t len = W.len;
+  res = GmresResult{};
+  bool first = true;
+  for (;;) {
+    // r0 = F - A x
+    if (first && x_zero) {
+      SG_CUDA(cudaMemcpyAsync(W.Vj(0), F, len * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    } else {
+      SG_TRY(A(x, dp<T>(W.w)));
+      SG_TRY(sub_into<T>(F, dp<T>(W.w), W.Vj(0), len, W, st));
+    }
+    first = false;
+    SG_TRY(vec_norm2<T>(W.Vj(0), len, W.s.scal + 3, dp<double>(W.partial), dp<unsigned>(W.counter), st));
+    SG_CUDA(cudaMemcpyAsync(W.host + 4, W.s.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    const double beta = std::sqrt(W.host[4]);
+    if (!std::isfinite(beta)) {
+      set_error("GMRES: non-finite residual");
+      return SG_ERR_BREAKDOWN;
+    }
+    res.est = beta;
+    if (beta <= tol_abs) {
+      res.converged = true;
+      return SG_OK;
+    }
+    if (res.its >= max_it) return SG_OK;
+    SG_TRY(vec_scale_by<T>(W.Vj(0), W.Vj(0), len, W.s.scal + 3, true, st));
+    SG_TRY(gmres_init(W.s, W.m, W.s.scal + 3, st));
+    int k = 0;
+    bool stop = false;
+    for (int j = 0; j < W.m; ++j) {
+      T* zj = W.flexible ? W.Zj(j) : dp<T>(W.tmp);
+      SG_TRY(M(W.Vj(j), zj));
+      SG_TRY(A(zj, dp<T>(W.w)));
+      double* h1 = W.s.hsum;
+      double* h2 = W.s.hsum + (W.m + 1);
+      SG_TRY(vec_mdot<T>(dp<T>(W.V), len, j + 1, dp<T>(W.w), len, h1, dp<double>(W.partial),
+                         dp<unsigned>(W.counter), st));
+      SG_TRY(vec_maxpy_mdot<T>(dp<T>(W.V), len, j + 1, h1, dp<T>(W.w), len, h2, dp<double>(W.partial),
+                               dp<unsigned>(W.counter), st));
+      SG_TRY(vec_maxpy_norm<T>(dp<T>(W.V), len, j + 1, h2, dp<T>(W.w), len, W.s.scal, dp<double>(W.partial),
+                               dp<unsigned>(W.counter), st));
+      SG_TRY(gmres_givens(W.s, W.m, j, W.host, st));
+      SG_TRY(vec_scale_by<T>(dp<T>(W.w), W.Vj(j + 1), len, W.s.scal + 1, false, st));
+      SG_CUDA(cudaStreamSynchronize(st));
+      res.its++;
+      k = j + 1;
+      const double est = W.host[0], hn = W.host[1];
+      if (W.host[2] != 0.0) {
+        set_error("GMRES: non-finite value in the Arnoldi process");
+        return SG_ERR_BREAKDOWN;
+      }
+      res.est = est;
+      if (hist) hist->push_back(est * hist_scale);
+      if (est <= tol_abs || hn == 0.0) {
+        stop = true;
+        break;
+      }
+      if (res.its >= max_it) break;
+    }
+    SG_TRY(gmres_backsolve(W.s, W.m, k, st));
+    if (W.flexible) {
+      SG_TRY(vec_axpy_multi<T>(dp<T>(W.Z), len, k, W.s.y, x, len, st));
+    } else {
+      SG_CUDA(cudaMemsetAsync(W.tmp2.ptr, 0, len * sizeof(T), st));
+      SG_TRY(vec_axpy_multi<T>(dp<T>(W.V), len, k, W.s.y, dp<T>(W.tmp2), len, st));
+      SG_TRY(M(dp<T>(W.tmp2), dp<T>(W.tmp)));
+      static thread_local double* one = nullptr;
+      if (!one) {
+        SG_CUDA(cudaMalloc(&one, sizeof(double)));
+        const double v = 1.0;
+        SG_CUDA(cudaMemcpy(one, &v, sizeof(double), cudaMemcpyHostToDevice));
+      }
+      SG_TRY(vec_axpy_multi<T>(dp<T>(W.tmp), 0, 1, one, x, len, st));
+    }
+    if (stop && !W.flexible) {  // inner solves trust the estimate
+      res.converged = true;
+      return SG_OK;
+    }
+    if (res.its >= max_it && !stop) {
+      // report the true residual of the final iterate
+      SG_TRY(A(x, dp<T>(W.w)));
+      SG_TRY(sub_into<T>(F, dp<T>(W.w), dp<T>(W.tmp), len, W, st));
+      SG_TRY(vec_norm2<T>(dp<T>(W.tmp), len, W.s.scal + 3, dp<double>(W.partial), dp<unsigned>(W.counter), st));
+      SG_CUDA(cudaMemcpyAsync(W.host + 4, W.s.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+      SG_CUDA(cudaStreamSynchronize(st));
+      res.est = std::sqrt(W.host[4]);
+      res.converged = res.est <= tol_abs;
+      return SG_OK;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Per-precision solver context: operator, preconditioner and workspaces.
+// --------------------------------------------------------------------------
+template <typename T>
+struct SolverCtx {
+  sg_problem* pr = nullptr;
+  Precond* pc = nullptr;
+  int64_t ld = 0, len = 0, ldc = 0, lenc = 0;
+  KrylovWork<T> fine, coarse;
+  DevBuf r1, zt, rc, ec;          // two-level temporaries
+  std::vector<DevBuf> amgbuf;     // b, x, t per level
+  AmgWork<T> aw;
+  bool ready = false;
+
+  sg_status init(sg_problem* p, Precond* c, int restart) {
+    pr = p;
+    pc = c;
+    ld = pr->ld;
+    len = int64_t(pr->P) * ld;
+    ldc = pc->co.ldc;
+    lenc = int64_t(pr->P) * ldc;
+    SG_TRY(fine.init(len, restart, true));
+    SG_TRY(coarse.init(lenc, pc->inner_restart, false));
+    SG_TRY(r1.alloc(len * sizeof(T)));
+    SG_TRY(zt.alloc(len * sizeof(T)));
+    SG_TRY(rc.alloc(lenc * sizeof(T)));
+    SG_TRY(ec.alloc(lenc * sizeof(T)));
+    amgbuf.resize(3 * pc->amg.size());
+    aw.b.clear();
+    aw.x.clear();
+    aw.t.clear();
+    for (size_t l = 0; l < pc->amg.size(); ++l) {
+      const size_t sz = size_t(pr->P) * pc->amg[l].ld * sizeof(T);
+      for (int q = 0; q < 3; ++q) SG_TRY(amgbuf[3 * l + q].alloc(sz));
+      aw.b.push_back(amgbuf[3 * l].as<T>());
+      aw.x.push_back(amgbuf[3 * l + 1].as<T>());
+      aw.t.push_back(amgbuf[3 * l + 2].as<T>());
+    }
+    ready = true;
+    return SG_OK;
+  }
+
+  sg_status apply_fine(const T* X, T* Y, const T* F, cudaStream_t st) {
+    return apply_ell<T>(pr->fine, pr->tri, pr->P, pr->K, X, ld, F, ld, Y, ld, st);
+  }
+  sg_status apply_coarse(const T* X, T* Y, cudaStream_t st) {
+    return apply_ell<T>(pc->co.ell, pc->co.tri, pr->P, pr->K, X, ldc, nullptr, 0, Y, ldc, st);
+  }
+  // AMG V-cycle per mode on a coarse block
+  sg_status amg(const T* B, T* X, cudaStream_t st) {
+    const AmgLevel& L0 = pc->amg[0];
+    SG_CUDA(cudaMemcpy2DAsync(aw.b[0], L0.ld * sizeof(T), B, ldc * sizeof(T), pc->co.nc * sizeof(T), pr->P,
+                              cudaMemcpyDeviceToDevice, st));
+    SG_TRY(amg_vcycle<T>(*pc, aw, pr->P, st));
+    SG_CUDA(cudaMemcpy2DAsync(X, ldc * sizeof(T), aw.x[0], L0.ld * sizeof(T), pc->co.nc * sizeof(T), pr->P,
+                              cudaMemcpyDeviceToDevice, st));
+    return SG_OK;
+  }
+  // e_c ~ A_c^{-1} r_c by GMRES preconditioned with the AMG V-cycle
+  sg_status coarse_solve(const T* Rc, T* Ec, cudaStream_t st) {
+    SG_CUDA(cudaMemsetAsync(Ec, 0, lenc * sizeof(T), st));
+    // absolute tolerance relative to ||r_c||
+    SG_TRY(vec_norm2<T>(Rc, lenc, coarse.s.scal + 5, dp<double>(coarse.partial), dp<unsigned>(coarse.counter), st));
+    SG_CUDA(cudaMemcpyAsync(coarse.host + 5, coarse.s.scal + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    const double nr = std::sqrt(coarse.host[5]);
+    if (nr == 0.0) return SG_OK;
+    Op<T> A = [&](const T* x, T* y) { return apply_coarse(x, y, st); };
+    Op<T> M = [&](const T* x, T* y) { return amg(x, y, st); };
+    GmresResult res;
+    SG_TRY(gmres_run<T>(coarse, A, M, Rc, Ec, true, pc->inner_rtol * nr, pc->inner_max, res, nullptr, 1.0, st));
+    pc->inner_its_last = res.its;
+    pc->inner_its_total += res.its;
+    pc->inner_calls++;
+    return SG_OK;
+  }
+  // Q r = R_0^T A_c^{-1} R_0 r
+  sg_status coarse_correction(const T* R, T* Z, bool add, cudaStream_t st) {
+    SG_TRY(spmm<T>(pc->co.R, R, ld, nullptr, 0, dp<T>(rc), ldc, pr->P, 0, st));
+    SG_TRY(coarse_solve(dp<T>(rc), dp<T>(ec), st));
+    if (!add) SG_CUDA(cudaMemsetAsync(Z, 0, len * sizeof(T), st));
+    SG_TRY(spmm<T>(pc->co.RT, dp<T>(ec), ldc, nullptr, 0, Z, ld, pr->P, 1, st));
+    return SG_OK;
+  }
+  // smoother S r = omega G~^{-1} RAS(r)
+  sg_status smooth(const T* R, T* Z, cudaStream_t st) { return ras_apply<T>(*pc, pr->n, pr->P, R, ld, Z, st, true); }
+  // two-level cycle: z = S r; z += Q (r - A z); z += S (r - A z)
+  sg_status twolevel(const T* R, T* Z, cudaStream_t st) {
+    SG_TRY(smooth(R, Z, st));
+    SG_TRY(apply_fine(Z, dp<T>(r1), R, st));
+    SG_TRY(coarse_correction(dp<T>(r1), Z, true, st));
+    SG_TRY(apply_fine(Z, dp<T>(r1), R, st));
+    SG_TRY(smooth(dp<T>(r1), dp<T>(zt), st));
+    static thread_local double* one = nullptr;
+    if (!one) {
+      SG_CUDA(cudaMalloc(&one, sizeof(double)));
+      const double v = 1.0;
+      SG_CUDA(cudaMemcpy(one, &v, sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return vec_axpy_multi<T>(dp<T>(zt), 0, 1, one, Z, len, st);
+  }
+};
+
+}  // namespace sg
+
+// ==========================================================================
+// Preconditioner and solver state attached to a problem handle.
+// ==========================================================================
+namespace sg {
+struct SolverState {
+  Precond pc;
+  std::unique_ptr<SolverCtx<double>> c64;
+  std::unique_ptr<SolverCtx<float>> c32;
+  int restart = 30;
+  DevBuf x64, r64, r32, d32, io, io2, scal;  // IR and I/O buffers
+  double* host = nullptr;                    // pinned scalars
+  ~SolverState() {
+    if (host) cudaFreeHost(host);
+  }
+};
+
+void solver_free(sg_problem* pr) {
+  delete pr->solver;
+  pr->solver = nullptr;
+}
+
+template <typename T> std::unique_ptr<SolverCtx<T>>& ctx_of(SolverState& S);
+template <> std::unique_ptr<SolverCtx<double>>& ctx_of<double>(SolverState& S) { return S.c64; }
+template <> std::unique_ptr<SolverCtx<float>>& ctx_of<float>(SolverState& S) { return S.c32; }
+
+template <typename T>
+static sg_status get_ctx(sg_problem* pr, SolverCtx<T>*& out) {
+  SolverState& S = *pr->solver;
+  auto& c = ctx_of<T>(S);
+  if (!c || !c->ready || c->fine.m != S.restart) {
+    c.reset(new SolverCtx<T>());
+    SG_TRY(c->init(pr, &S.pc, S.restart));
+  }
+  out = c.get();
+  return SG_OK;
+}
+
+// upload omega * G~^{-1}
+static sg_status upload_gtinv(sg_problem* pr, Precond& pc, const std::vector<double>& ginv) {
+  const int P = pr->P;
+  std::vector<double> m64(size_t(P) * P);
+  std::vector<float> m32(size_t(P) * P);
+  for (size_t e = 0; e < m64.size(); ++e) {
+    m64[e] = pc.omega * ginv[e];
+    m32[e] = float(m64[e]);
+  }
+  if (!pc.gtinv64.ptr) SG_TRY(pc.gtinv64.alloc(m64.size() * 8));
+  if (!pc.gtinv32.ptr) SG_TRY(pc.gtinv32.alloc(m32.size() * 4));
+  SG_CUDA(cudaMemcpy(pc.gtinv64.ptr, m64.data(), m64.size() * 8, cudaMemcpyHostToDevice));
+  SG_CUDA(cudaMemcpy(pc.gtinv32.ptr, m32.data(), m32.size() * 4, cudaMemcpyHostToDevice));
+  return SG_OK;
+}
+
+// Kronecker stochastic factor G~ = sum_k w_k G_k, w_k = <A_k, A_0>_F / <A_0, A_0>_F,
+// and its inverse (SPD: Cholesky on the host).
+static sg_status kronecker_factor(sg_problem* pr, Precond& pc, std::vector<double>& ginv) {
+  std::vector<double> fw;
+  SG_TRY(frobenius_weights(pr, fw));
+  const int P = pr->P;
+  pc.gt.assign(size_t(P) * P, 0.0);
+  for (int64_t t = 0; t < pr->T; ++t) {
+    int k = pr->kab[3 * t], a = pr->kab[3 * t + 1], b = pr->kab[3 * t + 2];
+    pc.gt[size_t(a) * P + b] += fw[k] / fw[0] * pr->g[t];
+  }
+  // Gauss-Jordan inverse with partial pivoting
+  std::vector<double> A = pc.gt;
+  ginv.assign(size_t(P) * P, 0.0);
+  for (int i = 0; i < P; ++i) ginv[size_t(i) * P + i] = 1.0;
+  for (int c = 0; c < P; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < P; ++r)
+      if (std::fabs(A[size_t(r) * P + c]) > std::fabs(A[size_t(piv) * P + c])) piv = r;
+    if (A[size_t(piv) * P + c] == 0.0) {
+      set_error("Kronecker factor is singular");
+      return SG_ERR_BREAKDOWN;
+    }
+    for (int k = 0; k < P; ++k) {
+      std::swap(A[size_t(c) * P + k], A[size_t(piv) * P + k]);
+      std::swap(ginv[size_t(c) * P + k], ginv[size_t(piv) * P + k]);
+    }
+    const double d = A[size_t(c) * P + c];
+    for (int k = 0; k < P; ++k) {
+      A[size_t(c) * P + k] /= d;
+      ginv[size_t(c) * P + k] /= d;
+    }
+    for (int r = 0; r < P; ++r) {
+      if (r == c) continue;
+      const double f = A[size_t(r) * P + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < P; ++k) {
+        A[size_t(r) * P + k] -= f * A[size_t(c) * P + k];
+        ginv[size_t(r) * P + k] -= f * ginv[size_t(c) * P + k];
+      }
+    }
+  }
+  return SG_OK;
+}
+
+// omega = 1 / rho(S A) by 20 power iterations (FP32) from the seed-free
+// start X[a][r] = 1 + (r + a) mod 3.
+static sg_status estimate_omega(sg_problem* pr, SolverState& S, cudaStream_t st) {
+  SolverCtx<float>* c = nullptr;
+  SG_TRY(get_ctx<float>(pr, c));
+  const int P = pr->P;
+  const int64_t ld = pr->ld, len = c->len;
+  std::vector<float> x0(len, 0.0f);
+  for (int a = 0; a < P; ++a)
+    for (int64_t r = 0; r < pr->n; ++r) x0[size_t(a) * ld + r] = float(1 + (r + a) % 3);
+  float* X = dp<float>(c->fine.tmp);
+  float* Y = dp<float>(c->fine.tmp2);
+  float* AX = dp<float>(c->fine.w);
+  SG_CUDA(cudaMemcpyAsync(X, x0.data(), len * 4, cudaMemcpyHostToDevice, st));
+  double* nrm = c->fine.s.scal + 6;
+  SG_TRY(vec_norm2<float>(X, len, nrm, dp<double>(c->fine.partial), dp<unsigned>(c->fine.counter), st));
+  SG_TRY(vec_scale_by<float>(X, X, len, nrm, true, st));
+  for (int it = 0; it < 20; ++it) {
+    SG_TRY(c->apply_fine(X, AX, nullptr, st));
+    SG_TRY(c->smooth(AX, Y, st));
+    SG_TRY(vec_norm2<float>(Y, len, nrm, dp<double>(c->fine.partial), dp<unsigned>(c->fine.counter), st));
+    SG_TRY(vec_scale_by<float>(Y, X, len, nrm, true, st));
+  }
+  SG_CUDA(cudaMemcpyAsync(c->fine.host + 6, nrm, 8, cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  const double rho = std::sqrt(c->fine.host[6]);
+  if (!(rho > 0.0) || !std::isfinite(rho)) {
+    set_error("omega estimate failed");
+    return SG_ERR_BREAKDOWN;
+  }
+  S.pc.omega = 1.0 / rho;
+  return SG_OK;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+template <typename T>
+static sg_status precond_apply_t(sg_problem* pr, int which, const T* Rin, int64_t ldr, T* Zout, int64_t ldz,
+                                 cudaStream_t st) {
+  SolverCtx<T>* c = nullptr;
+  SG_TRY(get_ctx<T>(pr, c));
+  SolverState& S = *pr->solver;
+  const int P = pr->P;
+  const bool coarse_in = which == 3 || which == 4 || which == 6;
+  const bool coarse_out = which == 3 || which == 4 || which == 5;
+  const int64_t nin = coarse_in ? S.pc.co.nc : pr->n, ldin = coarse_in ? c->ldc : c->ld;
+  const int64_t nout = coarse_out ? S.pc.co.nc : pr->n, ldout = coarse_out ? c->ldc : c->ld;
+  SG_ARG(ldr >= nin && ldz >= nout, "sg_precond_apply: leading dimension too small");
+  T* in = coarse_in ? dp<T>(c->coarse.tmp) : dp<T>(c->fine.tmp);
+  T* out = coarse_out ? dp<T>(c->coarse.tmp2) : dp<T>(c->fine.tmp2);
+  SG_CUDA(cudaMemsetAsync(in, 0, size_t(P) * ldin * sizeof(T), st));
+  SG_CUDA(cudaMemsetAsync(out, 0, size_t(P) * ldout * sizeof(T), st));
+  SG_CUDA(cudaMemcpy2DAsync(in, ldin * sizeof(T), Rin, ldr * sizeof(T), nin * sizeof(T), P,
+                            cudaMemcpyDeviceToDevice, st));
+  switch (which) {
+    case 0: SG_TRY(c->twolevel(in, out, st)); break;
+    case 1: SG_TRY(c->smooth(in, out, st)); break;
+    case 2: SG_TRY(c->coarse_correction(in, out, false, st)); break;
+    case 3: SG_TRY(c->amg(in, out, st)); break;
+    case 4: SG_TRY(c->apply_coarse(in, out, st)); break;
+    case 5: SG_TRY(spmm<T>(S.pc.co.R, in, c->ld, nullptr, 0, out, c->ldc, P, 0, st)); break;
+    case 6: SG_TRY(spmm<T>(S.pc.co.RT, in, c->ldc, nullptr, 0, out, c->ld, P, 0, st)); break;
+    case 7: SG_TRY(ras_apply<T>(S.pc, pr->n, P, in, c->ld, out, st, false)); break;
+    default: set_error("sg_precond_apply: unknown operator"); return SG_ERR_ARG;
+  }
+  SG_CUDA(cudaMemcpy2DAsync(Zout, ldz * sizeof(T), out, ldout * sizeof(T), nout * sizeof(T), P,
+                            cudaMemcpyDeviceToDevice, st));
+  return SG_OK;
+}
+
+
+extern "C" {
+
+sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* stream) {
+  SG_ARG(pr && o, "sg_precond_setup: NULL argument");
+  SG_ARG(pr->N % 2 == 0 && pr->N >= 4, "sg_precond_setup: the 2h coarse grid needs an even N >= 4");
+  SG_ARG(o->sx >= 1 && o->sy >= 1 && o->sx <= pr->N - 1 && o->sy <= pr->N - 1,
+         "sg_precond_setup: subdomain counts must be in [1, N-1]");
+  SG_ARG(o->overlap >= 0 && o->overlap <= 8, "sg_precond_setup: overlap must be in [0, 8]");
+  SG_ARG(o->smoother == 0, "sg_precond_setup: only the RAS smoother (0) is available");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  solver_free(pr);
+  pr->solver = new SolverState();
+  SolverState& S = *pr->solver;
+  Precond& pc = S.pc;
+  pc.sx = o->sx;
+  pc.sy = o->sy;
+  pc.overlap = o->overlap;
+  pc.inner_rtol = o->inner_rtol > 0 ? o->inner_rtol : 1e-5;
+  pc.inner_max = o->inner_max > 0 ? o->inner_max : 100;
+  pc.inner_restart = 30;
+  sg_status s = precond_setup_host(pr, pc);
+  std::vector<double> ginv;
+  if (s == SG_OK) s = kronecker_factor(pr, pc, ginv);
+  pc.omega = 1.0;
+  if (s == SG_OK) s = upload_gtinv(pr, pc, ginv);
+  if (s == SG_OK && o->omega <= 0) s = estimate_omega(pr, S, st);
+  if (s == SG_OK && o->omega > 0) pc.omega = o->omega;
+  if (s == SG_OK) s = upload_gtinv(pr, pc, ginv);
+  if (s != SG_OK) {
+    solver_free(pr);
+    return s;
+  }
+  pc.ready = true;
+  return SG_OK;
+}
+
+sg_status sg_precond_info(const sg_problem* pr, double* omega, int* amg_levels, int64_t* nc, int* inner_its_last) {
+  SG_ARG(pr && pr->solver && pr->solver->pc.ready, "sg_precond_info: no preconditioner set up");
+  const Precond& pc = pr->solver->pc;
+  if (omega) *omega = pc.omega;
+  if (amg_levels) *amg_levels = int(pc.amg.size());
+  if (nc) *nc = pc.co.nc;
+  if (inner_its_last) *inner_its_last = pc.inner_its_last;
+  return SG_OK;
+}
+
+sg_status sg_get_partition(const sg_problem* pr, int sub, int32_t* idx, int64_t* count, int32_t* owned) {
+  SG_ARG(pr && pr->solver && pr->solver->pc.ready && count, "sg_get_partition: no preconditioner set up");
+  const RasData& R = pr->solver->pc.ras;
+  SG_ARG(sub >= 0 && sub < R.nbox, "sg_get_partition: subdomain out of range");
+  *count = int64_t(R.idx[sub].size());
+  if (idx) std::memcpy(idx, R.idx[sub].data(), R.idx[sub].size() * 4);
+  if (owned) std::memcpy(owned, R.owned[sub].data(), R.owned[sub].size() * 4);
+  return SG_OK;
+}
+
+sg_status sg_get_coarse_csr(const sg_problem* pr, int64_t* nc, int64_t* nnz, int32_t* rowptr, int32_t* colidx) {
+  SG_ARG(pr && pr->solver && pr->solver->pc.ready, "sg_get_coarse_csr: no preconditioner set up");
+  const CoarseData& C = pr->solver->pc.co;
+  if (nc) *nc = C.nc;
+  if (nnz) *nnz = int64_t(C.colidx.size());
+  if (rowptr) std::memcpy(rowptr, C.rowptr.data(), C.rowptr.size() * 4);
+  if (colidx) std::memcpy(colidx, C.colidx.data(), C.colidx.size() * 4);
+  return SG_OK;
+}
+
+sg_status sg_get_amg_level(const sg_problem* pr, int level, int64_t* n, int32_t* agg) {
+  SG_ARG(pr && pr->solver && pr->solver->pc.ready, "sg_get_amg_level: no preconditioner set up");
+  const auto& L = pr->solver->pc.amg;
+  SG_ARG(level >= 0 && level < int(L.size()), "sg_get_amg_level: level out of range");
+  if (n) *n = L[level].n;
+  if (agg && !L[level].agg.empty()) std::memcpy(agg, L[level].agg.data(), L[level].agg.size() * 4);
+  return SG_OK;
+}
+
+sg_status sg_precond_apply(sg_problem* pr, sg_dtype dtype, int which, const void* R, int64_t ldr, void* Z,
+                           int64_t ldz, void* stream) {
+  SG_ARG(pr && R && Z, "sg_precond_apply: NULL argument");
+  SG_ARG(pr->solver && pr->solver->pc.ready, "sg_precond_apply: call sg_precond_setup first");
+  SG_ARG(dtype == SG_F64 || dtype == SG_F32, "sg_precond_apply: bad dtype");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (dtype == SG_F64)
+    return precond_apply_t<double>(pr, which, static_cast<const double*>(R), ldr, static_cast<double*>(Z), ldz, st);
+  return precond_apply_t<float>(pr, which, static_cast<const float*>(R), ldr, static_cast<float*>(Z), ldz, st);
+}
+
+sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int64_t ldx, const sg_solve_opts* o,
+                   sg_solve_info* info, void* stream) {
+  SG_ARG(pr && X && o, "sg_solve: NULL argument");
+  SG_ARG(pr->solver && pr->solver->pc.ready, "sg_solve: call sg_precond_setup first");
+  SG_ARG(ldx >= pr->n && (!F || ldf >= pr->n), "sg_solve: leading dimension < n");
+  SG_ARG(o->rtol > 0 && o->max_it > 0, "sg_solve: rtol and max_it must be > 0");
+  SG_ARG(o->mode == 0 || o->mode == 1, "sg_solve: mode must be 0 (FP64) or 1 (FP32 in FP64 refinement)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SolverState& S = *pr->solver;
+  S.restart = o->restart > 0 ? std::min(o->restart, 31) : 30;
+  const int P = pr->P;
+  const int64_t ld = pr->ld, len = int64_t(P) * ld;
+  auto t0 = std::chrono::steady_clock::now();
+  if (!S.host) SG_CUDA(cudaHostAlloc(&S.host, 16 * sizeof(double), cudaHostAllocDefault));
+  if (!S.x64.ptr) SG_TRY(S.x64.alloc(len * 8));
+  if (!S.r64.ptr) SG_TRY(S.r64.alloc(len * 8));
+  if (!S.io.ptr) SG_TRY(S.io.alloc(len * 8));
+  if (!S.scal.ptr) SG_TRY(S.scal.alloc(64 * 8));
+  double* x64 = dp<double>(S.x64);
+  double* F64 = dp<double>(S.io);
+  // internal copies with the library's leading dimension (padding zero)
+  SG_CUDA(cudaMemsetAsync(F64, 0, len * 8, st));
+  SG_CUDA(cudaMemsetAsync(x64, 0, len * 8, st));
+  if (F) {
+    SG_CUDA(cudaMemcpy2DAsync(F64, ld * 8, F, ldf * 8, pr->n * 8, P, cudaMemcpyDeviceToDevice, st));
+  } else {
+    SG_CUDA(cudaMemcpyAsync(F64, pr->b.data(), pr->n * 8, cudaMemcpyHostToDevice, st));
+  }
+  SG_CUDA(cudaMemcpy2DAsync(x64, ld * 8, X, ldx * 8, pr->n * 8, P, cudaMemcpyDeviceToDevice, st));
+  SolverCtx<double>* c64 = nullptr;
+  SG_TRY(get_ctx<double>(pr, c64));
+  double* scal = dp<double>(S.scal);
+  SG_TRY(vec_norm2<double>(F64, len, scal, dp<double>(c64->fine.partial), dp<unsigned>(c64->fine.counter), st));
+  SG_CUDA(cudaMemcpyAsync(S.host, scal, 8, cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  const double nF = std::sqrt(S.host[0]);
+  sg_solve_info inf{};
+  std::vector<double> hist;
+  S.pc.inner_its_total = 0;
+  S.pc.inner_calls = 0;
+  sg_status status = SG_OK;
+  if (nF == 0.0) {
+    SG_CUDA(cudaMemsetAsync(x64, 0, len * 8, st));
+  } else if (o->mode == 0) {
+    Op<double> A = [&](const double* x, double* y) { return c64->apply_fine(x, y, nullptr, st); };
+    Op<double> M = [&](const double* r, double* z) { return c64->twolevel(r, z, st); };
+    GmresResult res;
+    SG_TRY(gmres_run<double>(c64->fine, A, M, F64, x64, false, o->rtol * nF, o->max_it, res, &hist, 1.0 / nF, st));
+    inf.outer_it = res.its;
+  } else {
+    SolverCtx<float>* c32 = nullptr;
+    SG_TRY(get_ctx<float>(pr, c32));
+    if (!S.r32.ptr) SG_TRY(S.r32.alloc(len * 4));
+    if (!S.d32.ptr) SG_TRY(S.d32.alloc(len * 4));
+    float* r32 = dp<float>(S.r32);
+    float* d32 = dp<float>(S.d32);
+    Op<float> A = [&](const float* x, float* y) { return c32->apply_fine(x, y, nullptr, st); };
+    Op<float> M = [&](const float* r, float* z) { return c32->twolevel(r, z, st); };
+    const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
+    const int max_ir = o->max_ir > 0 ? o->max_ir : 20;
+    for (int ir = 0;; ++ir) {
+      SG_TRY(apply_ell<double>(pr->fine, pr->tri, P, pr->K, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+      SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 1, dp<double>(c64->fine.partial),
+                               dp<unsigned>(c64->fine.counter), st));
+      SG_CUDA(cudaMemcpyAsync(S.host + 1, scal + 1, 8, cudaMemcpyDeviceToHost, st));
+      SG_CUDA(cudaStreamSynchronize(st));
+      const double rr = std::sqrt(S.host[1]) / nF;
+      if (!std::isfinite(rr)) {
+        set_error("sg_solve: non-finite residual");
+        return SG_ERR_BREAKDOWN;
+      }
+      hist.push_back(rr);
+      if (rr <= o->rtol || ir >= max_ir || inf.outer_it >= o->max_it) break;
+      inf.ir_steps++;
+      SG_TRY((vec_convert<double, float>(dp<double>(S.r64), r32, len, nullptr, scal + 1, st)));
+      SG_CUDA(cudaMemsetAsync(d32, 0, len * 4, st));
+      GmresResult res;
+      SG_TRY(gmres_run<float>(c32->fine, A, M, r32, d32, true, inner, o->max_it - inf.outer_it, res, nullptr, 1.0,
+                              st));
+      inf.outer_it += res.its;
+      SG_TRY(vec_add_scaled_f32(x64, d32, len, scal + 1, st));
+    }
+  }
+  // true FP64 residual of the returned iterate
+  SG_TRY(apply_ell<double>(pr->fine, pr->tri, P, pr->K, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+  SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 2, dp<double>(c64->fine.partial),
+                           dp<unsigned>(c64->fine.counter), st));
+  SG_CUDA(cudaMemcpyAsync(S.host + 2, scal + 2, 8, cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaMemcpy2DAsync(X, ldx * 8, x64, ld * 8, pr->n * 8, P, cudaMemcpyDeviceToDevice, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  inf.relres = nF > 0 ? std::sqrt(S.host[2]) / nF : 0.0;
+  inf.inner_it = S.pc.inner_its_total;
+  inf.fallback_used = 0;
+  inf.t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (o->hist_host && o->hist_cap > 0) {
+    int cnt = std::min<int>(o->hist_cap, int(hist.size()));
+    std::memcpy(o->hist_host, hist.data(), cnt * sizeof(double));
+    inf.hist_len = cnt;
+  }
+  if (info) *info = inf;
+  status = inf.relres <= o->rtol ? SG_OK : SG_NOT_CONVERGED;
+  if (status == SG_NOT_CONVERGED) set_error("sg_solve: max_it reached before rtol");
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal declarations of the preconditioner and Krylov solvers.
+#pragma once
+
+#include "sg_internal.h"
+
+namespace sg {
+
+// Generic CSR matrix on the device (FP64 and FP32 values).
+struct DevCsr {
+  int64_t n = 0, m = 0, nnz = 0;  // rows, cols, entries
+  DevBuf rowptr, col, v64, v32;
+  sg_status upload(int64_t rows, int64_t cols, const std::vector<int32_t>& rp,
+                   const std::vector<int32_t>& ci, const std::vector<double>& v);
+  void free_() {
+    rowptr.free_();
+    col.free_();
+    v64.free_();
+    v32.free_();
+  }
+};
+
+// One level of the smoothed-aggregation hierarchy.
+struct AmgLevel {
+  int64_t n = 0, ld = 0;
+  DevCsr A, Pm, R;        // operator, prolongation (n x n_next), restriction
+  DevBuf dinv64, dinv32;  // 1 / l1 row norms
+  // host copies for tests
+  std::vector<int32_t> agg;
+};
+
+// Restricted additive Schwarz data: per box, block-tridiagonal (line)
+// Cholesky factors of the local mean block, stored as explicit inverses of
+// the diagonal blocks and the sub-diagonal blocks, padded to wmax x wmax.
+struct RasData {
+  int nbox = 0, wmax = 0, lmax = 0;
+  std::vector<int32_t> nlines;             // per box
+  std::vector<std::vector<int32_t>> idx;   // per box: ascending global indices
+  std::vector<std::vector<int32_t>> owned; // per box: 1 if owned
+  DevBuf d_nlines;                         // int32 nbox
+  DevBuf d_gidx;                           // int32 nbox x lmax x wmax (-1 pad, owned | 1<<30)
+  DevBuf linv64, loff64, linv32, loff32;   // nbox x lmax x wmax x wmax
+};
+
+// Coarse 2h space: interpolation R_0^T and the coarse Galerkin operator.
+struct CoarseData {
+  int Nc = 0;
+  int64_t nc = 0, ldc = 0;
+  std::vector<int32_t> rowptr, colidx;     // coarse CSR pattern (host)
+  Ell ell;                                 // coarse A_k in ELL form (device)
+  TripleTables tri;
+  DevCsr RT, R;                            // interpolation (n x nc) and restriction
+};
+
+struct Precond {
+  bool ready = false;
+  int sx = 0, sy = 0, overlap = 0;
+  double omega = 1.0;
+  double inner_rtol = 1e-5;
+  int inner_max = 100, inner_restart = 30;
+  RasData ras;
+  CoarseData co;
+  std::vector<AmgLevel> amg;
+  DevBuf coarsest_inv64;                   // dense inverse of the coarsest matrix (FP64)
+  std::vector<double> gt;                  // Kronecker factor G~ (P x P), host
+  DevBuf gtinv64, gtinv32;                 // omega * G~^{-1} (P x P)
+  int inner_its_last = 0, inner_its_total = 0, inner_calls = 0;
+};
+
+// For every coarse ELL position (s * ldc + I): the fine ELL positions
+// (s * ldr + f) and weights whose sum is the entry of R_0 A R_0^T.
+struct CoarsePlan {
+  std::vector<int32_t> rp;
+  std::vector<int64_t> src;
+  std::vector<double> w;
+};
+
+sg_status precond_setup_host(sg_problem* pr, Precond& pc);
+sg_status precond_setup_coarse_plan(sg_problem* pr, Precond& pc, const CoarsePlan& plan);
+sg_status precond_setup_device(sg_problem* pr, Precond& pc, double omega_opt, cudaStream_t st);
+void precond_free(Precond& pc);
+
+}  // namespace sg

@@ -1,0 +1,163 @@
+"""Preconditioner pieces (Sec. 3) through the C ABI versus the FP64 oracle
+(GPU): integer artefacts bit-exact, operators within rounding bounds."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import amg, coarse, galerkin, ras, twolevel
+from sg_inputs import random_block
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # N, L, p, q, sigma2, b, sx, sy, overlap
+    (32, 2, 2, 4, 0.3, 0.5, 2, 2, 1),
+    (36, 3, 2, 4, 0.5, 0.2, 3, 2, 2),
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "N%d_L%d_p%d" % c[:3])
+def pair(request, gpu):
+    import paper_2310_14649_gb300 as sg
+    N, L, p, q, s2, b, sx, sy, ov = request.param
+    prob = sg.sg_setup(N, L, p, q, sigma2=s2, bx=b, by=b)
+    sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200)
+    ref = galerkin.build(N, L, p, q, sigma2=s2, bx=b, by=b)
+    omega = sg.sg_precond_info(prob)[0]
+    tl = twolevel.TwoLevel(ref, sx, sy, ov, exact_coarse=True, omega=omega)
+    return prob, ref, tl, (sx, sy, ov)
+
+
+def dev(X, dtype, ld=None):
+    import torch
+    n, P = X.shape
+    out = torch.zeros((P, ld or n), dtype=dtype, device="cuda")
+    out[:, :n] = torch.from_numpy(np.ascontiguousarray(X.T)).to(dtype)
+    return out
+
+
+def host(Y, n):
+    return Y[:, :n].double().cpu().numpy().T
+
+
+def run(prob, which, X, nout, dtype):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    Xd = dev(X, dtype, X.shape[0] + 3)
+    Yd = torch.full((X.shape[1], nout + 5), float("nan"), dtype=dtype, device="cuda")
+    sg.sg_precond_apply(prob, which, Xd, Yd)
+    torch.cuda.synchronize()
+    return host(Yd, nout), host(Xd, X.shape[0])
+
+
+def test_partitions_bit_exact(pair):
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, (sx, sy, ov) = pair
+    parts = ras.partitions(ref.A(0), ref.N, sx, sy, ov)
+    for b, (idx, own) in enumerate(parts):
+        gi, go = sg.sg_get_partition(prob, b)
+        assert np.array_equal(gi, idx) and np.array_equal(go, own)
+
+
+def test_coarse_pattern_bit_exact(pair):
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, _ = pair
+    RT = abs(coarse.interpolation(ref.N))
+    pat = sp.csr_matrix((np.ones(len(ref.colidx)), ref.colidx, ref.rowptr), shape=(ref.n, ref.n))
+    S = (RT.T @ pat @ RT).tocsr()
+    S.sort_indices()
+    rp, ci = sg.sg_get_coarse_csr(prob)
+    assert np.array_equal(rp, S.indptr) and np.array_equal(ci, S.indices)
+
+
+def test_amg_aggregates_bit_exact(pair):
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, _ = pair
+    levels = amg.setup(tl.Acs[0])
+    nlev = sg.sg_precond_info(prob)[1]
+    assert nlev == len(levels)
+    A = tl.Acs[0]
+    for lev in range(nlev - 1):
+        n, agg = sg.sg_get_amg_level(prob, lev)
+        ragg, _ = amg.aggregate(A)
+        assert n == A.shape[0] and np.array_equal(agg, ragg)
+        A = levels[lev + 1].A
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_transfer_and_coarse_operator(pair, dt):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, _ = pair
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-14 if dt == "f64" else 2e-6
+    nc = tl.nc
+    X = random_block(ref.n, ref.P, seed=31)
+    Y, Xq = run(prob, sg.PC_RESTRICT, X, nc, dtype)
+    Yr = tl.R @ Xq
+    assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))
+    Xc = random_block(nc, ref.P, seed=32)
+    Y, Xq = run(prob, sg.PC_INTERP, Xc, ref.n, dtype)
+    Yr = tl.RT @ Xq
+    assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))
+    Y, Xq = run(prob, sg.PC_COARSE_APPLY, Xc, nc, dtype)
+    Yr = coarse.coarse_apply(tl.Acs, tl.G, Xq)
+    scale = np.max(np.abs(coarse.coarse_apply([abs(a) for a in tl.Acs], abs(tl.G), abs(Xq))))
+    assert np.max(np.abs(Y - Yr)) <= (50 * tol) * scale
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_amg_vcycle(pair, dt):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, _ = pair
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    levels = amg.setup(tl.Acs[0])
+    Xc = random_block(tl.nc, ref.P, seed=33)
+    Y, Xq = run(prob, sg.PC_AMG, Xc, tl.nc, dtype)
+    Yr = amg.vcycle(levels, Xq)
+    tol = 1e-11 if dt == "f64" else 1e-4
+    assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_ras_and_smoother(pair, dt):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, _ = pair
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-11 if dt == "f64" else 1e-4
+    X = random_block(ref.n, ref.P, seed=34)
+    Y, Xq = run(prob, sg.PC_RAS_LOCAL, X, ref.n, dtype)
+    Yr = ras.apply_ras(tl.parts, tl.solvers, Xq)
+    assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))
+    Y, Xq = run(prob, sg.PC_SMOOTH, X, ref.n, dtype)
+    Yr = tl.omega * tl.ras(Xq)
+    assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))
+
+
+def test_omega_estimate_is_the_smoother_radius(pair):
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, _ = pair
+    omega = sg.sg_precond_info(prob)[0]
+    tl1 = twolevel.TwoLevel(ref, *pair[3], exact_coarse=True, omega=None)
+    # both sides run 20 power iterations (FP32 on the GPU, FP64 here)
+    assert abs(omega - tl1.omega) <= 1e-3 * tl1.omega
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_coarse_correction_and_two_level(pair, dt):
+    """With the inner coarse GMRES driven to 1e-13, Q and the two-level
+    cycle match the oracle's exact coarse solve."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, _ = pair
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-9 if dt == "f64" else 2e-4
+    X = random_block(ref.n, ref.P, seed=35)
+    Y, Xq = run(prob, sg.PC_COARSE, X, ref.n, dtype)
+    Yr = tl.RT @ tl.coarse_solve(tl.R @ Xq)
+    assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))
+    Y, Xq = run(prob, sg.PC_TWOLEVEL, X, ref.n, dtype)
+    Yr = tl.apply(Xq)
+    assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))

@@ -1,0 +1,131 @@
+"""sg_solve through the C ABI versus the FP64 oracle (GPU).
+
+Bar (stated with the method): relres <= 1e-8 in the true FP64 residual and
+relative L2 error <= 1e-7 against the oracle's solution."""
+import numpy as np
+import pytest
+
+from oracle import galerkin
+from sg_inputs import CONFIGS, random_block
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(cfg, **pc):
+    import paper_2310_14649_gb300 as sg
+    c = dict(cfg)
+    prob = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], **pc)
+    return prob
+
+
+def zeros(prob):
+    import torch
+    return torch.zeros((prob.P, prob.n), dtype=torch.float64, device="cuda")
+
+
+def to_np(X, n):
+    return X[:, :n].cpu().numpy().T
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_solve_32_matches_direct_oracle(gpu, mode):
+    import paper_2310_14649_gb300 as sg
+    c = CONFIGS["poisson32_L2_p2"]
+    prob = setup(c)
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    X = zeros(prob)
+    info = sg.sg_solve(prob, X, rtol=1e-8, mode=mode)
+    Xh = to_np(X, prob.n)
+    Xd = galerkin.solve_direct(ref)
+    assert info["relres"] <= 1e-8
+    assert galerkin.relres(ref, Xh) <= 1.01e-8
+    err = np.linalg.norm(Xh - Xd) / np.linalg.norm(Xd)
+    assert err <= 1e-7, err
+    assert info["outer_it"] < 60
+    if mode == 1:
+        assert info["ir_steps"] >= 1
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_solve_64_L4_p3_matches_gmres_oracle(gpu, mode):
+    """The 256x256 family (L=4, p=3, q=6, 8x8 boxes, overlap 2) on a 64x64
+    mesh, small enough for the oracle's GMRES to 1e-12."""
+    import paper_2310_14649_gb300 as sg
+    c = dict(CONFIGS["poisson256_L4_p3"], N=64, sx=4, sy=4)
+    prob = setup(c)
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    X = zeros(prob)
+    info = sg.sg_solve(prob, X, rtol=1e-8, mode=mode)
+    Xh = to_np(X, prob.n)
+    Xo, its, _ = galerkin.solve_gmres(ref, tol=1e-12)
+    assert galerkin.relres(ref, Xh) <= 1.01e-8
+    err = np.linalg.norm(Xh - Xo) / np.linalg.norm(Xo)
+    assert err <= 1e-7, err
+
+
+def test_manufactured_rhs_and_warm_start(gpu):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    c = dict(CONFIGS["poisson32_L2_p2"], N=24, L=3, p=2, q=4)
+    prob = setup(c)
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    Xs = random_block(ref.n, ref.P, seed=1234)
+    F = galerkin.apply(ref, Xs)
+    Fd = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+    X = zeros(prob)
+    info = sg.sg_solve(prob, X, F=Fd, rtol=1e-10, mode=0)
+    assert np.linalg.norm(to_np(X, prob.n) - Xs) / np.linalg.norm(Xs) < 1e-8
+    # restarting from the solution needs no iteration
+    info2 = sg.sg_solve(prob, X, F=Fd, rtol=1e-10, mode=0)
+    assert info2["outer_it"] == 0 and info2["relres"] <= 1e-10
+
+
+def test_sigma_zero(gpu):
+    import paper_2310_14649_gb300 as sg
+    c = dict(CONFIGS["poisson32_L2_p2"], sigma2=0.0)
+    prob = setup(c)
+    X = zeros(prob)
+    sg.sg_solve(prob, X, rtol=1e-10, mode=1)
+    Xh = to_np(X, prob.n)
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], 0.0, c["b"], c["b"])
+    Xd = galerkin.solve_direct(ref)
+    assert np.linalg.norm(Xh - Xd) / np.linalg.norm(Xd) < 1e-9
+    assert np.max(np.abs(Xh[:, 1:])) < 1e-10 * np.max(np.abs(Xh[:, 0]))
+
+
+def test_not_converged_and_breakdown(gpu):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    c = CONFIGS["poisson32_L2_p2"]
+    prob = setup(c)
+    X = zeros(prob)
+    info = sg.sg_solve(prob, X, rtol=1e-12, max_it=2, mode=0, allow_not_converged=True)
+    assert info["status"] == 1 and info["outer_it"] == 2 and info["relres"] > 1e-12
+    F = torch.zeros((prob.P, prob.n), dtype=torch.float64, device="cuda")
+    F[0, 5] = float("nan")
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_solve(prob, zeros(prob), F=F, rtol=1e-8)
+    assert e.value.status == -4
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_precond_setup(prob, 0, 2, 1)
+    assert e.value.status == -1
+
+
+def test_solve_full_256_relres(gpu):
+    """The 256x256 mesh, L=4, p=3 (2.3M unknowns): both modes reach the
+    true FP64 relres 1e-8; the oracle checks the residual of the result."""
+    import paper_2310_14649_gb300 as sg
+    c = CONFIGS["poisson256_L4_p3"]
+    prob = setup(c)
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    sols = []
+    for mode in (0, 1):
+        X = zeros(prob)
+        info = sg.sg_solve(prob, X, rtol=1e-8, mode=mode)
+        Xh = to_np(X, prob.n)
+        assert info["relres"] <= 1e-8
+        assert galerkin.relres(ref, Xh) <= 1.02e-8
+        sols.append(Xh)
+    # the two precisions agree to the accuracy both reached
+    assert np.linalg.norm(sols[0] - sols[1]) / np.linalg.norm(sols[0]) < 1e-7
