@@ -13,14 +13,13 @@ import numpy as np
 import scipy.sparse as sp
 
 
-def coarse_hat(Nc, I, J, x, y):
-    """Value at (x, y) of the P1 hat function of coarse grid node (I, J) on
-    the Nc x Nc "/" mesh of the unit square (barycentric coordinates in the
-    coarse triangle that contains the point)."""
-    H = 1.0 / Nc
-    ci = min(int(np.floor(x / H)), Nc - 1)
-    cj = min(int(np.floor(y / H)), Nc - 1)
-    u, v = x / H - ci, y / H - cj            # local coordinates in [0, 1]^2
+def coarse_hat(I, J, i, j):
+    """Value at fine grid node (i, j) (coordinates (i h, j h)) of the P1 hat
+    function of coarse node (I, J) on the 2h "/" mesh.  In units of the
+    coarse spacing the point is (i/2, j/2), so the barycentric coordinates
+    inside the containing coarse triangle are multiples of 1/2 and exact."""
+    ci, cj = i // 2, j // 2
+    u, v = i / 2 - ci, j / 2 - cj            # local coordinates in [0, 1)^2
     if u >= v:   # lower triangle (0,0), (1,0), (1,1)
         verts = [(ci, cj), (ci + 1, cj), (ci + 1, cj + 1)]
         lam = [1 - u, u - v, v]
@@ -39,15 +38,13 @@ def interpolation(N):
     Nc = N // 2
     m, mc = N - 1, Nc - 1
     rows, cols, vals = [], [], []
-    h = 1.0 / N
     for j in range(1, N):
         for i in range(1, N):
             f = (j - 1) * m + (i - 1)
-            x, y = i * h, j * h
             # candidate coarse nodes: corners of the containing coarse cell
             for J in range(max(1, j // 2 - 1), min(Nc - 1, j // 2 + 1) + 1):
                 for I in range(max(1, i // 2 - 1), min(Nc - 1, i // 2 + 1) + 1):
-                    w = coarse_hat(Nc, I, J, x, y)
+                    w = coarse_hat(I, J, i, j)
                     if w != 0.0:
                         rows.append(f)
                         cols.append((J - 1) * mc + (I - 1))
