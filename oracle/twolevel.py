@@ -11,8 +11,9 @@ literally (Q is singular); it is read as (I - Q A) M^{-1}, so that
 which is exactly the pre-smooth / coarse / post-smooth cycle the text
 describes:  z1 = M^{-1} r;  z2 = z1 + Q (r - A z1);  z = z2 + M^{-1}(r - A z2).
 Q = R_0^T A_c^{-1} R_0; A_c^{-1} is applied either exactly (pins) or by an
-inner GMRES preconditioned by the AMG V-cycle on the coarse mean operator
-(the 2GV3 variant: rtol 1e-5, at most 100 iterations).
+inner GMRES (the 2GV3 variant: rtol 1e-5, at most 100 iterations)
+preconditioned by the AMG V-cycle on the coarse mean operator combined with
+the stochastic Kronecker factor, (G~^{-1} kron V-cycle).
 """
 import numpy as np
 import scipy.sparse.linalg as spla
@@ -28,7 +29,8 @@ class TwoLevel:
         A0 = prob.A(0)
         self.parts = ras.partitions(A0, prob.N, sx, sy, overlap)
         self.solvers = ras.local_solvers(A0, self.parts)
-        self.Gt_inv = np.linalg.inv(ras.kronecker_factor(prob)) if local == "kron" else None
+        self.Gk_inv = np.linalg.inv(ras.kronecker_factor(prob))
+        self.Gt_inv = self.Gk_inv if local == "kron" else None
         self.Acs, self.RT = coarse.coarse_matrices(prob)
         self.R = self.RT.T.tocsr()
         self.nc = self.RT.shape[1]
@@ -61,7 +63,8 @@ class TwoLevel:
         if self.exact:
             return galerkin.from_vec(self.coarse_lu.solve(galerkin.to_vec(Rc)), n, P)
         mv = lambda v: galerkin.to_vec(coarse.coarse_apply(self.Acs, self.G, galerkin.from_vec(v, n, P)))
-        pc = lambda v: galerkin.to_vec(amg.vcycle(self.levels, galerkin.from_vec(v, n, P)))
+        gk = self.Gk_inv
+        pc = lambda v: galerkin.to_vec(amg.vcycle(self.levels, galerkin.from_vec(v, n, P)) @ gk)
         x, its, _ = galerkin.gmres(mv, pc, galerkin.to_vec(Rc), tol=self.inner_rtol,
                                    restart=30, max_it=self.inner_max)
         self.inner_its.append(its)

@@ -63,6 +63,7 @@ struct Precond {
   DevBuf coarsest_inv64;                   // dense inverse of the coarsest matrix (FP64)
   std::vector<double> gt;                  // Kronecker factor G~ (P x P), host
   DevBuf gtinv64, gtinv32;                 // omega * G~^{-1} (P x P)
+  DevBuf gkron64, gkron32;                 // G~^{-1} (coarse AMG preconditioner)
   int inner_its_last = 0, inner_its_total = 0, inner_calls = 0;
 };
 
