@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the stochastic Galerkin solve on GB300.
+
+One step = one full solve of the linear stochastic Poisson Galerkin system
+to relres 1e-8 (true FP64 residual) on the 256x256 mesh, L=4, p=3 (P=35,
+2.28M unknowns), q=6 (K=210), 8x8 RAS boxes with overlap 2, 2h coarse grid
+with AMG: FGMRES with the two-level preconditioner, FP32 operator and
+preconditioner inside FP64 iterative refinement.  Inputs are synthetic (the
+paper's workloads are synthetic lognormal fields too) and resident in HBM;
+the matrix values (272 MB FP32 + 545 MB FP64) exceed the 129 MB L2, so no
+flush is needed between steps.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(rank 0 only).  Multi-GPU runs are independent replicas (weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "poisson256_L4_p3"
+METRIC = "SG solve time to relres 1e-8 (FP32 in FP64 refinement, two-level RAS+AMG FGMRES)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (also the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg, iters=2, repeats=1):
+    """Time the FP64 oracle's GMRES (mean-based I kron A_0^{-1}
+    preconditioner) for `iters` iterations from x = 0, `repeats` times, and
+    extrapolate to relres 1e-8 with the residual reduction it achieved."""
+    from oracle import galerkin
+    c = cfg
+    prob = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    pc = galerkin.mean_preconditioner(prob)
+    F = galerkin.to_vec(prob.rhs())
+    mv = lambda v: galerkin.to_vec(galerkin.apply(prob, galerkin.from_vec(v, prob.n, prob.P)))
+    times, rates = [], []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        _, its, hist = galerkin.gmres(mv, pc, F, tol=1e-8, restart=50, max_it=iters)
+        times.append((time.perf_counter() - t0) / max(its, 1))
+        rates.append(hist[-1] ** (1.0 / len(hist)))
+    per_it = statistics.median(times)
+    rate = statistics.median(rates)
+    need = math.log(1e-8) / math.log(rate)
+    return per_it * need * 1e3, per_it, need
+
+
+def run_reference(args):
+    from sg_inputs import CONFIGS
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = CONFIGS[WORKLOAD]
+    from oracle import galerkin
+    c = cfg
+    prob = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    pc = galerkin.mean_preconditioner(prob)
+    F = galerkin.to_vec(prob.rhs())
+    mv = lambda v: galerkin.to_vec(galerkin.apply(prob, galerkin.from_vec(v, prob.n, prob.P)))
+    step_ms, rates = [], []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, its, hist = galerkin.gmres(mv, pc, F, tol=1e-8, restart=50, max_it=2)
+        dt = (time.perf_counter() - t0) / its
+        if s >= args.warmup:
+            step_ms.append(dt)
+            rates.append(hist[-1] ** (1.0 / len(hist)))
+    per_it = statistics.median(step_ms)
+    need = math.log(1e-8) / math.log(statistics.median(rates))
+    value = per_it * need * 1e3
+    sample = ("FP64 oracle GMRES (I kron A_0^{-1} preconditioner), 2 iterations per step from x=0 on "
+              "the full %s system; ms/solve = time per iteration x %.1f iterations predicted by the "
+              "observed residual reduction" % (WORKLOAD, need))
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2310_14649_gb300 as sg
+    from sg_inputs import CONFIGS
+
+    world, rank, local = dist_setup()
+    cfg = CONFIGS[WORKLOAD]
+    c = cfg
+    t0 = time.perf_counter()
+    prob = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"])
+    torch.cuda.synchronize()
+    t_pc = time.perf_counter() - t0
+    n, P = prob.n, prob.P
+    X = torch.zeros((P, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve(mode=1):
+        X.zero_()
+        return sg.sg_solve(prob, X, rtol=1e-8, mode=mode, max_it=400)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    sg.sg_profile(prob, True)
+    l0 = sg.sg_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    infos = [solve() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = sg.sg_launch_count() - l0
+    barrier(world)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_all = max_over_ranks(world, ms)
+    kinds = {}
+    for kind, name in ((0, "apply_fine_f32"), (1, "apply_fine_f64"), (2, "apply_coarse_f32"), (3, "apply_coarse_f64")):
+        cnt, kms = sg.sg_profile_read(prob, kind)
+        kinds[name] = (cnt, kms)
+    sg.sg_profile(prob, False)
+
+    # roofline of the fine FP32 operator apply: algorithmic bytes per launch
+    K, nnz = prob.K, prob.nnzA
+    bytes_f32 = K * nnz * 4 + nnz * 4 + (n + 1) * 4 + 2 * n * P * 4
+    cnt, kms = kinds["apply_fine_f32"]
+    avg_ms = kms / max(cnt, 1)
+    achieved = bytes_f32 / (avg_ms * 1e-3) / 1e9 if cnt else None
+    peak, peak_kind = peaks()
+
+    # plain FP64 solve on the same system (the comparison the metric names)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    info64 = solve(mode=0)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1)
+
+    # end to end through the C ABI with host buffers: F host->device, solve,
+    # X device->host every step
+    Fh = torch.zeros((P, n), dtype=torch.float64).pin_memory()
+    Fd = torch.zeros((P, n), dtype=torch.float64, device="cuda")
+    sg.sg_get_rhs(prob, Fd)
+    Fh.copy_(Fd.cpu())
+    Xh = torch.zeros((P, n), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        Fd.copy_(Fh, non_blocking=True)
+        X.zero_()
+        sg.sg_solve(prob, X, F=Fd, rtol=1e-8, mode=1, max_it=400)
+        Xh.copy_(X, non_blocking=True)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(world, g0.elapsed_time(g1) / args.steps)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, per_it, need = oracle_sample(cfg, iters=2)
+        cpu = {"value": round(val, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle GMRES (I kron A_0^{-1} preconditioner, single-threaded numpy/scipy), "
+                         "2 iterations from x=0 on the full %s system: %.2f s/iteration x %.1f iterations "
+                         "predicted by the observed residual reduction" % (WORKLOAD, per_it, need)}
+
+    tot_kernel = sum(v[1] for v in kinds.values())
+    line = {
+        "metric": METRIC, "value": round(ms_all, 3), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_all, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": c["N"], "L": c["L"], "p": c["p"], "q": c["q"], "P": P, "K": K,
+                   "unknowns": n * P, "ras_boxes": "%dx%d" % (c["sx"], c["sy"]), "overlap": c["overlap"],
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (values 0.82 GB), no flush"},
+        "solve": {"outer_it": infos[-1]["outer_it"], "inner_it": infos[-1]["inner_it"],
+                  "ir_steps": infos[-1]["ir_steps"], "relres": infos[-1]["relres"],
+                  "setup_s": round(t_setup, 3), "precond_setup_s": round(t_pc, 3),
+                  "solves_per_s_all_gpus": round(world * 1e3 / ms_all, 3)},
+        "plain_fp64": {"ms": round(ms64, 3), "outer_it": info64["outer_it"], "relres": info64["relres"],
+                       "speedup_mixed": round(ms64 / ms_all, 3)},
+        "roofline": {"kernel": "sg_apply FP32 (fine Galerkin operator)", "bound": "hbm",
+                     "achieved": round(achieved, 1) if achieved else None, "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
+                     "peak_source": peak_kind, "bytes_per_launch": bytes_f32, "avg_launch_ms": avg_ms,
+                     "launches": cnt, "traffic": None},
+        "kernel_time_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in kinds.items()},
+        "apply_share_of_step": round(tot_kernel / args.steps / ms_all, 3),
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": n * P * 8,
+                "d2h_bytes_per_step": n * P * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -125,6 +125,23 @@ sg_status sg_get_rhs(const sg_problem* prob, double* F_dev, int64_t ld, void* st
 sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t ldx, void* Y_dev,
                    int64_t ldy, void* stream);
 
+/* Kernel used by the FP32 applies of this handle (fine and coarse):
+ *   0 auto (default): the register-specialised kernel when P <= 96 and
+ *     T <= 20000, else the shared-memory kernel;
+ *   1 the shared-memory kernel (any size; FP64 always uses it);
+ *   2 the register-specialised kernel (SG_ERR_UNSUPPORTED if too large).
+ * The specialised kernel is generated from the triple list, compiled for
+ * sm_103a with NVRTC on first use and cached on disk (SG_JIT_CACHE, default
+ * ~/.cache/sg_gb300); this call compiles it now when it will be used.
+ * Errors: SG_ERR_CUDA with the compiler log when compilation fails. */
+sg_status sg_set_apply_kernel(sg_problem* prob, int mode);
+
+/* Code-generation parameters of the register-specialised kernel (its
+ * tile shape): min_blocks = CTAs of 128 threads that must fit on one SM
+ * (bounds registers per thread; 0 = chosen from P), prefetch = input terms
+ * whose values are loaded ahead of use.  Recompiles the kernel. */
+sg_status sg_apply_config(sg_problem* prob, int min_blocks, int prefetch);
+
 /* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
  * sg_apply (F may equal R for an in-place update). */
 sg_status sg_residual(sg_problem* prob, sg_dtype dtype, const void* F_dev, int64_t ldf,
@@ -223,6 +240,20 @@ typedef struct {
  * when max_it is reached first, SG_ERR_BREAKDOWN on non-finite values. */
 sg_status sg_solve(sg_problem* prob, const double* F_dev, int64_t ldf, double* X_dev, int64_t ldx,
                    const sg_solve_opts* opts, sg_solve_info* info, void* stream);
+
+/* Per-launch timing of the operator-apply kernels, for benchmarks.  While
+ * enabled, every apply launched through this handle is bracketed by CUDA
+ * events on its stream (a few microseconds of overhead per launch).
+ * Enabling (or disabling) clears the records.  sg_profile_read waits for
+ * the recorded events and returns the number of launches and their summed
+ * device time in ms for one kind: 0 fine FP32, 1 fine FP64, 2 coarse FP32,
+ * 3 coarse FP64. */
+sg_status sg_profile(sg_problem* prob, int enable);
+sg_status sg_profile_read(sg_problem* prob, int kind, int64_t* launches, double* ms);
+
+/* Number of kernel launches this library has made in the process so far
+ * (all handles); differences bracket a region of interest. */
+sg_status sg_launch_count(int64_t* count);
 
 const char* sg_last_error(void);
 

@@ -15,6 +15,8 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_get_triples", "sg_get_csr", "sg_get_values", "sg_get_rhs", "sg_apply",
            "sg_residual", "sg_precond_setup", "sg_precond_info", "sg_get_partition",
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
+           "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel",
+           "sg_apply_config",
            "SgError", "SG_F32", "SG_F64", "PC_TWOLEVEL", "PC_SMOOTH", "PC_COARSE", "PC_AMG",
            "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL"]
 
@@ -203,3 +205,31 @@ def sg_solve(prob, X, F=None, rtol=1e-8, max_it=500, restart=30, mode=0, inner_r
     out["hist"] = hist[:info.hist_len].copy()
     out["status"] = st
     return out
+
+
+def sg_profile(prob, enable):
+    call("sg_profile", prob.handle, 1 if enable else 0)
+
+
+def sg_profile_read(prob, kind):
+    """(launches, total ms) of one apply kind: 0 fine FP32, 1 fine FP64,
+    2 coarse FP32, 3 coarse FP64."""
+    cnt, ms = ctypes.c_int64(), ctypes.c_double()
+    call("sg_profile_read", prob.handle, kind, ctypes.byref(cnt), ctypes.byref(ms))
+    return cnt.value, ms.value
+
+
+def sg_launch_count():
+    c = ctypes.c_int64()
+    call("sg_launch_count", ctypes.byref(c))
+    return c.value
+
+
+def sg_set_apply_kernel(prob, mode):
+    """0 auto, 1 shared-memory kernel, 2 register-specialised kernel."""
+    call("sg_set_apply_kernel",
+           "sg_apply_config", prob.handle, mode)
+
+
+def sg_apply_config(prob, min_blocks=0, prefetch=8):
+    call("sg_apply_config", prob.handle, min_blocks, prefetch)

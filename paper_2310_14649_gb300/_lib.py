@@ -78,6 +78,11 @@ SIGNATURES = {
     "sg_get_amg_level": [vp, ctypes.c_int, P_i64, P_i32],
     "sg_precond_apply": [vp, ctypes.c_int, ctypes.c_int, vp, i64, vp, i64, vp],
     "sg_solve": [vp, vp, i64, vp, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
+    "sg_profile": [vp, ctypes.c_int],
+    "sg_set_apply_kernel": [vp, ctypes.c_int],
+    "sg_apply_config": [vp, ctypes.c_int, ctypes.c_int],
+    "sg_launch_count": [P_i64],
+    "sg_profile_read": [vp, ctypes.c_int, P_i64, P_f64],
 }
 
 

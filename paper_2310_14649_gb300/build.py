@@ -65,7 +65,9 @@ def build(verbose=False, jobs=None):
             if verbose and err.strip():
                 print(os.path.basename(src), err, file=sys.stderr)
     if jobs_todo or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [cc, "-shared", "-o", LIB] + objs + ARCH + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+        cmd = [cc, "-shared", "-o", LIB] + objs + ARCH + ["-lcudart_static", "-lnvrtc", "-lrt", "-ldl", "-lpthread",
+                                                          "-L", cudalib, "-Xlinker", "-rpath=" + cudalib]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))

@@ -1,4 +1,5 @@
 // C ABI of libsg: argument checking and dispatch (declared in sg.h).
+#include <atomic>
 #include <cstring>
 #include <new>
 
@@ -9,6 +10,11 @@ namespace {
 thread_local std::string g_last_error;
 }
 void set_error(const std::string& msg) { g_last_error = msg; }
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace sg
 
 using namespace sg;
@@ -16,6 +22,12 @@ using namespace sg;
 extern "C" {
 
 const char* sg_last_error(void) { return g_last_error.c_str(); }
+
+sg_status sg_launch_count(int64_t* count) {
+  SG_ARG(count, "sg_launch_count: NULL argument");
+  *count = launch_count();
+  return SG_OK;
+}
 
 sg_status sg_setup(const sg_mesh_desc* mesh, const sg_kl_desc* kl, int p_out, int q_in,
                    sg_problem** out) {
@@ -55,6 +67,7 @@ sg_status sg_setup(const sg_mesh_desc* mesh, const sg_kl_desc* kl, int p_out, in
 sg_status sg_destroy(sg_problem* pr) {
   if (!pr) return SG_OK;
   solver_free(pr);
+  jit_free(pr);
   pr->fine.col.free_();
   pr->fine.v64.free_();
   pr->fine.v32.free_();
@@ -65,6 +78,22 @@ sg_status sg_destroy(sg_problem* pr) {
   pr->tri.off.free_();
   delete pr;
   return SG_OK;
+}
+
+sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
+  SG_ARG(pr && mode >= 0 && mode <= 2, "sg_set_apply_kernel: mode must be 0, 1 or 2");
+  if (mode == 2 && !jit_eligible(pr)) {
+    set_error("sg_set_apply_kernel: the specialised kernel needs P <= 96 and T <= 20000");
+    return SG_ERR_UNSUPPORTED;
+  }
+  pr->apply_mode = mode;
+  if (mode != 1 && jit_eligible(pr)) return jit_apply_build(pr);
+  return SG_OK;
+}
+
+sg_status sg_apply_config(sg_problem* pr, int min_blocks, int prefetch) {
+  SG_ARG(pr, "sg_apply_config: NULL handle");
+  return jit_configure(pr, min_blocks, prefetch);
 }
 
 sg_status sg_get_sizes(const sg_problem* pr, int64_t* n, int* P, int* K, int64_t* nnzA, int64_t* T) {
@@ -148,10 +177,10 @@ sg_status sg_apply(sg_problem* pr, sg_dtype dtype, const void* X, int64_t ldx, v
          "sg_apply: X and Y overlap");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (dtype == SG_F64)
-    return apply_ell<double>(pr->fine, pr->tri, pr->P, pr->K, static_cast<const double*>(X), ldx,
-                             nullptr, 0, static_cast<double*>(Y), ldy, st);
-  return apply_ell<float>(pr->fine, pr->tri, pr->P, pr->K, static_cast<const float*>(X), ldx, nullptr,
-                          0, static_cast<float*>(Y), ldy, st);
+    return apply_op<double>(pr, false, static_cast<const double*>(X), ldx, nullptr, 0, static_cast<double*>(Y),
+                            ldy, st);
+  return apply_op<float>(pr, false, static_cast<const float*>(X), ldx, nullptr, 0, static_cast<float*>(Y), ldy,
+                         st);
 }
 
 sg_status sg_residual(sg_problem* pr, sg_dtype dtype, const void* F, int64_t ldf, const void* X,
@@ -166,10 +195,10 @@ sg_status sg_residual(sg_problem* pr, sg_dtype dtype, const void* F, int64_t ldf
          "sg_residual: F and R overlap with different layouts");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (dtype == SG_F64)
-    return apply_ell<double>(pr->fine, pr->tri, pr->P, pr->K, static_cast<const double*>(X), ldx,
-                             static_cast<const double*>(F), ldf, static_cast<double*>(R), ldr, st);
-  return apply_ell<float>(pr->fine, pr->tri, pr->P, pr->K, static_cast<const float*>(X), ldx,
-                          static_cast<const float*>(F), ldf, static_cast<float*>(R), ldr, st);
+    return apply_op<double>(pr, false, static_cast<const double*>(X), ldx, static_cast<const double*>(F), ldf,
+                            static_cast<double*>(R), ldr, st);
+  return apply_op<float>(pr, false, static_cast<const float*>(X), ldx, static_cast<const float*>(F), ldf,
+                         static_cast<float*>(R), ldr, st);
 }
 
 }  // extern "C"

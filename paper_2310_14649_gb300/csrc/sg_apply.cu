@@ -11,7 +11,7 @@
 // free; the triple list of each output mode is walked warp-uniformly.
 #include <algorithm>
 
-#include "sg_internal.h"
+#include "sg_solver.h"
 
 namespace sg {
 
@@ -131,10 +131,75 @@ sg_status apply_ell(const Ell& A, const TripleTables& tri, int P, int K, const T
   dim3 block(32, W);
   dim3 grid(unsigned((A.n + 31) / 32));
   if (A.n == 0) return SG_OK;
-  k_apply_tile<T><<<grid, block, smem, st>>>(a);
+  k_apply_tile<T><<<grid, block, smem, st>>>(a); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
+
+Profiler::~Profiler() {
+  for (auto& r : pool) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
+}
+
+sg_status Profiler::begin(int kind, cudaStream_t st, size_t& slot) {
+  if (used == pool.size()) {
+    Rec r;
+    SG_CUDA(cudaEventCreate(&r.a));
+    SG_CUDA(cudaEventCreate(&r.b));
+    pool.push_back(r);
+  }
+  slot = used++;
+  pool[slot].kind = kind;
+  SG_CUDA(cudaEventRecord(pool[slot].a, st));
+  return SG_OK;
+}
+
+sg_status Profiler::end(size_t slot, cudaStream_t st) {
+  SG_CUDA(cudaEventRecord(pool[slot].b, st));
+  return SG_OK;
+}
+
+sg_status Profiler::read(int kind, int64_t* launches, double* ms) {
+  int64_t cnt = 0;
+  double tot = 0.0;
+  for (size_t i = 0; i < used; ++i) {
+    if (pool[i].kind != kind) continue;
+    SG_CUDA(cudaEventSynchronize(pool[i].b));
+    float t = 0.0f;
+    SG_CUDA(cudaEventElapsedTime(&t, pool[i].a, pool[i].b));
+    tot += t;
+    ++cnt;
+  }
+  if (launches) *launches = cnt;
+  if (ms) *ms = tot;
+  return SG_OK;
+}
+
+template <typename T>
+sg_status apply_op(sg_problem* pr, bool coarse, const T* X, int64_t ldx, const T* F, int64_t ldf, T* Y,
+                   int64_t ldy, cudaStream_t st) {
+  const Ell& A = coarse ? coarse_ell(pr) : pr->fine;
+  const TripleTables& tri = coarse ? coarse_tri(pr) : pr->tri;
+  size_t slot = 0;
+  const bool on = pr->prof.on;
+  if (on) SG_TRY(pr->prof.begin((coarse ? 2 : 0) + (sizeof(T) == 8 ? 1 : 0), st, slot));
+  const bool spec = sizeof(T) == 4 && pr->apply_mode != 1 && jit_eligible(pr);
+  if (spec) {
+    SG_TRY(jit_apply_launch(pr, A, reinterpret_cast<const float*>(X), ldx, reinterpret_cast<const float*>(F), ldf,
+                            reinterpret_cast<float*>(Y), ldy, st));
+  } else {
+    SG_TRY(apply_ell<T>(A, tri, pr->P, pr->K, X, ldx, F, ldf, Y, ldy, st));
+  }
+  if (on) SG_TRY(pr->prof.end(slot, st));
+  return SG_OK;
+}
+
+template sg_status apply_op<double>(sg_problem*, bool, const double*, int64_t, const double*, int64_t, double*,
+                                    int64_t, cudaStream_t);
+template sg_status apply_op<float>(sg_problem*, bool, const float*, int64_t, const float*, int64_t, float*,
+                                   int64_t, cudaStream_t);
 
 template sg_status apply_ell<double>(const Ell&, const TripleTables&, int, int, const double*, int64_t,
                                      const double*, int64_t, double*, int64_t, cudaStream_t);

@@ -140,10 +140,10 @@ sg_status assemble_fine(sg_problem* pr) {
   for (int k0 = 0; k0 < K; k0 += KC) {
     int kn = std::min(KC, K - k0);
     k_cbar<<<4 * 152, 256>>>(dg.as<double>(), dmi.as<int>(), disf.as<double>(), L, E, pr->g0, k0, kn,
-                             dcb.as<double>());
+                             dcb.as<double>()); note_launch();
     SG_CUDA(cudaGetLastError());
     k_fine_ell<<<4 * 152, 256>>>(dcb.as<double>(), N, n, ldr, k0, kn, A.v64.as<double>(),
-                                 A.v32.as<float>());
+                                 A.v32.as<float>()); note_launch();
     SG_CUDA(cudaGetLastError());
   }
   SG_CUDA(cudaDeviceSynchronize());

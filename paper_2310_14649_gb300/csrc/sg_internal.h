@@ -12,6 +12,9 @@
 namespace sg {
 
 void set_error(const std::string& msg);
+// process-wide count of kernel launches made by the library
+void note_launch();
+int64_t launch_count();
 
 #define SG_CUDA(call)                                                                    \
   do {                                                                                   \
@@ -72,6 +75,37 @@ struct TripleTables {
   DevBuf off;      // int32 P x (nchunk + 1)
 };
 
+// Optional per-launch timing of the operator-apply kernels (bench mode):
+// CUDA events bracket each launch on its stream; read() sums the elapsed
+// times per kind (0 fine FP32, 1 fine FP64, 2 coarse FP32, 3 coarse FP64).
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int kind = 0;
+  };
+  std::vector<Rec> pool;
+  size_t used = 0;
+  sg_status begin(int kind, cudaStream_t st, size_t& slot);
+  sg_status end(size_t slot, cudaStream_t st);
+  sg_status read(int kind, int64_t* launches, double* ms);
+  void reset() { used = 0; }
+  ~Profiler();
+};
+
+// Register-specialised FP32 apply compiled at setup time (sg_jit.cpp).
+constexpr int kJitMaxP = 96;
+constexpr int64_t kJitMaxT = 20000;
+struct JitConfig {
+  int min_blocks = 0;  // 0 = by P
+  int prefetch = 8;
+};
+struct JitApply {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kern = nullptr;
+  bool from_cache = false;
+};
+
 }  // namespace sg
 
 struct sg_problem {
@@ -92,6 +126,10 @@ struct sg_problem {
   sg::TripleTables tri;
   int64_t ld = 0;                      // internal leading dimension of blocks
   sg::SolverState* solver = nullptr;   // preconditioner + solver workspaces
+  sg::Profiler prof;
+  sg::JitApply* jit = nullptr;         // specialised FP32 apply (lazy)
+  sg::JitConfig jit_cfg;
+  int apply_mode = 0;                  // 0 auto, 1 shared-memory kernel, 2 specialised
 };
 
 namespace sg {
@@ -105,4 +143,16 @@ sg_status build_triple_tables(sg_problem* pr, TripleTables& t, int S);
 template <typename T>
 sg_status apply_ell(const Ell& A, const TripleTables& tri, int P, int K, const T* X, int64_t ldx,
                     const T* F, int64_t ldf, T* Y, int64_t ldy, cudaStream_t st);
+std::string jit_apply_source(const sg_problem* pr);
+sg_status jit_apply_build(sg_problem* pr);
+void jit_free(sg_problem* pr);
+sg_status jit_configure(sg_problem* pr, int min_blocks, int prefetch);
+bool jit_eligible(const sg_problem* pr);
+sg_status jit_apply_launch(sg_problem* pr, const Ell& A, const float* X, int64_t ldx, const float* F, int64_t ldf,
+                           float* Y, int64_t ldy, cudaStream_t st);
+// apply_ell on the fine (coarse = false) or coarse family of a problem,
+// timed when the problem's profiler is on
+template <typename T>
+sg_status apply_op(sg_problem* pr, bool coarse, const T* X, int64_t ldx, const T* F, int64_t ldf, T* Y,
+                   int64_t ldy, cudaStream_t st);
 }  // namespace sg

@@ -216,7 +216,7 @@ sg_status vec_mdot(const T* V, int64_t stride, int nv, const T* w, int64_t len, 
     return SG_ERR_ARG;
   }
   k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, nullptr, const_cast<T*>(w), len, 0, partial, counter,
-                                                 out);
+                                                 out); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
@@ -224,7 +224,7 @@ sg_status vec_mdot(const T* V, int64_t stride, int nv, const T* w, int64_t len, 
 template <typename T>
 sg_status vec_maxpy_mdot(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
                          double* partial, unsigned* counter, cudaStream_t st) {
-  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, h, w, len, 1, partial, counter, out);
+  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, h, w, len, 1, partial, counter, out); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
@@ -232,21 +232,21 @@ sg_status vec_maxpy_mdot(const T* V, int64_t stride, int nv, const double* h, T*
 template <typename T>
 sg_status vec_maxpy_norm(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
                          double* partial, unsigned* counter, cudaStream_t st) {
-  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, h, w, len, 2, partial, counter, out);
+  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, h, w, len, 2, partial, counter, out); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
 
 template <typename T>
 sg_status vec_norm2(const T* x, int64_t len, double* out, double* partial, unsigned* counter, cudaStream_t st) {
-  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, 0, 0, nullptr, const_cast<T*>(x), len, 2, partial, counter, out);
+  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, 0, 0, nullptr, const_cast<T*>(x), len, 2, partial, counter, out); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
 
 template <typename T>
 sg_status vec_scale_by(const T* x, T* y, int64_t len, const double* den, bool take_sqrt, cudaStream_t st) {
-  k_scale_by<T><<<grid_for(len), 256, 0, st>>>(x, y, len, den, take_sqrt);
+  k_scale_by<T><<<grid_for(len), 256, 0, st>>>(x, y, len, den, take_sqrt); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
@@ -256,7 +256,7 @@ sg_status vec_axpy_multi(const T* V, int64_t stride, int nv, const double* coef,
                          cudaStream_t st) {
   for (int i0 = 0; i0 < nv; i0 += kMaxV) {
     int cnt = nv - i0 < kMaxV ? nv - i0 : kMaxV;
-    k_axpy_multi<T><<<grid_for(len), 256, 0, st>>>(V + int64_t(i0) * stride, stride, cnt, coef + i0, x, len);
+    k_axpy_multi<T><<<grid_for(len), 256, 0, st>>>(V + int64_t(i0) * stride, stride, cnt, coef + i0, x, len); note_launch();
     SG_CUDA(cudaGetLastError());
   }
   return SG_OK;
@@ -264,31 +264,31 @@ sg_status vec_axpy_multi(const T* V, int64_t stride, int nv, const double* coef,
 
 template <typename Ti, typename To>
 sg_status vec_convert(const Ti* x, To* y, int64_t len, const double* num, const double* den, cudaStream_t st) {
-  k_convert<Ti, To><<<grid_for(len), 256, 0, st>>>(x, y, len, num, den);
+  k_convert<Ti, To><<<grid_for(len), 256, 0, st>>>(x, y, len, num, den); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
 
 sg_status vec_add_scaled_f32(double* x, const float* d, int64_t len, const double* s2, cudaStream_t st) {
-  k_add_scaled_f32<<<grid_for(len), 256, 0, st>>>(x, d, len, s2);
+  k_add_scaled_f32<<<grid_for(len), 256, 0, st>>>(x, d, len, s2); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
 
 sg_status gmres_init(GmresState s, int m, const double* beta2, cudaStream_t st) {
-  k_gmres_init<<<1, 64, 0, st>>>(s, m, beta2);
+  k_gmres_init<<<1, 64, 0, st>>>(s, m, beta2); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
 
 sg_status gmres_givens(GmresState s, int m, int j, double* host_est, cudaStream_t st) {
-  k_gmres_givens<<<1, 32, 0, st>>>(s, m, j, host_est);
+  k_gmres_givens<<<1, 32, 0, st>>>(s, m, j, host_est); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
 
 sg_status gmres_backsolve(GmresState s, int m, int k, cudaStream_t st) {
-  k_gmres_backsolve<<<1, 32, 0, st>>>(s, m, k);
+  k_gmres_backsolve<<<1, 32, 0, st>>>(s, m, k); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }

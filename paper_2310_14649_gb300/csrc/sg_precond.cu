@@ -212,7 +212,7 @@ sg_status spmm(const DevCsr& A, const T* X, int64_t ldx, const T* B, int64_t ldb
   if (A.n == 0) return SG_OK;
   dim3 grid(unsigned((A.n + 127) / 128), unsigned(P));
   k_spmm<T><<<grid, 128, 0, st>>>(A.n, A.rowptr.as<int>(), A.col.as<int>(), dv<T>(A.v64, A.v32), X, ldx, B, ldb, Y,
-                                  ldy, op);
+                                  ldy, op); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
@@ -239,7 +239,7 @@ sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld,
   dim3 grid(unsigned(D.nbox), unsigned(nchunk));
   k_ras_local<T><<<grid, threads, smem, st>>>(R, ld, Z, P, MC, D.wmax, D.lmax, D.d_nlines.as<int>(),
                                               D.d_gidx.as<int>(), dv<T>(D.linv64, D.linv32),
-                                              dv<T>(D.loff64, D.loff32));
+                                              dv<T>(D.loff64, D.loff32)); note_launch();
   SG_CUDA(cudaGetLastError());
   if (transform) SG_TRY(node_transform<T>(Z, ld, n, P, dv<T>(pc.gtinv64, pc.gtinv32), st));
   return SG_OK;
@@ -253,7 +253,7 @@ sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStr
     SG_CUDA(cudaFuncSetAttribute(k_node_transform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr[sizeof(T) == 8] = true;
   }
-  k_node_transform<T><<<unsigned((n + 127) / 128), 128, smem, st>>>(Z, ld, n, P, M);
+  k_node_transform<T><<<unsigned((n + 127) / 128), 128, smem, st>>>(Z, ld, n, P, M); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
@@ -266,7 +266,7 @@ sg_status amg_vcycle(const Precond& pc, AmgWork<T>& w, int P, cudaStream_t st) {
   for (int l = 0; l < nl - 1; ++l) {
     const AmgLevel& L = pc.amg[l];
     dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
-    k_diag<T><<<g, 128, 0, st>>>(L.n, dv<T>(L.dinv64, L.dinv32), w.b[l], L.ld, w.x[l], L.ld, 0);
+    k_diag<T><<<g, 128, 0, st>>>(L.n, dv<T>(L.dinv64, L.dinv32), w.b[l], L.ld, w.x[l], L.ld, 0); note_launch();
     SG_CUDA(cudaGetLastError());
     SG_TRY(spmm<T>(L.A, w.x[l], L.ld, w.b[l], L.ld, w.t[l], L.ld, P, 2, st));
     SG_TRY(spmm<T>(L.R, w.t[l], L.ld, nullptr, 0, w.b[l + 1], pc.amg[l + 1].ld, P, 0, st));
@@ -275,7 +275,7 @@ sg_status amg_vcycle(const Precond& pc, AmgWork<T>& w, int P, cudaStream_t st) {
     const AmgLevel& L = pc.amg[nl - 1];
     dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
     k_dense_solve<T><<<g, 128, 0, st>>>(int(L.n), pc.coarsest_inv64.as<double>(), w.b[nl - 1], L.ld, w.x[nl - 1],
-                                        L.ld);
+                                        L.ld); note_launch();
     SG_CUDA(cudaGetLastError());
   }
   for (int l = nl - 2; l >= 0; --l) {
@@ -283,7 +283,7 @@ sg_status amg_vcycle(const Precond& pc, AmgWork<T>& w, int P, cudaStream_t st) {
     dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
     SG_TRY(spmm<T>(L.Pm, w.x[l + 1], pc.amg[l + 1].ld, nullptr, 0, w.x[l], L.ld, P, 1, st));
     SG_TRY(spmm<T>(L.A, w.x[l], L.ld, w.b[l], L.ld, w.t[l], L.ld, P, 2, st));
-    k_diag<T><<<g, 128, 0, st>>>(L.n, dv<T>(L.dinv64, L.dinv32), w.t[l], L.ld, w.x[l], L.ld, 1);
+    k_diag<T><<<g, 128, 0, st>>>(L.n, dv<T>(L.dinv64, L.dinv32), w.t[l], L.ld, w.x[l], L.ld, 1); note_launch();
     SG_CUDA(cudaGetLastError());
   }
   return SG_OK;
@@ -306,7 +306,7 @@ sg_status precond_setup_coarse_plan(sg_problem* pr, Precond& pc, const CoarsePla
   SG_TRY(C.ell.v32.alloc(size_t(K) * npos * 4));
   k_coarse_values<<<4 * 152, 256>>>(pr->fine.v64.as<double>(), int64_t(pr->fine.S) * pr->fine.ldr, rp.as<int>(),
                                     src.as<int64_t>(), w.as<double>(), npos, K, C.ell.v64.as<double>(),
-                                    C.ell.v32.as<float>());
+                                    C.ell.v32.as<float>()); note_launch();
   SG_CUDA(cudaGetLastError());
   SG_CUDA(cudaDeviceSynchronize());
   SG_TRY(build_triple_tables(pr, C.tri, S));
@@ -317,7 +317,7 @@ sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w) {
   DevBuf out;
   SG_TRY(out.alloc(size_t(pr->K) * 8));
   const int64_t kstride = int64_t(pr->fine.S) * pr->fine.ldr;
-  k_frob<<<pr->K, 256>>>(pr->fine.v64.as<double>(), kstride, pr->K, out.as<double>());
+  k_frob<<<pr->K, 256>>>(pr->fine.v64.as<double>(), kstride, pr->K, out.as<double>()); note_launch();
   SG_CUDA(cudaGetLastError());
   w.resize(pr->K);
   SG_CUDA(cudaMemcpy(w.data(), out.ptr, size_t(pr->K) * 8, cudaMemcpyDeviceToHost));

@@ -232,10 +232,10 @@ struct SolverCtx {
   }
 
   sg_status apply_fine(const T* X, T* Y, const T* F, cudaStream_t st) {
-    return apply_ell<T>(pr->fine, pr->tri, pr->P, pr->K, X, ld, F, ld, Y, ld, st);
+    return apply_op<T>(pr, false, X, ld, F, ld, Y, ld, st);
   }
   sg_status apply_coarse(const T* X, T* Y, cudaStream_t st) {
-    return apply_ell<T>(pc->co.ell, pc->co.tri, pr->P, pr->K, X, ldc, nullptr, 0, Y, ldc, st);
+    return apply_op<T>(pr, true, X, ldc, nullptr, 0, Y, ldc, st);
   }
   // AMG V-cycle per mode on a coarse block
   sg_status amg(const T* B, T* X, cudaStream_t st) {
@@ -313,6 +313,9 @@ struct SolverState {
     if (host) cudaFreeHost(host);
   }
 };
+
+const Ell& coarse_ell(const sg_problem* pr) { return pr->solver->pc.co.ell; }
+const TripleTables& coarse_tri(const sg_problem* pr) { return pr->solver->pc.co.tri; }
 
 void solver_free(sg_problem* pr) {
   delete pr->solver;
@@ -512,6 +515,18 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   return SG_OK;
 }
 
+sg_status sg_profile(sg_problem* pr, int enable) {
+  SG_ARG(pr, "sg_profile: NULL handle");
+  pr->prof.on = enable != 0;
+  pr->prof.reset();
+  return SG_OK;
+}
+
+sg_status sg_profile_read(sg_problem* pr, int kind, int64_t* launches, double* ms) {
+  SG_ARG(pr && kind >= 0 && kind < 4, "sg_profile_read: bad argument");
+  return pr->prof.read(kind, launches, ms);
+}
+
 sg_status sg_precond_info(const sg_problem* pr, double* omega, int* amg_levels, int64_t* nc, int* inner_its_last) {
   SG_ARG(pr && pr->solver && pr->solver->pc.ready, "sg_precond_info: no preconditioner set up");
   const Precond& pc = pr->solver->pc;
@@ -624,7 +639,7 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
     const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
     const int max_ir = o->max_ir > 0 ? o->max_ir : 20;
     for (int ir = 0;; ++ir) {
-      SG_TRY(apply_ell<double>(pr->fine, pr->tri, P, pr->K, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+      SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
       SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 1, dp<double>(c64->fine.partial),
                                dp<unsigned>(c64->fine.counter), st));
       SG_CUDA(cudaMemcpyAsync(S.host + 1, scal + 1, 8, cudaMemcpyDeviceToHost, st));
@@ -650,7 +665,7 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
     }
   }
   // true FP64 residual of the returned iterate
-  SG_TRY(apply_ell<double>(pr->fine, pr->tri, P, pr->K, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+  SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
   SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 2, dp<double>(c64->fine.partial),
                            dp<unsigned>(c64->fine.counter), st));
   SG_CUDA(cudaMemcpyAsync(S.host + 2, scal + 2, 8, cudaMemcpyDeviceToHost, st));

@@ -76,6 +76,8 @@ struct CoarsePlan {
 };
 
 sg_status precond_setup_host(sg_problem* pr, Precond& pc);
+const Ell& coarse_ell(const sg_problem* pr);
+const TripleTables& coarse_tri(const sg_problem* pr);
 sg_status precond_setup_coarse_plan(sg_problem* pr, Precond& pc, const CoarsePlan& plan);
 sg_status precond_setup_device(sg_problem* pr, Precond& pc, double omega_opt, cudaStream_t st);
 void precond_free(Precond& pc);

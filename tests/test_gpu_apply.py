@@ -73,9 +73,10 @@ def test_stiffness_values(gpu, N, L, p, q, s2, b):
     assert np.max(np.abs(vals - ref.vals)) < 1e-13 * scale
 
 
-def check_apply(prob, ref, X, dtype, ld=None):
+def check_apply(prob, ref, X, dtype, ld=None, kernel=0):
     import torch
     import paper_2310_14649_gb300 as sg
+    sg.sg_set_apply_kernel(prob, kernel)
     Xd = to_dev(X, dtype, ld)
     Yd = torch.full_like(Xd, float("nan"))
     sg.sg_apply(prob, Xd, Yd)
@@ -89,16 +90,19 @@ def check_apply(prob, ref, X, dtype, ld=None):
     return Yd
 
 
-@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("dt", ["f64", "f32", "f32-shared"])
 @pytest.mark.parametrize("N,L,p,q", [(32, 2, 2, 4), (33, 3, 3, 6), (2, 2, 1, 2), (9, 0, 0, 0), (40, 1, 5, 10)])
 def test_apply_vs_oracle(gpu, dt, N, L, p, q):
+    """FP64 (shared-memory kernel), FP32 register-specialised kernel and
+    FP32 shared-memory kernel, each against the oracle."""
     import torch
     dtype = torch.float64 if dt == "f64" else torch.float32
+    kernel = 1 if dt == "f32-shared" else (2 if dt == "f32" else 0)
     prob, ref = setup_pair(N, L, p, q)
     X = random_block(ref.n, ref.P, seed=3)
-    check_apply(prob, ref, X, dtype)
+    check_apply(prob, ref, X, dtype, kernel=kernel)
     # ragged leading dimension and a second, different input
-    check_apply(prob, ref, random_block(ref.n, ref.P, seed=4), dtype, ld=ref.n + 37)
+    check_apply(prob, ref, random_block(ref.n, ref.P, seed=4), dtype, ld=ref.n + 37, kernel=kernel)
 
 
 def test_residual_in_place(gpu):
@@ -137,7 +141,8 @@ def test_apply_full_size_sampled_rows(gpu):
     rows = np.unique(np.concatenate([[0, 1, ref.n - 1, ref.n // 2],
                                      np.random.default_rng(0).integers(0, ref.n, 60)]))
     X = random_block(ref.n, ref.P, seed=21)
-    for dtype, u in ((torch.float64, U64), (torch.float32, U32)):
+    for dtype, u, kernel in ((torch.float64, U64, 0), (torch.float32, U32, 2), (torch.float32, U32, 1)):
+        sg.sg_set_apply_kernel(prob, kernel)
         Xd = to_dev(X, dtype)
         Yd = torch.empty_like(Xd)
         sg.sg_apply(prob, Xd, Yd)
@@ -163,3 +168,13 @@ def test_bad_arguments(gpu):
     Y = torch.zeros_like(X)
     st = _lib.lib().sg_apply(prob.handle, 0, _lib.dev_ptr(X), ref.n - 1, _lib.dev_ptr(Y), ref.n, None)
     assert st == -1
+
+
+@pytest.mark.parametrize("cfg", [(0, 8), (1, 0), (4, 32)])
+def test_specialised_kernel_configs(gpu, cfg):
+    """Every code-generation configuration computes the same operator."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(20, 3, 3, 6)
+    sg.sg_apply_config(prob, *cfg)
+    check_apply(prob, ref, random_block(ref.n, ref.P, seed=12), torch.float32, kernel=2)
