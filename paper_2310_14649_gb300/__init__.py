@@ -227,8 +227,7 @@ def sg_launch_count():
 
 def sg_set_apply_kernel(prob, mode):
     """0 auto, 1 shared-memory kernel, 2 register-specialised kernel."""
-    call("sg_set_apply_kernel",
-           "sg_apply_config", prob.handle, mode)
+    call("sg_set_apply_kernel", prob.handle, mode)
 
 
 def sg_apply_config(prob, min_blocks=0, prefetch=8):
