@@ -126,8 +126,8 @@ sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t 
                    int64_t ldy, void* stream);
 
 /* Kernel used by the FP32 applies of this handle (fine and coarse):
- *   0 auto (default): the register-specialised kernel when P <= 96 and
- *     T <= 20000, else the shared-memory kernel;
+ *   0 auto (default): the register-specialised kernel when P <= 128 and
+ *     T <= 40000, else the shared-memory kernel;
  *   1 the shared-memory kernel (any size; FP64 always uses it);
  *   2 the register-specialised kernel (SG_ERR_UNSUPPORTED if too large).
  * The specialised kernel is generated from the triple list, compiled for
@@ -136,11 +136,25 @@ sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t 
  * Errors: SG_ERR_CUDA with the compiler log when compilation fails. */
 sg_status sg_set_apply_kernel(sg_problem* prob, int mode);
 
-/* Code-generation parameters of the register-specialised kernel (its
- * tile shape): min_blocks = CTAs of 128 threads that must fit on one SM
- * (bounds registers per thread; 0 = chosen from P), prefetch = input terms
- * whose values are loaded ahead of use.  Recompiles the kernel. */
-sg_status sg_apply_config(sg_problem* prob, int min_blocks, int prefetch);
+/* Tile shape of the register-specialised kernel: rows per thread (1, or 2
+ * adjacent rows updated with the paired FP32 FMA), output groups (1..4:
+ * the P outputs split across groups of 4 warps), prefetch (input terms
+ * whose values are loaded ahead, 0..64) and min_blocks (CTAs per SM asked
+ * of the register allocator, 1..8).  Recompiles the kernel.
+ * Errors: SG_ERR_ARG out of range, SG_ERR_CUDA compile failure. */
+sg_status sg_apply_config(sg_problem* prob, int rows, int groups, int prefetch, int min_blocks);
+
+/* Autotuner: compiles the candidate tile shapes, times each on this
+ * problem's fine operator with CUDA events, keeps the fastest and stores
+ * the choice in the kernel cache directory (keyed by the triple structure,
+ * n and the device name) so later setups reuse it unless force != 0.
+ * best_ms (may be NULL) receives the time of the chosen shape.
+ * Synchronous; allocates two temporary blocks. */
+sg_status sg_apply_autotune(sg_problem* prob, int force, double* best_ms);
+
+/* Current tile shape (rows, groups, prefetch, min_blocks into cfg4) and the
+ * seconds spent compiling or loading the kernel. */
+sg_status sg_apply_info(const sg_problem* prob, int* cfg4, double* compile_s);
 
 /* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
  * sg_apply (F may equal R for an in-place update). */

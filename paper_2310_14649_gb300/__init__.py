@@ -16,7 +16,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_residual", "sg_precond_setup", "sg_precond_info", "sg_get_partition",
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel",
-           "sg_apply_config",
+           "sg_apply_config", "sg_apply_autotune", "sg_apply_info",
            "SgError", "SG_F32", "SG_F64", "PC_TWOLEVEL", "PC_SMOOTH", "PC_COARSE", "PC_AMG",
            "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL"]
 
@@ -230,5 +230,19 @@ def sg_set_apply_kernel(prob, mode):
     call("sg_set_apply_kernel", prob.handle, mode)
 
 
-def sg_apply_config(prob, min_blocks=0, prefetch=8):
-    call("sg_apply_config", prob.handle, min_blocks, prefetch)
+def sg_apply_config(prob, rows=1, groups=1, prefetch=8, min_blocks=1):
+    call("sg_apply_config", prob.handle, rows, groups, prefetch, min_blocks)
+
+
+def sg_apply_autotune(prob, force=False):
+    ms = ctypes.c_double()
+    call("sg_apply_autotune", prob.handle, 1 if force else 0, ctypes.byref(ms))
+    return ms.value
+
+
+def sg_apply_info(prob):
+    cfg = np.zeros(4, dtype=np.int32)
+    cs = ctypes.c_double()
+    call("sg_apply_info", prob.handle, _lib.ptr(cfg, ctypes.c_int32), ctypes.byref(cs))
+    return {"rows": int(cfg[0]), "groups": int(cfg[1]), "prefetch": int(cfg[2]), "min_blocks": int(cfg[3]),
+            "compile_s": cs.value}

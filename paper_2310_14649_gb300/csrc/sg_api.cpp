@@ -83,7 +83,7 @@ sg_status sg_destroy(sg_problem* pr) {
 sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
   SG_ARG(pr && mode >= 0 && mode <= 2, "sg_set_apply_kernel: mode must be 0, 1 or 2");
   if (mode == 2 && !jit_eligible(pr)) {
-    set_error("sg_set_apply_kernel: the specialised kernel needs P <= 96 and T <= 20000");
+    set_error("sg_set_apply_kernel: the specialised kernel needs P <= 128 and T <= 40000");
     return SG_ERR_UNSUPPORTED;
   }
   pr->apply_mode = mode;
@@ -91,9 +91,32 @@ sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
   return SG_OK;
 }
 
-sg_status sg_apply_config(sg_problem* pr, int min_blocks, int prefetch) {
+sg_status sg_apply_config(sg_problem* pr, int rows, int groups, int prefetch, int min_blocks) {
   SG_ARG(pr, "sg_apply_config: NULL handle");
-  return jit_configure(pr, min_blocks, prefetch);
+  JitConfig c;
+  c.rows = rows;
+  c.groups = groups;
+  c.prefetch = prefetch;
+  c.min_blocks = min_blocks;
+  return jit_configure(pr, c);
+}
+
+sg_status sg_apply_autotune(sg_problem* pr, int force, double* best_ms) {
+  SG_ARG(pr, "sg_apply_autotune: NULL handle");
+  return jit_autotune(pr, force, best_ms);
+}
+
+sg_status sg_apply_info(const sg_problem* pr, int* cfg4, double* compile_s) {
+  SG_ARG(pr, "sg_apply_info: NULL handle");
+  const JitConfig c = pr->jit_cfg_set ? pr->jit_cfg : jit_default_config(pr);
+  if (cfg4) {
+    cfg4[0] = c.rows;
+    cfg4[1] = c.groups;
+    cfg4[2] = c.prefetch;
+    cfg4[3] = c.min_blocks;
+  }
+  if (compile_s) *compile_s = pr->jit ? pr->jit->compile_s : 0.0;
+  return SG_OK;
 }
 
 sg_status sg_get_sizes(const sg_problem* pr, int64_t* n, int* P, int* K, int64_t* nnzA, int64_t* T) {

@@ -94,16 +94,19 @@ struct Profiler {
 };
 
 // Register-specialised FP32 apply compiled at setup time (sg_jit.cpp).
-constexpr int kJitMaxP = 96;
-constexpr int64_t kJitMaxT = 20000;
+constexpr int kJitMaxP = 128;
+constexpr int64_t kJitMaxT = 40000;
 struct JitConfig {
-  int min_blocks = 0;  // 0 = by P
-  int prefetch = 8;
+  int rows = 1;        // rows per thread (2: paired FP32 FMA)
+  int groups = 1;      // output groups (warp groups of 4 warps)
+  int prefetch = 8;    // input terms loaded ahead
+  int min_blocks = 1;  // CTAs per SM requested from the register allocator
 };
 struct JitApply {
   cudaLibrary_t lib = nullptr;
   cudaKernel_t kern = nullptr;
   bool from_cache = false;
+  double compile_s = 0.0;
 };
 
 }  // namespace sg
@@ -129,6 +132,7 @@ struct sg_problem {
   sg::Profiler prof;
   sg::JitApply* jit = nullptr;         // specialised FP32 apply (lazy)
   sg::JitConfig jit_cfg;
+  bool jit_cfg_set = false;
   int apply_mode = 0;                  // 0 auto, 1 shared-memory kernel, 2 specialised
 };
 
@@ -143,10 +147,12 @@ sg_status build_triple_tables(sg_problem* pr, TripleTables& t, int S);
 template <typename T>
 sg_status apply_ell(const Ell& A, const TripleTables& tri, int P, int K, const T* X, int64_t ldx,
                     const T* F, int64_t ldf, T* Y, int64_t ldy, cudaStream_t st);
-std::string jit_apply_source(const sg_problem* pr);
+std::string jit_apply_source(const sg_problem* pr, const JitConfig& c);
+JitConfig jit_default_config(const sg_problem* pr);
+sg_status jit_autotune(sg_problem* pr, int force, double* best_ms);
 sg_status jit_apply_build(sg_problem* pr);
 void jit_free(sg_problem* pr);
-sg_status jit_configure(sg_problem* pr, int min_blocks, int prefetch);
+sg_status jit_configure(sg_problem* pr, const JitConfig& c);
 bool jit_eligible(const sg_problem* pr);
 sg_status jit_apply_launch(sg_problem* pr, const Ell& A, const float* X, int64_t ldx, const float* F, int64_t ldf,
                            float* Y, int64_t ldy, cudaStream_t st);

@@ -170,11 +170,24 @@ def test_bad_arguments(gpu):
     assert st == -1
 
 
-@pytest.mark.parametrize("cfg", [(0, 8), (1, 0), (4, 32)])
-def test_specialised_kernel_configs(gpu, cfg):
-    """Every code-generation configuration computes the same operator."""
+@pytest.mark.parametrize("cfg", [(1, 1, 8, 1), (2, 1, 16, 1), (1, 2, 0, 2), (2, 3, 32, 1), (1, 4, 4, 1)])
+@pytest.mark.parametrize("N", [20, 21])
+def test_specialised_kernel_configs(gpu, cfg, N):
+    """Every tile shape (rows per thread, output groups, prefetch, CTAs per
+    SM) computes the same operator, for even and odd row counts."""
     import torch
     import paper_2310_14649_gb300 as sg
-    prob, ref = setup_pair(20, 3, 3, 6)
+    prob, ref = setup_pair(N, 3, 3, 6)
     sg.sg_apply_config(prob, *cfg)
     check_apply(prob, ref, random_block(ref.n, ref.P, seed=12), torch.float32, kernel=2)
+    check_apply(prob, ref, random_block(ref.n, ref.P, seed=13), torch.float32, kernel=2, ld=ref.n + 3)
+
+
+def test_autotune_picks_a_valid_shape(gpu):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(48, 2, 2, 4)
+    ms = sg.sg_apply_autotune(prob, force=True)
+    info = sg.sg_apply_info(prob)
+    assert ms > 0 and info["rows"] in (1, 2) and 1 <= info["groups"] <= 4
+    check_apply(prob, ref, random_block(ref.n, ref.P, seed=14), torch.float32, kernel=2)
