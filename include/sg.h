@@ -137,12 +137,15 @@ sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t 
 sg_status sg_set_apply_kernel(sg_problem* prob, int mode);
 
 /* Tile shape of the register-specialised kernel: rows per thread (1, or 2
- * adjacent rows updated with the paired FP32 FMA), output groups (1..4:
- * the P outputs split across groups of 4 warps), prefetch (input terms
- * whose values are loaded ahead, 0..64) and min_blocks (CTAs per SM asked
- * of the register allocator, 1..8).  Recompiles the kernel.
+ * adjacent rows updated with the paired FP32 FMA), output groups and input
+ * groups (1..4 each, product <= 8: the outputs and the gathered inputs are
+ * split across groups of 4 warps whose partial sums meet in shared
+ * memory), prefetch (input terms whose values are loaded ahead, 0..64) and
+ * min_blocks (CTAs per SM asked of the register allocator, 1..8).
+ * Recompiles the kernel.
  * Errors: SG_ERR_ARG out of range, SG_ERR_CUDA compile failure. */
-sg_status sg_apply_config(sg_problem* prob, int rows, int groups, int prefetch, int min_blocks);
+sg_status sg_apply_config(sg_problem* prob, int rows, int groups, int igroups, int prefetch,
+                          int min_blocks);
 
 /* Autotuner: compiles the candidate tile shapes, times each on this
  * problem's fine operator with CUDA events, keeps the fastest and stores
@@ -152,9 +155,9 @@ sg_status sg_apply_config(sg_problem* prob, int rows, int groups, int prefetch, 
  * Synchronous; allocates two temporary blocks. */
 sg_status sg_apply_autotune(sg_problem* prob, int force, double* best_ms);
 
-/* Current tile shape (rows, groups, prefetch, min_blocks into cfg4) and the
- * seconds spent compiling or loading the kernel. */
-sg_status sg_apply_info(const sg_problem* prob, int* cfg4, double* compile_s);
+/* Current tile shape (rows, groups, igroups, prefetch, min_blocks into
+ * cfg5) and the seconds spent compiling or loading the kernel. */
+sg_status sg_apply_info(const sg_problem* prob, int* cfg5, double* compile_s);
 
 /* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
  * sg_apply (F may equal R for an in-place update). */

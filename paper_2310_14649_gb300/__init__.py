@@ -230,8 +230,8 @@ def sg_set_apply_kernel(prob, mode):
     call("sg_set_apply_kernel", prob.handle, mode)
 
 
-def sg_apply_config(prob, rows=1, groups=1, prefetch=8, min_blocks=1):
-    call("sg_apply_config", prob.handle, rows, groups, prefetch, min_blocks)
+def sg_apply_config(prob, rows=1, groups=1, igroups=1, prefetch=8, min_blocks=1):
+    call("sg_apply_config", prob.handle, rows, groups, igroups, prefetch, min_blocks)
 
 
 def sg_apply_autotune(prob, force=False):
@@ -241,8 +241,8 @@ def sg_apply_autotune(prob, force=False):
 
 
 def sg_apply_info(prob):
-    cfg = np.zeros(4, dtype=np.int32)
+    cfg = np.zeros(5, dtype=np.int32)
     cs = ctypes.c_double()
     call("sg_apply_info", prob.handle, _lib.ptr(cfg, ctypes.c_int32), ctypes.byref(cs))
-    return {"rows": int(cfg[0]), "groups": int(cfg[1]), "prefetch": int(cfg[2]), "min_blocks": int(cfg[3]),
-            "compile_s": cs.value}
+    return {"rows": int(cfg[0]), "groups": int(cfg[1]), "igroups": int(cfg[2]), "prefetch": int(cfg[3]),
+            "min_blocks": int(cfg[4]), "compile_s": cs.value}

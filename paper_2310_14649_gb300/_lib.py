@@ -80,7 +80,7 @@ SIGNATURES = {
     "sg_solve": [vp, vp, i64, vp, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
     "sg_profile": [vp, ctypes.c_int],
     "sg_set_apply_kernel": [vp, ctypes.c_int],
-    "sg_apply_config": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "sg_apply_config": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sg_apply_autotune": [vp, ctypes.c_int, P_f64],
     "sg_apply_info": [vp, P_i32, P_f64],
     "sg_launch_count": [P_i64],

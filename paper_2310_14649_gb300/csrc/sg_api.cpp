@@ -91,11 +91,12 @@ sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
   return SG_OK;
 }
 
-sg_status sg_apply_config(sg_problem* pr, int rows, int groups, int prefetch, int min_blocks) {
+sg_status sg_apply_config(sg_problem* pr, int rows, int groups, int igroups, int prefetch, int min_blocks) {
   SG_ARG(pr, "sg_apply_config: NULL handle");
   JitConfig c;
   c.rows = rows;
   c.groups = groups;
+  c.igroups = igroups;
   c.prefetch = prefetch;
   c.min_blocks = min_blocks;
   return jit_configure(pr, c);
@@ -106,14 +107,15 @@ sg_status sg_apply_autotune(sg_problem* pr, int force, double* best_ms) {
   return jit_autotune(pr, force, best_ms);
 }
 
-sg_status sg_apply_info(const sg_problem* pr, int* cfg4, double* compile_s) {
+sg_status sg_apply_info(const sg_problem* pr, int* cfg5, double* compile_s) {
   SG_ARG(pr, "sg_apply_info: NULL handle");
   const JitConfig c = pr->jit_cfg_set ? pr->jit_cfg : jit_default_config(pr);
-  if (cfg4) {
-    cfg4[0] = c.rows;
-    cfg4[1] = c.groups;
-    cfg4[2] = c.prefetch;
-    cfg4[3] = c.min_blocks;
+  if (cfg5) {
+    cfg5[0] = c.rows;
+    cfg5[1] = c.groups;
+    cfg5[2] = c.igroups;
+    cfg5[3] = c.prefetch;
+    cfg5[4] = c.min_blocks;
   }
   if (compile_s) *compile_s = pr->jit ? pr->jit->compile_s : 0.0;
   return SG_OK;

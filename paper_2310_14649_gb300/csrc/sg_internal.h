@@ -99,6 +99,7 @@ constexpr int64_t kJitMaxT = 40000;
 struct JitConfig {
   int rows = 1;        // rows per thread (2: paired FP32 FMA)
   int groups = 1;      // output groups (warp groups of 4 warps)
+  int igroups = 1;     // input groups (partial sums meet in shared memory)
   int prefetch = 8;    // input terms loaded ahead
   int min_blocks = 1;  // CTAs per SM requested from the register allocator
 };
@@ -149,6 +150,7 @@ sg_status apply_ell(const Ell& A, const TripleTables& tri, int P, int K, const T
                     const T* F, int64_t ldf, T* Y, int64_t ldy, cudaStream_t st);
 std::string jit_apply_source(const sg_problem* pr, const JitConfig& c);
 JitConfig jit_default_config(const sg_problem* pr);
+size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c);
 sg_status jit_autotune(sg_problem* pr, int force, double* best_ms);
 sg_status jit_apply_build(sg_problem* pr);
 void jit_free(sg_problem* pr);

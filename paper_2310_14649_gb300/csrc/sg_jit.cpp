@@ -16,6 +16,9 @@
 //   H  output groups: the P outputs are split into H contiguous ranges of
 //      about T/H triples each, one range per group of 4 warps, so the
 //      registers per thread stay bounded for large P;
+//   HI input groups: the gathered x[b] are split into HI ranges as well;
+//      each (output, input) group accumulates partial sums that meet in
+//      shared memory, in a fixed order, before the single write of Y;
 //   pf input terms whose values are loaded ahead of use;
 //   mb CTAs per SM requested from the register allocator.
 // Kernels are compiled for sm_103a with NVRTC and cached on disk by a hash
@@ -95,65 +98,77 @@ std::vector<int> output_split(const sg_problem* pr, int H) {
 }  // namespace
 
 std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
-  const int P = pr->P, K = pr->K, R = c.rows, H = c.groups, pf = c.prefetch;
-  const int mb = c.min_blocks;
-  const std::vector<int> cut = output_split(pr, H);
+  const int P = pr->P, K = pr->K, R = c.rows, HO = c.groups, HI = c.igroups, pf = c.prefetch;
+  const int mb = c.min_blocks, NG = HO * HI;
+  const std::vector<int> cut = output_split(pr, HO);
+  std::vector<int> icut(HI + 1);
+  for (int i = 0; i <= HI; ++i) icut[i] = int(int64_t(P) * i / HI);
   // triples grouped by k, then by a
   std::vector<std::map<int, std::vector<std::pair<int, float>>>> by_k(K);
   for (int64_t t = 0; t < pr->T; ++t) {
     int k = pr->kab[3 * t], a = pr->kab[3 * t + 1], b = pr->kab[3 * t + 2];
     by_k[k][a].push_back({b, float(pr->g[t])});
   }
+  // paired rows take their coefficients from the constant bank (the paired
+  // FMA has no immediate operand)
+  std::map<uint32_t, int> gslot;
+  std::vector<float> gvals;
+  auto gref = [&](float g) -> std::string {
+    if (R == 1) return "G(" + hexf(g) + ")";
+    uint32_t u;
+    std::memcpy(&u, &g, 4);
+    auto it = gslot.find(u);
+    int id;
+    if (it == gslot.end()) {
+      id = int(gvals.size());
+      gslot[u] = id;
+      gvals.push_back(g);
+    } else {
+      id = it->second;
+    }
+    return "gq2[" + std::to_string(id) + "]";
+  };
   const char* ty = R == 2 ? "float2" : "float";
-  std::ostringstream os;
-  os << "// generated: Galerkin apply, P=" << P << " K=" << K << " T=" << pr->T << " R=" << R << " H=" << H
-     << " pf=" << pf << " mb=" << mb << "\n";
-  os << "#define G(h) __int_as_float(h)\n#define GG(h) make_float2(__int_as_float(h), __int_as_float(h))\n";
-  os << "extern \"C\" __global__ void __launch_bounds__(" << 128 * H << ", " << mb << ") sg_k1(\n"
-        "    const float* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
-        "    const float* __restrict__ X, long long ldx, const float* __restrict__ F, long long ldf,\n"
-        "    float* __restrict__ Y, long long ldy) {\n"
-        "  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
-        "  const int grp = warp >> 2;\n"
-        "  const int r = blockIdx.x * "
-     << 128 * R << " + (warp & 3) * " << 32 * R << " + lane * " << R << ";\n"
-     << "  if (r >= n) return;\n"
-        "  const long long kst = (long long)S * ldr;\n";
-  for (int h = 0; h < H; ++h) {
-    const int lo = cut[h], hi = cut[h + 1];
+  std::ostringstream body;
+  for (int g = 0; g < NG; ++g) {
+    const int ho = g / HI, hi = g % HI;
+    const int lo = cut[ho], up = cut[ho + 1], blo = icut[hi], bup = icut[hi + 1];
+    auto in_grp = [&](int a, int b) { return a >= lo && a < up && b >= blo && b < bup; };
     std::vector<int> ks;
+    std::vector<char> need_b(P, 0), has_a(P, 0);
     for (int k = 0; k < K; ++k) {
       bool any = false;
-      for (const auto& ga : by_k[k]) any |= ga.first >= lo && ga.first < hi;
+      for (const auto& ga : by_k[k])
+        for (const auto& e : ga.second)
+          if (in_grp(ga.first, e.first)) {
+            any = true;
+            need_b[e.first] = 1;
+            has_a[ga.first] = 1;
+          }
       if (any) ks.push_back(k);
     }
-    std::vector<char> need_b(P, 0);
-    for (int k : ks)
-      for (const auto& ga : by_k[k])
-        if (ga.first >= lo && ga.first < hi)
-          for (const auto& e : ga.second) need_b[e.first] = 1;
-    os << "  " << (h ? "else " : "") << "if (grp == " << h << ") {\n";
-    for (int a = lo; a < hi; ++a)
-      os << "    " << ty << " y" << a << (R == 2 ? " = make_float2(0.f, 0.f);\n" : " = 0.f;\n");
-    os << "#pragma unroll 1\n"
-          "    for (int s = 0; s < S; ++s) {\n"
-          "      const float* xp0 = X + col[(long long)s * ldr + r];\n";
-    if (R == 2) os << "      const float* xp1 = X + col[(long long)s * ldr + r + 1];\n";
+    body << "  " << (g ? "else " : "") << "if (grp == " << g << ") {\n";
+    for (int a = lo; a < up; ++a)
+      if (has_a[a]) body << "    " << ty << " y" << a << (R == 2 ? " = make_float2(0.f, 0.f);\n" : " = 0.f;\n");
+    body << "#pragma unroll 1\n"
+            "    for (int s = 0; s < S; ++s) {\n"
+            "      const float* xp0 = X + col[(long long)s * ldr + rr];\n";
+    if (R == 2) body << "      const float* xp1 = X + col[(long long)s * ldr + rr + 1];\n";
     for (int b = 0; b < P; ++b) {
       if (!need_b[b]) continue;
       if (R == 2)
-        os << "      const float2 x" << b << " = make_float2(__ldg(xp0 + (long long)" << b << " * ldx), __ldg(xp1 + (long long)"
-           << b << " * ldx));\n";
+        body << "      const float2 x" << b << " = make_float2(__ldg(xp0 + (long long)" << b
+             << " * ldx), __ldg(xp1 + (long long)" << b << " * ldx));\n";
       else
-        os << "      const float x" << b << " = __ldg(xp0 + (long long)" << b << " * ldx);\n";
+        body << "      const float x" << b << " = __ldg(xp0 + (long long)" << b << " * ldx);\n";
     }
-    os << "      const float* vp = V + (long long)s * ldr + r;\n";
+    body << "      const float* vp = V + (long long)s * ldr + rr;\n";
     auto load = [&](int k) {
       if (R == 2)
-        os << "      const float2 v" << k << " = __ldg(reinterpret_cast<const float2*>(vp + (long long)" << k
-           << " * kst));\n";
+        body << "      const float2 v" << k << " = __ldg(reinterpret_cast<const float2*>(vp + (long long)" << k
+             << " * kst));\n";
       else
-        os << "      const float v" << k << " = __ldg(vp + (long long)" << k << " * kst);\n";
+        body << "      const float v" << k << " = __ldg(vp + (long long)" << k << " * kst);\n";
     };
     const int nk = int(ks.size());
     for (int i = 0; i < std::min(nk, pf); ++i) load(ks[i]);
@@ -162,53 +177,110 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
       const int k = ks[i];
       for (const auto& ga : by_k[k]) {
         const int a = ga.first;
-        if (a < lo || a >= hi) continue;
-        const auto& lst = ga.second;
-        if (R == 1) {
-          if (lst.size() == 1 && lst[0].second == 1.0f) {
-            os << "      y" << a << " = fmaf(v" << k << ", x" << lst[0].first << ", y" << a << ");\n";
-            continue;
-          }
-          os << "      { float t = x" << lst[0].first << " * G(" << hexf(lst[0].second) << ");";
-          for (size_t e = 1; e < lst.size(); ++e)
-            os << " t = fmaf(x" << lst[e].first << ", G(" << hexf(lst[e].second) << "), t);";
-          os << " y" << a << " = fmaf(v" << k << ", t, y" << a << "); }\n";
-        } else {
-          if (lst.size() == 1 && lst[0].second == 1.0f) {
-            os << "      y" << a << " = __ffma2_rn(v" << k << ", x" << lst[0].first << ", y" << a << ");\n";
-            continue;
-          }
-          os << "      { float2 t = __fmul2_rn(x" << lst[0].first << ", GG(" << hexf(lst[0].second) << "));";
-          for (size_t e = 1; e < lst.size(); ++e)
-            os << " t = __ffma2_rn(x" << lst[e].first << ", GG(" << hexf(lst[e].second) << "), t);";
-          os << " y" << a << " = __ffma2_rn(v" << k << ", t, y" << a << "); }\n";
+        std::vector<std::pair<int, float>> lst;
+        for (const auto& e : ga.second)
+          if (in_grp(a, e.first)) lst.push_back(e);
+        if (lst.empty()) continue;
+        const char* fma = R == 2 ? "__ffma2_rn" : "fmaf";
+        if (lst.size() == 1 && lst[0].second == 1.0f) {
+          body << "      y" << a << " = " << fma << "(v" << k << ", x" << lst[0].first << ", y" << a << ");\n";
+          continue;
         }
+        if (R == 2)
+          body << "      { float2 t = __fmul2_rn(x" << lst[0].first << ", " << gref(lst[0].second) << ");";
+        else
+          body << "      { float t = x" << lst[0].first << " * " << gref(lst[0].second) << ";";
+        for (size_t e = 1; e < lst.size(); ++e)
+          body << " t = " << fma << "(x" << lst[e].first << ", " << gref(lst[e].second) << ", t);";
+        body << " y" << a << " = " << fma << "(v" << k << ", t, y" << a << "); }\n";
       }
     }
-    os << "    }\n";
-    for (int a = lo; a < hi; ++a) {
-      if (R == 2) {
-        os << "    Y[(long long)" << a << " * ldy + r] = F ? F[(long long)" << a << " * ldf + r] - y" << a
-           << ".x : y" << a << ".x;\n";
-        os << "    if (r + 1 < n) Y[(long long)" << a << " * ldy + r + 1] = F ? F[(long long)" << a
-           << " * ldf + r + 1] - y" << a << ".y : y" << a << ".y;\n";
-      } else {
-        os << "    Y[(long long)" << a << " * ldy + r] = F ? F[(long long)" << a << " * ldf + r] - y" << a << " : y"
-           << a << ";\n";
+    body << "    }\n";
+    // partial sums of the input groups meet in shared memory, in group order
+    for (int a = lo; a < up; ++a) {
+      if (!has_a[a]) continue;
+      for (int q = 0; q < R; ++q) {
+        const std::string val = R == 2 ? ("y" + std::to_string(a) + (q ? ".y" : ".x")) : ("y" + std::to_string(a));
+        body << "    part[" << a << " * " << 128 * R << " + lrow + " << q << "] = " << val << ";\n";
       }
     }
-    os << "  }\n";
+    body << "  }\n";
+  }
+  std::ostringstream os;
+  os << "// generated: Galerkin apply, P=" << P << " K=" << K << " T=" << pr->T << " R=" << R << " groups=" << HO
+     << "x" << HI << " pf=" << pf << " mb=" << mb << "\n";
+  os << "#define G(h) __int_as_float(h)\n";
+  if (R == 2 && !gvals.empty()) {
+    // both halves of each pair carry the same coefficient bits
+    os << "__constant__ unsigned long long gq_bits[" << gvals.size() << "] = {";
+    for (size_t i = 0; i < gvals.size(); ++i) {
+      const std::string h = hexf(gvals[i]).substr(2);
+      os << (i ? ", " : "") << "0x" << h << h << "ull";
+    }
+    os << "};\n#define gq2 (reinterpret_cast<const float2*>(gq_bits))\n";
+  }
+  const int rows_cta = 128 * R;
+  os << "extern \"C\" __global__ void __launch_bounds__(" << 128 * NG << ", " << mb << ") sg_k1(\n"
+        "    const float* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
+        "    const float* __restrict__ X, long long ldx, const float* __restrict__ F, long long ldf,\n"
+        "    float* __restrict__ Y, long long ldy) {\n"
+        "  extern __shared__ float smem[];\n"
+        "  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
+        "  const int grp = warp >> 2;\n"
+        "  const int lrow = (warp & 3) * "
+     << 32 * R << " + lane * " << R << ";\n"
+     << "  const int r = blockIdx.x * " << rows_cta << " + lrow;\n"
+     << "  const int rr = r < n ? r : (n - 1) & ~" << (R - 1) << ";\n"
+     << "  const long long kst = (long long)S * ldr;\n";
+  if (NG == 1) {
+    os << "  float* part = smem;\n  (void)part;\n";
+    // single group: write straight from registers
+    std::string b = body.str();
+    // drop the shared-memory hand-off of the single group
+    std::ostringstream direct;
+    std::istringstream in(b);
+    std::string line;
+    while (std::getline(in, line)) {
+      if (line.find("part[") != std::string::npos) continue;
+      direct << line << "\n";
+      if (line == "    }") {  // end of the slot loop: write the outputs
+        for (int a = 0; a < P; ++a)
+          for (int q = 0; q < R; ++q) {
+            const std::string val = R == 2 ? ("y" + std::to_string(a) + (q ? ".y" : ".x")) : ("y" + std::to_string(a));
+            direct << "    if (r + " << q << " < n) Y[(long long)" << a << " * ldy + r + " << q << "] = F ? F[(long long)"
+                   << a << " * ldf + r + " << q << "] - " << val << " : " << val << ";\n";
+          }
+      }
+    }
+    os << direct.str();
+  } else {
+    os << "  float* part = smem + (size_t)(grp % " << HI << ") * " << P * rows_cta << ";\n";
+    os << body.str();
+    os << "  __syncthreads();\n";
+    os << "  for (int e = threadIdx.x; e < " << P * rows_cta << "; e += " << 128 * NG << ") {\n"
+          "    const int a = e / "
+       << rows_cta << ", lr = e - a * " << rows_cta << ";\n"
+       << "    const int row = blockIdx.x * " << rows_cta << " + lr;\n"
+       << "    if (row >= n) continue;\n"
+          "    float acc = smem[e];\n";
+    for (int hi = 1; hi < HI; ++hi) os << "    acc += smem[" << hi * P * rows_cta << " + e];\n";
+    os << "    Y[(long long)a * ldy + row] = F ? F[(long long)a * ldf + row] - acc : acc;\n  }\n";
   }
   os << "}\n";
   return os.str();
 }
 
+size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c) {
+  if (c.groups * c.igroups == 1) return 0;
+  return size_t(c.igroups) * pr->P * 128 * c.rows * sizeof(float);
+}
+
 // Compile (or load from the cache) one configuration.
 static sg_status jit_compile(const std::string& src, cudaLibrary_t* lib, cudaKernel_t* kern, bool* cached,
-                             double* seconds) {
+                             double* seconds, int dev) {
   auto t0 = std::chrono::steady_clock::now();
   char key[32];
-  std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(src + "|sm_103a|v3"));
+  std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(src + "|sm_103a|v4"));
   const std::string dir = cache_dir();
   const std::string path = dir + "/k1_" + key + ".cubin";
   std::vector<char> cubin;
@@ -250,21 +322,17 @@ static sg_status jit_compile(const std::string& src, cudaLibrary_t* lib, cudaKer
   }
   SG_CUDA(cudaLibraryLoadData(lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
   SG_CUDA(cudaLibraryGetKernel(kern, *lib, "sg_k1"));
+  SG_CUDA(cudaKernelSetAttributeForDevice(*kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024, dev));
   if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return SG_OK;
 }
 
 JitConfig jit_default_config(const sg_problem* pr) {
   JitConfig c;
-  if (pr->P <= 48) {
-    c.rows = 2;
-    c.groups = 1;
-    c.prefetch = 16;
-  } else {
-    c.rows = 1;
-    c.groups = pr->P <= 96 ? 2 : 3;
-    c.prefetch = 8;
-  }
+  c.rows = 1;
+  c.prefetch = pr->P <= 48 ? 32 : 8;
+  c.groups = pr->P <= 48 ? 1 : 2;
+  c.igroups = pr->P <= 48 ? 1 : 2;
   c.min_blocks = 1;
   return c;
 }
@@ -277,13 +345,18 @@ sg_status jit_apply_build(sg_problem* pr) {
     pr->jit_cfg = jit_default_config(pr);
     pr->jit_cfg_set = true;
   }
-  return jit_compile(jit_apply_source(pr, pr->jit_cfg), &J.lib, &J.kern, &J.from_cache, &J.compile_s);
+  return jit_compile(jit_apply_source(pr, pr->jit_cfg), &J.lib, &J.kern, &J.from_cache, &J.compile_s, pr->device);
 }
 
 sg_status jit_configure(sg_problem* pr, const JitConfig& c) {
-  if (c.rows < 1 || c.rows > 2 || c.groups < 1 || c.groups > 4 || c.prefetch < 0 || c.prefetch > 64 ||
-      c.min_blocks < 1 || c.min_blocks > 8) {
-    set_error("sg_apply_config: rows in {1,2}, groups in [1,4], prefetch in [0,64], min_blocks in [1,8]");
+  if (c.rows < 1 || c.rows > 2 || c.groups < 1 || c.groups > 4 || c.igroups < 1 || c.igroups > 4 ||
+      c.groups * c.igroups > 8 || c.prefetch < 0 || c.prefetch > 64 || c.min_blocks < 1 || c.min_blocks > 8) {
+    set_error("sg_apply_config: rows in {1,2}, groups and igroups in [1,4] with product <= 8, prefetch in [0,64], "
+              "min_blocks in [1,8]");
+    return SG_ERR_ARG;
+  }
+  if (jit_smem_bytes(pr, c) > 200 * 1024) {
+    set_error("sg_apply_config: the input-group hand-off does not fit in shared memory");
     return SG_ERR_ARG;
   }
   jit_free(pr);
@@ -302,8 +375,8 @@ void jit_free(sg_problem* pr) {
 
 bool jit_eligible(const sg_problem* pr) { return pr->P <= kJitMaxP && pr->T <= kJitMaxT; }
 
-static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, const Ell& A, const float* X, int64_t ldx,
-                               const float* F, int64_t ldf, float* Y, int64_t ldy, cudaStream_t st) {
+static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, size_t smem, const Ell& A, const float* X,
+                               int64_t ldx, const float* F, int64_t ldf, float* Y, int64_t ldy, cudaStream_t st) {
   if (A.n == 0) return SG_OK;
   const float* V = dp<float>(A.v32);
   const int* col = dp<int>(A.col);
@@ -311,8 +384,8 @@ static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, const Ell&
   int n = int(A.n), S = A.S;
   void* args[] = {(void*)&V, (void*)&col, &ldr, &n, &S, (void*)&X, &lx, (void*)&F, &lf, (void*)&Y, &ly};
   const int64_t rows_per_cta = 128LL * c.rows;
-  dim3 grid(unsigned((A.n + rows_per_cta - 1) / rows_per_cta)), block(unsigned(128 * c.groups));
-  SG_CUDA(cudaLaunchKernel((const void*)kern, grid, block, args, 0, st));
+  dim3 grid(unsigned((A.n + rows_per_cta - 1) / rows_per_cta)), block(unsigned(128 * c.groups * c.igroups));
+  SG_CUDA(cudaLaunchKernel((const void*)kern, grid, block, args, smem, st));
   note_launch();
   return SG_OK;
 }
@@ -320,7 +393,7 @@ static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, const Ell&
 sg_status jit_apply_launch(sg_problem* pr, const Ell& A, const float* X, int64_t ldx, const float* F, int64_t ldf,
                            float* Y, int64_t ldy, cudaStream_t st) {
   SG_TRY(jit_apply_build(pr));
-  return launch_kernel(pr->jit->kern, pr->jit_cfg, A, X, ldx, F, ldf, Y, ldy, st);
+  return launch_kernel(pr->jit->kern, pr->jit_cfg, jit_smem_bytes(pr, pr->jit_cfg), A, X, ldx, F, ldf, Y, ldy, st);
 }
 
 // --------------------------------------------------------------------------
@@ -333,18 +406,21 @@ static std::vector<JitConfig> candidates(const sg_problem* pr) {
   std::vector<JitConfig> out;
   for (int R : {1, 2})
     for (int H : {1, 2, 3})
-      for (int pf : {8, 16, 32}) {
-        const int per = (pr->P + H - 1) / H;
-        const int est = R * (per + pr->P + pf);  // live registers, roughly
-        if (est > 200) continue;
-        if (H > 1 && pr->P <= 24) continue;
-        JitConfig c;
-        c.rows = R;
-        c.groups = H;
-        c.prefetch = pf;
-        c.min_blocks = 1;
-        out.push_back(c);
-      }
+      for (int HI : {1, 2})
+        for (int pf : {8, 32}) {
+          const int per = (pr->P + H - 1) / H, iper = (pr->P + HI - 1) / HI;
+          const int est = R * (per + iper + pf);  // live registers, roughly
+          if (est > 160 || H * HI > 8) continue;
+          if (H * HI > 1 && pr->P <= 24) continue;
+          JitConfig c;
+          c.rows = R;
+          c.groups = H;
+          c.igroups = HI;
+          c.prefetch = pf;
+          c.min_blocks = 1;
+          if (jit_smem_bytes(pr, c) > 200 * 1024) continue;
+          out.push_back(c);
+        }
   if (out.empty()) out.push_back(jit_default_config(pr));
   return out;
 }
@@ -370,7 +446,7 @@ sg_status jit_autotune(sg_problem* pr, int force, double* best_ms) {
     std::ifstream in(path);
     JitConfig c;
     double ms = 0;
-    if (in >> c.rows >> c.groups >> c.prefetch >> c.min_blocks >> ms) {
+    if (in >> c.rows >> c.groups >> c.igroups >> c.prefetch >> c.min_blocks >> ms) {
       if (best_ms) *best_ms = ms;
       return jit_configure(pr, c);
     }
@@ -391,14 +467,15 @@ sg_status jit_autotune(sg_problem* pr, int force, double* best_ms) {
   for (const JitConfig& c : candidates(pr)) {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
-    if (jit_compile(jit_apply_source(pr, c), &lib, &kern, nullptr, nullptr) != SG_OK) continue;
+    if (jit_compile(jit_apply_source(pr, c), &lib, &kern, nullptr, nullptr, pr->device) != SG_OK) continue;
     std::vector<float> ts;
     for (int rep = 0; rep < 7 && status == SG_OK; ++rep) {
-      status = launch_kernel(kern, c, A, dp<float>(X), pr->ld, nullptr, 0, dp<float>(Y), pr->ld, st);
+      status = launch_kernel(kern, c, jit_smem_bytes(pr, c), A, dp<float>(X), pr->ld, nullptr, 0, dp<float>(Y),
+                             pr->ld, st);
       if (status != SG_OK) break;
       if (rep < 2) continue;
       cudaEventRecord(e0, st);
-      launch_kernel(kern, c, A, dp<float>(X), pr->ld, nullptr, 0, dp<float>(Y), pr->ld, st);
+      launch_kernel(kern, c, jit_smem_bytes(pr, c), A, dp<float>(X), pr->ld, nullptr, 0, dp<float>(Y), pr->ld, st);
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
       float ms = 0;
@@ -421,7 +498,9 @@ sg_status jit_autotune(sg_problem* pr, int force, double* best_ms) {
   if (best_ms) *best_ms = best_t;
   mkdirs(cache_dir());
   std::ofstream out(path);
-  if (out) out << best.rows << " " << best.groups << " " << best.prefetch << " " << best.min_blocks << " " << best_t << "\n";
+  if (out)
+    out << best.rows << " " << best.groups << " " << best.igroups << " " << best.prefetch << " " << best.min_blocks
+        << " " << best_t << "\n";
   return jit_configure(pr, best);
 }
 
