@@ -258,6 +258,18 @@ typedef struct {
 sg_status sg_solve(sg_problem* prob, const double* F_dev, int64_t ldf, double* X_dev, int64_t ldx,
                    const sg_solve_opts* opts, sg_solve_info* info, void* stream);
 
+/* Multi-vector dot products, the classical Gram-Schmidt step of the
+ * Arnoldi process inside FGMRES (Sec. 3):  out[i] = sum_e V_i[e] w[e] for
+ * i < nv, where V_i = V + i * stride.  dtype selects double or float
+ * vectors; products of float vectors are summed in FP32 over at most 8
+ * elements per thread, every other sum is FP64.  out is a device array of
+ * nv doubles.  nv in [1, 32]; stride >= len when nv > 1.  The reduction
+ * scratch (2 x 152 x 32 doubles and a counter) is allocated in the handle
+ * on first use; calls through one handle must not overlap on the GPU.
+ * Errors: SG_ERR_ARG, SG_ERR_NOMEM, SG_ERR_CUDA. */
+sg_status sg_mdot(sg_problem* prob, sg_dtype dtype, const void* V, int64_t stride, int nv, const void* w,
+                  int64_t len, double* out_dev, void* stream);
+
 /* Per-launch timing of the operator-apply kernels, for benchmarks.  While
  * enabled, every apply launched through this handle is bracketed by CUDA
  * events on its stream (a few microseconds of overhead per launch).

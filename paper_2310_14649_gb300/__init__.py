@@ -16,7 +16,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_residual", "sg_precond_setup", "sg_precond_info", "sg_get_partition",
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel",
-           "sg_apply_config", "sg_apply_autotune", "sg_apply_info",
+           "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "SgError", "SG_F32", "SG_F64", "PC_TWOLEVEL", "PC_SMOOTH", "PC_COARSE", "PC_AMG",
            "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL"]
 
@@ -246,3 +246,12 @@ def sg_apply_info(prob):
     call("sg_apply_info", prob.handle, _lib.ptr(cfg, ctypes.c_int32), ctypes.byref(cs))
     return {"rows": int(cfg[0]), "groups": int(cfg[1]), "igroups": int(cfg[2]), "prefetch": int(cfg[3]),
             "min_blocks": int(cfg[4]), "compile_s": cs.value}
+
+
+def sg_mdot(prob, V, w, out, stream=None):
+    """out[i] = V[i] . w for the rows of a [nv, len] CUDA tensor V (float32
+    or float64) and a vector w of the same dtype; out: float64 CUDA [nv]."""
+    if V.dtype != w.dtype or out.dtype.itemsize != 8 or V.stride(1) != 1:
+        raise TypeError("V, w of one dtype (row-contiguous V), out float64")
+    call("sg_mdot", prob.handle, _dtype_code(V), dev_ptr(V), V.stride(0), V.shape[0], dev_ptr(w), V.shape[1],
+         dev_ptr(out), stream_handle(stream))

@@ -3,7 +3,7 @@
 #include <cstring>
 #include <new>
 
-#include "sg_internal.h"
+#include "sg_kernels.h"
 
 namespace sg {
 namespace {
@@ -68,6 +68,8 @@ sg_status sg_destroy(sg_problem* pr) {
   if (!pr) return SG_OK;
   solver_free(pr);
   jit_free(pr);
+  pr->mdot_partial.free_();
+  pr->mdot_counter.free_();
   pr->fine.col.free_();
   pr->fine.v64.free_();
   pr->fine.v32.free_();
@@ -224,6 +226,24 @@ sg_status sg_residual(sg_problem* pr, sg_dtype dtype, const void* F, int64_t ldf
                             static_cast<double*>(R), ldr, st);
   return apply_op<float>(pr, false, static_cast<const float*>(X), ldx, static_cast<const float*>(F), ldf,
                          static_cast<float*>(R), ldr, st);
+}
+
+sg_status sg_mdot(sg_problem* pr, sg_dtype dtype, const void* V, int64_t stride, int nv, const void* w, int64_t len,
+                  double* out, void* stream) {
+  SG_ARG(pr && V && w && out, "sg_mdot: NULL argument");
+  SG_ARG(dtype == SG_F64 || dtype == SG_F32, "sg_mdot: bad dtype");
+  SG_ARG(nv >= 1 && nv <= kMdotMaxVectors, "sg_mdot: nv must be in [1, 32]");
+  SG_ARG(len >= 0 && (nv == 1 || stride >= len), "sg_mdot: len < 0 or stride < len");
+  if (!pr->mdot_partial.ptr) {
+    SG_TRY(pr->mdot_partial.alloc(size_t(kMdotBlocks) * kMdotMaxVectors * sizeof(double)));
+    SG_TRY(pr->mdot_counter.alloc(256));
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (dtype == SG_F64)
+    return vec_mdot<double>(static_cast<const double*>(V), stride, nv, static_cast<const double*>(w), len, out,
+                            dp<double>(pr->mdot_partial), dp<unsigned>(pr->mdot_counter), st);
+  return vec_mdot<float>(static_cast<const float*>(V), stride, nv, static_cast<const float*>(w), len, out,
+                         dp<double>(pr->mdot_partial), dp<unsigned>(pr->mdot_counter), st);
 }
 
 }  // extern "C"

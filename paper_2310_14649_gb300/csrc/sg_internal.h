@@ -134,6 +134,7 @@ struct sg_problem {
   sg::JitApply* jit = nullptr;         // specialised FP32 apply (lazy)
   sg::JitConfig jit_cfg;
   bool jit_cfg_set = false;
+  sg::DevBuf mdot_partial, mdot_counter;  // scratch of sg_mdot
   int apply_mode = 0;                  // 0 auto, 1 shared-memory kernel, 2 specialised
 };
 

@@ -26,6 +26,10 @@ sg_status amg_vcycle(const Precond& pc, AmgWork<T>& w, int P, cudaStream_t st);
 sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w);
 
 // ---- vector kernels (sg_krylov.cu) ----
+// grid of the fused multi-vector reductions and the vectors per pass; the
+// reduction scratch holds kMdotBlocks x kMdotMaxVectors doubles + a counter
+constexpr int kMdotBlocks = 2 * 152;
+constexpr int kMdotMaxVectors = 32;
 // Device-resident scalar state of one (F)GMRES cycle.
 struct GmresState {
   double* H;      // (m+1) x m, column-major; upper triangle R after rotations

@@ -13,8 +13,8 @@ namespace sg {
 namespace {
 
 constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 2 * 152;
-constexpr int kMaxV = 32;  // vectors per fused pass
+constexpr int kRedBlocks = kMdotBlocks;
+constexpr int kMaxV = kMdotMaxVectors;  // vectors per fused pass
 
 template <typename T> struct Acc;
 template <> struct Acc<double> { using type = double; };

@@ -192,3 +192,25 @@ def test_autotune_picks_a_valid_shape(gpu):
     info = sg.sg_apply_info(prob)
     assert ms > 0 and info["rows"] in (1, 2) and 1 <= info["groups"] <= 4
     check_apply(prob, ref, random_block(ref.n, ref.P, seed=14), torch.float32, kernel=2)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+@pytest.mark.parametrize("nv,length", [(1, 1), (7, 1000), (32, 300001)])
+def test_mdot(gpu, dt, nv, length):
+    """Multi-vector dot products against numpy FP64 sums."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(8, 1, 1, 2)
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    g = torch.Generator().manual_seed(nv * 7 + length)
+    V = torch.randn((nv, length + 5), generator=g, dtype=torch.float64).to(dtype).cuda()[:, :length]
+    w = torch.randn(length, generator=g, dtype=torch.float64).to(dtype).cuda()
+    out = torch.zeros(nv, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        sg.sg_mdot(prob, V, w, out)
+    torch.cuda.synchronize()
+    Vh, wh = V.double().cpu().numpy(), w.double().cpu().numpy()
+    refv = Vh @ wh
+    bound = np.abs(Vh) @ np.abs(wh)
+    u = U64 if dt == "f64" else U32
+    assert np.all(np.abs(out.cpu().numpy() - refv) <= gamma(8 if dt == "f32" else 1, u) * bound + 1e-12 * bound)
