@@ -270,6 +270,26 @@ sg_status sg_solve(sg_problem* prob, const double* F_dev, int64_t ldf, double* X
 sg_status sg_mdot(sg_problem* prob, sg_dtype dtype, const void* V, int64_t stride, int nv, const void* w,
                   int64_t len, double* out_dev, void* stream);
 
+/* sg_mdot without any allocation, for callers that cannot call cudaMalloc:
+ * code that shares the GPU with a framework whose caching allocator already
+ * holds the free device memory, latency-critical loops that cannot afford
+ * the device-wide synchronisation cudaMalloc may cause, and callers that
+ * have no sg_problem handle to own scratch.  (The paper has no counterpart:
+ * this is a property of the library, not of the method.)
+ * Same arguments and results as sg_mdot, without the handle.  The reduction
+ * scratch is a fixed static device array of 304 x 32 doubles plus a counter,
+ * present on every GPU that loads the library until the process exits; nv
+ * above 32 is rejected with SG_ERR_ARG.  Each call clears the counter on
+ * `stream` and allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).  All calls share the one array per device and it keeps
+ * the last call's contents, so calls whose kernels overlap on the GPU (other
+ * streams, other threads) race: serialise them.  The first call on a device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture.
+ * Errors: SG_ERR_ARG, SG_ERR_CUDA. */
+sg_status sg_mdot_noalloc(sg_dtype dtype, const void* V, int64_t stride, int nv, const void* w,
+                          int64_t len, double* out_dev, void* stream);
+
 /* Per-launch timing of the operator-apply kernels, for benchmarks.  While
  * enabled, every apply launched through this handle is bracketed by CUDA
  * events on its stream (a few microseconds of overhead per launch).

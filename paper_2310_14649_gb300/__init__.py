@@ -17,6 +17,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
+           "sg_mdot_noalloc",
            "SgError", "SG_F32", "SG_F64", "PC_TWOLEVEL", "PC_SMOOTH", "PC_COARSE", "PC_AMG",
            "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL"]
 
@@ -254,4 +255,13 @@ def sg_mdot(prob, V, w, out, stream=None):
     if V.dtype != w.dtype or out.dtype.itemsize != 8 or V.stride(1) != 1:
         raise TypeError("V, w of one dtype (row-contiguous V), out float64")
     call("sg_mdot", prob.handle, _dtype_code(V), dev_ptr(V), V.stride(0), V.shape[0], dev_ptr(w), V.shape[1],
+         dev_ptr(out), stream_handle(stream))
+
+
+def sg_mdot_noalloc(V, w, out, stream=None):
+    """sg_mdot without a handle and without any device allocation (static
+    scratch inside the library); calls that overlap on the GPU race."""
+    if V.dtype != w.dtype or out.dtype.itemsize != 8 or V.stride(1) != 1:
+        raise TypeError("V, w of one dtype (row-contiguous V), out float64")
+    call("sg_mdot_noalloc", _dtype_code(V), dev_ptr(V), V.stride(0), V.shape[0], dev_ptr(w), V.shape[1],
          dev_ptr(out), stream_handle(stream))

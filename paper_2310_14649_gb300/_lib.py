@@ -80,6 +80,7 @@ SIGNATURES = {
     "sg_solve": [vp, vp, i64, vp, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
     "sg_profile": [vp, ctypes.c_int],
     "sg_mdot": [vp, ctypes.c_int, vp, i64, ctypes.c_int, vp, i64, vp, vp],
+    "sg_mdot_noalloc": [ctypes.c_int, vp, i64, ctypes.c_int, vp, i64, vp, vp],
     "sg_set_apply_kernel": [vp, ctypes.c_int],
     "sg_apply_config": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sg_apply_autotune": [vp, ctypes.c_int, P_f64],

@@ -5,6 +5,7 @@
 // device.  Dot products accumulate in FP64 across threads; for FP32 vectors
 // each thread first sums its few products in FP32.
 #include <cmath>
+#include <mutex>
 
 #include "sg_kernels.h"
 
@@ -306,6 +307,52 @@ sg_status gmres_backsolve(GmresState s, int m, int k, cudaStream_t st) {
 INST(float)
 INST(double)
 #undef INST
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the multi-vector dot product.  The reduction
+// scratch of k_multi (one partial sum per block and vector, plus the
+// arrival counter of the last-block reduction) lives in file-scope device
+// arrays instead of caller- or handle-owned memory, so the entry point needs
+// neither a handle nor any allocation.  Every GPU that loads the library
+// holds these arrays (about 78 KB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __align__(256) double g_noalloc_partial[kMdotBlocks * kMdotMaxVectors];
+__device__ __align__(256) unsigned g_noalloc_counter[64];
+
+constexpr int kMaxDevices = 64;
+struct NoallocScratch {
+  double* partial = nullptr;
+  unsigned* counter = nullptr;
+};
+std::mutex g_noalloc_mu;
+NoallocScratch g_noalloc[kMaxDevices];
+
+// Device address of the arrays on the current device.  In host code the
+// array names are host-side stand-ins, not device addresses, so the first
+// call on each device asks the runtime for the addresses (with that device
+// current) and keeps them.
+sg_status noalloc_scratch(NoallocScratch& out) {
+  int dev = 0;
+  SG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("sg_mdot_noalloc: device index out of range");
+    return SG_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoallocScratch& s = g_noalloc[dev];
+  if (!s.partial) {
+    void* p = nullptr;
+    void* c = nullptr;
+    SG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_partial));
+    SG_CUDA(cudaGetSymbolAddress(&c, g_noalloc_counter));
+    s.partial = static_cast<double*>(p);
+    s.counter = static_cast<unsigned*>(c);
+  }
+  out = s;
+  return SG_OK;
+}
+}  // namespace
+
 template sg_status vec_convert<double, float>(const double*, float*, int64_t, const double*, const double*,
                                               cudaStream_t);
 template sg_status vec_convert<float, double>(const float*, double*, int64_t, const double*, const double*,
@@ -316,3 +363,24 @@ template sg_status vec_convert<float, float>(const float*, float*, int64_t, cons
                                              cudaStream_t);
 
 }  // namespace sg
+
+extern "C" sg_status sg_mdot_noalloc(sg_dtype dtype, const void* V, int64_t stride, int nv, const void* w,
+                                     int64_t len, double* out, void* stream) {
+  using namespace sg;
+  SG_ARG(V && w && out, "sg_mdot_noalloc: NULL argument");
+  SG_ARG(dtype == SG_F64 || dtype == SG_F32, "sg_mdot_noalloc: bad dtype");
+  SG_ARG(nv >= 1 && nv <= kMdotMaxVectors,
+         "sg_mdot_noalloc: nv must be in [1, 32] (the static scratch holds 304 x 32 partial sums)");
+  SG_ARG(len >= 0 && (nv == 1 || stride >= len), "sg_mdot_noalloc: len < 0 or stride < len");
+  NoallocScratch s;
+  SG_TRY(noalloc_scratch(s));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the arrival counter must start at zero; the partial sums are written
+  // before they are read
+  SG_CUDA(cudaMemsetAsync(s.counter, 0, sizeof(unsigned), st));
+  if (dtype == SG_F64)
+    return vec_mdot<double>(static_cast<const double*>(V), stride, nv, static_cast<const double*>(w), len, out,
+                            s.partial, s.counter, st);
+  return vec_mdot<float>(static_cast<const float*>(V), stride, nv, static_cast<const float*>(w), len, out,
+                         s.partial, s.counter, st);
+}
