@@ -213,9 +213,15 @@ def main():
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
+    tune_ms = sg.sg_apply_autotune(prob)       # cached after the first run
+    t_tune = time.perf_counter() - t0
+    t0 = time.perf_counter()
     sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"])
     torch.cuda.synchronize()
     t_pc = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sg.sg_apply_autotune(prob, which=1)        # coarse operator, cached too
+    t_tune += time.perf_counter() - t0
     n, P = prob.n, prob.P
     X = torch.zeros((P, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -306,6 +312,8 @@ def main():
         "solve": {"outer_it": infos[-1]["outer_it"], "inner_it": infos[-1]["inner_it"],
                   "ir_steps": infos[-1]["ir_steps"], "relres": infos[-1]["relres"],
                   "setup_s": round(t_setup, 3), "precond_setup_s": round(t_pc, 3),
+                  "apply_tuning_s": round(t_tune, 3), "apply_shape": sg.sg_apply_info(prob),
+                  "coarse_apply_shape": sg.sg_apply_info(prob, which=1),
                   "solves_per_s_all_gpus": round(world * 1e3 / ms_all, 3)},
         "plain_fp64": {"ms": round(ms64, 3), "outer_it": info64["outer_it"], "relres": info64["relres"],
                        "speedup_mixed": round(ms64 / ms_all, 3)},

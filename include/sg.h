@@ -136,28 +136,31 @@ sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t 
  * Errors: SG_ERR_CUDA with the compiler log when compilation fails. */
 sg_status sg_set_apply_kernel(sg_problem* prob, int mode);
 
-/* Tile shape of the register-specialised kernel: rows per thread (1, or 2
- * adjacent rows updated with the paired FP32 FMA), output groups and input
- * groups (1..4 each, product <= 8: the outputs and the gathered inputs are
- * split across groups of 4 warps whose partial sums meet in shared
- * memory), prefetch (input terms whose values are loaded ahead, 0..64) and
- * min_blocks (CTAs per SM asked of the register allocator, 1..8).
- * Recompiles the kernel.
+/* Tile shape of the register-specialised kernel of the fine (which = 0)
+ * or coarse (which = 1) operator family: rows per thread (1, or 2 adjacent
+ * rows updated with the paired FP32 FMA); output groups, input groups
+ * (1..4 each) and stencil-slot groups (1..8), product <= 8: the outputs,
+ * the gathered inputs and the slots are split across groups of 4 warps
+ * whose partial sums meet in shared memory; prefetch (input terms whose
+ * values are loaded ahead, 0..64); min_blocks (CTAs per SM asked of the
+ * register allocator, 1..8).  Recompiles the kernel.
  * Errors: SG_ERR_ARG out of range, SG_ERR_CUDA compile failure. */
-sg_status sg_apply_config(sg_problem* prob, int rows, int groups, int igroups, int prefetch,
-                          int min_blocks);
+sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int igroups, int sgroups,
+                          int prefetch, int min_blocks);
 
 /* Autotuner: compiles the candidate tile shapes, times each on this
- * problem's fine operator with CUDA events, keeps the fastest and stores
+ * problem's fine (which = 0) or coarse (which = 1, after
+ * sg_precond_setup) operator with CUDA events, keeps the fastest and stores
  * the choice in the kernel cache directory (keyed by the triple structure,
- * n and the device name) so later setups reuse it unless force != 0.
- * best_ms (may be NULL) receives the time of the chosen shape.
+ * rows, slots and the device name) so later setups reuse it unless
+ * force != 0.  best_ms (may be NULL) receives the time of the chosen shape.
  * Synchronous; allocates two temporary blocks. */
-sg_status sg_apply_autotune(sg_problem* prob, int force, double* best_ms);
+sg_status sg_apply_autotune(sg_problem* prob, int which, int force, double* best_ms);
 
-/* Current tile shape (rows, groups, igroups, prefetch, min_blocks into
- * cfg5) and the seconds spent compiling or loading the kernel. */
-sg_status sg_apply_info(const sg_problem* prob, int* cfg5, double* compile_s);
+/* Current tile shape of one family (rows, groups, igroups, sgroups,
+ * prefetch, min_blocks into cfg6) and the seconds spent compiling or
+ * loading its kernel. */
+sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg6, double* compile_s);
 
 /* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
  * sg_apply (F may equal R for an in-place update). */

@@ -231,22 +231,24 @@ def sg_set_apply_kernel(prob, mode):
     call("sg_set_apply_kernel", prob.handle, mode)
 
 
-def sg_apply_config(prob, rows=1, groups=1, igroups=1, prefetch=8, min_blocks=1):
-    call("sg_apply_config", prob.handle, rows, groups, igroups, prefetch, min_blocks)
+def sg_apply_config(prob, rows=1, groups=1, igroups=1, sgroups=1, prefetch=8, min_blocks=1, which=0):
+    call("sg_apply_config", prob.handle, which, rows, groups, igroups, sgroups, prefetch, min_blocks)
 
 
-def sg_apply_autotune(prob, force=False):
+def sg_apply_autotune(prob, force=False, which=0):
     ms = ctypes.c_double()
-    call("sg_apply_autotune", prob.handle, 1 if force else 0, ctypes.byref(ms))
+    call("sg_apply_autotune", prob.handle, which, 1 if force else 0, ctypes.byref(ms))
     return ms.value
 
 
-def sg_apply_info(prob):
-    cfg = np.zeros(5, dtype=np.int32)
+def sg_apply_info(prob, which=0):
+    cfg = np.zeros(6, dtype=np.int32)
     cs = ctypes.c_double()
-    call("sg_apply_info", prob.handle, _lib.ptr(cfg, ctypes.c_int32), ctypes.byref(cs))
-    return {"rows": int(cfg[0]), "groups": int(cfg[1]), "igroups": int(cfg[2]), "prefetch": int(cfg[3]),
-            "min_blocks": int(cfg[4]), "compile_s": cs.value}
+    call("sg_apply_info", prob.handle, which, _lib.ptr(cfg, ctypes.c_int32), ctypes.byref(cs))
+    keys = ["rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks"]
+    out = {k: int(v) for k, v in zip(keys, cfg)}
+    out["compile_s"] = cs.value
+    return out
 
 
 def sg_mdot(prob, V, w, out, stream=None):

@@ -67,7 +67,8 @@ sg_status sg_setup(const sg_mesh_desc* mesh, const sg_kl_desc* kl, int p_out, in
 sg_status sg_destroy(sg_problem* pr) {
   if (!pr) return SG_OK;
   solver_free(pr);
-  jit_free(pr);
+  jit_free(pr, 0);
+  jit_free(pr, 1);
   pr->mdot_partial.free_();
   pr->mdot_counter.free_();
   pr->fine.col.free_();
@@ -89,37 +90,40 @@ sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
     return SG_ERR_UNSUPPORTED;
   }
   pr->apply_mode = mode;
-  if (mode != 1 && jit_eligible(pr)) return jit_apply_build(pr);
+  if (mode != 1 && jit_eligible(pr)) return jit_apply_build(pr, 0);
   return SG_OK;
 }
 
-sg_status sg_apply_config(sg_problem* pr, int rows, int groups, int igroups, int prefetch, int min_blocks) {
-  SG_ARG(pr, "sg_apply_config: NULL handle");
+sg_status sg_apply_config(sg_problem* pr, int which, int rows, int groups, int igroups, int sgroups, int prefetch,
+                          int min_blocks) {
+  SG_ARG(pr && (which == 0 || which == 1), "sg_apply_config: NULL handle or which not in {0, 1}");
   JitConfig c;
   c.rows = rows;
   c.groups = groups;
   c.igroups = igroups;
+  c.sgroups = sgroups;
   c.prefetch = prefetch;
   c.min_blocks = min_blocks;
-  return jit_configure(pr, c);
+  return jit_configure(pr, which, c);
 }
 
-sg_status sg_apply_autotune(sg_problem* pr, int force, double* best_ms) {
-  SG_ARG(pr, "sg_apply_autotune: NULL handle");
-  return jit_autotune(pr, force, best_ms);
+sg_status sg_apply_autotune(sg_problem* pr, int which, int force, double* best_ms) {
+  SG_ARG(pr && (which == 0 || which == 1), "sg_apply_autotune: NULL handle or which not in {0, 1}");
+  return jit_autotune(pr, which, force, best_ms);
 }
 
-sg_status sg_apply_info(const sg_problem* pr, int* cfg5, double* compile_s) {
-  SG_ARG(pr, "sg_apply_info: NULL handle");
-  const JitConfig c = pr->jit_cfg_set ? pr->jit_cfg : jit_default_config(pr);
-  if (cfg5) {
-    cfg5[0] = c.rows;
-    cfg5[1] = c.groups;
-    cfg5[2] = c.igroups;
-    cfg5[3] = c.prefetch;
-    cfg5[4] = c.min_blocks;
+sg_status sg_apply_info(const sg_problem* pr, int which, int* cfg6, double* compile_s) {
+  SG_ARG(pr && (which == 0 || which == 1), "sg_apply_info: NULL handle or which not in {0, 1}");
+  const JitConfig c = pr->jit_cfg_set[which] ? pr->jit_cfg[which] : jit_default_config(pr, which);
+  if (cfg6) {
+    cfg6[0] = c.rows;
+    cfg6[1] = c.groups;
+    cfg6[2] = c.igroups;
+    cfg6[3] = c.sgroups;
+    cfg6[4] = c.prefetch;
+    cfg6[5] = c.min_blocks;
   }
-  if (compile_s) *compile_s = pr->jit ? pr->jit->compile_s : 0.0;
+  if (compile_s) *compile_s = pr->jit[which] ? pr->jit[which]->compile_s : 0.0;
   return SG_OK;
 }
 

@@ -100,6 +100,7 @@ struct JitConfig {
   int rows = 1;        // rows per thread (2: paired FP32 FMA)
   int groups = 1;      // output groups (warp groups of 4 warps)
   int igroups = 1;     // input groups (partial sums meet in shared memory)
+  int sgroups = 1;     // stencil-slot groups (partial sums meet in shared memory)
   int prefetch = 8;    // input terms loaded ahead
   int min_blocks = 1;  // CTAs per SM requested from the register allocator
 };
@@ -131,9 +132,9 @@ struct sg_problem {
   int64_t ld = 0;                      // internal leading dimension of blocks
   sg::SolverState* solver = nullptr;   // preconditioner + solver workspaces
   sg::Profiler prof;
-  sg::JitApply* jit = nullptr;         // specialised FP32 apply (lazy)
-  sg::JitConfig jit_cfg;
-  bool jit_cfg_set = false;
+  sg::JitApply* jit[2] = {nullptr, nullptr};  // specialised FP32 apply: [0] fine, [1] coarse
+  sg::JitConfig jit_cfg[2];
+  bool jit_cfg_set[2] = {false, false};
   sg::DevBuf mdot_partial, mdot_counter;  // scratch of sg_mdot
   int apply_mode = 0;                  // 0 auto, 1 shared-memory kernel, 2 specialised
 };
@@ -150,15 +151,15 @@ template <typename T>
 sg_status apply_ell(const Ell& A, const TripleTables& tri, int P, int K, const T* X, int64_t ldx,
                     const T* F, int64_t ldf, T* Y, int64_t ldy, cudaStream_t st);
 std::string jit_apply_source(const sg_problem* pr, const JitConfig& c);
-JitConfig jit_default_config(const sg_problem* pr);
+JitConfig jit_default_config(const sg_problem* pr, int which);
 size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c);
-sg_status jit_autotune(sg_problem* pr, int force, double* best_ms);
-sg_status jit_apply_build(sg_problem* pr);
-void jit_free(sg_problem* pr);
-sg_status jit_configure(sg_problem* pr, const JitConfig& c);
+sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms);
+sg_status jit_apply_build(sg_problem* pr, int which);
+void jit_free(sg_problem* pr, int which);
+sg_status jit_configure(sg_problem* pr, int which, const JitConfig& c);
 bool jit_eligible(const sg_problem* pr);
-sg_status jit_apply_launch(sg_problem* pr, const Ell& A, const float* X, int64_t ldx, const float* F, int64_t ldf,
-                           float* Y, int64_t ldy, cudaStream_t st);
+sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const float* X, int64_t ldx, const float* F,
+                           int64_t ldf, float* Y, int64_t ldy, cudaStream_t st);
 // apply_ell on the fine (coarse = false) or coarse family of a problem,
 // timed when the problem's profiler is on
 template <typename T>

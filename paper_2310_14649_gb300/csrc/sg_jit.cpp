@@ -19,6 +19,8 @@
 //   HI input groups: the gathered x[b] are split into HI ranges as well;
 //      each (output, input) group accumulates partial sums that meet in
 //      shared memory, in a fixed order, before the single write of Y;
+//   SG slot groups: the stencil slots are dealt round-robin to SG groups
+//      (more threads for small row counts such as the coarse operator);
 //   pf input terms whose values are loaded ahead of use;
 //   mb CTAs per SM requested from the register allocator.
 // Kernels are compiled for sm_103a with NVRTC and cached on disk by a hash
@@ -98,8 +100,8 @@ std::vector<int> output_split(const sg_problem* pr, int H) {
 }  // namespace
 
 std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
-  const int P = pr->P, K = pr->K, R = c.rows, HO = c.groups, HI = c.igroups, pf = c.prefetch;
-  const int mb = c.min_blocks, NG = HO * HI;
+  const int P = pr->P, K = pr->K, R = c.rows, HO = c.groups, HI = c.igroups, SG = c.sgroups, pf = c.prefetch;
+  const int mb = c.min_blocks, NG = HO * HI * SG, NPART = HI * SG;
   const std::vector<int> cut = output_split(pr, HO);
   std::vector<int> icut(HI + 1);
   for (int i = 0; i <= HI; ++i) icut[i] = int(int64_t(P) * i / HI);
@@ -131,7 +133,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
   const char* ty = R == 2 ? "float2" : "float";
   std::ostringstream body;
   for (int g = 0; g < NG; ++g) {
-    const int ho = g / HI, hi = g % HI;
+    const int ho = g / (HI * SG), hi = (g / SG) % HI, sgi = g % SG;
     const int lo = cut[ho], up = cut[ho + 1], blo = icut[hi], bup = icut[hi + 1];
     auto in_grp = [&](int a, int b) { return a >= lo && a < up && b >= blo && b < bup; };
     std::vector<int> ks;
@@ -151,7 +153,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
     for (int a = lo; a < up; ++a)
       if (has_a[a]) body << "    " << ty << " y" << a << (R == 2 ? " = make_float2(0.f, 0.f);\n" : " = 0.f;\n");
     body << "#pragma unroll 1\n"
-            "    for (int s = 0; s < S; ++s) {\n"
+            "    for (int s = " << sgi << "; s < S; s += " << SG << ") {\n"
             "      const float* xp0 = X + col[(long long)s * ldr + rr];\n";
     if (R == 2) body << "      const float* xp1 = X + col[(long long)s * ldr + rr + 1];\n";
     for (int b = 0; b < P; ++b) {
@@ -196,9 +198,13 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
       }
     }
     body << "    }\n";
-    // partial sums of the input groups meet in shared memory, in group order
+    // partial sums of the input and slot groups meet in shared memory, in
+    // group order; outputs this group never touches contribute zero
     for (int a = lo; a < up; ++a) {
-      if (!has_a[a]) continue;
+      if (!has_a[a]) {
+        for (int q = 0; q < R; ++q) body << "    part[" << a << " * " << 128 * R << " + lrow + " << q << "] = 0.f;\n";
+        continue;
+      }
       for (int q = 0; q < R; ++q) {
         const std::string val = R == 2 ? ("y" + std::to_string(a) + (q ? ".y" : ".x")) : ("y" + std::to_string(a));
         body << "    part[" << a << " * " << 128 * R << " + lrow + " << q << "] = " << val << ";\n";
@@ -208,7 +214,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
   }
   std::ostringstream os;
   os << "// generated: Galerkin apply, P=" << P << " K=" << K << " T=" << pr->T << " R=" << R << " groups=" << HO
-     << "x" << HI << " pf=" << pf << " mb=" << mb << "\n";
+     << "x" << HI << "x" << SG << " pf=" << pf << " mb=" << mb << "\n";
   os << "#define G(h) __int_as_float(h)\n";
   if (R == 2 && !gvals.empty()) {
     // both halves of each pair carry the same coefficient bits
@@ -254,7 +260,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
     }
     os << direct.str();
   } else {
-    os << "  float* part = smem + (size_t)(grp % " << HI << ") * " << P * rows_cta << ";\n";
+    os << "  float* part = smem + (size_t)(grp % " << NPART << ") * " << P * rows_cta << ";\n";
     os << body.str();
     os << "  __syncthreads();\n";
     os << "  for (int e = threadIdx.x; e < " << P * rows_cta << "; e += " << 128 * NG << ") {\n"
@@ -263,7 +269,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
        << "    const int row = blockIdx.x * " << rows_cta << " + lr;\n"
        << "    if (row >= n) continue;\n"
           "    float acc = smem[e];\n";
-    for (int hi = 1; hi < HI; ++hi) os << "    acc += smem[" << hi * P * rows_cta << " + e];\n";
+    for (int q = 1; q < NPART; ++q) os << "    acc += smem[" << q * P * rows_cta << " + e];\n";
     os << "    Y[(long long)a * ldy + row] = F ? F[(long long)a * ldf + row] - acc : acc;\n  }\n";
   }
   os << "}\n";
@@ -271,8 +277,8 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
 }
 
 size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c) {
-  if (c.groups * c.igroups == 1) return 0;
-  return size_t(c.igroups) * pr->P * 128 * c.rows * sizeof(float);
+  if (c.groups * c.igroups * c.sgroups == 1) return 0;
+  return size_t(c.igroups) * c.sgroups * pr->P * 128 * c.rows * sizeof(float);
 }
 
 // Compile (or load from the cache) one configuration.
@@ -280,7 +286,7 @@ static sg_status jit_compile(const std::string& src, cudaLibrary_t* lib, cudaKer
                              double* seconds, int dev) {
   auto t0 = std::chrono::steady_clock::now();
   char key[32];
-  std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(src + "|sm_103a|v4"));
+  std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(src + "|sm_103a|v5"));
   const std::string dir = cache_dir();
   const std::string path = dir + "/k1_" + key + ".cubin";
   std::vector<char> cubin;
@@ -327,50 +333,55 @@ static sg_status jit_compile(const std::string& src, cudaLibrary_t* lib, cudaKer
   return SG_OK;
 }
 
-JitConfig jit_default_config(const sg_problem* pr) {
+JitConfig jit_default_config(const sg_problem* pr, int which) {
   JitConfig c;
   c.rows = 1;
   c.prefetch = pr->P <= 48 ? 32 : 8;
   c.groups = pr->P <= 48 ? 1 : 2;
   c.igroups = pr->P <= 48 ? 1 : 2;
+  // the coarse operator has a quarter of the rows: deal the slots to groups
+  // so that the grid still fills the GPU
+  c.sgroups = which == 1 ? (pr->P <= 48 ? 4 : 2) : 1;
   c.min_blocks = 1;
   return c;
 }
 
-sg_status jit_apply_build(sg_problem* pr) {
-  if (pr->jit && pr->jit->kern) return SG_OK;
-  if (!pr->jit) pr->jit = new JitApply();
-  JitApply& J = *pr->jit;
-  if (!pr->jit_cfg_set) {
-    pr->jit_cfg = jit_default_config(pr);
-    pr->jit_cfg_set = true;
+sg_status jit_apply_build(sg_problem* pr, int which) {
+  if (pr->jit[which] && pr->jit[which]->kern) return SG_OK;
+  if (!pr->jit[which]) pr->jit[which] = new JitApply();
+  JitApply& J = *pr->jit[which];
+  if (!pr->jit_cfg_set[which]) {
+    pr->jit_cfg[which] = jit_default_config(pr, which);
+    pr->jit_cfg_set[which] = true;
   }
-  return jit_compile(jit_apply_source(pr, pr->jit_cfg), &J.lib, &J.kern, &J.from_cache, &J.compile_s, pr->device);
+  return jit_compile(jit_apply_source(pr, pr->jit_cfg[which]), &J.lib, &J.kern, &J.from_cache, &J.compile_s,
+                     pr->device);
 }
 
-sg_status jit_configure(sg_problem* pr, const JitConfig& c) {
+sg_status jit_configure(sg_problem* pr, int which, const JitConfig& c) {
   if (c.rows < 1 || c.rows > 2 || c.groups < 1 || c.groups > 4 || c.igroups < 1 || c.igroups > 4 ||
-      c.groups * c.igroups > 8 || c.prefetch < 0 || c.prefetch > 64 || c.min_blocks < 1 || c.min_blocks > 8) {
-    set_error("sg_apply_config: rows in {1,2}, groups and igroups in [1,4] with product <= 8, prefetch in [0,64], "
-              "min_blocks in [1,8]");
+      c.sgroups < 1 || c.sgroups > 8 || c.groups * c.igroups * c.sgroups > 8 || c.prefetch < 0 ||
+      c.prefetch > 64 || c.min_blocks < 1 || c.min_blocks > 8) {
+    set_error("sg_apply_config: rows in {1,2}; groups, igroups in [1,4]; sgroups in [1,8]; "
+              "groups*igroups*sgroups <= 8; prefetch in [0,64]; min_blocks in [1,8]");
     return SG_ERR_ARG;
   }
   if (jit_smem_bytes(pr, c) > 200 * 1024) {
     set_error("sg_apply_config: the input-group hand-off does not fit in shared memory");
     return SG_ERR_ARG;
   }
-  jit_free(pr);
-  pr->jit_cfg = c;
-  pr->jit_cfg_set = true;
+  jit_free(pr, which);
+  pr->jit_cfg[which] = c;
+  pr->jit_cfg_set[which] = true;
   if (!jit_eligible(pr)) return SG_OK;
-  return jit_apply_build(pr);
+  return jit_apply_build(pr, which);
 }
 
-void jit_free(sg_problem* pr) {
-  if (!pr->jit) return;
-  if (pr->jit->lib) cudaLibraryUnload(pr->jit->lib);
-  delete pr->jit;
-  pr->jit = nullptr;
+void jit_free(sg_problem* pr, int which) {
+  if (!pr->jit[which]) return;
+  if (pr->jit[which]->lib) cudaLibraryUnload(pr->jit[which]->lib);
+  delete pr->jit[which];
+  pr->jit[which] = nullptr;
 }
 
 bool jit_eligible(const sg_problem* pr) { return pr->P <= kJitMaxP && pr->T <= kJitMaxT; }
@@ -384,16 +395,18 @@ static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, size_t sme
   int n = int(A.n), S = A.S;
   void* args[] = {(void*)&V, (void*)&col, &ldr, &n, &S, (void*)&X, &lx, (void*)&F, &lf, (void*)&Y, &ly};
   const int64_t rows_per_cta = 128LL * c.rows;
-  dim3 grid(unsigned((A.n + rows_per_cta - 1) / rows_per_cta)), block(unsigned(128 * c.groups * c.igroups));
+  dim3 grid(unsigned((A.n + rows_per_cta - 1) / rows_per_cta)),
+      block(unsigned(128 * c.groups * c.igroups * c.sgroups));
   SG_CUDA(cudaLaunchKernel((const void*)kern, grid, block, args, smem, st));
   note_launch();
   return SG_OK;
 }
 
-sg_status jit_apply_launch(sg_problem* pr, const Ell& A, const float* X, int64_t ldx, const float* F, int64_t ldf,
-                           float* Y, int64_t ldy, cudaStream_t st) {
-  SG_TRY(jit_apply_build(pr));
-  return launch_kernel(pr->jit->kern, pr->jit_cfg, jit_smem_bytes(pr, pr->jit_cfg), A, X, ldx, F, ldf, Y, ldy, st);
+sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const float* X, int64_t ldx, const float* F,
+                           int64_t ldf, float* Y, int64_t ldy, cudaStream_t st) {
+  SG_TRY(jit_apply_build(pr, which));
+  const JitConfig& c = pr->jit_cfg[which];
+  return launch_kernel(pr->jit[which]->kern, c, jit_smem_bytes(pr, c), A, X, ldx, F, ldf, Y, ldy, st);
 }
 
 // --------------------------------------------------------------------------
@@ -402,57 +415,64 @@ sg_status jit_apply_launch(sg_problem* pr, const Ell& A, const float* X, int64_t
 // keep the fastest and remember the choice in the cache directory, keyed by
 // the triple structure, n and the device name.
 // --------------------------------------------------------------------------
-static std::vector<JitConfig> candidates(const sg_problem* pr) {
+static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
   std::vector<JitConfig> out;
   for (int R : {1, 2})
     for (int H : {1, 2, 3})
       for (int HI : {1, 2})
-        for (int pf : {8, 32}) {
-          const int per = (pr->P + H - 1) / H, iper = (pr->P + HI - 1) / HI;
-          const int est = R * (per + iper + pf);  // live registers, roughly
-          if (est > 160 || H * HI > 8) continue;
-          if (H * HI > 1 && pr->P <= 24) continue;
-          JitConfig c;
-          c.rows = R;
-          c.groups = H;
-          c.igroups = HI;
-          c.prefetch = pf;
-          c.min_blocks = 1;
-          if (jit_smem_bytes(pr, c) > 200 * 1024) continue;
-          out.push_back(c);
-        }
-  if (out.empty()) out.push_back(jit_default_config(pr));
+        for (int SG : {1, 2, 4})
+          for (int pf : {8, 32}) {
+            const int per = (pr->P + H - 1) / H, iper = (pr->P + HI - 1) / HI;
+            const int est = R * (per + iper + pf);  // live registers, roughly
+            if (est > 160 || H * HI * SG > 8) continue;
+            if (H * HI > 1 && pr->P <= 24) continue;
+            if (SG > 1 && which == 0 && pr->n > 16384) continue;  // enough rows already
+            JitConfig c;
+            c.rows = R;
+            c.groups = H;
+            c.igroups = HI;
+            c.sgroups = SG;
+            c.prefetch = pf;
+            c.min_blocks = 1;
+            if (jit_smem_bytes(pr, c) > 200 * 1024) continue;
+            out.push_back(c);
+          }
+  if (out.empty()) out.push_back(jit_default_config(pr, which));
   return out;
 }
 
-static std::string tune_key(const sg_problem* pr) {
+static std::string tune_key(const sg_problem* pr, const Ell& A) {
   cudaDeviceProp prop{};
   cudaGetDeviceProperties(&prop, pr->device);
   std::ostringstream os;
-  os << prop.name << "|" << pr->P << "|" << pr->K << "|" << pr->T << "|" << pr->n;
+  os << prop.name << "|" << pr->P << "|" << pr->K << "|" << pr->T << "|" << A.n << "|" << A.S;
   for (int64_t t = 0; t < pr->T; ++t) os << "," << pr->kab[3 * t] << ":" << pr->kab[3 * t + 1] << ":" << pr->kab[3 * t + 2];
   char key[32];
   std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(os.str()));
   return key;
 }
 
-sg_status jit_autotune(sg_problem* pr, int force, double* best_ms) {
+sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
   if (!jit_eligible(pr)) {
     set_error("sg_apply_autotune: the specialised kernel is not available for this size");
     return SG_ERR_UNSUPPORTED;
   }
-  const std::string path = cache_dir() + "/tune_" + tune_key(pr) + ".txt";
+  if (which == 1 && !pr->solver) {
+    set_error("sg_apply_autotune: the coarse operator exists after sg_precond_setup");
+    return SG_ERR_ARG;
+  }
+  const Ell& A = which == 1 ? coarse_ell(pr) : pr->fine;
+  const std::string path = cache_dir() + "/tune_" + tune_key(pr, A) + ".txt";
   if (!force) {
     std::ifstream in(path);
     JitConfig c;
     double ms = 0;
-    if (in >> c.rows >> c.groups >> c.igroups >> c.prefetch >> c.min_blocks >> ms) {
+    if (in >> c.rows >> c.groups >> c.igroups >> c.sgroups >> c.prefetch >> c.min_blocks >> ms) {
       if (best_ms) *best_ms = ms;
-      return jit_configure(pr, c);
+      return jit_configure(pr, which, c);
     }
   }
-  const Ell& A = pr->fine;
-  const int64_t len = int64_t(pr->P) * pr->ld;
+  const int64_t len = int64_t(pr->P) * std::max<int64_t>(pr->ld, A.ldr);
   DevBuf X, Y;
   SG_TRY(X.alloc(len * 4));
   SG_TRY(Y.alloc(len * 4));
@@ -461,21 +481,21 @@ sg_status jit_autotune(sg_problem* pr, int force, double* best_ms) {
   cudaEvent_t e0, e1;
   SG_CUDA(cudaEventCreate(&e0));
   SG_CUDA(cudaEventCreate(&e1));
-  JitConfig best = jit_default_config(pr);
+  JitConfig best = jit_default_config(pr, which);
   double best_t = 1e30;
   sg_status status = SG_OK;
-  for (const JitConfig& c : candidates(pr)) {
+  for (const JitConfig& c : candidates(pr, which)) {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
     if (jit_compile(jit_apply_source(pr, c), &lib, &kern, nullptr, nullptr, pr->device) != SG_OK) continue;
     std::vector<float> ts;
     for (int rep = 0; rep < 7 && status == SG_OK; ++rep) {
-      status = launch_kernel(kern, c, jit_smem_bytes(pr, c), A, dp<float>(X), pr->ld, nullptr, 0, dp<float>(Y),
-                             pr->ld, st);
+      status = launch_kernel(kern, c, jit_smem_bytes(pr, c), A, dp<float>(X), A.ldr, nullptr, 0, dp<float>(Y),
+                             A.ldr, st);
       if (status != SG_OK) break;
       if (rep < 2) continue;
       cudaEventRecord(e0, st);
-      launch_kernel(kern, c, jit_smem_bytes(pr, c), A, dp<float>(X), pr->ld, nullptr, 0, dp<float>(Y), pr->ld, st);
+      launch_kernel(kern, c, jit_smem_bytes(pr, c), A, dp<float>(X), A.ldr, nullptr, 0, dp<float>(Y), A.ldr, st);
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
       float ms = 0;
@@ -499,9 +519,9 @@ sg_status jit_autotune(sg_problem* pr, int force, double* best_ms) {
   mkdirs(cache_dir());
   std::ofstream out(path);
   if (out)
-    out << best.rows << " " << best.groups << " " << best.igroups << " " << best.prefetch << " " << best.min_blocks
-        << " " << best_t << "\n";
-  return jit_configure(pr, best);
+    out << best.rows << " " << best.groups << " " << best.igroups << " " << best.sgroups << " " << best.prefetch
+        << " " << best.min_blocks << " " << best_t << "\n";
+  return jit_configure(pr, which, best);
 }
 
 }  // namespace sg

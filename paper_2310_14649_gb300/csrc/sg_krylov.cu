@@ -4,6 +4,7 @@
 // update of the Hessenberg column and the triangular solve, all on the
 // device.  Dot products accumulate in FP64 across threads; for FP32 vectors
 // each thread first sums its few products in FP32.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -59,52 +60,97 @@ __device__ void block_reduce_finish(double (&v)[NV], int nv, double* __restrict_
   }
 }
 
-// mode 0: out = V^T w
-// mode 1: w -= V h; out = V^T w
-// mode 2: w -= V h; out[0] = w^T w
+// One partial sum per (block, vector), reduced by the last block to finish.
+// blockIdx.y = vector index i, blockIdx.x = chunk of the elements; every
+// block reads its chunk of V_i and w once, so the grid has nv x chunks
+// blocks of few registers each.  FP32 products are summed in FP32 over at
+// most 8 elements per thread, then in FP64.
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_multi(const T* __restrict__ V, int64_t stride, int nv,
-                                                       const double* __restrict__ h, T* __restrict__ w, int64_t len,
-                                                       int mode, double* __restrict__ partial,
-                                                       unsigned* __restrict__ counter, double* __restrict__ out) {
-  using A = typename Acc<T>::type;
-  double tot[kMaxV];
-  A loc[kMaxV];
-  T hc[kMaxV];
-#pragma unroll
-  for (int i = 0; i < kMaxV; ++i) {
-    tot[i] = 0.0;
-    loc[i] = A(0);
-    hc[i] = (mode > 0 && i < nv) ? T(h[i]) : T(0);
+__device__ void last_block_finish(double v, double* __restrict__ partial, unsigned* __restrict__ counter,
+                                  double* __restrict__ out) {
+  __shared__ double red[kRedThreads / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  const int nbx = gridDim.x, nv = gridDim.y;
+  if (threadIdx.x == 0) {
+    double x = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) x += red[w];
+    partial[blockIdx.y * nbx + blockIdx.x] = x;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == unsigned(nbx * nv) - 1u);
   }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    for (int i = wid; i < nv; i += kRedThreads / 32) {
+      double x = 0.0;
+      for (int b = lane; b < nbx; b += 32) x += partial[i * nbx + b];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) out[i] = x;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// out[i] = V_i . w  (V_i = V + i * stride), or out[0] = w . w when V == w
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_mdot(const T* __restrict__ V, int64_t stride, const T* __restrict__ w,
+                                                      int64_t len, double* __restrict__ partial,
+                                                      unsigned* __restrict__ counter, double* __restrict__ out) {
+  using A = typename Acc<T>::type;
+  const T* v = V + int64_t(blockIdx.y) * stride;
+  double tot = 0.0;
+  A loc = A(0);
   int cnt = 0;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x) {
-    T we = w[e];
-    if (mode > 0) {
-#pragma unroll
-      for (int i = 0; i < kMaxV; ++i)
-        if (i < nv) we -= hc[i] * V[int64_t(i) * stride + e];
-      w[e] = we;
-    }
-    if (mode == 2) {
-      loc[0] += A(we) * A(we);
-    } else {
-#pragma unroll
-      for (int i = 0; i < kMaxV; ++i)
-        if (i < nv) loc[i] += A(V[int64_t(i) * stride + e]) * A(we);
-    }
-    if (++cnt == 8) {  // flush the short FP32 partial sums into FP64
-#pragma unroll
-      for (int i = 0; i < kMaxV; ++i) {
-        tot[i] += double(loc[i]);
-        loc[i] = A(0);
-      }
+    loc += A(v[e]) * A(w[e]);
+    if (++cnt == 8) {
+      tot += double(loc);
+      loc = A(0);
       cnt = 0;
     }
   }
-#pragma unroll
-  for (int i = 0; i < kMaxV; ++i) tot[i] += double(loc[i]);
-  block_reduce_finish<kMaxV>(tot, mode == 2 ? 1 : nv, partial, counter, out);
+  tot += double(loc);
+  last_block_finish<T>(tot, partial, counter, out);
+}
+
+// w -= sum_i h_i V_i, and (when out) out[0] = w . w of the updated w
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_axpy_norm(const T* __restrict__ V, int64_t stride, int nv,
+                                                           const double* __restrict__ h, T* __restrict__ w,
+                                                           int64_t len, double* __restrict__ partial,
+                                                           unsigned* __restrict__ counter, double* __restrict__ out) {
+  using A = typename Acc<T>::type;
+  __shared__ T hs[kMaxV];
+  if (threadIdx.x < nv) hs[threadIdx.x] = T(h[threadIdx.x]);
+  __syncthreads();
+  double tot = 0.0;
+  A loc = A(0);
+  int cnt = 0;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x) {
+    T we = w[e];
+    for (int i = 0; i < nv; ++i) we -= hs[i] * V[int64_t(i) * stride + e];
+    w[e] = we;
+    loc += A(we) * A(we);
+    if (++cnt == 8) {
+      tot += double(loc);
+      loc = A(0);
+      cnt = 0;
+    }
+  }
+  tot += double(loc);
+  if (out) last_block_finish<T>(tot, partial, counter, out);
+}
+
+inline unsigned chunks_for(int64_t len, int nv) {
+  // about 4 x 152 blocks in total, at least one 256-thread block per 1024 elements
+  int64_t want = (4 * 152 + nv - 1) / nv;
+  int64_t cap = (len + 1023) / 1024;
+  int64_t c = want < cap ? want : cap;
+  return unsigned(c < 1 ? 1 : c);
 }
 
 template <typename T>
@@ -212,12 +258,13 @@ inline unsigned grid_for(int64_t len) {
 template <typename T>
 sg_status vec_mdot(const T* V, int64_t stride, int nv, const T* w, int64_t len, double* out, double* partial,
                    unsigned* counter, cudaStream_t st) {
-  if (nv > kMaxV) {
-    set_error("vec_mdot: too many vectors");
+  if (nv < 1 || nv > kMaxV) {
+    set_error("vec_mdot: nv must be in [1, 32]");
     return SG_ERR_ARG;
   }
-  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, nullptr, const_cast<T*>(w), len, 0, partial, counter,
-                                                 out); note_launch();
+  const unsigned nbx = std::min<unsigned>(chunks_for(len, nv), unsigned(kRedBlocks));
+  k_mdot<T><<<dim3(nbx, unsigned(nv)), kRedThreads, 0, st>>>(V, stride, w, len, partial, counter, out);
+  note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
@@ -225,24 +272,26 @@ sg_status vec_mdot(const T* V, int64_t stride, int nv, const T* w, int64_t len, 
 template <typename T>
 sg_status vec_maxpy_mdot(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
                          double* partial, unsigned* counter, cudaStream_t st) {
-  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, h, w, len, 1, partial, counter, out); note_launch();
+  const unsigned nb = std::min<unsigned>(chunks_for(len, 1), unsigned(kRedBlocks));
+  k_axpy_norm<T><<<dim3(nb, 1), kRedThreads, 0, st>>>(V, stride, nv, h, w, len, partial, counter, nullptr);
+  note_launch();
   SG_CUDA(cudaGetLastError());
-  return SG_OK;
+  return vec_mdot<T>(V, stride, nv, w, len, out, partial, counter, st);
 }
 
 template <typename T>
 sg_status vec_maxpy_norm(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
                          double* partial, unsigned* counter, cudaStream_t st) {
-  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(V, stride, nv, h, w, len, 2, partial, counter, out); note_launch();
+  const unsigned nb = std::min<unsigned>(chunks_for(len, 1), unsigned(kRedBlocks));
+  k_axpy_norm<T><<<dim3(nb, 1), kRedThreads, 0, st>>>(V, stride, nv, h, w, len, partial, counter, out);
+  note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
 
 template <typename T>
 sg_status vec_norm2(const T* x, int64_t len, double* out, double* partial, unsigned* counter, cudaStream_t st) {
-  k_multi<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, 0, 0, nullptr, const_cast<T*>(x), len, 2, partial, counter, out); note_launch();
-  SG_CUDA(cudaGetLastError());
-  return SG_OK;
+  return vec_mdot<T>(x, 0, 1, x, len, out, partial, counter, st);
 }
 
 template <typename T>

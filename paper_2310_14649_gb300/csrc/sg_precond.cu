@@ -20,22 +20,45 @@ constexpr int kIdxMask = kOwnedBit - 1;
 //   forward  y_j = Linv_j (r_j - Loff_j y_{j-1})
 //   backward x_j = Linv_j^T (y_j - Loff_{j+1}^T x_{j+1})
 // One CTA per (box, chunk of MC modes); the local block lives in shared
-// memory as y[line][slot][mode] with a padded mode stride (MC + 1).
+// memory as y[line][slot][mode] with a padded mode stride (MC + 1).  The two
+// W x W matrices of the next line step are copied into shared memory with
+// cp.async while the current step computes (double buffering), so every
+// step reads only shared memory.  W is a multiple of 4 (16-byte rows).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void stage_mats(T* dst_off, T* dst_lin, const T* src_off, const T* src_lin, int WW) {
+  const int chunks = WW * int(sizeof(T)) / 16;
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+    if (src_off) cp_async16(reinterpret_cast<char*>(dst_off) + 16 * c, reinterpret_cast<const char*>(src_off) + 16 * c);
+    cp_async16(reinterpret_cast<char*>(dst_lin) + 16 * c, reinterpret_cast<const char*>(src_lin) + 16 * c);
+  }
+  cp_async_commit();
+}
+
 template <typename T>
 __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__ Z, int P, int MC,
                             int W, int Lm, const int* __restrict__ nlines, const int* __restrict__ gidx,
                             const T* __restrict__ linv, const T* __restrict__ loff) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int MS = MC + 1;
-  T* y = reinterpret_cast<T*>(smem_raw);  // [Lm * W][MS]
-  T* s = y + size_t(Lm) * W * MS;         // [W][MS]
+  const int MS = MC + 1, WW = W * W;
+  T* mats = reinterpret_cast<T*>(smem_raw);  // [2 buffers][off, lin][W*W]
+  T* y = mats + 4 * WW;                      // [Lm * W][MS]
+  T* s = y + size_t(Lm) * W * MS;            // [W][MS]
   const int box = blockIdx.x, a0 = blockIdx.y * MC;
   const int nl = nlines[box];
   const int* gbox = gidx + size_t(box) * Lm * W;
-  const T* Li = linv + size_t(box) * Lm * W * W;
-  const T* Lo = loff + size_t(box) * Lm * W * W;
+  const T* Li = linv + size_t(box) * Lm * WW;
+  const T* Lo = loff + size_t(box) * Lm * WW;
   const int nthr = blockDim.x;
+  // first forward step's matrices
+  stage_mats<T>(mats, mats + WW, nullptr, Li, WW);
   // gather (nodes fastest across threads)
   const int nslot = nl * W;
   for (int e = threadIdx.x; e < nslot * MC; e += nthr) {
@@ -45,13 +68,22 @@ __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__
     if (g >= 0 && a0 + a < P) v = R[int64_t(a0 + a) * ld + (g & kIdxMask)];
     y[q * MS + a] = v;
   }
-  __syncthreads();
   const int a = threadIdx.x % MC, grp = threadIdx.x / MC, ngrp = nthr / MC;
   const bool act = grp < ngrp;
-  // forward sweep
+  int buf = 0;
+  // forward sweep: step j uses Loff_j (j > 0) and Linv_j
   for (int j = 0; j < nl; ++j) {
+    cp_async_wait_all();
+    __syncthreads();
+    const T* Lof = mats + buf * 2 * WW;
+    const T* Lin = Lof + WW;
+    // prefetch the next step's matrices into the other buffer
+    T* nb = mats + (buf ^ 1) * 2 * WW;
+    if (j + 1 < nl)
+      stage_mats<T>(nb, nb + WW, Lo + size_t(j + 1) * WW, Li + size_t(j + 1) * WW, WW);
+    else  // first backward step: Linv_{nl-1}, no Loff
+      stage_mats<T>(nb, nb + WW, nullptr, Li + size_t(nl - 1) * WW, WW);
     if (act) {
-      const T* Lof = Lo + size_t(j) * W * W;
       for (int t = grp; t < W; t += ngrp) {
         T acc = y[(j * W + t) * MS + a];
         if (j > 0)
@@ -61,19 +93,23 @@ __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__
     }
     __syncthreads();
     if (act) {
-      const T* Lin = Li + size_t(j) * W * W;
       for (int t = grp; t < W; t += ngrp) {
         T acc = T(0);
         for (int u = 0; u <= t; ++u) acc += Lin[t * W + u] * s[u * MS + a];
         y[(j * W + t) * MS + a] = acc;
       }
     }
-    __syncthreads();
+    buf ^= 1;
   }
-  // backward sweep
+  // backward sweep: step j uses Loff_{j+1} (j + 1 < nl) and Linv_j
   for (int j = nl - 1; j >= 0; --j) {
+    cp_async_wait_all();
+    __syncthreads();
+    const T* Lof = mats + buf * 2 * WW;
+    const T* Lin = Lof + WW;
+    T* nb = mats + (buf ^ 1) * 2 * WW;
+    if (j > 0) stage_mats<T>(nb, nb + WW, Lo + size_t(j) * WW, Li + size_t(j - 1) * WW, WW);
     if (act) {
-      const T* Lof = Lo + size_t(j + 1) * W * W;
       for (int t = grp; t < W; t += ngrp) {
         T acc = y[(j * W + t) * MS + a];
         if (j + 1 < nl)
@@ -83,15 +119,16 @@ __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__
     }
     __syncthreads();
     if (act) {
-      const T* Lin = Li + size_t(j) * W * W;
       for (int t = grp; t < W; t += ngrp) {
         T acc = T(0);
         for (int u = t; u < W; ++u) acc += Lin[u * W + t] * s[u * MS + a];
         y[(j * W + t) * MS + a] = acc;
       }
     }
-    __syncthreads();
+    buf ^= 1;
   }
+  cp_async_wait_all();
+  __syncthreads();
   // scatter owned nodes
   for (int e = threadIdx.x; e < nslot * MC; e += nthr) {
     int aa = e / nslot, q = e - aa * nslot;
@@ -226,7 +263,7 @@ sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld,
   const int MC = (P + nchunk - 1) / nchunk;
   const int ngrp = std::max(1, 256 / MC);
   const int threads = ngrp * MC;
-  const size_t smem = (size_t(D.lmax) * D.wmax + D.wmax) * (MC + 1) * sizeof(T);
+  const size_t smem = ((size_t(D.lmax) * D.wmax + D.wmax) * (MC + 1) + 4 * size_t(D.wmax) * D.wmax) * sizeof(T);
   static bool attr[2] = {false, false};
   if (!attr[sizeof(T) == 8]) {
     SG_CUDA(cudaFuncSetAttribute(k_ras_local<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));

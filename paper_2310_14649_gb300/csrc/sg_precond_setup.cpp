@@ -188,6 +188,7 @@ static sg_status setup_ras(sg_problem* pr, Precond& pc) {
     R.nlines[b] = int32_t(lines[b].size());
     R.lmax = std::max<int>(R.lmax, R.nlines[b]);
   }
+  R.wmax = int(round_up(R.wmax, 4));  // 16-byte matrix rows for cp.async
   const int W = R.wmax, Lm = R.lmax;
   const size_t per_line = size_t(W) * W;
   std::vector<double> linv(size_t(R.nbox) * Lm * per_line, 0.0), loff(linv.size(), 0.0);

@@ -170,8 +170,9 @@ def test_bad_arguments(gpu):
     assert st == -1
 
 
-@pytest.mark.parametrize("cfg", [(1, 1, 1, 8, 1), (2, 1, 1, 16, 1), (1, 2, 1, 0, 2), (2, 3, 2, 32, 1),
-                                 (1, 4, 1, 4, 1), (1, 2, 2, 8, 1), (1, 1, 3, 8, 1)])
+@pytest.mark.parametrize("cfg", [(1, 1, 1, 1, 8, 1), (2, 1, 1, 1, 16, 1), (1, 2, 1, 1, 0, 2), (2, 3, 2, 1, 32, 1),
+                                 (1, 4, 1, 2, 4, 1), (1, 2, 2, 2, 8, 1), (1, 1, 3, 1, 8, 1), (1, 1, 1, 4, 8, 1),
+                                 (2, 1, 1, 8, 8, 1)])
 @pytest.mark.parametrize("N", [20, 21])
 def test_specialised_kernel_configs(gpu, cfg, N):
     """Every tile shape (rows per thread, output groups, prefetch, CTAs per

@@ -161,3 +161,18 @@ def test_coarse_correction_and_two_level(pair, dt):
     Y, Xq = run(prob, sg.PC_TWOLEVEL, X, ref.n, dtype)
     Yr = tl.apply(Xq)
     assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))
+
+
+@pytest.mark.parametrize("cfg", [(1, 1, 1, 4, 8, 1), (1, 2, 1, 2, 16, 1), (2, 1, 1, 2, 8, 1), (1, 1, 2, 1, 8, 1)])
+def test_coarse_apply_tile_shapes(pair, cfg):
+    """The coarse family's specialised kernel in several tile shapes."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, _ = pair
+    sg.sg_apply_config(prob, *cfg, which=1)
+    Xc = random_block(tl.nc, ref.P, seed=41)
+    Y, Xq = run(prob, sg.PC_COARSE_APPLY, Xc, tl.nc, torch.float32)
+    Yr = coarse.coarse_apply(tl.Acs, tl.G, Xq)
+    scale = np.max(np.abs(coarse.coarse_apply([abs(a) for a in tl.Acs], abs(tl.G), abs(Xq))))
+    assert np.max(np.abs(Y - Yr)) <= 1e-4 * scale
+    sg.sg_apply_config(prob, 1, 1, 1, 4, 32, 1, which=1)
