@@ -188,6 +188,10 @@ typedef struct {
   double inner_rtol;   /* coarse GMRES tolerance; <= 0 = 1e-5           */
   int inner_max;       /* coarse GMRES iteration cap; <= 0 = 100        */
   int smoother;        /* 0 = RAS (only value accepted)                 */
+  int host_loops;      /* 0 (default): each coarse solve is one CUDA graph
+                          launch whose restart and Arnoldi loops are
+                          conditional WHILE nodes decided on the device;
+                          1: the same GMRES driven from the host         */
 } sg_precond_opts;
 
 /* Builds partitions, local factors, the coarse space, the AMG hierarchy,

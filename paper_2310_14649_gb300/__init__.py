@@ -137,8 +137,8 @@ def sg_residual(prob, F, X, R, stream=None):
 
 
 def sg_precond_setup(prob, sx, sy, overlap, omega=0.0, inner_rtol=0.0, inner_max=0, smoother=0,
-                     stream=None):
-    opts = _lib.PrecondOpts(sx, sy, overlap, omega, inner_rtol, inner_max, smoother)
+                     host_loops=False, stream=None):
+    opts = _lib.PrecondOpts(sx, sy, overlap, omega, inner_rtol, inner_max, smoother, 1 if host_loops else 0)
     call("sg_precond_setup", prob.handle, ctypes.byref(opts), stream_handle(stream))
     prob.nc = sg_precond_info(prob)[2]
 

@@ -136,6 +136,12 @@ sg_status apply_ell(const Ell& A, const TripleTables& tri, int P, int K, const T
   return SG_OK;
 }
 
+sg_status apply_attrs_init() {
+  SG_CUDA(cudaFuncSetAttribute(k_apply_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  SG_CUDA(cudaFuncSetAttribute(k_apply_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  return SG_OK;
+}
+
 Profiler::~Profiler() {
   for (auto& r : pool) {
     if (r.a) cudaEventDestroy(r.a);

@@ -24,6 +24,9 @@ sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStr
 template <typename T>
 sg_status amg_vcycle(const Precond& pc, AmgWork<T>& w, int P, cudaStream_t st);
 sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w);
+// sets the dynamic shared-memory limits of the library's kernels once per
+// process (before any graph capture)
+sg_status kernel_attrs_init();
 
 // ---- vector kernels (sg_krylov.cu) ----
 // grid of the fused multi-vector reductions and the vectors per pass; the
@@ -66,6 +69,34 @@ sg_status vec_convert(const Ti* x, To* y, int64_t len, const double* scale_num, 
 // x64 += s * double(d)   (s on the device)
 sg_status vec_add_scaled_f32(double* x, const float* d, int64_t len, const double* s, cudaStream_t st);
 sg_status gmres_init(GmresState s, int m, const double* beta, cudaStream_t st);
+
+// Device-driven GMRES state: iv[0] j, iv[1] iterations of this solve,
+// iv[2] iteration cap, iv[3] stop flag, iv[4] iterations summed over
+// solves, iv[5] breakdown flag; dtol[0] absolute tolerance.
+struct DevGmres {
+  int* iv;
+  double* dtol;
+};
+template <typename T>
+sg_status dg_mdot(const T* V, int64_t stride, const T* w, int64_t len, double* out, double* partial, unsigned* counter,
+                  const int* jdev, int nv_max, cudaStream_t st);
+template <typename T>
+sg_status dg_axpy_norm(const T* V, int64_t stride, const double* h, T* w, int64_t len, double* out, double* partial,
+                       unsigned* counter, const int* jdev, cudaStream_t st);
+template <typename T>
+sg_status dg_axpy_multi(const T* V, int64_t stride, const double* coef, T* x, int64_t len, const int* kdev,
+                        cudaStream_t st);
+template <typename T>
+sg_status dg_scale_next(const T* w, T* V, int64_t stride, int64_t len, DevGmres d, const double* hn, cudaStream_t st);
+template <typename T>
+sg_status dg_copy_vj(const T* V, int64_t stride, int64_t lds, T* dst, int64_t ldd, int64_t n, int P, DevGmres d,
+                     cudaStream_t st);
+sg_status dg_init(DevGmres d, const double* rnorm2, double rtol, cudaGraphConditionalHandle outer, cudaStream_t st);
+sg_status dg_start(DevGmres d, GmresState s, int m, const double* beta2, cudaGraphConditionalHandle inner,
+                   cudaStream_t st);
+sg_status dg_givens(DevGmres d, GmresState s, int m, cudaGraphConditionalHandle inner, cudaStream_t st);
+sg_status dg_end(DevGmres d, GmresState s, cudaGraphConditionalHandle outer, cudaStream_t st);
+sg_status dg_backsolve(DevGmres d, GmresState s, int m, cudaStream_t st);
 sg_status gmres_givens(GmresState s, int m, int j, double* host_est, cudaStream_t st);
 sg_status gmres_backsolve(GmresState s, int m, int k, cudaStream_t st);
 

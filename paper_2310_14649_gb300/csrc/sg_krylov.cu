@@ -22,44 +22,6 @@ template <typename T> struct Acc;
 template <> struct Acc<double> { using type = double; };
 template <> struct Acc<float> { using type = float; };
 
-// block-reduce nv values (in registers) into partial[blockIdx * nv + i];
-// the last block to finish sums the partials into out[i] and resets the
-// counter (threadfence reduction).
-template <int NV>
-__device__ void block_reduce_finish(double (&v)[NV], int nv, double* __restrict__ partial,
-                                    unsigned* __restrict__ counter, double* __restrict__ out) {
-  __shared__ double red[kRedThreads / 32][kMaxV];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    if (i >= nv) break;
-    double x = v[i];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) red[wid][i] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double x = 0.0;
-    for (int w = 0; w < kRedThreads / 32; ++w) x += red[w][threadIdx.x];
-    partial[blockIdx.x * nv + threadIdx.x] = x;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    for (int i = wid; i < nv; i += kRedThreads / 32) {
-      double x = 0.0;
-      for (int b = lane; b < gridDim.x; b += 32) x += partial[b * nv + i];
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) out[i] = x;
-    }
-    if (threadIdx.x == 0) *counter = 0u;
-  }
-}
-
 // One partial sum per (block, vector), reduced by the last block to finish.
 // blockIdx.y = vector index i, blockIdx.x = chunk of the elements; every
 // block reads its chunk of V_i and w once, so the grid has nv x chunks
@@ -67,7 +29,7 @@ __device__ void block_reduce_finish(double (&v)[NV], int nv, double* __restrict_
 // most 8 elements per thread, then in FP64.
 template <typename T>
 __device__ void last_block_finish(double v, double* __restrict__ partial, unsigned* __restrict__ counter,
-                                  double* __restrict__ out) {
+                                  double* __restrict__ out, int nv_used) {
   __shared__ double red[kRedThreads / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -85,7 +47,7 @@ __device__ void last_block_finish(double v, double* __restrict__ partial, unsign
   __syncthreads();
   if (last) {
     __threadfence();
-    for (int i = wid; i < nv; i += kRedThreads / 32) {
+    for (int i = wid; i < nv_used; i += kRedThreads / 32) {
       double x = 0.0;
       for (int b = lane; b < nbx; b += 32) x += partial[i * nbx + b];
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -95,17 +57,22 @@ __device__ void last_block_finish(double v, double* __restrict__ partial, unsign
   }
 }
 
-// out[i] = V_i . w  (V_i = V + i * stride), or out[0] = w . w when V == w
+// out[i] = V_i . w  (V_i = V + i * stride), or out[0] = w . w when V == w.
+// With jdev the number of vectors is *jdev + 1 (read on the device; the
+// grid is sized for the maximum and the extra rows of blocks contribute 0).
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_mdot(const T* __restrict__ V, int64_t stride, const T* __restrict__ w,
                                                       int64_t len, double* __restrict__ partial,
-                                                      unsigned* __restrict__ counter, double* __restrict__ out) {
+                                                      unsigned* __restrict__ counter, double* __restrict__ out,
+                                                      const int* __restrict__ jdev) {
   using A = typename Acc<T>::type;
+  const int nv_used = jdev ? *jdev + 1 : int(gridDim.y);
   const T* v = V + int64_t(blockIdx.y) * stride;
   double tot = 0.0;
   A loc = A(0);
   int cnt = 0;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x) {
+  const int64_t lim = int(blockIdx.y) < nv_used ? len : 0;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < lim; e += int64_t(gridDim.x) * blockDim.x) {
     loc += A(v[e]) * A(w[e]);
     if (++cnt == 8) {
       tot += double(loc);
@@ -114,17 +81,20 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot(const T* __restrict__ V, i
     }
   }
   tot += double(loc);
-  last_block_finish<T>(tot, partial, counter, out);
+  last_block_finish<T>(tot, partial, counter, out, nv_used);
 }
 
-// w -= sum_i h_i V_i, and (when out) out[0] = w . w of the updated w
+// w -= sum_i h_i V_i, and (when out) out[0] = w . w of the updated w.
+// With jdev the number of vectors is *jdev + 1.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_axpy_norm(const T* __restrict__ V, int64_t stride, int nv,
                                                            const double* __restrict__ h, T* __restrict__ w,
                                                            int64_t len, double* __restrict__ partial,
-                                                           unsigned* __restrict__ counter, double* __restrict__ out) {
+                                                           unsigned* __restrict__ counter, double* __restrict__ out,
+                                                           const int* __restrict__ jdev) {
   using A = typename Acc<T>::type;
   __shared__ T hs[kMaxV];
+  if (jdev) nv = *jdev + 1;
   if (threadIdx.x < nv) hs[threadIdx.x] = T(h[threadIdx.x]);
   __syncthreads();
   double tot = 0.0;
@@ -142,7 +112,7 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_norm(const T* __restrict__
     }
   }
   tot += double(loc);
-  if (out) last_block_finish<T>(tot, partial, counter, out);
+  if (out) last_block_finish<T>(tot, partial, counter, out, 1);
 }
 
 inline unsigned chunks_for(int64_t len, int nv) {
@@ -165,7 +135,8 @@ __global__ void k_scale_by(const T* __restrict__ x, T* __restrict__ y, int64_t l
 
 template <typename T>
 __global__ void k_axpy_multi(const T* __restrict__ V, int64_t stride, int nv, const double* __restrict__ coef,
-                             T* __restrict__ x, int64_t len) {
+                             T* __restrict__ x, int64_t len, const int* __restrict__ kdev) {
+  if (kdev) nv = *kdev;
   T c[kMaxV];
 #pragma unroll
   for (int i = 0; i < kMaxV; ++i) c[i] = i < nv ? T(coef[i]) : T(0);
@@ -263,7 +234,7 @@ sg_status vec_mdot(const T* V, int64_t stride, int nv, const T* w, int64_t len, 
     return SG_ERR_ARG;
   }
   const unsigned nbx = std::min<unsigned>(chunks_for(len, nv), unsigned(kRedBlocks));
-  k_mdot<T><<<dim3(nbx, unsigned(nv)), kRedThreads, 0, st>>>(V, stride, w, len, partial, counter, out);
+  k_mdot<T><<<dim3(nbx, unsigned(nv)), kRedThreads, 0, st>>>(V, stride, w, len, partial, counter, out, nullptr);
   note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
@@ -273,7 +244,8 @@ template <typename T>
 sg_status vec_maxpy_mdot(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
                          double* partial, unsigned* counter, cudaStream_t st) {
   const unsigned nb = std::min<unsigned>(chunks_for(len, 1), unsigned(kRedBlocks));
-  k_axpy_norm<T><<<dim3(nb, 1), kRedThreads, 0, st>>>(V, stride, nv, h, w, len, partial, counter, nullptr);
+  k_axpy_norm<T><<<dim3(nb, 1), kRedThreads, 0, st>>>(V, stride, nv, h, w, len, partial, counter, nullptr,
+                                                       nullptr);
   note_launch();
   SG_CUDA(cudaGetLastError());
   return vec_mdot<T>(V, stride, nv, w, len, out, partial, counter, st);
@@ -283,7 +255,7 @@ template <typename T>
 sg_status vec_maxpy_norm(const T* V, int64_t stride, int nv, const double* h, T* w, int64_t len, double* out,
                          double* partial, unsigned* counter, cudaStream_t st) {
   const unsigned nb = std::min<unsigned>(chunks_for(len, 1), unsigned(kRedBlocks));
-  k_axpy_norm<T><<<dim3(nb, 1), kRedThreads, 0, st>>>(V, stride, nv, h, w, len, partial, counter, out);
+  k_axpy_norm<T><<<dim3(nb, 1), kRedThreads, 0, st>>>(V, stride, nv, h, w, len, partial, counter, out, nullptr);
   note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
@@ -306,7 +278,8 @@ sg_status vec_axpy_multi(const T* V, int64_t stride, int nv, const double* coef,
                          cudaStream_t st) {
   for (int i0 = 0; i0 < nv; i0 += kMaxV) {
     int cnt = nv - i0 < kMaxV ? nv - i0 : kMaxV;
-    k_axpy_multi<T><<<grid_for(len), 256, 0, st>>>(V + int64_t(i0) * stride, stride, cnt, coef + i0, x, len); note_launch();
+    k_axpy_multi<T><<<grid_for(len), 256, 0, st>>>(V + int64_t(i0) * stride, stride, cnt, coef + i0, x, len,
+                                                   nullptr); note_launch();
     SG_CUDA(cudaGetLastError());
   }
   return SG_OK;
@@ -342,6 +315,203 @@ sg_status gmres_backsolve(GmresState s, int m, int k, cudaStream_t st) {
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Device-driven GMRES: the iteration index, the counters and the stopping
+// decisions live in device memory (DevGmres), so a whole restarted solve
+// runs inside one CUDA graph whose loops are conditional WHILE nodes.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_dg_init(DevGmres d, const double* __restrict__ rnorm2, double rtol, cudaGraphConditionalHandle outer) {
+  const double nr = sqrt(*rnorm2);
+  d.dtol[0] = rtol * nr;
+  d.iv[1] = 0;  // iterations
+  d.iv[3] = 0;  // stop
+  cudaGraphSetConditional(outer, nr > 0.0 ? 1u : 0u);
+}
+
+// start of a restart cycle: beta = ||r0||, g = beta e_0, j = 0
+__global__ void k_dg_start(DevGmres d, GmresState s, int m, const double* __restrict__ beta2,
+                           cudaGraphConditionalHandle inner) {
+  const double beta = sqrt(*beta2);
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) s.g[i] = i == 0 ? beta : 0.0;
+  if (threadIdx.x == 0) {
+    s.scal[3] = beta;
+    d.iv[0] = 0;
+    const bool go = beta > d.dtol[0] && isfinite(beta) && d.iv[1] < d.iv[2];
+    if (!go) d.iv[3] = 1;
+    cudaGraphSetConditional(inner, go ? 1u : 0u);
+  }
+}
+
+// Hessenberg column j (device j), rotations, estimate; j and the iteration
+// count advance; the inner loop continues while the estimate is above the
+// tolerance, the cycle has room and the iteration cap is not reached.
+__global__ void k_dg_givens(DevGmres d, GmresState s, int m, cudaGraphConditionalHandle inner) {
+  if (threadIdx.x != 0) return;
+  const int j = d.iv[0];
+  double* col = s.H + int64_t(j) * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = s.hsum[i] + s.hsum[(m + 1) + i];
+  const double hn = sqrt(s.scal[0]);
+  col[j + 1] = hn;
+  s.scal[1] = hn;
+  for (int i = 0; i < j; ++i) {
+    double t = s.cs[i] * col[i] + s.sn[i] * col[i + 1];
+    col[i + 1] = -s.sn[i] * col[i] + s.cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  const double c = den != 0.0 ? col[j] / den : 1.0, sn = den != 0.0 ? col[j + 1] / den : 0.0;
+  s.cs[j] = c;
+  s.sn[j] = sn;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  s.g[j + 1] = -sn * s.g[j];
+  s.g[j] = c * s.g[j];
+  const double est = fabs(s.g[j + 1]);
+  s.scal[2] = est;
+  const bool bad = !isfinite(est) || !isfinite(hn);
+  d.iv[0] = j + 1;
+  d.iv[1] += 1;
+  d.iv[4] += 1;  // iterations summed over solves
+  if (bad) d.iv[5] = 1;
+  const bool go = !bad && est > d.dtol[0] && hn != 0.0 && j + 1 < m && d.iv[1] < d.iv[2];
+  cudaGraphSetConditional(inner, go ? 1u : 0u);
+}
+
+// end of a cycle: stop when converged, stalled, failed or out of iterations
+__global__ void k_dg_end(DevGmres d, GmresState s, cudaGraphConditionalHandle outer) {
+  const double est = s.scal[2];
+  const bool done = d.iv[3] || d.iv[5] || !(est > d.dtol[0]) || d.iv[1] >= d.iv[2];
+  cudaGraphSetConditional(outer, done ? 0u : 1u);
+}
+
+__global__ void k_dg_backsolve(DevGmres d, GmresState s, int m) {
+  if (threadIdx.x != 0) return;
+  const int k = d.iv[0];
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = s.g[i];
+    for (int c = i + 1; c < k; ++c) acc -= s.H[int64_t(c) * (m + 1) + i] * s.y[c];
+    const double dg = s.H[int64_t(i) * (m + 1) + i];
+    s.y[i] = dg != 0.0 ? acc / dg : 0.0;
+  }
+}
+
+// V_{j} = w / h_{j,j-1} for the device index j (already advanced)
+template <typename T>
+__global__ void k_dg_scale_next(const T* __restrict__ w, T* __restrict__ V, int64_t stride, int64_t len, DevGmres d,
+                                const double* __restrict__ hn) {
+  const double h = *hn;
+  const T sc = T(h != 0.0 ? 1.0 / h : 0.0);
+  T* v = V + int64_t(d.iv[0]) * stride;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x)
+    v[e] = w[e] * sc;
+}
+
+// mode-major block copy from V_j (device index j) with a change of
+// leading dimension: dst[a * ldd + r] = V_j[a * lds + r], r < n
+template <typename T>
+__global__ void k_dg_copy_vj(const T* __restrict__ V, int64_t stride, int64_t lds, T* __restrict__ dst, int64_t ldd,
+                             int64_t n, DevGmres d) {
+  const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int a = blockIdx.y;
+  if (r >= n) return;
+  dst[int64_t(a) * ldd + r] = V[int64_t(d.iv[0]) * stride + int64_t(a) * lds + r];
+}
+
+}  // namespace
+
+template <typename T>
+sg_status dg_mdot(const T* V, int64_t stride, const T* w, int64_t len, double* out, double* partial, unsigned* counter,
+                  const int* jdev, int nv_max, cudaStream_t st) {
+  const unsigned nbx = std::min<unsigned>(chunks_for(len, nv_max), unsigned(kRedBlocks));
+  k_mdot<T><<<dim3(nbx, unsigned(nv_max)), kRedThreads, 0, st>>>(V, stride, w, len, partial, counter, out, jdev);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status dg_axpy_norm(const T* V, int64_t stride, const double* h, T* w, int64_t len, double* out, double* partial,
+                       unsigned* counter, const int* jdev, cudaStream_t st) {
+  const unsigned nb = std::min<unsigned>(chunks_for(len, 1), unsigned(kRedBlocks));
+  k_axpy_norm<T><<<dim3(nb, 1), kRedThreads, 0, st>>>(V, stride, 0, h, w, len, partial, counter, out, jdev);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status dg_axpy_multi(const T* V, int64_t stride, const double* coef, T* x, int64_t len, const int* kdev,
+                        cudaStream_t st) {
+  k_axpy_multi<T><<<grid_for(len), 256, 0, st>>>(V, stride, 0, coef, x, len, kdev);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status dg_scale_next(const T* w, T* V, int64_t stride, int64_t len, DevGmres d, const double* hn, cudaStream_t st) {
+  k_dg_scale_next<T><<<grid_for(len), 256, 0, st>>>(w, V, stride, len, d, hn);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status dg_copy_vj(const T* V, int64_t stride, int64_t lds, T* dst, int64_t ldd, int64_t n, int P, DevGmres d,
+                     cudaStream_t st) {
+  dim3 g(unsigned((n + 255) / 256), unsigned(P));
+  k_dg_copy_vj<T><<<g, 256, 0, st>>>(V, stride, lds, dst, ldd, n, d);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+sg_status dg_init(DevGmres d, const double* rnorm2, double rtol, cudaGraphConditionalHandle outer, cudaStream_t st) {
+  k_dg_init<<<1, 1, 0, st>>>(d, rnorm2, rtol, outer);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+sg_status dg_start(DevGmres d, GmresState s, int m, const double* beta2, cudaGraphConditionalHandle inner,
+                   cudaStream_t st) {
+  k_dg_start<<<1, 64, 0, st>>>(d, s, m, beta2, inner);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+sg_status dg_givens(DevGmres d, GmresState s, int m, cudaGraphConditionalHandle inner, cudaStream_t st) {
+  k_dg_givens<<<1, 32, 0, st>>>(d, s, m, inner);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+sg_status dg_end(DevGmres d, GmresState s, cudaGraphConditionalHandle outer, cudaStream_t st) {
+  k_dg_end<<<1, 1, 0, st>>>(d, s, outer);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+sg_status dg_backsolve(DevGmres d, GmresState s, int m, cudaStream_t st) {
+  k_dg_backsolve<<<1, 32, 0, st>>>(d, s, m);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+#define INST_DG(T)                                                                                             \
+  template sg_status dg_mdot<T>(const T*, int64_t, const T*, int64_t, double*, double*, unsigned*, const int*, \
+                                int, cudaStream_t);                                                            \
+  template sg_status dg_axpy_norm<T>(const T*, int64_t, const double*, T*, int64_t, double*, double*,          \
+                                     unsigned*, const int*, cudaStream_t);                                     \
+  template sg_status dg_axpy_multi<T>(const T*, int64_t, const double*, T*, int64_t, const int*, cudaStream_t); \
+  template sg_status dg_scale_next<T>(const T*, T*, int64_t, int64_t, DevGmres, const double*, cudaStream_t);   \
+  template sg_status dg_copy_vj<T>(const T*, int64_t, int64_t, T*, int64_t, int64_t, int, DevGmres, cudaStream_t);
+INST_DG(float)
+INST_DG(double)
+#undef INST_DG
 
 #define INST(T)                                                                                                   \
   template sg_status vec_mdot<T>(const T*, int64_t, int, const T*, int64_t, double*, double*, unsigned*,         \

@@ -350,6 +350,20 @@ sg_status precond_setup_coarse_plan(sg_problem* pr, Precond& pc, const CoarsePla
   return SG_OK;
 }
 
+sg_status apply_attrs_init();
+
+sg_status kernel_attrs_init() {
+  static bool done = false;
+  if (done) return SG_OK;
+  SG_CUDA(cudaFuncSetAttribute(k_ras_local<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  SG_CUDA(cudaFuncSetAttribute(k_ras_local<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  SG_CUDA(cudaFuncSetAttribute(k_node_transform<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  SG_CUDA(cudaFuncSetAttribute(k_node_transform<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  SG_TRY(apply_attrs_init());
+  done = true;
+  return SG_OK;
+}
+
 sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w) {
   DevBuf out;
   SG_TRY(out.alloc(size_t(pr->K) * 8));

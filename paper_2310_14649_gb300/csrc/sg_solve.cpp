@@ -199,6 +199,12 @@ struct SolverCtx {
   int64_t ld = 0, len = 0, ldc = 0, lenc = 0;
   KrylovWork<T> fine, coarse;
   DevBuf r1, zt, rc, ec;          // two-level temporaries
+  DevBuf consts;                  // device doubles {1, -1}
+  // device-driven coarse solve, captured once into a CUDA graph
+  DevBuf dg_iv, dg_tol;
+  DevGmres dg{};
+  cudaGraphExec_t cexec = nullptr;
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
   std::vector<DevBuf> amgbuf;     // b, x, t per level
   AmgWork<T> aw;
   bool ready = false;
@@ -214,6 +220,19 @@ struct SolverCtx {
     SG_TRY(coarse.init(lenc, pc->inner_restart, false));
     SG_TRY(r1.alloc(len * sizeof(T)));
     SG_TRY(zt.alloc(len * sizeof(T)));
+    SG_TRY(consts.alloc(2 * sizeof(double)));
+    {
+      const double cv[2] = {1.0, -1.0};
+      SG_CUDA(cudaMemcpy(consts.ptr, cv, sizeof cv, cudaMemcpyHostToDevice));
+    }
+    SG_TRY(dg_iv.alloc(16 * sizeof(int)));
+    SG_TRY(dg_tol.alloc(4 * sizeof(double)));
+    dg.iv = dp<int>(dg_iv);
+    dg.dtol = dp<double>(dg_tol);
+    {
+      const int cap_it = pc->inner_max;
+      SG_CUDA(cudaMemcpy(dg.iv + 2, &cap_it, sizeof(int), cudaMemcpyHostToDevice));
+    }
     SG_TRY(rc.alloc(lenc * sizeof(T)));
     SG_TRY(ec.alloc(lenc * sizeof(T)));
     amgbuf.resize(3 * pc->amg.size());
@@ -229,6 +248,12 @@ struct SolverCtx {
     }
     ready = true;
     return SG_OK;
+  }
+
+  ~SolverCtx() {
+    if (cexec) cudaGraphExecDestroy(cexec);
+    for (auto& c : cap)
+      if (c) cudaStreamDestroy(c);
   }
 
   sg_status apply_fine(const T* X, T* Y, const T* F, cudaStream_t st) {
@@ -247,7 +272,133 @@ struct SolverCtx {
                               cudaMemcpyDeviceToDevice, st));
     return SG_OK;
   }
+  // coarse preconditioner on a block already in the AMG level-0 input:
+  // V-cycle, copy out to `out` (coarse ld), Kronecker factor
+  sg_status coarse_pc_from_b0(T* out, cudaStream_t st) {
+    const AmgLevel& L0 = pc->amg[0];
+    SG_TRY(amg_vcycle<T>(*pc, aw, pr->P, st));
+    SG_CUDA(cudaMemcpy2DAsync(out, ldc * sizeof(T), aw.x[0], L0.ld * sizeof(T), pc->co.nc * sizeof(T), pr->P,
+                              cudaMemcpyDeviceToDevice, st));
+    return node_transform<T>(out, ldc, pc->co.nc, pr->P, dp_sel<T>(pc->gkron64, pc->gkron32), st);
+  }
+
+  // adds a WHILE node driven by `h` at the capture point of `st`
+  static sg_status add_while(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    SG_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    SG_CUDA(cudaGraphAddNode(&node, g, deps, ed, nd, &p));
+    *body = p.conditional.phGraph_out[0];
+    SG_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return SG_OK;
+  }
+
+  // coarse apply without the profiler (used inside graph capture)
+  sg_status apply_raw(const T* X, T* Y, const T* F, cudaStream_t st) {
+    if (sizeof(T) == 4 && pr->apply_mode != 1 && jit_eligible(pr))
+      return jit_apply_launch(pr, 1, pc->co.ell, reinterpret_cast<const float*>(X), ldc,
+                              reinterpret_cast<const float*>(F), ldc, reinterpret_cast<float*>(Y), ldc, st);
+    return apply_ell<T>(pc->co.ell, pc->co.tri, pr->P, pr->K, X, ldc, F, ldc, Y, ldc, st);
+  }
+
+  // Device-driven restarted GMRES on the coarse system (the 2GV3 inner
+  // solve): every decision is taken on the device, loops are conditional
+  // WHILE nodes, so one graph launch performs a whole coarse solve from rc
+  // into ec without a host round trip.
+  sg_status build_coarse_graph() {
+    // everything a captured launch needs must exist before the capture
+    if (sizeof(T) == 4 && pr->apply_mode != 1 && jit_eligible(pr)) SG_TRY(jit_apply_build(pr, 1));
+    SG_TRY(kernel_attrs_init());
+    for (auto& c : cap)
+      if (!c) SG_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    KrylovWork<T>& W = coarse;
+    const int m = W.m;
+    const AmgLevel& L0 = pc->amg[0];
+    const double* one = dp<double>(consts);
+    const double* minus_one = one + 1;
+    double* h1 = W.s.hsum;
+    double* h2 = W.s.hsum + (m + 1);
+    T* V = dp<T>(W.V);
+    T* w = dp<T>(W.w);
+    T* tmp = dp<T>(W.tmp);
+    T* tmp2 = dp<T>(W.tmp2);
+    T* Rc = dp<T>(rc);
+    T* Ec = dp<T>(ec);
+    double* part = dp<double>(W.partial);
+    unsigned* cnt = dp<unsigned>(W.counter);
+    const int* jdev = dg.iv;
+    cudaStream_t s1 = cap[0], s2 = cap[1], s3 = cap[2];
+
+    SG_CUDA(cudaStreamBeginCapture(s1, cudaStreamCaptureModeRelaxed));
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    SG_CUDA(cudaStreamGetCaptureInfo(s1, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle hout, hin;
+    SG_CUDA(cudaGraphConditionalHandleCreate(&hout, g, 0, 0));
+    SG_CUDA(cudaMemsetAsync(Ec, 0, lenc * sizeof(T), s1));
+    SG_TRY(vec_norm2<T>(Rc, lenc, W.s.scal + 5, part, cnt, s1));
+    SG_TRY(dg_init(dg, W.s.scal + 5, pc->inner_rtol, hout, s1));
+    cudaGraph_t body_out;
+    SG_TRY(add_while(s1, hout, &body_out));
+    {
+      SG_CUDA(cudaStreamBeginCaptureToGraph(s2, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      // r0 = rc - A_c ec
+      SG_TRY(apply_raw(Ec, V, Rc, s2));
+      SG_TRY(vec_norm2<T>(V, lenc, W.s.scal + 3, part, cnt, s2));
+      SG_CUDA(cudaGraphConditionalHandleCreate(&hin, body_out, 0, 0));
+      SG_TRY(dg_start(dg, W.s, m, W.s.scal + 3, hin, s2));
+      SG_TRY(vec_scale_by<T>(V, V, lenc, W.s.scal + 3, true, s2));
+      cudaGraph_t body_in;
+      SG_TRY(add_while(s2, hin, &body_in));
+      {
+        SG_CUDA(cudaStreamBeginCaptureToGraph(s3, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        SG_TRY(dg_copy_vj<T>(V, lenc, ldc, aw.b[0], L0.ld, pc->co.nc, pr->P, dg, s3));
+        SG_TRY(coarse_pc_from_b0(tmp, s3));
+        SG_TRY(apply_raw(tmp, w, nullptr, s3));
+        SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h1, part, cnt, jdev, m, s3));
+        SG_TRY(dg_axpy_norm<T>(V, lenc, h1, w, lenc, nullptr, part, cnt, jdev, s3));
+        SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h2, part, cnt, jdev, m, s3));
+        SG_TRY(dg_axpy_norm<T>(V, lenc, h2, w, lenc, W.s.scal, part, cnt, jdev, s3));
+        SG_TRY(dg_givens(dg, W.s, m, hin, s3));
+        SG_TRY(dg_scale_next<T>(w, V, lenc, lenc, dg, W.s.scal + 1, s3));
+        SG_CUDA(cudaStreamEndCapture(s3, &body_in));
+      }
+      // x += M (V y)
+      SG_TRY(dg_backsolve(dg, W.s, m, s2));
+      SG_CUDA(cudaMemsetAsync(tmp2, 0, lenc * sizeof(T), s2));
+      SG_TRY(dg_axpy_multi<T>(V, lenc, W.s.y, tmp2, lenc, jdev, s2));
+      SG_CUDA(cudaMemcpy2DAsync(aw.b[0], L0.ld * sizeof(T), tmp2, ldc * sizeof(T), pc->co.nc * sizeof(T), pr->P,
+                                cudaMemcpyDeviceToDevice, s2));
+      SG_TRY(coarse_pc_from_b0(tmp, s2));
+      SG_TRY(vec_axpy_multi<T>(tmp, 0, 1, one, Ec, lenc, s2));
+      SG_TRY(dg_end(dg, W.s, hout, s2));
+      SG_CUDA(cudaStreamEndCapture(s2, &body_out));
+    }
+    (void)minus_one;
+    SG_CUDA(cudaStreamEndCapture(s1, &g));
+    SG_CUDA(cudaGraphInstantiate(&cexec, g, 0));
+    SG_CUDA(cudaGraphDestroy(g));
+    return SG_OK;
+  }
+
+  // e_c ~ A_c^{-1} r_c by one launch of the device-driven coarse GMRES graph
+  sg_status coarse_solve_graph(cudaStream_t st) {
+    if (!cexec) SG_TRY(build_coarse_graph());
+    SG_CUDA(cudaGraphLaunch(cexec, st));
+    return SG_OK;
+  }
+
   // e_c ~ A_c^{-1} r_c by GMRES preconditioned with the AMG V-cycle
+  // (host-driven reference path of the same algorithm)
   sg_status coarse_solve(const T* Rc, T* Ec, cudaStream_t st) {
     SG_CUDA(cudaMemsetAsync(Ec, 0, lenc * sizeof(T), st));
     // absolute tolerance relative to ||r_c||
@@ -272,7 +423,10 @@ struct SolverCtx {
   // Q r = R_0^T A_c^{-1} R_0 r
   sg_status coarse_correction(const T* R, T* Z, bool add, cudaStream_t st) {
     SG_TRY(spmm<T>(pc->co.R, R, ld, nullptr, 0, dp<T>(rc), ldc, pr->P, 0, st));
-    SG_TRY(coarse_solve(dp<T>(rc), dp<T>(ec), st));
+    if (pc->device_loops)
+      SG_TRY(coarse_solve_graph(st));
+    else
+      SG_TRY(coarse_solve(dp<T>(rc), dp<T>(ec), st));
     if (!add) SG_CUDA(cudaMemsetAsync(Z, 0, len * sizeof(T), st));
     SG_TRY(spmm<T>(pc->co.RT, dp<T>(ec), ldc, nullptr, 0, Z, ld, pr->P, 1, st));
     return SG_OK;
@@ -499,6 +653,8 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   pc.inner_rtol = o->inner_rtol > 0 ? o->inner_rtol : 1e-5;
   pc.inner_max = o->inner_max > 0 ? o->inner_max : 100;
   pc.inner_restart = 30;
+  pc.device_loops = o->host_loops == 0;
+  SG_TRY(kernel_attrs_init());
   sg_status s = precond_setup_host(pr, pc);
   std::vector<double> ginv;
   if (s == SG_OK) s = kronecker_factor(pr, pc, ginv);
@@ -617,6 +773,9 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
   std::vector<double> hist;
   S.pc.inner_its_total = 0;
   S.pc.inner_calls = 0;
+  const int zero = 0;
+  SG_CUDA(cudaMemcpy(c64->dg.iv + 4, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  if (S.c32) SG_CUDA(cudaMemcpy(S.c32->dg.iv + 4, &zero, sizeof(int), cudaMemcpyHostToDevice));
   sg_status status = SG_OK;
   if (nF == 0.0) {
     SG_CUDA(cudaMemsetAsync(x64, 0, len * 8, st));
@@ -673,6 +832,13 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
   SG_CUDA(cudaStreamSynchronize(st));
   inf.relres = nF > 0 ? std::sqrt(S.host[2]) / nF : 0.0;
   inf.inner_it = S.pc.inner_its_total;
+  if (S.pc.device_loops) {
+    int dev_its = 0;
+    SolverCtx<float>* c32u = o->mode == 1 ? S.c32.get() : nullptr;
+    if (c32u) SG_CUDA(cudaMemcpy(&dev_its, c32u->dg.iv + 4, sizeof(int), cudaMemcpyDeviceToHost));
+    else SG_CUDA(cudaMemcpy(&dev_its, c64->dg.iv + 4, sizeof(int), cudaMemcpyDeviceToHost));
+    inf.inner_it += dev_its;
+  }
   inf.fallback_used = 0;
   inf.t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (o->hist_host && o->hist_cap > 0) {

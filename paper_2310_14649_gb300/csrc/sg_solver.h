@@ -65,6 +65,7 @@ struct Precond {
   DevBuf gtinv64, gtinv32;                 // omega * G~^{-1} (P x P)
   DevBuf gkron64, gkron32;                 // G~^{-1} (coarse AMG preconditioner)
   int inner_its_last = 0, inner_its_total = 0, inner_calls = 0;
+  bool device_loops = true;                // coarse GMRES as one CUDA graph launch
 };
 
 // For every coarse ELL position (s * ldc + I): the fine ELL positions
