@@ -337,7 +337,7 @@ __global__ void k_dg_start(DevGmres d, GmresState s, int m, const double* __rest
   const double beta = sqrt(*beta2);
   for (int i = threadIdx.x; i <= m; i += blockDim.x) s.g[i] = i == 0 ? beta : 0.0;
   if (threadIdx.x == 0) {
-    s.scal[3] = beta;
+    // scal[3] keeps beta^2: the normalisation of V_0 that follows reads it
     d.iv[0] = 0;
     const bool go = beta > d.dtol[0] && isfinite(beta) && d.iv[1] < d.iv[2];
     if (!go) d.iv[3] = 1;

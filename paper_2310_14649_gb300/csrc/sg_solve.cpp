@@ -423,8 +423,10 @@ struct SolverCtx {
   // Q r = R_0^T A_c^{-1} R_0 r
   sg_status coarse_correction(const T* R, T* Z, bool add, cudaStream_t st) {
     SG_TRY(spmm<T>(pc->co.R, R, ld, nullptr, 0, dp<T>(rc), ldc, pr->P, 0, st));
-    if (pc->device_loops)
+    if (pc->device_loops) {
       SG_TRY(coarse_solve_graph(st));
+      pc->last_coarse_dtype = sizeof(T) == 8 ? 0 : 1;
+    }
     else
       SG_TRY(coarse_solve(dp<T>(rc), dp<T>(ec), st));
     if (!add) SG_CUDA(cudaMemsetAsync(Z, 0, len * sizeof(T), st));
@@ -689,7 +691,15 @@ sg_status sg_precond_info(const sg_problem* pr, double* omega, int* amg_levels, 
   if (omega) *omega = pc.omega;
   if (amg_levels) *amg_levels = int(pc.amg.size());
   if (nc) *nc = pc.co.nc;
-  if (inner_its_last) *inner_its_last = pc.inner_its_last;
+  if (inner_its_last) {
+    *inner_its_last = pc.inner_its_last;
+    if (pc.device_loops && pc.last_coarse_dtype >= 0) {
+      // iterations of the last device-driven coarse solve (device counter)
+      const int* iv = pc.last_coarse_dtype == 0 ? pr->solver->c64->dg.iv : pr->solver->c32->dg.iv;
+      SG_CUDA(cudaDeviceSynchronize());
+      SG_CUDA(cudaMemcpy(inner_its_last, iv + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    }
+  }
   return SG_OK;
 }
 

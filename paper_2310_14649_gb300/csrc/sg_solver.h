@@ -66,6 +66,7 @@ struct Precond {
   DevBuf gkron64, gkron32;                 // G~^{-1} (coarse AMG preconditioner)
   int inner_its_last = 0, inner_its_total = 0, inner_calls = 0;
   bool device_loops = true;                // coarse GMRES as one CUDA graph launch
+  int last_coarse_dtype = -1;              // 0 FP64, 1 FP32: context of the last graph solve
 };
 
 // For every coarse ELL position (s * ldc + I): the fine ELL positions
