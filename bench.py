@@ -40,6 +40,27 @@ def parse():
     return ap.parse_args()
 
 
+def measured_traffic(shape):
+    """DRAM bytes per launch of the fine apply from the committed ncu
+    summary, when it was taken on the same generated kernel (same tile shape
+    and code-generator version); otherwise None."""
+    path = os.path.join(ROOT, "profiles", "sg_k1_poisson256_L4_p3.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("traffic-key:"):
+            for kv in line.split(":", 1)[1].split():
+                k, v = kv.split("=")
+                vals[k] = v
+    key = {k: str(shape[k]) for k in ("rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "generator")}
+    if not vals or any(vals.get(k) != v for k, v in key.items()):
+        return None
+    return int(vals["bytes"])
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -321,7 +342,7 @@ def main():
                      "achieved": round(achieved, 1) if achieved else None, "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
                      "peak_source": peak_kind, "bytes_per_launch": bytes_f32, "avg_launch_ms": avg_ms,
-                     "launches": cnt, "traffic": None},
+                     "launches": cnt, "traffic": measured_traffic(sg.sg_apply_info(prob))},
         "kernel_time_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in kinds.items()},
         "apply_share_of_step": round(tot_kernel / args.steps / ms_all, 3),
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": n * P * 8,

@@ -158,9 +158,9 @@ sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int
 sg_status sg_apply_autotune(sg_problem* prob, int which, int force, double* best_ms);
 
 /* Current tile shape of one family (rows, groups, igroups, sgroups,
- * prefetch, min_blocks into cfg6) and the seconds spent compiling or
- * loading its kernel. */
-sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg6, double* compile_s);
+ * prefetch, min_blocks, code-generator version into cfg7) and the seconds
+ * spent compiling or loading its kernel. */
+sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg7, double* compile_s);
 
 /* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
  * sg_apply (F may equal R for an in-place update). */

@@ -242,10 +242,10 @@ def sg_apply_autotune(prob, force=False, which=0):
 
 
 def sg_apply_info(prob, which=0):
-    cfg = np.zeros(6, dtype=np.int32)
+    cfg = np.zeros(7, dtype=np.int32)
     cs = ctypes.c_double()
     call("sg_apply_info", prob.handle, which, _lib.ptr(cfg, ctypes.c_int32), ctypes.byref(cs))
-    keys = ["rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks"]
+    keys = ["rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "generator"]
     out = {k: int(v) for k, v in zip(keys, cfg)}
     out["compile_s"] = cs.value
     return out

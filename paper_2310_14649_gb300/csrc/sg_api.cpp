@@ -112,16 +112,17 @@ sg_status sg_apply_autotune(sg_problem* pr, int which, int force, double* best_m
   return jit_autotune(pr, which, force, best_ms);
 }
 
-sg_status sg_apply_info(const sg_problem* pr, int which, int* cfg6, double* compile_s) {
+sg_status sg_apply_info(const sg_problem* pr, int which, int* cfg7, double* compile_s) {
   SG_ARG(pr && (which == 0 || which == 1), "sg_apply_info: NULL handle or which not in {0, 1}");
   const JitConfig c = pr->jit_cfg_set[which] ? pr->jit_cfg[which] : jit_default_config(pr, which);
-  if (cfg6) {
-    cfg6[0] = c.rows;
-    cfg6[1] = c.groups;
-    cfg6[2] = c.igroups;
-    cfg6[3] = c.sgroups;
-    cfg6[4] = c.prefetch;
-    cfg6[5] = c.min_blocks;
+  if (cfg7) {
+    cfg7[0] = c.rows;
+    cfg7[1] = c.groups;
+    cfg7[2] = c.igroups;
+    cfg7[3] = c.sgroups;
+    cfg7[4] = c.prefetch;
+    cfg7[5] = c.min_blocks;
+    cfg7[6] = kJitGeneratorVersion;
   }
   if (compile_s) *compile_s = pr->jit[which] ? pr->jit[which]->compile_s : 0.0;
   return SG_OK;

@@ -95,6 +95,7 @@ struct Profiler {
 
 // Register-specialised FP32 apply compiled at setup time (sg_jit.cpp).
 constexpr int kJitMaxP = 128;
+constexpr int kJitGeneratorVersion = 5;  // bump when the generated code changes
 constexpr int64_t kJitMaxT = 40000;
 struct JitConfig {
   int rows = 1;        // rows per thread (2: paired FP32 FMA)

@@ -286,7 +286,7 @@ static sg_status jit_compile(const std::string& src, cudaLibrary_t* lib, cudaKer
                              double* seconds, int dev) {
   auto t0 = std::chrono::steady_clock::now();
   char key[32];
-  std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(src + "|sm_103a|v5"));
+  std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(src + "|sm_103a|v" + std::to_string(kJitGeneratorVersion)));
   const std::string dir = cache_dir();
   const std::string path = dir + "/k1_" + key + ".cubin";
   std::vector<char> cubin;
