@@ -415,28 +415,38 @@ sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const float*
 // keep the fastest and remember the choice in the cache directory, keyed by
 // the triple structure, n and the device name.
 // --------------------------------------------------------------------------
+// A short list of tile shapes per family, from sweeps on GB300: small P
+// keeps the whole row in one thread (more prefetch helps); large P splits
+// outputs and inputs over warp groups; the coarse family (a quarter of the
+// rows) adds stencil-slot groups to fill the GPU.
 static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
+  struct S6 {
+    int r, g, i, s, pf;
+  };
+  std::vector<S6> list;
+  if (pr->P <= 48) {
+    if (which == 0)
+      list = {{1, 1, 1, 1, 32}, {1, 1, 1, 1, 16}, {1, 1, 2, 1, 16}, {1, 2, 1, 1, 16}};
+    else
+      list = {{1, 1, 1, 1, 32}, {1, 1, 1, 2, 32}, {1, 1, 1, 4, 16}, {1, 1, 1, 2, 16}, {1, 2, 1, 2, 16}};
+  } else {
+    if (which == 0)
+      list = {{1, 2, 2, 1, 8}, {1, 2, 1, 1, 8}, {1, 3, 2, 1, 8}, {1, 4, 2, 1, 8}};
+    else
+      list = {{1, 2, 2, 1, 8}, {1, 2, 2, 2, 8}, {1, 2, 1, 2, 8}, {1, 4, 2, 1, 8}};
+  }
   std::vector<JitConfig> out;
-  for (int R : {1, 2})
-    for (int H : {1, 2, 3})
-      for (int HI : {1, 2})
-        for (int SG : {1, 2, 4})
-          for (int pf : {8, 32}) {
-            const int per = (pr->P + H - 1) / H, iper = (pr->P + HI - 1) / HI;
-            const int est = R * (per + iper + pf);  // live registers, roughly
-            if (est > 160 || H * HI * SG > 8) continue;
-            if (H * HI > 1 && pr->P <= 24) continue;
-            if (SG > 1 && which == 0 && pr->n > 16384) continue;  // enough rows already
-            JitConfig c;
-            c.rows = R;
-            c.groups = H;
-            c.igroups = HI;
-            c.sgroups = SG;
-            c.prefetch = pf;
-            c.min_blocks = 1;
-            if (jit_smem_bytes(pr, c) > 200 * 1024) continue;
-            out.push_back(c);
-          }
+  for (const S6& e : list) {
+    JitConfig c;
+    c.rows = e.r;
+    c.groups = e.g;
+    c.igroups = e.i;
+    c.sgroups = e.s;
+    c.prefetch = e.pf;
+    c.min_blocks = 1;
+    if (jit_smem_bytes(pr, c) > 200 * 1024) continue;
+    out.push_back(c);
+  }
   if (out.empty()) out.push_back(jit_default_config(pr, which));
   return out;
 }
