@@ -187,7 +187,8 @@ typedef struct {
   double omega;        /* smoother damping; <= 0 = estimate             */
   double inner_rtol;   /* coarse GMRES tolerance; <= 0 = 1e-5           */
   int inner_max;       /* coarse GMRES iteration cap; <= 0 = 100        */
-  int smoother;        /* 0 = RAS (only value accepted)                 */
+  int smoother;        /* 0 = RAS; 1 = learned (needs weights: sg_cnn_init,
+                          sg_cnn_set_weights or sg_train_precond)       */
   int host_loops;      /* 0 (default): each coarse solve is one CUDA graph
                           launch whose restart and Arnoldi loops are
                           conditional WHILE nodes decided on the device;
@@ -229,6 +230,9 @@ sg_status sg_get_amg_level(const sg_problem* prob, int level, int64_t* n, int32_
  *   5 restriction R_0 r               (fine -> coarse)
  *   6 interpolation R_0^T e           (coarse -> fine)
  *   7 RAS local mean solves only      (fine -> fine)
+ *   8 learned smoother S_cnn r        (fine -> fine; after sg_precond_set_smoother)
+ *   9 network only, CNN(r) per mode   (fine -> fine)
+ * Operators 0 and 1 use the smoother currently selected.
  * Coarse blocks have nc rows (sg_precond_info).  R and Z must not overlap. */
 sg_status sg_precond_apply(sg_problem* prob, sg_dtype dtype, int which, const void* R, int64_t ldr,
                            void* Z, int64_t ldz, void* stream);
@@ -244,13 +248,14 @@ typedef struct {
   int max_ir;         /* mode 1: refinement steps cap; <= 0 = 20               */
   double* hist_host;  /* optional host buffer for the residual history         */
   int hist_cap;
+  int no_fallback;    /* 1: keep the learned smoother even when it stagnates   */
 } sg_solve_opts;
 
 typedef struct {
   int outer_it;       /* (F)GMRES iterations (all refinement steps)  */
   int inner_it;       /* coarse GMRES iterations, summed              */
   int ir_steps;       /* refinement corrections applied (mode 1)      */
-  int fallback_used;  /* learned smoother replaced by RAS (0 here)    */
+  int fallback_used;  /* learned smoother replaced by RAS mid-solve    */
   int hist_len;       /* entries written to hist_host                 */
   double relres;      /* ||F - A X|| / ||F|| in FP64 at return       */
   double t_setup, t_solve; /* seconds (t_setup unused here)          */
@@ -264,6 +269,102 @@ typedef struct {
  * when max_it is reached first, SG_ERR_BREAKDOWN on non-finite values. */
 sg_status sg_solve(sg_problem* prob, const double* F_dev, int64_t ldf, double* X_dev, int64_t ldx,
                    const sg_solve_opts* opts, sg_solve_info* info, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned smoother.  The method statement replaces the mean-based local
+ * solve (I (x) A_0)^{-1} inside the smoother by a small convolutional
+ * network applied to the P mode images of the residual; the paper has no
+ * counterpart.  The network: 3x3 convolutions with zero padding, channels
+ * 2 -> 32 -> 32 -> 32 -> 32 -> 1, bias, ReLU after the first four layers;
+ * BF16 weights and activations, FP32 accumulation and FP32 master weights.
+ * Mode image a of a block R (n = (N-1)^2 nodes in mesh order, row-major
+ * (N-1) x (N-1)) enters as channel 0 = r_a / rms(r_a) and channel 1 =
+ * log(a_rr / 4) (a_rr: diagonal of A_0); the output is multiplied by
+ * rms(r_a).  The learned smoother is
+ *     S_cnn r = omega_cnn (G~^{-1} (x) I) CNN(r),
+ * omega_cnn = 1 / rho(S_cnn A) by the same power iteration as RAS.  Inside
+ * sg_solve a solve that stagnates (residual estimate above 0.7 x its value
+ * 10 iterations earlier, or a refinement step that does not halve the
+ * residual) or produces non-finite values switches to RAS for the rest of
+ * the solve and reports fallback_used = 1.
+ * Weights cross the ABI as a flat FP32 host array in this order, for each
+ * layer l = 0..4: W_l[3][3][C_l][C_{l+1}] (tap row, tap column, input
+ * channel, output channel), then b_l[C_{l+1}]; sg_cnn_param_count() values.
+ * ------------------------------------------------------------------------ */
+int64_t sg_cnn_param_count(void);
+
+/* He-normal weights (standard deviation sqrt(2 / (9 C_in))), zero biases,
+ * from a splitmix64 stream and the Box-Muller transform.  Resets Adam. */
+sg_status sg_cnn_init(sg_problem* prob, uint64_t seed, void* stream);
+
+/* Loads (save: sg_cnn_get_weights) the flat weight array; count must equal
+ * sg_cnn_param_count().  Loading resets the Adam moments.  Synchronous. */
+sg_status sg_cnn_set_weights(sg_problem* prob, const float* w_host, int64_t count, void* stream);
+
+/* what = 0: current weights; 1: the gradient of the last training step
+ * (same layout).  Synchronous. */
+sg_status sg_cnn_get_weights(sg_problem* prob, float* w_host, int64_t count, int what, void* stream);
+
+/* Z[:, a] = rms(r_a) CNN(features(r_a)) for nimg FP32 device columns of R
+ * (column a at R + a ldr); rows n..ldz-1 of Z are cleared.  nimg <= 65535.
+ * Allocates activation buffers on first use or growth. */
+sg_status sg_cnn_apply(sg_problem* prob, const float* R_dev, int64_t ldr, float* Z_dev, int64_t ldz, int nimg,
+                       void* stream);
+
+/* One training step on nimg (residual, target) column pairs, the target in
+ * residual units (e.g. A_0^{-1} r):  loss = sum_a ||y_a - z*_a / rms(r_a)||^2
+ * / ||z*_a / rms(r_a)||^2 with y_a the network output; gradients by the
+ * backward convolution kernels; with update != 0 one Adam step (beta1 0.9,
+ * beta2 0.999, eps 1e-8) with learning rate lr.  loss (host, may be NULL)
+ * receives the loss before the update and makes the call synchronous. */
+sg_status sg_cnn_train_step(sg_problem* prob, const float* R_dev, int64_t ldr, const float* Zstar_dev,
+                            int64_t ldz, int nimg, float lr, int update, double* loss, void* stream);
+
+/* Z = A_0^{-1} B for nb FP32 device columns (the training targets): FP64
+ * conjugate gradients preconditioned by one smoothed-aggregation V(1,1)
+ * cycle of A_0 per iteration, all columns together, until every column
+ * has ||b - A_0 z|| <= rtol ||b|| or max_it iterations.  relres_max and its
+ * (host, may be NULL) receive the worst relative residual and the
+ * iterations.  Builds the A_0 hierarchy on first use.  Synchronous.
+ * Errors: SG_ERR_ARG, SG_ERR_NOMEM, SG_ERR_BREAKDOWN (non-finite). */
+sg_status sg_mean_solve(sg_problem* prob, const float* B_dev, int64_t ldb, float* Z_dev, int64_t ldz, int nb,
+                        double rtol, int max_it, double* relres_max, int* its, void* stream);
+
+typedef struct {
+  int n_pairs;        /* training pairs (e.g. 4096)                      */
+  int epochs;         /* passes over the pairs                           */
+  int batch;          /* images per Adam step (e.g. 32)                  */
+  float lr;           /* Adam learning rate (e.g. 1e-3)                  */
+  uint64_t seed;      /* He init, right-hand sides, sampling, batch order */
+  double target_rtol; /* relative residual of the targets; <= 0 = 1e-6   */
+  int keep_weights;   /* 1: continue from the current weights            */
+} sg_train_opts;
+
+typedef struct {
+  int n_pairs, steps;     /* pairs used, Adam steps taken                  */
+  int harvest_solves;     /* plain solves run to collect residuals         */
+  int target_its;         /* CG iterations of the slowest target batch     */
+  double target_relres;   /* worst relative residual of the targets        */
+  double loss_first;      /* mean loss per image, first and last batch     */
+  double loss_last;
+  double omega_cnn;       /* damping chosen for the learned smoother       */
+  double t_harvest, t_targets, t_train;  /* seconds                        */
+} sg_train_info;
+
+/* Trains the learned smoother on the method's own data and selects it:
+ * (1) plain mixed-precision solves (RAS smoother; the load vector, then
+ * seeded Gaussian right-hand sides) record every FP32 smoother input until
+ * 1.5 n_pairs mode images are pooled; n_pairs are drawn uniformly without
+ * replacement; (2) targets z* = A_0^{-1} r by sg_mean_solve; (3) Adam over
+ * `epochs` passes, batches of consecutive pairs in a fresh order each
+ * epoch; (4) omega_cnn estimated, smoother set to 1.  Needs
+ * sg_precond_setup.  Synchronous.  Allocates the pool, the pairs and the
+ * training buffers. */
+sg_status sg_train_precond(sg_problem* prob, const sg_train_opts* opts, sg_train_info* info, void* stream);
+
+/* Selects the smoother of later solves: 0 RAS, 1 learned (needs weights;
+ * omega <= 0 estimates omega_cnn). */
+sg_status sg_precond_set_smoother(sg_problem* prob, int smoother, double omega, void* stream);
 
 /* Multi-vector dot products, the classical Gram-Schmidt step of the
  * Arnoldi process inside FGMRES (Sec. 3):  out[i] = sum_e V_i[e] w[e] for

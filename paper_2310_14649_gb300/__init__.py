@@ -17,13 +17,19 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
-           "sg_mdot_noalloc",
+           "sg_mdot_noalloc", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
+           "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
+           "sg_train_precond", "sg_precond_set_smoother", "cnn_flatten", "cnn_unflatten",
            "SgError", "SG_F32", "SG_F64", "PC_TWOLEVEL", "PC_SMOOTH", "PC_COARSE", "PC_AMG",
-           "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL"]
+           "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL", "PC_LEARNED",
+           "PC_NETWORK"]
 
 # operators of sg_precond_apply
 (PC_TWOLEVEL, PC_SMOOTH, PC_COARSE, PC_AMG, PC_COARSE_APPLY, PC_RESTRICT, PC_INTERP,
- PC_RAS_LOCAL) = range(8)
+ PC_RAS_LOCAL, PC_LEARNED, PC_NETWORK) = range(10)
+
+# channels of the learned smoother's convolution layers
+CNN_CHANNELS = (2, 32, 32, 32, 32, 1)
 
 
 class Problem:
@@ -186,7 +192,7 @@ def sg_precond_apply(prob, which, R, Z, stream=None):
 
 
 def sg_solve(prob, X, F=None, rtol=1e-8, max_it=500, restart=30, mode=0, inner_rtol=0.0, max_ir=0,
-             hist_cap=256, stream=None, allow_not_converged=False):
+             hist_cap=256, stream=None, allow_not_converged=False, fallback=True):
     """Solve sum_k A_k X G_k^T = F (F None: the load vector).  X (FP64, [P, ld])
     holds the initial guess and receives the solution.  Returns a dict of
     the solve info (and the residual history)."""
@@ -196,7 +202,8 @@ def sg_solve(prob, X, F=None, rtol=1e-8, max_it=500, restart=30, mode=0, inner_r
         raise TypeError("sg_solve works on FP64 blocks")
     hist = np.zeros(max(hist_cap, 1), dtype=np.float64)
     opts = _lib.SolveOpts(rtol, max_it, restart, mode, inner_rtol, max_ir,
-                          hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), hist_cap)
+                          hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), hist_cap,
+                          0 if fallback else 1)
     info = _lib.SolveInfo()
     allow = (0, 1) if allow_not_converged else (0,)
     st = call("sg_solve", prob.handle, dev_ptr(F) if F is not None else None,
@@ -267,3 +274,102 @@ def sg_mdot_noalloc(V, w, out, stream=None):
         raise TypeError("V, w of one dtype (row-contiguous V), out float64")
     call("sg_mdot_noalloc", _dtype_code(V), dev_ptr(V), V.stride(0), V.shape[0], dev_ptr(w), V.shape[1],
          dev_ptr(out), stream_handle(stream))
+
+
+# ---------------------------------------------------------------------------
+# learned smoother
+# ---------------------------------------------------------------------------
+def sg_cnn_param_count():
+    return int(_lib.lib().sg_cnn_param_count())
+
+
+def cnn_flatten(params):
+    """[(W [3,3,Cin,Cout], b [Cout])] per layer -> the flat FP32 array of the ABI."""
+    parts = []
+    for W, b in params:
+        parts.append(np.asarray(W, dtype=np.float32).ravel())
+        parts.append(np.asarray(b, dtype=np.float32).ravel())
+    return np.ascontiguousarray(np.concatenate(parts), dtype=np.float32)
+
+
+def cnn_unflatten(flat):
+    """Inverse of cnn_flatten (float64 arrays)."""
+    out, off = [], 0
+    for l in range(5):
+        ci, co = CNN_CHANNELS[l], CNN_CHANNELS[l + 1]
+        W = np.asarray(flat[off:off + 9 * ci * co], dtype=np.float64).reshape(3, 3, ci, co)
+        off += 9 * ci * co
+        b = np.asarray(flat[off:off + co], dtype=np.float64)
+        off += co
+        out.append((W, b))
+    return out
+
+
+def sg_cnn_init(prob, seed=0, stream=None):
+    call("sg_cnn_init", prob.handle, seed, stream_handle(stream))
+
+
+def sg_cnn_set_weights(prob, params, stream=None):
+    """params: flat FP32 array or [(W, b)] per layer."""
+    flat = params if isinstance(params, np.ndarray) else cnn_flatten(params)
+    flat = np.ascontiguousarray(flat, dtype=np.float32)
+    call("sg_cnn_set_weights", prob.handle, _lib.ptr(flat, ctypes.c_float), flat.size, stream_handle(stream))
+
+
+def sg_cnn_get_weights(prob, gradient=False, stream=None):
+    """Flat FP32 weights (or the last step's gradient)."""
+    flat = np.zeros(sg_cnn_param_count(), dtype=np.float32)
+    call("sg_cnn_get_weights", prob.handle, _lib.ptr(flat, ctypes.c_float), flat.size, 1 if gradient else 0,
+         stream_handle(stream))
+    return flat
+
+
+def _check_images(prob, t, name):
+    import torch
+    if not t.is_cuda or t.dtype != torch.float32 or t.dim() != 2 or t.stride(1) != 1 or t.shape[1] < prob.n:
+        raise ValueError("%s must be a float32 CUDA tensor [nimg, ld >= n]" % name)
+
+
+def sg_cnn_apply(prob, R, Z, stream=None):
+    """Z[a] = rms(R[a]) CNN(features(R[a])) for every row a of R (Z rows
+    are written up to their stride: Z must be contiguous)."""
+    _check_images(prob, R, "R")
+    _check_images(prob, Z, "Z")
+    if not Z.is_contiguous():
+        raise ValueError("Z must be contiguous")
+    call("sg_cnn_apply", prob.handle, dev_ptr(R), R.stride(0), dev_ptr(Z), Z.stride(0), R.shape[0],
+         stream_handle(stream))
+
+
+def sg_cnn_train_step(prob, R, Zstar, lr=1e-3, update=True, stream=None):
+    """One step on (R[a], Zstar[a]) pairs; returns the loss before the update."""
+    _check_images(prob, R, "R")
+    _check_images(prob, Zstar, "Zstar")
+    loss = ctypes.c_double()
+    call("sg_cnn_train_step", prob.handle, dev_ptr(R), R.stride(0), dev_ptr(Zstar), Zstar.stride(0), R.shape[0],
+         lr, 1 if update else 0, ctypes.byref(loss), stream_handle(stream))
+    return loss.value
+
+
+def sg_mean_solve(prob, B, Z, rtol=1e-6, max_it=500, stream=None):
+    """Z[a] = A_0^{-1} B[a] (float32 CUDA rows); returns (worst relres, its)."""
+    _check_images(prob, B, "B")
+    _check_images(prob, Z, "Z")
+    rel, its = ctypes.c_double(), ctypes.c_int()
+    call("sg_mean_solve", prob.handle, dev_ptr(B), B.stride(0), dev_ptr(Z), Z.stride(0), B.shape[0], rtol,
+         max_it, ctypes.byref(rel), ctypes.byref(its), stream_handle(stream))
+    return rel.value, its.value
+
+
+def sg_train_precond(prob, n_pairs=4096, epochs=4, batch=32, lr=1e-3, seed=0, target_rtol=1e-6,
+                     keep_weights=False, stream=None):
+    """Harvest residuals, build A_0^{-1} targets, train, select the learned smoother."""
+    opts = _lib.TrainOpts(n_pairs, epochs, batch, lr, seed, target_rtol, 1 if keep_weights else 0)
+    info = _lib.TrainInfo()
+    call("sg_train_precond", prob.handle, ctypes.byref(opts), ctypes.byref(info), stream_handle(stream))
+    return {f: getattr(info, f) for f, _ in _lib.TrainInfo._fields_}
+
+
+def sg_precond_set_smoother(prob, smoother, omega=0.0, stream=None):
+    """0 RAS, 1 learned (omega <= 0: estimate)."""
+    call("sg_precond_set_smoother", prob.handle, smoother, omega, stream_handle(stream))

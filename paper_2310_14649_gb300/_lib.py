@@ -45,13 +45,28 @@ class PrecondOpts(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("restart", ctypes.c_int),
                 ("mode", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_ir", ctypes.c_int),
-                ("hist_host", ctypes.POINTER(ctypes.c_double)), ("hist_cap", ctypes.c_int)]
+                ("hist_host", ctypes.POINTER(ctypes.c_double)), ("hist_cap", ctypes.c_int),
+                ("no_fallback", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("outer_it", ctypes.c_int), ("inner_it", ctypes.c_int), ("ir_steps", ctypes.c_int),
                 ("fallback_used", ctypes.c_int), ("hist_len", ctypes.c_int),
                 ("relres", ctypes.c_double), ("t_setup", ctypes.c_double), ("t_solve", ctypes.c_double)]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
+                ("lr", ctypes.c_float), ("seed", ctypes.c_uint64), ("target_rtol", ctypes.c_double),
+                ("keep_weights", ctypes.c_int)]
+
+
+class TrainInfo(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int), ("steps", ctypes.c_int), ("harvest_solves", ctypes.c_int),
+                ("target_its", ctypes.c_int), ("target_relres", ctypes.c_double),
+                ("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double),
+                ("omega_cnn", ctypes.c_double), ("t_harvest", ctypes.c_double),
+                ("t_targets", ctypes.c_double), ("t_train", ctypes.c_double)]
 
 
 _lib = None
@@ -87,6 +102,20 @@ SIGNATURES = {
     "sg_apply_info": [vp, ctypes.c_int, P_i32, P_f64],
     "sg_launch_count": [P_i64],
     "sg_profile_read": [vp, ctypes.c_int, P_i64, P_f64],
+    "sg_cnn_init": [vp, ctypes.c_uint64, vp],
+    "sg_cnn_set_weights": [vp, ctypes.POINTER(ctypes.c_float), i64, vp],
+    "sg_cnn_get_weights": [vp, ctypes.POINTER(ctypes.c_float), i64, ctypes.c_int, vp],
+    "sg_cnn_apply": [vp, vp, i64, vp, i64, ctypes.c_int, vp],
+    "sg_cnn_train_step": [vp, vp, i64, vp, i64, ctypes.c_int, ctypes.c_float, ctypes.c_int, P_f64, vp],
+    "sg_mean_solve": [vp, vp, i64, vp, i64, ctypes.c_int, f64, ctypes.c_int, P_f64,
+                      ctypes.POINTER(ctypes.c_int), vp],
+    "sg_train_precond": [vp, ctypes.POINTER(TrainOpts), ctypes.POINTER(TrainInfo), vp],
+    "sg_precond_set_smoother": [vp, ctypes.c_int, f64, vp],
+}
+
+# functions whose result is not an sg_status: name -> (argtypes, restype)
+VALUE_FUNCTIONS = {
+    "sg_cnn_param_count": ([], ctypes.c_int64),
 }
 
 
@@ -101,6 +130,10 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        for name, (args, res) in VALUE_FUNCTIONS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
         L.sg_last_error.argtypes = []
         L.sg_last_error.restype = ctypes.c_char_p
         _lib = L

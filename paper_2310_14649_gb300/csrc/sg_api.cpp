@@ -67,6 +67,7 @@ sg_status sg_setup(const sg_mesh_desc* mesh, const sg_kl_desc* kl, int p_out, in
 sg_status sg_destroy(sg_problem* pr) {
   if (!pr) return SG_OK;
   solver_free(pr);
+  cnn_free(pr);
   jit_free(pr, 0);
   jit_free(pr, 1);
   pr->mdot_partial.free_();

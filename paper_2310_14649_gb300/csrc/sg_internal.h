@@ -45,6 +45,24 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 struct DevBuf {
   void* ptr = nullptr;
   size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : ptr(o.ptr), bytes(o.bytes) {
+    o.ptr = nullptr;
+    o.bytes = 0;
+  }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      free_();
+      ptr = o.ptr;
+      bytes = o.bytes;
+      o.ptr = nullptr;
+      o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { free_(); }
   sg_status alloc(size_t nbytes);
   void free_();
   template <typename T> T* as() const { return static_cast<T*>(ptr); }
@@ -65,6 +83,8 @@ struct Ell {
 
 struct SolverState;
 void solver_free(sg_problem* pr);
+struct Cnn;
+void cnn_free(sg_problem* pr);
 
 // Triple products re-ordered by output mode a, then k, then b, split into
 // chunks of input terms [c*kc, (c+1)*kc) for the shared-memory apply.
@@ -132,6 +152,7 @@ struct sg_problem {
   sg::TripleTables tri;
   int64_t ld = 0;                      // internal leading dimension of blocks
   sg::SolverState* solver = nullptr;   // preconditioner + solver workspaces
+  sg::Cnn* cnn = nullptr;              // learned smoother network
   sg::Profiler prof;
   sg::JitApply* jit[2] = {nullptr, nullptr};  // specialised FP32 apply: [0] fine, [1] coarse
   sg::JitConfig jit_cfg[2];

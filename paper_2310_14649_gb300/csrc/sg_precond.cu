@@ -298,27 +298,27 @@ sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStr
 // One V(1,1) cycle with l1-Jacobi on every column, from a zero guess.
 // Level buffers: b (rhs), x (solution), t (temporary), each [P][ld_l].
 template <typename T>
-sg_status amg_vcycle(const Precond& pc, AmgWork<T>& w, int P, cudaStream_t st) {
-  const int nl = int(pc.amg.size());
+sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st) {
+  const int nl = int(H.size());
   for (int l = 0; l < nl - 1; ++l) {
-    const AmgLevel& L = pc.amg[l];
+    const AmgLevel& L = H[l];
     dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
     k_diag<T><<<g, 128, 0, st>>>(L.n, dv<T>(L.dinv64, L.dinv32), w.b[l], L.ld, w.x[l], L.ld, 0); note_launch();
     SG_CUDA(cudaGetLastError());
     SG_TRY(spmm<T>(L.A, w.x[l], L.ld, w.b[l], L.ld, w.t[l], L.ld, P, 2, st));
-    SG_TRY(spmm<T>(L.R, w.t[l], L.ld, nullptr, 0, w.b[l + 1], pc.amg[l + 1].ld, P, 0, st));
+    SG_TRY(spmm<T>(L.R, w.t[l], L.ld, nullptr, 0, w.b[l + 1], H[l + 1].ld, P, 0, st));
   }
   {
-    const AmgLevel& L = pc.amg[nl - 1];
+    const AmgLevel& L = H[nl - 1];
     dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
-    k_dense_solve<T><<<g, 128, 0, st>>>(int(L.n), pc.coarsest_inv64.as<double>(), w.b[nl - 1], L.ld, w.x[nl - 1],
+    k_dense_solve<T><<<g, 128, 0, st>>>(int(L.n), H.coarsest_inv64.as<double>(), w.b[nl - 1], L.ld, w.x[nl - 1],
                                         L.ld); note_launch();
     SG_CUDA(cudaGetLastError());
   }
   for (int l = nl - 2; l >= 0; --l) {
-    const AmgLevel& L = pc.amg[l];
+    const AmgLevel& L = H[l];
     dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
-    SG_TRY(spmm<T>(L.Pm, w.x[l + 1], pc.amg[l + 1].ld, nullptr, 0, w.x[l], L.ld, P, 1, st));
+    SG_TRY(spmm<T>(L.Pm, w.x[l + 1], H[l + 1].ld, nullptr, 0, w.x[l], L.ld, P, 1, st));
     SG_TRY(spmm<T>(L.A, w.x[l], L.ld, w.b[l], L.ld, w.t[l], L.ld, P, 2, st));
     k_diag<T><<<g, 128, 0, st>>>(L.n, dv<T>(L.dinv64, L.dinv32), w.t[l], L.ld, w.x[l], L.ld, 1); note_launch();
     SG_CUDA(cudaGetLastError());
@@ -380,7 +380,7 @@ sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w) {
                              cudaStream_t);                                                               \
   template sg_status ras_apply<T>(const Precond&, int64_t, int, const T*, int64_t, T*, cudaStream_t, bool);        \
   template sg_status node_transform<T>(T*, int64_t, int64_t, int, const T*, cudaStream_t);                \
-  template sg_status amg_vcycle<T>(const Precond&, AmgWork<T>&, int, cudaStream_t);
+  template sg_status amg_vcycle<T>(const AmgHier&, AmgWork<T>&, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

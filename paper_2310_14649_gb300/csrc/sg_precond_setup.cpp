@@ -465,8 +465,8 @@ static int32_t aggregate(const HCsr& A, std::vector<int32_t>& agg) {
   return na;
 }
 
-static sg_status setup_amg(Precond& pc, const HCsr& A0c) {
-  pc.amg.clear();
+static sg_status setup_amg(AmgHier& H, const HCsr& A0c) {
+  H.lev.clear();
   HCsr A = A0c;
   std::vector<HCsr> As, Ps;
   std::vector<std::vector<int32_t>> aggs;
@@ -536,9 +536,9 @@ static sg_status setup_amg(Precond& pc, const HCsr& A0c) {
     aggs.push_back(agg);
     A = Anext;
   }
-  pc.amg.resize(As.size());
+  H.lev.resize(As.size());
   for (size_t l = 0; l < As.size(); ++l) {
-    AmgLevel& L = pc.amg[l];
+    AmgLevel& L = H.lev[l];
     L.n = As[l].n;
     L.ld = round_up(L.n, 32);
     SG_TRY(L.A.upload(As[l].n, As[l].m, As[l].rp, As[l].ci, As[l].v));
@@ -577,9 +577,19 @@ static sg_status setup_amg(Precond& pc, const HCsr& A0c) {
       for (int k = std::max(i, j); k < nc; ++k) s += Li[size_t(k) * nc + i] * Li[size_t(k) * nc + j];
       inv[size_t(i) * nc + j] = s;
     }
-  SG_TRY(pc.coarsest_inv64.alloc(inv.size() * 8));
-  SG_CUDA(cudaMemcpy(pc.coarsest_inv64.ptr, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice));
+  SG_TRY(H.coarsest_inv64.alloc(inv.size() * 8));
+  SG_CUDA(cudaMemcpy(H.coarsest_inv64.ptr, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice));
   return SG_OK;
+}
+
+sg_status amg_setup_fine(const sg_problem* pr, AmgHier& h) {
+  HCsr A;
+  A.n = pr->n;
+  A.m = pr->n;
+  A.rp = pr->rowptr;
+  A.ci = pr->colidx;
+  A.v = pr->a0;
+  return setup_amg(h, A);
 }
 
 sg_status precond_setup_host(sg_problem* pr, Precond& pc) {
@@ -587,7 +597,7 @@ sg_status precond_setup_host(sg_problem* pr, Precond& pc) {
   CoarsePlan plan;
   HCsr Ac0;
   SG_TRY(setup_coarse(pr, pc, plan, Ac0));
-  SG_TRY(setup_amg(pc, Ac0));
+  SG_TRY(setup_amg(pc.amg, Ac0));
   SG_TRY(precond_setup_coarse_plan(pr, pc, plan));
   return SG_OK;
 }

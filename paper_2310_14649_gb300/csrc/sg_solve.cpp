@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <memory>
 
+#include "sg_cnn.h"
 #include "sg_kernels.h"
 
 namespace sg {
@@ -87,7 +88,14 @@ struct GmresResult {
   int its = 0;
   double est = 0.0;     // last residual estimate (absolute)
   bool converged = false;
+  bool stalled = false; // stopped by the stagnation test
 };
+
+// stagnation test of a solve with the learned smoother: after kStallIts
+// iterations the residual estimate must have dropped below kStallRatio
+// times its value kStallIts iterations earlier
+constexpr int kStallIts = 10;
+constexpr double kStallRatio = 0.7;
 
 // Right-preconditioned restarted GMRES (flexible when W.flexible: the
 // preconditioned vectors are kept and x += Z y).  Stops when the residual
@@ -95,9 +103,10 @@ struct GmresResult {
 template <typename T>
 static sg_status gmres_run(KrylovWork<T>& W, const Op<T>& A, const Op<T>& M, const T* F, T* x, bool x_zero,
                            double tol_abs, int max_it, GmresResult& res, std::vector<double>* hist, double hist_scale,
-                           cudaStream_t st, bool trust_estimate) {
+                           cudaStream_t st, bool trust_estimate, bool stall_test = false) {
   const int64_t len = W.len;
   res = GmresResult{};
+  std::vector<double> ests;
   bool first = true;
   for (;;) {
     // r0 = F - A x
@@ -154,6 +163,14 @@ static sg_status gmres_run(KrylovWork<T>& W, const Op<T>& A, const Op<T>& M, con
         stop = true;
         break;
       }
+      if (stall_test) {
+        ests.push_back(est);
+        const size_t q = ests.size();
+        if (q > size_t(kStallIts) && est > kStallRatio * ests[q - 1 - kStallIts]) {
+          res.stalled = true;
+          break;
+        }
+      }
       if (res.its >= max_it) break;
     }
     SG_TRY(gmres_backsolve(W.s, W.m, k, st));
@@ -175,6 +192,7 @@ static sg_status gmres_run(KrylovWork<T>& W, const Op<T>& A, const Op<T>& M, con
       res.converged = true;
       return SG_OK;
     }
+    if (res.stalled) return SG_OK;
     if (res.its >= max_it && !stop) {
       // report the true residual of the final iterate
       SG_TRY(A(x, dp<T>(W.w)));
@@ -267,7 +285,7 @@ struct SolverCtx {
     const AmgLevel& L0 = pc->amg[0];
     SG_CUDA(cudaMemcpy2DAsync(aw.b[0], L0.ld * sizeof(T), B, ldc * sizeof(T), pc->co.nc * sizeof(T), pr->P,
                               cudaMemcpyDeviceToDevice, st));
-    SG_TRY(amg_vcycle<T>(*pc, aw, pr->P, st));
+    SG_TRY(amg_vcycle<T>(pc->amg, aw, pr->P, st));
     SG_CUDA(cudaMemcpy2DAsync(X, ldc * sizeof(T), aw.x[0], L0.ld * sizeof(T), pc->co.nc * sizeof(T), pr->P,
                               cudaMemcpyDeviceToDevice, st));
     return SG_OK;
@@ -276,7 +294,7 @@ struct SolverCtx {
   // V-cycle, copy out to `out` (coarse ld), Kronecker factor
   sg_status coarse_pc_from_b0(T* out, cudaStream_t st) {
     const AmgLevel& L0 = pc->amg[0];
-    SG_TRY(amg_vcycle<T>(*pc, aw, pr->P, st));
+    SG_TRY(amg_vcycle<T>(pc->amg, aw, pr->P, st));
     SG_CUDA(cudaMemcpy2DAsync(out, ldc * sizeof(T), aw.x[0], L0.ld * sizeof(T), pc->co.nc * sizeof(T), pr->P,
                               cudaMemcpyDeviceToDevice, st));
     return node_transform<T>(out, ldc, pc->co.nc, pr->P, dp_sel<T>(pc->gkron64, pc->gkron32), st);
@@ -433,8 +451,18 @@ struct SolverCtx {
     SG_TRY(spmm<T>(pc->co.RT, dp<T>(ec), ldc, nullptr, 0, Z, ld, pr->P, 1, st));
     return SG_OK;
   }
-  // smoother S r = omega G~^{-1} RAS(r)
-  sg_status smooth(const T* R, T* Z, cudaStream_t st) { return ras_apply<T>(*pc, pr->n, pr->P, R, ld, Z, st, true); }
+  // smoother S r = omega G~^{-1} RAS(r), or omega_cnn G~^{-1} CNN(r) while
+  // the learned smoother is active; FP32 inputs are recorded while a
+  // harvest for training is on
+  sg_status smooth(const T* R, T* Z, cudaStream_t st) {
+    Harvest& h = pc->harvest;
+    if (sizeof(T) == 4 && h.on && h.count < h.cap) {
+      SG_CUDA(cudaMemcpyAsync(dp<float>(h.pool) + h.count * len, R, len * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      ++h.count;
+    }
+    if (pc->use_cnn) return cnn_smooth<T>(pr, *pc, R, ld, Z, true, st);
+    return ras_apply<T>(*pc, pr->n, pr->P, R, ld, Z, st, true);
+  }
   // two-level cycle: z = S r; z += Q (r - A z); z += S (r - A z)
   sg_status twolevel(const T* R, T* Z, cudaStream_t st) {
     SG_TRY(smooth(R, Z, st));
@@ -494,27 +522,26 @@ static sg_status get_ctx(sg_problem* pr, SolverCtx<T>*& out) {
   return SG_OK;
 }
 
-// upload omega * G~^{-1}
-static sg_status upload_gtinv(sg_problem* pr, Precond& pc, const std::vector<double>& ginv) {
-  const int P = pr->P;
-  std::vector<double> m64(size_t(P) * P);
-  std::vector<float> m32(size_t(P) * P);
+// d = omega * G~^{-1} in FP64 and FP32
+static sg_status upload_scaled(const std::vector<double>& ginv, double omega, DevBuf& d64, DevBuf& d32) {
+  std::vector<double> m64(ginv.size());
+  std::vector<float> m32(ginv.size());
   for (size_t e = 0; e < m64.size(); ++e) {
-    m64[e] = pc.omega * ginv[e];
+    m64[e] = omega * ginv[e];
     m32[e] = float(m64[e]);
   }
-  if (!pc.gkron64.ptr) {
-    std::vector<float> k32(ginv.begin(), ginv.end());
-    SG_TRY(pc.gkron64.alloc(ginv.size() * 8));
-    SG_TRY(pc.gkron32.alloc(ginv.size() * 4));
-    SG_CUDA(cudaMemcpy(pc.gkron64.ptr, ginv.data(), ginv.size() * 8, cudaMemcpyHostToDevice));
-    SG_CUDA(cudaMemcpy(pc.gkron32.ptr, k32.data(), k32.size() * 4, cudaMemcpyHostToDevice));
-  }
-  if (!pc.gtinv64.ptr) SG_TRY(pc.gtinv64.alloc(m64.size() * 8));
-  if (!pc.gtinv32.ptr) SG_TRY(pc.gtinv32.alloc(m32.size() * 4));
-  SG_CUDA(cudaMemcpy(pc.gtinv64.ptr, m64.data(), m64.size() * 8, cudaMemcpyHostToDevice));
-  SG_CUDA(cudaMemcpy(pc.gtinv32.ptr, m32.data(), m32.size() * 4, cudaMemcpyHostToDevice));
+  if (!d64.ptr) SG_TRY(d64.alloc(m64.size() * 8));
+  if (!d32.ptr) SG_TRY(d32.alloc(m32.size() * 4));
+  SG_CUDA(cudaMemcpy(d64.ptr, m64.data(), m64.size() * 8, cudaMemcpyHostToDevice));
+  SG_CUDA(cudaMemcpy(d32.ptr, m32.data(), m32.size() * 4, cudaMemcpyHostToDevice));
   return SG_OK;
+}
+
+// upload omega * G~^{-1} (smoother) and G~^{-1} (coarse preconditioner)
+static sg_status upload_gtinv(sg_problem*, Precond& pc, const std::vector<double>& ginv) {
+  pc.ginv = ginv;
+  if (!pc.gkron64.ptr) SG_TRY(upload_scaled(ginv, 1.0, pc.gkron64, pc.gkron32));
+  return upload_scaled(ginv, pc.omega, pc.gtinv64, pc.gtinv32);
 }
 
 // Kronecker stochastic factor G~ = sum_k w_k G_k, w_k = <A_k, A_0>_F / <A_0, A_0>_F,
@@ -562,9 +589,9 @@ static sg_status kronecker_factor(sg_problem* pr, Precond& pc, std::vector<doubl
   return SG_OK;
 }
 
-// omega = 1 / rho(S A) by 20 power iterations (FP32) from the seed-free
-// start X[a][r] = 1 + (r + a) mod 3.
-static sg_status estimate_omega(sg_problem* pr, SolverState& S, cudaStream_t st) {
+// rho(S A) by 20 power iterations (FP32) from the seed-free start
+// X[a][r] = 1 + (r + a) mod 3, with the smoother currently selected
+static sg_status estimate_rho(sg_problem* pr, cudaStream_t st, double& rho) {
   SolverCtx<float>* c = nullptr;
   SG_TRY(get_ctx<float>(pr, c));
   const int P = pr->P;
@@ -587,12 +614,42 @@ static sg_status estimate_omega(sg_problem* pr, SolverState& S, cudaStream_t st)
   }
   SG_CUDA(cudaMemcpyAsync(c->fine.host + 6, nrm, 8, cudaMemcpyDeviceToHost, st));
   SG_CUDA(cudaStreamSynchronize(st));
-  const double rho = std::sqrt(c->fine.host[6]);
+  rho = std::sqrt(c->fine.host[6]);
   if (!(rho > 0.0) || !std::isfinite(rho)) {
     set_error("omega estimate failed");
     return SG_ERR_BREAKDOWN;
   }
+  return SG_OK;
+}
+
+// omega = 1 / rho(S A) for the RAS smoother
+static sg_status estimate_omega(sg_problem* pr, SolverState& S, cudaStream_t st) {
+  double rho = 0.0;
+  SG_TRY(estimate_rho(pr, st, rho));
   S.pc.omega = 1.0 / rho;
+  return SG_OK;
+}
+
+Precond& precond_of(sg_problem* pr) { return pr->solver->pc; }
+
+// Selects the learned smoother for later solves with damping omega_cnn
+// (= 1 / rho(S_cnn A) by the same power iteration when omega <= 0).
+sg_status learned_smoother_enable(sg_problem* pr, double omega, cudaStream_t st) {
+  Precond& pc = pr->solver->pc;
+  pc.omega_cnn = 1.0;
+  SG_TRY(upload_scaled(pc.ginv, 1.0, pc.gtcnn64, pc.gtcnn32));
+  if (omega <= 0) {
+    const bool prev = pc.use_cnn;
+    pc.use_cnn = true;
+    double rho = 0.0;
+    sg_status s = estimate_rho(pr, st, rho);
+    pc.use_cnn = prev;
+    SG_TRY(s);
+    omega = 1.0 / rho;
+  }
+  pc.omega_cnn = omega;
+  SG_TRY(upload_scaled(pc.ginv, omega, pc.gtcnn64, pc.gtcnn32));
+  pc.smoother = 1;
   return SG_OK;
 }
 
@@ -612,6 +669,18 @@ static sg_status precond_apply_t(sg_problem* pr, int which, const T* Rin, int64_
   const int64_t nin = coarse_in ? S.pc.co.nc : pr->n, ldin = coarse_in ? c->ldc : c->ld;
   const int64_t nout = coarse_out ? S.pc.co.nc : pr->n, ldout = coarse_out ? c->ldc : c->ld;
   SG_ARG(ldr >= nin && ldz >= nout, "sg_precond_apply: leading dimension too small");
+  const bool learned = which == 8 || which == 9;
+  if (learned) {
+    SG_ARG(pr->cnn && pr->cnn->trained, "sg_precond_apply: the learned smoother has no weights");
+    SG_ARG(which == 9 || S.pc.gtcnn64.ptr, "sg_precond_apply: learned smoother not enabled");
+  }
+  const bool prev_cnn = S.pc.use_cnn;
+  S.pc.use_cnn = learned || (S.pc.smoother == 1 && pr->cnn && pr->cnn->trained);
+  struct Restore {
+    Precond& pc;
+    bool v;
+    ~Restore() { pc.use_cnn = v; }
+  } restore{S.pc, prev_cnn};
   T* in = coarse_in ? dp<T>(c->coarse.tmp) : dp<T>(c->fine.tmp);
   T* out = coarse_out ? dp<T>(c->coarse.tmp2) : dp<T>(c->fine.tmp2);
   SG_CUDA(cudaMemsetAsync(in, 0, size_t(P) * ldin * sizeof(T), st));
@@ -627,6 +696,8 @@ static sg_status precond_apply_t(sg_problem* pr, int which, const T* Rin, int64_
     case 5: SG_TRY(spmm<T>(S.pc.co.R, in, c->ld, nullptr, 0, out, c->ldc, P, 0, st)); break;
     case 6: SG_TRY(spmm<T>(S.pc.co.RT, in, c->ldc, nullptr, 0, out, c->ld, P, 0, st)); break;
     case 7: SG_TRY(ras_apply<T>(S.pc, pr->n, P, in, c->ld, out, st, false)); break;
+    case 8: SG_TRY(c->smooth(in, out, st)); break;
+    case 9: SG_TRY(cnn_smooth<T>(pr, S.pc, in, c->ld, out, false, st)); break;
     default: set_error("sg_precond_apply: unknown operator"); return SG_ERR_ARG;
   }
   SG_CUDA(cudaMemcpy2DAsync(Zout, ldz * sizeof(T), out, ldout * sizeof(T), nout * sizeof(T), P,
@@ -643,7 +714,9 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   SG_ARG(o->sx >= 1 && o->sy >= 1 && o->sx <= pr->N - 1 && o->sy <= pr->N - 1,
          "sg_precond_setup: subdomain counts must be in [1, N-1]");
   SG_ARG(o->overlap >= 0 && o->overlap <= 8, "sg_precond_setup: overlap must be in [0, 8]");
-  SG_ARG(o->smoother == 0, "sg_precond_setup: only the RAS smoother (0) is available");
+  SG_ARG(o->smoother == 0 || o->smoother == 1, "sg_precond_setup: smoother must be 0 (RAS) or 1 (learned)");
+  SG_ARG(o->smoother == 0 || (pr->cnn && pr->cnn->trained),
+         "sg_precond_setup: the learned smoother needs trained or loaded weights");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   solver_free(pr);
   pr->solver = new SolverState();
@@ -665,6 +738,7 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   if (s == SG_OK && o->omega <= 0) s = estimate_omega(pr, S, st);
   if (s == SG_OK && o->omega > 0) pc.omega = o->omega;
   if (s == SG_OK) s = upload_gtinv(pr, pc, ginv);
+  if (s == SG_OK && o->smoother == 1) s = learned_smoother_enable(pr, 0.0, st);
   if (s != SG_OK) {
     solver_free(pr);
     return s;
@@ -781,6 +855,12 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
   const double nF = std::sqrt(S.host[0]);
   sg_solve_info inf{};
   std::vector<double> hist;
+  S.pc.use_cnn = S.pc.smoother == 1 && pr->cnn && pr->cnn->trained;
+  const bool stall_test = S.pc.use_cnn && !o->no_fallback;
+  struct ClearCnn {
+    Precond& pc;
+    ~ClearCnn() { pc.use_cnn = false; }
+  } clear_cnn{S.pc};
   S.pc.inner_its_total = 0;
   S.pc.inner_calls = 0;
   const int zero = 0;
@@ -792,10 +872,20 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
   } else if (o->mode == 0) {
     Op<double> A = [&](const double* x, double* y) { return c64->apply_fine(x, y, nullptr, st); };
     Op<double> M = [&](const double* r, double* z) { return c64->twolevel(r, z, st); };
-    GmresResult res;
-    SG_TRY(gmres_run<double>(c64->fine, A, M, F64, x64, false, o->rtol * nF, o->max_it, res, &hist, 1.0 / nF, st,
-                             false));
-    inf.outer_it = res.its;
+    for (;;) {
+      GmresResult res;
+      const sg_status gs = gmres_run<double>(c64->fine, A, M, F64, x64, false, o->rtol * nF, o->max_it - inf.outer_it,
+                                             res, &hist, 1.0 / nF, st, false, stall_test && S.pc.use_cnn);
+      inf.outer_it += res.its;
+      // learned smoother: non-finite values or stagnation switch to RAS
+      if (stall_test && S.pc.use_cnn && (gs == SG_ERR_BREAKDOWN || res.stalled) && inf.outer_it < o->max_it) {
+        S.pc.use_cnn = false;
+        inf.fallback_used = 1;
+        continue;
+      }
+      SG_TRY(gs);
+      break;
+    }
   } else {
     SolverCtx<float>* c32 = nullptr;
     SG_TRY(get_ctx<float>(pr, c32));
@@ -807,6 +897,7 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
     Op<float> M = [&](const float* r, float* z) { return c32->twolevel(r, z, st); };
     const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
     const int max_ir = o->max_ir > 0 ? o->max_ir : 20;
+    double rr_prev = 0.0;
     for (int ir = 0;; ++ir) {
       SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
       SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 1, dp<double>(c64->fine.partial),
@@ -820,6 +911,13 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
       }
       hist.push_back(rr);
       if (rr <= o->rtol || ir >= max_ir || inf.outer_it >= o->max_it) break;
+      // learned smoother: a refinement step that did not halve the residual
+      // switches to RAS
+      if (stall_test && S.pc.use_cnn && ir > 0 && rr > 0.5 * rr_prev) {
+        S.pc.use_cnn = false;
+        inf.fallback_used = 1;
+      }
+      rr_prev = rr;
       inf.ir_steps++;
       SG_TRY((vec_convert<double, float>(dp<double>(S.r64), r32, len, nullptr, scal + 1, st)));
       SG_CUDA(cudaMemsetAsync(d32, 0, len * 4, st));
@@ -827,9 +925,15 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
       // the FP32 correction solve stops on its Arnoldi estimate: its true FP32
       // residual cannot fall much below u_32 * cond(A), the FP64 loop
       // measures the real progress
-      SG_TRY(gmres_run<float>(c32->fine, A, M, r32, d32, true, inner, o->max_it - inf.outer_it, res, nullptr, 1.0,
-                              st, true));
+      const sg_status gs = gmres_run<float>(c32->fine, A, M, r32, d32, true, inner, o->max_it - inf.outer_it, res,
+                                            nullptr, 1.0, st, true, stall_test && S.pc.use_cnn);
       inf.outer_it += res.its;
+      if (stall_test && S.pc.use_cnn && (gs == SG_ERR_BREAKDOWN || res.stalled)) {
+        S.pc.use_cnn = false;
+        inf.fallback_used = 1;
+        if (gs != SG_OK) continue;  // the correction is not usable
+      }
+      SG_TRY(gs);
       SG_TRY(vec_add_scaled_f32(x64, d32, len, scal + 1, st));
     }
   }
@@ -849,7 +953,6 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
     else SG_CUDA(cudaMemcpy(&dev_its, c64->dg.iv + 4, sizeof(int), cudaMemcpyDeviceToHost));
     inf.inner_it += dev_its;
   }
-  inf.fallback_used = 0;
   inf.t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (o->hist_host && o->hist_cap > 0) {
     int cnt = std::min<int>(o->hist_cap, int(hist.size()));

@@ -28,6 +28,16 @@ struct AmgLevel {
   std::vector<int32_t> agg;
 };
 
+// Smoothed-aggregation hierarchy: levels plus the explicit FP64 inverse of
+// the coarsest matrix.
+struct AmgHier {
+  std::vector<AmgLevel> lev;
+  DevBuf coarsest_inv64;
+  size_t size() const { return lev.size(); }
+  AmgLevel& operator[](size_t l) { return lev[l]; }
+  const AmgLevel& operator[](size_t l) const { return lev[l]; }
+};
+
 // Restricted additive Schwarz data: per box, block-tridiagonal (line)
 // Cholesky factors of the local mean block, stored as explicit inverses of
 // the diagonal blocks and the sub-diagonal blocks, padded to wmax x wmax.
@@ -51,6 +61,14 @@ struct CoarseData {
   DevCsr RT, R;                            // interpolation (n x nc) and restriction
 };
 
+// Smoother inputs recorded during solves: the training residuals of the
+// learned smoother.  pool holds cap blocks of P x ld FP32 values.
+struct Harvest {
+  bool on = false;
+  int64_t cap = 0, count = 0;
+  DevBuf pool;
+};
+
 struct Precond {
   bool ready = false;
   int sx = 0, sy = 0, overlap = 0;
@@ -59,11 +77,17 @@ struct Precond {
   int inner_max = 100, inner_restart = 30;
   RasData ras;
   CoarseData co;
-  std::vector<AmgLevel> amg;
-  DevBuf coarsest_inv64;                   // dense inverse of the coarsest matrix (FP64)
+  AmgHier amg;                             // on the coarse mean operator
   std::vector<double> gt;                  // Kronecker factor G~ (P x P), host
   DevBuf gtinv64, gtinv32;                 // omega * G~^{-1} (P x P)
   DevBuf gkron64, gkron32;                 // G~^{-1} (coarse AMG preconditioner)
+  std::vector<double> ginv;                // G~^{-1}, host
+  // learned smoother: S r = omega_cnn (G~^{-1} (x) I) CNN(r)
+  int smoother = 0;                        // 0 RAS, 1 learned
+  bool use_cnn = false;                    // learned smoother active in the current solve
+  double omega_cnn = 1.0;
+  DevBuf gtcnn64, gtcnn32;                 // omega_cnn * G~^{-1}
+  Harvest harvest;
   int inner_its_last = 0, inner_its_total = 0, inner_calls = 0;
   bool device_loops = true;                // coarse GMRES as one CUDA graph launch
   int last_coarse_dtype = -1;              // 0 FP64, 1 FP32: context of the last graph solve
@@ -78,6 +102,9 @@ struct CoarsePlan {
 };
 
 sg_status precond_setup_host(sg_problem* pr, Precond& pc);
+// smoothed-aggregation hierarchy of the fine mean matrix A_0 (training
+// targets of the learned smoother)
+sg_status amg_setup_fine(const sg_problem* pr, AmgHier& h);
 const Ell& coarse_ell(const sg_problem* pr);
 const TripleTables& coarse_tri(const sg_problem* pr);
 sg_status precond_setup_coarse_plan(sg_problem* pr, Precond& pc, const CoarsePlan& plan);

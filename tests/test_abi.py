@@ -15,7 +15,7 @@ def declared_symbols():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        for m in re.finditer(r"^\s*(?:sg_status|const\s+char\s*\*|void|int)\s+\**\s*(sg_\w+)\s*\(",
+        for m in re.finditer(r"^\s*(?:sg_status|const\s+char\s*\*|void|int|int64_t)\s+\**\s*(sg_\w+)\s*\(",
                              src, flags=re.M):
             names.add(m.group(1))
     return sorted(names)
@@ -43,7 +43,9 @@ def test_exports_every_declared_symbol(libsg):
 def test_binding_covers_header(libsg):
     from paper_2310_14649_gb300 import _lib
     names = set(declared_symbols()) - {"sg_last_error"}
-    assert names <= set(_lib.SIGNATURES), sorted(names - set(_lib.SIGNATURES))
+    bound = set(_lib.SIGNATURES) | set(_lib.VALUE_FUNCTIONS)
+    assert names <= bound, sorted(names - bound)
+    assert "sg_cnn_param_count" in names
 
 
 def test_argument_errors_without_gpu(libsg):
@@ -56,3 +58,10 @@ def test_argument_errors_without_gpu(libsg):
     assert st == -1 and b"N must be" in libsg.sg_last_error()
     assert libsg.sg_apply(None, 0, None, 0, None, 0, None) == -1
     assert libsg.sg_destroy(None) == 0
+
+
+def test_cnn_param_count_without_gpu(libsg):
+    """The flat weight array of the learned smoother: 9 Cin Cout + Cout per layer."""
+    from paper_2310_14649_gb300 import CNN_CHANNELS, sg_cnn_param_count
+    ch = CNN_CHANNELS
+    assert sg_cnn_param_count() == sum(9 * ch[l] * ch[l + 1] + ch[l + 1] for l in range(5))

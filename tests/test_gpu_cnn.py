@@ -1,0 +1,199 @@
+"""Learned smoother through the C ABI versus the FP64 oracle (GPU).
+
+The kernels compute in BF16 (weights, activations) with FP32 accumulation,
+the oracle in FP64 on the same BF16-rounded weights and inputs; the
+remaining difference is the BF16 rounding of the four hidden activations
+(relative 2^-9 each), so outputs are compared at 2e-2 of their scale and
+gradients at 5e-2 in relative L2 per layer."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import cnn, galerkin
+from sg_inputs import random_block
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # N, L, p, q: 23 x 23 and 35 x 35 images (several 8 x 16 tiles with a ragged edge)
+    (24, 2, 2, 4),
+    (36, 2, 1, 2),
+]
+
+
+def bf16(a):
+    import torch
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def params_for(seed):
+    rng = np.random.default_rng(seed)
+    params = cnn.he_init(rng)
+    # non-zero biases exercise the epilogue
+    params = [(W, 0.05 * rng.standard_normal(b.shape)) for W, b in params]
+    return params
+
+
+def rounded(params):
+    return [(bf16(W), np.asarray(b, dtype=np.float32).astype(np.float64)) for W, b in params]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "N%d_L%d_p%d" % c[:3])
+def pair(request, gpu):
+    import paper_2310_14649_gb300 as sg
+    N, L, p, q = request.param
+    prob = sg.sg_setup(N, L, p, q, sigma2=0.3, bx=0.5, by=0.5)
+    ref = galerkin.build(N, L, p, q, 0.3, 0.5, 0.5)
+    return prob, ref
+
+
+def dev_rows(M, ld=None):
+    """[n, P] host block -> [P, ld] float32 CUDA tensor (padding zero)."""
+    import torch
+    n, P = M.shape
+    out = torch.zeros((P, ld or n + 5), dtype=torch.float32, device="cuda")
+    out[:, :n] = torch.from_numpy(np.ascontiguousarray(M.T)).float()
+    return out
+
+
+def oracle_features(ref, R):
+    diag = ref.A(0).diagonal()
+    x, rms = cnn.features(R, diag, ref.N)
+    x[..., 0] = bf16(x[..., 0])
+    x[..., 1] = bf16(x[..., 1])
+    return x, rms
+
+
+def test_forward_matches_oracle(pair):
+    import paper_2310_14649_gb300 as sg
+    prob, ref = pair
+    params = params_for(7)
+    sg.sg_cnn_set_weights(prob, params)
+    R = random_block(ref.n, ref.P, seed=70).astype(np.float32).astype(np.float64)
+    Rd = dev_rows(R)
+    Zd = dev_rows(np.full((ref.n, ref.P), np.nan), ld=ref.n + 9)
+    sg.sg_cnn_apply(prob, Rd, Zd)
+    Z = Zd.double().cpu().numpy()
+    assert np.all(Z[:, ref.n:] == 0.0)
+    x, rms = oracle_features(ref, R)
+    y, _ = cnn.forward(rounded(params), x)
+    Zr = y[..., 0].reshape(ref.P, -1) * rms[:, None]
+    scale = np.max(np.abs(Zr))
+    assert np.max(np.abs(Z[:, :ref.n] - Zr)) <= 2e-2 * scale
+    assert np.linalg.norm(Z[:, :ref.n] - Zr) <= 1e-2 * np.linalg.norm(Zr)
+
+
+def test_zero_and_constant_images(pair):
+    """A zero residual image gives a zero correction (rms = 0), and the
+    network commutes with positive scaling of its input."""
+    import paper_2310_14649_gb300 as sg
+    prob, ref = pair
+    sg.sg_cnn_set_weights(prob, params_for(8))
+    R = random_block(ref.n, 3, seed=71).astype(np.float32).astype(np.float64)
+    R[:, 1] = 0.0
+    R2 = R.copy()
+    R2[:, 2] *= 1024.0
+    out = []
+    for M in (R, R2):
+        Rd = dev_rows(M)
+        Zd = dev_rows(np.zeros_like(M))
+        sg.sg_cnn_apply(prob, Rd, Zd)
+        out.append(Zd.double().cpu().numpy())
+    assert np.all(out[0][1] == 0.0)
+    np.testing.assert_allclose(out[1][2], 1024.0 * out[0][2], rtol=1e-6, atol=0)
+    np.testing.assert_array_equal(out[1][0], out[0][0])
+
+
+def test_gradient_matches_oracle(pair):
+    import paper_2310_14649_gb300 as sg
+    prob, ref = pair
+    params = params_for(9)
+    sg.sg_cnn_set_weights(prob, params)
+    P = ref.P
+    R = random_block(ref.n, P, seed=72).astype(np.float32).astype(np.float64)
+    A0 = ref.A(0).tocsc()
+    Zs = np.column_stack([spla.spsolve(A0, R[:, a]) for a in range(P)]).astype(np.float32).astype(np.float64)
+    loss = sg.sg_cnn_train_step(prob, dev_rows(R), dev_rows(Zs), update=False)
+    g = sg.sg_cnn_get_weights(prob, gradient=True)
+    # the weights are unchanged by a step without update
+    np.testing.assert_array_equal(sg.sg_cnn_get_weights(prob), sg.cnn_flatten(params))
+    x, rms = oracle_features(ref, R)
+    m = ref.N - 1
+    zt = (Zs / rms[None, :]).T.reshape(P, m, m, 1)
+    pr = rounded(params)
+    y, acts = cnn.forward(pr, x)
+    L, dy = cnn.loss(y, zt)
+    grads, _ = cnn.backward(pr, acts, dy)
+    assert abs(loss - L) <= 2e-2 * L
+    gl = sg.cnn_unflatten(g)
+    for l, ((dW, db), (gW, gb)) in enumerate(zip(grads, gl)):
+        assert np.linalg.norm(gW - dW) <= 5e-2 * np.linalg.norm(dW), l
+        assert np.linalg.norm(gb - db) <= 5e-2 * np.linalg.norm(db) + 1e-6, l
+
+
+def test_adam_step_matches_oracle(pair):
+    """One update: the new weights follow the oracle's Adam from the
+    gradient the kernels produced (FP32 arithmetic)."""
+    import paper_2310_14649_gb300 as sg
+    prob, ref = pair
+    params = params_for(10)
+    sg.sg_cnn_set_weights(prob, params)
+    R = random_block(ref.n, 2, seed=73).astype(np.float32).astype(np.float64)
+    Zs = random_block(ref.n, 2, seed=74).astype(np.float32).astype(np.float64)
+    sg.sg_cnn_train_step(prob, dev_rows(R), dev_rows(Zs), lr=1e-3, update=True)
+    g = sg.cnn_unflatten(sg.sg_cnn_get_weights(prob, gradient=True))
+    w1 = sg.sg_cnn_get_weights(prob)
+    p32 = sg.cnn_unflatten(sg.cnn_flatten(params))
+    ref_new, _ = cnn.adam_step(p32, g, cnn.adam_init(p32), lr=1e-3)
+    np.testing.assert_allclose(w1, sg.cnn_flatten(ref_new), rtol=1e-5, atol=1e-8)
+
+
+def test_mean_solve_matches_sparse_direct(pair):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = pair
+    B = random_block(ref.n, 5, seed=75).astype(np.float32).astype(np.float64)
+    B[:, 3] = 0.0
+    Zd = dev_rows(np.zeros_like(B))
+    rel, its = sg.sg_mean_solve(prob, dev_rows(B), Zd, rtol=1e-6)
+    assert rel <= 1e-6 and its < 100
+    Z = Zd.double().cpu().numpy()[:, :ref.n].T
+    A0 = ref.A(0).tocsc()
+    for c in range(5):
+        zr = spla.spsolve(A0, B[:, c])
+        if c == 3:
+            assert np.all(Z[:, c] == 0.0)
+            continue
+        # FP32 storage of the result on top of the 1e-6 residual
+        assert np.linalg.norm(Z[:, c] - zr) <= 1e-4 * np.linalg.norm(zr)
+    torch.cuda.synchronize()
+
+
+def test_network_operators_in_precond_apply(pair):
+    """PC_NETWORK is the network per mode; PC_LEARNED adds omega_cnn G~^{-1}
+    across the modes at every node."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = pair
+    sx = 2
+    sg.sg_precond_setup(prob, sx, sx, 1)
+    params = params_for(11)
+    sg.sg_cnn_set_weights(prob, params)
+    sg.sg_precond_set_smoother(prob, 1, omega=0.75)
+    R = random_block(ref.n, ref.P, seed=76).astype(np.float32).astype(np.float64)
+    Rd = dev_rows(R)
+    Z1 = torch.zeros_like(Rd)
+    Z2 = torch.zeros_like(Rd)
+    sg.sg_precond_apply(prob, sg.PC_NETWORK, Rd, Z1)
+    sg.sg_precond_apply(prob, sg.PC_LEARNED, Rd, Z2)
+    Zn = Z1.double().cpu().numpy()[:, :ref.n]
+    Zl = Z2.double().cpu().numpy()[:, :ref.n]
+    x, rms = oracle_features(ref, R)
+    y, _ = cnn.forward(rounded(params), x)
+    Zr = y[..., 0].reshape(ref.P, -1) * rms[:, None]
+    assert np.max(np.abs(Zn - Zr)) <= 2e-2 * np.max(np.abs(Zr))
+    from oracle import ras
+    Gt = ras.kronecker_factor(ref)
+    Zlr = 0.75 * np.linalg.solve(Gt, Zn)
+    assert np.max(np.abs(Zl - Zlr)) <= 1e-5 * np.max(np.abs(Zlr))
+    sg.sg_precond_set_smoother(prob, 0)

@@ -1,0 +1,125 @@
+"""The learned smoother inside the solver (GPU): training on the method's own
+residuals and A_0^{-1} targets, what the trained network gains, and the
+fallback to RAS when the network misbehaves."""
+import numpy as np
+import pytest
+
+from oracle import galerkin
+from sg_inputs import CONFIGS
+
+pytestmark = pytest.mark.gpu
+
+CASE = dict(CONFIGS["poisson32_L2_p2"])
+
+
+def setup(**kw):
+    import paper_2310_14649_gb300 as sg
+    c = dict(CASE, **kw)
+    prob = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"])
+    return prob, c
+
+
+def zeros(prob):
+    import torch
+    return torch.zeros((prob.P, prob.n), dtype=torch.float64, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def trained(gpu):
+    import paper_2310_14649_gb300 as sg
+    prob, c = setup()
+    info = sg.sg_train_precond(prob, n_pairs=768, epochs=12, batch=16, lr=1e-3, seed=0)
+    return prob, c, info
+
+
+def test_training_lowers_the_loss(trained):
+    prob, c, info = trained
+    print("train info", info)
+    assert info["n_pairs"] == 768 and info["steps"] == 12 * (768 // 16)
+    assert info["target_relres"] <= 1e-6
+    assert np.isfinite(info["loss_last"]) and info["loss_last"] < 0.5 * info["loss_first"]
+    assert info["omega_cnn"] > 0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_learned_solve_matches_oracle(trained, mode):
+    """With the learned smoother the solve still reaches relres 1e-8 and
+    the oracle's solution to 1e-7."""
+    import paper_2310_14649_gb300 as sg
+    prob, c, _ = trained
+    sg.sg_precond_set_smoother(prob, 1)
+    X = zeros(prob)
+    info = sg.sg_solve(prob, X, rtol=1e-8, mode=mode)
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    Xh = X.cpu().numpy().T
+    Xd = galerkin.solve_direct(ref)
+    assert info["relres"] <= 1e-8
+    assert galerkin.relres(ref, Xh) <= 1.01e-8
+    assert np.linalg.norm(Xh - Xd) / np.linalg.norm(Xd) <= 1e-7
+
+
+def test_trained_network_gains_over_untrained(trained):
+    """Outer iterations to 1e-8 with the trained network against the same
+    network at its He initialisation (no fallback in either), and against
+    the RAS smoother for reference."""
+    import paper_2310_14649_gb300 as sg
+    prob, c, _ = trained
+    w_trained = sg.sg_cnn_get_weights(prob)
+    its = {}
+    sg.sg_precond_set_smoother(prob, 1)
+    X = zeros(prob)
+    its["trained"] = sg.sg_solve(prob, X, rtol=1e-8, mode=0, max_it=400, fallback=False,
+                                 allow_not_converged=True)
+    sg.sg_cnn_init(prob, seed=0)
+    sg.sg_precond_set_smoother(prob, 1)
+    X = zeros(prob)
+    its["untrained"] = sg.sg_solve(prob, X, rtol=1e-8, mode=0, max_it=400, fallback=False,
+                                   allow_not_converged=True)
+    sg.sg_precond_set_smoother(prob, 0)
+    X = zeros(prob)
+    its["ras"] = sg.sg_solve(prob, X, rtol=1e-8, mode=0)
+    print({k: (v["outer_it"], v["relres"]) for k, v in its.items()})
+    sg.sg_cnn_set_weights(prob, w_trained)
+    sg.sg_precond_set_smoother(prob, 1)
+    assert its["trained"]["relres"] <= 1e-8
+    assert its["trained"]["outer_it"] < its["untrained"]["outer_it"]
+
+
+def test_fallback_on_nan_weights(gpu):
+    import paper_2310_14649_gb300 as sg
+    prob, c = setup()
+    w = np.zeros(sg.sg_cnn_param_count(), dtype=np.float32)
+    w[5] = np.nan
+    sg.sg_cnn_set_weights(prob, w)
+    sg.sg_precond_set_smoother(prob, 1, omega=1.0)
+    for mode in (0, 1):
+        X = zeros(prob)
+        info = sg.sg_solve(prob, X, rtol=1e-8, mode=mode)
+        assert info["fallback_used"] == 1 and info["relres"] <= 1e-8
+    # without fallback the non-finite preconditioner is a breakdown
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_solve(prob, zeros(prob), rtol=1e-8, mode=0, fallback=False)
+    assert e.value.status == -4
+
+
+def test_fallback_on_zero_weights(gpu):
+    """A network that outputs zero leaves only the coarse correction: the
+    solve stagnates, switches to RAS and still converges."""
+    import paper_2310_14649_gb300 as sg
+    prob, c = setup()
+    sg.sg_cnn_set_weights(prob, np.zeros(sg.sg_cnn_param_count(), dtype=np.float32))
+    sg.sg_precond_set_smoother(prob, 1, omega=1.0)
+    X = zeros(prob)
+    info = sg.sg_solve(prob, X, rtol=1e-8, mode=1)
+    assert info["fallback_used"] == 1 and info["relres"] <= 1e-8
+
+
+def test_learned_smoother_needs_weights(gpu):
+    import paper_2310_14649_gb300 as sg
+    prob, c = setup()
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_precond_set_smoother(prob, 1)
+    assert e.value.status == -1
+    with pytest.raises(sg.SgError):
+        sg.sg_precond_setup(prob, 2, 2, 1, smoother=1)
