@@ -328,6 +328,7 @@ __global__ void k_dg_init(DevGmres d, const double* __restrict__ rnorm2, double 
   d.dtol[0] = rtol * nr;
   d.iv[1] = 0;  // iterations
   d.iv[3] = 0;  // stop
+  d.iv[5] = 0;  // breakdown
   cudaGraphSetConditional(outer, nr > 0.0 ? 1u : 0u);
 }
 

@@ -274,6 +274,19 @@ struct SolverCtx {
       if (c) cudaStreamDestroy(c);
   }
 
+  // Clears every work vector.  After a non-finite value the padding rows
+  // (n..ld-1) of the Krylov vectors can hold NaN that later full-length
+  // reductions would pick up; a solve that continues after such a value
+  // (the fallback from the learned smoother) starts from clean buffers.
+  sg_status scrub(cudaStream_t st) {
+    for (DevBuf* b : {&fine.V, &fine.Z, &fine.w, &fine.tmp, &fine.tmp2, &coarse.V, &coarse.w, &coarse.tmp,
+                      &coarse.tmp2, &r1, &zt, &rc, &ec})
+      if (b->ptr) SG_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, st));
+    for (DevBuf& b : amgbuf)
+      if (b.ptr) SG_CUDA(cudaMemsetAsync(b.ptr, 0, b.bytes, st));
+    return SG_OK;
+  }
+
   sg_status apply_fine(const T* X, T* Y, const T* F, cudaStream_t st) {
     return apply_op<T>(pr, false, X, ld, F, ld, Y, ld, st);
   }
@@ -492,6 +505,7 @@ struct SolverState {
   std::unique_ptr<SolverCtx<float>> c32;
   int restart = 30;
   DevBuf x64, r64, r32, d32, io, io2, scal;  // IR and I/O buffers
+  bool dirty = false;                        // the last solve ended on an error
   double* host = nullptr;                    // pinned scalars
   ~SolverState() {
     if (host) cudaFreeHost(host);
@@ -812,13 +826,28 @@ sg_status sg_precond_apply(sg_problem* pr, sg_dtype dtype, int which, const void
   SG_ARG(pr->solver && pr->solver->pc.ready, "sg_precond_apply: call sg_precond_setup first");
   SG_ARG(dtype == SG_F64 || dtype == SG_F32, "sg_precond_apply: bad dtype");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (dtype == SG_F64)
-    return precond_apply_t<double>(pr, which, static_cast<const double*>(R), ldr, static_cast<double*>(Z), ldz, st);
-  return precond_apply_t<float>(pr, which, static_cast<const float*>(R), ldr, static_cast<float*>(Z), ldz, st);
+  const sg_status s =
+      dtype == SG_F64
+          ? precond_apply_t<double>(pr, which, static_cast<const double*>(R), ldr, static_cast<double*>(Z), ldz, st)
+          : precond_apply_t<float>(pr, which, static_cast<const float*>(R), ldr, static_cast<float*>(Z), ldz, st);
+  if (s < 0) pr->solver->dirty = true;
+  return s;
 }
+
+static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double* X, int64_t ldx,
+                            const sg_solve_opts* o, sg_solve_info* info, void* stream);
 
 sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int64_t ldx, const sg_solve_opts* o,
                    sg_solve_info* info, void* stream) {
+  const sg_status s = solve_impl(pr, F, ldf, X, ldx, o, info, stream);
+  if (s < 0 && pr && pr->solver) pr->solver->dirty = true;
+  return s;
+}
+
+}  // extern "C"
+
+static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double* X, int64_t ldx,
+                            const sg_solve_opts* o, sg_solve_info* info, void* stream) {
   SG_ARG(pr && X && o, "sg_solve: NULL argument");
   SG_ARG(pr->solver && pr->solver->pc.ready, "sg_solve: call sg_precond_setup first");
   SG_ARG(ldx >= pr->n && (!F || ldf >= pr->n), "sg_solve: leading dimension < n");
@@ -855,6 +884,11 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
   const double nF = std::sqrt(S.host[0]);
   sg_solve_info inf{};
   std::vector<double> hist;
+  if (S.dirty) {
+    SG_TRY(c64->scrub(st));
+    if (S.c32) SG_TRY(S.c32->scrub(st));
+    S.dirty = false;
+  }
   S.pc.use_cnn = S.pc.smoother == 1 && pr->cnn && pr->cnn->trained;
   const bool stall_test = S.pc.use_cnn && !o->no_fallback;
   struct ClearCnn {
@@ -881,6 +915,7 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
       if (stall_test && S.pc.use_cnn && (gs == SG_ERR_BREAKDOWN || res.stalled) && inf.outer_it < o->max_it) {
         S.pc.use_cnn = false;
         inf.fallback_used = 1;
+        SG_TRY(c64->scrub(st));
         continue;
       }
       SG_TRY(gs);
@@ -931,6 +966,7 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
       if (stall_test && S.pc.use_cnn && (gs == SG_ERR_BREAKDOWN || res.stalled)) {
         S.pc.use_cnn = false;
         inf.fallback_used = 1;
+        SG_TRY(c32->scrub(st));
         if (gs != SG_OK) continue;  // the correction is not usable
       }
       SG_TRY(gs);
@@ -965,4 +1001,4 @@ sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int6
   return status;
 }
 
-}  // extern "C"
+
