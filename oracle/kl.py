@@ -76,7 +76,9 @@ def modes_2d(sigma2, bx, by, L):
     cand = []
     for m in range(L):
         for n in range(L):
-            lam = sigma2 * ex[m][0] * ey[n][0]
+            # sigma^2 (lambda_m lambda_n): the 1D product is commutative, so
+            # the equal pairs (m, n), (n, m) of b_x = b_y stay exact ties
+            lam = sigma2 * (ex[m][0] * ey[n][0])
             cand.append((-lam, m, n))
     cand.sort()
     return [(-nl, m, n, ex[m], ey[n]) for (nl, m, n) in cand[:L]]

@@ -28,7 +28,11 @@ def nvcc():
 
 
 def _flags(src):
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    # host code without contracted multiply-adds: the setup's floating-point
+    # decisions (root brackets, mode order, aggregation) then round alike on
+    # x86-64 and aarch64 hosts
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "-I", INCLUDE, "-I", CSRC]
     if src.endswith(".cu"):
         return ARCH + common + ["--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
     return common

@@ -142,7 +142,10 @@ sg_status build_host(sg_problem* pr, const sg_kl_desc* kl) {
       std::vector<std::tuple<double, int, int>> cand;
       for (int m = 0; m < L; ++m)
         for (int nn = 0; nn < L; ++nn)
-          cand.emplace_back(-(kl->sigma2 * mx[m].lam * my[nn].lam), m, nn);
+          // sigma^2 (lambda_m lambda_n): the product of the two 1D values is
+          // commutative, so the equal pairs (m, n), (n, m) of b_x = b_y stay
+          // exactly equal and the (m, n) tie-break decides their order
+          cand.emplace_back(-(kl->sigma2 * (mx[m].lam * my[nn].lam)), m, nn);
       std::sort(cand.begin(), cand.end());
       for (int i = 0; i < L; ++i) {
         double lam = -std::get<0>(cand[i]);
