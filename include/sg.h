@@ -366,6 +366,48 @@ sg_status sg_train_precond(sg_problem* prob, const sg_train_opts* opts, sg_train
  * omega <= 0 estimates omega_cnn). */
 sg_status sg_precond_set_smoother(sg_problem* prob, int smoother, double omega, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Graph-captured and batched solves.  sg_batch_create records, for every
+ * problem, the whole solve of sg_solve (mode 1: the refinement loop with
+ * its FP64 residuals, every FP32 FGMRES restart and Arnoldi step, every
+ * two-level cycle with its inner coarse GMRES + AMG; mode 0: the FP64
+ * FGMRES) as CUDA graph nodes whose loops are conditional WHILE nodes
+ * decided on the device, the problems as parallel branches of one graph.
+ * sg_batch_solve launches that graph once: all systems are solved with no
+ * host round trip.  The recorded smoother is the one selected at creation;
+ * there is no learned-to-RAS fallback inside the graph.  The batch uses
+ * each problem's solver workspaces: do not call sg_precond_setup on a member
+ * problem (sg_batch_solve then fails with SG_ERR_ARG) or run the problems
+ * on other streams while a batch solve is in flight; destroy the batch
+ * before its problems.  The paper solves one system at a time; batching
+ * independent systems is a property of this library.
+ * ------------------------------------------------------------------------ */
+typedef struct sg_batch sg_batch;
+
+/* count in [1, 256] distinct problems, each after sg_precond_setup; opts as
+ * for sg_solve (hist_host ignored; restart, rtol, max_it, mode, inner_rtol
+ * and max_ir are recorded).  Allocates each problem's solve workspaces,
+ * compiles its specialised kernels and records the graph.  Synchronous. */
+sg_status sg_batch_create(sg_problem* const* probs, int count, const sg_solve_opts* opts, sg_batch** out);
+
+/* Solves every system of the batch: F[i] (FP64 device block, ldf[i] rows;
+ * F or F[i] NULL = the load vector) and X[i] (initial guess in, solution
+ * out, ldx[i] rows).  infos[i] (may be NULL): outer_it = FGMRES iterations,
+ * inner_it = coarse GMRES iterations, ir_steps, relres = true FP64
+ * relative residual of the returned X[i], t_solve = wall time of the whole
+ * batch.  Returns SG_OK when every system reached rtol, SG_NOT_CONVERGED
+ * when one stopped at max_it / max_ir, SG_ERR_BREAKDOWN on a non-finite
+ * residual.  Synchronises the stream once. */
+sg_status sg_batch_solve(sg_batch* batch, const double* const* F, const int64_t* ldf, double* const* X,
+                         const int64_t* ldx, sg_solve_info* infos, void* stream);
+
+sg_status sg_batch_destroy(sg_batch* batch);
+
+/* sg_batch_create + sg_batch_solve + sg_batch_destroy in one call. */
+sg_status sg_solve_batch(sg_problem* const* probs, int count, const double* const* F, const int64_t* ldf,
+                         double* const* X, const int64_t* ldx, const sg_solve_opts* opts, sg_solve_info* infos,
+                         void* stream);
+
 /* Multi-vector dot products, the classical Gram-Schmidt step of the
  * Arnoldi process inside FGMRES (Sec. 3):  out[i] = sum_e V_i[e] w[e] for
  * i < nv, where V_i = V + i * stride.  dtype selects double or float

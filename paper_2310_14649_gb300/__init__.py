@@ -20,6 +20,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_mdot_noalloc", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
            "sg_train_precond", "sg_precond_set_smoother", "cnn_flatten", "cnn_unflatten",
+           "Batch", "sg_batch_create", "sg_batch_solve", "sg_batch_destroy", "sg_solve_batch",
            "SgError", "SG_F32", "SG_F64", "PC_TWOLEVEL", "PC_SMOOTH", "PC_COARSE", "PC_AMG",
            "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL", "PC_LEARNED",
            "PC_NETWORK"]
@@ -373,3 +374,93 @@ def sg_train_precond(prob, n_pairs=4096, epochs=4, batch=32, lr=1e-3, seed=0, ta
 def sg_precond_set_smoother(prob, smoother, omega=0.0, stream=None):
     """0 RAS, 1 learned (omega <= 0: estimate)."""
     call("sg_precond_set_smoother", prob.handle, smoother, omega, stream_handle(stream))
+
+
+# ---------------------------------------------------------------------------
+# graph-captured batches of systems
+# ---------------------------------------------------------------------------
+class Batch:
+    """Owning wrapper of an sg_batch handle (keeps its problems alive)."""
+
+    def __init__(self, handle, probs):
+        self.handle = handle
+        self.probs = list(probs)
+
+    def close(self):
+        if self.handle:
+            sg_batch_destroy(self)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _solve_opts(rtol, max_it, restart, mode, inner_rtol, max_ir):
+    return _lib.SolveOpts(rtol, max_it, restart, mode, inner_rtol, max_ir, None, 0, 0)
+
+
+def _ptr_array(ts, allow_none=False):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = None if (t is None and allow_none) else t.data_ptr()
+    return arr
+
+
+def _ld_array(ts):
+    arr = (ctypes.c_int64 * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = 0 if t is None else t.stride(0)
+    return arr
+
+
+def sg_batch_create(probs, rtol=1e-8, max_it=500, restart=30, mode=1, inner_rtol=0.0, max_ir=0):
+    handles = (ctypes.c_void_p * len(probs))(*[p.handle.value for p in probs])
+    opts = _solve_opts(rtol, max_it, restart, mode, inner_rtol, max_ir)
+    h = ctypes.c_void_p()
+    call("sg_batch_create", handles, len(probs), ctypes.byref(opts), ctypes.byref(h))
+    return Batch(h, probs)
+
+
+def _infos_out(infos, sts):
+    out = []
+    for inf in infos:
+        d = {f: getattr(inf, f) for f, _ in _lib.SolveInfo._fields_}
+        d["status"] = sts
+        out.append(d)
+    return out
+
+
+def sg_batch_solve(batch, Xs, Fs=None, stream=None, allow_not_converged=False):
+    """Solve all systems of the batch (Xs: FP64 [P_i, ld_i] CUDA tensors,
+    guesses in, solutions out; Fs: None or per-system FP64 blocks / None)."""
+    import torch
+    for p, X in zip(batch.probs, Xs):
+        _check_block(p, X, "X")
+        if X.dtype != torch.float64:
+            raise TypeError("batch solves work on FP64 blocks")
+    Fs = Fs if Fs is not None else [None] * len(Xs)
+    infos = (_lib.SolveInfo * len(Xs))()
+    allow = (0, 1) if allow_not_converged else (0,)
+    st = call("sg_batch_solve", batch.handle, _ptr_array(Fs, True), _ld_array(Fs), _ptr_array(Xs), _ld_array(Xs),
+              infos, stream_handle(stream), allow=allow)
+    return _infos_out(infos, st)
+
+
+def sg_batch_destroy(batch):
+    call("sg_batch_destroy", batch.handle)
+
+
+def sg_solve_batch(probs, Xs, Fs=None, rtol=1e-8, max_it=500, restart=30, mode=1, inner_rtol=0.0, max_ir=0,
+                   stream=None, allow_not_converged=False):
+    """One-shot batch: record, solve, release."""
+    handles = (ctypes.c_void_p * len(probs))(*[p.handle.value for p in probs])
+    opts = _solve_opts(rtol, max_it, restart, mode, inner_rtol, max_ir)
+    Fs = Fs if Fs is not None else [None] * len(Xs)
+    infos = (_lib.SolveInfo * len(Xs))()
+    allow = (0, 1) if allow_not_converged else (0,)
+    st = call("sg_solve_batch", handles, len(probs), _ptr_array(Fs, True), _ld_array(Fs), _ptr_array(Xs),
+              _ld_array(Xs), ctypes.byref(opts), infos, stream_handle(stream), allow=allow)
+    return _infos_out(infos, st)

@@ -111,6 +111,11 @@ SIGNATURES = {
                       ctypes.POINTER(ctypes.c_int), vp],
     "sg_train_precond": [vp, ctypes.POINTER(TrainOpts), ctypes.POINTER(TrainInfo), vp],
     "sg_precond_set_smoother": [vp, ctypes.c_int, f64, vp],
+    "sg_batch_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(SolveOpts), ctypes.POINTER(vp)],
+    "sg_batch_solve": [vp, ctypes.POINTER(vp), P_i64, ctypes.POINTER(vp), P_i64, ctypes.POINTER(SolveInfo), vp],
+    "sg_batch_destroy": [vp],
+    "sg_solve_batch": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), P_i64, ctypes.POINTER(vp), P_i64,
+                       ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
 }
 
 # functions whose result is not an sg_status: name -> (argtypes, restype)

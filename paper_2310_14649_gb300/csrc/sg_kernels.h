@@ -95,7 +95,13 @@ sg_status dg_init(DevGmres d, const double* rnorm2, double rtol, cudaGraphCondit
 sg_status dg_start(DevGmres d, GmresState s, int m, const double* beta2, cudaGraphConditionalHandle inner,
                    cudaStream_t st);
 sg_status dg_givens(DevGmres d, GmresState s, int m, cudaGraphConditionalHandle inner, cudaStream_t st);
-sg_status dg_end(DevGmres d, GmresState s, cudaGraphConditionalHandle outer, cudaStream_t st);
+sg_status dg_end(DevGmres d, GmresState s, cudaGraphConditionalHandle outer, cudaStream_t st, bool trust = true);
+// V_j = src for the device index j = d.iv[0]
+template <typename T>
+sg_status dg_store_j(const T* src, T* V, int64_t stride, int64_t len, DevGmres d, cudaStream_t st);
+// refinement loop control of a graph-captured mixed-precision solve
+sg_status ir_decide(const double* rr, const double* nf2, int* iv, double rtol, int max_ir, const int* its_total,
+                    int max_it, cudaGraphConditionalHandle h, cudaStream_t st);
 sg_status dg_backsolve(DevGmres d, GmresState s, int m, cudaStream_t st);
 sg_status gmres_givens(GmresState s, int m, int j, double* host_est, cudaStream_t st);
 sg_status gmres_backsolve(GmresState s, int m, int k, cudaStream_t st);

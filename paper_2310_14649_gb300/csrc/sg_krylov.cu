@@ -381,11 +381,36 @@ __global__ void k_dg_givens(DevGmres d, GmresState s, int m, cudaGraphConditiona
   cudaGraphSetConditional(inner, go ? 1u : 0u);
 }
 
-// end of a cycle: stop when converged, stalled, failed or out of iterations
-__global__ void k_dg_end(DevGmres d, GmresState s, cudaGraphConditionalHandle outer) {
+// end of a cycle: stop when converged (by the Arnoldi estimate when trust,
+// else only by the true residual of the next restart), stalled, failed or
+// out of iterations
+__global__ void k_dg_end(DevGmres d, GmresState s, cudaGraphConditionalHandle outer, int trust) {
   const double est = s.scal[2];
-  const bool done = d.iv[3] || d.iv[5] || !(est > d.dtol[0]) || d.iv[1] >= d.iv[2];
+  const bool done = d.iv[3] || d.iv[5] || (trust && !(est > d.dtol[0])) || d.iv[1] >= d.iv[2];
   cudaGraphSetConditional(outer, done ? 0u : 1u);
+}
+
+// V_j = src (device index j), full length
+template <typename T>
+__global__ void k_dg_store_j(const T* __restrict__ src, T* __restrict__ V, int64_t stride, int64_t len, DevGmres d) {
+  T* v = V + int64_t(d.iv[0]) * stride;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x)
+    v[e] = src[e];
+}
+
+// Refinement loop control: rr = ||F - A x||^2, nf2 = ||F||^2; continue
+// while sqrt(rr / nf2) > rtol, the step cap and the iteration cap allow it
+// and rr is finite.  iv[0] steps taken, iv[1] non-finite flag.
+__global__ void k_ir_decide(const double* __restrict__ rr, const double* __restrict__ nf2, int* __restrict__ iv,
+                            double rtol, int max_ir, const int* __restrict__ its_total, int max_it,
+                            cudaGraphConditionalHandle h) {
+  const double r = *rr, f = *nf2;
+  const bool bad = !isfinite(r);
+  if (bad) iv[1] = 1;
+  const double rel = f > 0.0 ? sqrt(r / f) : 0.0;
+  const bool go = !bad && rel > rtol && iv[0] < max_ir && *its_total < max_it;
+  if (go) iv[0] += 1;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 __global__ void k_dg_backsolve(DevGmres d, GmresState s, int m) {
@@ -489,14 +514,30 @@ sg_status dg_givens(DevGmres d, GmresState s, int m, cudaGraphConditionalHandle 
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
-sg_status dg_end(DevGmres d, GmresState s, cudaGraphConditionalHandle outer, cudaStream_t st) {
-  k_dg_end<<<1, 1, 0, st>>>(d, s, outer);
+sg_status dg_end(DevGmres d, GmresState s, cudaGraphConditionalHandle outer, cudaStream_t st, bool trust) {
+  k_dg_end<<<1, 1, 0, st>>>(d, s, outer, trust ? 1 : 0);
   note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
 sg_status dg_backsolve(DevGmres d, GmresState s, int m, cudaStream_t st) {
   k_dg_backsolve<<<1, 32, 0, st>>>(d, s, m);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status dg_store_j(const T* src, T* V, int64_t stride, int64_t len, DevGmres d, cudaStream_t st) {
+  k_dg_store_j<T><<<grid_for(len), 256, 0, st>>>(src, V, stride, len, d);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+sg_status ir_decide(const double* rr, const double* nf2, int* iv, double rtol, int max_ir, const int* its_total,
+                    int max_it, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_ir_decide<<<1, 1, 0, st>>>(rr, nf2, iv, rtol, max_ir, its_total, max_it, h);
   note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
@@ -509,7 +550,8 @@ sg_status dg_backsolve(DevGmres d, GmresState s, int m, cudaStream_t st) {
                                      unsigned*, const int*, cudaStream_t);                                     \
   template sg_status dg_axpy_multi<T>(const T*, int64_t, const double*, T*, int64_t, const int*, cudaStream_t); \
   template sg_status dg_scale_next<T>(const T*, T*, int64_t, int64_t, DevGmres, const double*, cudaStream_t);   \
-  template sg_status dg_copy_vj<T>(const T*, int64_t, int64_t, T*, int64_t, int64_t, int, DevGmres, cudaStream_t);
+  template sg_status dg_copy_vj<T>(const T*, int64_t, int64_t, T*, int64_t, int64_t, int, DevGmres, cudaStream_t); \
+  template sg_status dg_store_j<T>(const T*, T*, int64_t, int64_t, DevGmres, cudaStream_t);
 INST_DG(float)
 INST_DG(double)
 #undef INST_DG
