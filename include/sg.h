@@ -312,13 +312,19 @@ sg_status sg_cnn_apply(sg_problem* prob, const float* R_dev, int64_t ldr, float*
                        void* stream);
 
 /* One training step on nimg (residual, target) column pairs, the target in
- * residual units (e.g. A_0^{-1} r):  loss = sum_a ||y_a - z*_a / rms(r_a)||^2
- * / ||z*_a / rms(r_a)||^2 with y_a the network output; gradients by the
+ * residual units (e.g. A_0^{-1} r), with the loss of sg_cnn_set_loss (y_a
+ * the network output, e_a = y_a - z*_a / rms(r_a)); gradients by the
  * backward convolution kernels; with update != 0 one Adam step (beta1 0.9,
  * beta2 0.999, eps 1e-8) with learning rate lr.  loss (host, may be NULL)
  * receives the loss before the update and makes the call synchronous. */
 sg_status sg_cnn_train_step(sg_problem* prob, const float* R_dev, int64_t ldr, const float* Zstar_dev,
                             int64_t ldz, int nimg, float lr, int update, double* loss, void* stream);
+
+/* Loss of sg_cnn_train_step: 0 (default) sum_a (e_a^T A_0 e_a) /
+ * (z*_a^T A_0 z*_a), e_a = y_a - z*_a / rms(r_a): the error in the energy
+ * norm of A_0, which weights the oscillatory error a smoother must remove;
+ * 1: sum_a ||e_a||^2 / ||z*_a||^2. */
+sg_status sg_cnn_set_loss(sg_problem* prob, int kind);
 
 /* Z = A_0^{-1} B for nb FP32 device columns (the training targets): FP64
  * conjugate gradients preconditioned by one smoothed-aggregation V(1,1)
@@ -338,6 +344,8 @@ typedef struct {
   uint64_t seed;      /* He init, right-hand sides, sampling, batch order */
   double target_rtol; /* relative residual of the targets; <= 0 = 1e-6   */
   int keep_weights;   /* 1: continue from the current weights            */
+  int loss;           /* 0: relative error in the energy norm of A_0,
+                         1: relative L2 error of the correction          */
 } sg_train_opts;
 
 typedef struct {

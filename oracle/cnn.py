@@ -5,7 +5,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 Not in the paper (the method statement adds it in place of the mean-based
 block solve): parity with the paper is unpinned; the gradients below are
-pinned by central differences.
+pinned by central differences.  Two training losses: the relative squared
+error ||zhat - z*||^2 / ||z*||^2, and the same error in the energy norm of
+A_0 (weights the oscillatory error a smoother must remove).
 
 Network: channels 2 -> 32 -> 32 -> 32 -> 32 -> 1, 3x3 kernels, zero padding
 1, bias, ReLU after the first four layers.  Input channel 0 is the residual
@@ -81,6 +83,21 @@ def loss(zhat, zstar):
     den = np.sum(zstar ** 2, axis=(1, 2, 3))
     L = np.sum(num / den)
     return L, 2.0 * (zhat - zstar) / den[:, None, None, None]
+
+
+def loss_energy(zhat, zstar, A0):
+    """sum over images of (e^T A_0 e) / (z*^T A_0 z*), e = zhat - z*: the
+    squared error in the energy norm of the SPD mean matrix A_0 (images
+    [batch, m, m, 1] in node order), and its gradient 2 A_0 e / (z*^T A_0 z*)."""
+    nb = zhat.shape[0]
+    e = (zhat - zstar).reshape(nb, -1)
+    z = zstar.reshape(nb, -1)
+    Ae = (A0 @ e.T).T
+    Az = (A0 @ z.T).T
+    num = np.sum(e * Ae, axis=1)
+    den = np.sum(z * Az, axis=1)
+    L = np.sum(num / den)
+    return L, (2.0 * Ae / den[:, None]).reshape(zhat.shape)
 
 
 def he_init(rng):

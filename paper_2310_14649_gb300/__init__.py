@@ -19,7 +19,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "sg_mdot_noalloc", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
-           "sg_train_precond", "sg_precond_set_smoother", "cnn_flatten", "cnn_unflatten",
+           "sg_train_precond", "sg_precond_set_smoother", "cnn_flatten", "cnn_unflatten", "sg_cnn_set_loss",
            "Batch", "sg_batch_create", "sg_batch_solve", "sg_batch_destroy", "sg_solve_batch",
            "SgError", "SG_F32", "SG_F64", "PC_TWOLEVEL", "PC_SMOOTH", "PC_COARSE", "PC_AMG",
            "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL", "PC_LEARNED",
@@ -352,6 +352,11 @@ def sg_cnn_train_step(prob, R, Zstar, lr=1e-3, update=True, stream=None):
     return loss.value
 
 
+def sg_cnn_set_loss(prob, kind):
+    """Loss of sg_cnn_train_step: 0 energy norm of A_0, 1 relative L2 error."""
+    call("sg_cnn_set_loss", prob.handle, kind)
+
+
 def sg_mean_solve(prob, B, Z, rtol=1e-6, max_it=500, stream=None):
     """Z[a] = A_0^{-1} B[a] (float32 CUDA rows); returns (worst relres, its)."""
     _check_images(prob, B, "B")
@@ -362,10 +367,11 @@ def sg_mean_solve(prob, B, Z, rtol=1e-6, max_it=500, stream=None):
     return rel.value, its.value
 
 
-def sg_train_precond(prob, n_pairs=4096, epochs=4, batch=32, lr=1e-3, seed=0, target_rtol=1e-6,
-                     keep_weights=False, stream=None):
-    """Harvest residuals, build A_0^{-1} targets, train, select the learned smoother."""
-    opts = _lib.TrainOpts(n_pairs, epochs, batch, lr, seed, target_rtol, 1 if keep_weights else 0)
+def sg_train_precond(prob, n_pairs=4096, epochs=12, batch=32, lr=1e-3, seed=0, target_rtol=1e-6,
+                     keep_weights=False, loss=0, stream=None):
+    """Harvest residuals, build A_0^{-1} targets, train, select the learned
+    smoother.  loss: 0 energy norm of A_0, 1 relative L2 error."""
+    opts = _lib.TrainOpts(n_pairs, epochs, batch, lr, seed, target_rtol, 1 if keep_weights else 0, loss)
     info = _lib.TrainInfo()
     call("sg_train_precond", prob.handle, ctypes.byref(opts), ctypes.byref(info), stream_handle(stream))
     return {f: getattr(info, f) for f, _ in _lib.TrainInfo._fields_}

@@ -58,7 +58,7 @@ class SolveInfo(ctypes.Structure):
 class TrainOpts(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
                 ("lr", ctypes.c_float), ("seed", ctypes.c_uint64), ("target_rtol", ctypes.c_double),
-                ("keep_weights", ctypes.c_int)]
+                ("keep_weights", ctypes.c_int), ("loss", ctypes.c_int)]
 
 
 class TrainInfo(ctypes.Structure):
@@ -110,6 +110,7 @@ SIGNATURES = {
     "sg_mean_solve": [vp, vp, i64, vp, i64, ctypes.c_int, f64, ctypes.c_int, P_f64,
                       ctypes.POINTER(ctypes.c_int), vp],
     "sg_train_precond": [vp, ctypes.POINTER(TrainOpts), ctypes.POINTER(TrainInfo), vp],
+    "sg_cnn_set_loss": [vp, ctypes.c_int],
     "sg_precond_set_smoother": [vp, ctypes.c_int, f64, vp],
     "sg_batch_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(SolveOpts), ctypes.POINTER(vp)],
     "sg_batch_solve": [vp, ctypes.POINTER(vp), P_i64, ctypes.POINTER(vp), P_i64, ctypes.POINTER(SolveInfo), vp],

@@ -333,6 +333,46 @@ __global__ void k_loss_grad(const float* __restrict__ Yf, const float* __restric
   for (int q = 1; q < 8; ++q) o[q] = 0u;
 }
 
+// energy-norm loss: E = Y - Z*, then (with AE = A_0 E, AZ = A_0 Z* from the
+// sparse product) per image e.AE and z.AZ, and the gradient 2 AE / (z.AZ)
+__global__ void k_diff(const float* __restrict__ Y, const float* __restrict__ Z, float* __restrict__ E, int64_t cnt) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cnt; i += int64_t(gridDim.x) * blockDim.x)
+    E[i] = Y[i] - Z[i];
+}
+
+__global__ void k_energy_parts(const float* __restrict__ E, const float* __restrict__ AE, const float* __restrict__ Z,
+                               const float* __restrict__ AZ, int64_t npix, double* __restrict__ num,
+                               double* __restrict__ den) {
+  const int img = blockIdx.y;
+  const size_t o = size_t(img) * npix;
+  double a = 0.0, b = 0.0;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < npix; p += int64_t(gridDim.x) * blockDim.x) {
+    a += double(E[o + p]) * double(AE[o + p]);
+    b += double(Z[o + p]) * double(AZ[o + p]);
+  }
+  for (int w = 16; w > 0; w >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, w);
+    b += __shfl_xor_sync(0xffffffffu, b, w);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(num + img, a);
+    atomicAdd(den + img, b);
+  }
+}
+
+__global__ void k_energy_grad(const float* __restrict__ AE, int64_t npix, const double* __restrict__ den,
+                              bf16* __restrict__ dY) {
+  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int img = blockIdx.y;
+  if (p >= npix) return;
+  const double d = den[img];
+  const float g = d > 0.0 ? float(2.0 * double(AE[size_t(img) * npix + p]) / d) : 0.f;
+  uint32_t* o = reinterpret_cast<uint32_t*>(dY + (size_t(img) * npix + p) * 16);
+  o[0] = pack2(__float2bfloat16(g), __float2bfloat16(0.f));
+#pragma unroll
+  for (int q = 1; q < 8; ++q) o[q] = 0u;
+}
+
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, int64_t cnt, float lr, float b1, float b2, float eps, float c1,
                        float c2) {
@@ -380,9 +420,11 @@ int64_t cnn_param_count() {
   return c;
 }
 
-sg_status Cnn::init(const std::vector<double>& logdiag, int H_, int W_) {
+sg_status Cnn::init(const std::vector<double>& logdiag, int H_, int W_, const std::vector<int32_t>& rowptr,
+                    const std::vector<int32_t>& colidx, const std::vector<double>& a0) {
   H = H_;
   W = W_;
+  SG_TRY(A0.upload(int64_t(H_) * W_, int64_t(H_) * W_, rowptr, colidx, a0));
   const int64_t np = cnn_param_count_padded();
   SG_TRY(params.alloc(np * 4));
   SG_TRY(grads.alloc(np * 4));
@@ -415,6 +457,7 @@ sg_status Cnn::reserve(int nimg) {
   SG_TRY(gbuf[1].alloc(size_t(nimg) * npix * 32 * 2));
   SG_TRY(out.alloc(size_t(nimg) * npix * 4));
   SG_TRY(ztgt.alloc(size_t(nimg) * npix * 4));
+  for (DevBuf* b : {&ebuf, &aebuf, &azbuf}) SG_TRY(b->alloc(size_t(nimg) * npix * 4));
   if (nimg > 4096) {
     SG_TRY(sumsq.alloc(size_t(nimg) * 8));
     SG_TRY(lossbuf.alloc(size_t(2) * nimg * 8));
@@ -554,9 +597,19 @@ sg_status Cnn::loss_and_grad(int nimg, double* host_loss, cudaStream_t st) {
   double* num = dp<double>(lossbuf);
   double* den = num + nimg;
   SG_CUDA(cudaMemsetAsync(num, 0, size_t(2) * nimg * 8, st));
-  k_loss_parts<<<dim3(64, unsigned(nimg)), 256, 0, st>>>(dp<float>(out), Zs, npix, num, den); note_launch();
-  k_loss_grad<<<dim3(unsigned((npix + 255) / 256), unsigned(nimg)), 256, 0, st>>>(dp<float>(out), Zs, npix, den,
-                                                                                 dp<bf16>(gbuf[0])); note_launch();
+  const dim3 gimg(unsigned((npix + 255) / 256), unsigned(nimg));
+  if (loss_kind == 0) {
+    const int64_t cnt = int64_t(nimg) * npix;
+    k_diff<<<4 * 152, 256, 0, st>>>(dp<float>(out), Zs, dp<float>(ebuf), cnt); note_launch();
+    SG_TRY(spmm<float>(A0, dp<float>(ebuf), npix, nullptr, 0, dp<float>(aebuf), npix, nimg, 0, st));
+    SG_TRY(spmm<float>(A0, Zs, npix, nullptr, 0, dp<float>(azbuf), npix, nimg, 0, st));
+    k_energy_parts<<<dim3(64, unsigned(nimg)), 256, 0, st>>>(dp<float>(ebuf), dp<float>(aebuf), Zs, dp<float>(azbuf),
+                                                             npix, num, den); note_launch();
+    k_energy_grad<<<gimg, 256, 0, st>>>(dp<float>(aebuf), npix, den, dp<bf16>(gbuf[0])); note_launch();
+  } else {
+    k_loss_parts<<<dim3(64, unsigned(nimg)), 256, 0, st>>>(dp<float>(out), Zs, npix, num, den); note_launch();
+    k_loss_grad<<<gimg, 256, 0, st>>>(dp<float>(out), Zs, npix, den, dp<bf16>(gbuf[0])); note_launch();
+  }
   SG_CUDA(cudaGetLastError());
   if (host_loss) {
     std::vector<double> h(size_t(2) * nimg);

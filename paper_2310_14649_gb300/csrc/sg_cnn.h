@@ -20,12 +20,16 @@ struct Cnn {
   DevBuf act[5], gbuf[2], out, ztgt;     // activations, gradients, FP32 output, targets
   DevBuf sumsq, lossbuf;                 // per-image scalars
   MeanSolver* mean = nullptr;            // batched A_0 solves (training targets)
+  int loss_kind = 0;                     // 0 energy norm of A_0, 1 relative L2 error
+  DevCsr A0;                             // fine mean matrix (energy loss)
+  DevBuf ebuf, aebuf, azbuf;             // error, A_0 error, A_0 target (energy loss)
   Cnn() = default;
   Cnn(const Cnn&) = delete;
   Cnn& operator=(const Cnn&) = delete;
   ~Cnn();
 
-  sg_status init(const std::vector<double>& logdiag, int H, int W);
+  sg_status init(const std::vector<double>& logdiag, int H, int W, const std::vector<int32_t>& rowptr,
+                 const std::vector<int32_t>& colidx, const std::vector<double>& a0);
   sg_status reserve(int nimg);
   sg_status set_weights(const float* host_oracle_layout, cudaStream_t st);
   sg_status get_weights(float* host_oracle_layout, bool grad, cudaStream_t st);

@@ -213,6 +213,16 @@ inline sg_status gmres_run(KrylovWork<T>& W, const Op<T>& A, const Op<T>& M, con
 // --------------------------------------------------------------------------
 // Per-precision solver context: operator, preconditioner and workspaces.
 // --------------------------------------------------------------------------
+// Kernel nodes of a recorded loop nest: outside the loops, per restart
+// cycle, per Arnoldi iteration (nested loops excluded).  The launch count
+// adds them for the executions the device counters report.
+struct RegionCounts {
+  int64_t fixed = 0, restart = 0, iter = 0;
+  int64_t total(int64_t calls, int64_t restarts, int64_t iters) const {
+    return calls * fixed + restarts * restart + iters * iter;
+  }
+};
+
 template <typename T>
 struct SolverCtx;
 // Records a device-driven coarse GMRES solve r_c -> e_c (the 2GV3 inner
@@ -235,6 +245,8 @@ struct SolverCtx {
   // device-driven fine FGMRES (graph-captured solves)
   DevBuf fdg_iv, fdg_tol;
   DevGmres fdg{};
+  RegionCounts cc_coarse, cc_fine;  // kernel nodes per region of the recorded loops
+  int64_t coarse_graph_launches = 0;
   cudaGraphExec_t cexec = nullptr;
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
   std::vector<DevBuf> amgbuf;     // b, x, t per level
@@ -360,13 +372,31 @@ struct SolverCtx {
   }
   // iteration counters summed over solves (device): fine FGMRES, coarse GMRES
   sg_status clear_counters(cudaStream_t st) {
-    SG_CUDA(cudaMemsetAsync(fdg.iv + 4, 0, sizeof(int), st));
-    SG_CUDA(cudaMemsetAsync(dg.iv + 4, 0, sizeof(int), st));
+    for (int* iv : {fdg.iv, dg.iv}) {
+      SG_CUDA(cudaMemsetAsync(iv + 4, 0, sizeof(int), st));
+      SG_CUDA(cudaMemsetAsync(iv + 6, 0, sizeof(int), st));
+    }
+    coarse_graph_launches = 0;
     return SG_OK;
   }
-  sg_status read_counters(int* fine_its, int* coarse_its) {
-    SG_CUDA(cudaMemcpy(fine_its, fdg.iv + 4, sizeof(int), cudaMemcpyDeviceToHost));
-    SG_CUDA(cudaMemcpy(coarse_its, dg.iv + 4, sizeof(int), cudaMemcpyDeviceToHost));
+  // fine and coarse iterations and restart cycles summed since clear_counters
+  sg_status read_counters(int* fine_its, int* coarse_its, int* fine_restarts = nullptr,
+                          int* coarse_restarts = nullptr) {
+    int f[8], c[8];
+    SG_CUDA(cudaMemcpy(f, fdg.iv, sizeof f, cudaMemcpyDeviceToHost));
+    SG_CUDA(cudaMemcpy(c, dg.iv, sizeof c, cudaMemcpyDeviceToHost));
+    *fine_its = f[4];
+    *coarse_its = c[4];
+    if (fine_restarts) *fine_restarts = f[6];
+    if (coarse_restarts) *coarse_restarts = c[6];
+    return SG_OK;
+  }
+  // kernels run inside the standalone coarse-solve graph launches since
+  // clear_counters (host-driven solves)
+  sg_status coarse_graph_kernels(int64_t* out) {
+    int fits = 0, cits = 0, fr = 0, cr = 0;
+    SG_TRY(read_counters(&fits, &cits, &fr, &cr));
+    *out = cc_coarse.total(coarse_graph_launches, cr, cits);
     return SG_OK;
   }
 
@@ -413,6 +443,7 @@ struct SolverCtx {
   sg_status coarse_solve_graph(cudaStream_t st) {
     if (!cexec) SG_TRY(build_coarse_graph());
     SG_CUDA(cudaGraphLaunch(cexec, st));
+    ++coarse_graph_launches;
     return SG_OK;
   }
 

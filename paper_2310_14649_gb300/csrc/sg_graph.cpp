@@ -46,6 +46,7 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
   const int64_t ldc = c.ldc, lenc = c.lenc;
   const int* jdev = c.dg.iv;
 
+  const int64_t k0 = launch_count();
   cudaStreamCaptureStatus cs;
   cudaGraph_t g;
   SG_CUDA(cudaStreamGetCaptureInfo(s1, &cs, nullptr, &g, nullptr, nullptr, nullptr));
@@ -54,6 +55,8 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
   SG_CUDA(cudaMemsetAsync(Ec, 0, lenc * sizeof(T), s1));
   SG_TRY(vec_norm2<T>(Rc, lenc, W.s.scal + 5, part, cnt, s1));
   SG_TRY(dg_init(c.dg, W.s.scal + 5, pc.inner_rtol, hout, s1));
+  const int64_t k1 = launch_count();
+  int64_t k2 = 0, k3 = 0;
   cudaGraph_t body_out;
   SG_TRY(SolverCtx<T>::add_while(s1, hout, &body_out));
   {
@@ -66,6 +69,7 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
     SG_TRY(vec_scale_by<T>(V, V, lenc, W.s.scal + 3, true, s2));
     cudaGraph_t body_in;
     SG_TRY(SolverCtx<T>::add_while(s2, hin, &body_in));
+    k2 = launch_count();
     {
       SG_CUDA(cudaStreamBeginCaptureToGraph(s3, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       SG_TRY(dg_copy_vj<T>(V, lenc, ldc, c.aw.b[0], L0.ld, pc.co.nc, c.pr->P, c.dg, s3));
@@ -79,6 +83,7 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
       SG_TRY(dg_scale_next<T>(w, V, lenc, lenc, c.dg, W.s.scal + 1, s3));
       SG_CUDA(cudaStreamEndCapture(s3, &body_in));
     }
+    k3 = launch_count();
     // x += M (V y)
     SG_TRY(dg_backsolve(c.dg, W.s, m, s2));
     SG_CUDA(cudaMemsetAsync(tmp2, 0, lenc * sizeof(T), s2));
@@ -90,6 +95,9 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
     SG_TRY(dg_end(c.dg, W.s, hout, s2));
     SG_CUDA(cudaStreamEndCapture(s2, &body_out));
   }
+  const int64_t k4 = launch_count();
+  c.cc_coarse = RegionCounts{k1 - k0, (k2 - k1) + (k4 - k3), k3 - k2};
+  note_launches(-(k4 - k0));  // recorded, not launched
   return SG_OK;
 }
 
@@ -148,6 +156,7 @@ static sg_status capture_fine(SolverCtx<T>& c, const T* b, T* x, double rtol, bo
   const int* jdev = c.fdg.iv;
   const cudaStream_t f2 = S.s[2], f3 = S.s[3];
 
+  const int64_t k0 = launch_count();
   SG_TRY(vec_norm2<T>(b, len, W.s.scal + 5, part, cnt, top));
   cudaStreamCaptureStatus cs;
   cudaGraph_t g;
@@ -155,6 +164,8 @@ static sg_status capture_fine(SolverCtx<T>& c, const T* b, T* x, double rtol, bo
   cudaGraphConditionalHandle hout, hin;
   SG_CUDA(cudaGraphConditionalHandleCreate(&hout, g, 0, 0));
   SG_TRY(dg_init(c.fdg, W.s.scal + 5, rtol, hout, top));
+  const int64_t k1 = launch_count();
+  int64_t k2 = 0, k3 = 0;
   cudaGraph_t body_out;
   SG_TRY(SolverCtx<T>::add_while(top, hout, &body_out));
   {
@@ -167,6 +178,7 @@ static sg_status capture_fine(SolverCtx<T>& c, const T* b, T* x, double rtol, bo
     SG_TRY(vec_scale_by<T>(V, V, len, W.s.scal + 3, true, f2));
     cudaGraph_t body_in;
     SG_TRY(SolverCtx<T>::add_while(f2, hin, &body_in));
+    k2 = launch_count();
     {
       SG_CUDA(cudaStreamBeginCaptureToGraph(f3, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       // Z_j = B V_j, w = A Z_j, CGS2 against V_0..V_j, rotation, V_{j+1}
@@ -182,12 +194,16 @@ static sg_status capture_fine(SolverCtx<T>& c, const T* b, T* x, double rtol, bo
       SG_TRY(dg_scale_next<T>(w, V, len, len, c.fdg, W.s.scal + 1, f3));
       SG_CUDA(cudaStreamEndCapture(f3, &body_in));
     }
+    k3 = launch_count();
     // x += Z y
     SG_TRY(dg_backsolve(c.fdg, W.s, m, f2));
     SG_TRY(dg_axpy_multi<T>(Zs, len, W.s.y, x, len, jdev, f2));
     SG_TRY(dg_end(c.fdg, W.s, hout, f2, trust));
     SG_CUDA(cudaStreamEndCapture(f2, &body_out));
   }
+  const int64_t k4 = launch_count();
+  c.cc_fine = RegionCounts{k1 - k0, (k2 - k1) + (k4 - k3), k3 - k2};
+  note_launches(-(k4 - k0));  // recorded, not launched
   return SG_OK;
 }
 
@@ -197,14 +213,24 @@ struct GraphSystem {
   uint64_t serial = 0;
   const void* ctx64 = nullptr;  // the workspaces the graph was recorded with
   const void* ctx32 = nullptr;
+  RegionCounts ir;              // refinement loop: fixed, -, per step
   CapStreams streams;
 };
+
+static sg_status capture_system_nodes(GraphSystem& gs, const sg_solve_opts& o, cudaStream_t top);
 
 // Records the solve of one system on `top` (already capturing):
 // mode 1: x64 += corrections of FP32 FGMRES solves of the normalised FP64
 //         residual, until relres <= rtol (refinement loop as a WHILE node);
 // mode 0: FP64 FGMRES on F64 from x64.
 static sg_status capture_system(GraphSystem& gs, const sg_solve_opts& o, cudaStream_t top) {
+  const int64_t k0 = launch_count();
+  const sg_status s = capture_system_nodes(gs, o, top);
+  note_launches(-(launch_count() - k0));  // recorded, not launched
+  return s;
+}
+
+static sg_status capture_system_nodes(GraphSystem& gs, const sg_solve_opts& o, cudaStream_t top) {
   sg_problem* pr = gs.pr;
   SolverState& S = *pr->solver;
   const int64_t len = int64_t(pr->P) * pr->ld;
@@ -217,6 +243,7 @@ static sg_status capture_system(GraphSystem& gs, const sg_solve_opts& o, cudaStr
   ProfilerOff off(pr->prof);
   if (o.mode == 0) {
     SG_TRY(vec_norm2<double>(F64, len, ird + 1, dp<double>(c64->fine.partial), dp<unsigned>(c64->fine.counter), top));
+    gs.ir = RegionCounts{1, 0, 0};
     return capture_fine<double>(*c64, F64, x64, o.rtol, false, gs.streams, top);
   }
   SolverCtx<float>* c32 = nullptr;
@@ -229,6 +256,7 @@ static sg_status capture_system(GraphSystem& gs, const sg_solve_opts& o, cudaStr
   const double inner = o.inner_rtol > 0 ? o.inner_rtol : 1e-4;
   const int max_ir = o.max_ir > 0 ? o.max_ir : 20;
   const cudaStream_t i2 = gs.streams.s[1];
+  const int64_t k0 = launch_count();
   SG_TRY(vec_norm2<double>(F64, len, ird + 1, part, cnt, top));
   SG_TRY(c64->apply_raw_fine(x64, r64, F64, top));
   SG_TRY(vec_norm2<double>(r64, len, ird, part, cnt, top));
@@ -238,6 +266,7 @@ static sg_status capture_system(GraphSystem& gs, const sg_solve_opts& o, cudaStr
   SG_CUDA(cudaStreamGetCaptureInfo(top, &cs, nullptr, &g, nullptr, nullptr, nullptr));
   SG_CUDA(cudaGraphConditionalHandleCreate(&hir, g, 0, 0));
   SG_TRY(ir_decide(ird, ird + 1, iri, o.rtol, max_ir, c32->fdg.iv + 4, o.max_it, hir, top));
+  const int64_t k1 = launch_count();
   cudaGraph_t body;
   SG_TRY(SolverCtx<float>::add_while(top, hir, &body));
   SG_CUDA(cudaStreamBeginCaptureToGraph(i2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
@@ -249,6 +278,7 @@ static sg_status capture_system(GraphSystem& gs, const sg_solve_opts& o, cudaStr
   SG_TRY(vec_norm2<double>(r64, len, ird, part, cnt, i2));
   SG_TRY(ir_decide(ird, ird + 1, iri, o.rtol, max_ir, c32->fdg.iv + 4, o.max_it, hir, i2));
   SG_CUDA(cudaStreamEndCapture(i2, &body));
+  gs.ir = RegionCounts{k1 - k0, 0, launch_count() - k1};
   return SG_OK;
 }
 
@@ -436,11 +466,19 @@ sg_status sg_batch_solve(sg_batch* B, const double* const* F, const int64_t* ldf
     int iv[8];
     SG_CUDA(cudaMemcpy(d, S.ir_d.ptr, sizeof d, cudaMemcpyDeviceToHost));
     SG_CUDA(cudaMemcpy(iv, S.ir_i.ptr, sizeof iv, cudaMemcpyDeviceToHost));
-    int fits = 0, cits = 0;
-    if (B->opts.mode == 1)
-      SG_TRY(S.c32->read_counters(&fits, &cits));
+    int fits = 0, cits = 0, fr = 0, cr = 0;
+    const bool m1 = B->opts.mode == 1;
+    const RegionCounts& cf = m1 ? S.c32->cc_fine : S.c64->cc_fine;
+    const RegionCounts& cc = m1 ? S.c32->cc_coarse : S.c64->cc_coarse;
+    if (m1)
+      SG_TRY(S.c32->read_counters(&fits, &cits, &fr, &cr));
     else
-      SG_TRY(S.c64->read_counters(&fits, &cits));
+      SG_TRY(S.c64->read_counters(&fits, &cits, &fr, &cr));
+    // kernels the graph ran for this system: refinement steps, FGMRES
+    // solves (one per step), two-level cycles with their coarse solves (one
+    // per FGMRES iteration)
+    const int64_t steps = m1 ? iv[0] : 0, fine_calls = m1 ? steps : 1;
+    note_launches(B->sys[i].ir.total(1, 0, steps) + cf.total(fine_calls, fr, fits) + cc.total(fits, cr, cits));
     sg_solve_info inf{};
     inf.outer_it = fits;
     inf.inner_it = cits;

@@ -14,6 +14,10 @@ namespace sg {
 void set_error(const std::string& msg);
 // process-wide count of kernel launches made by the library
 void note_launch();
+// adds n (possibly negative) to the launch count: kernels executed inside
+// graphs, minus kernel nodes counted while a graph was being recorded
+void note_launches(int64_t n);
+int64_t launch_count();
 int64_t launch_count();
 
 #define SG_CUDA(call)                                                                    \

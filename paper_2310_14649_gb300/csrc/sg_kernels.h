@@ -72,7 +72,8 @@ sg_status gmres_init(GmresState s, int m, const double* beta, cudaStream_t st);
 
 // Device-driven GMRES state: iv[0] j, iv[1] iterations of this solve,
 // iv[2] iteration cap, iv[3] stop flag, iv[4] iterations summed over
-// solves, iv[5] breakdown flag; dtol[0] absolute tolerance.
+// solves, iv[5] breakdown flag, iv[6] restart cycles summed over solves;
+// dtol[0] absolute tolerance.
 struct DevGmres {
   int* iv;
   double* dtol;

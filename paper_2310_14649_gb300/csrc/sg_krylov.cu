@@ -340,6 +340,7 @@ __global__ void k_dg_start(DevGmres d, GmresState s, int m, const double* __rest
   if (threadIdx.x == 0) {
     // scal[3] keeps beta^2: the normalisation of V_0 that follows reads it
     d.iv[0] = 0;
+    d.iv[6] += 1;  // restart cycles summed over solves
     const bool go = beta > d.dtol[0] && isfinite(beta) && d.iv[1] < d.iv[2];
     if (!go) d.iv[3] = 1;
     cudaGraphSetConditional(inner, go ? 1u : 0u);

@@ -28,7 +28,7 @@ sg_status ensure_cnn(sg_problem* pr) {
     for (int32_t t = pr->rowptr[r]; t < pr->rowptr[r + 1]; ++t)
       if (pr->colidx[t] == r) logd[r] = std::log(pr->a0[t] / 4.0);
   Cnn* c = new Cnn();
-  sg_status s = c->init(logd, m, m);
+  sg_status s = c->init(logd, m, m, pr->rowptr, pr->colidx, pr->a0);
   if (s != SG_OK) {
     delete c;
     return s;
@@ -122,6 +122,14 @@ sg_status sg_cnn_train_step(sg_problem* pr, const float* R, int64_t ldr, const f
   return SG_OK;
 }
 
+sg_status sg_cnn_set_loss(sg_problem* pr, int kind) {
+  SG_ARG(pr, "sg_cnn_set_loss: NULL handle");
+  SG_ARG(kind == 0 || kind == 1, "sg_cnn_set_loss: kind must be 0 (energy norm) or 1 (relative L2)");
+  SG_TRY(ensure_cnn(pr));
+  pr->cnn->loss_kind = kind;
+  return SG_OK;
+}
+
 sg_status sg_mean_solve(sg_problem* pr, const float* B, int64_t ldb, float* Z, int64_t ldz, int nb, double rtol,
                         int max_it, double* relres_max, int* its, void* stream) {
   SG_ARG(pr && B && Z, "sg_mean_solve: NULL argument");
@@ -152,6 +160,7 @@ sg_status sg_train_precond(sg_problem* pr, const sg_train_opts* o, sg_train_info
   SG_ARG(o->n_pairs >= 1 && o->epochs >= 0 && o->batch >= 1 && o->batch <= o->n_pairs,
          "sg_train_precond: need n_pairs >= 1, epochs >= 0, 1 <= batch <= n_pairs");
   SG_ARG(o->lr > 0, "sg_train_precond: lr must be > 0");
+  SG_ARG(o->loss == 0 || o->loss == 1, "sg_train_precond: loss must be 0 (energy norm) or 1 (relative L2)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Precond& pc = precond_of(pr);
   const int P = pr->P;
@@ -165,6 +174,7 @@ sg_status sg_train_precond(sg_problem* pr, const sg_train_opts* o, sg_train_info
   }
   const int prev_smoother = pc.smoother;
   pc.smoother = 0;
+  cnn.loss_kind = o->loss;
 
   // 1. harvest smoother inputs of plain mixed-precision solves: first with
   //    the problem's load vector, then with seeded Gaussian right-hand sides

@@ -381,9 +381,8 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
   } clear_cnn{S.pc};
   S.pc.inner_its_total = 0;
   S.pc.inner_calls = 0;
-  const int zero = 0;
-  SG_CUDA(cudaMemcpy(c64->dg.iv + 4, &zero, sizeof(int), cudaMemcpyHostToDevice));
-  if (S.c32) SG_CUDA(cudaMemcpy(S.c32->dg.iv + 4, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  SG_TRY(c64->clear_counters(st));
+  if (S.c32) SG_TRY(S.c32->clear_counters(st));
   sg_status status = SG_OK;
   if (nF == 0.0) {
     SG_CUDA(cudaMemsetAsync(x64, 0, len * 8, st));
@@ -467,11 +466,23 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
   inf.relres = nF > 0 ? std::sqrt(S.host[2]) / nF : 0.0;
   inf.inner_it = S.pc.inner_its_total;
   if (S.pc.device_loops) {
-    int dev_its = 0;
-    SolverCtx<float>* c32u = o->mode == 1 ? S.c32.get() : nullptr;
-    if (c32u) SG_CUDA(cudaMemcpy(&dev_its, c32u->dg.iv + 4, sizeof(int), cudaMemcpyDeviceToHost));
-    else SG_CUDA(cudaMemcpy(&dev_its, c64->dg.iv + 4, sizeof(int), cudaMemcpyDeviceToHost));
-    inf.inner_it += dev_its;
+    // coarse iterations and the kernels the coarse-solve graphs ran (the
+    // launch count sees each graph launch only on the host)
+    int64_t graph_kernels = 0;
+    for (int which = 0; which < 2; ++which) {
+      int fits = 0, cits = 0;
+      int64_t k = 0;
+      if (which == 0) {
+        SG_TRY(c64->read_counters(&fits, &cits));
+        SG_TRY(c64->coarse_graph_kernels(&k));
+      } else if (S.c32) {
+        SG_TRY(S.c32->read_counters(&fits, &cits));
+        SG_TRY(S.c32->coarse_graph_kernels(&k));
+      }
+      inf.inner_it += cits;
+      graph_kernels += k;
+    }
+    note_launches(graph_kernels);
   }
   inf.t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (o->hist_host && o->hist_cap > 0) {

@@ -109,11 +109,13 @@ def test_gradient_matches_oracle(pair):
     prob, ref = pair
     params = params_for(9)
     sg.sg_cnn_set_weights(prob, params)
+    sg.sg_cnn_set_loss(prob, 1)
     P = ref.P
     R = random_block(ref.n, P, seed=72).astype(np.float32).astype(np.float64)
     A0 = ref.A(0).tocsc()
     Zs = np.column_stack([spla.spsolve(A0, R[:, a]) for a in range(P)]).astype(np.float32).astype(np.float64)
     loss = sg.sg_cnn_train_step(prob, dev_rows(R), dev_rows(Zs), update=False)
+    sg.sg_cnn_set_loss(prob, 0)
     g = sg.sg_cnn_get_weights(prob, gradient=True)
     # the weights are unchanged by a step without update
     np.testing.assert_array_equal(sg.sg_cnn_get_weights(prob), sg.cnn_flatten(params))
@@ -127,6 +129,33 @@ def test_gradient_matches_oracle(pair):
     assert abs(loss - L) <= 2e-2 * L
     gl = sg.cnn_unflatten(g)
     for l, ((dW, db), (gW, gb)) in enumerate(zip(grads, gl)):
+        assert np.linalg.norm(gW - dW) <= 5e-2 * np.linalg.norm(dW), l
+        assert np.linalg.norm(gb - db) <= 5e-2 * np.linalg.norm(db) + 1e-6, l
+
+
+def test_energy_gradient_matches_oracle(pair):
+    """The energy-norm loss (A_0 applied to the error on the device) and
+    its gradients against the oracle."""
+    import paper_2310_14649_gb300 as sg
+    prob, ref = pair
+    params = params_for(12)
+    sg.sg_cnn_set_weights(prob, params)
+    sg.sg_cnn_set_loss(prob, 0)
+    P = ref.P
+    R = random_block(ref.n, P, seed=77).astype(np.float32).astype(np.float64)
+    A0 = ref.A(0).tocsc()
+    Zs = np.column_stack([spla.spsolve(A0, R[:, a]) for a in range(P)]).astype(np.float32).astype(np.float64)
+    loss = sg.sg_cnn_train_step(prob, dev_rows(R), dev_rows(Zs), update=False)
+    g = sg.cnn_unflatten(sg.sg_cnn_get_weights(prob, gradient=True))
+    x, rms = oracle_features(ref, R)
+    m = ref.N - 1
+    zt = (Zs / rms[None, :]).T.reshape(P, m, m, 1)
+    pr = rounded(params)
+    y, acts = cnn.forward(pr, x)
+    L, dy = cnn.loss_energy(y, zt, ref.A(0))
+    grads, _ = cnn.backward(pr, acts, dy)
+    assert abs(loss - L) <= 3e-2 * L
+    for l, ((dW, db), (gW, gb)) in enumerate(zip(grads, g)):
         assert np.linalg.norm(gW - dW) <= 5e-2 * np.linalg.norm(dW), l
         assert np.linalg.norm(gb - db) <= 5e-2 * np.linalg.norm(db) + 1e-6, l
 

@@ -66,3 +66,37 @@ def test_he_init_scale():
     W = p[1][0]
     assert W.shape == (3, 3, 32, 32)
     assert abs(W.std() - np.sqrt(2.0 / 288)) < 0.05 * np.sqrt(2.0 / 288)
+
+
+def test_energy_loss_gradient_and_special_cases():
+    """The energy-norm loss: its gradient by central differences through the
+    network, the value for A_0 = I equals the plain relative squared error,
+    and it is zero at the target."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(3)
+    m = 5
+    T = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(m, m))
+    A0 = (sp.kron(sp.identity(m), T) + sp.kron(T, sp.identity(m))).tocsr()
+    params = [(rng.standard_normal((3, 3, ci, co)) * 0.4, rng.standard_normal(co) * 0.1)
+              for ci, co in [(2, 3), (3, 1)]]
+    x = rng.standard_normal((2, m, m, 2))
+    zs = rng.standard_normal((2, m, m, 1))
+
+    def L(p):
+        y, _ = cnn.forward(p, x)
+        return cnn.loss_energy(y, zs, A0)[0]
+    y, acts = cnn.forward(params, x)
+    _, dy = cnn.loss_energy(y, zs, A0)
+    grads, _ = cnn.backward(params, acts, dy)
+    h = 1e-6
+    for l, which, idx in [(0, 0, (2, 1, 1, 2)), (1, 0, (0, 2, 1, 0)), (0, 1, (1,)), (1, 1, (0,))]:
+        pp = [(W.copy(), b.copy()) for W, b in params]
+        pm = [(W.copy(), b.copy()) for W, b in params]
+        pp[l][which][idx] += h
+        pm[l][which][idx] -= h
+        num = (L(pp) - L(pm)) / (2 * h)
+        assert abs(num - grads[l][which][idx]) <= 1e-6 * max(1.0, abs(num))
+    eye = sp.identity(m * m, format="csr")
+    assert abs(cnn.loss_energy(y, zs, eye)[0] - cnn.loss(y, zs)[0]) <= 1e-12 * cnn.loss(y, zs)[0]
+    L0, g0 = cnn.loss_energy(zs, zs, A0)
+    assert L0 == 0.0 and np.all(g0 == 0.0)
