@@ -246,7 +246,8 @@ def extra_measurements(sg, torch, prob, stream):
         p = sg.sg_setup(cc["N"], cc["L"], cc["p"], cc["q"], sigma2=cc["sigma2"], bx=cc["b"], by=cc["b"])
         sg.sg_apply_autotune(p)
         sg.sg_precond_setup(p, cc["sx"], cc["sy"], cc["overlap"], inner_rtol=INNER_RTOL)
-        sg.sg_apply_autotune(p, which=1)
+        for which in (1, 2):
+            sg.sg_apply_autotune(p, which=which)
         probs.append(p)
     t_setup = time.perf_counter() - t0
     Xs = [torch.zeros((p.P, p.n), dtype=torch.float64, device="cuda") for p in probs]
@@ -344,7 +345,8 @@ def main():
     torch.cuda.synchronize()
     t_pc = time.perf_counter() - t0
     t0 = time.perf_counter()
-    sg.sg_apply_autotune(prob, which=1)        # coarse operator, cached too
+    for which in (1, 2, 3):                    # coarse FP32, fine and coarse FP64, cached too
+        sg.sg_apply_autotune(prob, which=which)
     t_tune += time.perf_counter() - t0
     n, P = prob.n, prob.P
     X = torch.zeros((P, n), dtype=torch.float64, device="cuda")
@@ -450,6 +452,7 @@ def main():
                   "setup_s": round(t_setup, 3), "precond_setup_s": round(t_pc, 3),
                   "apply_tuning_s": round(t_tune, 3), "apply_shape": sg.sg_apply_info(prob),
                   "coarse_apply_shape": sg.sg_apply_info(prob, which=1),
+                  "fine_apply_shape_f64": sg.sg_apply_info(prob, which=2),
                   "solves_per_s_all_gpus": round(world * 1e3 / ms_all, 3)},
         "plain_fp64": {"ms": round(ms64, 3), "outer_it": info64["outer_it"], "relres": info64["relres"],
                        "speedup_mixed": round(ms64 / ms_all, 3)},

@@ -125,10 +125,11 @@ sg_status sg_get_rhs(const sg_problem* prob, double* F_dev, int64_t ld, void* st
 sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t ldx, void* Y_dev,
                    int64_t ldy, void* stream);
 
-/* Kernel used by the FP32 applies of this handle (fine and coarse):
+/* Kernel used by the applies of this handle (fine and coarse, FP32 and
+ * FP64):
  *   0 auto (default): the register-specialised kernel when P <= 128 and
  *     T <= 40000, else the shared-memory kernel;
- *   1 the shared-memory kernel (any size; FP64 always uses it);
+ *   1 the shared-memory kernel (any size);
  *   2 the register-specialised kernel (SG_ERR_UNSUPPORTED if too large).
  * The specialised kernel is generated from the triple list, compiled for
  * sm_103a with NVRTC on first use and cached on disk (SG_JIT_CACHE, default
@@ -136,9 +137,10 @@ sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t 
  * Errors: SG_ERR_CUDA with the compiler log when compilation fails. */
 sg_status sg_set_apply_kernel(sg_problem* prob, int mode);
 
-/* Tile shape of the register-specialised kernel of the fine (which = 0)
- * or coarse (which = 1) operator family: rows per thread (1, or 2 adjacent
- * rows updated with the paired FP32 FMA); output groups, input groups
+/* Tile shape of the register-specialised kernel of one family: which = 0
+ * fine FP32, 1 coarse FP32, 2 fine FP64, 3 coarse FP64 (the FP64 kernels
+ * carry the triple products as exact double immediates): rows per thread
+ * (1, or for FP32 2 adjacent rows updated with the paired FP32 FMA); output groups, input groups
  * (1..4 each) and stencil-slot groups (1..8), product <= 8: the outputs,
  * the gathered inputs and the slots are split across groups of 4 warps
  * whose partial sums meet in shared memory; prefetch (input terms whose
@@ -149,8 +151,8 @@ sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int
                           int prefetch, int min_blocks);
 
 /* Autotuner: compiles the candidate tile shapes, times each on this
- * problem's fine (which = 0) or coarse (which = 1, after
- * sg_precond_setup) operator with CUDA events, keeps the fastest and stores
+ * problem's operator of family `which` (as for sg_apply_config; the
+ * coarse families after sg_precond_setup) with CUDA events, keeps the fastest and stores
  * the choice in the kernel cache directory (keyed by the triple structure,
  * rows, slots and the device name) so later setups reuse it unless
  * force != 0.  best_ms (may be NULL) receives the time of the chosen shape.

@@ -69,8 +69,7 @@ sg_status sg_destroy(sg_problem* pr) {
   if (!pr) return SG_OK;
   solver_free(pr);
   cnn_free(pr);
-  jit_free(pr, 0);
-  jit_free(pr, 1);
+  for (int w = 0; w < kJitFamilies; ++w) jit_free(pr, w);
   pr->mdot_partial.free_();
   pr->mdot_counter.free_();
   pr->fine.col.free_();
@@ -98,7 +97,7 @@ sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
 
 sg_status sg_apply_config(sg_problem* pr, int which, int rows, int groups, int igroups, int sgroups, int prefetch,
                           int min_blocks) {
-  SG_ARG(pr && (which == 0 || which == 1), "sg_apply_config: NULL handle or which not in {0, 1}");
+  SG_ARG(pr && which >= 0 && which < kJitFamilies, "sg_apply_config: NULL handle or which not in [0, 3]");
   JitConfig c;
   c.rows = rows;
   c.groups = groups;
@@ -110,12 +109,12 @@ sg_status sg_apply_config(sg_problem* pr, int which, int rows, int groups, int i
 }
 
 sg_status sg_apply_autotune(sg_problem* pr, int which, int force, double* best_ms) {
-  SG_ARG(pr && (which == 0 || which == 1), "sg_apply_autotune: NULL handle or which not in {0, 1}");
+  SG_ARG(pr && which >= 0 && which < kJitFamilies, "sg_apply_autotune: NULL handle or which not in [0, 3]");
   return jit_autotune(pr, which, force, best_ms);
 }
 
 sg_status sg_apply_info(const sg_problem* pr, int which, int* cfg7, double* compile_s) {
-  SG_ARG(pr && (which == 0 || which == 1), "sg_apply_info: NULL handle or which not in {0, 1}");
+  SG_ARG(pr && which >= 0 && which < kJitFamilies, "sg_apply_info: NULL handle or which not in [0, 3]");
   const JitConfig c = pr->jit_cfg_set[which] ? pr->jit_cfg[which] : jit_default_config(pr, which);
   if (cfg7) {
     cfg7[0] = c.rows;

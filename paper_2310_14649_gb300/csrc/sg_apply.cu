@@ -191,10 +191,9 @@ sg_status apply_op(sg_problem* pr, bool coarse, const T* X, int64_t ldx, const T
   size_t slot = 0;
   const bool on = pr->prof.on;
   if (on) SG_TRY(pr->prof.begin((coarse ? 2 : 0) + (sizeof(T) == 8 ? 1 : 0), st, slot));
-  const bool spec = sizeof(T) == 4 && pr->apply_mode != 1 && jit_eligible(pr);
+  const bool spec = pr->apply_mode != 1 && jit_eligible(pr);
   if (spec) {
-    SG_TRY(jit_apply_launch(pr, coarse ? 1 : 0, A, reinterpret_cast<const float*>(X), ldx,
-                            reinterpret_cast<const float*>(F), ldf, reinterpret_cast<float*>(Y), ldy, st));
+    SG_TRY(jit_apply_launch(pr, (coarse ? 1 : 0) + (sizeof(T) == 8 ? 2 : 0), A, X, ldx, F, ldf, Y, ldy, st));
   } else {
     SG_TRY(apply_ell<T>(A, tri, pr->P, pr->K, X, ldx, F, ldf, Y, ldy, st));
   }

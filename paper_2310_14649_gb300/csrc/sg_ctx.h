@@ -365,9 +365,8 @@ struct SolverCtx {
 
   // fine apply without the profiler (Y = F - A X when F, else A X)
   sg_status apply_raw_fine(const T* X, T* Y, const T* F, cudaStream_t st) {
-    if (sizeof(T) == 4 && pr->apply_mode != 1 && jit_eligible(pr))
-      return jit_apply_launch(pr, 0, pr->fine, reinterpret_cast<const float*>(X), ld,
-                              reinterpret_cast<const float*>(F), ld, reinterpret_cast<float*>(Y), ld, st);
+    if (pr->apply_mode != 1 && jit_eligible(pr))
+      return jit_apply_launch(pr, sizeof(T) == 8 ? 2 : 0, pr->fine, X, ld, F, ld, Y, ld, st);
     return apply_ell<T>(pr->fine, pr->tri, pr->P, pr->K, X, ld, F, ld, Y, ld, st);
   }
   // iteration counters summed over solves (device): fine FGMRES, coarse GMRES
@@ -402,9 +401,8 @@ struct SolverCtx {
 
   // coarse apply without the profiler (used inside graph capture)
   sg_status apply_raw(const T* X, T* Y, const T* F, cudaStream_t st) {
-    if (sizeof(T) == 4 && pr->apply_mode != 1 && jit_eligible(pr))
-      return jit_apply_launch(pr, 1, pc->co.ell, reinterpret_cast<const float*>(X), ldc,
-                              reinterpret_cast<const float*>(F), ldc, reinterpret_cast<float*>(Y), ldc, st);
+    if (pr->apply_mode != 1 && jit_eligible(pr))
+      return jit_apply_launch(pr, sizeof(T) == 8 ? 3 : 1, pc->co.ell, X, ldc, F, ldc, Y, ldc, st);
     return apply_ell<T>(pc->co.ell, pc->co.tri, pr->P, pr->K, X, ldc, F, ldc, Y, ldc, st);
   }
 
@@ -430,9 +428,9 @@ struct SolverCtx {
   // everything a captured launch needs must exist before a capture starts:
   // specialised kernels, kernel attributes, network buffers
   sg_status capture_prepare() {
-    if (sizeof(T) == 4 && pr->apply_mode != 1 && jit_eligible(pr)) {
-      SG_TRY(jit_apply_build(pr, 0));
-      SG_TRY(jit_apply_build(pr, 1));
+    if (pr->apply_mode != 1 && jit_eligible(pr)) {
+      SG_TRY(jit_apply_build(pr, sizeof(T) == 8 ? 2 : 0));
+      SG_TRY(jit_apply_build(pr, sizeof(T) == 8 ? 3 : 1));
     }
     SG_TRY(kernel_attrs_init());
     if (pr->cnn) SG_TRY(pr->cnn->reserve(pr->P));

@@ -117,7 +117,9 @@ struct Profiler {
   ~Profiler();
 };
 
-// Register-specialised FP32 apply compiled at setup time (sg_jit.cpp).
+// Register-specialised apply compiled at setup time (sg_jit.cpp).  Four
+// families: which = 0 fine FP32, 1 coarse FP32, 2 fine FP64, 3 coarse FP64.
+constexpr int kJitFamilies = 4;
 constexpr int kJitMaxP = 128;
 constexpr int kJitGeneratorVersion = 5;  // bump when the generated code changes
 constexpr int64_t kJitMaxT = 40000;
@@ -158,9 +160,9 @@ struct sg_problem {
   sg::SolverState* solver = nullptr;   // preconditioner + solver workspaces
   sg::Cnn* cnn = nullptr;              // learned smoother network
   sg::Profiler prof;
-  sg::JitApply* jit[2] = {nullptr, nullptr};  // specialised FP32 apply: [0] fine, [1] coarse
-  sg::JitConfig jit_cfg[2];
-  bool jit_cfg_set[2] = {false, false};
+  sg::JitApply* jit[sg::kJitFamilies] = {};     // specialised apply per family (fine/coarse x f32/f64)
+  sg::JitConfig jit_cfg[sg::kJitFamilies];
+  bool jit_cfg_set[sg::kJitFamilies] = {};
   sg::DevBuf mdot_partial, mdot_counter;  // scratch of sg_mdot
   int apply_mode = 0;                  // 0 auto, 1 shared-memory kernel, 2 specialised
 };
@@ -176,14 +178,16 @@ sg_status build_triple_tables(sg_problem* pr, TripleTables& t, int S);
 template <typename T>
 sg_status apply_ell(const Ell& A, const TripleTables& tri, int P, int K, const T* X, int64_t ldx,
                     const T* F, int64_t ldf, T* Y, int64_t ldy, cudaStream_t st);
-std::string jit_apply_source(const sg_problem* pr, const JitConfig& c);
+std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64 = false);
 JitConfig jit_default_config(const sg_problem* pr, int which);
-size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c);
+size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c, bool fp64 = false);
 sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms);
 sg_status jit_apply_build(sg_problem* pr, int which);
 void jit_free(sg_problem* pr, int which);
 sg_status jit_configure(sg_problem* pr, int which, const JitConfig& c);
 bool jit_eligible(const sg_problem* pr);
+sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const double* X, int64_t ldx, const double* F,
+                           int64_t ldf, double* Y, int64_t ldy, cudaStream_t st);
 sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const float* X, int64_t ldx, const float* F,
                            int64_t ldf, float* Y, int64_t ldy, cudaStream_t st);
 // apply_ell on the fine (coarse = false) or coarse family of a problem,

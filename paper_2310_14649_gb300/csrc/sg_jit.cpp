@@ -81,6 +81,14 @@ std::string hexf(float g) {
   return b;
 }
 
+std::string hexd(double g) {
+  uint64_t u;
+  std::memcpy(&u, &g, 8);
+  char b[24];
+  std::snprintf(b, sizeof b, "0x%016llxull", (unsigned long long)u);
+  return b;
+}
+
 // contiguous output ranges [lo_h, hi_h) with about T/H triples each
 std::vector<int> output_split(const sg_problem* pr, int H) {
   std::vector<int64_t> per_a(pr->P, 0);
@@ -99,23 +107,30 @@ std::vector<int> output_split(const sg_problem* pr, int H) {
 
 }  // namespace
 
-std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
-  const int P = pr->P, K = pr->K, R = c.rows, HO = c.groups, HI = c.igroups, SG = c.sgroups, pf = c.prefetch;
+std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64) {
+  const int P = pr->P, K = pr->K, R = fp64 ? 1 : c.rows, HO = c.groups, HI = c.igroups, SG = c.sgroups,
+            pf = c.prefetch;
+  // FP64 family: the same code over double values, inputs and outputs, the
+  // coefficients as exact double immediates
+  const char* T = fp64 ? "double" : "float";
+  const std::string Ts = T;
   const int mb = c.min_blocks, NG = HO * HI * SG, NPART = HI * SG;
   const std::vector<int> cut = output_split(pr, HO);
   std::vector<int> icut(HI + 1);
   for (int i = 0; i <= HI; ++i) icut[i] = int(int64_t(P) * i / HI);
   // triples grouped by k, then by a
-  std::vector<std::map<int, std::vector<std::pair<int, float>>>> by_k(K);
+  std::vector<std::map<int, std::vector<std::pair<int, double>>>> by_k(K);
   for (int64_t t = 0; t < pr->T; ++t) {
     int k = pr->kab[3 * t], a = pr->kab[3 * t + 1], b = pr->kab[3 * t + 2];
-    by_k[k][a].push_back({b, float(pr->g[t])});
+    by_k[k][a].push_back({b, fp64 ? pr->g[t] : double(float(pr->g[t]))});
   }
   // paired rows take their coefficients from the constant bank (the paired
   // FMA has no immediate operand)
   std::map<uint32_t, int> gslot;
   std::vector<float> gvals;
-  auto gref = [&](float g) -> std::string {
+  auto gref = [&](double gd) -> std::string {
+    if (fp64) return "GD(" + hexd(gd) + ")";
+    const float g = float(gd);
     if (R == 1) return "G(" + hexf(g) + ")";
     uint32_t u;
     std::memcpy(&u, &g, 4);
@@ -130,7 +145,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
     }
     return "gq2[" + std::to_string(id) + "]";
   };
-  const char* ty = R == 2 ? "float2" : "float";
+  const char* ty = R == 2 ? "float2" : T;
   std::ostringstream body;
   for (int g = 0; g < NG; ++g) {
     const int ho = g / (HI * SG), hi = (g / SG) % HI, sgi = g % SG;
@@ -151,10 +166,10 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
     }
     body << "  " << (g ? "else " : "") << "if (grp == " << g << ") {\n";
     for (int a = lo; a < up; ++a)
-      if (has_a[a]) body << "    " << ty << " y" << a << (R == 2 ? " = make_float2(0.f, 0.f);\n" : " = 0.f;\n");
+      if (has_a[a]) body << "    " << ty << " y" << a << (R == 2 ? " = make_float2(0.f, 0.f);\n" : (fp64 ? " = 0.0;\n" : " = 0.f;\n"));
     body << "#pragma unroll 1\n"
             "    for (int s = " << sgi << "; s < S; s += " << SG << ") {\n"
-            "      const float* xp0 = X + col[(long long)s * ldr + rr];\n";
+            "      const " << Ts << "* xp0 = X + col[(long long)s * ldr + rr];\n";
     if (R == 2) body << "      const float* xp1 = X + col[(long long)s * ldr + rr + 1];\n";
     for (int b = 0; b < P; ++b) {
       if (!need_b[b]) continue;
@@ -162,15 +177,15 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
         body << "      const float2 x" << b << " = make_float2(__ldg(xp0 + (long long)" << b
              << " * ldx), __ldg(xp1 + (long long)" << b << " * ldx));\n";
       else
-        body << "      const float x" << b << " = __ldg(xp0 + (long long)" << b << " * ldx);\n";
+        body << "      const " << Ts << " x" << b << " = __ldg(xp0 + (long long)" << b << " * ldx);\n";
     }
-    body << "      const float* vp = V + (long long)s * ldr + rr;\n";
+    body << "      const " << Ts << "* vp = V + (long long)s * ldr + rr;\n";
     auto load = [&](int k) {
       if (R == 2)
         body << "      const float2 v" << k << " = __ldg(reinterpret_cast<const float2*>(vp + (long long)" << k
              << " * kst));\n";
       else
-        body << "      const float v" << k << " = __ldg(vp + (long long)" << k << " * kst);\n";
+        body << "      const " << Ts << " v" << k << " = __ldg(vp + (long long)" << k << " * kst);\n";
     };
     const int nk = int(ks.size());
     for (int i = 0; i < std::min(nk, pf); ++i) load(ks[i]);
@@ -179,19 +194,19 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
       const int k = ks[i];
       for (const auto& ga : by_k[k]) {
         const int a = ga.first;
-        std::vector<std::pair<int, float>> lst;
+        std::vector<std::pair<int, double>> lst;
         for (const auto& e : ga.second)
           if (in_grp(a, e.first)) lst.push_back(e);
         if (lst.empty()) continue;
-        const char* fma = R == 2 ? "__ffma2_rn" : "fmaf";
-        if (lst.size() == 1 && lst[0].second == 1.0f) {
+        const char* fma = R == 2 ? "__ffma2_rn" : (fp64 ? "fma" : "fmaf");
+        if (lst.size() == 1 && lst[0].second == 1.0) {
           body << "      y" << a << " = " << fma << "(v" << k << ", x" << lst[0].first << ", y" << a << ");\n";
           continue;
         }
         if (R == 2)
           body << "      { float2 t = __fmul2_rn(x" << lst[0].first << ", " << gref(lst[0].second) << ");";
         else
-          body << "      { float t = x" << lst[0].first << " * " << gref(lst[0].second) << ";";
+          body << "      { " << Ts << " t = x" << lst[0].first << " * " << gref(lst[0].second) << ";";
         for (size_t e = 1; e < lst.size(); ++e)
           body << " t = " << fma << "(x" << lst[e].first << ", " << gref(lst[e].second) << ", t);";
         body << " y" << a << " = " << fma << "(v" << k << ", t, y" << a << "); }\n";
@@ -202,7 +217,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
     // group order; outputs this group never touches contribute zero
     for (int a = lo; a < up; ++a) {
       if (!has_a[a]) {
-        for (int q = 0; q < R; ++q) body << "    part[" << a << " * " << 128 * R << " + lrow + " << q << "] = 0.f;\n";
+        for (int q = 0; q < R; ++q) body << "    part[" << a << " * " << 128 * R << " + lrow + " << q << "] = 0;\n";
         continue;
       }
       for (int q = 0; q < R; ++q) {
@@ -214,8 +229,8 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
   }
   std::ostringstream os;
   os << "// generated: Galerkin apply, P=" << P << " K=" << K << " T=" << pr->T << " R=" << R << " groups=" << HO
-     << "x" << HI << "x" << SG << " pf=" << pf << " mb=" << mb << "\n";
-  os << "#define G(h) __int_as_float(h)\n";
+     << "x" << HI << "x" << SG << " pf=" << pf << " mb=" << mb << (fp64 ? " fp64" : "") << "\n";
+  os << (fp64 ? "#define GD(h) __longlong_as_double(h)\n" : "#define G(h) __int_as_float(h)\n");
   if (R == 2 && !gvals.empty()) {
     // both halves of each pair carry the same coefficient bits
     os << "__constant__ unsigned long long gq_bits[" << gvals.size() << "] = {";
@@ -227,10 +242,10 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
   }
   const int rows_cta = 128 * R;
   os << "extern \"C\" __global__ void __launch_bounds__(" << 128 * NG << ", " << mb << ") sg_k1(\n"
-        "    const float* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
-        "    const float* __restrict__ X, long long ldx, const float* __restrict__ F, long long ldf,\n"
-        "    float* __restrict__ Y, long long ldy) {\n"
-        "  extern __shared__ float smem[];\n"
+        "    const " << Ts << "* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
+        "    const " << Ts << "* __restrict__ X, long long ldx, const " << Ts << "* __restrict__ F, long long ldf,\n"
+        "    " << Ts << "* __restrict__ Y, long long ldy) {\n"
+        "  extern __shared__ " << Ts << " smem[];\n"
         "  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
         "  const int grp = warp >> 2;\n"
         "  const int lrow = (warp & 3) * "
@@ -239,7 +254,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
      << "  const int rr = r < n ? r : (n - 1) & ~" << (R - 1) << ";\n"
      << "  const long long kst = (long long)S * ldr;\n";
   if (NG == 1) {
-    os << "  float* part = smem;\n  (void)part;\n";
+    os << "  " << Ts << "* part = smem;\n  (void)part;\n";
     // single group: write straight from registers
     std::string b = body.str();
     // drop the shared-memory hand-off of the single group
@@ -260,7 +275,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
     }
     os << direct.str();
   } else {
-    os << "  float* part = smem + (size_t)(grp % " << NPART << ") * " << P * rows_cta << ";\n";
+    os << "  " << Ts << "* part = smem + (size_t)(grp % " << NPART << ") * " << P * rows_cta << ";\n";
     os << body.str();
     os << "  __syncthreads();\n";
     os << "  for (int e = threadIdx.x; e < " << P * rows_cta << "; e += " << 128 * NG << ") {\n"
@@ -268,7 +283,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
        << rows_cta << ", lr = e - a * " << rows_cta << ";\n"
        << "    const int row = blockIdx.x * " << rows_cta << " + lr;\n"
        << "    if (row >= n) continue;\n"
-          "    float acc = smem[e];\n";
+          "    " << Ts << " acc = smem[e];\n";
     for (int q = 1; q < NPART; ++q) os << "    acc += smem[" << q * P * rows_cta << " + e];\n";
     os << "    Y[(long long)a * ldy + row] = F ? F[(long long)a * ldf + row] - acc : acc;\n  }\n";
   }
@@ -276,9 +291,9 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c) {
   return os.str();
 }
 
-size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c) {
+size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c, bool fp64) {
   if (c.groups * c.igroups * c.sgroups == 1) return 0;
-  return size_t(c.igroups) * c.sgroups * pr->P * 128 * c.rows * sizeof(float);
+  return size_t(c.igroups) * c.sgroups * pr->P * 128 * c.rows * (fp64 ? sizeof(double) : sizeof(float));
 }
 
 // Compile (or load from the cache) one configuration.
@@ -334,14 +349,15 @@ static sg_status jit_compile(const std::string& src, cudaLibrary_t* lib, cudaKer
 }
 
 JitConfig jit_default_config(const sg_problem* pr, int which) {
+  const bool fp64 = which >= 2, coarse = which % 2 == 1;
   JitConfig c;
   c.rows = 1;
-  c.prefetch = pr->P <= 48 ? 32 : 8;
+  c.prefetch = pr->P <= 48 ? (fp64 ? 16 : 32) : 8;
   c.groups = pr->P <= 48 ? 1 : 2;
   c.igroups = pr->P <= 48 ? 1 : 2;
   // the coarse operator has a quarter of the rows: deal the slots to groups
   // so that the grid still fills the GPU
-  c.sgroups = which == 1 ? (pr->P <= 48 ? 4 : 2) : 1;
+  c.sgroups = coarse ? (pr->P <= 48 ? 4 : 2) : 1;
   c.min_blocks = 1;
   return c;
 }
@@ -354,19 +370,19 @@ sg_status jit_apply_build(sg_problem* pr, int which) {
     pr->jit_cfg[which] = jit_default_config(pr, which);
     pr->jit_cfg_set[which] = true;
   }
-  return jit_compile(jit_apply_source(pr, pr->jit_cfg[which]), &J.lib, &J.kern, &J.from_cache, &J.compile_s,
-                     pr->device);
+  return jit_compile(jit_apply_source(pr, pr->jit_cfg[which], which >= 2), &J.lib, &J.kern, &J.from_cache,
+                     &J.compile_s, pr->device);
 }
 
 sg_status jit_configure(sg_problem* pr, int which, const JitConfig& c) {
   if (c.rows < 1 || c.rows > 2 || c.groups < 1 || c.groups > 4 || c.igroups < 1 || c.igroups > 4 ||
       c.sgroups < 1 || c.sgroups > 8 || c.groups * c.igroups * c.sgroups > 8 || c.prefetch < 0 ||
-      c.prefetch > 64 || c.min_blocks < 1 || c.min_blocks > 8) {
+      c.prefetch > 64 || c.min_blocks < 1 || c.min_blocks > 8 || (which >= 2 && c.rows != 1)) {
     set_error("sg_apply_config: rows in {1,2}; groups, igroups in [1,4]; sgroups in [1,8]; "
-              "groups*igroups*sgroups <= 8; prefetch in [0,64]; min_blocks in [1,8]");
+              "groups*igroups*sgroups <= 8; prefetch in [0,64]; min_blocks in [1,8]; FP64 families: rows 1");
     return SG_ERR_ARG;
   }
-  if (jit_smem_bytes(pr, c) > 200 * 1024) {
+  if (jit_smem_bytes(pr, c, which >= 2) > 200 * 1024) {
     set_error("sg_apply_config: the input-group hand-off does not fit in shared memory");
     return SG_ERR_ARG;
   }
@@ -386,10 +402,11 @@ void jit_free(sg_problem* pr, int which) {
 
 bool jit_eligible(const sg_problem* pr) { return pr->P <= kJitMaxP && pr->T <= kJitMaxT; }
 
-static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, size_t smem, const Ell& A, const float* X,
-                               int64_t ldx, const float* F, int64_t ldf, float* Y, int64_t ldy, cudaStream_t st) {
+template <typename T>
+static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, size_t smem, const Ell& A, const T* X,
+                               int64_t ldx, const T* F, int64_t ldf, T* Y, int64_t ldy, cudaStream_t st) {
   if (A.n == 0) return SG_OK;
-  const float* V = dp<float>(A.v32);
+  const T* V = sizeof(T) == 8 ? reinterpret_cast<const T*>(A.v64.ptr) : reinterpret_cast<const T*>(A.v32.ptr);
   const int* col = dp<int>(A.col);
   long long ldr = A.ldr, lx = ldx, lf = ldf, ly = ldy;
   int n = int(A.n), S = A.S;
@@ -406,7 +423,14 @@ sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const float*
                            int64_t ldf, float* Y, int64_t ldy, cudaStream_t st) {
   SG_TRY(jit_apply_build(pr, which));
   const JitConfig& c = pr->jit_cfg[which];
-  return launch_kernel(pr->jit[which]->kern, c, jit_smem_bytes(pr, c), A, X, ldx, F, ldf, Y, ldy, st);
+  return launch_kernel<float>(pr->jit[which]->kern, c, jit_smem_bytes(pr, c, false), A, X, ldx, F, ldf, Y, ldy, st);
+}
+
+sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const double* X, int64_t ldx, const double* F,
+                           int64_t ldf, double* Y, int64_t ldy, cudaStream_t st) {
+  SG_TRY(jit_apply_build(pr, which));
+  const JitConfig& c = pr->jit_cfg[which];
+  return launch_kernel<double>(pr->jit[which]->kern, c, jit_smem_bytes(pr, c, true), A, X, ldx, F, ldf, Y, ldy, st);
 }
 
 // --------------------------------------------------------------------------
@@ -424,7 +448,21 @@ static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
     int r, g, i, s, pf;
   };
   std::vector<S6> list;
-  if (pr->P <= 48) {
+  const bool fp64 = which >= 2;
+  if (fp64) {
+    // twice the register bytes per value: more output/input splitting
+    if (pr->P <= 48) {
+      if (which == 2)
+        list = {{1, 1, 1, 1, 16}, {1, 1, 1, 1, 8}, {1, 2, 1, 1, 16}, {1, 1, 2, 1, 16}, {1, 2, 2, 1, 8}};
+      else
+        list = {{1, 1, 1, 2, 16}, {1, 1, 1, 4, 8}, {1, 2, 1, 2, 8}, {1, 1, 2, 2, 8}};
+    } else {
+      if (which == 2)
+        list = {{1, 2, 2, 1, 8}, {1, 4, 2, 1, 8}, {1, 2, 4, 1, 4}, {1, 4, 2, 1, 4}};
+      else
+        list = {{1, 2, 2, 2, 8}, {1, 4, 2, 1, 8}, {1, 2, 2, 1, 8}};
+    }
+  } else if (pr->P <= 48) {
     if (which == 0)
       list = {{1, 1, 1, 1, 32}, {1, 1, 1, 1, 16}, {1, 1, 2, 1, 16}, {1, 2, 1, 1, 16}};
     else
@@ -444,18 +482,18 @@ static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
     c.sgroups = e.s;
     c.prefetch = e.pf;
     c.min_blocks = 1;
-    if (jit_smem_bytes(pr, c) > 200 * 1024) continue;
+    if (jit_smem_bytes(pr, c, fp64) > 200 * 1024) continue;
     out.push_back(c);
   }
   if (out.empty()) out.push_back(jit_default_config(pr, which));
   return out;
 }
 
-static std::string tune_key(const sg_problem* pr, const Ell& A) {
+static std::string tune_key(const sg_problem* pr, const Ell& A, bool fp64) {
   cudaDeviceProp prop{};
   cudaGetDeviceProperties(&prop, pr->device);
   std::ostringstream os;
-  os << prop.name << "|" << pr->P << "|" << pr->K << "|" << pr->T << "|" << A.n << "|" << A.S;
+  os << prop.name << "|" << pr->P << "|" << pr->K << "|" << pr->T << "|" << A.n << "|" << A.S << (fp64 ? "|f64" : "");
   for (int64_t t = 0; t < pr->T; ++t) os << "," << pr->kab[3 * t] << ":" << pr->kab[3 * t + 1] << ":" << pr->kab[3 * t + 2];
   char key[32];
   std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(os.str()));
@@ -467,12 +505,13 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
     set_error("sg_apply_autotune: the specialised kernel is not available for this size");
     return SG_ERR_UNSUPPORTED;
   }
-  if (which == 1 && !pr->solver) {
+  const bool coarse = which % 2 == 1, fp64 = which >= 2;
+  if (coarse && !pr->solver) {
     set_error("sg_apply_autotune: the coarse operator exists after sg_precond_setup");
     return SG_ERR_ARG;
   }
-  const Ell& A = which == 1 ? coarse_ell(pr) : pr->fine;
-  const std::string path = cache_dir() + "/tune_" + tune_key(pr, A) + ".txt";
+  const Ell& A = coarse ? coarse_ell(pr) : pr->fine;
+  const std::string path = cache_dir() + "/tune_" + tune_key(pr, A, fp64) + ".txt";
   if (!force) {
     std::ifstream in(path);
     JitConfig c;
@@ -483,9 +522,10 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
     }
   }
   const int64_t len = int64_t(pr->P) * std::max<int64_t>(pr->ld, A.ldr);
+  const size_t esz = fp64 ? 8 : 4;
   DevBuf X, Y;
-  SG_TRY(X.alloc(len * 4));
-  SG_TRY(Y.alloc(len * 4));
+  SG_TRY(X.alloc(len * esz));
+  SG_TRY(Y.alloc(len * esz));
   cudaStream_t st;
   SG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   cudaEvent_t e0, e1;
@@ -497,15 +537,19 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
   for (const JitConfig& c : candidates(pr, which)) {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
-    if (jit_compile(jit_apply_source(pr, c), &lib, &kern, nullptr, nullptr, pr->device) != SG_OK) continue;
+    if (jit_compile(jit_apply_source(pr, c, fp64), &lib, &kern, nullptr, nullptr, pr->device) != SG_OK) continue;
+    const size_t sm = jit_smem_bytes(pr, c, fp64);
+    auto run = [&]() {
+      return fp64 ? launch_kernel<double>(kern, c, sm, A, dp<double>(X), A.ldr, nullptr, 0, dp<double>(Y), A.ldr, st)
+                  : launch_kernel<float>(kern, c, sm, A, dp<float>(X), A.ldr, nullptr, 0, dp<float>(Y), A.ldr, st);
+    };
     std::vector<float> ts;
     for (int rep = 0; rep < 7 && status == SG_OK; ++rep) {
-      status = launch_kernel(kern, c, jit_smem_bytes(pr, c), A, dp<float>(X), A.ldr, nullptr, 0, dp<float>(Y),
-                             A.ldr, st);
+      status = run();
       if (status != SG_OK) break;
       if (rep < 2) continue;
       cudaEventRecord(e0, st);
-      launch_kernel(kern, c, jit_smem_bytes(pr, c), A, dp<float>(X), A.ldr, nullptr, 0, dp<float>(Y), A.ldr, st);
+      run();
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
       float ms = 0;

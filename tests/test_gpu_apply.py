@@ -93,14 +93,14 @@ def check_apply(prob, ref, X, dtype, ld=None, kernel=0):
     return Yd
 
 
-@pytest.mark.parametrize("dt", ["f64", "f32", "f32-shared"])
+@pytest.mark.parametrize("dt", ["f64", "f64-shared", "f32", "f32-shared"])
 @pytest.mark.parametrize("N,L,p,q", [(32, 2, 2, 4), (33, 3, 3, 6), (2, 2, 1, 2), (9, 0, 0, 0), (40, 1, 5, 10)])
 def test_apply_vs_oracle(gpu, dt, N, L, p, q):
-    """FP64 (shared-memory kernel), FP32 register-specialised kernel and
-    FP32 shared-memory kernel, each against the oracle."""
+    """Register-specialised and shared-memory kernels, FP64 and FP32, each
+    against the oracle within the deterministic rounding bound."""
     import torch
-    dtype = torch.float64 if dt == "f64" else torch.float32
-    kernel = 1 if dt == "f32-shared" else (2 if dt == "f32" else 0)
+    dtype = torch.float64 if dt.startswith("f64") else torch.float32
+    kernel = 1 if dt.endswith("shared") else 2
     prob, ref = setup_pair(N, L, p, q)
     X = random_block(ref.n, ref.P, seed=3)
     check_apply(prob, ref, X, dtype, kernel=kernel)
@@ -188,6 +188,21 @@ def test_specialised_kernel_configs(gpu, cfg, N):
     check_apply(prob, ref, random_block(ref.n, ref.P, seed=13), torch.float32, kernel=2, ld=ref.n + 3)
 
 
+@pytest.mark.parametrize("cfg", [(1, 1, 1, 1, 16, 1), (1, 2, 2, 1, 8, 1), (1, 1, 1, 4, 8, 1), (1, 4, 2, 1, 4, 1),
+                                 (1, 2, 4, 1, 4, 1)])
+@pytest.mark.parametrize("N", [20, 21])
+def test_specialised_fp64_configs(gpu, cfg, N):
+    """The FP64 family (exact double coefficients) in several tile shapes."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(N, 3, 3, 6)
+    sg.sg_apply_config(prob, *cfg, which=2)
+    check_apply(prob, ref, random_block(ref.n, ref.P, seed=15), torch.float64, kernel=2)
+    check_apply(prob, ref, random_block(ref.n, ref.P, seed=16), torch.float64, kernel=2, ld=ref.n + 5)
+    with pytest.raises(sg.SgError):
+        sg.sg_apply_config(prob, 2, 1, 1, 1, 8, 1, which=2)   # paired rows are FP32 only
+
+
 def test_autotune_picks_a_valid_shape(gpu):
     import torch
     import paper_2310_14649_gb300 as sg
@@ -196,6 +211,9 @@ def test_autotune_picks_a_valid_shape(gpu):
     info = sg.sg_apply_info(prob)
     assert ms > 0 and info["rows"] in (1, 2) and 1 <= info["groups"] <= 4
     check_apply(prob, ref, random_block(ref.n, ref.P, seed=14), torch.float32, kernel=2)
+    ms64 = sg.sg_apply_autotune(prob, force=True, which=2)
+    assert ms64 > 0 and sg.sg_apply_info(prob, which=2)["rows"] == 1
+    check_apply(prob, ref, random_block(ref.n, ref.P, seed=17), torch.float64, kernel=2)
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
