@@ -195,6 +195,8 @@ typedef struct {
                           launch whose restart and Arnoldi loops are
                           conditional WHILE nodes decided on the device;
                           1: the same GMRES driven from the host         */
+  int ras_modes;       /* modes per CTA of the RAS local solve kernel
+                          (tile shape); <= 0 = automatic                 */
 } sg_precond_opts;
 
 /* Builds partitions, local factors, the coarse space, the AMG hierarchy,

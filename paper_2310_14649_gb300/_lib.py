@@ -39,7 +39,8 @@ class KlDesc(ctypes.Structure):
 class PrecondOpts(ctypes.Structure):
     _fields_ = [("sx", ctypes.c_int), ("sy", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("omega", ctypes.c_double), ("inner_rtol", ctypes.c_double),
-                ("inner_max", ctypes.c_int), ("smoother", ctypes.c_int), ("host_loops", ctypes.c_int)]
+                ("inner_max", ctypes.c_int), ("smoother", ctypes.c_int), ("host_loops", ctypes.c_int),
+                ("ras_modes", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):

@@ -20,10 +20,11 @@ constexpr int kIdxMask = kOwnedBit - 1;
 //   forward  y_j = Linv_j (r_j - Loff_j y_{j-1})
 //   backward x_j = Linv_j^T (y_j - Loff_{j+1}^T x_{j+1})
 // One CTA per (box, chunk of MC modes); the local block lives in shared
-// memory as y[line][slot][mode] with a padded mode stride (MC + 1).  The two
-// W x W matrices of the next line step are copied into shared memory with
-// cp.async while the current step computes (double buffering), so every
-// step reads only shared memory.  W is a multiple of 4 (16-byte rows).
+// memory as y[line][slot][mode] with a padded mode stride.  The two W x W
+// matrices of each line step are copied into shared memory with cp.async
+// two steps ahead (a ring of three buffers), so every step reads only shared
+// memory and the copies' latency hides behind two steps of compute.  W is a
+// multiple of 4 (16-byte rows).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
@@ -31,6 +32,12 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// line steps whose matrices are in flight or resident (ring of buffers)
+constexpr int kRasStages = 3;
 
 template <typename T>
 __device__ __forceinline__ void stage_mats(T* dst_off, T* dst_lin, const T* src_off, const T* src_lin, int WW) {
@@ -42,90 +49,159 @@ __device__ __forceinline__ void stage_mats(T* dst_off, T* dst_lin, const T* src_
   cp_async_commit();
 }
 
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// Each thread owns two adjacent rows (t0, t0 + 1) of a line and two adjacent
+// modes (a0, a0 + 1): every shared-memory value it loads feeds two FMAs, and
+// the mode pairs are read as one vector.  The sums run over u in the same
+// order as a one-row, one-mode loop.
 template <typename T>
 __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__ Z, int P, int MC,
                             int W, int Lm, const int* __restrict__ nlines, const int* __restrict__ gidx,
                             const T* __restrict__ linv, const T* __restrict__ loff) {
+  using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int MS = MC + 1, WW = W * W;
-  T* mats = reinterpret_cast<T*>(smem_raw);  // [2 buffers][off, lin][W*W]
-  T* y = mats + 4 * WW;                      // [Lm * W][MS]
+  const int MCe = (MC + 1) & ~1, MS = MCe + 2, MS2 = MS / 2, WW = W * W;
+  T* mats = reinterpret_cast<T*>(smem_raw);  // [kRasStages buffers][off, lin][W*W]
+  T* y = mats + 2 * kRasStages * WW;         // [Lm * W][MS]
   T* s = y + size_t(Lm) * W * MS;            // [W][MS]
+  T2* y2 = reinterpret_cast<T2*>(y);
+  T2* s2 = reinterpret_cast<T2*>(s);
   const int box = blockIdx.x, a0 = blockIdx.y * MC;
   const int nl = nlines[box];
   const int* gbox = gidx + size_t(box) * Lm * W;
   const T* Li = linv + size_t(box) * Lm * WW;
   const T* Lo = loff + size_t(box) * Lm * WW;
   const int nthr = blockDim.x;
-  // first forward step's matrices
-  stage_mats<T>(mats, mats + WW, nullptr, Li, WW);
-  // gather (nodes fastest across threads)
+  // matrices of sweep step st (forward j = st, backward j = 2 nl - 1 - st)
+  auto step_off = [&](int st) -> const T* {
+    if (st < nl) return st > 0 ? Lo + size_t(st) * WW : nullptr;
+    const int j = 2 * nl - 1 - st;
+    return j + 1 < nl ? Lo + size_t(j + 1) * WW : nullptr;
+  };
+  auto step_lin = [&](int st) -> const T* { return Li + size_t(st < nl ? st : 2 * nl - 1 - st) * WW; };
+  // prologue: the first kRasStages - 1 steps' matrices in flight
+  for (int st = 0; st < kRasStages - 1; ++st) {
+    T* d = mats + (st % kRasStages) * 2 * WW;
+    if (st < 2 * nl)
+      stage_mats<T>(d, d + WW, step_off(st), step_lin(st), WW);
+    else
+      cp_async_commit();
+  }
+  // gather (nodes fastest across threads); padding modes are zero
   const int nslot = nl * W;
-  for (int e = threadIdx.x; e < nslot * MC; e += nthr) {
+  for (int e = threadIdx.x; e < nslot * MCe; e += nthr) {
     int a = e / nslot, q = e - a * nslot;
     int g = gbox[q];
     T v = T(0);
-    if (g >= 0 && a0 + a < P) v = R[int64_t(a0 + a) * ld + (g & kIdxMask)];
+    if (g >= 0 && a < MC && a0 + a < P) v = R[int64_t(a0 + a) * ld + (g & kIdxMask)];
     y[q * MS + a] = v;
   }
-  const int a = threadIdx.x % MC, grp = threadIdx.x / MC, ngrp = nthr / MC;
-  const bool act = grp < ngrp;
-  int buf = 0;
-  // forward sweep: step j uses Loff_j (j > 0) and Linv_j
-  for (int j = 0; j < nl; ++j) {
-    cp_async_wait_all();
+  const int np = MCe / 2;
+  const int tm = threadIdx.x % np, tr = threadIdx.x / np;
+  const int t0 = 2 * tr, t1 = t0 + 1;
+  const bool act = t0 < W;
+  for (int st = 0; st < 2 * nl; ++st) {
+    cp_async_wait_group<kRasStages - 2>();
     __syncthreads();
-    const T* Lof = mats + buf * 2 * WW;
+    const T* Lof = mats + (st % kRasStages) * 2 * WW;
     const T* Lin = Lof + WW;
-    // prefetch the next step's matrices into the other buffer
-    T* nb = mats + (buf ^ 1) * 2 * WW;
-    if (j + 1 < nl)
-      stage_mats<T>(nb, nb + WW, Lo + size_t(j + 1) * WW, Li + size_t(j + 1) * WW, WW);
-    else  // first backward step: Linv_{nl-1}, no Loff
-      stage_mats<T>(nb, nb + WW, nullptr, Li + size_t(nl - 1) * WW, WW);
-    if (act) {
-      for (int t = grp; t < W; t += ngrp) {
-        T acc = y[(j * W + t) * MS + a];
-        if (j > 0)
-          for (int u = 0; u < W; ++u) acc -= Lof[t * W + u] * y[((j - 1) * W + u) * MS + a];
-        s[t * MS + a] = acc;
+    {  // keep kRasStages - 1 steps ahead in flight (buffer of step st - 1 is free)
+      const int nx = st + kRasStages - 1;
+      T* d = mats + (nx % kRasStages) * 2 * WW;
+      if (nx < 2 * nl)
+        stage_mats<T>(d, d + WW, step_off(nx), step_lin(nx), WW);
+      else
+        cp_async_commit();
+    }
+    if (st < nl) {
+      // forward: y_j = Linv_j (r_j - Loff_j y_{j-1})
+      const int j = st;
+      if (act) {
+        T2 c0 = y2[(j * W + t0) * MS2 + tm], c1 = y2[(j * W + t1) * MS2 + tm];
+        if (j > 0) {
+          const T2* yp = y2 + size_t(j - 1) * W * MS2 + tm;
+          const T* l0 = Lof + t0 * W;
+          const T* l1 = Lof + t1 * W;
+#pragma unroll 4
+          for (int u = 0; u < W; ++u) {
+            const T2 v = yp[u * MS2];
+            const T p0 = l0[u], p1 = l1[u];
+            c0.x -= p0 * v.x;
+            c0.y -= p0 * v.y;
+            c1.x -= p1 * v.x;
+            c1.y -= p1 * v.y;
+          }
+        }
+        s2[t0 * MS2 + tm] = c0;
+        s2[t1 * MS2 + tm] = c1;
+      }
+      __syncthreads();
+      if (act) {
+        const T* l0 = Lin + t0 * W;
+        const T* l1 = Lin + t1 * W;
+        T2 c0, c1;
+        c0.x = c0.y = c1.x = c1.y = T(0);
+#pragma unroll 4
+        for (int u = 0; u <= t0; ++u) {
+          const T2 v = s2[u * MS2 + tm];
+          const T p0 = l0[u], p1 = l1[u];
+          c0.x += p0 * v.x;
+          c0.y += p0 * v.y;
+          c1.x += p1 * v.x;
+          c1.y += p1 * v.y;
+        }
+        const T2 v = s2[t1 * MS2 + tm];
+        c1.x += l1[t1] * v.x;
+        c1.y += l1[t1] * v.y;
+        y2[(j * W + t0) * MS2 + tm] = c0;
+        y2[(j * W + t1) * MS2 + tm] = c1;
+      }
+    } else {
+      // backward: x_j = Linv_j^T (y_j - Loff_{j+1}^T x_{j+1})
+      const int j = 2 * nl - 1 - st;
+      if (act) {
+        T2 c0 = y2[(j * W + t0) * MS2 + tm], c1 = y2[(j * W + t1) * MS2 + tm];
+        if (j + 1 < nl) {
+          const T2* yp = y2 + size_t(j + 1) * W * MS2 + tm;
+#pragma unroll 4
+          for (int u = 0; u < W; ++u) {
+            const T2 v = yp[u * MS2];
+            const T2 p = *reinterpret_cast<const T2*>(Lof + u * W + t0);  // Loff[u][t0], Loff[u][t1]
+            c0.x -= p.x * v.x;
+            c0.y -= p.x * v.y;
+            c1.x -= p.y * v.x;
+            c1.y -= p.y * v.y;
+          }
+        }
+        s2[t0 * MS2 + tm] = c0;
+        s2[t1 * MS2 + tm] = c1;
+      }
+      __syncthreads();
+      if (act) {
+        T2 c0, c1;
+        {
+          const T2 v = s2[t0 * MS2 + tm];
+          const T p = Lin[t0 * W + t0];
+          c0.x = T(0) + p * v.x;
+          c0.y = T(0) + p * v.y;
+          c1.x = c1.y = T(0);
+        }
+#pragma unroll 4
+        for (int u = t1; u < W; ++u) {
+          const T2 v = s2[u * MS2 + tm];
+          const T2 p = *reinterpret_cast<const T2*>(Lin + u * W + t0);  // Linv[u][t0], Linv[u][t1]
+          c0.x += p.x * v.x;
+          c0.y += p.x * v.y;
+          c1.x += p.y * v.x;
+          c1.y += p.y * v.y;
+        }
+        y2[(j * W + t0) * MS2 + tm] = c0;
+        y2[(j * W + t1) * MS2 + tm] = c1;
       }
     }
-    __syncthreads();
-    if (act) {
-      for (int t = grp; t < W; t += ngrp) {
-        T acc = T(0);
-        for (int u = 0; u <= t; ++u) acc += Lin[t * W + u] * s[u * MS + a];
-        y[(j * W + t) * MS + a] = acc;
-      }
-    }
-    buf ^= 1;
-  }
-  // backward sweep: step j uses Loff_{j+1} (j + 1 < nl) and Linv_j
-  for (int j = nl - 1; j >= 0; --j) {
-    cp_async_wait_all();
-    __syncthreads();
-    const T* Lof = mats + buf * 2 * WW;
-    const T* Lin = Lof + WW;
-    T* nb = mats + (buf ^ 1) * 2 * WW;
-    if (j > 0) stage_mats<T>(nb, nb + WW, Lo + size_t(j) * WW, Li + size_t(j - 1) * WW, WW);
-    if (act) {
-      for (int t = grp; t < W; t += ngrp) {
-        T acc = y[(j * W + t) * MS + a];
-        if (j + 1 < nl)
-          for (int u = 0; u < W; ++u) acc -= Lof[u * W + t] * y[((j + 1) * W + u) * MS + a];
-        s[t * MS + a] = acc;
-      }
-    }
-    __syncthreads();
-    if (act) {
-      for (int t = grp; t < W; t += ngrp) {
-        T acc = T(0);
-        for (int u = t; u < W; ++u) acc += Lin[u * W + t] * s[u * MS + a];
-        y[(j * W + t) * MS + a] = acc;
-      }
-    }
-    buf ^= 1;
   }
   cp_async_wait_all();
   __syncthreads();
@@ -258,12 +334,20 @@ template <typename T>
 sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld, T* Z, cudaStream_t st,
                     bool transform) {
   const RasData& D = pc.ras;
-  const int maxmc = sizeof(T) == 8 ? 16 : 32;
-  const int nchunk = (P + maxmc - 1) / maxmc;
+  // modes per CTA: at most what shared memory holds
+  const size_t per_mode = (size_t(D.lmax) * D.wmax + D.wmax) * sizeof(T);
+  const size_t fixed = 2 * kRasStages * size_t(D.wmax) * D.wmax * sizeof(T);
+  const int fit = int(std::max<size_t>(2, ((227 * 1024 - fixed) / per_mode - 2) & ~size_t(1)));
+  const int by_threads = std::max(2, (2048 / std::max(2, D.wmax)) & ~1);  // (W/2) * (MC/2) <= 1024
+  int maxmc = std::min(fit, by_threads);
+  if (pc.ras_modes > 0) maxmc = std::min(maxmc, pc.ras_modes);
+  int nchunk = (P + maxmc - 1) / maxmc;
+  // about 18 modes per CTA measured best on GB300 (64 boxes of 36^2 nodes)
+  if (pc.ras_modes <= 0) nchunk = std::max(nchunk, (P + 17) / 18);
   const int MC = (P + nchunk - 1) / nchunk;
-  const int ngrp = std::max(1, 256 / MC);
-  const int threads = ngrp * MC;
-  const size_t smem = ((size_t(D.lmax) * D.wmax + D.wmax) * (MC + 1) + 4 * size_t(D.wmax) * D.wmax) * sizeof(T);
+  const int MCe = (MC + 1) & ~1;
+  const int threads = (D.wmax / 2) * (MCe / 2);
+  const size_t smem = (size_t(D.lmax) * D.wmax + D.wmax) * (MCe + 2) * sizeof(T) + fixed;
   static bool attr[2] = {false, false};
   if (!attr[sizeof(T) == 8]) {
     SG_CUDA(cudaFuncSetAttribute(k_ras_local<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));

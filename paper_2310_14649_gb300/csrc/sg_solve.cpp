@@ -227,6 +227,7 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   pc.inner_max = o->inner_max > 0 ? o->inner_max : 100;
   pc.inner_restart = 30;
   pc.device_loops = o->host_loops == 0;
+  pc.ras_modes = o->ras_modes > 0 ? o->ras_modes : 0;
   SG_TRY(kernel_attrs_init());
   sg_status s = precond_setup_host(pr, pc);
   std::vector<double> ginv;
@@ -384,8 +385,12 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
   SG_TRY(c64->clear_counters(st));
   if (S.c32) SG_TRY(S.c32->clear_counters(st));
   sg_status status = SG_OK;
+  // squared norm of F - A x for the returned x when a solve path already
+  // computed it in FP64 (it then needs no extra residual apply)
+  double final_r2 = -1.0;
   if (nF == 0.0) {
     SG_CUDA(cudaMemsetAsync(x64, 0, len * 8, st));
+    final_r2 = 0.0;
   } else if (o->mode == 0) {
     Op<double> A = [&](const double* x, double* y) { return c64->apply_fine(x, y, nullptr, st); };
     Op<double> M = [&](const double* r, double* z) { return c64->twolevel(r, z, st); };
@@ -402,6 +407,9 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
         continue;
       }
       SG_TRY(gs);
+      // without a stagnation stop the last estimate is the true FP64
+      // residual of the final x (computed at the closing restart)
+      if (!res.stalled) final_r2 = res.est * res.est;
       break;
     }
   } else {
@@ -416,8 +424,17 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
     const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
     const int max_ir = o->max_ir > 0 ? o->max_ir : 20;
     double rr_prev = 0.0;
+    // a zero initial guess has residual F: no apply for the first step
+    SG_TRY(vec_norm2<double>(x64, len, scal + 3, dp<double>(c64->fine.partial), dp<unsigned>(c64->fine.counter), st));
+    SG_CUDA(cudaMemcpyAsync(S.host + 3, scal + 3, 8, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    bool x_is_zero = S.host[3] == 0.0;
     for (int ir = 0;; ++ir) {
-      SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+      if (x_is_zero)
+        SG_CUDA(cudaMemcpyAsync(dp<double>(S.r64), F64, len * 8, cudaMemcpyDeviceToDevice, st));
+      else
+        SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+      x_is_zero = false;
       SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 1, dp<double>(c64->fine.partial),
                                dp<unsigned>(c64->fine.counter), st));
       SG_CUDA(cudaMemcpyAsync(S.host + 1, scal + 1, 8, cudaMemcpyDeviceToHost, st));
@@ -428,7 +445,10 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
         return SG_ERR_BREAKDOWN;
       }
       hist.push_back(rr);
-      if (rr <= o->rtol || ir >= max_ir || inf.outer_it >= o->max_it) break;
+      if (rr <= o->rtol || ir >= max_ir || inf.outer_it >= o->max_it) {
+        final_r2 = S.host[1];  // the residual of the returned x
+        break;
+      }
       // learned smoother: a refinement step that did not halve the residual
       // switches to RAS
       if (stall_test && S.pc.use_cnn && ir > 0 && rr > 0.5 * rr_prev) {
@@ -457,13 +477,16 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
     }
   }
   // true FP64 residual of the returned iterate
-  SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
-  SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 2, dp<double>(c64->fine.partial),
-                           dp<unsigned>(c64->fine.counter), st));
-  SG_CUDA(cudaMemcpyAsync(S.host + 2, scal + 2, 8, cudaMemcpyDeviceToHost, st));
+  if (final_r2 < 0.0) {
+    SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+    SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 2, dp<double>(c64->fine.partial),
+                             dp<unsigned>(c64->fine.counter), st));
+    SG_CUDA(cudaMemcpyAsync(S.host + 2, scal + 2, 8, cudaMemcpyDeviceToHost, st));
+  }
   SG_CUDA(cudaMemcpy2DAsync(X, ldx * 8, x64, ld * 8, pr->n * 8, P, cudaMemcpyDeviceToDevice, st));
   SG_CUDA(cudaStreamSynchronize(st));
-  inf.relres = nF > 0 ? std::sqrt(S.host[2]) / nF : 0.0;
+  const double r2 = final_r2 >= 0.0 ? final_r2 : S.host[2];
+  inf.relres = nF > 0 ? std::sqrt(r2) / nF : 0.0;
   inf.inner_it = S.pc.inner_its_total;
   if (S.pc.device_loops) {
     // coarse iterations and the kernels the coarse-solve graphs ran (the

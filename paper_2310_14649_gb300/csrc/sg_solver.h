@@ -75,6 +75,7 @@ struct Precond {
   double omega = 1.0;
   double inner_rtol = 1e-5;
   int inner_max = 100, inner_restart = 30;
+  int ras_modes = 0;                       // modes per CTA of the RAS kernel (0 automatic)
   RasData ras;
   CoarseData co;
   AmgHier amg;                             // on the coarse mean operator
