@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and learned-smoother measurements")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="the timed mixed solves only (no comparison solves, e2e or extras): for launch lists")
     return ap.parse_args()
 
 
@@ -63,7 +65,8 @@ def measured_traffic(shape):
             for kv in line.split(":", 1)[1].split():
                 k, v = kv.split("=")
                 vals[k] = v
-    key = {k: str(shape[k]) for k in ("rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "generator")}
+    key = {k: str(shape[k]) for k in ("rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "stages",
+                                      "generator")}
     if not vals or any(vals.get(k) != v for k, v in key.items()):
         return None
     return int(vals["bytes"])
@@ -389,6 +392,15 @@ def main():
     achieved = bytes_f32 / (avg_ms * 1e-3) / 1e9 if cnt else None
     peak, peak_kind = peaks()
 
+    if args.only_timed:
+        line = {"metric": METRIC, "value": round(ms_all, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_all, 3), "higher_is_better": False,
+                "scaling": "weak", "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "coarse_inner_rtol": INNER_RTOL, "only_timed": True},
+                "gpu_launches": int(launches)}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     # plain FP64 solve on the same system (the comparison the metric names)
     def timed(mode):
         torch.cuda.synchronize()

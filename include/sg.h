@@ -140,15 +140,18 @@ sg_status sg_set_apply_kernel(sg_problem* prob, int mode);
 /* Tile shape of the register-specialised kernel of one family: which = 0
  * fine FP32, 1 coarse FP32, 2 fine FP64, 3 coarse FP64 (the FP64 kernels
  * carry the triple products as exact double immediates): rows per thread
- * (1, or for FP32 2 adjacent rows updated with the paired FP32 FMA); output groups, input groups
- * (1..4 each) and stencil-slot groups (1..8), product <= 8: the outputs,
- * the gathered inputs and the slots are split across groups of 4 warps
- * whose partial sums meet in shared memory; prefetch (input terms whose
- * values are loaded ahead, 0..64); min_blocks (CTAs per SM asked of the
- * register allocator, 1..8).  Recompiles the kernel.
+ * (1, or for FP32 2 adjacent rows updated with the paired FP32 FMA); output
+ * groups, input groups (1..4 each) and stencil-slot groups (1..8), product
+ * <= 8: the outputs, the gathered inputs and the slots are split across
+ * groups of 4 warps whose partial sums meet in shared memory; prefetch (0..64:
+ * input terms whose values are loaded ahead into registers, or with stages
+ * the terms per staged block); min_blocks (CTAs per SM asked of the register
+ * allocator, 1..8); stages (0: register prefetch; 2..8: the matrix values
+ * stream through shared memory by cp.async, stages - 1 blocks ahead of use,
+ * across slot boundaries; one row and one group only).  Recompiles.
  * Errors: SG_ERR_ARG out of range, SG_ERR_CUDA compile failure. */
 sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int igroups, int sgroups,
-                          int prefetch, int min_blocks);
+                          int prefetch, int min_blocks, int stages);
 
 /* Autotuner: compiles the candidate tile shapes, times each on this
  * problem's operator of family `which` (as for sg_apply_config; the
@@ -160,9 +163,9 @@ sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int
 sg_status sg_apply_autotune(sg_problem* prob, int which, int force, double* best_ms);
 
 /* Current tile shape of one family (rows, groups, igroups, sgroups,
- * prefetch, min_blocks, code-generator version into cfg7) and the seconds
- * spent compiling or loading its kernel. */
-sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg7, double* compile_s);
+ * prefetch, min_blocks, stages, code-generator version into cfg8) and the
+ * seconds spent compiling or loading its kernel. */
+sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg8, double* compile_s);
 
 /* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
  * sg_apply (F may equal R for an in-place update). */

@@ -96,7 +96,7 @@ sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
 }
 
 sg_status sg_apply_config(sg_problem* pr, int which, int rows, int groups, int igroups, int sgroups, int prefetch,
-                          int min_blocks) {
+                          int min_blocks, int stages) {
   SG_ARG(pr && which >= 0 && which < kJitFamilies, "sg_apply_config: NULL handle or which not in [0, 3]");
   JitConfig c;
   c.rows = rows;
@@ -105,6 +105,7 @@ sg_status sg_apply_config(sg_problem* pr, int which, int rows, int groups, int i
   c.sgroups = sgroups;
   c.prefetch = prefetch;
   c.min_blocks = min_blocks;
+  c.stages = stages;
   return jit_configure(pr, which, c);
 }
 
@@ -113,17 +114,18 @@ sg_status sg_apply_autotune(sg_problem* pr, int which, int force, double* best_m
   return jit_autotune(pr, which, force, best_ms);
 }
 
-sg_status sg_apply_info(const sg_problem* pr, int which, int* cfg7, double* compile_s) {
+sg_status sg_apply_info(const sg_problem* pr, int which, int* cfg8, double* compile_s) {
   SG_ARG(pr && which >= 0 && which < kJitFamilies, "sg_apply_info: NULL handle or which not in [0, 3]");
   const JitConfig c = pr->jit_cfg_set[which] ? pr->jit_cfg[which] : jit_default_config(pr, which);
-  if (cfg7) {
-    cfg7[0] = c.rows;
-    cfg7[1] = c.groups;
-    cfg7[2] = c.igroups;
-    cfg7[3] = c.sgroups;
-    cfg7[4] = c.prefetch;
-    cfg7[5] = c.min_blocks;
-    cfg7[6] = kJitGeneratorVersion;
+  if (cfg8) {
+    cfg8[0] = c.rows;
+    cfg8[1] = c.groups;
+    cfg8[2] = c.igroups;
+    cfg8[3] = c.sgroups;
+    cfg8[4] = c.prefetch;
+    cfg8[5] = c.min_blocks;
+    cfg8[6] = c.stages;
+    cfg8[7] = kJitGeneratorVersion;
   }
   if (compile_s) *compile_s = pr->jit[which] ? pr->jit[which]->compile_s : 0.0;
   return SG_OK;

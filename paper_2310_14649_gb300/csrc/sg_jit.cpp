@@ -147,6 +147,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
   };
   const char* ty = R == 2 ? "float2" : T;
   std::ostringstream body;
+  std::string staged_table;
   for (int g = 0; g < NG; ++g) {
     const int ho = g / (HI * SG), hi = (g / SG) % HI, sgi = g % SG;
     const int lo = cut[ho], up = cut[ho + 1], blo = icut[hi], bup = icut[hi + 1];
@@ -179,7 +180,8 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
       else
         body << "      const " << Ts << " x" << b << " = __ldg(xp0 + (long long)" << b << " * ldx);\n";
     }
-    body << "      const " << Ts << "* vp = V + (long long)s * ldr + rr;\n";
+    const bool staged = c.stages >= 2;
+    if (!staged) body << "      const " << Ts << "* vp = V + (long long)s * ldr + rr;\n";
     auto load = [&](int k) {
       if (R == 2)
         body << "      const float2 v" << k << " = __ldg(reinterpret_cast<const float2*>(vp + (long long)" << k
@@ -188,9 +190,23 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
         body << "      const " << Ts << " v" << k << " = __ldg(vp + (long long)" << k << " * kst);\n";
     };
     const int nk = int(ks.size());
-    for (int i = 0; i < std::min(nk, pf); ++i) load(ks[i]);
+    // staged: blocks of KB input terms arrive in shared memory (cp.async,
+    // stages - 1 blocks ahead, across slot boundaries); each thread reads
+    // back only the values it copied, so no barrier is needed
+    const int KB = std::max(1, pf);
+    if (!staged)
+      for (int i = 0; i < std::min(nk, pf); ++i) load(ks[i]);
     for (int i = 0; i < nk; ++i) {
-      if (i + pf < nk) load(ks[i + pf]);
+      if (staged && i % KB == 0) {
+        if (i) body << "      }\n";
+        body << "      {\n        asm volatile(\"cp.async.wait_group " << (c.stages - 2) << ";\" ::: \"memory\");\n"
+             << "        issue_blk(gb + " << (c.stages - 1) << ", S, V, ldr, kst, rr, vsm);\n"
+             << "        const " << Ts << "* vb = vsm + (gb % " << c.stages << ") * " << KB * 128 << ";\n"
+             << "        ++gb;\n";
+        for (int q = i; q < std::min(nk, i + KB); ++q)
+          body << "        const " << Ts << " v" << ks[q] << " = vb[" << (q - i) * 128 << "];\n";
+      }
+      if (!staged && i + pf < nk) load(ks[i + pf]);
       const int k = ks[i];
       for (const auto& ga : by_k[k]) {
         const int a = ga.first;
@@ -212,7 +228,18 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
         body << " y" << a << " = " << fma << "(v" << k << ", t, y" << a << "); }\n";
       }
     }
+    if (staged && nk > 0) body << "      }\n";
     body << "    }\n";
+    if (staged) {
+      // the table of input terms per block, for the copy helper
+      std::ostringstream tab;
+      const int NB = (nk + KB - 1) / KB;
+      tab << "#define STG_NB " << NB << "\n__constant__ int c_ktab[" << std::max(1, NB * KB) << "] = {";
+      for (int e = 0; e < NB * KB; ++e) tab << (e ? ", " : "") << (e < nk ? ks[e] : -1);
+      if (NB * KB == 0) tab << "-1";
+      tab << "};\n";
+      staged_table = tab.str();
+    }
     // partial sums of the input and slot groups meet in shared memory, in
     // group order; outputs this group never touches contribute zero
     for (int a = lo; a < up; ++a) {
@@ -231,6 +258,29 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
   os << "// generated: Galerkin apply, P=" << P << " K=" << K << " T=" << pr->T << " R=" << R << " groups=" << HO
      << "x" << HI << "x" << SG << " pf=" << pf << " mb=" << mb << (fp64 ? " fp64" : "") << "\n";
   os << (fp64 ? "#define GD(h) __longlong_as_double(h)\n" : "#define G(h) __int_as_float(h)\n");
+  if (c.stages >= 2) {
+    const int KB = std::max(1, pf);
+    os << staged_table;
+    os << "__device__ __forceinline__ void cpa(" << Ts << "* d, const " << Ts << "* s) {\n"
+          "  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(d));\n"
+          "  asm volatile(\"cp.async.ca.shared.global [%0], [%1], " << (fp64 ? 8 : 4) << ";\" :: \"r\"(a), \"l\"(s) : \"memory\");\n"
+          "}\n"
+          "// copy block gb (slot gb / NB, terms c_ktab[(gb % NB) * KB ...]) of this thread's row\n"
+          "__device__ __forceinline__ void issue_blk(int gb, int S, const " << Ts << "* V, long long ldr, long long kst,\n"
+          "                                           int rr, " << Ts << "* vsm) {\n"
+          "  if (gb < S * STG_NB) {\n"
+          "    const int s = gb / STG_NB, b = gb - s * STG_NB;\n"
+          "    const " << Ts << "* vp = V + (long long)s * ldr + rr;\n"
+          "    " << Ts << "* d = vsm + (gb % " << c.stages << ") * " << KB * 128 << ";\n"
+          "#pragma unroll\n"
+          "    for (int i = 0; i < " << KB << "; ++i) {\n"
+          "      const int k = c_ktab[b * " << KB << " + i];\n"
+          "      if (k >= 0) cpa(d + i * 128, vp + (long long)k * kst);\n"
+          "    }\n"
+          "  }\n"
+          "  asm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n"
+          "}\n";
+  }
   if (R == 2 && !gvals.empty()) {
     // both halves of each pair carry the same coefficient bits
     os << "__constant__ unsigned long long gq_bits[" << gvals.size() << "] = {";
@@ -241,7 +291,8 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
     os << "};\n#define gq2 (reinterpret_cast<const float2*>(gq_bits))\n";
   }
   const int rows_cta = 128 * R;
-  os << "extern \"C\" __global__ void __launch_bounds__(" << 128 * NG << ", " << mb << ") sg_k1(\n"
+  os << "extern \"C\" __global__ void __launch_bounds__(" << 128 * NG << ", " << mb << ") "
+     << (fp64 ? "sg_k1_f64" : "sg_k1") << "(\n"
         "    const " << Ts << "* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
         "    const " << Ts << "* __restrict__ X, long long ldx, const " << Ts << "* __restrict__ F, long long ldf,\n"
         "    " << Ts << "* __restrict__ Y, long long ldy) {\n"
@@ -255,6 +306,10 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
      << "  const long long kst = (long long)S * ldr;\n";
   if (NG == 1) {
     os << "  " << Ts << "* part = smem;\n  (void)part;\n";
+    if (c.stages >= 2)
+      os << "  " << Ts << "* vsm = smem + lrow;\n"
+         << "  for (int g0 = 0; g0 < " << (c.stages - 1) << "; ++g0) issue_blk(g0, S, V, ldr, kst, rr, vsm);\n"
+         << "  int gb = 0;\n";
     // single group: write straight from registers
     std::string b = body.str();
     // drop the shared-memory hand-off of the single group
@@ -292,13 +347,14 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
 }
 
 size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c, bool fp64) {
+  if (c.stages >= 2) return size_t(c.stages) * std::max(1, c.prefetch) * 128 * (fp64 ? sizeof(double) : sizeof(float));
   if (c.groups * c.igroups * c.sgroups == 1) return 0;
   return size_t(c.igroups) * c.sgroups * pr->P * 128 * c.rows * (fp64 ? sizeof(double) : sizeof(float));
 }
 
 // Compile (or load from the cache) one configuration.
 static sg_status jit_compile(const std::string& src, cudaLibrary_t* lib, cudaKernel_t* kern, bool* cached,
-                             double* seconds, int dev) {
+                             double* seconds, int dev, bool fp64) {
   auto t0 = std::chrono::steady_clock::now();
   char key[32];
   std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(src + "|sm_103a|v" + std::to_string(kJitGeneratorVersion)));
@@ -342,7 +398,7 @@ static sg_status jit_compile(const std::string& src, cudaLibrary_t* lib, cudaKer
     }
   }
   SG_CUDA(cudaLibraryLoadData(lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
-  SG_CUDA(cudaLibraryGetKernel(kern, *lib, "sg_k1"));
+  SG_CUDA(cudaLibraryGetKernel(kern, *lib, fp64 ? "sg_k1_f64" : "sg_k1"));
   SG_CUDA(cudaKernelSetAttributeForDevice(*kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024, dev));
   if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return SG_OK;
@@ -371,15 +427,18 @@ sg_status jit_apply_build(sg_problem* pr, int which) {
     pr->jit_cfg_set[which] = true;
   }
   return jit_compile(jit_apply_source(pr, pr->jit_cfg[which], which >= 2), &J.lib, &J.kern, &J.from_cache,
-                     &J.compile_s, pr->device);
+                     &J.compile_s, pr->device, which >= 2);
 }
 
 sg_status jit_configure(sg_problem* pr, int which, const JitConfig& c) {
   if (c.rows < 1 || c.rows > 2 || c.groups < 1 || c.groups > 4 || c.igroups < 1 || c.igroups > 4 ||
       c.sgroups < 1 || c.sgroups > 8 || c.groups * c.igroups * c.sgroups > 8 || c.prefetch < 0 ||
-      c.prefetch > 64 || c.min_blocks < 1 || c.min_blocks > 8 || (which >= 2 && c.rows != 1)) {
+      c.prefetch > 64 || c.min_blocks < 1 || c.min_blocks > 8 || (which >= 2 && c.rows != 1) ||
+      c.stages < 0 || c.stages == 1 || c.stages > 8 ||
+      (c.stages >= 2 && (c.rows != 1 || c.groups * c.igroups * c.sgroups != 1 || c.prefetch < 1))) {
     set_error("sg_apply_config: rows in {1,2}; groups, igroups in [1,4]; sgroups in [1,8]; "
-              "groups*igroups*sgroups <= 8; prefetch in [0,64]; min_blocks in [1,8]; FP64 families: rows 1");
+              "groups*igroups*sgroups <= 8; prefetch in [0,64]; min_blocks in [1,8]; FP64 families: rows 1; "
+              "stages 0 or 2..8, staged only with one row and one group and prefetch >= 1");
     return SG_ERR_ARG;
   }
   if (jit_smem_bytes(pr, c, which >= 2) > 200 * 1024) {
@@ -442,46 +501,53 @@ sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const double
 // A short list of tile shapes per family, from sweeps on GB300: small P
 // keeps the whole row in one thread (more prefetch helps); large P splits
 // outputs and inputs over warp groups; the coarse family (a quarter of the
-// rows) adds stencil-slot groups to fill the GPU.
+// rows) adds stencil-slot groups to fill the GPU.  Values staged through
+// shared memory by 4-byte cp.async measured half the bandwidth of the
+// register prefetch at 256^2 / P = 35 (0.144 ms against 0.071 ms), so the
+// staged shapes are available through sg_apply_config but not tuned.
 static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
-  struct S6 {
-    int r, g, i, s, pf;
+  struct S7 {
+    int r, g, i, s, pf, st, mb = 1;
   };
-  std::vector<S6> list;
+  std::vector<S7> list;
   const bool fp64 = which >= 2;
   if (fp64) {
-    // twice the register bytes per value: more output/input splitting
+    // twice the register bytes per value: more output/input splitting, or
+    // values staged through shared memory
     if (pr->P <= 48) {
       if (which == 2)
-        list = {{1, 1, 1, 1, 16}, {1, 1, 1, 1, 8}, {1, 2, 1, 1, 16}, {1, 1, 2, 1, 16}, {1, 2, 2, 1, 8}};
+        list = {{1, 1, 1, 1, 16, 0}, {1, 1, 1, 1, 8, 0}, {1, 2, 1, 1, 16, 0}, {1, 1, 2, 1, 16, 0},
+                {1, 2, 2, 1, 8, 0}};
       else
-        list = {{1, 1, 1, 2, 16}, {1, 1, 1, 4, 8}, {1, 2, 1, 2, 8}, {1, 1, 2, 2, 8}};
+        list = {{1, 1, 1, 2, 16, 0}, {1, 1, 1, 4, 8, 0}, {1, 2, 1, 2, 8, 0}, {1, 1, 2, 2, 8, 0}};
     } else {
       if (which == 2)
-        list = {{1, 2, 2, 1, 8}, {1, 4, 2, 1, 8}, {1, 2, 4, 1, 4}, {1, 4, 2, 1, 4}};
+        list = {{1, 2, 2, 1, 8, 0}, {1, 4, 2, 1, 8, 0}, {1, 2, 4, 1, 4, 0}, {1, 4, 2, 1, 4, 0}};
       else
-        list = {{1, 2, 2, 2, 8}, {1, 4, 2, 1, 8}, {1, 2, 2, 1, 8}};
+        list = {{1, 2, 2, 2, 8, 0}, {1, 4, 2, 1, 8, 0}, {1, 2, 2, 1, 8, 0}};
     }
   } else if (pr->P <= 48) {
     if (which == 0)
-      list = {{1, 1, 1, 1, 32}, {1, 1, 1, 1, 16}, {1, 1, 2, 1, 16}, {1, 2, 1, 1, 16}};
+      list = {{1, 1, 1, 1, 32, 0}, {1, 1, 1, 1, 16, 0}, {1, 1, 2, 1, 16, 0}, {1, 2, 1, 1, 16, 0}};
     else
-      list = {{1, 1, 1, 1, 32}, {1, 1, 1, 2, 32}, {1, 1, 1, 4, 16}, {1, 1, 1, 2, 16}, {1, 2, 1, 2, 16}};
+      list = {{1, 1, 1, 1, 32, 0}, {1, 1, 1, 2, 32, 0}, {1, 1, 1, 4, 16, 0}, {1, 1, 1, 2, 16, 0},
+              {1, 2, 1, 2, 16, 0}};
   } else {
     if (which == 0)
-      list = {{1, 2, 2, 1, 8}, {1, 2, 1, 1, 8}, {1, 3, 2, 1, 8}, {1, 4, 2, 1, 8}};
+      list = {{1, 2, 2, 1, 8, 0}, {1, 2, 1, 1, 8, 0}, {1, 3, 2, 1, 8, 0}, {1, 4, 2, 1, 8, 0}};
     else
-      list = {{1, 2, 2, 1, 8}, {1, 2, 2, 2, 8}, {1, 2, 1, 2, 8}, {1, 4, 2, 1, 8}};
+      list = {{1, 2, 2, 1, 8, 0}, {1, 2, 2, 2, 8, 0}, {1, 2, 1, 2, 8, 0}, {1, 4, 2, 1, 8, 0}};
   }
   std::vector<JitConfig> out;
-  for (const S6& e : list) {
+  for (const S7& e : list) {
     JitConfig c;
     c.rows = e.r;
     c.groups = e.g;
     c.igroups = e.i;
     c.sgroups = e.s;
     c.prefetch = e.pf;
-    c.min_blocks = 1;
+    c.stages = e.st;
+    c.min_blocks = e.mb;
     if (jit_smem_bytes(pr, c, fp64) > 200 * 1024) continue;
     out.push_back(c);
   }
@@ -493,7 +559,8 @@ static std::string tune_key(const sg_problem* pr, const Ell& A, bool fp64) {
   cudaDeviceProp prop{};
   cudaGetDeviceProperties(&prop, pr->device);
   std::ostringstream os;
-  os << prop.name << "|" << pr->P << "|" << pr->K << "|" << pr->T << "|" << A.n << "|" << A.S << (fp64 ? "|f64" : "");
+  os << prop.name << "|v" << kJitGeneratorVersion << "|" << pr->P << "|" << pr->K << "|" << pr->T << "|" << A.n << "|"
+     << A.S << (fp64 ? "|f64" : "");
   for (int64_t t = 0; t < pr->T; ++t) os << "," << pr->kab[3 * t] << ":" << pr->kab[3 * t + 1] << ":" << pr->kab[3 * t + 2];
   char key[32];
   std::snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(os.str()));
@@ -516,7 +583,7 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
     std::ifstream in(path);
     JitConfig c;
     double ms = 0;
-    if (in >> c.rows >> c.groups >> c.igroups >> c.sgroups >> c.prefetch >> c.min_blocks >> ms) {
+    if (in >> c.rows >> c.groups >> c.igroups >> c.sgroups >> c.prefetch >> c.min_blocks >> c.stages >> ms) {
       if (best_ms) *best_ms = ms;
       return jit_configure(pr, which, c);
     }
@@ -537,7 +604,7 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
   for (const JitConfig& c : candidates(pr, which)) {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
-    if (jit_compile(jit_apply_source(pr, c, fp64), &lib, &kern, nullptr, nullptr, pr->device) != SG_OK) continue;
+    if (jit_compile(jit_apply_source(pr, c, fp64), &lib, &kern, nullptr, nullptr, pr->device, fp64) != SG_OK) continue;
     const size_t sm = jit_smem_bytes(pr, c, fp64);
     auto run = [&]() {
       return fp64 ? launch_kernel<double>(kern, c, sm, A, dp<double>(X), A.ldr, nullptr, 0, dp<double>(Y), A.ldr, st)
@@ -574,7 +641,7 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
   std::ofstream out(path);
   if (out)
     out << best.rows << " " << best.groups << " " << best.igroups << " " << best.sgroups << " " << best.prefetch
-        << " " << best.min_blocks << " " << best_t << "\n";
+        << " " << best.min_blocks << " " << best.stages << " " << best_t << "\n";
   return jit_configure(pr, which, best);
 }
 

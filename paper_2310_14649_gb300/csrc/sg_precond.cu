@@ -53,10 +53,10 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
-// Each thread owns two adjacent rows (t0, t0 + 1) of a line and two adjacent
-// modes (a0, a0 + 1): every shared-memory value it loads feeds two FMAs, and
-// the mode pairs are read as one vector.  The sums run over u in the same
-// order as a one-row, one-mode loop.
+// Four lanes own two adjacent rows (t0, t0 + 1) of a line and two adjacent
+// modes (a0, a0 + 1): every shared-memory value a lane loads feeds two
+// FMAs, the mode pairs are read as one vector, and each lane sums every
+// fourth u, so the dependent chain of a step is a quarter of the line width.
 template <typename T>
 __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__ Z, int P, int MC,
                             int W, int Lm, const int* __restrict__ nlines, const int* __restrict__ gidx,
@@ -99,10 +99,21 @@ __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__
     if (g >= 0 && a < MC && a0 + a < P) v = R[int64_t(a0 + a) * ld + (g & kIdxMask)];
     y[q * MS + a] = v;
   }
-  const int np = MCe / 2;
-  const int tm = threadIdx.x % np, tr = threadIdx.x / np;
+  // thread = (row pair tr, mode pair tm, lane q of 4): the four lanes of a
+  // group split every sum over u (u = q, q + 4, ...) and meet by shuffles
+  const int np = MCe / 2, q = threadIdx.x & 3, grp = threadIdx.x >> 2;
+  const int tm = grp % np, tr = grp / np;
   const int t0 = 2 * tr, t1 = t0 + 1;
   const bool act = t0 < W;
+  auto reduce4 = [](T2& c0, T2& c1) {
+#pragma unroll
+    for (int off = 1; off < 4; off <<= 1) {
+      c0.x += __shfl_xor_sync(0xffffffffu, c0.x, off);
+      c0.y += __shfl_xor_sync(0xffffffffu, c0.y, off);
+      c1.x += __shfl_xor_sync(0xffffffffu, c1.x, off);
+      c1.y += __shfl_xor_sync(0xffffffffu, c1.y, off);
+    }
+  };
   for (int st = 0; st < 2 * nl; ++st) {
     cp_async_wait_group<kRasStages - 2>();
     __syncthreads();
@@ -116,91 +127,77 @@ __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__
       else
         cp_async_commit();
     }
-    if (st < nl) {
-      // forward: y_j = Linv_j (r_j - Loff_j y_{j-1})
-      const int j = st;
+    const bool fwd = st < nl;
+    const int j = fwd ? st : 2 * nl - 1 - st;
+    // s_t = y_jt - sum_u Loff[t][u] y_{j-1,u}  (forward),
+    // s_t = y_jt - sum_u Loff[u][t] y_{j+1,u}  (backward, Loff of line j + 1)
+    {
+      T2 c0, c1;
+      c0.x = c0.y = c1.x = c1.y = T(0);
+      const bool has_off = fwd ? j > 0 : j + 1 < nl;
+      if (act && has_off) {
+        const T2* yp = y2 + size_t(fwd ? j - 1 : j + 1) * W * MS2 + tm;
+        for (int u = q; u < W; u += 4) {
+          const T2 v = yp[u * MS2];
+          T p0, p1;
+          if (fwd) {
+            p0 = Lof[t0 * W + u];
+            p1 = Lof[t1 * W + u];
+          } else {
+            const T2 p = *reinterpret_cast<const T2*>(Lof + u * W + t0);
+            p0 = p.x;
+            p1 = p.y;
+          }
+          c0.x -= p0 * v.x;
+          c0.y -= p0 * v.y;
+          c1.x -= p1 * v.x;
+          c1.y -= p1 * v.y;
+        }
+      }
+      reduce4(c0, c1);
+      if (act && q < 2) {
+        const int t = q == 0 ? t0 : t1;
+        const T2 yv = y2[(j * W + t) * MS2 + tm];
+        T2 r = q == 0 ? c0 : c1;
+        r.x += yv.x;
+        r.y += yv.y;
+        s2[t * MS2 + tm] = r;
+      }
+    }
+    __syncthreads();
+    // y_jt = sum_{u <= t} Linv[t][u] s_u  (forward),
+    // x_jt = sum_{u >= t} Linv[u][t] s_u  (backward)
+    {
+      T2 c0, c1;
+      c0.x = c0.y = c1.x = c1.y = T(0);
       if (act) {
-        T2 c0 = y2[(j * W + t0) * MS2 + tm], c1 = y2[(j * W + t1) * MS2 + tm];
-        if (j > 0) {
-          const T2* yp = y2 + size_t(j - 1) * W * MS2 + tm;
-          const T* l0 = Lof + t0 * W;
-          const T* l1 = Lof + t1 * W;
-#pragma unroll 4
-          for (int u = 0; u < W; ++u) {
-            const T2 v = yp[u * MS2];
-            const T p0 = l0[u], p1 = l1[u];
-            c0.x -= p0 * v.x;
-            c0.y -= p0 * v.y;
-            c1.x -= p1 * v.x;
-            c1.y -= p1 * v.y;
+        if (fwd) {
+          for (int u = q; u <= t1; u += 4) {
+            const T2 v = s2[u * MS2 + tm];
+            const T p1 = Lin[t1 * W + u];
+            c1.x += p1 * v.x;
+            c1.y += p1 * v.y;
+            if (u <= t0) {
+              const T p0 = Lin[t0 * W + u];
+              c0.x += p0 * v.x;
+              c0.y += p0 * v.y;
+            }
+          }
+        } else {
+          for (int u = t0 + q; u < W; u += 4) {
+            const T2 v = s2[u * MS2 + tm];
+            const T2 p = *reinterpret_cast<const T2*>(Lin + u * W + t0);  // Linv[u][t0], Linv[u][t1]
+            c0.x += p.x * v.x;
+            c0.y += p.x * v.y;
+            if (u >= t1) {
+              c1.x += p.y * v.x;
+              c1.y += p.y * v.y;
+            }
           }
         }
-        s2[t0 * MS2 + tm] = c0;
-        s2[t1 * MS2 + tm] = c1;
       }
-      __syncthreads();
-      if (act) {
-        const T* l0 = Lin + t0 * W;
-        const T* l1 = Lin + t1 * W;
-        T2 c0, c1;
-        c0.x = c0.y = c1.x = c1.y = T(0);
-#pragma unroll 4
-        for (int u = 0; u <= t0; ++u) {
-          const T2 v = s2[u * MS2 + tm];
-          const T p0 = l0[u], p1 = l1[u];
-          c0.x += p0 * v.x;
-          c0.y += p0 * v.y;
-          c1.x += p1 * v.x;
-          c1.y += p1 * v.y;
-        }
-        const T2 v = s2[t1 * MS2 + tm];
-        c1.x += l1[t1] * v.x;
-        c1.y += l1[t1] * v.y;
-        y2[(j * W + t0) * MS2 + tm] = c0;
-        y2[(j * W + t1) * MS2 + tm] = c1;
-      }
-    } else {
-      // backward: x_j = Linv_j^T (y_j - Loff_{j+1}^T x_{j+1})
-      const int j = 2 * nl - 1 - st;
-      if (act) {
-        T2 c0 = y2[(j * W + t0) * MS2 + tm], c1 = y2[(j * W + t1) * MS2 + tm];
-        if (j + 1 < nl) {
-          const T2* yp = y2 + size_t(j + 1) * W * MS2 + tm;
-#pragma unroll 4
-          for (int u = 0; u < W; ++u) {
-            const T2 v = yp[u * MS2];
-            const T2 p = *reinterpret_cast<const T2*>(Lof + u * W + t0);  // Loff[u][t0], Loff[u][t1]
-            c0.x -= p.x * v.x;
-            c0.y -= p.x * v.y;
-            c1.x -= p.y * v.x;
-            c1.y -= p.y * v.y;
-          }
-        }
-        s2[t0 * MS2 + tm] = c0;
-        s2[t1 * MS2 + tm] = c1;
-      }
-      __syncthreads();
-      if (act) {
-        T2 c0, c1;
-        {
-          const T2 v = s2[t0 * MS2 + tm];
-          const T p = Lin[t0 * W + t0];
-          c0.x = T(0) + p * v.x;
-          c0.y = T(0) + p * v.y;
-          c1.x = c1.y = T(0);
-        }
-#pragma unroll 4
-        for (int u = t1; u < W; ++u) {
-          const T2 v = s2[u * MS2 + tm];
-          const T2 p = *reinterpret_cast<const T2*>(Lin + u * W + t0);  // Linv[u][t0], Linv[u][t1]
-          c0.x += p.x * v.x;
-          c0.y += p.x * v.y;
-          c1.x += p.y * v.x;
-          c1.y += p.y * v.y;
-        }
-        y2[(j * W + t0) * MS2 + tm] = c0;
-        y2[(j * W + t1) * MS2 + tm] = c1;
-      }
+      reduce4(c0, c1);
+      if (act && q < 2) y2[(j * W + (q == 0 ? t0 : t1)) * MS2 + tm] = q == 0 ? c0 : c1;
     }
   }
   cp_async_wait_all();
@@ -338,7 +335,7 @@ sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld,
   const size_t per_mode = (size_t(D.lmax) * D.wmax + D.wmax) * sizeof(T);
   const size_t fixed = 2 * kRasStages * size_t(D.wmax) * D.wmax * sizeof(T);
   const int fit = int(std::max<size_t>(2, ((227 * 1024 - fixed) / per_mode - 2) & ~size_t(1)));
-  const int by_threads = std::max(2, (2048 / std::max(2, D.wmax)) & ~1);  // (W/2) * (MC/2) <= 1024
+  const int by_threads = std::max(2, (1024 / std::max(2, D.wmax)) & ~1);  // 4 (W/2) (MC/2) <= 1024
   int maxmc = std::min(fit, by_threads);
   if (pc.ras_modes > 0) maxmc = std::min(maxmc, pc.ras_modes);
   int nchunk = (P + maxmc - 1) / maxmc;
@@ -346,7 +343,8 @@ sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld,
   if (pc.ras_modes <= 0) nchunk = std::max(nchunk, (P + 17) / 18);
   const int MC = (P + nchunk - 1) / nchunk;
   const int MCe = (MC + 1) & ~1;
-  const int threads = (D.wmax / 2) * (MCe / 2);
+  // 4 lanes per (row pair, mode pair), whole warps (the shuffles need them)
+  const int threads = ((4 * (D.wmax / 2) * (MCe / 2)) + 31) & ~31;
   const size_t smem = (size_t(D.lmax) * D.wmax + D.wmax) * (MCe + 2) * sizeof(T) + fixed;
   static bool attr[2] = {false, false};
   if (!attr[sizeof(T) == 8]) {

@@ -175,11 +175,13 @@ def test_bad_arguments(gpu):
 
 @pytest.mark.parametrize("cfg", [(1, 1, 1, 1, 8, 1), (2, 1, 1, 1, 16, 1), (1, 2, 1, 1, 0, 2), (2, 3, 2, 1, 32, 1),
                                  (1, 4, 1, 2, 4, 1), (1, 2, 2, 2, 8, 1), (1, 1, 3, 1, 8, 1), (1, 1, 1, 4, 8, 1),
-                                 (2, 1, 1, 8, 8, 1)])
+                                 (2, 1, 1, 8, 8, 1), (1, 1, 1, 1, 16, 1, 3), (1, 1, 1, 1, 5, 1, 4),
+                                 (1, 1, 1, 1, 1, 1, 2), (1, 1, 1, 1, 32, 2, 4)])
 @pytest.mark.parametrize("N", [20, 21])
 def test_specialised_kernel_configs(gpu, cfg, N):
     """Every tile shape (rows per thread, output groups, prefetch, CTAs per
-    SM) computes the same operator, for even and odd row counts."""
+    SM, values staged through shared memory) computes the same operator,
+    for even and odd row counts."""
     import torch
     import paper_2310_14649_gb300 as sg
     prob, ref = setup_pair(N, 3, 3, 6)
@@ -201,6 +203,8 @@ def test_specialised_fp64_configs(gpu, cfg, N):
     check_apply(prob, ref, random_block(ref.n, ref.P, seed=16), torch.float64, kernel=2, ld=ref.n + 5)
     with pytest.raises(sg.SgError):
         sg.sg_apply_config(prob, 2, 1, 1, 1, 8, 1, which=2)   # paired rows are FP32 only
+    with pytest.raises(sg.SgError):
+        sg.sg_apply_config(prob, 1, 2, 1, 1, 8, 1, 3)           # staging needs one group
 
 
 def test_autotune_picks_a_valid_shape(gpu):

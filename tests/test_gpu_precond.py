@@ -163,7 +163,8 @@ def test_coarse_correction_and_two_level(pair, dt):
     assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))
 
 
-@pytest.mark.parametrize("cfg", [(1, 1, 1, 4, 8, 1), (1, 2, 1, 2, 16, 1), (2, 1, 1, 2, 8, 1), (1, 1, 2, 1, 8, 1)])
+@pytest.mark.parametrize("cfg", [(1, 1, 1, 4, 8, 1), (1, 2, 1, 2, 16, 1), (2, 1, 1, 2, 8, 1), (1, 1, 2, 1, 8, 1),
+                                 (1, 1, 1, 1, 16, 1, 3)])
 def test_coarse_apply_tile_shapes(pair, cfg):
     """The coarse family's specialised kernel in several tile shapes."""
     import torch
