@@ -379,7 +379,8 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     ms_all = max_over_ranks(world, ms)
     kinds = {}
-    for kind, name in ((0, "apply_fine_f32"), (1, "apply_fine_f64"), (2, "apply_coarse_f32"), (3, "apply_coarse_f64")):
+    for kind, name in ((0, "apply_fine_f32"), (1, "apply_fine_f64"), (2, "apply_coarse_f32"), (3, "apply_coarse_f64"),
+                       (4, "ras_local_f32")):
         cnt, kms = sg.sg_profile_read(prob, kind)
         kinds[name] = (cnt, kms)
     sg.sg_profile(prob, False)
@@ -391,6 +392,12 @@ def main():
     avg_ms = kms / max(cnt, 1)
     achieved = bytes_f32 / (avg_ms * 1e-3) / 1e9 if cnt else None
     peak, peak_kind = peaks()
+    # the RAS local solves, the top kernel of the timed solve by device time
+    ras_flops, ras_boxes, ras_w = sg.sg_precond_stats(prob)
+    rcnt, rms = kinds["ras_local_f32"]
+    ras_avg = rms / max(rcnt, 1)
+    ras_tflops = ras_flops / (ras_avg * 1e-3) / 1e12 if rcnt else None
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 
     if args.only_timed:
         line = {"metric": METRIC, "value": round(ms_all, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -477,6 +484,15 @@ def main():
                      "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
                      "peak_source": peak_kind, "bytes_per_launch": bytes_f32, "avg_launch_ms": avg_ms,
                      "launches": cnt, "traffic": measured_traffic(sg.sg_apply_info(prob))},
+        "roofline_top_kernel": {"kernel": "k_ras_local FP32 (RAS line solves, %d boxes, line width %d)"
+                                          % (ras_boxes, ras_w),
+                                "bound": "alu", "achieved": round(ras_tflops, 2) if ras_tflops else None,
+                                "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                                "frac": round(ras_tflops / fp32_peak, 4) if ras_tflops else None,
+                                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                                "flops_per_launch": ras_flops, "avg_launch_ms": ras_avg, "launches": rcnt,
+                                "note": "latency-bound line recurrences (36 dependent steps per sweep); "
+                                        "a few percent of DRAM bandwidth"},
         "kernel_time_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in kinds.items()},
         "apply_share_of_step": round(tot_kernel / args.steps / ms_all, 3),
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": n * P * 8,

@@ -214,6 +214,12 @@ sg_status sg_precond_setup(sg_problem* prob, const sg_precond_opts* opts, void* 
 sg_status sg_precond_info(const sg_problem* prob, double* omega, int* amg_levels, int64_t* nc,
                           int* inner_its_last);
 
+/* Size of the RAS local solves: useful flops of one application over all P
+ * modes (forward and backward block sweeps: per line the w_l x w_{l-1}
+ * sub-diagonal block and the triangular inverse), number of boxes, padded
+ * line width.  Any pointer may be NULL. */
+sg_status sg_precond_stats(const sg_problem* prob, double* ras_flops, int* ras_boxes, int* ras_wmax);
+
 /* Overlapped node set of box `sub` (ascending global indices) and its owned
  * flags (D_i).  Call with idx = owned = NULL to get the count first. */
 sg_status sg_get_partition(const sg_problem* prob, int sub, int32_t* idx, int64_t* count,
@@ -455,13 +461,14 @@ sg_status sg_mdot(sg_problem* prob, sg_dtype dtype, const void* V, int64_t strid
 sg_status sg_mdot_noalloc(sg_dtype dtype, const void* V, int64_t stride, int nv, const void* w,
                           int64_t len, double* out_dev, void* stream);
 
-/* Per-launch timing of the operator-apply kernels, for benchmarks.  While
- * enabled, every apply launched through this handle is bracketed by CUDA
- * events on its stream (a few microseconds of overhead per launch).
- * Enabling (or disabling) clears the records.  sg_profile_read waits for
- * the recorded events and returns the number of launches and their summed
- * device time in ms for one kind: 0 fine FP32, 1 fine FP64, 2 coarse FP32,
- * 3 coarse FP64. */
+/* Per-launch timing of the operator-apply and RAS local-solve kernels, for
+ * benchmarks.  While enabled, every such launch through this handle (outside
+ * recorded graphs) is bracketed by CUDA events on its stream (a few
+ * microseconds of overhead per launch).  Enabling (or disabling) clears the
+ * records.  sg_profile_read waits for the recorded events and returns the
+ * number of launches and their summed device time in ms for one kind:
+ * 0 fine apply FP32, 1 fine apply FP64, 2 coarse apply FP32, 3 coarse apply
+ * FP64, 4 RAS local solve FP32, 5 RAS local solve FP64. */
 sg_status sg_profile(sg_problem* prob, int enable);
 sg_status sg_profile_read(sg_problem* prob, int kind, int64_t* launches, double* ms);
 

@@ -17,7 +17,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
-           "sg_mdot_noalloc", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
+           "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
            "sg_train_precond", "sg_precond_set_smoother", "cnn_flatten", "cnn_unflatten", "sg_cnn_set_loss",
            "Batch", "sg_batch_create", "sg_batch_solve", "sg_batch_destroy", "sg_solve_batch",
@@ -156,6 +156,13 @@ def sg_precond_info(prob):
     call("sg_precond_info", prob.handle, ctypes.byref(om), ctypes.byref(lev), ctypes.byref(nc),
          ctypes.byref(inner))
     return om.value, lev.value, nc.value, inner.value
+
+
+def sg_precond_stats(prob):
+    """(RAS useful flops per application, boxes, padded line width)."""
+    f, nb, w = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+    call("sg_precond_stats", prob.handle, ctypes.byref(f), ctypes.byref(nb), ctypes.byref(w))
+    return f.value, nb.value, w.value
 
 
 def sg_get_partition(prob, sub):

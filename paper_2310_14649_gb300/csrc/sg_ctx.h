@@ -491,7 +491,7 @@ struct SolverCtx {
       ++h.count;
     }
     if (pc->use_cnn) return cnn_smooth<T>(pr, *pc, R, ld, Z, true, st);
-    return ras_apply<T>(*pc, pr->n, pr->P, R, ld, Z, st, true);
+    return ras_apply<T>(*pc, pr->n, pr->P, R, ld, Z, st, true, &pr->prof);
   }
   // two-level cycle: z = S r; z += Q (r - A z); z += S (r - A z)
   sg_status twolevel(const T* R, T* Z, cudaStream_t st) {

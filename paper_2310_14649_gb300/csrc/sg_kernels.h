@@ -16,9 +16,10 @@ struct AmgWork {
 template <typename T>
 sg_status spmm(const DevCsr& A, const T* X, int64_t ldx, const T* B, int64_t ldb, T* Y, int64_t ldy, int P,
                int op, cudaStream_t st);
+// prof (may be NULL): times the local-solve launch as kind 4 (FP32) / 5 (FP64)
 template <typename T>
 sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld, T* Z, cudaStream_t st,
-                    bool transform);
+                    bool transform, Profiler* prof = nullptr);
 template <typename T>
 sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st);
 template <typename T>

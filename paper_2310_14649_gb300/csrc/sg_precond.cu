@@ -329,7 +329,7 @@ sg_status spmm(const DevCsr& A, const T* X, int64_t ldx, const T* B, int64_t ldb
 
 template <typename T>
 sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld, T* Z, cudaStream_t st,
-                    bool transform) {
+                    bool transform, Profiler* prof) {
   const RasData& D = pc.ras;
   // modes per CTA: at most what shared memory holds
   const size_t per_mode = (size_t(D.lmax) * D.wmax + D.wmax) * sizeof(T);
@@ -356,10 +356,14 @@ sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld,
     return SG_ERR_UNSUPPORTED;
   }
   dim3 grid(unsigned(D.nbox), unsigned(nchunk));
+  size_t slot = 0;
+  const bool timed = prof && prof->on;
+  if (timed) SG_TRY(prof->begin(sizeof(T) == 8 ? 5 : 4, st, slot));
   k_ras_local<T><<<grid, threads, smem, st>>>(R, ld, Z, P, MC, D.wmax, D.lmax, D.d_nlines.as<int>(),
                                               D.d_gidx.as<int>(), dv<T>(D.linv64, D.linv32),
                                               dv<T>(D.loff64, D.loff32)); note_launch();
   SG_CUDA(cudaGetLastError());
+  if (timed) SG_TRY(prof->end(slot, st));
   if (transform) SG_TRY(node_transform<T>(Z, ld, n, P, dv<T>(pc.gtinv64, pc.gtinv32), st));
   return SG_OK;
 }
@@ -460,7 +464,8 @@ sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w) {
 #define INST(T)                                                                                           \
   template sg_status spmm<T>(const DevCsr&, const T*, int64_t, const T*, int64_t, T*, int64_t, int, int,  \
                              cudaStream_t);                                                               \
-  template sg_status ras_apply<T>(const Precond&, int64_t, int, const T*, int64_t, T*, cudaStream_t, bool);        \
+  template sg_status ras_apply<T>(const Precond&, int64_t, int, const T*, int64_t, T*, cudaStream_t, bool,        \
+                                  Profiler*);                                                                      \
   template sg_status node_transform<T>(T*, int64_t, int64_t, int, const T*, cudaStream_t);                \
   template sg_status amg_vcycle<T>(const AmgHier&, AmgWork<T>&, int, cudaStream_t);
 INST(float)

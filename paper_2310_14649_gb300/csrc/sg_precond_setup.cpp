@@ -140,6 +140,7 @@ static sg_status setup_ras(sg_problem* pr, Precond& pc) {
   const int N = pr->N, m = N - 1;
   const int64_t n = pr->n;
   R.nbox = pc.sx * pc.sy;
+  R.flops_per_mode = 0.0;
   std::vector<int32_t> owner(n);
   for (int64_t r = 0; r < n; ++r) {
     int i = int(r % m) + 1, j = int(r / m) + 1;
@@ -187,6 +188,12 @@ static sg_status setup_ras(sg_problem* pr, Precond& pc) {
     }
     R.nlines[b] = int32_t(lines[b].size());
     R.lmax = std::max<int>(R.lmax, R.nlines[b]);
+    // forward and backward sweep: the sub-diagonal block (w_l x w_{l-1}) and
+    // the triangular inverse (w_l (w_l + 1) / 2) per line, 2 flops per term
+    for (size_t l = 0; l < lines[b].size(); ++l) {
+      const double w = lines[b][l][2], wp = l ? lines[b][l - 1][2] : 0.0;
+      R.flops_per_mode += 2.0 * 2.0 * (w * wp + 0.5 * w * (w + 1.0));
+    }
   }
   R.wmax = int(round_up(R.wmax, 4));  // 16-byte matrix rows for cp.async
   const int W = R.wmax, Lm = R.lmax;

@@ -254,7 +254,7 @@ sg_status sg_profile(sg_problem* pr, int enable) {
 }
 
 sg_status sg_profile_read(sg_problem* pr, int kind, int64_t* launches, double* ms) {
-  SG_ARG(pr && kind >= 0 && kind < 4, "sg_profile_read: bad argument");
+  SG_ARG(pr && kind >= 0 && kind < 6, "sg_profile_read: bad argument");
   return pr->prof.read(kind, launches, ms);
 }
 
@@ -273,6 +273,15 @@ sg_status sg_precond_info(const sg_problem* pr, double* omega, int* amg_levels, 
       SG_CUDA(cudaMemcpy(inner_its_last, iv + 1, sizeof(int), cudaMemcpyDeviceToHost));
     }
   }
+  return SG_OK;
+}
+
+sg_status sg_precond_stats(const sg_problem* pr, double* ras_flops, int* ras_boxes, int* ras_wmax) {
+  SG_ARG(pr && pr->solver && pr->solver->pc.ready, "sg_precond_stats: no preconditioner set up");
+  const RasData& R = pr->solver->pc.ras;
+  if (ras_flops) *ras_flops = R.flops_per_mode * pr->P;
+  if (ras_boxes) *ras_boxes = R.nbox;
+  if (ras_wmax) *ras_wmax = R.wmax;
   return SG_OK;
 }
 

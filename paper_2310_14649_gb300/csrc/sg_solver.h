@@ -43,6 +43,7 @@ struct AmgHier {
 // the diagonal blocks and the sub-diagonal blocks, padded to wmax x wmax.
 struct RasData {
   int nbox = 0, wmax = 0, lmax = 0;
+  double flops_per_mode = 0.0;             // useful flops of one local solve per PCE mode
   std::vector<int32_t> nlines;             // per box
   std::vector<std::vector<int32_t>> idx;   // per box: ascending global indices
   std::vector<std::vector<int32_t>> owned; // per box: 1 if owned
