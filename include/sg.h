@@ -333,6 +333,13 @@ sg_status sg_cnn_apply(sg_problem* prob, const float* R_dev, int64_t ldr, float*
 sg_status sg_cnn_train_step(sg_problem* prob, const float* R_dev, int64_t ldr, const float* Zstar_dev,
                             int64_t ldz, int nimg, float lr, int update, double* loss, void* stream);
 
+/* Forward-convolution kernels of the network: 1 (default) the
+ * fifth-generation tensor cores (tcgen05: 128-pixel row tiles, BF16 operands
+ * in shared memory, FP32 accumulators in tensor memory); 0 the BF16 mma.sync
+ * kernels (also used for every backward pass).  sg_cnn_apply returns
+ * SG_ERR_TIMEOUT if a tcgen05 completion wait ran out (no output then). */
+sg_status sg_cnn_set_kernel(sg_problem* prob, int kind);
+
 /* Loss of sg_cnn_train_step: 0 (default) sum_a (e_a^T A_0 e_a) /
  * (z*_a^T A_0 z*_a), e_a = y_a - z*_a / rms(r_a): the error in the energy
  * norm of A_0, which weights the oscillatory error a smoother must remove;

@@ -19,7 +19,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
-           "sg_train_precond", "sg_precond_set_smoother", "cnn_flatten", "cnn_unflatten", "sg_cnn_set_loss",
+           "sg_train_precond", "sg_precond_set_smoother", "cnn_flatten", "cnn_unflatten", "sg_cnn_set_loss", "sg_cnn_set_kernel",
            "Batch", "sg_batch_create", "sg_batch_solve", "sg_batch_destroy", "sg_solve_batch",
            "SgError", "SG_F32", "SG_F64", "PC_TWOLEVEL", "PC_SMOOTH", "PC_COARSE", "PC_AMG",
            "PC_COARSE_APPLY", "PC_RESTRICT", "PC_INTERP", "PC_RAS_LOCAL", "PC_LEARNED",
@@ -358,6 +358,11 @@ def sg_cnn_train_step(prob, R, Zstar, lr=1e-3, update=True, stream=None):
     call("sg_cnn_train_step", prob.handle, dev_ptr(R), R.stride(0), dev_ptr(Zstar), Zstar.stride(0), R.shape[0],
          lr, 1 if update else 0, ctypes.byref(loss), stream_handle(stream))
     return loss.value
+
+
+def sg_cnn_set_kernel(prob, kind):
+    """Forward convolutions: 1 tcgen05 (default), 0 mma.sync."""
+    call("sg_cnn_set_kernel", prob.handle, kind)
 
 
 def sg_cnn_set_loss(prob, kind):

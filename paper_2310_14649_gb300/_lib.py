@@ -113,6 +113,7 @@ SIGNATURES = {
                       ctypes.POINTER(ctypes.c_int), vp],
     "sg_train_precond": [vp, ctypes.POINTER(TrainOpts), ctypes.POINTER(TrainInfo), vp],
     "sg_cnn_set_loss": [vp, ctypes.c_int],
+    "sg_cnn_set_kernel": [vp, ctypes.c_int],
     "sg_precond_set_smoother": [vp, ctypes.c_int, f64, vp],
     "sg_batch_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(SolveOpts), ctypes.POINTER(vp)],
     "sg_batch_solve": [vp, ctypes.POINTER(vp), P_i64, ctypes.POINTER(vp), P_i64, ctypes.POINTER(SolveInfo), vp],

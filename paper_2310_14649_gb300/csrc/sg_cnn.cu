@@ -438,12 +438,15 @@ sg_status Cnn::init(const std::vector<double>& logdiag, int H_, int W_, const st
     off += kCoPad[l];
     SG_TRY(wf[l].alloc(size_t(9) * kCoPad[l] * kCiPad[l] * 2));
     SG_TRY(wr[l].alloc(size_t(9) * kCoPad[l] * kCiPad[l] * 2));
+    SG_TRY(wtc[l].alloc(size_t(9) * kCoPad[l] * kCiPad[l] * 2));
   }
   std::vector<float> ld(logdiag.begin(), logdiag.end());
   SG_TRY(logd.alloc(ld.size() * 4));
   SG_CUDA(cudaMemcpy(logd.ptr, ld.data(), ld.size() * 4, cudaMemcpyHostToDevice));
   SG_TRY(sumsq.alloc(4096 * 8));
   SG_TRY(lossbuf.alloc(2 * 4096 * 8));
+  SG_TRY(tcerr.alloc(16));
+  SG_TRY(conv_tc_attrs());
   ready = true;
   return SG_OK;
 }
@@ -509,6 +512,7 @@ sg_status Cnn::pack(cudaStream_t st) {
     k_pack_weights<<<64, 256, 0, st>>>(dp<float>(params) + woff[l], kCiPad[l], kCoPad[l], dp<bf16>(wf[l]),
                                       dp<bf16>(wr[l])); note_launch();
     SG_CUDA(cudaGetLastError());
+    SG_TRY(conv_tc_pack(dp<float>(params) + woff[l], kCiPad[l], kCoPad[l], wtc[l].ptr, st));
   }
   return SG_OK;
 }
@@ -518,6 +522,12 @@ sg_status Cnn::forward(int nimg, cudaStream_t st) {
   dim3 grid(unsigned((W + TW - 1) / TW), unsigned((H + TH - 1) / TH), unsigned(nimg));
   const float* b[5];
   for (int l = 0; l < 5; ++l) b[l] = dp<float>(params) + boff[l];
+  if (use_tc) {
+    for (int l = 0; l < 5; ++l)
+      SG_TRY(conv_tc_layer(l, act[l].ptr, wtc[l].ptr, b[l], l < 4 ? act[l + 1].ptr : nullptr,
+                           l == 4 ? dp<float>(out) : nullptr, H, W, nimg, dp<int>(tcerr), st));
+    return SG_OK;
+  }
   k_conv<16, 32, 0><<<grid, 128, 0, st>>>(dp<bf16>(act[0]), dp<bf16>(wf[0]), b[0], nullptr, dp<bf16>(act[1]), nullptr, H,
                                           W); note_launch();
   for (int l = 1; l < 4; ++l) {

@@ -1,0 +1,262 @@
+// Forward 3x3 convolution of the learned smoother on the fifth-generation
+// tensor cores (tcgen05): one CTA computes 128 consecutive pixels of kRows
+// image rows for all output channels as implicit GEMMs
+//     D_r[pixel][co] = sum_tap sum_ci A_{r,tap}[pixel][ci] W_tap[co][ci],
+// M = 128 pixels, N = C_out, K = 9 taps x C_in in steps of 16, BF16 operands
+// in shared memory, one FP32 accumulator per row in tensor memory (TMEM).
+// One thread issues the kRows x 9 x C_in / 16 MMAs; their completion arrives
+// on an mbarrier; each warp then reads its 32 pixels of every accumulator
+// and applies bias, ReLU and the BF16 (or FP32) store.
+//
+// Shared-memory operand layout (K-major, no swizzle, the canonical layout of
+// 8-row x 16-byte core matrices): a "plane" holds 8 channels of every row
+// (16 bytes per row, rows 16 bytes apart).  The activation tile is
+// kRows + 2 image rows x 130 pixels (the output rows with their one-pixel
+// halo) per plane, so the A operand of output row r and tap (dy, dx) is the
+// same planes started (r + dy) * 130 + dx rows later: M-adjacent core
+// matrices are 128 bytes apart (SBO) and K-adjacent ones a plane apart
+// (LBO).  Weights are packed the same way, C_out rows per plane, C_in / 8
+// planes per tap.
+#include <cuda_bf16.h>
+
+#include "sg_cnn.h"
+
+namespace sg {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kHalo = 130;  // halo pixels per row: 128 outputs + 2
+constexpr int kRows = 4;    // output rows per CTA (TMEM: 32 columns each)
+constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before the error exit
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: start, LBO (K-adjacent core matrices),
+// SBO (M/N-adjacent core matrices), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t mat_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr uint32_t inst_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+  return uint32_t(__bfloat16_as_ushort(__float2bfloat16(lo))) |
+         (uint32_t(__bfloat16_as_ushort(__float2bfloat16(hi))) << 16);
+}
+
+__device__ __forceinline__ float relu_nan(float x) { return (x > 0.f || x != x) ? x : 0.f; }
+
+// 16-byte global -> shared copy; src_bytes < 16 zero-fills the rest
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+template <int CI, int CO>
+struct TcShape {
+  static constexpr int NPA = CI / 8;            // activation planes
+  static constexpr int PLA = (kRows + 2) * kHalo * 16;  // bytes per activation plane
+  static constexpr int NPB = CI / 8;            // weight planes per tap
+  static constexpr int PLB = CO * 16;           // bytes per weight plane
+  static constexpr int SB = 9 * NPB * PLB;      // weight bytes
+  static constexpr int SA = NPA * PLA;          // activation bytes
+  static constexpr int SMEM = SB + SA + 16;
+};
+
+// EPI 0: bias + ReLU, BF16 out (CO = 32 channels); EPI 1: bias, FP32 out of
+// channel 0 (CO = 16)
+template <int CI, int CO, int EPI>
+__global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ X, const bf16* __restrict__ Wp,
+                                                 const float* __restrict__ bias, bf16* __restrict__ Yb,
+                                                 float* __restrict__ Yf, int H, int W, int* __restrict__ err) {
+  using S = TcShape<CI, CO>;
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint8_t* sB = sm;
+  uint8_t* sA = sm + S::SB;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sA + S::SA);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int img = blockIdx.z, y0 = blockIdx.y * kRows, x0 = blockIdx.x * 128;
+
+  // all tile copies in flight at once (cp.async, 16 bytes each; outside the
+  // image the source size is 0 and the destination is zero-filled)
+  for (int e = tid; e < S::SB / 16; e += 128) cp_async16(sB + 16 * e, Wp + 8 * e, 16);
+  const bf16* Ximg = X + size_t(img) * H * W * CI;
+  for (int e = tid; e < (kRows + 2) * kHalo * S::NPA; e += 128) {
+    const int c8 = e % S::NPA, pos = e / S::NPA;
+    const int hr = pos / kHalo, hc = pos - hr * kHalo;
+    const int gy = y0 + hr - 1, gx = x0 + hc - 1;
+    const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+    const bf16* src = in ? Ximg + (size_t(gy) * W + gx) * CI + c8 * 8 : Ximg;
+    cp_async16(sA + c8 * S::PLA + pos * 16, src, in ? 16 : 0);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "n"(32 * kRows)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  // the tiles written by ordinary stores become visible to the tensor core
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    constexpr uint32_t idesc = inst_desc(128, CO);
+#pragma unroll 1
+    for (int r = 0; r < kRows; ++r) {
+      uint32_t acc = 0;
+#pragma unroll 1
+      for (int t = 0; t < 9; ++t) {
+        const int p0 = (r + t / 3) * kHalo + (t % 3);
+#pragma unroll
+        for (int kc = 0; kc < CI / 16; ++kc) {
+          const uint64_t ad = mat_desc(a0 + uint32_t(2 * kc * S::PLA + p0 * 16), S::PLA, 128);
+          const uint64_t bd = mat_desc(b0 + uint32_t((t * S::NPB + 2 * kc) * S::PLB), S::PLB, 128);
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + uint32_t(32 * r)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+          acc = 1;
+        }
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+  }
+  // accumulator complete (bounded wait; on a timeout the error flag is set
+  // and nothing is stored)
+  uint32_t done = 0;
+  for (int it = 0; it < kWaitLimit && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar))
+        : "memory");
+  const bool ok = __all_sync(0xffffffffu, done != 0);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (!ok) {
+    if (lane == 0) atomicExch(err, 1);
+  } else {
+    const int x = x0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int rr = 0; rr < kRows; ++rr) {
+      const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16) + uint32_t(32 * rr);
+      const int y = y0 + rr;
+      const size_t pix = (size_t(img) * H + y) * W + x;
+      const bool store = x < W && y < H;
+      if (CO == 32) {
+        uint32_t r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (store) {
+          uint32_t o[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            o[c] = pack_bf2(relu_nan(__uint_as_float(r[2 * c]) + bias[2 * c]),
+                            relu_nan(__uint_as_float(r[2 * c + 1]) + bias[2 * c + 1]));
+          uint4* dst = reinterpret_cast<uint4*>(Yb + pix * 32);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        }
+      } else {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (store && EPI == 1) Yf[pix] = __uint_as_float(r[0]) + bias[0];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(32 * kRows) : "memory");
+}
+
+// FP32 padded weights [tap][co][ci] -> BF16 planes [tap][ci / 8][co][8]
+__global__ void k_pack_planes(const float* __restrict__ Wsrc, int ci_pad, int co_pad, bf16* __restrict__ out) {
+  const int total = 9 * co_pad * ci_pad;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int t = e / (co_pad * ci_pad), rem = e - t * co_pad * ci_pad;
+    const int co = rem / ci_pad, ci = rem - co * ci_pad;
+    const size_t dst = ((size_t(t) * (ci_pad / 8) + ci / 8) * co_pad + co) * 8 + (ci % 8);
+    out[dst] = __float2bfloat16(Wsrc[e]);
+  }
+}
+
+template <int CI, int CO, int EPI>
+sg_status launch_tc(const bf16* X, const bf16* Wp, const float* b, bf16* Yb, float* Yf, int H, int W, int nimg,
+                    int* err, cudaStream_t st) {
+  dim3 grid(unsigned((W + 127) / 128), unsigned((H + kRows - 1) / kRows), unsigned(nimg));
+  k_conv_tc<CI, CO, EPI><<<grid, 128, TcShape<CI, CO>::SMEM, st>>>(X, Wp, b, Yb, Yf, H, W, err);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+}  // namespace
+
+sg_status conv_tc_attrs() {
+  static bool done = false;
+  if (done) return SG_OK;
+  SG_CUDA(cudaFuncSetAttribute(k_conv_tc<16, 32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcShape<16, 32>::SMEM));
+  SG_CUDA(cudaFuncSetAttribute(k_conv_tc<32, 32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcShape<32, 32>::SMEM));
+  SG_CUDA(cudaFuncSetAttribute(k_conv_tc<32, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcShape<32, 16>::SMEM));
+  done = true;
+  return SG_OK;
+}
+
+sg_status conv_tc_pack(const float* Wsrc, int ci_pad, int co_pad, void* out, cudaStream_t st) {
+  k_pack_planes<<<64, 256, 0, st>>>(Wsrc, ci_pad, co_pad, static_cast<bf16*>(out));
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+// layer l of the network: 0 (16 -> 32), 1..3 (32 -> 32), 4 (32 -> 16, FP32 out)
+sg_status conv_tc_layer(int l, const void* X, const void* Wp, const float* b, void* Yb, float* Yf, int H, int W,
+                        int nimg, int* err, cudaStream_t st) {
+  const bf16* x = static_cast<const bf16*>(X);
+  const bf16* w = static_cast<const bf16*>(Wp);
+  if (l == 0) return launch_tc<16, 32, 0>(x, w, b, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, st);
+  if (l == 4) return launch_tc<32, 16, 1>(x, w, b, nullptr, Yf, H, W, nimg, err, st);
+  return launch_tc<32, 32, 0>(x, w, b, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, st);
+}
+
+}  // namespace sg

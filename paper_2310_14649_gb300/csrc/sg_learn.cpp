@@ -101,7 +101,26 @@ sg_status sg_cnn_apply(sg_problem* pr, const float* R, int64_t ldr, float* Z, in
   SG_TRY(c.reserve(nimg));
   SG_TRY(c.pack_input<float>(R, ldr, nimg, st));
   SG_TRY(c.forward(nimg, st));
-  return c.unpack_output<float>(Z, ldz, nimg, st);
+  SG_TRY(c.unpack_output<float>(Z, ldz, nimg, st));
+  if (c.use_tc) {  // a tensor-core wait that ran out is reported here
+    int e = 0;
+    SG_CUDA(cudaMemcpyAsync(&e, c.tcerr.ptr, sizeof e, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    if (e) {
+      SG_CUDA(cudaMemsetAsync(c.tcerr.ptr, 0, sizeof e, st));
+      set_error("sg_cnn_apply: a tensor-core completion wait timed out");
+      return SG_ERR_TIMEOUT;
+    }
+  }
+  return SG_OK;
+}
+
+sg_status sg_cnn_set_kernel(sg_problem* pr, int kind) {
+  SG_ARG(pr, "sg_cnn_set_kernel: NULL handle");
+  SG_ARG(kind == 0 || kind == 1, "sg_cnn_set_kernel: kind must be 0 (mma.sync) or 1 (tcgen05)");
+  SG_TRY(ensure_cnn(pr));
+  pr->cnn->use_tc = kind == 1;
+  return SG_OK;
 }
 
 sg_status sg_cnn_train_step(sg_problem* pr, const float* R, int64_t ldr, const float* Zs, int64_t ldz, int nimg,

@@ -64,10 +64,14 @@ def oracle_features(ref, R):
     return x, rms
 
 
-def test_forward_matches_oracle(pair):
+@pytest.mark.parametrize("kernel", [1, 0], ids=["tcgen05", "mma_sync"])
+def test_forward_matches_oracle(pair, kernel):
+    """Both forward-convolution kernels (tcgen05 with TMEM accumulators, and
+    mma.sync) against the oracle."""
     import paper_2310_14649_gb300 as sg
     prob, ref = pair
     params = params_for(7)
+    sg.sg_cnn_set_kernel(prob, kernel)
     sg.sg_cnn_set_weights(prob, params)
     R = random_block(ref.n, ref.P, seed=70).astype(np.float32).astype(np.float64)
     Rd = dev_rows(R)
@@ -81,6 +85,26 @@ def test_forward_matches_oracle(pair):
     scale = np.max(np.abs(Zr))
     assert np.max(np.abs(Z[:, :ref.n] - Zr)) <= 2e-2 * scale
     assert np.linalg.norm(Z[:, :ref.n] - Zr) <= 1e-2 * np.linalg.norm(Zr)
+    sg.sg_cnn_set_kernel(prob, 1)
+
+
+def test_tcgen05_and_mma_sync_agree_on_large_images(gpu):
+    """255 x 255 images (two 128-pixel row tiles, ragged last tile and row
+    group) through both kernels: the FP32 sums of BF16 products agree."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob = sg.sg_setup(256, 2, 1, 2)
+    sg.sg_cnn_set_weights(prob, params_for(13))
+    R = torch.from_numpy(random_block(prob.n, 3, seed=78).T.copy()).float().cuda()
+    out = []
+    for kernel in (1, 0):
+        sg.sg_cnn_set_kernel(prob, kernel)
+        Z = torch.full_like(R, float("nan"))
+        sg.sg_cnn_apply(prob, R, Z)
+        out.append(Z)
+    assert not torch.isnan(out[0]).any()
+    assert (out[0] - out[1]).abs().max().item() <= 1e-2 * out[1].abs().max().item()
+    prob.close()
 
 
 def test_zero_and_constant_images(pair):
