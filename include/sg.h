@@ -148,10 +148,13 @@ sg_status sg_set_apply_kernel(sg_problem* prob, int mode);
  * the terms per staged block); min_blocks (CTAs per SM asked of the register
  * allocator, 1..8); stages (0: register prefetch; 2..8: the matrix values
  * stream through shared memory by cp.async, stages - 1 blocks ahead of use,
- * across slot boundaries; one row and one group only).  Recompiles.
+ * across slot boundaries; one row and one group only); cgroups (1..16: the
+ * outputs split over that many separate 128-thread CTAs per row tile, each
+ * with the full register file of its threads; one row and one group only).
+ * Recompiles.
  * Errors: SG_ERR_ARG out of range, SG_ERR_CUDA compile failure. */
 sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int igroups, int sgroups,
-                          int prefetch, int min_blocks, int stages);
+                          int prefetch, int min_blocks, int stages, int cgroups);
 
 /* Autotuner: compiles the candidate tile shapes, times each on this
  * problem's operator of family `which` (as for sg_apply_config; the
@@ -163,9 +166,9 @@ sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int
 sg_status sg_apply_autotune(sg_problem* prob, int which, int force, double* best_ms);
 
 /* Current tile shape of one family (rows, groups, igroups, sgroups,
- * prefetch, min_blocks, stages, code-generator version into cfg8) and the
- * seconds spent compiling or loading its kernel. */
-sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg8, double* compile_s);
+ * prefetch, min_blocks, stages, cgroups, code-generator version into cfg9)
+ * and the seconds spent compiling or loading its kernel. */
+sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg9, double* compile_s);
 
 /* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
  * sg_apply (F may equal R for an in-place update). */

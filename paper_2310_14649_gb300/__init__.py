@@ -247,8 +247,9 @@ def sg_set_apply_kernel(prob, mode):
     call("sg_set_apply_kernel", prob.handle, mode)
 
 
-def sg_apply_config(prob, rows=1, groups=1, igroups=1, sgroups=1, prefetch=8, min_blocks=1, stages=0, which=0):
-    call("sg_apply_config", prob.handle, which, rows, groups, igroups, sgroups, prefetch, min_blocks, stages)
+def sg_apply_config(prob, rows=1, groups=1, igroups=1, sgroups=1, prefetch=8, min_blocks=1, stages=0, cgroups=1,
+                    which=0):
+    call("sg_apply_config", prob.handle, which, rows, groups, igroups, sgroups, prefetch, min_blocks, stages, cgroups)
 
 
 def sg_apply_autotune(prob, force=False, which=0):
@@ -258,10 +259,10 @@ def sg_apply_autotune(prob, force=False, which=0):
 
 
 def sg_apply_info(prob, which=0):
-    cfg = np.zeros(8, dtype=np.int32)
+    cfg = np.zeros(9, dtype=np.int32)
     cs = ctypes.c_double()
     call("sg_apply_info", prob.handle, which, _lib.ptr(cfg, ctypes.c_int32), ctypes.byref(cs))
-    keys = ["rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "stages", "generator"]
+    keys = ["rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "stages", "cgroups", "generator"]
     out = {k: int(v) for k, v in zip(keys, cfg)}
     out["compile_s"] = cs.value
     return out

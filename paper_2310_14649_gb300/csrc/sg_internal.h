@@ -121,7 +121,7 @@ struct Profiler {
 // families: which = 0 fine FP32, 1 coarse FP32, 2 fine FP64, 3 coarse FP64.
 constexpr int kJitFamilies = 4;
 constexpr int kJitMaxP = 128;
-constexpr int kJitGeneratorVersion = 6;  // bump when the generated code changes
+constexpr int kJitGeneratorVersion = 7;  // bump when the generated code changes
 constexpr int64_t kJitMaxT = 40000;
 struct JitConfig {
   int rows = 1;        // rows per thread (2: paired FP32 FMA)
@@ -132,6 +132,7 @@ struct JitConfig {
   int min_blocks = 1;  // CTAs per SM requested from the register allocator
   int stages = 0;      // 0: matrix values prefetched into registers; >= 2: staged through shared
                        // memory by cp.async in blocks of `prefetch` terms, stages - 1 blocks ahead
+  int cgroups = 1;     // output groups as separate 128-thread CTAs (no register cap from wide CTAs)
 };
 struct JitApply {
   cudaLibrary_t lib = nullptr;

@@ -108,8 +108,13 @@ std::vector<int> output_split(const sg_problem* pr, int H) {
 }  // namespace
 
 std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64) {
-  const int P = pr->P, K = pr->K, R = fp64 ? 1 : c.rows, HO = c.groups, HI = c.igroups, SG = c.sgroups,
-            pf = c.prefetch;
+  // output groups either as 4-warp groups of one CTA (partial sums meet in
+  // shared memory, registers capped by the CTA width) or as separate
+  // 128-thread CTAs (each writes its own outputs; rows shared by
+  // consecutive CTAs, so their matrix values meet in L2)
+  const bool csplit = c.cgroups > 1;
+  const int P = pr->P, K = pr->K, R = fp64 ? 1 : c.rows, HO = csplit ? c.cgroups : c.groups,
+            HI = csplit ? 1 : c.igroups, SG = csplit ? 1 : c.sgroups, pf = c.prefetch;
   // FP64 family: the same code over double values, inputs and outputs, the
   // coefficients as exact double immediates
   const char* T = fp64 ? "double" : "float";
@@ -240,6 +245,15 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
       tab << "};\n";
       staged_table = tab.str();
     }
+    if (csplit) {  // this CTA's outputs, written straight from registers
+      for (int a = lo; a < up; ++a) {
+        const std::string val = has_a[a] ? "y" + std::to_string(a) : std::string(fp64 ? "0.0" : "0.f");
+        body << "    if (r < n) Y[(long long)" << a << " * ldy + r] = F ? F[(long long)" << a << " * ldf + r] - " << val
+             << " : " << val << ";\n";
+      }
+      body << "  }\n";
+      continue;
+    }
     // partial sums of the input and slot groups meet in shared memory, in
     // group order; outputs this group never touches contribute zero
     for (int a = lo; a < up; ++a) {
@@ -291,6 +305,20 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
     os << "};\n#define gq2 (reinterpret_cast<const float2*>(gq_bits))\n";
   }
   const int rows_cta = 128 * R;
+  if (csplit) {
+    os << "extern \"C\" __global__ void __launch_bounds__(128, " << mb << ") " << (fp64 ? "sg_k1_f64" : "sg_k1")
+       << "(\n"
+          "    const " << Ts << "* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
+          "    const " << Ts << "* __restrict__ X, long long ldx, const " << Ts << "* __restrict__ F, long long ldf,\n"
+          "    " << Ts << "* __restrict__ Y, long long ldy) {\n"
+          "  const int grp = blockIdx.x % " << HO << ";\n"
+          "  const int r = (blockIdx.x / " << HO << ") * 128 + threadIdx.x;\n"
+          "  const int rr = r < n ? r : n - 1;\n"
+          "  const long long kst = (long long)S * ldr;\n";
+    os << body.str();
+    os << "}\n";
+    return os.str();
+  }
   os << "extern \"C\" __global__ void __launch_bounds__(" << 128 * NG << ", " << mb << ") "
      << (fp64 ? "sg_k1_f64" : "sg_k1") << "(\n"
         "    const " << Ts << "* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
@@ -347,6 +375,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
 }
 
 size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c, bool fp64) {
+  if (c.cgroups > 1) return 0;
   if (c.stages >= 2) return size_t(c.stages) * std::max(1, c.prefetch) * 128 * (fp64 ? sizeof(double) : sizeof(float));
   if (c.groups * c.igroups * c.sgroups == 1) return 0;
   return size_t(c.igroups) * c.sgroups * pr->P * 128 * c.rows * (fp64 ? sizeof(double) : sizeof(float));
@@ -408,13 +437,18 @@ JitConfig jit_default_config(const sg_problem* pr, int which) {
   const bool fp64 = which >= 2, coarse = which % 2 == 1;
   JitConfig c;
   c.rows = 1;
-  c.prefetch = pr->P <= 48 ? (fp64 ? 16 : 32) : 8;
-  c.groups = pr->P <= 48 ? 1 : 2;
-  c.igroups = pr->P <= 48 ? 1 : 2;
+  c.min_blocks = 1;
+  if (pr->P > 48) {
+    // large P: output groups as separate CTAs keep every register of a
+    // 128-thread CTA for one output range
+    c.prefetch = 8;
+    c.cgroups = std::min(16, (pr->P + (fp64 ? 15 : 23)) / (fp64 ? 16 : 24));
+    return c;
+  }
+  c.prefetch = fp64 ? 16 : 32;
   // the coarse operator has a quarter of the rows: deal the slots to groups
   // so that the grid still fills the GPU
-  c.sgroups = coarse ? (pr->P <= 48 ? 4 : 2) : 1;
-  c.min_blocks = 1;
+  c.sgroups = coarse ? 4 : 1;
   return c;
 }
 
@@ -435,10 +469,13 @@ sg_status jit_configure(sg_problem* pr, int which, const JitConfig& c) {
       c.sgroups < 1 || c.sgroups > 8 || c.groups * c.igroups * c.sgroups > 8 || c.prefetch < 0 ||
       c.prefetch > 64 || c.min_blocks < 1 || c.min_blocks > 8 || (which >= 2 && c.rows != 1) ||
       c.stages < 0 || c.stages == 1 || c.stages > 8 ||
-      (c.stages >= 2 && (c.rows != 1 || c.groups * c.igroups * c.sgroups != 1 || c.prefetch < 1))) {
+      (c.stages >= 2 && (c.rows != 1 || c.groups * c.igroups * c.sgroups != 1 || c.prefetch < 1)) ||
+      c.cgroups < 1 || c.cgroups > 16 ||
+      (c.cgroups > 1 && (c.rows != 1 || c.groups * c.igroups * c.sgroups != 1 || c.stages != 0))) {
     set_error("sg_apply_config: rows in {1,2}; groups, igroups in [1,4]; sgroups in [1,8]; "
               "groups*igroups*sgroups <= 8; prefetch in [0,64]; min_blocks in [1,8]; FP64 families: rows 1; "
-              "stages 0 or 2..8, staged only with one row and one group and prefetch >= 1");
+              "stages 0 or 2..8, staged only with one row and one group and prefetch >= 1; "
+              "cgroups 1..16, split only with one row, one group and no staging");
     return SG_ERR_ARG;
   }
   if (jit_smem_bytes(pr, c, which >= 2) > 200 * 1024) {
@@ -471,8 +508,9 @@ static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, size_t sme
   int n = int(A.n), S = A.S;
   void* args[] = {(void*)&V, (void*)&col, &ldr, &n, &S, (void*)&X, &lx, (void*)&F, &lf, (void*)&Y, &ly};
   const int64_t rows_per_cta = 128LL * c.rows;
-  dim3 grid(unsigned((A.n + rows_per_cta - 1) / rows_per_cta)),
-      block(unsigned(128 * c.groups * c.igroups * c.sgroups));
+  const bool cs = c.cgroups > 1;
+  dim3 grid(unsigned((A.n + rows_per_cta - 1) / rows_per_cta * (cs ? c.cgroups : 1))),
+      block(unsigned(cs ? 128 : 128 * c.groups * c.igroups * c.sgroups));
   SG_CUDA(cudaLaunchKernel((const void*)kern, grid, block, args, smem, st));
   note_launch();
   return SG_OK;
@@ -507,7 +545,7 @@ sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const double
 // staged shapes are available through sg_apply_config but not tuned.
 static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
   struct S7 {
-    int r, g, i, s, pf, st, mb = 1;
+    int r, g, i, s, pf, st, mb = 1, cg = 1;
   };
   std::vector<S7> list;
   const bool fp64 = which >= 2;
@@ -521,10 +559,8 @@ static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
       else
         list = {{1, 1, 1, 2, 16, 0}, {1, 1, 1, 4, 8, 0}, {1, 2, 1, 2, 8, 0}, {1, 1, 2, 2, 8, 0}};
     } else {
-      if (which == 2)
-        list = {{1, 2, 2, 1, 8, 0}, {1, 4, 2, 1, 8, 0}, {1, 2, 4, 1, 4, 0}, {1, 4, 2, 1, 4, 0}};
-      else
-        list = {{1, 2, 2, 2, 8, 0}, {1, 4, 2, 1, 8, 0}, {1, 2, 2, 1, 8, 0}};
+      list = {{1, 1, 1, 1, 8, 0, 1, 4}, {1, 1, 1, 1, 8, 0, 1, 6}, {1, 1, 1, 1, 8, 0, 1, 8},
+              {1, 1, 1, 1, 4, 0, 1, 6}};
     }
   } else if (pr->P <= 48) {
     if (which == 0)
@@ -533,10 +569,8 @@ static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
       list = {{1, 1, 1, 1, 32, 0}, {1, 1, 1, 2, 32, 0}, {1, 1, 1, 4, 16, 0}, {1, 1, 1, 2, 16, 0},
               {1, 2, 1, 2, 16, 0}};
   } else {
-    if (which == 0)
-      list = {{1, 2, 2, 1, 8, 0}, {1, 2, 1, 1, 8, 0}, {1, 3, 2, 1, 8, 0}, {1, 4, 2, 1, 8, 0}};
-    else
-      list = {{1, 2, 2, 1, 8, 0}, {1, 2, 2, 2, 8, 0}, {1, 2, 1, 2, 8, 0}, {1, 4, 2, 1, 8, 0}};
+    list = {{1, 1, 1, 1, 8, 0, 1, 3}, {1, 1, 1, 1, 8, 0, 1, 4}, {1, 1, 1, 1, 16, 0, 1, 4},
+            {1, 1, 1, 1, 8, 0, 1, 6}, {1, 1, 1, 1, 4, 0, 1, 8}};
   }
   std::vector<JitConfig> out;
   for (const S7& e : list) {
@@ -548,6 +582,7 @@ static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
     c.prefetch = e.pf;
     c.stages = e.st;
     c.min_blocks = e.mb;
+    c.cgroups = e.cg;
     if (jit_smem_bytes(pr, c, fp64) > 200 * 1024) continue;
     out.push_back(c);
   }
@@ -583,7 +618,8 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
     std::ifstream in(path);
     JitConfig c;
     double ms = 0;
-    if (in >> c.rows >> c.groups >> c.igroups >> c.sgroups >> c.prefetch >> c.min_blocks >> c.stages >> ms) {
+    if (in >> c.rows >> c.groups >> c.igroups >> c.sgroups >> c.prefetch >> c.min_blocks >> c.stages >> c.cgroups >>
+        ms) {
       if (best_ms) *best_ms = ms;
       return jit_configure(pr, which, c);
     }
@@ -641,7 +677,7 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
   std::ofstream out(path);
   if (out)
     out << best.rows << " " << best.groups << " " << best.igroups << " " << best.sgroups << " " << best.prefetch
-        << " " << best.min_blocks << " " << best.stages << " " << best_t << "\n";
+        << " " << best.min_blocks << " " << best.stages << " " << best.cgroups << " " << best_t << "\n";
   return jit_configure(pr, which, best);
 }
 

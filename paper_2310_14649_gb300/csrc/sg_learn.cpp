@@ -91,7 +91,7 @@ sg_status sg_cnn_get_weights(sg_problem* pr, float* w, int64_t count, int what, 
 }
 
 sg_status sg_cnn_apply(sg_problem* pr, const float* R, int64_t ldr, float* Z, int64_t ldz, int nimg, void* stream) {
-  SG_ARG(pr && R && Z, "sg_cnn_apply: NULL argument");
+  SG_ARG(pr && (nimg == 0 || (R && Z)), "sg_cnn_apply: NULL argument");
   SG_ARG(pr->cnn && pr->cnn->trained, "sg_cnn_apply: no weights set");
   SG_ARG(nimg >= 0 && nimg <= 65535, "sg_cnn_apply: nimg must be in [0, 65535]");
   SG_ARG(ldr >= pr->n && ldz >= pr->n, "sg_cnn_apply: leading dimension < n");

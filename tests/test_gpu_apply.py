@@ -176,7 +176,8 @@ def test_bad_arguments(gpu):
 @pytest.mark.parametrize("cfg", [(1, 1, 1, 1, 8, 1), (2, 1, 1, 1, 16, 1), (1, 2, 1, 1, 0, 2), (2, 3, 2, 1, 32, 1),
                                  (1, 4, 1, 2, 4, 1), (1, 2, 2, 2, 8, 1), (1, 1, 3, 1, 8, 1), (1, 1, 1, 4, 8, 1),
                                  (2, 1, 1, 8, 8, 1), (1, 1, 1, 1, 16, 1, 3), (1, 1, 1, 1, 5, 1, 4),
-                                 (1, 1, 1, 1, 1, 1, 2), (1, 1, 1, 1, 32, 2, 4)])
+                                 (1, 1, 1, 1, 1, 1, 2), (1, 1, 1, 1, 32, 2, 4), (1, 1, 1, 1, 8, 1, 0, 3),
+                                 (1, 1, 1, 1, 16, 1, 0, 5)])
 @pytest.mark.parametrize("N", [20, 21])
 def test_specialised_kernel_configs(gpu, cfg, N):
     """Every tile shape (rows per thread, output groups, prefetch, CTAs per
@@ -191,7 +192,7 @@ def test_specialised_kernel_configs(gpu, cfg, N):
 
 
 @pytest.mark.parametrize("cfg", [(1, 1, 1, 1, 16, 1), (1, 2, 2, 1, 8, 1), (1, 1, 1, 4, 8, 1), (1, 4, 2, 1, 4, 1),
-                                 (1, 2, 4, 1, 4, 1)])
+                                 (1, 2, 4, 1, 4, 1), (1, 1, 1, 1, 8, 1, 0, 4)])
 @pytest.mark.parametrize("N", [20, 21])
 def test_specialised_fp64_configs(gpu, cfg, N):
     """The FP64 family (exact double coefficients) in several tile shapes."""
