@@ -203,6 +203,10 @@ typedef struct {
                           1: the same GMRES driven from the host         */
   int ras_modes;       /* modes per CTA of the RAS local solve kernel
                           (tile shape); <= 0 = automatic                 */
+  int inner_orth_passes; /* Gram-Schmidt passes per Arnoldi step of the
+                          coarse GMRES: 1 (<= 0) = classical, the
+                          PETSc default the paper's runs used (Sec. 5);
+                          2 = classical with one re-orthogonalisation   */
 } sg_precond_opts;
 
 /* Builds partitions, local factors, the coarse space, the AMG hierarchy,
@@ -265,6 +269,9 @@ typedef struct {
   double* hist_host;  /* optional host buffer for the residual history         */
   int hist_cap;
   int no_fallback;    /* 1: keep the learned smoother even when it stagnates   */
+  int orth_passes;    /* Gram-Schmidt passes per Arnoldi step of the outer
+                         (F)GMRES: 1 (<= 0) = classical (PETSc default);
+                         2 = classical with one re-orthogonalisation       */
 } sg_solve_opts;
 
 typedef struct {

@@ -144,9 +144,9 @@ def sg_residual(prob, F, X, R, stream=None):
 
 
 def sg_precond_setup(prob, sx, sy, overlap, omega=0.0, inner_rtol=0.0, inner_max=0, smoother=0,
-                     host_loops=False, ras_modes=0, stream=None):
+                     host_loops=False, ras_modes=0, inner_orth_passes=0, stream=None):
     opts = _lib.PrecondOpts(sx, sy, overlap, omega, inner_rtol, inner_max, smoother, 1 if host_loops else 0,
-                            ras_modes)
+                            ras_modes, inner_orth_passes)
     call("sg_precond_setup", prob.handle, ctypes.byref(opts), stream_handle(stream))
     prob.nc = sg_precond_info(prob)[2]
 
@@ -201,7 +201,7 @@ def sg_precond_apply(prob, which, R, Z, stream=None):
 
 
 def sg_solve(prob, X, F=None, rtol=1e-8, max_it=500, restart=30, mode=0, inner_rtol=0.0, max_ir=0,
-             hist_cap=256, stream=None, allow_not_converged=False, fallback=True):
+             hist_cap=256, stream=None, allow_not_converged=False, fallback=True, orth_passes=0):
     """Solve sum_k A_k X G_k^T = F (F None: the load vector).  X (FP64, [P, ld])
     holds the initial guess and receives the solution.  Returns a dict of
     the solve info (and the residual history)."""
@@ -212,7 +212,7 @@ def sg_solve(prob, X, F=None, rtol=1e-8, max_it=500, restart=30, mode=0, inner_r
     hist = np.zeros(max(hist_cap, 1), dtype=np.float64)
     opts = _lib.SolveOpts(rtol, max_it, restart, mode, inner_rtol, max_ir,
                           hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), hist_cap,
-                          0 if fallback else 1)
+                          0 if fallback else 1, orth_passes)
     info = _lib.SolveInfo()
     allow = (0, 1) if allow_not_converged else (0,)
     st = call("sg_solve", prob.handle, dev_ptr(F) if F is not None else None,
@@ -418,8 +418,8 @@ class Batch:
             pass
 
 
-def _solve_opts(rtol, max_it, restart, mode, inner_rtol, max_ir):
-    return _lib.SolveOpts(rtol, max_it, restart, mode, inner_rtol, max_ir, None, 0, 0)
+def _solve_opts(rtol, max_it, restart, mode, inner_rtol, max_ir, orth_passes=0):
+    return _lib.SolveOpts(rtol, max_it, restart, mode, inner_rtol, max_ir, None, 0, 0, orth_passes)
 
 
 def _ptr_array(ts, allow_none=False):
@@ -436,9 +436,9 @@ def _ld_array(ts):
     return arr
 
 
-def sg_batch_create(probs, rtol=1e-8, max_it=500, restart=30, mode=1, inner_rtol=0.0, max_ir=0):
+def sg_batch_create(probs, rtol=1e-8, max_it=500, restart=30, mode=1, inner_rtol=0.0, max_ir=0, orth_passes=0):
     handles = (ctypes.c_void_p * len(probs))(*[p.handle.value for p in probs])
-    opts = _solve_opts(rtol, max_it, restart, mode, inner_rtol, max_ir)
+    opts = _solve_opts(rtol, max_it, restart, mode, inner_rtol, max_ir, orth_passes)
     h = ctypes.c_void_p()
     call("sg_batch_create", handles, len(probs), ctypes.byref(opts), ctypes.byref(h))
     return Batch(h, probs)
@@ -474,10 +474,10 @@ def sg_batch_destroy(batch):
 
 
 def sg_solve_batch(probs, Xs, Fs=None, rtol=1e-8, max_it=500, restart=30, mode=1, inner_rtol=0.0, max_ir=0,
-                   stream=None, allow_not_converged=False):
+                   stream=None, allow_not_converged=False, orth_passes=0):
     """One-shot batch: record, solve, release."""
     handles = (ctypes.c_void_p * len(probs))(*[p.handle.value for p in probs])
-    opts = _solve_opts(rtol, max_it, restart, mode, inner_rtol, max_ir)
+    opts = _solve_opts(rtol, max_it, restart, mode, inner_rtol, max_ir, orth_passes)
     Fs = Fs if Fs is not None else [None] * len(Xs)
     infos = (_lib.SolveInfo * len(Xs))()
     allow = (0, 1) if allow_not_converged else (0,)

@@ -40,14 +40,14 @@ class PrecondOpts(ctypes.Structure):
     _fields_ = [("sx", ctypes.c_int), ("sy", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("omega", ctypes.c_double), ("inner_rtol", ctypes.c_double),
                 ("inner_max", ctypes.c_int), ("smoother", ctypes.c_int), ("host_loops", ctypes.c_int),
-                ("ras_modes", ctypes.c_int)]
+                ("ras_modes", ctypes.c_int), ("inner_orth_passes", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("restart", ctypes.c_int),
                 ("mode", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_ir", ctypes.c_int),
                 ("hist_host", ctypes.POINTER(ctypes.c_double)), ("hist_cap", ctypes.c_int),
-                ("no_fallback", ctypes.c_int)]
+                ("no_fallback", ctypes.c_int), ("orth_passes", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -24,6 +24,7 @@ struct KrylovWork {
   int64_t len = 0;
   int m = 0;
   bool flexible = false;
+  int passes = 1;  // Gram-Schmidt passes per Arnoldi step: 1 (CGS) or 2 (CGS2)
   DevBuf V, Z, w, tmp, tmp2, state, partial, counter;
   GmresState s{};
   double* host = nullptr;  // pinned: [0] est, [1] h_{j+1,j}, [2] bad, [4..] scalars
@@ -111,6 +112,7 @@ inline sg_status gmres_run(KrylovWork<T>& W, const Op<T>& A, const Op<T>& M, con
   res = GmresResult{};
   std::vector<double> ests;
   bool first = true;
+  if (W.passes == 1) SG_CUDA(cudaMemsetAsync(W.s.hsum + (W.m + 1), 0, (W.m + 1) * sizeof(double), st));
   for (;;) {
     // r0 = F - A x
     if (first && x_zero) {
@@ -146,10 +148,16 @@ inline sg_status gmres_run(KrylovWork<T>& W, const Op<T>& A, const Op<T>& M, con
       double* h2 = W.s.hsum + (W.m + 1);
       SG_TRY(vec_mdot<T>(dp<T>(W.V), len, j + 1, dp<T>(W.w), len, h1, dp<double>(W.partial),
                          dp<unsigned>(W.counter), st));
-      SG_TRY(vec_maxpy_mdot<T>(dp<T>(W.V), len, j + 1, h1, dp<T>(W.w), len, h2, dp<double>(W.partial),
-                               dp<unsigned>(W.counter), st));
-      SG_TRY(vec_maxpy_norm<T>(dp<T>(W.V), len, j + 1, h2, dp<T>(W.w), len, W.s.scal, dp<double>(W.partial),
-                               dp<unsigned>(W.counter), st));
+      if (W.passes == 1) {
+        // one classical pass; the second coefficient column stays zero
+        SG_TRY(vec_maxpy_norm<T>(dp<T>(W.V), len, j + 1, h1, dp<T>(W.w), len, W.s.scal, dp<double>(W.partial),
+                                 dp<unsigned>(W.counter), st));
+      } else {
+        SG_TRY(vec_maxpy_mdot<T>(dp<T>(W.V), len, j + 1, h1, dp<T>(W.w), len, h2, dp<double>(W.partial),
+                                 dp<unsigned>(W.counter), st));
+        SG_TRY(vec_maxpy_norm<T>(dp<T>(W.V), len, j + 1, h2, dp<T>(W.w), len, W.s.scal, dp<double>(W.partial),
+                                 dp<unsigned>(W.counter), st));
+      }
       SG_TRY(gmres_givens(W.s, W.m, j, W.host, st));
       SG_TRY(vec_scale_by<T>(dp<T>(W.w), W.Vj(j + 1), len, W.s.scal + 1, false, st));
       SG_CUDA(cudaStreamSynchronize(st));
@@ -262,6 +270,7 @@ struct SolverCtx {
     lenc = int64_t(pr->P) * ldc;
     SG_TRY(fine.init(len, restart, true));
     SG_TRY(coarse.init(lenc, pc->inner_restart, false));
+    coarse.passes = pc->inner_passes;
     SG_TRY(r1.alloc(len * sizeof(T)));
     SG_TRY(zt.alloc(len * sizeof(T)));
     SG_TRY(consts.alloc(2 * sizeof(double)));
@@ -545,5 +554,8 @@ inline sg_status get_ctx(sg_problem* pr, SolverCtx<T>*& out) {
   out = c.get();
   return SG_OK;
 }
+
+// Gram-Schmidt passes of the outer (F)GMRES chosen by the solve options
+inline int fine_orth_passes(const sg_solve_opts& o) { return o.orth_passes > 0 ? o.orth_passes : 1; }
 
 }  // namespace sg

@@ -53,6 +53,7 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
   cudaGraphConditionalHandle hout, hin;
   SG_CUDA(cudaGraphConditionalHandleCreate(&hout, g, 0, 0));
   SG_CUDA(cudaMemsetAsync(Ec, 0, lenc * sizeof(T), s1));
+  if (W.passes == 1) SG_CUDA(cudaMemsetAsync(h2, 0, (m + 1) * sizeof(double), s1));
   SG_TRY(vec_norm2<T>(Rc, lenc, W.s.scal + 5, part, cnt, s1));
   SG_TRY(dg_init(c.dg, W.s.scal + 5, pc.inner_rtol, hout, s1));
   const int64_t k1 = launch_count();
@@ -76,9 +77,13 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
       SG_TRY(c.coarse_pc_from_b0(tmp, s3));
       SG_TRY(c.apply_raw(tmp, w, nullptr, s3));
       SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h1, part, cnt, jdev, m, s3));
-      SG_TRY(dg_axpy_norm<T>(V, lenc, h1, w, lenc, nullptr, part, cnt, jdev, s3));
-      SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h2, part, cnt, jdev, m, s3));
-      SG_TRY(dg_axpy_norm<T>(V, lenc, h2, w, lenc, W.s.scal, part, cnt, jdev, s3));
+      if (W.passes == 1) {
+        SG_TRY(dg_axpy_norm<T>(V, lenc, h1, w, lenc, W.s.scal, part, cnt, jdev, s3));
+      } else {
+        SG_TRY(dg_axpy_norm<T>(V, lenc, h1, w, lenc, nullptr, part, cnt, jdev, s3));
+        SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h2, part, cnt, jdev, m, s3));
+        SG_TRY(dg_axpy_norm<T>(V, lenc, h2, w, lenc, W.s.scal, part, cnt, jdev, s3));
+      }
       SG_TRY(dg_givens(c.dg, W.s, m, hin, s3));
       SG_TRY(dg_scale_next<T>(w, V, lenc, lenc, c.dg, W.s.scal + 1, s3));
       SG_CUDA(cudaStreamEndCapture(s3, &body_in));
@@ -157,6 +162,7 @@ static sg_status capture_fine(SolverCtx<T>& c, const T* b, T* x, double rtol, bo
   const cudaStream_t f2 = S.s[2], f3 = S.s[3];
 
   const int64_t k0 = launch_count();
+  if (W.passes == 1) SG_CUDA(cudaMemsetAsync(h2, 0, (m + 1) * sizeof(double), top));
   SG_TRY(vec_norm2<T>(b, len, W.s.scal + 5, part, cnt, top));
   cudaStreamCaptureStatus cs;
   cudaGraph_t g;
@@ -181,15 +187,19 @@ static sg_status capture_fine(SolverCtx<T>& c, const T* b, T* x, double rtol, bo
     k2 = launch_count();
     {
       SG_CUDA(cudaStreamBeginCaptureToGraph(f3, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      // Z_j = B V_j, w = A Z_j, CGS2 against V_0..V_j, rotation, V_{j+1}
+      // Z_j = B V_j, w = A Z_j, Gram-Schmidt against V_0..V_j, rotation, V_{j+1}
       SG_TRY(dg_copy_vj<T>(V, len, c.ld, vbuf, c.ld, c.pr->n, c.pr->P, c.fdg, f3));
       SG_TRY(capture_twolevel<T>(c, vbuf, zbuf, f3, S.s[4], S.s[5]));
       SG_TRY(dg_store_j<T>(zbuf, Zs, len, len, c.fdg, f3));
       SG_TRY(c.apply_raw_fine(zbuf, w, nullptr, f3));
       SG_TRY(dg_mdot<T>(V, len, w, len, h1, part, cnt, jdev, m, f3));
-      SG_TRY(dg_axpy_norm<T>(V, len, h1, w, len, nullptr, part, cnt, jdev, f3));
-      SG_TRY(dg_mdot<T>(V, len, w, len, h2, part, cnt, jdev, m, f3));
-      SG_TRY(dg_axpy_norm<T>(V, len, h2, w, len, W.s.scal, part, cnt, jdev, f3));
+      if (W.passes == 1) {
+        SG_TRY(dg_axpy_norm<T>(V, len, h1, w, len, W.s.scal, part, cnt, jdev, f3));
+      } else {
+        SG_TRY(dg_axpy_norm<T>(V, len, h1, w, len, nullptr, part, cnt, jdev, f3));
+        SG_TRY(dg_mdot<T>(V, len, w, len, h2, part, cnt, jdev, m, f3));
+        SG_TRY(dg_axpy_norm<T>(V, len, h2, w, len, W.s.scal, part, cnt, jdev, f3));
+      }
       SG_TRY(dg_givens(c.fdg, W.s, m, hin, f3));
       SG_TRY(dg_scale_next<T>(w, V, len, len, c.fdg, W.s.scal + 1, f3));
       SG_CUDA(cudaStreamEndCapture(f3, &body_in));
@@ -302,6 +312,8 @@ static sg_status prepare_system(GraphSystem& gs, const sg_solve_opts& o) {
   SolverCtx<float>* c32 = nullptr;
   SG_TRY(get_ctx<float>(pr, c32));
   SG_TRY(c32->capture_prepare());
+  c64->fine.passes = fine_orth_passes(o);
+  c32->fine.passes = fine_orth_passes(o);
   // iteration caps of the device-driven loops
   const int cap_fine = o.max_it;
   SG_CUDA(cudaMemcpy(c64->fdg.iv + 2, &cap_fine, sizeof(int), cudaMemcpyHostToDevice));
@@ -371,6 +383,7 @@ sg_status sg_batch_create(sg_problem* const* probs, int count, const sg_solve_op
   SG_ARG(probs && o && out && count >= 1 && count <= 256, "sg_batch_create: need 1..256 problems and options");
   SG_ARG(o->rtol > 0 && o->max_it > 0, "sg_batch_create: rtol and max_it must be > 0");
   SG_ARG(o->mode == 0 || o->mode == 1, "sg_batch_create: mode must be 0 or 1");
+  SG_ARG(o->orth_passes >= 0 && o->orth_passes <= 2, "sg_batch_create: orth_passes must be 0, 1 or 2");
   for (int i = 0; i < count; ++i) {
     SG_ARG(probs[i] && probs[i]->solver && probs[i]->solver->pc.ready,
            "sg_batch_create: every problem needs sg_precond_setup");

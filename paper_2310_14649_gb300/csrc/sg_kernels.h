@@ -41,7 +41,7 @@ struct GmresState {
   double* sn;     // m
   double* g;      // m+1
   double* y;      // m
-  double* hsum;   // 2 (m+1): CGS2 coefficients of the two passes
+  double* hsum;   // 2 (m+1): Gram-Schmidt coefficients of pass 1 and pass 2 (zero with one pass)
   double* scal;   // [0] norm^2 of w, [1] h_{j+1,j}, [2] estimate |g_{j+1}|, [3] beta, [4] flags
 };
 

@@ -1,6 +1,6 @@
 // Krylov building blocks (Sec. 3: FGMRES outer solver, inner GMRES on the
 // coarse problem): fused multi-vector dot products and updates for
-// classical Gram-Schmidt with one re-orthogonalisation (CGS2), the Givens
+// classical Gram-Schmidt (one pass, or two for CGS2), the Givens
 // update of the Hessenberg column and the triangular solve, all on the
 // device.  Dot products accumulate in FP64 across threads; for FP32 vectors
 // each thread first sums its few products in FP32.
@@ -176,7 +176,8 @@ __global__ void k_gmres_init(GmresState s, int m, const double* beta2) {
   }
 }
 
-// Column j of the Hessenberg matrix from the two CGS passes, previous
+// Column j of the Hessenberg matrix from the Gram-Schmidt coefficients of
+// both passes (the second column is zero with one pass), previous
 // rotations, new rotation, residual estimate |g_{j+1}|.
 __global__ void k_gmres_givens(GmresState s, int m, int j, double* host_est) {
   if (threadIdx.x != 0) return;

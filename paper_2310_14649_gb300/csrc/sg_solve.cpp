@@ -212,6 +212,8 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   SG_ARG(o->sx >= 1 && o->sy >= 1 && o->sx <= pr->N - 1 && o->sy <= pr->N - 1,
          "sg_precond_setup: subdomain counts must be in [1, N-1]");
   SG_ARG(o->overlap >= 0 && o->overlap <= 8, "sg_precond_setup: overlap must be in [0, 8]");
+  SG_ARG(o->inner_orth_passes >= 0 && o->inner_orth_passes <= 2,
+         "sg_precond_setup: inner_orth_passes must be 0 (default), 1 or 2");
   SG_ARG(o->smoother == 0 || o->smoother == 1, "sg_precond_setup: smoother must be 0 (RAS) or 1 (learned)");
   SG_ARG(o->smoother == 0 || (pr->cnn && pr->cnn->trained),
          "sg_precond_setup: the learned smoother needs trained or loaded weights");
@@ -228,6 +230,7 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   pc.inner_restart = 30;
   pc.device_loops = o->host_loops == 0;
   pc.ras_modes = o->ras_modes > 0 ? o->ras_modes : 0;
+  pc.inner_passes = o->inner_orth_passes > 0 ? o->inner_orth_passes : 1;
   SG_TRY(kernel_attrs_init());
   sg_status s = precond_setup_host(pr, pc);
   std::vector<double> ginv;
@@ -347,6 +350,7 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
   SG_ARG(ldx >= pr->n && (!F || ldf >= pr->n), "sg_solve: leading dimension < n");
   SG_ARG(o->rtol > 0 && o->max_it > 0, "sg_solve: rtol and max_it must be > 0");
   SG_ARG(o->mode == 0 || o->mode == 1, "sg_solve: mode must be 0 (FP64) or 1 (FP32 in FP64 refinement)");
+  SG_ARG(o->orth_passes >= 0 && o->orth_passes <= 2, "sg_solve: orth_passes must be 0 (default), 1 or 2");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SolverState& S = *pr->solver;
   S.restart = o->restart > 0 ? std::min(o->restart, 31) : 30;
@@ -371,6 +375,7 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
   SG_CUDA(cudaMemcpy2DAsync(x64, ld * 8, X, ldx * 8, pr->n * 8, P, cudaMemcpyDeviceToDevice, st));
   SolverCtx<double>* c64 = nullptr;
   SG_TRY(get_ctx<double>(pr, c64));
+  c64->fine.passes = fine_orth_passes(*o);
   double* scal = dp<double>(S.scal);
   SG_TRY(vec_norm2<double>(F64, len, scal, dp<double>(c64->fine.partial), dp<unsigned>(c64->fine.counter), st));
   SG_CUDA(cudaMemcpyAsync(S.host, scal, 8, cudaMemcpyDeviceToHost, st));
@@ -424,6 +429,7 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
   } else {
     SolverCtx<float>* c32 = nullptr;
     SG_TRY(get_ctx<float>(pr, c32));
+    c32->fine.passes = fine_orth_passes(*o);
     if (!S.r32.ptr) SG_TRY(S.r32.alloc(len * 4));
     if (!S.d32.ptr) SG_TRY(S.d32.alloc(len * 4));
     float* r32 = dp<float>(S.r32);

@@ -76,6 +76,7 @@ struct Precond {
   double omega = 1.0;
   double inner_rtol = 1e-5;
   int inner_max = 100, inner_restart = 30;
+  int inner_passes = 1;  // Gram-Schmidt passes of the coarse GMRES
   int ras_modes = 0;                       // modes per CTA of the RAS kernel (0 automatic)
   RasData ras;
   CoarseData co;

@@ -38,12 +38,12 @@ def small(gpu):
     return probs, refs, sols
 
 
-@pytest.mark.parametrize("mode", [1, 0])
-def test_batch_matches_oracle(small, mode):
+@pytest.mark.parametrize("mode,passes", [(1, 0), (0, 0), (1, 2)])
+def test_batch_matches_oracle(small, mode, passes):
     import paper_2310_14649_gb300 as sg
     probs, refs, sols = small
     Xs = [zeros(p) for p in probs]
-    infos = sg.sg_solve_batch(probs, Xs, rtol=1e-8, mode=mode)
+    infos = sg.sg_solve_batch(probs, Xs, rtol=1e-8, mode=mode, orth_passes=passes)
     for X, ref, Xd, inf in zip(Xs, refs, sols, infos):
         Xh = X.cpu().numpy().T
         assert inf["relres"] <= 1e-8

@@ -149,3 +149,44 @@ def test_device_and_host_loops_agree(gpu, mode):
     assert idev["outer_it"] == ihost["outer_it"]
     assert abs(idev["inner_it"] - ihost["inner_it"]) <= max(2, ihost["inner_it"] // 20)
     assert np.linalg.norm(Xd - Xh) / np.linalg.norm(Xh) < 1e-7
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gram_schmidt_passes(gpu, mode):
+    """One classical Gram-Schmidt pass (the default) and two (CGS2), in the
+    outer (F)GMRES and in the coarse GMRES: every combination reaches the
+    oracle's solution, with the same outer iteration count to within 2.  The
+    mixed solve stops at 1e-10: its second refinement step ends at relres
+    1.0e-8, so a target of 1e-8 would decide on rounding whether a third
+    step runs."""
+    import paper_2310_14649_gb300 as sg
+    c = dict(CONFIGS["poisson256_L4_p3"], N=64, sx=4, sy=4)
+    rtol = 1e-8 if mode == 0 else 1e-10
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    Xo, _, _ = galerkin.solve_gmres(ref, tol=1e-12)
+    its = {}
+    for cp in (1, 2):
+        prob = setup(c, inner_orth_passes=cp)
+        for fp in (1, 2):
+            X = zeros(prob)
+            info = sg.sg_solve(prob, X, rtol=rtol, mode=mode, orth_passes=fp)
+            Xh = to_np(X, prob.n)
+            assert galerkin.relres(ref, Xh) <= 1.01 * rtol
+            assert np.linalg.norm(Xh - Xo) / np.linalg.norm(Xo) <= 1e-7
+            its[(cp, fp)] = info["outer_it"]
+        prob.close()
+    print(its)
+    assert max(its.values()) - min(its.values()) <= 2
+
+
+def test_gram_schmidt_passes_rejected(gpu):
+    import paper_2310_14649_gb300 as sg
+    c = CONFIGS["poisson32_L2_p2"]
+    prob = setup(c)
+    for bad in (-1, 3):
+        with pytest.raises(sg.SgError) as e:
+            sg.sg_solve(prob, zeros(prob), rtol=1e-8, orth_passes=bad)
+        assert e.value.status == -1
+        with pytest.raises(sg.SgError) as e:
+            sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_orth_passes=bad)
+        assert e.value.status == -1
