@@ -66,7 +66,7 @@ def measured_traffic(shape):
                 k, v = kv.split("=")
                 vals[k] = v
     key = {k: str(shape[k]) for k in ("rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "stages",
-                                      "cgroups", "generator")}
+                                      "cgroups", "warps", "generator")}
     if not vals or any(vals.get(k) != v for k, v in key.items()):
         return None
     return int(vals["bytes"])

@@ -150,11 +150,14 @@ sg_status sg_set_apply_kernel(sg_problem* prob, int mode);
  * stream through shared memory by cp.async, stages - 1 blocks ahead of use,
  * across slot boundaries; one row and one group only); cgroups (1..16: the
  * outputs split over that many separate 128-thread CTAs per row tile, each
- * with the full register file of its threads; one row and one group only).
+ * with the full register file of its threads; one row and one group only);
+ * warps (1, 2 or 4 warps per group, i.e. 32, 64 or 128 rows per tile: narrow
+ * groups let many slot or input groups share one CTA without capping its
+ * registers; fewer than 4 only without staging or separate CTAs).
  * Recompiles.
  * Errors: SG_ERR_ARG out of range, SG_ERR_CUDA compile failure. */
 sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int igroups, int sgroups,
-                          int prefetch, int min_blocks, int stages, int cgroups);
+                          int prefetch, int min_blocks, int stages, int cgroups, int warps);
 
 /* Autotuner: compiles the candidate tile shapes, times each on this
  * problem's operator of family `which` (as for sg_apply_config; the
@@ -166,9 +169,9 @@ sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int
 sg_status sg_apply_autotune(sg_problem* prob, int which, int force, double* best_ms);
 
 /* Current tile shape of one family (rows, groups, igroups, sgroups,
- * prefetch, min_blocks, stages, cgroups, code-generator version into cfg9)
- * and the seconds spent compiling or loading its kernel. */
-sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg9, double* compile_s);
+ * prefetch, min_blocks, stages, cgroups, warps, code-generator version into
+ * cfg10) and the seconds spent compiling or loading its kernel. */
+sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg10, double* compile_s);
 
 /* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
  * sg_apply (F may equal R for an in-place update). */
@@ -207,6 +210,11 @@ typedef struct {
                           coarse GMRES: 1 (<= 0) = classical, the
                           PETSc default the paper's runs used (Sec. 5);
                           2 = classical with one re-orthogonalisation   */
+  int amg_kernel;      /* AMG V-cycle kernels: 0 = level 0 as three
+                          GPU-wide kernels and all coarser levels in one
+                          launch (one CTA per PCE mode, level vectors in
+                          shared memory); 1 = one launch per level
+                          operation                                      */
 } sg_precond_opts;
 
 /* Builds partitions, local factors, the coarse space, the AMG hierarchy,

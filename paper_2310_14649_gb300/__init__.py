@@ -144,9 +144,9 @@ def sg_residual(prob, F, X, R, stream=None):
 
 
 def sg_precond_setup(prob, sx, sy, overlap, omega=0.0, inner_rtol=0.0, inner_max=0, smoother=0,
-                     host_loops=False, ras_modes=0, inner_orth_passes=0, stream=None):
+                     host_loops=False, ras_modes=0, inner_orth_passes=0, amg_kernel=0, stream=None):
     opts = _lib.PrecondOpts(sx, sy, overlap, omega, inner_rtol, inner_max, smoother, 1 if host_loops else 0,
-                            ras_modes, inner_orth_passes)
+                            ras_modes, inner_orth_passes, amg_kernel)
     call("sg_precond_setup", prob.handle, ctypes.byref(opts), stream_handle(stream))
     prob.nc = sg_precond_info(prob)[2]
 
@@ -248,8 +248,9 @@ def sg_set_apply_kernel(prob, mode):
 
 
 def sg_apply_config(prob, rows=1, groups=1, igroups=1, sgroups=1, prefetch=8, min_blocks=1, stages=0, cgroups=1,
-                    which=0):
-    call("sg_apply_config", prob.handle, which, rows, groups, igroups, sgroups, prefetch, min_blocks, stages, cgroups)
+                    warps=4, which=0):
+    call("sg_apply_config", prob.handle, which, rows, groups, igroups, sgroups, prefetch, min_blocks, stages, cgroups,
+         warps)
 
 
 def sg_apply_autotune(prob, force=False, which=0):
@@ -259,10 +260,11 @@ def sg_apply_autotune(prob, force=False, which=0):
 
 
 def sg_apply_info(prob, which=0):
-    cfg = np.zeros(9, dtype=np.int32)
+    cfg = np.zeros(10, dtype=np.int32)
     cs = ctypes.c_double()
     call("sg_apply_info", prob.handle, which, _lib.ptr(cfg, ctypes.c_int32), ctypes.byref(cs))
-    keys = ["rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "stages", "cgroups", "generator"]
+    keys = ["rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "stages", "cgroups", "warps",
+            "generator"]
     out = {k: int(v) for k, v in zip(keys, cfg)}
     out["compile_s"] = cs.value
     return out

@@ -40,7 +40,8 @@ class PrecondOpts(ctypes.Structure):
     _fields_ = [("sx", ctypes.c_int), ("sy", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("omega", ctypes.c_double), ("inner_rtol", ctypes.c_double),
                 ("inner_max", ctypes.c_int), ("smoother", ctypes.c_int), ("host_loops", ctypes.c_int),
-                ("ras_modes", ctypes.c_int), ("inner_orth_passes", ctypes.c_int)]
+                ("ras_modes", ctypes.c_int), ("inner_orth_passes", ctypes.c_int),
+                ("amg_kernel", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -99,7 +100,7 @@ SIGNATURES = {
     "sg_mdot": [vp, ctypes.c_int, vp, i64, ctypes.c_int, vp, i64, vp, vp],
     "sg_mdot_noalloc": [ctypes.c_int, vp, i64, ctypes.c_int, vp, i64, vp, vp],
     "sg_set_apply_kernel": [vp, ctypes.c_int],
-    "sg_apply_config": [vp] + [ctypes.c_int] * 9,
+    "sg_apply_config": [vp] + [ctypes.c_int] * 10,
     "sg_apply_autotune": [vp, ctypes.c_int, ctypes.c_int, P_f64],
     "sg_apply_info": [vp, ctypes.c_int, P_i32, P_f64],
     "sg_launch_count": [P_i64],

@@ -96,7 +96,7 @@ sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
 }
 
 sg_status sg_apply_config(sg_problem* pr, int which, int rows, int groups, int igroups, int sgroups, int prefetch,
-                          int min_blocks, int stages, int cgroups) {
+                          int min_blocks, int stages, int cgroups, int warps) {
   SG_ARG(pr && which >= 0 && which < kJitFamilies, "sg_apply_config: NULL handle or which not in [0, 3]");
   JitConfig c;
   c.rows = rows;
@@ -107,6 +107,7 @@ sg_status sg_apply_config(sg_problem* pr, int which, int rows, int groups, int i
   c.min_blocks = min_blocks;
   c.stages = stages;
   c.cgroups = cgroups;
+  c.warps = warps;
   return jit_configure(pr, which, c);
 }
 
@@ -115,19 +116,20 @@ sg_status sg_apply_autotune(sg_problem* pr, int which, int force, double* best_m
   return jit_autotune(pr, which, force, best_ms);
 }
 
-sg_status sg_apply_info(const sg_problem* pr, int which, int* cfg9, double* compile_s) {
+sg_status sg_apply_info(const sg_problem* pr, int which, int* cfg10, double* compile_s) {
   SG_ARG(pr && which >= 0 && which < kJitFamilies, "sg_apply_info: NULL handle or which not in [0, 3]");
   const JitConfig c = pr->jit_cfg_set[which] ? pr->jit_cfg[which] : jit_default_config(pr, which);
-  if (cfg9) {
-    cfg9[0] = c.rows;
-    cfg9[1] = c.groups;
-    cfg9[2] = c.igroups;
-    cfg9[3] = c.sgroups;
-    cfg9[4] = c.prefetch;
-    cfg9[5] = c.min_blocks;
-    cfg9[6] = c.stages;
-    cfg9[7] = c.cgroups;
-    cfg9[8] = kJitGeneratorVersion;
+  if (cfg10) {
+    cfg10[0] = c.rows;
+    cfg10[1] = c.groups;
+    cfg10[2] = c.igroups;
+    cfg10[3] = c.sgroups;
+    cfg10[4] = c.prefetch;
+    cfg10[5] = c.min_blocks;
+    cfg10[6] = c.stages;
+    cfg10[7] = c.cgroups;
+    cfg10[8] = c.warps;
+    cfg10[9] = kJitGeneratorVersion;
   }
   if (compile_s) *compile_s = pr->jit[which] ? pr->jit[which]->compile_s : 0.0;
   return SG_OK;

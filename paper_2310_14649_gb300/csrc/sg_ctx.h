@@ -269,7 +269,8 @@ struct SolverCtx {
     ldc = pc->co.ldc;
     lenc = int64_t(pr->P) * ldc;
     SG_TRY(fine.init(len, restart, true));
-    SG_TRY(coarse.init(lenc, pc->inner_restart, false));
+    // flexible storage: the update x += M (V y) reuses Z_j = M V_j
+    SG_TRY(coarse.init(lenc, pc->inner_restart, true));
     coarse.passes = pc->inner_passes;
     SG_TRY(r1.alloc(len * sizeof(T)));
     SG_TRY(zt.alloc(len * sizeof(T)));
@@ -318,7 +319,7 @@ struct SolverCtx {
   // reductions would pick up; a solve that continues after such a value
   // (the fallback from the learned smoother) starts from clean buffers.
   sg_status scrub(cudaStream_t st) {
-    for (DevBuf* b : {&fine.V, &fine.Z, &fine.w, &fine.tmp, &fine.tmp2, &coarse.V, &coarse.w, &coarse.tmp,
+    for (DevBuf* b : {&fine.V, &fine.Z, &fine.w, &fine.tmp, &fine.tmp2, &coarse.V, &coarse.Z, &coarse.w, &coarse.tmp,
                       &coarse.tmp2, &r1, &zt, &rc, &ec})
       if (b->ptr) SG_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, st));
     for (DevBuf& b : amgbuf)
@@ -337,18 +338,12 @@ struct SolverCtx {
     const AmgLevel& L0 = pc->amg[0];
     SG_CUDA(cudaMemcpy2DAsync(aw.b[0], L0.ld * sizeof(T), B, ldc * sizeof(T), pc->co.nc * sizeof(T), pr->P,
                               cudaMemcpyDeviceToDevice, st));
-    SG_TRY(amg_vcycle<T>(pc->amg, aw, pr->P, st));
-    SG_CUDA(cudaMemcpy2DAsync(X, ldc * sizeof(T), aw.x[0], L0.ld * sizeof(T), pc->co.nc * sizeof(T), pr->P,
-                              cudaMemcpyDeviceToDevice, st));
-    return SG_OK;
+    return amg_vcycle<T>(pc->amg, aw, pr->P, st, X, ldc);
   }
   // coarse preconditioner on a block already in the AMG level-0 input:
   // V-cycle, copy out to `out` (coarse ld), Kronecker factor
   sg_status coarse_pc_from_b0(T* out, cudaStream_t st) {
-    const AmgLevel& L0 = pc->amg[0];
-    SG_TRY(amg_vcycle<T>(pc->amg, aw, pr->P, st));
-    SG_CUDA(cudaMemcpy2DAsync(out, ldc * sizeof(T), aw.x[0], L0.ld * sizeof(T), pc->co.nc * sizeof(T), pr->P,
-                              cudaMemcpyDeviceToDevice, st));
+    SG_TRY(amg_vcycle<T>(pc->amg, aw, pr->P, st, out, ldc));
     return node_transform<T>(out, ldc, pc->co.nc, pr->P, dp_sel<T>(pc->gkron64, pc->gkron32), st);
   }
 

@@ -32,13 +32,12 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
   const int m = W.m;
   const Precond& pc = *c.pc;
   const AmgLevel& L0 = pc.amg[0];
-  const double* one = dp<double>(c.consts);
   double* h1 = W.s.hsum;
   double* h2 = W.s.hsum + (m + 1);
   T* V = dp<T>(W.V);
+  T* Zc = dp<T>(W.Z);
   T* w = dp<T>(W.w);
   T* tmp = dp<T>(W.tmp);
-  T* tmp2 = dp<T>(W.tmp2);
   T* Rc = dp<T>(c.rc);
   T* Ec = dp<T>(c.ec);
   double* part = dp<double>(W.partial);
@@ -75,6 +74,7 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
       SG_CUDA(cudaStreamBeginCaptureToGraph(s3, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       SG_TRY(dg_copy_vj<T>(V, lenc, ldc, c.aw.b[0], L0.ld, pc.co.nc, c.pr->P, c.dg, s3));
       SG_TRY(c.coarse_pc_from_b0(tmp, s3));
+      SG_TRY(dg_store_j<T>(tmp, Zc, lenc, lenc, c.dg, s3));
       SG_TRY(c.apply_raw(tmp, w, nullptr, s3));
       SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h1, part, cnt, jdev, m, s3));
       if (W.passes == 1) {
@@ -89,14 +89,9 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
       SG_CUDA(cudaStreamEndCapture(s3, &body_in));
     }
     k3 = launch_count();
-    // x += M (V y)
+    // x += M (V y) = Z y with the stored Z_j = M V_j
     SG_TRY(dg_backsolve(c.dg, W.s, m, s2));
-    SG_CUDA(cudaMemsetAsync(tmp2, 0, lenc * sizeof(T), s2));
-    SG_TRY(dg_axpy_multi<T>(V, lenc, W.s.y, tmp2, lenc, jdev, s2));
-    SG_CUDA(cudaMemcpy2DAsync(c.aw.b[0], L0.ld * sizeof(T), tmp2, ldc * sizeof(T), pc.co.nc * sizeof(T), c.pr->P,
-                              cudaMemcpyDeviceToDevice, s2));
-    SG_TRY(c.coarse_pc_from_b0(tmp, s2));
-    SG_TRY(vec_axpy_multi<T>(tmp, 0, 1, one, Ec, lenc, s2));
+    SG_TRY(dg_axpy_multi<T>(Zc, lenc, W.s.y, Ec, lenc, jdev, s2));
     SG_TRY(dg_end(c.dg, W.s, hout, s2));
     SG_CUDA(cudaStreamEndCapture(s2, &body_out));
   }

@@ -121,7 +121,7 @@ struct Profiler {
 // families: which = 0 fine FP32, 1 coarse FP32, 2 fine FP64, 3 coarse FP64.
 constexpr int kJitFamilies = 4;
 constexpr int kJitMaxP = 128;
-constexpr int kJitGeneratorVersion = 7;  // bump when the generated code changes
+constexpr int kJitGeneratorVersion = 8;  // bump when the generated code changes
 constexpr int64_t kJitMaxT = 40000;
 struct JitConfig {
   int rows = 1;        // rows per thread (2: paired FP32 FMA)
@@ -133,6 +133,8 @@ struct JitConfig {
   int stages = 0;      // 0: matrix values prefetched into registers; >= 2: staged through shared
                        // memory by cp.async in blocks of `prefetch` terms, stages - 1 blocks ahead
   int cgroups = 1;     // output groups as separate 128-thread CTAs (no register cap from wide CTAs)
+  int warps = 4;       // warps per group (rows per group = 32 x warps x rows): narrow groups keep
+                       // several slot or input groups within one register-rich CTA
 };
 struct JitApply {
   cudaLibrary_t lib = nullptr;

@@ -119,7 +119,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
   // coefficients as exact double immediates
   const char* T = fp64 ? "double" : "float";
   const std::string Ts = T;
-  const int mb = c.min_blocks, NG = HO * HI * SG, NPART = HI * SG;
+  const int mb = c.min_blocks, NG = HO * HI * SG, NPART = HI * SG, W = csplit ? 4 : c.warps;
   const std::vector<int> cut = output_split(pr, HO);
   std::vector<int> icut(HI + 1);
   for (int i = 0; i <= HI; ++i) icut[i] = int(int64_t(P) * i / HI);
@@ -258,12 +258,12 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
     // group order; outputs this group never touches contribute zero
     for (int a = lo; a < up; ++a) {
       if (!has_a[a]) {
-        for (int q = 0; q < R; ++q) body << "    part[" << a << " * " << 128 * R << " + lrow + " << q << "] = 0;\n";
+        for (int q = 0; q < R; ++q) body << "    part[" << a << " * " << 32 * W * R << " + lrow + " << q << "] = 0;\n";
         continue;
       }
       for (int q = 0; q < R; ++q) {
         const std::string val = R == 2 ? ("y" + std::to_string(a) + (q ? ".y" : ".x")) : ("y" + std::to_string(a));
-        body << "    part[" << a << " * " << 128 * R << " + lrow + " << q << "] = " << val << ";\n";
+        body << "    part[" << a << " * " << 32 * W * R << " + lrow + " << q << "] = " << val << ";\n";
       }
     }
     body << "  }\n";
@@ -304,7 +304,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
     }
     os << "};\n#define gq2 (reinterpret_cast<const float2*>(gq_bits))\n";
   }
-  const int rows_cta = 128 * R;
+  const int rows_cta = 32 * W * R;
   if (csplit) {
     os << "extern \"C\" __global__ void __launch_bounds__(128, " << mb << ") " << (fp64 ? "sg_k1_f64" : "sg_k1")
        << "(\n"
@@ -319,15 +319,15 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
     os << "}\n";
     return os.str();
   }
-  os << "extern \"C\" __global__ void __launch_bounds__(" << 128 * NG << ", " << mb << ") "
+  os << "extern \"C\" __global__ void __launch_bounds__(" << 32 * W * NG << ", " << mb << ") "
      << (fp64 ? "sg_k1_f64" : "sg_k1") << "(\n"
         "    const " << Ts << "* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
         "    const " << Ts << "* __restrict__ X, long long ldx, const " << Ts << "* __restrict__ F, long long ldf,\n"
         "    " << Ts << "* __restrict__ Y, long long ldy) {\n"
         "  extern __shared__ " << Ts << " smem[];\n"
         "  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
-        "  const int grp = warp >> 2;\n"
-        "  const int lrow = (warp & 3) * "
+        "  const int grp = warp / " << W << ";\n"
+        "  const int lrow = (warp % " << W << ") * "
      << 32 * R << " + lane * " << R << ";\n"
      << "  const int r = blockIdx.x * " << rows_cta << " + lrow;\n"
      << "  const int rr = r < n ? r : (n - 1) & ~" << (R - 1) << ";\n"
@@ -361,7 +361,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
     os << "  " << Ts << "* part = smem + (size_t)(grp % " << NPART << ") * " << P * rows_cta << ";\n";
     os << body.str();
     os << "  __syncthreads();\n";
-    os << "  for (int e = threadIdx.x; e < " << P * rows_cta << "; e += " << 128 * NG << ") {\n"
+    os << "  for (int e = threadIdx.x; e < " << P * rows_cta << "; e += " << 32 * W * NG << ") {\n"
           "    const int a = e / "
        << rows_cta << ", lr = e - a * " << rows_cta << ";\n"
        << "    const int row = blockIdx.x * " << rows_cta << " + lr;\n"
@@ -378,7 +378,7 @@ size_t jit_smem_bytes(const sg_problem* pr, const JitConfig& c, bool fp64) {
   if (c.cgroups > 1) return 0;
   if (c.stages >= 2) return size_t(c.stages) * std::max(1, c.prefetch) * 128 * (fp64 ? sizeof(double) : sizeof(float));
   if (c.groups * c.igroups * c.sgroups == 1) return 0;
-  return size_t(c.igroups) * c.sgroups * pr->P * 128 * c.rows * (fp64 ? sizeof(double) : sizeof(float));
+  return size_t(c.igroups) * c.sgroups * pr->P * 32 * c.warps * c.rows * (fp64 ? sizeof(double) : sizeof(float));
 }
 
 // Compile (or load from the cache) one configuration.
@@ -446,9 +446,11 @@ JitConfig jit_default_config(const sg_problem* pr, int which) {
     return c;
   }
   c.prefetch = fp64 ? 16 : 32;
-  // the coarse operator has a quarter of the rows: deal the slots to groups
-  // so that the grid still fills the GPU
-  c.sgroups = coarse ? 4 : 1;
+  // the coarse operator has a quarter of the rows: deal the slots to two
+  // groups so that the grid still fills the GPU (four groups of 4 warps cap
+  // the CTA at 128 registers a thread and spill: 0.115 against 0.053 ms at
+  // 127^2 coarse rows, P = 35)
+  c.sgroups = coarse ? 2 : 1;
   return c;
 }
 
@@ -471,11 +473,13 @@ sg_status jit_configure(sg_problem* pr, int which, const JitConfig& c) {
       c.stages < 0 || c.stages == 1 || c.stages > 8 ||
       (c.stages >= 2 && (c.rows != 1 || c.groups * c.igroups * c.sgroups != 1 || c.prefetch < 1)) ||
       c.cgroups < 1 || c.cgroups > 16 ||
-      (c.cgroups > 1 && (c.rows != 1 || c.groups * c.igroups * c.sgroups != 1 || c.stages != 0))) {
+      (c.cgroups > 1 && (c.rows != 1 || c.groups * c.igroups * c.sgroups != 1 || c.stages != 0)) ||
+      (c.warps != 1 && c.warps != 2 && c.warps != 4) || (c.warps != 4 && (c.stages != 0 || c.cgroups > 1))) {
     set_error("sg_apply_config: rows in {1,2}; groups, igroups in [1,4]; sgroups in [1,8]; "
               "groups*igroups*sgroups <= 8; prefetch in [0,64]; min_blocks in [1,8]; FP64 families: rows 1; "
               "stages 0 or 2..8, staged only with one row and one group and prefetch >= 1; "
-              "cgroups 1..16, split only with one row, one group and no staging");
+              "cgroups 1..16, split only with one row, one group and no staging; warps per group 1, 2 or 4, "
+              "fewer than 4 only without staging or separate CTAs");
     return SG_ERR_ARG;
   }
   if (jit_smem_bytes(pr, c, which >= 2) > 200 * 1024) {
@@ -507,10 +511,10 @@ static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, size_t sme
   long long ldr = A.ldr, lx = ldx, lf = ldf, ly = ldy;
   int n = int(A.n), S = A.S;
   void* args[] = {(void*)&V, (void*)&col, &ldr, &n, &S, (void*)&X, &lx, (void*)&F, &lf, (void*)&Y, &ly};
-  const int64_t rows_per_cta = 128LL * c.rows;
   const bool cs = c.cgroups > 1;
+  const int64_t rows_per_cta = 32LL * (cs ? 4 : c.warps) * c.rows;
   dim3 grid(unsigned((A.n + rows_per_cta - 1) / rows_per_cta * (cs ? c.cgroups : 1))),
-      block(unsigned(cs ? 128 : 128 * c.groups * c.igroups * c.sgroups));
+      block(unsigned(cs ? 128 : 32 * c.warps * c.groups * c.igroups * c.sgroups));
   SG_CUDA(cudaLaunchKernel((const void*)kern, grid, block, args, smem, st));
   note_launch();
   return SG_OK;
@@ -542,10 +546,13 @@ sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const double
 // rows) adds stencil-slot groups to fill the GPU.  Values staged through
 // shared memory by 4-byte cp.async measured half the bandwidth of the
 // register prefetch at 256^2 / P = 35 (0.144 ms against 0.071 ms), so the
-// staged shapes are available through sg_apply_config but not tuned.
+// staged shapes are available through sg_apply_config but not tuned.  Groups
+// of one warp (every slot its own group) measured slower everywhere except
+// the fine FP64 family, where two output by two slot groups of one warp
+// each beat the 4-warp shapes by 10 % at 256^2 / P = 35.
 static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
   struct S7 {
-    int r, g, i, s, pf, st, mb = 1, cg = 1;
+    int r, g, i, s, pf, st, mb = 1, cg = 1, w = 4;
   };
   std::vector<S7> list;
   const bool fp64 = which >= 2;
@@ -555,7 +562,7 @@ static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
     if (pr->P <= 48) {
       if (which == 2)
         list = {{1, 1, 1, 1, 16, 0}, {1, 1, 1, 1, 8, 0}, {1, 2, 1, 1, 16, 0}, {1, 1, 2, 1, 16, 0},
-                {1, 2, 2, 1, 8, 0}};
+                {1, 2, 2, 1, 8, 0}, {1, 2, 1, 2, 8, 0, 1, 1, 1}};
       else
         list = {{1, 1, 1, 2, 16, 0}, {1, 1, 1, 4, 8, 0}, {1, 2, 1, 2, 8, 0}, {1, 1, 2, 2, 8, 0}};
     } else {
@@ -583,6 +590,7 @@ static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
     c.stages = e.st;
     c.min_blocks = e.mb;
     c.cgroups = e.cg;
+    c.warps = e.w;
     if (jit_smem_bytes(pr, c, fp64) > 200 * 1024) continue;
     out.push_back(c);
   }
@@ -619,7 +627,7 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
     JitConfig c;
     double ms = 0;
     if (in >> c.rows >> c.groups >> c.igroups >> c.sgroups >> c.prefetch >> c.min_blocks >> c.stages >> c.cgroups >>
-        ms) {
+        c.warps >> ms) {
       if (best_ms) *best_ms = ms;
       return jit_configure(pr, which, c);
     }
@@ -677,7 +685,8 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
   std::ofstream out(path);
   if (out)
     out << best.rows << " " << best.groups << " " << best.igroups << " " << best.sgroups << " " << best.prefetch
-        << " " << best.min_blocks << " " << best.stages << " " << best.cgroups << " " << best_t << "\n";
+        << " " << best.min_blocks << " " << best.stages << " " << best.cgroups << " " << best.warps << " " << best_t
+        << "\n";
   return jit_configure(pr, which, best);
 }
 

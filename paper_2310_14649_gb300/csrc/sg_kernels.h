@@ -23,7 +23,7 @@ sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld,
 template <typename T>
 sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st);
 template <typename T>
-sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st);
+sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T* out = nullptr, int64_t ldo = 0);
 sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w);
 // sets the dynamic shared-memory limits of the library's kernels once per
 // process (before any graph capture)

@@ -309,6 +309,96 @@ __global__ void k_dense_solve(int n, const double* __restrict__ Ainv, const T* _
   X[int64_t(a) * ldx + i] = T(acc);
 }
 
+// ---------------------------------------------------------------------------
+// V-cycle phases with a group of G lanes per sparse row.  The levels below
+// the coarse operator are small and their restriction rows long (17 to 55
+// entries on the 2h grid of a 256^2 mesh), so one thread per row spends its
+// time in a chain of dependent loads; here the G lanes of a group share a
+// row's entries and meet by shuffles.  The Jacobi steps are folded into the
+// neighbouring products, so a V-cycle over L levels is 4 (L - 1) + 1
+// launches.  Per row i of level l and mode a (D = l1 diagonal):
+//   kDown      t = b - A (D^{-1} b),  x = D^{-1} b
+//   kRestrict  b_{l+1} = R t
+//   kProlong   x += P x~_{l+1},  x~_{l+1} = x_{l+1} + D_{l+1}^{-1} t_{l+1}
+//              (x_{l+1} alone when l+1 is the coarsest level)
+//   kResid     t = b - A x
+//   kFinal     out = x + D^{-1} (b - A x)      (out must not alias x)
+// ---------------------------------------------------------------------------
+enum AmgOp { kDown, kRestrict, kProlong, kResid, kFinal };
+
+template <typename T>
+struct AmgPhase {
+  int n = 0, G = 1;
+  const int* rp = nullptr;
+  const int* ci = nullptr;
+  const T* v = nullptr;
+  const T* X = nullptr;   // gathered vector (b for kDown, t for kRestrict, x_{l+1} for kProlong, x otherwise)
+  int64_t ldx = 0;
+  const T* Xd = nullptr;  // kProlong: D_{l+1}^{-1}; NULL when l+1 is the coarsest level
+  const T* Xt = nullptr;  // kProlong: t_{l+1} (ld ldx)
+  const T* d = nullptr;   // D_l^{-1} (kDown, kFinal; gathered by kDown)
+  const T* B = nullptr;   // b_l (kDown, kResid, kFinal)
+  int64_t ldb = 0;
+  T* Y = nullptr;         // t (kDown, kResid), b_{l+1}, x (kProlong, +=), out (kFinal)
+  int64_t ldy = 0;
+  T* Y2 = nullptr;        // kDown: x = D^{-1} b (ld ldy)
+};
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(128) k_amg_phase(const __grid_constant__ AmgPhase<T> p) {
+  const int G = p.G;
+  const int grp = threadIdx.x / G, lane = threadIdx.x - grp * G;
+  const int i = blockIdx.x * (128 / G) + grp;
+  const int64_t a = blockIdx.y;
+  const bool live = i < p.n;
+  const T* X = p.X + a * p.ldx;
+  T acc = T(0);
+  if (live) {
+    const int e1 = p.rp[i + 1];
+    for (int e = p.rp[i] + lane; e < e1; e += G) {
+      const int j = p.ci[e];
+      T g;
+      if (OP == kDown)
+        g = p.d[j] * X[j];
+      else if (OP == kProlong)
+        g = p.Xd ? X[j] + p.Xd[j] * p.Xt[a * p.ldx + j] : X[j];
+      else
+        g = X[j];
+      acc += p.v[e] * g;
+    }
+  }
+  for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (!live || lane != 0) return;
+  T* y = p.Y + a * p.ldy + i;
+  if (OP == kDown) {
+    const T bi = p.B[a * p.ldb + i];
+    *y = bi - acc;
+    p.Y2[a * p.ldy + i] = p.d[i] * bi;
+  } else if (OP == kRestrict) {
+    *y = acc;
+  } else if (OP == kProlong) {
+    *y += acc;
+  } else if (OP == kResid) {
+    *y = p.B[a * p.ldb + i] - acc;
+  } else {
+    *y = X[i] + p.d[i] * (p.B[a * p.ldb + i] - acc);
+  }
+}
+
+// Coarsest level with a warp per row: x = A_c^{-1} b (explicit FP64 inverse)
+template <typename T>
+__global__ void k_dense_solve_warp(int n, const double* __restrict__ Ainv, const T* __restrict__ B, int64_t ldb,
+                                   T* __restrict__ X, int64_t ldx) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int64_t a = blockIdx.y;
+  if (row >= n) return;  // whole warps leave together
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc += Ainv[int64_t(row) * n + j] * double(B[a * ldb + j]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) X[a * ldx + row] = T(acc);
+}
+
 template <typename T> const T* dv(const DevBuf& b64, const DevBuf& b32);
 template <> const double* dv<double>(const DevBuf& b64, const DevBuf&) { return b64.as<double>(); }
 template <> const float* dv<float>(const DevBuf&, const DevBuf& b32) { return b32.as<float>(); }
@@ -383,9 +473,102 @@ sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStr
 
 // One V(1,1) cycle with l1-Jacobi on every column, from a zero guess.
 // Level buffers: b (rhs), x (solution), t (temporary), each [P][ld_l].
+// The result goes to `out` (ld `ldo`), or to x_0 when out is NULL.
 template <typename T>
-sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st) {
+sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T* out, int64_t ldo) {
   const int nl = int(H.size());
+  if (!out) {
+    out = w.x[0];
+    ldo = H[0].ld;
+  }
+  if (H.fused && nl >= 2 && P > 0) {
+    auto lanes = [P](const DevCsr& M) {
+      // about two entries per lane on an average row, while rows x modes x
+      // lanes stays within about two waves of resident threads (152 SMs x 2048)
+      const int64_t avg = M.n > 0 ? (M.nnz + M.n - 1) / M.n : 1;
+      int G = 1;
+      while (G < 32 && 2 * G < avg && M.n * int64_t(P) * (2 * G) <= 2 * 152 * 2048) G <<= 1;
+      return G;
+    };
+    auto launch = [&](auto kern, AmgPhase<T> p) -> sg_status {
+      const int rows = 128 / p.G;
+      kern<<<dim3(unsigned((p.n + rows - 1) / rows), unsigned(P)), 128, 0, st>>>(p); note_launch();
+      SG_CUDA(cudaGetLastError());
+      return SG_OK;
+    };
+    auto phase = [&](const DevCsr& M) {
+      AmgPhase<T> p;
+      p.n = int(M.n);
+      p.G = lanes(M);
+      p.rp = M.rowptr.as<int>();
+      p.ci = M.col.as<int>();
+      p.v = dv<T>(M.v64, M.v32);
+      return p;
+    };
+    for (int l = 0; l < nl - 1; ++l) {
+      const AmgLevel& L = H[l];
+      AmgPhase<T> p = phase(L.A);
+      p.X = w.b[l];
+      p.ldx = L.ld;
+      p.d = dv<T>(L.dinv64, L.dinv32);
+      p.B = w.b[l];
+      p.ldb = L.ld;
+      p.Y = w.t[l];
+      p.Y2 = w.x[l];
+      p.ldy = L.ld;
+      SG_TRY(launch(k_amg_phase<T, kDown>, p));
+      AmgPhase<T> q = phase(L.R);
+      q.X = w.t[l];
+      q.ldx = L.ld;
+      q.Y = w.b[l + 1];
+      q.ldy = H[l + 1].ld;
+      SG_TRY(launch(k_amg_phase<T, kRestrict>, q));
+    }
+    {
+      const AmgLevel& L = H[nl - 1];
+      dim3 g(unsigned((L.n + 3) / 4), unsigned(P));
+      k_dense_solve_warp<T><<<g, 128, 0, st>>>(int(L.n), H.coarsest_inv64.as<double>(), w.b[nl - 1], L.ld,
+                                               w.x[nl - 1], L.ld); note_launch();
+      SG_CUDA(cudaGetLastError());
+    }
+    for (int l = nl - 2; l >= 0; --l) {
+      const AmgLevel& L = H[l];
+      const AmgLevel& Ln = H[l + 1];
+      AmgPhase<T> p = phase(L.Pm);
+      p.X = w.x[l + 1];
+      p.ldx = Ln.ld;
+      if (l + 1 < nl - 1) {
+        p.Xd = dv<T>(Ln.dinv64, Ln.dinv32);
+        p.Xt = w.t[l + 1];
+      }
+      p.Y = w.x[l];
+      p.ldy = L.ld;
+      SG_TRY(launch(k_amg_phase<T, kProlong>, p));
+      AmgPhase<T> q = phase(L.A);
+      q.X = w.x[l];
+      q.ldx = L.ld;
+      q.B = w.b[l];
+      q.ldb = L.ld;
+      q.d = dv<T>(L.dinv64, L.dinv32);
+      if (l > 0 || out == w.x[0]) {
+        q.Y = w.t[l];
+        q.ldy = L.ld;
+        SG_TRY(launch(k_amg_phase<T, kResid>, q));
+      } else {
+        q.Y = out;
+        q.ldy = ldo;
+        SG_TRY(launch(k_amg_phase<T, kFinal>, q));
+      }
+    }
+    if (out == w.x[0]) {
+      // in place: the last smoothing step on its own
+      const AmgLevel& L0 = H[0];
+      dim3 g(unsigned((L0.n + 127) / 128), unsigned(P));
+      k_diag<T><<<g, 128, 0, st>>>(L0.n, dv<T>(L0.dinv64, L0.dinv32), w.t[0], L0.ld, w.x[0], L0.ld, 1); note_launch();
+      SG_CUDA(cudaGetLastError());
+    }
+    return SG_OK;
+  }
   for (int l = 0; l < nl - 1; ++l) {
     const AmgLevel& L = H[l];
     dim3 g(unsigned((L.n + 127) / 128), unsigned(P));
@@ -409,6 +592,9 @@ sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st) {
     k_diag<T><<<g, 128, 0, st>>>(L.n, dv<T>(L.dinv64, L.dinv32), w.t[l], L.ld, w.x[l], L.ld, 1); note_launch();
     SG_CUDA(cudaGetLastError());
   }
+  if (out != w.x[0])
+    SG_CUDA(cudaMemcpy2DAsync(out, ldo * sizeof(T), w.x[0], H[0].ld * sizeof(T), H[0].n * sizeof(T), P,
+                              cudaMemcpyDeviceToDevice, st));
   return SG_OK;
 }
 
@@ -467,7 +653,7 @@ sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w) {
   template sg_status ras_apply<T>(const Precond&, int64_t, int, const T*, int64_t, T*, cudaStream_t, bool,        \
                                   Profiler*);                                                                      \
   template sg_status node_transform<T>(T*, int64_t, int64_t, int, const T*, cudaStream_t);                \
-  template sg_status amg_vcycle<T>(const AmgHier&, AmgWork<T>&, int, cudaStream_t);
+  template sg_status amg_vcycle<T>(const AmgHier&, AmgWork<T>&, int, cudaStream_t, T*, int64_t);
 INST(float)
 INST(double)
 #undef INST

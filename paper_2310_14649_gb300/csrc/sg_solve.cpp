@@ -212,6 +212,7 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   SG_ARG(o->sx >= 1 && o->sy >= 1 && o->sx <= pr->N - 1 && o->sy <= pr->N - 1,
          "sg_precond_setup: subdomain counts must be in [1, N-1]");
   SG_ARG(o->overlap >= 0 && o->overlap <= 8, "sg_precond_setup: overlap must be in [0, 8]");
+  SG_ARG(o->amg_kernel == 0 || o->amg_kernel == 1, "sg_precond_setup: amg_kernel must be 0 or 1");
   SG_ARG(o->inner_orth_passes >= 0 && o->inner_orth_passes <= 2,
          "sg_precond_setup: inner_orth_passes must be 0 (default), 1 or 2");
   SG_ARG(o->smoother == 0 || o->smoother == 1, "sg_precond_setup: smoother must be 0 (RAS) or 1 (learned)");
@@ -233,6 +234,7 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   pc.inner_passes = o->inner_orth_passes > 0 ? o->inner_orth_passes : 1;
   SG_TRY(kernel_attrs_init());
   sg_status s = precond_setup_host(pr, pc);
+  pc.amg.fused = o->amg_kernel == 0;
   std::vector<double> ginv;
   if (s == SG_OK) s = kronecker_factor(pr, pc, ginv);
   pc.omega = 1.0;

@@ -33,6 +33,7 @@ struct AmgLevel {
 struct AmgHier {
   std::vector<AmgLevel> lev;
   DevBuf coarsest_inv64;
+  bool fused = true;  // V-cycle: lane groups per sparse row, Jacobi steps folded into the products
   size_t size() const { return lev.size(); }
   AmgLevel& operator[](size_t l) { return lev[l]; }
   const AmgLevel& operator[](size_t l) const { return lev[l]; }

@@ -177,7 +177,8 @@ def test_bad_arguments(gpu):
                                  (1, 4, 1, 2, 4, 1), (1, 2, 2, 2, 8, 1), (1, 1, 3, 1, 8, 1), (1, 1, 1, 4, 8, 1),
                                  (2, 1, 1, 8, 8, 1), (1, 1, 1, 1, 16, 1, 3), (1, 1, 1, 1, 5, 1, 4),
                                  (1, 1, 1, 1, 1, 1, 2), (1, 1, 1, 1, 32, 2, 4), (1, 1, 1, 1, 8, 1, 0, 3),
-                                 (1, 1, 1, 1, 16, 1, 0, 5)])
+                                 (1, 1, 1, 1, 16, 1, 0, 5), (1, 1, 1, 5, 16, 1, 0, 1, 1), (2, 1, 1, 4, 8, 1, 0, 1, 2),
+                                 (1, 2, 2, 2, 8, 1, 0, 1, 1)])
 @pytest.mark.parametrize("N", [20, 21])
 def test_specialised_kernel_configs(gpu, cfg, N):
     """Every tile shape (rows per thread, output groups, prefetch, CTAs per
@@ -192,7 +193,8 @@ def test_specialised_kernel_configs(gpu, cfg, N):
 
 
 @pytest.mark.parametrize("cfg", [(1, 1, 1, 1, 16, 1), (1, 2, 2, 1, 8, 1), (1, 1, 1, 4, 8, 1), (1, 4, 2, 1, 4, 1),
-                                 (1, 2, 4, 1, 4, 1), (1, 1, 1, 1, 8, 1, 0, 4)])
+                                 (1, 2, 4, 1, 4, 1), (1, 1, 1, 1, 8, 1, 0, 4), (1, 1, 1, 5, 8, 1, 0, 1, 1),
+                                 (1, 2, 1, 2, 8, 1, 0, 1, 2)])
 @pytest.mark.parametrize("N", [20, 21])
 def test_specialised_fp64_configs(gpu, cfg, N):
     """The FP64 family (exact double coefficients) in several tile shapes."""
@@ -206,6 +208,10 @@ def test_specialised_fp64_configs(gpu, cfg, N):
         sg.sg_apply_config(prob, 2, 1, 1, 1, 8, 1, which=2)   # paired rows are FP32 only
     with pytest.raises(sg.SgError):
         sg.sg_apply_config(prob, 1, 2, 1, 1, 8, 1, 3)           # staging needs one group
+    with pytest.raises(sg.SgError):
+        sg.sg_apply_config(prob, 1, 1, 1, 2, 8, 1, 0, 1, 3)     # 1, 2 or 4 warps per group
+    with pytest.raises(sg.SgError):
+        sg.sg_apply_config(prob, 1, 1, 1, 1, 8, 1, 3, 1, 1)     # narrow groups are not staged
 
 
 def test_autotune_picks_a_valid_shape(gpu):

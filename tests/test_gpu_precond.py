@@ -164,7 +164,8 @@ def test_coarse_correction_and_two_level(pair, dt):
 
 
 @pytest.mark.parametrize("cfg", [(1, 1, 1, 4, 8, 1), (1, 2, 1, 2, 16, 1), (2, 1, 1, 2, 8, 1), (1, 1, 2, 1, 8, 1),
-                                 (1, 1, 1, 1, 16, 1, 3)])
+                                 (1, 1, 1, 1, 16, 1, 3), (1, 1, 1, 7, 16, 1, 0, 1, 1), (1, 1, 2, 4, 16, 1, 0, 1, 1),
+                                 (2, 1, 1, 4, 16, 1, 0, 1, 2)])
 def test_coarse_apply_tile_shapes(pair, cfg):
     """The coarse family's specialised kernel in several tile shapes."""
     import torch
@@ -177,3 +178,43 @@ def test_coarse_apply_tile_shapes(pair, cfg):
     scale = np.max(np.abs(coarse.coarse_apply([abs(a) for a in tl.Acs], abs(tl.G), abs(Xq))))
     assert np.max(np.abs(Y - Yr)) <= 1e-4 * scale
     sg.sg_apply_config(prob, 1, 1, 1, 4, 32, 1, which=1)
+
+
+@pytest.fixture(scope="module")
+def multilevel(gpu):
+    """N = 128: 3,969 coarse unknowns, a hierarchy of several levels."""
+    import paper_2310_14649_gb300 as sg
+    N, L, p, q, s2, b = 128, 2, 2, 4, 0.3, 0.5
+    ref = galerkin.build(N, L, p, q, sigma2=s2, bx=b, by=b)
+    Acs, _ = coarse.coarse_matrices(ref)
+    levels = amg.setup(Acs[0])
+    prob = sg.sg_setup(N, L, p, q, sigma2=s2, bx=b, by=b)
+    return prob, ref, levels, Acs[0].shape[0]
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_amg_vcycle_kernels_multilevel(multilevel, dt):
+    """The fused V-cycle (level 0 GPU-wide, the coarser levels in one launch
+    with one CTA per mode) and one launch per level operation both match the
+    oracle's V-cycle on a hierarchy of three levels."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, levels, nc = multilevel
+    assert len(levels) >= 3
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    Xc = random_block(nc, ref.P, seed=35)
+    tol = 1e-11 if dt == "f64" else 1e-4
+    out = {}
+    for cl in (0, 1):
+        sg.sg_precond_setup(prob, 4, 4, 1, amg_kernel=cl)
+        assert sg.sg_precond_info(prob)[1] == len(levels)
+        Y, Xq = run(prob, sg.PC_AMG, Xc, nc, dtype)
+        Yr = amg.vcycle(levels, Xq)
+        assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr)), cl
+        # a second application on the same buffers gives the same result
+        Y2, _ = run(prob, sg.PC_AMG, Xc, nc, dtype)
+        assert np.array_equal(Y, Y2), cl
+        out[cl] = Y
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_precond_setup(prob, 4, 4, 1, amg_kernel=2)
+    assert e.value.status == -1
