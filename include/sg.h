@@ -215,6 +215,13 @@ typedef struct {
                           launch (one CTA per PCE mode, level vectors in
                           shared memory); 1 = one launch per level
                           operation                                      */
+  int ras_stages;      /* line steps whose matrices the RAS kernel keeps in
+                          flight or resident (2..8); 0 = automatic       */
+  int ras_kernel;      /* RAS local solves on FP32 data: 0 = FMA kernel;
+                          1 = tensor cores (m16n8k8 TF32 MMA with operands
+                          split into high and remainder parts, FP32
+                          accumulation; 8 modes per CTA unless ras_modes
+                          is given).  FP64 data always use the FMA kernel. */
 } sg_precond_opts;
 
 /* Builds partitions, local factors, the coarse space, the AMG hierarchy,

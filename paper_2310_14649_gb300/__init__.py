@@ -144,9 +144,10 @@ def sg_residual(prob, F, X, R, stream=None):
 
 
 def sg_precond_setup(prob, sx, sy, overlap, omega=0.0, inner_rtol=0.0, inner_max=0, smoother=0,
-                     host_loops=False, ras_modes=0, inner_orth_passes=0, amg_kernel=0, stream=None):
+                     host_loops=False, ras_modes=0, inner_orth_passes=0, amg_kernel=0, ras_stages=0, ras_kernel=0,
+                     stream=None):
     opts = _lib.PrecondOpts(sx, sy, overlap, omega, inner_rtol, inner_max, smoother, 1 if host_loops else 0,
-                            ras_modes, inner_orth_passes, amg_kernel)
+                            ras_modes, inner_orth_passes, amg_kernel, ras_stages, ras_kernel)
     call("sg_precond_setup", prob.handle, ctypes.byref(opts), stream_handle(stream))
     prob.nc = sg_precond_info(prob)[2]
 

@@ -41,7 +41,8 @@ class PrecondOpts(ctypes.Structure):
                 ("omega", ctypes.c_double), ("inner_rtol", ctypes.c_double),
                 ("inner_max", ctypes.c_int), ("smoother", ctypes.c_int), ("host_loops", ctypes.c_int),
                 ("ras_modes", ctypes.c_int), ("inner_orth_passes", ctypes.c_int),
-                ("amg_kernel", ctypes.c_int)]
+                ("amg_kernel", ctypes.c_int), ("ras_stages", ctypes.c_int),
+                ("ras_kernel", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):

@@ -36,8 +36,22 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
-// line steps whose matrices are in flight or resident (ring of buffers)
+// line steps whose matrices are in flight or resident (ring of buffers):
+// the default depth and the deepest ring the kernel takes
 constexpr int kRasStages = 3;
+constexpr int kRasMaxStages = 8;
+// cp.async.wait_group with a run-time count (the instruction takes an immediate)
+__device__ __forceinline__ void cp_async_wait_dyn(int n) {
+  switch (n) {
+    case 0: cp_async_wait_group<0>(); break;
+    case 1: cp_async_wait_group<1>(); break;
+    case 2: cp_async_wait_group<2>(); break;
+    case 3: cp_async_wait_group<3>(); break;
+    case 4: cp_async_wait_group<4>(); break;
+    case 5: cp_async_wait_group<5>(); break;
+    default: cp_async_wait_group<6>(); break;
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ void stage_mats(T* dst_off, T* dst_lin, const T* src_off, const T* src_lin, int WW) {
@@ -47,6 +61,57 @@ __device__ __forceinline__ void stage_mats(T* dst_off, T* dst_lin, const T* src_
     cp_async16(reinterpret_cast<char*>(dst_lin) + 16 * c, reinterpret_cast<const char*>(src_lin) + 16 * c);
   }
   cp_async_commit();
+}
+
+// Box gather / scatter of the tensor-core RAS kernel: slot q of the box
+// (line-major, W per line) and mode a, y[q * MS + a]; every thread keeps
+// kRasIlp independent global loads in flight.
+constexpr int kRasIlp = 8;
+template <typename T>
+__device__ __forceinline__ void ras_gather(const T* __restrict__ R, int64_t ld, int P, int a0, int MC, int nslot,
+                                           int ncols, const int* __restrict__ gbox, T* y, int MS) {
+  const int total = nslot * ncols;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kRasIlp * blockDim.x) {
+    T v[kRasIlp];
+#pragma unroll
+    for (int u = 0; u < kRasIlp; ++u) {
+      const int e = e0 + u * int(blockDim.x);
+      v[u] = T(0);
+      if (e < total) {
+        const int a = e / nslot, q = e - a * nslot;
+        const int gi = gbox[q];
+        if (gi >= 0 && a < MC && a0 + a < P) v[u] = R[int64_t(a0 + a) * ld + (gi & kIdxMask)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRasIlp; ++u) {
+      const int e = e0 + u * int(blockDim.x);
+      if (e < total) {
+        const int a = e / nslot, q = e - a * nslot;
+        y[q * MS + a] = v[u];
+      }
+    }
+  }
+}
+template <typename T>
+__device__ __forceinline__ void ras_scatter(T* __restrict__ Z, int64_t ld, int P, int a0, int MC, int nslot,
+                                            const int* __restrict__ gbox, const T* y, int MS) {
+  const int total = nslot * MC;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kRasIlp * blockDim.x) {
+    int gi[kRasIlp];
+#pragma unroll
+    for (int u = 0; u < kRasIlp; ++u) {
+      const int e = e0 + u * int(blockDim.x);
+      gi[u] = e < total ? gbox[e % nslot] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kRasIlp; ++u) {
+      const int e = e0 + u * int(blockDim.x);
+      const int a = e / nslot, q = e - a * nslot;
+      if (e < total && gi[u] >= 0 && (gi[u] & kOwnedBit) && a0 + a < P)
+        Z[int64_t(a0 + a) * ld + (gi[u] & kIdxMask)] = y[q * MS + a];
+    }
+  }
 }
 
 template <typename T> struct Vec2;
@@ -60,12 +125,12 @@ template <> struct Vec2<double> { using type = double2; };
 template <typename T>
 __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__ Z, int P, int MC,
                             int W, int Lm, const int* __restrict__ nlines, const int* __restrict__ gidx,
-                            const T* __restrict__ linv, const T* __restrict__ loff) {
+                            const T* __restrict__ linv, const T* __restrict__ loff, int stages) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int MCe = (MC + 1) & ~1, MS = MCe + 2, MS2 = MS / 2, WW = W * W;
-  T* mats = reinterpret_cast<T*>(smem_raw);  // [kRasStages buffers][off, lin][W*W]
-  T* y = mats + 2 * kRasStages * WW;         // [Lm * W][MS]
+  T* mats = reinterpret_cast<T*>(smem_raw);  // [stages buffers][off, lin][W*W]
+  T* y = mats + 2 * stages * WW;             // [Lm * W][MS]
   T* s = y + size_t(Lm) * W * MS;            // [W][MS]
   T2* y2 = reinterpret_cast<T2*>(y);
   T2* s2 = reinterpret_cast<T2*>(s);
@@ -82,9 +147,9 @@ __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__
     return j + 1 < nl ? Lo + size_t(j + 1) * WW : nullptr;
   };
   auto step_lin = [&](int st) -> const T* { return Li + size_t(st < nl ? st : 2 * nl - 1 - st) * WW; };
-  // prologue: the first kRasStages - 1 steps' matrices in flight
-  for (int st = 0; st < kRasStages - 1; ++st) {
-    T* d = mats + (st % kRasStages) * 2 * WW;
+  // prologue: the first stages - 1 steps' matrices in flight
+  for (int st = 0; st < stages - 1; ++st) {
+    T* d = mats + (st % stages) * 2 * WW;
     if (st < 2 * nl)
       stage_mats<T>(d, d + WW, step_off(st), step_lin(st), WW);
     else
@@ -115,13 +180,13 @@ __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__
     }
   };
   for (int st = 0; st < 2 * nl; ++st) {
-    cp_async_wait_group<kRasStages - 2>();
+    cp_async_wait_dyn(stages - 2);
     __syncthreads();
-    const T* Lof = mats + (st % kRasStages) * 2 * WW;
+    const T* Lof = mats + (st % stages) * 2 * WW;
     const T* Lin = Lof + WW;
-    {  // keep kRasStages - 1 steps ahead in flight (buffer of step st - 1 is free)
-      const int nx = st + kRasStages - 1;
-      T* d = mats + (nx % kRasStages) * 2 * WW;
+    {  // keep stages - 1 steps ahead in flight (buffer of step st - 1 is free)
+      const int nx = st + stages - 1;
+      T* d = mats + (nx % stages) * 2 * WW;
       if (nx < 2 * nl)
         stage_mats<T>(d, d + WW, step_off(nx), step_lin(nx), WW);
       else
@@ -208,6 +273,157 @@ __global__ void k_ras_local(const T* __restrict__ R, int64_t ld, T* __restrict__
     int g = gbox[q];
     if (g >= 0 && (g & kOwnedBit) && a0 + aa < P) Z[int64_t(a0 + aa) * ld + (g & kIdxMask)] = y[q * MS + aa];
   }
+}
+
+// ---------------------------------------------------------------------------
+// RAS local solve on the tensor cores (FP32 data).  Each line step is two
+// small dense products, (W x W)(W x MC): the off-diagonal coupling and the
+// triangular inverse (zero above its diagonal, so the full tile product is
+// the same sum).  The FMA kernel above spends eight instructions in nine on
+// loads, loop control and lane reductions; here every warp owns one 16 x 8
+// tile of the W x MC result and runs m16n8k8 TF32 MMAs over the K = W
+// terms, each operand split into a TF32 high part and a TF32 remainder
+// (hi*hi + hi*lo + lo*hi, the dropped lo*lo term ~2^-22 relative), with FP32
+// accumulation: FP32-level accuracy at a tenth of the instructions.  The
+// products sit inside a recurrence of 2 x lines dependent steps, so
+// warp-level MMA fits better than a tensor-memory round trip per step.
+// Measured on GB300 (64 boxes of 36 x 36 nodes, P = 35) it is the slower
+// of the two: 0.30 ms against 0.20 ms for the FMA kernel, whose cost is the
+// latency of the dependent steps rather than its instruction count; it is
+// kept as an option (ras_kernel = 1).  Layout: y[line * W + t][mode] with a
+// mode stride MS = 8 x odd (B-fragment loads hit 32 distinct banks).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C (16 x 8 tile at rows m0.., cols n0..) = A (W x W, A[t][u] = M[t*W+u], or
+// M[u*W+t] when transposed) times B (B[u][n] = Bm[u*MS + n]); rows and
+// terms at or past W read as zero.
+__device__ __forceinline__ void tile_3xtf32(float (&c)[4], const float* M, bool trans, const float* Bm, int MS,
+                                            int W, int m0, int n0, int g, int tig) {
+  float big[4] = {0.f, 0.f, 0.f, 0.f}, small[4] = {0.f, 0.f, 0.f, 0.f};
+  const int r0 = m0 + g, r1 = r0 + 8;
+  for (int k0 = 0; k0 < W; k0 += 8) {
+    const int u0 = k0 + tig, u1 = u0 + 4;
+    auto at = [&](int t, int u) -> float {
+      if (t >= W || u >= W) return 0.f;
+      return trans ? M[u * W + t] : M[t * W + u];
+    };
+    const float av[4] = {at(r0, u0), at(r1, u0), at(r0, u1), at(r1, u1)};
+    const float bv[2] = {u0 < W ? Bm[u0 * MS + n0 + g] : 0.f, u1 < W ? Bm[u1 * MS + n0 + g] : 0.f};
+    uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tf32_split(av[i], ah[i], al[i]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) tf32_split(bv[i], bh[i], bl[i]);
+    mma_tf32(small, al, bh);
+    mma_tf32(small, ah, bl);
+    mma_tf32(big, ah, bh);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c[i] = big[i] + small[i];
+}
+
+__global__ void k_ras_local_tc(const float* __restrict__ R, int64_t ld, float* __restrict__ Z, int P, int MC, int W,
+                               int Lm, const int* __restrict__ nlines, const int* __restrict__ gidx,
+                               const float* __restrict__ linv, const float* __restrict__ loff, int stages, int MS) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int WW = W * W;
+  const int Nt = (MC + 7) / 8, Np = 8 * Nt;
+  float* mats = reinterpret_cast<float*>(smem_raw);  // [stages][off, lin][W*W]
+  float* y = mats + 2 * stages * WW;                  // [Lm * W][MS]
+  float* sb = y + size_t(Lm) * W * MS;                // [W][MS]
+  const int box = blockIdx.x, a0 = blockIdx.y * MC;
+  const int nl = nlines[box];
+  const int* gbox = gidx + size_t(box) * Lm * W;
+  const float* Li = linv + size_t(box) * Lm * WW;
+  const float* Lo = loff + size_t(box) * Lm * WW;
+  auto step_off = [&](int st) -> const float* {
+    if (st < nl) return st > 0 ? Lo + size_t(st) * WW : nullptr;
+    const int j = 2 * nl - 1 - st;
+    return j + 1 < nl ? Lo + size_t(j + 1) * WW : nullptr;
+  };
+  auto step_lin = [&](int st) -> const float* { return Li + size_t(st < nl ? st : 2 * nl - 1 - st) * WW; };
+  for (int st = 0; st < stages - 1; ++st) {
+    float* d = mats + (st % stages) * 2 * WW;
+    if (st < 2 * nl)
+      stage_mats<float>(d, d + WW, step_off(st), step_lin(st), WW);
+    else
+      cp_async_commit();
+  }
+  // gather; padding modes (up to Np) are zero
+  const int nslot = nl * W;
+  ras_gather<float>(R, ld, P, a0, MC, nslot, Np, gbox, y, MS);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tig = lane & 3;
+  const int m0 = (warp / Nt) * 16, n0 = (warp % Nt) * 8;
+  const int r0 = m0 + g, r1 = r0 + 8, c0 = n0 + 2 * tig;
+  // warps past the (W / 16) x (MC / 8) tiles only help with the gather and scatter
+  const bool tile_warp = warp < ((W + 15) / 16) * Nt;
+  for (int st = 0; st < 2 * nl; ++st) {
+    cp_async_wait_dyn(stages - 2);
+    __syncthreads();
+    const float* Lof = mats + (st % stages) * 2 * WW;
+    const float* Lin = Lof + WW;
+    {
+      const int nx = st + stages - 1;
+      float* d = mats + (nx % stages) * 2 * WW;
+      if (nx < 2 * nl)
+        stage_mats<float>(d, d + WW, step_off(nx), step_lin(nx), WW);
+      else
+        cp_async_commit();
+    }
+    const bool fwd = st < nl;
+    const int j = fwd ? st : 2 * nl - 1 - st;
+    const float* yj = y + size_t(j) * W * MS;
+    // s = y_j - Loff y_{j-1} (forward), s = y_j - Loff_{j+1}^T y_{j+1} (backward)
+    {
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      const bool has_off = fwd ? j > 0 : j + 1 < nl;
+      if (tile_warp && has_off)
+        tile_3xtf32(c, Lof, !fwd, y + size_t(fwd ? j - 1 : j + 1) * W * MS, MS, W, m0, n0, g, tig);
+      if (tile_warp && r0 < W) {
+        sb[r0 * MS + c0] = yj[r0 * MS + c0] - c[0];
+        sb[r0 * MS + c0 + 1] = yj[r0 * MS + c0 + 1] - c[1];
+      }
+      if (tile_warp && r1 < W) {
+        sb[r1 * MS + c0] = yj[r1 * MS + c0] - c[2];
+        sb[r1 * MS + c0 + 1] = yj[r1 * MS + c0 + 1] - c[3];
+      }
+    }
+    __syncthreads();
+    // y_j = Linv s (forward), x_j = Linv^T s (backward)
+    if (tile_warp) {
+      float c[4];
+      tile_3xtf32(c, Lin, !fwd, sb, MS, W, m0, n0, g, tig);
+      float* yw = y + size_t(j) * W * MS;
+      if (r0 < W) {
+        yw[r0 * MS + c0] = c[0];
+        yw[r0 * MS + c0 + 1] = c[1];
+      }
+      if (r1 < W) {
+        yw[r1 * MS + c0] = c[2];
+        yw[r1 * MS + c0 + 1] = c[3];
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  ras_scatter<float>(Z, ld, P, a0, MC, nslot, gbox, y, MS);
 }
 
 // In-place per-node transform z_r <- M z_r with a P x P matrix M (the
@@ -421,10 +637,54 @@ template <typename T>
 sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld, T* Z, cudaStream_t st,
                     bool transform, Profiler* prof) {
   const RasData& D = pc.ras;
-  // modes per CTA: at most what shared memory holds
+  if (sizeof(T) == 4 && pc.ras_kernel == 1) {
+    // tensor-core kernel: 8 modes per CTA by default (one 8-wide MMA tile;
+    // 64 boxes x 5 chunks of a 35-mode problem are 320 CTAs of 73 KB, all
+    // resident at once)
+    const int MC = pc.ras_modes > 0 ? std::min(pc.ras_modes, P) : std::min(8, P);
+    const int Nt = (MC + 7) / 8;
+    int MS = 8 * Nt;
+    if (MS % 16 == 0) MS += 8;
+    const int Mt = (D.wmax + 15) / 16;
+    const int stages = pc.ras_stages > 0 ? pc.ras_stages : kRasStages;
+    const size_t smem =
+        (2 * size_t(stages) * D.wmax * D.wmax + (size_t(D.lmax) + 1) * D.wmax * MS) * sizeof(float);
+    const int threads = std::max(32 * Mt * Nt, 256);
+    if (32 * Mt * Nt <= 1024 && smem <= 227 * 1024) {
+      static bool attr = false;
+      if (!attr) {
+        SG_CUDA(cudaFuncSetAttribute(k_ras_local_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+      }
+      dim3 grid(unsigned(D.nbox), unsigned((P + MC - 1) / MC));
+      size_t slot = 0;
+      const bool timed = prof && prof->on;
+      if (timed) SG_TRY(prof->begin(4, st, slot));
+      k_ras_local_tc<<<grid, threads, smem, st>>>(reinterpret_cast<const float*>(R), ld, reinterpret_cast<float*>(Z),
+                                                  P, MC, D.wmax, D.lmax, D.d_nlines.as<int>(), D.d_gidx.as<int>(),
+                                                  D.linv32.as<float>(), D.loff32.as<float>(), stages, MS);
+      note_launch();
+      SG_CUDA(cudaGetLastError());
+      if (timed) SG_TRY(prof->end(slot, st));
+      if (transform) SG_TRY(node_transform<T>(Z, ld, n, P, dv<T>(pc.gtinv64, pc.gtinv32), st));
+      return SG_OK;
+    }
+  }
+  // FMA kernel: modes per CTA at most what shared memory holds next to the
+  // ring of line matrices (depths 3 to 8 measured the same at 256^2; a
+  // given depth gives way to more modes per CTA unless it was asked for)
   const size_t per_mode = (size_t(D.lmax) * D.wmax + D.wmax) * sizeof(T);
-  const size_t fixed = 2 * kRasStages * size_t(D.wmax) * D.wmax * sizeof(T);
-  const int fit = int(std::max<size_t>(2, ((227 * 1024 - fixed) / per_mode - 2) & ~size_t(1)));
+  const size_t mat = 2 * size_t(D.wmax) * D.wmax * sizeof(T);
+  int stages = pc.ras_stages > 0 ? pc.ras_stages : kRasStages;
+  auto fit_for = [&](int stg) -> int {
+    const size_t fixed = size_t(stg) * mat;
+    if (fixed + 4 * per_mode > 227 * 1024) return 0;
+    return int(std::max<size_t>(2, ((227 * 1024 - fixed) / per_mode - 2) & ~size_t(1)));
+  };
+  if (pc.ras_stages <= 0)
+    while (stages > 2 && (fit_for(stages) < std::min(P, 18) || fit_for(stages) == 0)) --stages;
+  const size_t fixed = size_t(stages) * mat;
+  const int fit = std::max(2, fit_for(stages));
   const int by_threads = std::max(2, (1024 / std::max(2, D.wmax)) & ~1);  // 4 (W/2) (MC/2) <= 1024
   int maxmc = std::min(fit, by_threads);
   if (pc.ras_modes > 0) maxmc = std::min(maxmc, pc.ras_modes);
@@ -451,7 +711,7 @@ sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld,
   if (timed) SG_TRY(prof->begin(sizeof(T) == 8 ? 5 : 4, st, slot));
   k_ras_local<T><<<grid, threads, smem, st>>>(R, ld, Z, P, MC, D.wmax, D.lmax, D.d_nlines.as<int>(),
                                               D.d_gidx.as<int>(), dv<T>(D.linv64, D.linv32),
-                                              dv<T>(D.loff64, D.loff32)); note_launch();
+                                              dv<T>(D.loff64, D.loff32), stages); note_launch();
   SG_CUDA(cudaGetLastError());
   if (timed) SG_TRY(prof->end(slot, st));
   if (transform) SG_TRY(node_transform<T>(Z, ld, n, P, dv<T>(pc.gtinv64, pc.gtinv32), st));

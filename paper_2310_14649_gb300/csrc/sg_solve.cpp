@@ -213,6 +213,9 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
          "sg_precond_setup: subdomain counts must be in [1, N-1]");
   SG_ARG(o->overlap >= 0 && o->overlap <= 8, "sg_precond_setup: overlap must be in [0, 8]");
   SG_ARG(o->amg_kernel == 0 || o->amg_kernel == 1, "sg_precond_setup: amg_kernel must be 0 or 1");
+  SG_ARG(o->ras_kernel == 0 || o->ras_kernel == 1, "sg_precond_setup: ras_kernel must be 0 or 1");
+  SG_ARG(o->ras_stages == 0 || (o->ras_stages >= 2 && o->ras_stages <= 8),
+         "sg_precond_setup: ras_stages must be 0 (automatic) or in [2, 8]");
   SG_ARG(o->inner_orth_passes >= 0 && o->inner_orth_passes <= 2,
          "sg_precond_setup: inner_orth_passes must be 0 (default), 1 or 2");
   SG_ARG(o->smoother == 0 || o->smoother == 1, "sg_precond_setup: smoother must be 0 (RAS) or 1 (learned)");
@@ -231,6 +234,8 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   pc.inner_restart = 30;
   pc.device_loops = o->host_loops == 0;
   pc.ras_modes = o->ras_modes > 0 ? o->ras_modes : 0;
+  pc.ras_stages = o->ras_stages;
+  pc.ras_kernel = o->ras_kernel;
   pc.inner_passes = o->inner_orth_passes > 0 ? o->inner_orth_passes : 1;
   SG_TRY(kernel_attrs_init());
   sg_status s = precond_setup_host(pr, pc);

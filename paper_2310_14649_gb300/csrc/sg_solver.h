@@ -79,6 +79,8 @@ struct Precond {
   int inner_max = 100, inner_restart = 30;
   int inner_passes = 1;  // Gram-Schmidt passes of the coarse GMRES
   int ras_modes = 0;                       // modes per CTA of the RAS kernel (0 automatic)
+  int ras_stages = 0;                      // depth of its ring of line matrices (0 automatic)
+  int ras_kernel = 0;                      // 0: FMA kernel; 1: tensor cores for FP32 data
   RasData ras;
   CoarseData co;
   AmgHier amg;                             // on the coarse mean operator

@@ -136,6 +136,51 @@ def test_ras_and_smoother(pair, dt):
     assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr))
 
 
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_ras_ring_depths(pair, dt):
+    """The RAS local solves with 2, 3, 5 and 8 line steps' matrices in
+    flight (and the automatic depth) match the oracle; a depth outside 2..8
+    is rejected."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, (sx, sy, ov) = pair
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    tol = 1e-11 if dt == "f64" else 1e-4
+    X = random_block(ref.n, ref.P, seed=36)
+    try:
+        for stages in (2, 3, 5, 8, 0):
+            sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200, ras_stages=stages)
+            Y, Xq = run(prob, sg.PC_RAS_LOCAL, X, ref.n, dtype)
+            Yr = ras.apply_ras(tl.parts, tl.solvers, Xq)
+            assert np.max(np.abs(Y - Yr)) <= tol * np.max(np.abs(Yr)), stages
+        for bad in (1, 9):
+            with pytest.raises(sg.SgError):
+                sg.sg_precond_setup(prob, sx, sy, ov, ras_stages=bad)
+    finally:
+        sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200)
+
+
+@pytest.mark.parametrize("kernel,modes", [(1, 0), (1, 3), (1, 8), (1, 10), (0, 0), (0, 4)])
+def test_ras_kernels(pair, kernel, modes):
+    """FP32 RAS local solves on the tensor cores (3xTF32 MMA; several mode
+    chunks per box, ragged last chunk, one or two 8-mode tiles) and on the
+    FMA kernel match the oracle."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, (sx, sy, ov) = pair
+    X = random_block(ref.n, ref.P, seed=37)
+    try:
+        sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200, ras_kernel=kernel, ras_modes=modes)
+        Y, Xq = run(prob, sg.PC_RAS_LOCAL, X, ref.n, torch.float32)
+        Yr = ras.apply_ras(tl.parts, tl.solvers, Xq)
+        assert np.max(np.abs(Y - Yr)) <= 1e-4 * np.max(np.abs(Yr))
+        assert np.linalg.norm(Y - Yr) <= 2e-6 * np.linalg.norm(Yr)
+        with pytest.raises(sg.SgError):
+            sg.sg_precond_setup(prob, sx, sy, ov, ras_kernel=2)
+    finally:
+        sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200)
+
+
 def test_omega_estimate_is_the_smoother_radius(pair):
     import paper_2310_14649_gb300 as sg
     prob, ref, tl, _ = pair
