@@ -137,6 +137,23 @@ sg_status sg_apply(sg_problem* prob, sg_dtype dtype, const void* X_dev, int64_t 
  * Errors: SG_ERR_CUDA with the compiler log when compilation fails. */
 sg_status sg_set_apply_kernel(sg_problem* prob, int mode);
 
+/* FP64 applies (Sec. 2.1, Eq. Galerkin_L_exp) over assembled blocks: the K
+ * values of each stencil edge summed once into its symmetric P x P block,
+ * C_ab = sum_k g_kab v_k (P (P + 1) / 2 doubles per edge, S per row), so an
+ * FP64 apply costs P^2 FMAs per edge instead of two FP64 operations per
+ * triple (GB300's FP64 units bound the FP64 applies).  mode 0 (default):
+ * built on the first FP64 apply of the fine and of the coarse operator
+ * when the blocks take at most a quarter of the free device memory; 1:
+ * never (the generated or shared-memory kernel); 2: always, built now
+ * (SG_ERR_NOMEM when they do not fit).  A change drops the recorded
+ * coarse-solve graphs (rebuilt on the next solve); recorded batches of this
+ * problem then refuse to run.  FP32 applies are unaffected. */
+sg_status sg_set_apply_fp64(sg_problem* prob, int mode);
+
+/* Whether the fine and the coarse FP64 applies use assembled blocks (0/1)
+ * and the device bytes the blocks hold.  Any pointer may be NULL. */
+sg_status sg_apply_fp64_info(const sg_problem* prob, int* fine, int* coarse, int64_t* bytes);
+
 /* Tile shape of the register-specialised kernel of one family: which = 0
  * fine FP32, 1 coarse FP32, 2 fine FP64, 3 coarse FP64 (the FP64 kernels
  * carry the triple products as exact double immediates): rows per thread

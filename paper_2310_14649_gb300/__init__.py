@@ -15,7 +15,8 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_get_triples", "sg_get_csr", "sg_get_values", "sg_get_rhs", "sg_apply",
            "sg_residual", "sg_precond_setup", "sg_precond_info", "sg_get_partition",
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
-           "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel",
+           "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel", "sg_set_apply_fp64",
+           "sg_apply_fp64_info",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
@@ -246,6 +247,18 @@ def sg_launch_count():
 def sg_set_apply_kernel(prob, mode):
     """0 auto, 1 shared-memory kernel, 2 register-specialised kernel."""
     call("sg_set_apply_kernel", prob.handle, mode)
+
+
+def sg_set_apply_fp64(prob, mode):
+    """FP64 applies over assembled P x P edge blocks: 0 auto (memory
+    permitting), 1 never, 2 always."""
+    call("sg_set_apply_fp64", prob.handle, mode)
+
+
+def sg_apply_fp64_info(prob):
+    f, c, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    call("sg_apply_fp64_info", prob.handle, ctypes.byref(f), ctypes.byref(c), ctypes.byref(b))
+    return {"fine": f.value, "coarse": c.value, "bytes": b.value}
 
 
 def sg_apply_config(prob, rows=1, groups=1, igroups=1, sgroups=1, prefetch=8, min_blocks=1, stages=0, cgroups=1,

@@ -90,6 +90,7 @@ sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
     set_error("sg_set_apply_kernel: the specialised kernel needs P <= 128 and T <= 40000");
     return SG_ERR_UNSUPPORTED;
   }
+  drop_recorded(pr);
   pr->apply_mode = mode;
   if (mode != 1 && jit_eligible(pr)) return jit_apply_build(pr, 0);
   return SG_OK;
@@ -98,6 +99,7 @@ sg_status sg_set_apply_kernel(sg_problem* pr, int mode) {
 sg_status sg_apply_config(sg_problem* pr, int which, int rows, int groups, int igroups, int sgroups, int prefetch,
                           int min_blocks, int stages, int cgroups, int warps) {
   SG_ARG(pr && which >= 0 && which < kJitFamilies, "sg_apply_config: NULL handle or which not in [0, 3]");
+  drop_recorded(pr);
   JitConfig c;
   c.rows = rows;
   c.groups = groups;

@@ -87,6 +87,57 @@ __global__ void __launch_bounds__(256) k_apply_tile(ApplyArgs<T> p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Assembled FP64 apply.  The generated FP64 kernel spends two FP64
+// operations per triple and slot (2,395 triples at P = 35), and GB300's FP64
+// units (about 1.2 TFLOP/s) bound it; summing the K values of each stencil
+// edge into its symmetric P x P block once leaves P^2 FMAs per edge (3x
+// fewer FP64 operations) for (S P (P+1) / 2) doubles per row of memory.
+// Block build: thread per (row, packed pair), loop over the pair's (k, g)
+// list and the slots.  Apply: lane = row of a 32-row tile, warps over the
+// output modes; C_ab and C_ba are one stored value, read by two warps of
+// the same CTA (the second from L1).
+// ---------------------------------------------------------------------------
+__global__ void k_asm_build(int64_t ldr, int S, int npair, const int* __restrict__ pptr, const int* __restrict__ pk,
+                            const double* __restrict__ pg, const double* __restrict__ V, double* __restrict__ C) {
+  const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int p = blockIdx.y;
+  if (r >= ldr) return;
+  const int e0 = pptr[p], e1 = pptr[p + 1];
+  for (int s = 0; s < S; ++s) {
+    double c = 0.0;
+    for (int e = e0; e < e1; ++e) c += pg[e] * V[(int64_t(pk[e]) * S + s) * ldr + r];
+    C[(int64_t(s) * npair + p) * ldr + r] = c;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_apply_asm64(int64_t n, int64_t ldr, int S, int P, int npair,
+                                                      const int* __restrict__ col, const double* __restrict__ C,
+                                                      const double* __restrict__ X, int64_t ldx,
+                                                      const double* __restrict__ F, int64_t ldf,
+                                                      double* __restrict__ Y, int64_t ldy) {
+  const int64_t r = int64_t(blockIdx.x) * 32 + threadIdx.x;
+  if (r >= n) return;
+  for (int a = threadIdx.y; a < P; a += blockDim.y) {
+    // packed index of (lo, hi), lo <= hi: off(lo) + hi with
+    // off(b) = b P - b (b - 1) / 2 - b
+    const int off_a = a * P - a * (a - 1) / 2 - a;
+    double acc = 0.0;
+    for (int s = 0; s < S; ++s) {
+      const int c = col[int64_t(s) * ldr + r];
+      const double* Cs = C + int64_t(s) * npair * ldr + r;
+      const double* xc = X + c;
+      int off_b = 0;
+      for (int b = 0; b < P; ++b) {
+        const int pidx = b < a ? off_b + a : off_a + b;
+        acc = fma(Cs[int64_t(pidx) * ldr], xc[int64_t(b) * ldx], acc);
+        off_b += P - b - 1;
+      }
+    }
+    Y[int64_t(a) * ldy + r] = F ? F[int64_t(a) * ldf + r] - acc : acc;
+  }
+}
+
 template <typename T> const T* vals_of(const Ell& A);
 template <> const double* vals_of<double>(const Ell& A) { return A.v64.as<double>(); }
 template <> const float* vals_of<float>(const Ell& A) { return A.v32.as<float>(); }
@@ -183,20 +234,96 @@ sg_status Profiler::read(int kind, int64_t* launches, double* ms) {
   return SG_OK;
 }
 
+sg_status asm_prepare(sg_problem* pr, const Ell& A, AsmBlocks& B, cudaStream_t st) {
+  if (B.tried || pr->asm_mode == 1) return SG_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  SG_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return SG_OK;
+  B.tried = true;
+  const int P = pr->P, S = A.S;
+  const int npair = P * (P + 1) / 2;
+  const size_t bytes = size_t(S) * npair * A.ldr * sizeof(double);
+  if (pr->asm_mode == 0) {
+    // automatic: only while the blocks take at most a quarter of free memory
+    size_t fr = 0, tot = 0;
+    SG_CUDA(cudaMemGetInfo(&fr, &tot));
+    if (bytes > fr / 4) return SG_OK;
+  }
+  // (k, g) list of every packed pair a <= b
+  std::vector<std::vector<std::pair<int, double>>> lst(npair);
+  for (int64_t t = 0; t < pr->T; ++t) {
+    const int k = pr->kab[3 * t], a = pr->kab[3 * t + 1], b = pr->kab[3 * t + 2];
+    if (a > b) continue;
+    lst[size_t(a) * P - size_t(a) * (a - 1) / 2 + (b - a)].push_back({k, pr->g[t]});
+  }
+  std::vector<int> pptr(npair + 1, 0), pk;
+  std::vector<double> pg;
+  for (int q = 0; q < npair; ++q) {
+    for (const auto& e : lst[q]) {
+      pk.push_back(e.first);
+      pg.push_back(e.second);
+    }
+    pptr[q + 1] = int(pk.size());
+  }
+  DevBuf dptr, dk, dg, c;
+  SG_TRY(c.alloc(bytes));
+  SG_TRY(dptr.alloc(pptr.size() * 4));
+  SG_TRY(dk.alloc(std::max<size_t>(1, pk.size()) * 4));
+  SG_TRY(dg.alloc(std::max<size_t>(1, pg.size()) * 8));
+  SG_CUDA(cudaMemcpy(dptr.ptr, pptr.data(), pptr.size() * 4, cudaMemcpyHostToDevice));
+  if (!pk.empty()) {
+    SG_CUDA(cudaMemcpy(dk.ptr, pk.data(), pk.size() * 4, cudaMemcpyHostToDevice));
+    SG_CUDA(cudaMemcpy(dg.ptr, pg.data(), pg.size() * 8, cudaMemcpyHostToDevice));
+  }
+  k_asm_build<<<dim3(unsigned((A.ldr + 127) / 128), unsigned(npair)), 128, 0, st>>>(
+      A.ldr, S, npair, dptr.as<int>(), dk.as<int>(), dg.as<double>(), A.v64.as<double>(), c.as<double>());
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  SG_CUDA(cudaStreamSynchronize(st));
+  B.npair = npair;
+  B.c = std::move(c);
+  return SG_OK;
+}
+
+sg_status apply_asm64(const sg_problem* pr, const Ell& A, const AsmBlocks& B, const double* X, int64_t ldx,
+                      const double* F, int64_t ldf, double* Y, int64_t ldy, cudaStream_t st) {
+  if (A.n == 0) return SG_OK;
+  const dim3 block(32, 8);
+  k_apply_asm64<<<unsigned((A.n + 31) / 32), block, 0, st>>>(A.n, A.ldr, A.S, pr->P, B.npair, A.col.as<int>(),
+                                                              B.c.as<double>(), X, ldx, F, ldf, Y, ldy);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename T>
+sg_status apply_any(sg_problem* pr, bool coarse, const T* X, int64_t ldx, const T* F, int64_t ldf, T* Y,
+                    int64_t ldy, cudaStream_t st) {
+  const Ell& A = coarse ? coarse_ell(pr) : pr->fine;
+  if (sizeof(T) == 8) {
+    const AsmBlocks& B = coarse ? coarse_asm(pr) : pr->asm_fine;
+    if (B.c.ptr)
+      return apply_asm64(pr, A, B, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<const double*>(F),
+                         ldf, reinterpret_cast<double*>(Y), ldy, st);
+  }
+  if (pr->apply_mode != 1 && jit_eligible(pr))
+    return jit_apply_launch(pr, (coarse ? 1 : 0) + (sizeof(T) == 8 ? 2 : 0), A, X, ldx, F, ldf, Y, ldy, st);
+  return apply_ell<T>(A, coarse ? coarse_tri(pr) : pr->tri, pr->P, pr->K, X, ldx, F, ldf, Y, ldy, st);
+}
+
+template sg_status apply_any<double>(sg_problem*, bool, const double*, int64_t, const double*, int64_t, double*,
+                                     int64_t, cudaStream_t);
+template sg_status apply_any<float>(sg_problem*, bool, const float*, int64_t, const float*, int64_t, float*,
+                                    int64_t, cudaStream_t);
+
 template <typename T>
 sg_status apply_op(sg_problem* pr, bool coarse, const T* X, int64_t ldx, const T* F, int64_t ldf, T* Y,
                    int64_t ldy, cudaStream_t st) {
-  const Ell& A = coarse ? coarse_ell(pr) : pr->fine;
-  const TripleTables& tri = coarse ? coarse_tri(pr) : pr->tri;
+  if (sizeof(T) == 8) SG_TRY(asm_prepare(pr, coarse ? coarse_ell(pr) : pr->fine, coarse ? coarse_asm(pr) : pr->asm_fine, st));
   size_t slot = 0;
   const bool on = pr->prof.on;
   if (on) SG_TRY(pr->prof.begin((coarse ? 2 : 0) + (sizeof(T) == 8 ? 1 : 0), st, slot));
-  const bool spec = pr->apply_mode != 1 && jit_eligible(pr);
-  if (spec) {
-    SG_TRY(jit_apply_launch(pr, (coarse ? 1 : 0) + (sizeof(T) == 8 ? 2 : 0), A, X, ldx, F, ldf, Y, ldy, st));
-  } else {
-    SG_TRY(apply_ell<T>(A, tri, pr->P, pr->K, X, ldx, F, ldf, Y, ldy, st));
-  }
+  SG_TRY(apply_any<T>(pr, coarse, X, ldx, F, ldf, Y, ldy, st));
   if (on) SG_TRY(pr->prof.end(slot, st));
   return SG_OK;
 }

@@ -369,9 +369,7 @@ struct SolverCtx {
 
   // fine apply without the profiler (Y = F - A X when F, else A X)
   sg_status apply_raw_fine(const T* X, T* Y, const T* F, cudaStream_t st) {
-    if (pr->apply_mode != 1 && jit_eligible(pr))
-      return jit_apply_launch(pr, sizeof(T) == 8 ? 2 : 0, pr->fine, X, ld, F, ld, Y, ld, st);
-    return apply_ell<T>(pr->fine, pr->tri, pr->P, pr->K, X, ld, F, ld, Y, ld, st);
+    return apply_any<T>(pr, false, X, ld, F, ld, Y, ld, st);
   }
   // iteration counters summed over solves (device): fine FGMRES, coarse GMRES
   sg_status clear_counters(cudaStream_t st) {
@@ -405,9 +403,7 @@ struct SolverCtx {
 
   // coarse apply without the profiler (used inside graph capture)
   sg_status apply_raw(const T* X, T* Y, const T* F, cudaStream_t st) {
-    if (pr->apply_mode != 1 && jit_eligible(pr))
-      return jit_apply_launch(pr, sizeof(T) == 8 ? 3 : 1, pc->co.ell, X, ldc, F, ldc, Y, ldc, st);
-    return apply_ell<T>(pc->co.ell, pc->co.tri, pr->P, pr->K, X, ldc, F, ldc, Y, ldc, st);
+    return apply_any<T>(pr, true, X, ldc, F, ldc, Y, ldc, st);
   }
 
   // Device-driven restarted GMRES on the coarse system (the 2GV3 inner
@@ -432,6 +428,10 @@ struct SolverCtx {
   // everything a captured launch needs must exist before a capture starts:
   // specialised kernels, kernel attributes, network buffers
   sg_status capture_prepare() {
+    if (sizeof(T) == 8) {
+      SG_TRY(asm_prepare(pr, pr->fine, pr->asm_fine, nullptr));
+      SG_TRY(asm_prepare(pr, pc->co.ell, pc->co.asm_c, nullptr));
+    }
     if (pr->apply_mode != 1 && jit_eligible(pr)) {
       SG_TRY(jit_apply_build(pr, sizeof(T) == 8 ? 2 : 0));
       SG_TRY(jit_apply_build(pr, sizeof(T) == 8 ? 3 : 1));

@@ -85,6 +85,15 @@ struct Ell {
   DevBuf v32;      // float  K x S x ldr
 };
 
+// The Galerkin operator summed per stencil edge into its P x P block (FP64),
+//   C_ab^{r,s} = sum_k g_kab v_k^{r,s}   (symmetric: a <= b stored, packed
+//   row by row), layout [S][npair][ldr]; built on demand for FP64 applies.
+struct AsmBlocks {
+  int npair = 0;
+  bool tried = false;  // the policy was applied (built or declined)
+  DevBuf c;
+};
+
 struct SolverState;
 void solver_free(sg_problem* pr);
 struct Cnn;
@@ -170,6 +179,8 @@ struct sg_problem {
   bool jit_cfg_set[sg::kJitFamilies] = {};
   sg::DevBuf mdot_partial, mdot_counter;  // scratch of sg_mdot
   int apply_mode = 0;                  // 0 auto, 1 shared-memory kernel, 2 specialised
+  sg::AsmBlocks asm_fine;              // assembled FP64 blocks of the fine operator
+  int asm_mode = 0;                    // FP64 applies: 0 auto, 1 never assembled, 2 always
 };
 
 namespace sg {
@@ -195,6 +206,16 @@ sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const double
                            int64_t ldf, double* Y, int64_t ldy, cudaStream_t st);
 sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const float* X, int64_t ldx, const float* F,
                            int64_t ldf, float* Y, int64_t ldy, cudaStream_t st);
+// assembled FP64 blocks (sg_apply.cu): build per the problem's policy (no-op
+// once tried; never while `st` is capturing), and the apply over them
+sg_status asm_prepare(sg_problem* pr, const Ell& A, AsmBlocks& B, cudaStream_t st);
+sg_status apply_asm64(const sg_problem* pr, const Ell& A, const AsmBlocks& B, const double* X, int64_t ldx,
+                      const double* F, int64_t ldf, double* Y, int64_t ldy, cudaStream_t st);
+// the operator apply without timing: assembled blocks (FP64, when built),
+// else the specialised kernel, else the shared-memory kernel
+template <typename T>
+sg_status apply_any(sg_problem* pr, bool coarse, const T* X, int64_t ldx, const T* F, int64_t ldf, T* Y,
+                    int64_t ldy, cudaStream_t st);
 // apply_ell on the fine (coarse = false) or coarse family of a problem,
 // timed when the problem's profiler is on
 template <typename T>

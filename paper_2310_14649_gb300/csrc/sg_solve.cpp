@@ -14,6 +14,19 @@ namespace sg {
 
 const Ell& coarse_ell(const sg_problem* pr) { return pr->solver->pc.co.ell; }
 const TripleTables& coarse_tri(const sg_problem* pr) { return pr->solver->pc.co.tri; }
+AsmBlocks& coarse_asm(sg_problem* pr) { return pr->solver->pc.co.asm_c; }
+
+// Recorded graphs (the coarse-solve graphs of the solver contexts) hold the
+// kernels and buffers of the applies they captured: a change of apply
+// kernel drops the contexts, so they are rebuilt, and recorded batches of
+// this problem refuse to run (their contexts no longer match).
+void drop_recorded(sg_problem* pr) {
+  if (!pr->solver) return;
+  cudaDeviceSynchronize();
+  pr->solver->c64.reset();
+  pr->solver->c32.reset();
+}
+
 
 void solver_free(sg_problem* pr) {
   delete pr->solver;
@@ -253,6 +266,29 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
     return s;
   }
   pc.ready = true;
+  return SG_OK;
+}
+
+sg_status sg_set_apply_fp64(sg_problem* pr, int mode) {
+  SG_ARG(pr && mode >= 0 && mode <= 2, "sg_set_apply_fp64: mode must be 0, 1 or 2");
+  drop_recorded(pr);
+  pr->asm_mode = mode;
+  pr->asm_fine = AsmBlocks();
+  if (pr->solver) pr->solver->pc.co.asm_c = AsmBlocks();
+  if (mode == 2) {
+    SG_TRY(asm_prepare(pr, pr->fine, pr->asm_fine, nullptr));
+    if (pr->solver && pr->solver->pc.ready) SG_TRY(asm_prepare(pr, coarse_ell(pr), coarse_asm(pr), nullptr));
+  }
+  return SG_OK;
+}
+
+sg_status sg_apply_fp64_info(const sg_problem* pr, int* fine, int* coarse, int64_t* bytes) {
+  SG_ARG(pr, "sg_apply_fp64_info: NULL handle");
+  const bool f = pr->asm_fine.c.ptr != nullptr;
+  const bool c = pr->solver && pr->solver->pc.co.asm_c.c.ptr != nullptr;
+  if (fine) *fine = f;
+  if (coarse) *coarse = c;
+  if (bytes) *bytes = int64_t((f ? pr->asm_fine.c.bytes : 0) + (c ? pr->solver->pc.co.asm_c.c.bytes : 0));
   return SG_OK;
 }
 

@@ -61,6 +61,7 @@ struct CoarseData {
   Ell ell;                                 // coarse A_k in ELL form (device)
   TripleTables tri;
   DevCsr RT, R;                            // interpolation (n x nc) and restriction
+  AsmBlocks asm_c;                         // assembled FP64 blocks of the coarse operator
 };
 
 // Smoother inputs recorded during solves: the training residuals of the
@@ -113,6 +114,10 @@ sg_status precond_setup_host(sg_problem* pr, Precond& pc);
 sg_status amg_setup_fine(const sg_problem* pr, AmgHier& h);
 const Ell& coarse_ell(const sg_problem* pr);
 const TripleTables& coarse_tri(const sg_problem* pr);
+AsmBlocks& coarse_asm(sg_problem* pr);
+// drops the solver contexts and their recorded graphs after a change of
+// apply kernel (recorded batches of the problem then refuse to run)
+void drop_recorded(sg_problem* pr);
 sg_status precond_setup_coarse_plan(sg_problem* pr, Precond& pc, const CoarsePlan& plan);
 sg_status precond_setup_device(sg_problem* pr, Precond& pc, double omega_opt, cudaStream_t st);
 void precond_free(Precond& pc);

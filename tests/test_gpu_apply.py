@@ -76,10 +76,13 @@ def test_stiffness_values(gpu, N, L, p, q, s2, b):
     assert np.max(np.abs(vals - ref.vals)) < 1e-13 * scale
 
 
-def check_apply(prob, ref, X, dtype, ld=None, kernel=0):
+def check_apply(prob, ref, X, dtype, ld=None, kernel=0, fp64=1):
+    """fp64: 1 keeps FP64 applies on the selected kernel, 2 on the
+    assembled edge blocks."""
     import torch
     import paper_2310_14649_gb300 as sg
     sg.sg_set_apply_kernel(prob, kernel)
+    sg.sg_set_apply_fp64(prob, fp64)
     Xd = to_dev(X, dtype, ld)
     Yd = torch.full_like(Xd, float("nan"))
     sg.sg_apply(prob, Xd, Yd)
@@ -93,30 +96,37 @@ def check_apply(prob, ref, X, dtype, ld=None, kernel=0):
     return Yd
 
 
-@pytest.mark.parametrize("dt", ["f64", "f64-shared", "f32", "f32-shared"])
+@pytest.mark.parametrize("dt", ["f64", "f64-shared", "f64-asm", "f32", "f32-shared"])
 @pytest.mark.parametrize("N,L,p,q", [(32, 2, 2, 4), (33, 3, 3, 6), (2, 2, 1, 2), (9, 0, 0, 0), (40, 1, 5, 10)])
 def test_apply_vs_oracle(gpu, dt, N, L, p, q):
-    """Register-specialised and shared-memory kernels, FP64 and FP32, each
-    against the oracle within the deterministic rounding bound."""
+    """Register-specialised, shared-memory and (FP64) assembled-block
+    kernels, FP64 and FP32, each against the oracle within the
+    deterministic rounding bound."""
     import torch
+    import paper_2310_14649_gb300 as sg
     dtype = torch.float64 if dt.startswith("f64") else torch.float32
     kernel = 1 if dt.endswith("shared") else 2
+    fp64 = 2 if dt.endswith("asm") else 1
     prob, ref = setup_pair(N, L, p, q)
     X = random_block(ref.n, ref.P, seed=3)
-    check_apply(prob, ref, X, dtype, kernel=kernel)
+    check_apply(prob, ref, X, dtype, kernel=kernel, fp64=fp64)
+    assert sg.sg_apply_fp64_info(prob)["fine"] == (fp64 == 2)
     # ragged leading dimension and a second, different input
-    check_apply(prob, ref, random_block(ref.n, ref.P, seed=4), dtype, ld=ref.n + 37, kernel=kernel)
+    check_apply(prob, ref, random_block(ref.n, ref.P, seed=4), dtype, ld=ref.n + 37, kernel=kernel, fp64=fp64)
 
 
-def test_residual_in_place(gpu):
+@pytest.mark.parametrize("fp64", [1, 2])
+def test_residual_in_place(gpu, fp64):
     import torch
     import paper_2310_14649_gb300 as sg
     prob, ref = setup_pair(32, 2, 2, 4)
+    sg.sg_set_apply_fp64(prob, fp64)
     X = random_block(ref.n, ref.P, seed=8)
     F = random_block(ref.n, ref.P, seed=9)
     Xd, Fd = to_dev(X, torch.float64), to_dev(F, torch.float64)
     sg.sg_residual(prob, Fd, Xd, Fd)
     torch.cuda.synchronize()
+    assert sg.sg_apply_fp64_info(prob)["fine"] == (fp64 == 2)
     R = from_dev(Fd, ref.n)
     Rref = F - galerkin.apply(ref, X)
     Yb, m = bound_and_terms(ref, X)
@@ -144,8 +154,10 @@ def test_apply_full_size_sampled_rows(gpu):
     rows = np.unique(np.concatenate([[0, 1, ref.n - 1, ref.n // 2],
                                      np.random.default_rng(0).integers(0, ref.n, 60)]))
     X = random_block(ref.n, ref.P, seed=21)
-    for dtype, u, kernel in ((torch.float64, U64, 0), (torch.float32, U32, 2), (torch.float32, U32, 1)):
+    for dtype, u, kernel, fp64 in ((torch.float64, U64, 0, 2), (torch.float64, U64, 2, 1), (torch.float32, U32, 2, 1),
+                                   (torch.float32, U32, 1, 1)):
         sg.sg_set_apply_kernel(prob, kernel)
+        sg.sg_set_apply_fp64(prob, fp64)
         Xd = to_dev(X, dtype)
         Yd = torch.empty_like(Xd)
         sg.sg_apply(prob, Xd, Yd)

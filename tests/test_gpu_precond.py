@@ -106,6 +106,26 @@ def test_transfer_and_coarse_operator(pair, dt):
     assert np.max(np.abs(Y - Yr)) <= (50 * tol) * scale
 
 
+@pytest.mark.parametrize("fp64", [1, 2])
+def test_coarse_apply_fp64_paths(pair, fp64):
+    """The FP64 coarse operator on its generated kernel and on assembled
+    edge blocks, against the oracle."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, _ = pair
+    try:
+        sg.sg_set_apply_fp64(prob, fp64)
+        Xc = random_block(tl.nc, ref.P, seed=38)
+        Y, Xq = run(prob, sg.PC_COARSE_APPLY, Xc, tl.nc, torch.float64)
+        info = sg.sg_apply_fp64_info(prob)
+        assert info["coarse"] == (fp64 == 2) and (info["bytes"] > 0) == (fp64 == 2)
+        Yr = coarse.coarse_apply(tl.Acs, tl.G, Xq)
+        scale = np.max(np.abs(coarse.coarse_apply([abs(a) for a in tl.Acs], abs(tl.G), abs(Xq))))
+        assert np.max(np.abs(Y - Yr)) <= 5e-13 * scale
+    finally:
+        sg.sg_set_apply_fp64(prob, 0)
+
+
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 def test_amg_vcycle(pair, dt):
     import torch

@@ -179,6 +179,30 @@ def test_gram_schmidt_passes(gpu, mode):
     assert max(its.values()) - min(its.values()) <= 2
 
 
+def test_fp64_apply_paths_in_solve(gpu):
+    """The FP64 solve with its applies on assembled edge blocks and on the
+    generated kernels: both reach the oracle's solution in the same number
+    of outer iterations (to within one)."""
+    import paper_2310_14649_gb300 as sg
+    c = dict(CONFIGS["poisson256_L4_p3"], N=64, sx=4, sy=4)
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    Xo, _, _ = galerkin.solve_gmres(ref, tol=1e-12)
+    prob = setup(c)
+    its = []
+    for fp64 in (2, 1):
+        sg.sg_set_apply_fp64(prob, fp64)
+        X = zeros(prob)
+        info = sg.sg_solve(prob, X, rtol=1e-8, mode=0)
+        assert sg.sg_apply_fp64_info(prob)["fine"] == (fp64 == 2)
+        Xh = to_np(X, prob.n)
+        assert galerkin.relres(ref, Xh) <= 1.01e-8
+        assert np.linalg.norm(Xh - Xo) / np.linalg.norm(Xo) <= 1e-7
+        its.append(info["outer_it"])
+    assert abs(its[0] - its[1]) <= 1
+    with pytest.raises(sg.SgError):
+        sg.sg_set_apply_fp64(prob, 3)
+
+
 def test_gram_schmidt_passes_rejected(gpu):
     import paper_2310_14649_gb300 as sg
     c = CONFIGS["poisson32_L2_p2"]
