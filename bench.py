@@ -81,6 +81,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def bf16_sustained():
+    """Sustained dense BF16 rate (TFLOP/s) for kernels timed inside a step."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 1700.0, "fallback"
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -317,8 +326,9 @@ def extra_measurements(sg, torch, prob, stream):
                       "fp64_ms": round(m_l64, 3), "fp64_outer_it": i_l64["outer_it"],
                       "network_ms_per_apply": round(m_net, 4),
                       "network_tflops": round(flops / m_net / 1e9, 1),
-                      "network_bound": "tensor (BF16 mma.sync)",
-                      "network_frac_of_bf16_sustained": round(flops / m_net / 1e9 / 1699.7, 4)}
+                      "network_bound": "tensor (tcgen05 forward, BF16 operands, FP32 in tensor memory)",
+                      "network_frac_of_bf16_sustained": round(flops / m_net / 1e9 / bf16_sustained()[0], 4),
+                      "bf16_sustained_source": bf16_sustained()[1]}
     return out
 
 
