@@ -130,7 +130,7 @@ struct Profiler {
 // families: which = 0 fine FP32, 1 coarse FP32, 2 fine FP64, 3 coarse FP64.
 constexpr int kJitFamilies = 4;
 constexpr int kJitMaxP = 128;
-constexpr int kJitGeneratorVersion = 8;  // bump when the generated code changes
+constexpr int kJitGeneratorVersion = 9;  // bump when the generated code changes
 constexpr int64_t kJitMaxT = 40000;
 struct JitConfig {
   int rows = 1;        // rows per thread (2: paired FP32 FMA)

@@ -153,7 +153,11 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
   const char* ty = R == 2 ? "float2" : T;
   std::ostringstream body;
   std::string staged_table;
-  for (int g = 0; g < NG; ++g) {
+  // slot groups alone run the same code from different first slots: one
+  // body with the slot offset taken from the group index (separate unrolled
+  // bodies per group multiply the instruction footprint)
+  const bool slot_only = !csplit && HO == 1 && HI == 1 && SG > 1;
+  for (int g = 0; g < (slot_only ? 1 : NG); ++g) {
     const int ho = g / (HI * SG), hi = (g / SG) % HI, sgi = g % SG;
     const int lo = cut[ho], up = cut[ho + 1], blo = icut[hi], bup = icut[hi + 1];
     auto in_grp = [&](int a, int b) { return a >= lo && a < up && b >= blo && b < bup; };
@@ -170,11 +174,15 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
           }
       if (any) ks.push_back(k);
     }
-    body << "  " << (g ? "else " : "") << "if (grp == " << g << ") {\n";
+    if (slot_only)
+      body << "  {\n";
+    else
+      body << "  " << (g ? "else " : "") << "if (grp == " << g << ") {\n";
     for (int a = lo; a < up; ++a)
       if (has_a[a]) body << "    " << ty << " y" << a << (R == 2 ? " = make_float2(0.f, 0.f);\n" : (fp64 ? " = 0.0;\n" : " = 0.f;\n"));
     body << "#pragma unroll 1\n"
-            "    for (int s = " << sgi << "; s < S; s += " << SG << ") {\n"
+            "    for (int s = " << (slot_only ? std::string("grp") : std::to_string(sgi)) << "; s < S; s += " << SG
+         << ") {\n"
             "      const " << Ts << "* xp0 = X + col[(long long)s * ldr + rr];\n";
     if (R == 2) body << "      const float* xp1 = X + col[(long long)s * ldr + rr + 1];\n";
     for (int b = 0; b < P; ++b) {
@@ -549,7 +557,9 @@ sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const double
 // staged shapes are available through sg_apply_config but not tuned.  Groups
 // of one warp (every slot its own group) measured slower everywhere except
 // the fine FP64 family, where two output by two slot groups of one warp
-// each beat the 4-warp shapes by 10 % at 256^2 / P = 35.
+// each beat the 4-warp shapes by 10 % at 256^2 / P = 35.  Slot groups alone
+// share one generated body (0.0526 -> 0.0487 ms for the coarse family's two
+// slot groups at 127^2 coarse rows, P = 35).
 static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
   struct S7 {
     int r, g, i, s, pf, st, mb = 1, cg = 1, w = 4;
