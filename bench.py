@@ -197,6 +197,14 @@ def oracle_sample(cfg, iters=2, repeats=1):
     return per_it * need * 1e3, per_it, need
 
 
+def workload_config(c, P, K, n, world):
+    """The config object of the bench line (both arms)."""
+    return {"workload": WORKLOAD, "N": c["N"], "L": c["L"], "p": c["p"], "q": c["q"], "P": P, "K": K,
+            "unknowns": n * P, "ras_boxes": "%dx%d" % (c["sx"], c["sy"]), "overlap": c["overlap"],
+            "parallelism": "replicas" if world > 1 else "single", "coarse_inner_rtol": INNER_RTOL,
+            "l2": "inputs larger than L2 (values 0.82 GB), no flush"}
+
+
 def run_reference(args):
     from sg_inputs import CONFIGS
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -227,7 +235,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 3),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": workload_config(c, prob.P, prob.K, prob.n, world),
             "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -472,10 +480,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_all, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": c["N"], "L": c["L"], "p": c["p"], "q": c["q"], "P": P, "K": K,
-                   "unknowns": n * P, "ras_boxes": "%dx%d" % (c["sx"], c["sy"]), "overlap": c["overlap"],
-                   "parallelism": "replicas" if world > 1 else "single", "coarse_inner_rtol": INNER_RTOL,
-                   "l2": "inputs larger than L2 (values 0.82 GB), no flush"},
+        "config": workload_config(c, P, K, n, world),
         "solve": {"outer_it": infos[-1]["outer_it"], "inner_it": infos[-1]["inner_it"],
                   "ir_steps": infos[-1]["ir_steps"], "relres": infos[-1]["relres"],
                   "setup_s": round(t_setup, 3), "precond_setup_s": round(t_pc, 3),
