@@ -45,59 +45,76 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
   const int64_t ldc = c.ldc, lenc = c.lenc;
   const int* jdev = c.dg.iv;
 
-  const int64_t k0 = launch_count();
   cudaStreamCaptureStatus cs;
   cudaGraph_t g;
   SG_CUDA(cudaStreamGetCaptureInfo(s1, &cs, nullptr, &g, nullptr, nullptr, nullptr));
-  cudaGraphConditionalHandle hout, hin;
+  cudaGraphConditionalHandle hout;
   SG_CUDA(cudaGraphConditionalHandleCreate(&hout, g, 0, 0));
+  // one Arnoldi step (the WHILE body of a cycle), recorded on s3
+  auto arnoldi_step = [&](cudaGraph_t body_in, cudaGraphConditionalHandle hin) -> sg_status {
+    SG_CUDA(cudaStreamBeginCaptureToGraph(s3, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    SG_TRY(dg_copy_vj<T>(V, lenc, ldc, c.aw.b[0], L0.ld, pc.co.nc, c.pr->P, c.dg, s3));
+    SG_TRY(c.coarse_pc_from_b0(tmp, s3));
+    SG_TRY(dg_store_j<T>(tmp, Zc, lenc, lenc, c.dg, s3));
+    SG_TRY(c.apply_raw(tmp, w, nullptr, s3));
+    SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h1, part, cnt, jdev, m, s3));
+    if (W.passes == 1) {
+      SG_TRY(dg_axpy_norm<T>(V, lenc, h1, w, lenc, W.s.scal, part, cnt, jdev, s3));
+    } else {
+      SG_TRY(dg_axpy_norm<T>(V, lenc, h1, w, lenc, nullptr, part, cnt, jdev, s3));
+      SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h2, part, cnt, jdev, m, s3));
+      SG_TRY(dg_axpy_norm<T>(V, lenc, h2, w, lenc, W.s.scal, part, cnt, jdev, s3));
+    }
+    SG_TRY(dg_givens(c.dg, W.s, m, hin, s3));
+    SG_TRY(dg_scale_next<T>(w, V, lenc, lenc, c.dg, W.s.scal + 1, s3));
+    SG_CUDA(cudaStreamEndCapture(s3, &body_in));
+    return SG_OK;
+  };
+  // one restart cycle from V_0 = r0 with ||r0||^2 in scal[3], recorded on sc
+  // (part of graph gc); n_step receives the kernels of one Arnoldi step
+  auto cycle = [&](cudaStream_t sc, cudaGraph_t gc, int64_t* n_step) -> sg_status {
+    cudaGraphConditionalHandle hin;
+    SG_CUDA(cudaGraphConditionalHandleCreate(&hin, gc, 0, 0));
+    SG_TRY(dg_start(c.dg, W.s, m, W.s.scal + 3, hin, sc));
+    SG_TRY(vec_scale_by<T>(V, V, lenc, W.s.scal + 3, true, sc));
+    cudaGraph_t body_in;
+    SG_TRY(SolverCtx<T>::add_while(sc, hin, &body_in));
+    const int64_t a = launch_count();
+    SG_TRY(arnoldi_step(body_in, hin));
+    *n_step = launch_count() - a;
+    // x += M (V y) = Z y with the stored Z_j = M V_j
+    SG_TRY(dg_backsolve(c.dg, W.s, m, sc));
+    SG_TRY(dg_axpy_multi<T>(Zc, lenc, W.s.y, Ec, lenc, jdev, sc));
+    SG_TRY(dg_end(c.dg, W.s, hout, sc));
+    return SG_OK;
+  };
+
+  const int64_t k0 = launch_count();
+  // e_c = 0, so the first cycle starts from r0 = r_c without an apply
   SG_CUDA(cudaMemsetAsync(Ec, 0, lenc * sizeof(T), s1));
   if (W.passes == 1) SG_CUDA(cudaMemsetAsync(h2, 0, (m + 1) * sizeof(double), s1));
   SG_TRY(vec_norm2<T>(Rc, lenc, W.s.scal + 5, part, cnt, s1));
+  SG_CUDA(cudaMemcpyAsync(V, Rc, lenc * sizeof(T), cudaMemcpyDeviceToDevice, s1));
+  SG_CUDA(cudaMemcpyAsync(W.s.scal + 3, W.s.scal + 5, sizeof(double), cudaMemcpyDeviceToDevice, s1));
   SG_TRY(dg_init(c.dg, W.s.scal + 5, pc.inner_rtol, hout, s1));
   const int64_t k1 = launch_count();
-  int64_t k2 = 0, k3 = 0;
+  int64_t n1 = 0, n2 = 0;
+  SG_TRY(cycle(s1, g, &n1));
+  const int64_t k2 = launch_count();
+  // further cycles (a full cycle without convergence): r0 = r_c - A_c e_c
   cudaGraph_t body_out;
   SG_TRY(SolverCtx<T>::add_while(s1, hout, &body_out));
-  {
-    SG_CUDA(cudaStreamBeginCaptureToGraph(s2, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    // r0 = rc - A_c ec
-    SG_TRY(c.apply_raw(Ec, V, Rc, s2));
-    SG_TRY(vec_norm2<T>(V, lenc, W.s.scal + 3, part, cnt, s2));
-    SG_CUDA(cudaGraphConditionalHandleCreate(&hin, body_out, 0, 0));
-    SG_TRY(dg_start(c.dg, W.s, m, W.s.scal + 3, hin, s2));
-    SG_TRY(vec_scale_by<T>(V, V, lenc, W.s.scal + 3, true, s2));
-    cudaGraph_t body_in;
-    SG_TRY(SolverCtx<T>::add_while(s2, hin, &body_in));
-    k2 = launch_count();
-    {
-      SG_CUDA(cudaStreamBeginCaptureToGraph(s3, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      SG_TRY(dg_copy_vj<T>(V, lenc, ldc, c.aw.b[0], L0.ld, pc.co.nc, c.pr->P, c.dg, s3));
-      SG_TRY(c.coarse_pc_from_b0(tmp, s3));
-      SG_TRY(dg_store_j<T>(tmp, Zc, lenc, lenc, c.dg, s3));
-      SG_TRY(c.apply_raw(tmp, w, nullptr, s3));
-      SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h1, part, cnt, jdev, m, s3));
-      if (W.passes == 1) {
-        SG_TRY(dg_axpy_norm<T>(V, lenc, h1, w, lenc, W.s.scal, part, cnt, jdev, s3));
-      } else {
-        SG_TRY(dg_axpy_norm<T>(V, lenc, h1, w, lenc, nullptr, part, cnt, jdev, s3));
-        SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h2, part, cnt, jdev, m, s3));
-        SG_TRY(dg_axpy_norm<T>(V, lenc, h2, w, lenc, W.s.scal, part, cnt, jdev, s3));
-      }
-      SG_TRY(dg_givens(c.dg, W.s, m, hin, s3));
-      SG_TRY(dg_scale_next<T>(w, V, lenc, lenc, c.dg, W.s.scal + 1, s3));
-      SG_CUDA(cudaStreamEndCapture(s3, &body_in));
-    }
-    k3 = launch_count();
-    // x += M (V y) = Z y with the stored Z_j = M V_j
-    SG_TRY(dg_backsolve(c.dg, W.s, m, s2));
-    SG_TRY(dg_axpy_multi<T>(Zc, lenc, W.s.y, Ec, lenc, jdev, s2));
-    SG_TRY(dg_end(c.dg, W.s, hout, s2));
-    SG_CUDA(cudaStreamEndCapture(s2, &body_out));
-  }
-  const int64_t k4 = launch_count();
-  c.cc_coarse = RegionCounts{k1 - k0, (k2 - k1) + (k4 - k3), k3 - k2};
-  note_launches(-(k4 - k0));  // recorded, not launched
+  SG_CUDA(cudaStreamBeginCaptureToGraph(s2, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  SG_TRY(c.apply_raw(Ec, V, Rc, s2));
+  SG_TRY(vec_norm2<T>(V, lenc, W.s.scal + 3, part, cnt, s2));
+  SG_TRY(cycle(s2, body_out, &n2));
+  SG_CUDA(cudaStreamEndCapture(s2, &body_out));
+  const int64_t k3 = launch_count();
+  // kernels per solve = fixed + cycles x restart + steps x iter, every
+  // solve running the first cycle once
+  const int64_t first = (k2 - k1) - n1, later = (k3 - k2) - n2;
+  c.cc_coarse = RegionCounts{(k1 - k0) + first - later, later, n2};
+  note_launches(-(k3 - k0));  // recorded, not launched
   return SG_OK;
 }
 
