@@ -342,9 +342,11 @@ struct SolverCtx {
   }
   // coarse preconditioner on a block already in the AMG level-0 input:
   // V-cycle, copy out to `out` (coarse ld), Kronecker factor
-  sg_status coarse_pc_from_b0(T* out, cudaStream_t st) {
+  // (with Zs: the result also into slot dg.iv[0] of Zs, slot stride lenc)
+  sg_status coarse_pc_from_b0(T* out, cudaStream_t st, T* Zs = nullptr) {
     SG_TRY(amg_vcycle<T>(pc->amg, aw, pr->P, st, out, ldc));
-    return node_transform<T>(out, ldc, pc->co.nc, pr->P, dp_sel<T>(pc->gkron64, pc->gkron32), st);
+    return node_transform<T>(out, ldc, pc->co.nc, pr->P, dp_sel<T>(pc->gkron64, pc->gkron32), st, Zs, lenc,
+                             Zs ? dg.iv : nullptr);
   }
 
   // adds a WHILE node driven by `h` at the capture point of `st`

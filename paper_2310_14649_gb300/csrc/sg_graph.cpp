@@ -53,9 +53,8 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
   // one Arnoldi step (the WHILE body of a cycle), recorded on s3
   auto arnoldi_step = [&](cudaGraph_t body_in, cudaGraphConditionalHandle hin) -> sg_status {
     SG_CUDA(cudaStreamBeginCaptureToGraph(s3, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    SG_TRY(dg_copy_vj<T>(V, lenc, ldc, c.aw.b[0], L0.ld, pc.co.nc, c.pr->P, c.dg, s3));
-    SG_TRY(c.coarse_pc_from_b0(tmp, s3));
-    SG_TRY(dg_store_j<T>(tmp, Zc, lenc, lenc, c.dg, s3));
+    // the AMG input b_0 holds V_j (written with V_j), Z_j = M V_j
+    SG_TRY(c.coarse_pc_from_b0(tmp, s3, Zc));
     SG_TRY(c.apply_raw(tmp, w, nullptr, s3));
     SG_TRY(dg_mdot<T>(V, lenc, w, lenc, h1, part, cnt, jdev, m, s3));
     if (W.passes == 1) {
@@ -66,7 +65,7 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
       SG_TRY(dg_axpy_norm<T>(V, lenc, h2, w, lenc, W.s.scal, part, cnt, jdev, s3));
     }
     SG_TRY(dg_givens(c.dg, W.s, m, hin, s3));
-    SG_TRY(dg_scale_next<T>(w, V, lenc, lenc, c.dg, W.s.scal + 1, s3));
+    SG_TRY(dg_scale_next<T>(w, V, lenc, lenc, c.dg, W.s.scal + 1, s3, c.aw.b[0], L0.ld, ldc, pc.co.nc));
     SG_CUDA(cudaStreamEndCapture(s3, &body_in));
     return SG_OK;
   };
@@ -77,6 +76,7 @@ sg_status capture_coarse(SolverCtx<T>& c, cudaStream_t s1, cudaStream_t s2, cuda
     SG_CUDA(cudaGraphConditionalHandleCreate(&hin, gc, 0, 0));
     SG_TRY(dg_start(c.dg, W.s, m, W.s.scal + 3, hin, sc));
     SG_TRY(vec_scale_by<T>(V, V, lenc, W.s.scal + 3, true, sc));
+    SG_TRY(dg_copy_vj<T>(V, lenc, ldc, c.aw.b[0], L0.ld, pc.co.nc, c.pr->P, c.dg, sc));  // b_0 = V_0
     cudaGraph_t body_in;
     SG_TRY(SolverCtx<T>::add_while(sc, hin, &body_in));
     const int64_t a = launch_count();

@@ -21,7 +21,10 @@ template <typename T>
 sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld, T* Z, cudaStream_t st,
                     bool transform, Profiler* prof = nullptr);
 template <typename T>
-sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st);
+// in place Z <- M Z per node; with Z2, also into slot *j2 of the array Z2
+// (slot stride stride2, the same leading dimension)
+sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st, T* Z2 = nullptr,
+                         int64_t stride2 = 0, const int* j2 = nullptr);
 template <typename T>
 sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T* out = nullptr, int64_t ldo = 0);
 sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w);
@@ -89,7 +92,10 @@ template <typename T>
 sg_status dg_axpy_multi(const T* V, int64_t stride, const double* coef, T* x, int64_t len, const int* kdev,
                         cudaStream_t st);
 template <typename T>
-sg_status dg_scale_next(const T* w, T* V, int64_t stride, int64_t len, DevGmres d, const double* hn, cudaStream_t st);
+// V_{j+1} = w / h (device j after the Givens step); with dst, also the
+// first n rows of every mode into dst (leading dimension ldd; V's is lds)
+sg_status dg_scale_next(const T* w, T* V, int64_t stride, int64_t len, DevGmres d, const double* hn, cudaStream_t st,
+                        T* dst = nullptr, int64_t ldd = 0, int64_t lds = 0, int64_t n = 0);
 template <typename T>
 sg_status dg_copy_vj(const T* V, int64_t stride, int64_t lds, T* dst, int64_t ldd, int64_t n, int P, DevGmres d,
                      cudaStream_t st);

@@ -429,12 +429,19 @@ __global__ void k_dg_backsolve(DevGmres d, GmresState s, int m) {
 // V_{j} = w / h_{j,j-1} for the device index j (already advanced)
 template <typename T>
 __global__ void k_dg_scale_next(const T* __restrict__ w, T* __restrict__ V, int64_t stride, int64_t len, DevGmres d,
-                                const double* __restrict__ hn) {
+                                const double* __restrict__ hn, T* __restrict__ dst, int64_t ldd, int64_t lds,
+                                int64_t n) {
   const double h = *hn;
   const T sc = T(h != 0.0 ? 1.0 / h : 0.0);
   T* v = V + int64_t(d.iv[0]) * stride;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x)
-    v[e] = w[e] * sc;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < len; e += int64_t(gridDim.x) * blockDim.x) {
+    const T x = w[e] * sc;
+    v[e] = x;
+    if (dst) {
+      const int64_t a = e / lds, r = e - a * lds;
+      if (r < n) dst[a * ldd + r] = x;
+    }
+  }
 }
 
 // mode-major block copy from V_j (device index j) with a change of
@@ -480,8 +487,9 @@ sg_status dg_axpy_multi(const T* V, int64_t stride, const double* coef, T* x, in
 }
 
 template <typename T>
-sg_status dg_scale_next(const T* w, T* V, int64_t stride, int64_t len, DevGmres d, const double* hn, cudaStream_t st) {
-  k_dg_scale_next<T><<<grid_for(len), 256, 0, st>>>(w, V, stride, len, d, hn);
+sg_status dg_scale_next(const T* w, T* V, int64_t stride, int64_t len, DevGmres d, const double* hn, cudaStream_t st,
+                        T* dst, int64_t ldd, int64_t lds, int64_t n) {
+  k_dg_scale_next<T><<<grid_for(len), 256, 0, st>>>(w, V, stride, len, d, hn, dst, ldd, lds > 0 ? lds : 1, n);
   note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
@@ -551,7 +559,8 @@ sg_status ir_decide(const double* rr, const double* nf2, int* iv, double rtol, i
   template sg_status dg_axpy_norm<T>(const T*, int64_t, const double*, T*, int64_t, double*, double*,          \
                                      unsigned*, const int*, cudaStream_t);                                     \
   template sg_status dg_axpy_multi<T>(const T*, int64_t, const double*, T*, int64_t, const int*, cudaStream_t); \
-  template sg_status dg_scale_next<T>(const T*, T*, int64_t, int64_t, DevGmres, const double*, cudaStream_t);   \
+  template sg_status dg_scale_next<T>(const T*, T*, int64_t, int64_t, DevGmres, const double*, cudaStream_t, T*, \
+                                      int64_t, int64_t, int64_t);                                                \
   template sg_status dg_copy_vj<T>(const T*, int64_t, int64_t, T*, int64_t, int64_t, int, DevGmres, cudaStream_t); \
   template sg_status dg_store_j<T>(const T*, T*, int64_t, int64_t, DevGmres, cudaStream_t);
 INST_DG(float)

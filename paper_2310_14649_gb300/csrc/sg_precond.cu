@@ -429,7 +429,8 @@ __global__ void k_ras_local_tc(const float* __restrict__ R, int64_t ld, float* _
 // In-place per-node transform z_r <- M z_r with a P x P matrix M (the
 // stochastic factor omega G~^{-1}).  128 nodes per CTA staged in shared memory.
 template <typename T>
-__global__ void k_node_transform(T* __restrict__ Z, int64_t ld, int64_t n, int P, const T* __restrict__ M) {
+__global__ void k_node_transform(T* __restrict__ Z, int64_t ld, int64_t n, int P, const T* __restrict__ M,
+                                 T* __restrict__ Z2, int64_t stride2, const int* __restrict__ j2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ms = reinterpret_cast<T*>(smem_raw);  // P x P
   T* zs = Ms + size_t(P) * P;               // P x 128
@@ -439,10 +440,13 @@ __global__ void k_node_transform(T* __restrict__ Z, int64_t ld, int64_t n, int P
   for (int b = 0; b < P; ++b) zs[b * 128 + threadIdx.x] = valid ? Z[int64_t(b) * ld + r] : T(0);
   __syncthreads();
   if (!valid) return;
+  // optional copy into slot j2 (device index) of a vector array, same ld
+  T* z2 = Z2 ? Z2 + int64_t(*j2) * stride2 : nullptr;
   for (int a = 0; a < P; ++a) {
     T acc = T(0);
     for (int b = 0; b < P; ++b) acc += Ms[a * P + b] * zs[b * 128 + threadIdx.x];
     Z[int64_t(a) * ld + r] = acc;
+    if (z2) z2[int64_t(a) * ld + r] = acc;
   }
 }
 
@@ -719,14 +723,15 @@ sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld,
 }
 
 template <typename T>
-sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st) {
+sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st, T* Z2, int64_t stride2,
+                         const int* j2) {
   const size_t smem = (size_t(P) * P + size_t(P) * 128) * sizeof(T);
   static bool attr[2] = {false, false};
   if (!attr[sizeof(T) == 8]) {
     SG_CUDA(cudaFuncSetAttribute(k_node_transform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr[sizeof(T) == 8] = true;
   }
-  k_node_transform<T><<<unsigned((n + 127) / 128), 128, smem, st>>>(Z, ld, n, P, M); note_launch();
+  k_node_transform<T><<<unsigned((n + 127) / 128), 128, smem, st>>>(Z, ld, n, P, M, Z2, stride2, j2); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
@@ -912,7 +917,7 @@ sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w) {
                              cudaStream_t);                                                               \
   template sg_status ras_apply<T>(const Precond&, int64_t, int, const T*, int64_t, T*, cudaStream_t, bool,        \
                                   Profiler*);                                                                      \
-  template sg_status node_transform<T>(T*, int64_t, int64_t, int, const T*, cudaStream_t);                \
+  template sg_status node_transform<T>(T*, int64_t, int64_t, int, const T*, cudaStream_t, T*, int64_t, const int*);                \
   template sg_status amg_vcycle<T>(const AmgHier&, AmgWork<T>&, int, cudaStream_t, T*, int64_t);
 INST(float)
 INST(double)
