@@ -58,6 +58,9 @@ def test_argument_errors_without_gpu(libsg):
     assert st == -1 and b"N must be" in libsg.sg_last_error()
     assert libsg.sg_apply(None, 0, None, 0, None, 0, None) == -1
     assert libsg.sg_destroy(None) == 0
+    assert libsg.sg_set_apply_fp64(None, 0) == -1
+    assert libsg.sg_apply_fp64_info(None, None, None, None) == -1
+    assert libsg.sg_apply_config(None, 0, 1, 1, 1, 1, 8, 1, 0, 1, 4) == -1
 
 
 def test_cnn_param_count_without_gpu(libsg):
