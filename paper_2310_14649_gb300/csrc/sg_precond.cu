@@ -450,6 +450,51 @@ __global__ void k_node_transform(T* __restrict__ Z, int64_t ld, int64_t n, int P
   }
 }
 
+// FP32 node transform with the node's P inputs in registers (PM >= P, a
+// compile-time bound): M^T staged in shared memory as [b][a] rows padded to
+// a multiple of 4, so one 16-byte load feeds four outputs; a smem load per
+// four FMAs instead of two per FMA.
+template <int PM>
+__global__ void __launch_bounds__(128) k_node_transform_reg(float* __restrict__ Z, int64_t ld, int64_t n, int P,
+                                                            const float* __restrict__ M, float* __restrict__ Z2,
+                                                            int64_t stride2, const int* __restrict__ j2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* MT = reinterpret_cast<float*>(smem_raw);  // [P][P4]
+  const int P4 = (P + 3) & ~3;
+  for (int e = threadIdx.x; e < P * P4; e += blockDim.x) {
+    const int b = e / P4, a = e - b * P4;
+    MT[e] = a < P ? M[a * P + b] : 0.f;
+  }
+  const int64_t r = int64_t(blockIdx.x) * 128 + threadIdx.x;
+  const bool valid = r < n;
+  float z[PM];
+#pragma unroll
+  for (int b = 0; b < PM; ++b) z[b] = (valid && b < P) ? Z[int64_t(b) * ld + r] : 0.f;
+  __syncthreads();
+  if (!valid) return;
+  float* z2 = Z2 ? Z2 + int64_t(*j2) * stride2 : nullptr;
+  for (int a = 0; a < P; a += 4) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < PM; ++b) {
+      if (b < P) {
+        const float4 m = *reinterpret_cast<const float4*>(MT + b * P4 + a);
+        acc.x = fmaf(m.x, z[b], acc.x);
+        acc.y = fmaf(m.y, z[b], acc.y);
+        acc.z = fmaf(m.z, z[b], acc.z);
+        acc.w = fmaf(m.w, z[b], acc.w);
+      }
+    }
+    const float o[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (a + i < P) {
+        Z[int64_t(a + i) * ld + r] = o[i];
+        if (z2) z2[int64_t(a + i) * ld + r] = o[i];
+      }
+  }
+}
+
 // Coarse ELL values of all K terms from the fine ELL values by the RAP plan.
 __global__ void k_coarse_values(const double* __restrict__ fine, int64_t fine_kstride, const int* __restrict__ rp,
                                 const int64_t* __restrict__ src, const double* __restrict__ w, int64_t npos,
@@ -722,9 +767,27 @@ sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld,
   return SG_OK;
 }
 
+template <int PM>
+static sg_status node_transform_reg(float* Z, int64_t ld, int64_t n, int P, const float* M, cudaStream_t st, float* Z2,
+                                    int64_t stride2, const int* j2) {
+  const size_t smem = size_t(P) * ((P + 3) & ~3) * sizeof(float);
+  k_node_transform_reg<PM><<<unsigned((n + 127) / 128), 128, smem, st>>>(Z, ld, n, P, M, Z2, stride2, j2);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
 template <typename T>
 sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st, T* Z2, int64_t stride2,
                          const int* j2) {
+  if (sizeof(T) == 4 && P <= 64) {
+    float* Zf = reinterpret_cast<float*>(Z);
+    const float* Mf = reinterpret_cast<const float*>(M);
+    float* Z2f = reinterpret_cast<float*>(Z2);
+    if (P <= 16) return node_transform_reg<16>(Zf, ld, n, P, Mf, st, Z2f, stride2, j2);
+    if (P <= 40) return node_transform_reg<40>(Zf, ld, n, P, Mf, st, Z2f, stride2, j2);
+    return node_transform_reg<64>(Zf, ld, n, P, Mf, st, Z2f, stride2, j2);
+  }
   const size_t smem = (size_t(P) * P + size_t(P) * 128) * sizeof(T);
   static bool attr[2] = {false, false};
   if (!attr[sizeof(T) == 8]) {
