@@ -529,16 +529,23 @@ __global__ void k_frob(const double* __restrict__ V, int64_t kstride, int K, dou
 
 // CSR SpMM over P columns (mode-major blocks):
 //   op 0: Y = A X;  op 1: Y += A X;  op 2: Y = B - A X
+// G lanes (a power of two <= 32) share each row's entries and meet by
+// shuffles; rows per 128-thread block = 128 / G.
 template <typename T>
-__global__ void k_spmm(int64_t nrows, const int* __restrict__ rp, const int* __restrict__ ci,
-                       const T* __restrict__ v, const T* __restrict__ X, int64_t ldx, const T* __restrict__ B,
-                       int64_t ldb, T* __restrict__ Y, int64_t ldy, int op) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__global__ void __launch_bounds__(128) k_spmm(int64_t nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                              const T* __restrict__ v, const T* __restrict__ X, int64_t ldx,
+                                              const T* __restrict__ B, int64_t ldb, T* __restrict__ Y, int64_t ldy,
+                                              int op, int G) {
+  const int grp = threadIdx.x / G, lane = threadIdx.x - grp * G;
+  const int64_t i = blockIdx.x * int64_t(128 / G) + grp;
   const int a = blockIdx.y;
-  if (i >= nrows) return;
+  const bool live = i < nrows;
   const T* x = X + int64_t(a) * ldx;
   T acc = T(0);
-  for (int t = rp[i]; t < rp[i + 1]; ++t) acc += v[t] * x[ci[t]];
+  if (live)
+    for (int t = rp[i] + lane; t < rp[i + 1]; t += G) acc += v[t] * x[ci[t]];
+  for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (!live || lane != 0) return;
   T* y = Y + int64_t(a) * ldy + i;
   if (op == 0)
     *y = acc;
@@ -675,9 +682,15 @@ template <typename T>
 sg_status spmm(const DevCsr& A, const T* X, int64_t ldx, const T* B, int64_t ldb, T* Y, int64_t ldy, int P,
                int op, cudaStream_t st) {
   if (A.n == 0) return SG_OK;
-  dim3 grid(unsigned((A.n + 127) / 128), unsigned(P));
+  // about two entries per lane on an average row, while rows x columns x
+  // lanes stays within about two waves of resident threads (152 SMs x 2048)
+  const int64_t avg = (A.nnz + A.n - 1) / A.n;
+  int G = 1;
+  while (G < 32 && 2 * G < avg && A.n * int64_t(P) * (2 * G) <= 2 * 152 * 2048) G <<= 1;
+  const int rows = 128 / G;
+  dim3 grid(unsigned((A.n + rows - 1) / rows), unsigned(P));
   k_spmm<T><<<grid, 128, 0, st>>>(A.n, A.rowptr.as<int>(), A.col.as<int>(), dv<T>(A.v64, A.v32), X, ldx, B, ldb, Y,
-                                  ldy, op); note_launch();
+                                  ldy, op, G); note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
 }
