@@ -436,6 +436,26 @@ sg_status sg_train_precond(sg_problem* prob, const sg_train_opts* opts, sg_train
  * omega <= 0 estimates omega_cnn). */
 sg_status sg_precond_set_smoother(sg_problem* prob, int smoother, double omega, void* stream);
 
+/* Saves the learned smoother (method statement; no paper counterpart):
+ * its network weights, its damping omega_cnn and whether it is the selected
+ * smoother, into the caller's host buffer buf of *bytes bytes.  With
+ * buf = NULL only *bytes (the size needed) is written.  The format is a
+ * fixed 32-byte header (magic "SGLSMTH", version 1, parameter count,
+ * omega_cnn, selection flag) followed by the FP32 weights in the order of
+ * sg_cnn_set_weights.  Synchronous.
+ * Errors: SG_ERR_ARG (NULL handle or bytes, no weights set, buffer too
+ * small). */
+sg_status sg_precond_save(const sg_problem* prob, void* buf, int64_t* bytes);
+
+/* Restores a smoother saved by sg_precond_save into any problem (the
+ * network does not depend on the mesh size or P): the weights, and, when
+ * this problem has a preconditioner set up and the smoother was selected at
+ * save time, the learned smoother is selected with the saved damping (or a
+ * new estimate when none was saved).  Synchronous.
+ * Errors: SG_ERR_ARG (NULL argument, wrong magic or version, a parameter
+ * count or size that does not match this build's network, bad damping). */
+sg_status sg_precond_load(sg_problem* prob, const void* buf, int64_t bytes);
+
 /* ------------------------------------------------------------------------
  * Graph-captured and batched solves.  sg_batch_create records, for every
  * problem, the whole solve of sg_solve (mode 1: the refinement loop with

@@ -16,7 +16,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_residual", "sg_precond_setup", "sg_precond_info", "sg_get_partition",
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel", "sg_set_apply_fp64",
-           "sg_apply_fp64_info",
+           "sg_apply_fp64_info", "sg_precond_save", "sg_precond_load",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
@@ -253,6 +253,21 @@ def sg_set_apply_fp64(prob, mode):
     """FP64 applies over assembled P x P edge blocks: 0 auto (memory
     permitting), 1 never, 2 always."""
     call("sg_set_apply_fp64", prob.handle, mode)
+
+
+def sg_precond_save(prob):
+    """The learned smoother (weights, damping, selection) as bytes."""
+    n = ctypes.c_int64()
+    call("sg_precond_save", prob.handle, None, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value)
+    call("sg_precond_save", prob.handle, buf, ctypes.byref(n))
+    return buf.raw[:n.value]
+
+
+def sg_precond_load(prob, data):
+    """Restores what sg_precond_save returned."""
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    call("sg_precond_load", prob.handle, buf, len(data))
 
 
 def sg_apply_fp64_info(prob):

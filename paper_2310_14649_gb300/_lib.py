@@ -102,6 +102,8 @@ SIGNATURES = {
     "sg_mdot_noalloc": [ctypes.c_int, vp, i64, ctypes.c_int, vp, i64, vp, vp],
     "sg_set_apply_kernel": [vp, ctypes.c_int],
     "sg_set_apply_fp64": [vp, ctypes.c_int],
+    "sg_precond_save": [vp, vp, P_i64],
+    "sg_precond_load": [vp, vp, ctypes.c_int64],
     "sg_apply_fp64_info": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), P_i64],
     "sg_apply_config": [vp] + [ctypes.c_int] * 10,
     "sg_apply_autotune": [vp, ctypes.c_int, ctypes.c_int, P_f64],

@@ -173,6 +173,65 @@ sg_status sg_precond_set_smoother(sg_problem* pr, int smoother, double omega, vo
   return learned_smoother_enable(pr, omega, static_cast<cudaStream_t>(stream));
 }
 
+// Saved learned smoother: a fixed header, then the flat FP32 weights in the
+// order of sg_cnn_set_weights.
+namespace {
+struct SavedSmoother {
+  char magic[8];      // "SGLSMTH" + NUL
+  int32_t version;    // 1
+  int32_t nparam;     // sg_cnn_param_count()
+  double omega_cnn;   // damping of the learned smoother, 0 = not known
+  int32_t selected;   // 1: the learned smoother was the selected one
+  int32_t reserved;
+};
+constexpr char kSavedMagic[8] = {'S', 'G', 'L', 'S', 'M', 'T', 'H', '\0'};
+}  // namespace
+
+sg_status sg_precond_save(const sg_problem* pr, void* buf, int64_t* bytes) {
+  SG_ARG(pr && bytes, "sg_precond_save: NULL argument");
+  SG_ARG(pr->cnn && pr->cnn->trained, "sg_precond_save: the learned smoother has no weights");
+  const int64_t np = cnn_param_count();
+  const int64_t need = int64_t(sizeof(SavedSmoother)) + np * int64_t(sizeof(float));
+  if (!buf) {
+    *bytes = need;
+    return SG_OK;
+  }
+  SG_ARG(*bytes >= need, "sg_precond_save: buffer smaller than the size asked with buf = NULL");
+  SavedSmoother h{};
+  std::memcpy(h.magic, kSavedMagic, sizeof h.magic);
+  h.version = 1;
+  h.nparam = int32_t(np);
+  const Precond* pc = pr->solver ? &precond_of(const_cast<sg_problem*>(pr)) : nullptr;
+  h.omega_cnn = pc ? pc->omega_cnn : 0.0;
+  h.selected = pc && pc->smoother == 1 ? 1 : 0;
+  if (!h.selected) h.omega_cnn = 0.0;
+  std::vector<float> w(np);
+  SG_TRY(pr->cnn->get_weights(w.data(), false, nullptr));
+  std::memcpy(buf, &h, sizeof h);
+  std::memcpy(static_cast<char*>(buf) + sizeof h, w.data(), np * sizeof(float));
+  *bytes = need;
+  return SG_OK;
+}
+
+sg_status sg_precond_load(sg_problem* pr, const void* buf, int64_t bytes) {
+  SG_ARG(pr && buf, "sg_precond_load: NULL argument");
+  SG_ARG(bytes >= int64_t(sizeof(SavedSmoother)), "sg_precond_load: buffer shorter than the header");
+  SavedSmoother h;
+  std::memcpy(&h, buf, sizeof h);
+  SG_ARG(std::memcmp(h.magic, kSavedMagic, sizeof h.magic) == 0 && h.version == 1,
+         "sg_precond_load: not a saved learned smoother (magic or version)");
+  const int64_t np = cnn_param_count();
+  SG_ARG(h.nparam == np && bytes >= int64_t(sizeof h) + np * int64_t(sizeof(float)),
+         "sg_precond_load: parameter count or size does not match this build's network");
+  SG_ARG(!(h.omega_cnn < 0.0) && std::isfinite(h.omega_cnn), "sg_precond_load: bad damping");
+  std::vector<float> w(np);
+  std::memcpy(w.data(), static_cast<const char*>(buf) + sizeof h, np * sizeof(float));
+  SG_TRY(sg_cnn_set_weights(pr, w.data(), np, nullptr));
+  // with a preconditioner set up, the saved selection and damping return
+  if (h.selected && pr->solver && precond_of(pr).ready) return sg_precond_set_smoother(pr, 1, h.omega_cnn, nullptr);
+  return SG_OK;
+}
+
 sg_status sg_train_precond(sg_problem* pr, const sg_train_opts* o, sg_train_info* info, void* stream) {
   SG_ARG(pr && o, "sg_train_precond: NULL argument");
   SG_ARG(pr->solver, "sg_train_precond: call sg_precond_setup first");

@@ -59,6 +59,9 @@ def test_argument_errors_without_gpu(libsg):
     assert libsg.sg_apply(None, 0, None, 0, None, 0, None) == -1
     assert libsg.sg_destroy(None) == 0
     assert libsg.sg_set_apply_fp64(None, 0) == -1
+    n = ctypes.c_int64(0)
+    assert libsg.sg_precond_save(None, None, ctypes.byref(n)) == -1
+    assert libsg.sg_precond_load(None, b"x" * 64, 64) == -1
     assert libsg.sg_apply_fp64_info(None, None, None, None) == -1
     assert libsg.sg_apply_config(None, 0, 1, 1, 1, 1, 8, 1, 0, 1, 4) == -1
 

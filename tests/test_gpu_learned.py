@@ -123,3 +123,45 @@ def test_learned_smoother_needs_weights(gpu):
     assert e.value.status == -1
     with pytest.raises(sg.SgError):
         sg.sg_precond_setup(prob, 2, 2, 1, smoother=1)
+
+
+def test_save_and_load_learned_smoother(gpu):
+    """A saved learned smoother restores, in a second problem, the same
+    weights, the same selection and damping (the smoother operators agree
+    bit for bit); a problem without a preconditioner takes the weights
+    only; a corrupted or truncated buffer is refused."""
+    import struct
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, c = setup()
+    sg.sg_cnn_init(prob, seed=3)
+    sg.sg_precond_set_smoother(prob, 1, omega=0.37)
+    data = sg.sg_precond_save(prob)
+    npar = sg.sg_cnn_param_count()
+    assert len(data) == 32 + 4 * npar and data[:7] == b"SGLSMTH"
+    assert struct.unpack_from("<iid", data, 8) == (1, npar, 0.37)
+    prob2, _ = setup()
+    sg.sg_precond_load(prob2, data)
+    assert np.array_equal(sg.sg_cnn_get_weights(prob2), sg.sg_cnn_get_weights(prob))
+    R = torch.from_numpy(np.ascontiguousarray(galerkin_block(prob))).cuda()
+    Z1, Z2 = torch.zeros_like(R), torch.zeros_like(R)
+    sg.sg_precond_apply(prob, sg.PC_SMOOTH, R, Z1)
+    sg.sg_precond_apply(prob2, sg.PC_SMOOTH, R, Z2)
+    torch.cuda.synchronize()
+    assert torch.equal(Z1, Z2)
+    # weights only, then the learned smoother selectable by hand
+    prob3 = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
+    sg.sg_precond_load(prob3, data)
+    assert np.array_equal(sg.sg_cnn_get_weights(prob3), sg.sg_cnn_get_weights(prob))
+    bad = bytearray(data)
+    bad[0] ^= 1
+    for b in (bytes(bad), data[:100], data[:20]):
+        with pytest.raises(sg.SgError) as e:
+            sg.sg_precond_load(prob2, b)
+        assert e.value.status == -1
+
+
+def galerkin_block(prob):
+    """A seeded FP32 residual block [P, n]."""
+    from sg_inputs import random_block
+    return random_block(prob.n, prob.P, seed=91).T.astype(np.float32)
