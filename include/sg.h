@@ -325,6 +325,13 @@ typedef struct {
 sg_status sg_solve(sg_problem* prob, const double* F_dev, int64_t ldf, double* X_dev, int64_t ldx,
                    const sg_solve_opts* opts, sg_solve_info* info, void* stream);
 
+/* Newton iteration for the nonlinear stochastic Poisson problem of Sec. 2.2
+ * (Eqs. NLP_StrongPDE, stonlp_system; stop at a relative update of
+ * tol_update).  Not built in this library: after the argument checks
+ * (SG_ERR_ARG) it returns SG_ERR_UNSUPPORTED and leaves X unchanged. */
+sg_status sg_newton(sg_problem* prob, double* X_dev, int64_t ldx, double tol_update, int max_newton,
+                    const sg_solve_opts* opts, sg_solve_info* info, void* stream);
+
 /* ------------------------------------------------------------------------
  * Learned smoother.  The method statement replaces the mean-based local
  * solve (I (x) A_0)^{-1} inside the smoother by a small convolutional
