@@ -24,6 +24,10 @@ coarse     2h interpolation R_0^T and the Galerkin coarse operator (Sec. 3,
            Eq. coarse)
 amg        smoothed-aggregation hierarchy and V-cycle (the AMG of Sec. 3)
 twolevel   multiplicative two-level preconditioner (Sec. 3, Eq. RAS_2L)
+nonlinear  the nonlinear problem (Sec. 2.2, Eqs. NLP_StrongPDE,
+           stonlp_system, AjkTkl): fourfold products t_ijkl, the linearised
+           operator A + T(U) and the Picard iteration; the deterministic
+           problem for collocation pins
 cnn        FP64 convolutional smoother forward/backward (not in the paper:
            parity unpinned against the paper, gradients pinned by
            central differences)
