@@ -104,6 +104,19 @@ sg_status sg_get_multi_indices(const sg_problem* prob, int32_t* out, int which);
  * value num / sqrt(k! a! b!)).  num or g may be NULL. */
 sg_status sg_get_triples(const sg_problem* prob, int32_t* kab, int64_t* num, double* g);
 
+/* Fourfold products <psi_i psi_j psi_k psi_l> != 0 of the nonlinear problem
+ * (Sec. 2.2, the t_ijkl of Eq. stonlp_system): i over the input set
+ * (degree q), j, k, l over the output set (degree p), ordered by i, j, k, l
+ * in the multi-index order of sg_get_multi_indices.  Host-only: needs no
+ * handle and no GPU.  Call with ijkl = num = t = NULL to get *count; then
+ * with *count = the capacity: ijkl (host count x 4), num (unnormalised
+ * integer prod over dimensions of <He He He He>) and t (orthonormal value
+ * num / sqrt(i! j! k! l!)), each optional; *count receives the number.
+ * Errors: SG_ERR_ARG (NULL count; L outside 1..12, p outside 0..8, q
+ * outside 0..16; capacity too small), SG_ERR_UNSUPPORTED (an integer beyond
+ * 64 bits). */
+sg_status sg_fourfold_products(int L, int p, int q, int64_t* count, int32_t* ijkl, int64_t* num, double* t);
+
 /* Shared CSR pattern on the host: rowptr n+1, colidx nnzA, columns ascending. */
 sg_status sg_get_csr(const sg_problem* prob, int32_t* rowptr, int32_t* colidx);
 

@@ -16,7 +16,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_residual", "sg_precond_setup", "sg_precond_info", "sg_get_partition",
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel", "sg_set_apply_fp64",
-           "sg_apply_fp64_info", "sg_precond_save", "sg_precond_load",
+           "sg_apply_fp64_info", "sg_precond_save", "sg_precond_load", "sg_fourfold_products",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
@@ -268,6 +268,19 @@ def sg_precond_load(prob, data):
     """Restores what sg_precond_save returned."""
     buf = ctypes.create_string_buffer(bytes(data), len(data))
     call("sg_precond_load", prob.handle, buf, len(data))
+
+
+def sg_fourfold_products(L, p, q):
+    """Nonzero <psi_i psi_j psi_k psi_l> (host-only): (ijkl int32 [T4, 4],
+    num int64 [T4], t float64 [T4])."""
+    n = ctypes.c_int64(0)
+    call("sg_fourfold_products", L, p, q, ctypes.byref(n), None, None, None)
+    ijkl = np.zeros((n.value, 4), dtype=np.int32)
+    num = np.zeros(n.value, dtype=np.int64)
+    t = np.zeros(n.value, dtype=np.float64)
+    call("sg_fourfold_products", L, p, q, ctypes.byref(n), _lib.ptr(ijkl, ctypes.c_int32),
+         _lib.ptr(num, ctypes.c_int64), _lib.ptr(t, ctypes.c_double))
+    return ijkl, num, t
 
 
 def sg_apply_fp64_info(prob):

@@ -236,3 +236,105 @@ sg_status build_host(sg_problem* pr, const sg_kl_desc* kl) {
 }
 
 }  // namespace sg
+
+// ---------------------------------------------------------------------------
+// Fourfold products of the nonlinear problem (Sec. 2.2, t_ijkl of Eq.
+// stonlp_system).  1D: He_a He_b = sum_m (<He_a He_b He_m> / m!) He_m, so
+// <He_a He_b He_c He_d> = sum_m (<He_a He_b He_m> / m!) <He_m He_c He_d>;
+// every factor is an integer.  Multi-dimensional values are products over
+// the dimensions.  Integers are formed in 128 bits and must fit 64.
+// ---------------------------------------------------------------------------
+namespace {
+
+using i128 = __int128;
+
+i128 fact128(int v) {
+  i128 f = 1;
+  for (int i = 2; i <= v; ++i) f *= i;
+  return f;
+}
+
+// <He_a He_b He_c> with a = y + z, b = x + z, c = x + y: a! b! c! / (x! y! z!)
+i128 he_triple128(int a, int b, int c) {
+  if ((a + b + c) & 1) return 0;
+  const int s = (a + b + c) / 2;
+  if (s < a || s < b || s < c) return 0;
+  return fact128(a) * fact128(b) * fact128(c) / (fact128(s - a) * fact128(s - b) * fact128(s - c));
+}
+
+const i128 kI64Max = i128(INT64_MAX);
+
+}  // namespace
+
+extern "C" sg_status sg_fourfold_products(int L, int p, int q, int64_t* count, int32_t* ijkl, int64_t* num,
+                                          double* t) {
+  using sg::set_error;
+  SG_ARG(count, "sg_fourfold_products: NULL count");
+  SG_ARG(L >= 1 && L <= 12 && p >= 0 && p <= 8 && q >= 0 && q <= 16,
+         "sg_fourfold_products: need 1 <= L <= 12, 0 <= p <= 8, 0 <= q <= 16");
+  // 1D table q1[a][b][c][d], a <= q (input degree), b, c, d <= p
+  const int Q = q + 1, R = p + 1;
+  std::vector<int64_t> q1(size_t(Q) * R * R * R, 0);
+  for (int a = 0; a <= q; ++a)
+    for (int b = 0; b <= p; ++b)
+      for (int c = 0; c <= p; ++c)
+        for (int d = 0; d <= p; ++d) {
+          i128 tot = 0;
+          for (int m = 0; m <= a + b; ++m) {
+            const i128 tab = he_triple128(a, b, m);
+            if (tab == 0) continue;
+            tot += tab / fact128(m) * he_triple128(m, c, d);
+          }
+          if (tot > kI64Max || tot < -kI64Max) {
+            set_error("sg_fourfold_products: a 1D fourfold moment exceeds 64 bits");
+            return SG_ERR_UNSUPPORTED;
+          }
+          q1[((size_t(a) * R + b) * R + c) * R + d] = int64_t(tot);
+        }
+  const std::vector<int32_t> in = sg::multi_indices(L, q), out = sg::multi_indices(L, p);
+  const int64_t K = int64_t(in.size()) / L, P = int64_t(out.size()) / L;
+  auto fact_of = [&](const int32_t* al) {
+    double f = 1.0;
+    for (int d = 0; d < L; ++d)
+      for (int v = 2; v <= al[d]; ++v) f *= v;
+    return f;
+  };
+  const bool fill = ijkl || num || t;
+  const int64_t cap = *count;
+  int64_t n = 0;
+  for (int64_t i = 0; i < K; ++i)
+    for (int64_t j = 0; j < P; ++j)
+      for (int64_t k = 0; k < P; ++k)
+        for (int64_t l = 0; l < P; ++l) {
+          i128 v = 1;
+          for (int d = 0; d < L && v != 0; ++d) {
+            const int64_t f = q1[((size_t(in[i * L + d]) * R + out[j * L + d]) * R + out[k * L + d]) * R +
+                                 out[l * L + d]];
+            v *= f;
+            if (v > kI64Max || v < -kI64Max) {
+              set_error("sg_fourfold_products: a fourfold product exceeds 64 bits");
+              return SG_ERR_UNSUPPORTED;
+            }
+          }
+          if (v == 0) continue;
+          if (fill) {
+            if (n >= cap) {
+              set_error("sg_fourfold_products: *count is smaller than the number of products");
+              return SG_ERR_ARG;
+            }
+            if (ijkl) {
+              ijkl[4 * n] = int32_t(i);
+              ijkl[4 * n + 1] = int32_t(j);
+              ijkl[4 * n + 2] = int32_t(k);
+              ijkl[4 * n + 3] = int32_t(l);
+            }
+            if (num) num[n] = int64_t(v);
+            if (t)
+              t[n] = double(int64_t(v)) / std::sqrt(fact_of(&in[i * L]) * fact_of(&out[j * L]) *
+                                                    fact_of(&out[k * L]) * fact_of(&out[l * L]));
+          }
+          ++n;
+        }
+  *count = n;
+  return SG_OK;
+}

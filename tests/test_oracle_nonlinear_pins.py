@@ -114,3 +114,48 @@ def test_deterministic_reading_converges_to_the_kirchhoff_solution():
     assert errs[0] < 1e-3
     for a, b in zip(errs, errs[1:]):
         assert 3.5 <= a / b <= 4.5
+
+
+@pytest.fixture(scope="module")
+def built():
+    """The library, built in tree if needed (the table needs no GPU)."""
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("L,p,q", [(1, 4, 8), (2, 2, 4), (3, 2, 3), (4, 3, 6)])
+def test_library_fourfold_products_match_the_oracle(built, L, p, q):
+    """The library's host-only table of fourfold products (no GPU needed):
+    the nonzero set and the integers bit-exact, the orthonormal values to
+    rounding, against the oracle's linearisation."""
+    import paper_2310_14649_gb300 as sg
+    ijkl, num, t = sg.sg_fourfold_products(L, p, q)
+    t4 = nonlinear.four_products(L, p, q)
+    nz = np.argwhere(t4 != 0.0)
+    assert np.array_equal(ijkl, nz.astype(np.int32))
+    assert np.allclose(t, t4[tuple(nz.T)], rtol=1e-14, atol=0.0)
+    # integers: the product over dimensions of the 1D moments
+    ins, outs = pce.multi_indices(L, q), pce.multi_indices(L, p)
+    for row, v in zip(ijkl[:: max(1, len(ijkl) // 400)], num[:: max(1, len(ijkl) // 400)]):
+        i, j, k, l = row
+        ref = 1
+        for d in range(L):
+            ref *= nonlinear.hermite_quad_1d(int(ins[i, d]), int(outs[j, d]), int(outs[k, d]), int(outs[l, d]))
+        assert v == ref
+
+
+def test_library_fourfold_products_arguments(built):
+    import ctypes
+    import paper_2310_14649_gb300 as sg
+    from paper_2310_14649_gb300 import _lib
+    lib = _lib.lib()
+    n = ctypes.c_int64(0)
+    assert lib.sg_fourfold_products(0, 2, 4, ctypes.byref(n), None, None, None) == -1
+    assert lib.sg_fourfold_products(2, 9, 4, ctypes.byref(n), None, None, None) == -1
+    assert lib.sg_fourfold_products(2, 2, 4, None, None, None, None) == -1
+    assert lib.sg_fourfold_products(2, 2, 4, ctypes.byref(n), None, None, None) == 0 and n.value > 0
+    small = ctypes.c_int64(n.value - 1)
+    buf = (ctypes.c_int64 * n.value)()
+    assert lib.sg_fourfold_products(2, 2, 4, ctypes.byref(small), None, buf, None) == -1
+    with pytest.raises(sg.SgError):
+        sg.sg_fourfold_products(13, 1, 1)
