@@ -24,6 +24,8 @@ coarse     2h interpolation R_0^T and the Galerkin coarse operator (Sec. 3,
            Eq. coarse)
 amg        smoothed-aggregation hierarchy and V-cycle (the AMG of Sec. 3)
 twolevel   multiplicative two-level preconditioner (Sec. 3, Eq. RAS_2L)
+variants   the paper's own preconditioner variants: RAS with ILU(0) of the
+           coupled local block, the 2GV2 coarse solve (Sec. 3, Sec. 5)
 nonlinear  the nonlinear problem (Sec. 2.2, Eqs. NLP_StrongPDE,
            stonlp_system, AjkTkl): fourfold products t_ijkl, the linearised
            operator A + T(U) and the Picard iteration; the deterministic
