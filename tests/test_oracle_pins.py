@@ -13,7 +13,6 @@ import scipy.sparse.linalg as spla
 
 from oracle import fem, galerkin, kl, pce
 
-GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
 
 
 # --------------------------------------------------------------------------
