@@ -494,6 +494,8 @@ sg_status jit_configure(sg_problem* pr, int which, const JitConfig& c) {
     set_error("sg_apply_config: the input-group hand-off does not fit in shared memory");
     return SG_ERR_ARG;
   }
+  // recorded coarse-solve graphs reference the kernel about to be unloaded
+  if (pr->jit[which]) drop_recorded(pr);
   jit_free(pr, which);
   pr->jit_cfg[which] = c;
   pr->jit_cfg_set[which] = true;

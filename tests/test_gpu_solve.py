@@ -217,3 +217,20 @@ def test_gram_schmidt_passes_rejected(gpu):
         with pytest.raises(sg.SgError) as e:
             sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_orth_passes=bad)
         assert e.value.status == -1
+
+
+def test_new_kernel_shape_after_a_solve(gpu):
+    """Changing a generated kernel after a solve (its coarse-solve graph
+    already recorded) drops the recorded graphs before the old kernel is
+    unloaded: the next solve records afresh and gives the same answer."""
+    import paper_2310_14649_gb300 as sg
+    c = dict(CONFIGS["poisson256_L4_p3"], N=64, sx=4, sy=4)
+    prob = setup(c)
+    X = zeros(prob)
+    sg.sg_solve(prob, X, rtol=1e-8, mode=1)
+    sg.sg_apply_config(prob, 1, 1, 1, 4, 16, 1, which=1)
+    sg.sg_apply_config(prob, 1, 1, 1, 1, 16, 1, which=0)
+    Y = zeros(prob)
+    info = sg.sg_solve(prob, Y, rtol=1e-8, mode=1)
+    assert info["relres"] <= 1e-8
+    assert (X - Y).norm().item() <= 1e-6 * X.norm().item()
