@@ -33,6 +33,15 @@
  * - Errors are returned as sg_status codes; no exception crosses the ABI.
  *   sg_last_error() returns a thread-local message for the last failure.
  *   A handle is not thread-safe: one host thread at a time.
+ * - Errors every entry point shares, unless its comment says otherwise:
+ *   SG_ERR_ARG for a NULL handle or a NULL pointer it needs, a leading
+ *   dimension below n, an index out of range, or a call made before the
+ *   setup it depends on (sg_precond_setup, weights of the learned smoother);
+ *   SG_ERR_NOMEM when a device or host allocation fails; SG_ERR_CUDA when a
+ *   CUDA call fails (the message names it).  Getters have no other errors.
+ * - Entry points marked "plumbing" (tile shapes, profiling, launch counts,
+ *   kernel selection) have no counterpart in the paper; those of the learned
+ *   smoother and of batching come from the method statement, not the paper.
  */
 #ifndef SG_H_
 #define SG_H_
@@ -203,8 +212,9 @@ sg_status sg_apply_autotune(sg_problem* prob, int which, int force, double* best
  * cfg10) and the seconds spent compiling or loading its kernel. */
 sg_status sg_apply_info(const sg_problem* prob, int which, int* cfg10, double* compile_s);
 
-/* Residual R = F - sum_k A_k X G_k^T, same layout and dtype rules as
- * sg_apply (F may equal R for an in-place update). */
+/* Residual R = F - sum_k A_k X G_k^T (Sec. 2.1, Eq. Galerkin_L_exp), same
+ * layout and dtype rules as sg_apply (F may equal R for an in-place
+ * update; X must not overlap R).  Errors as for sg_apply. */
 sg_status sg_residual(sg_problem* prob, sg_dtype dtype, const void* F_dev, int64_t ldf,
                       const void* X_dev, int64_t ldx, void* R_dev, int64_t ldr, void* stream);
 
@@ -329,8 +339,10 @@ typedef struct {
   double t_setup, t_solve; /* seconds (t_setup unused here)          */
 } sg_solve_info;
 
-/* Solves sum_k A_k X G_k^T = F.  F = NULL uses the load vector of
- * sg_get_rhs.  X holds the initial guess on entry and the solution on
+/* Solves sum_k A_k X G_k^T = F (Sec. 2.1, Eq. Galerkin_L_exp) by flexible
+ * GMRES with the two-level preconditioner (Sec. 3; mode 1 adds the FP32
+ * inner solves in FP64 refinement of the method statement).  F = NULL uses
+ * the load vector of sg_get_rhs.  X holds the initial guess on entry and the solution on
  * return (FP64 device blocks).  Needs sg_precond_setup.  Synchronises the
  * stream once per iteration to test convergence.
  * Returns SG_OK when relres <= rtol, SG_NOT_CONVERGED (X = last iterate)
@@ -511,9 +523,11 @@ sg_status sg_batch_create(sg_problem* const* probs, int count, const sg_solve_op
 sg_status sg_batch_solve(sg_batch* batch, const double* const* F, const int64_t* ldf, double* const* X,
                          const int64_t* ldx, sg_solve_info* infos, void* stream);
 
+/* Releases a recorded batch (NULL is accepted); the problems stay valid. */
 sg_status sg_batch_destroy(sg_batch* batch);
 
-/* sg_batch_create + sg_batch_solve + sg_batch_destroy in one call. */
+/* sg_batch_create + sg_batch_solve + sg_batch_destroy in one call (method
+ * statement: batching).  Errors as for those three. */
 sg_status sg_solve_batch(sg_problem* const* probs, int count, const double* const* F, const int64_t* ldf,
                          double* const* X, const int64_t* ldx, const sg_solve_opts* opts, sg_solve_info* infos,
                          void* stream);
@@ -550,21 +564,25 @@ sg_status sg_mdot(sg_problem* prob, sg_dtype dtype, const void* V, int64_t strid
 sg_status sg_mdot_noalloc(sg_dtype dtype, const void* V, int64_t stride, int nv, const void* w,
                           int64_t len, double* out_dev, void* stream);
 
-/* Per-launch timing of the operator-apply and RAS local-solve kernels, for
- * benchmarks.  While enabled, every such launch through this handle (outside
+/* Plumbing.  Per-launch timing of the operator-apply and RAS local-solve
+ * kernels, for benchmarks.  While enabled, every such launch through this handle (outside
  * recorded graphs) is bracketed by CUDA events on its stream (a few
  * microseconds of overhead per launch).  Enabling (or disabling) clears the
  * records.  sg_profile_read waits for the recorded events and returns the
  * number of launches and their summed device time in ms for one kind:
  * 0 fine apply FP32, 1 fine apply FP64, 2 coarse apply FP32, 3 coarse apply
- * FP64, 4 RAS local solve FP32, 5 RAS local solve FP64. */
+ * FP64, 4 RAS local solve FP32, 5 RAS local solve FP64.
+ * Errors: SG_ERR_ARG for a kind outside 0..5. */
 sg_status sg_profile(sg_problem* prob, int enable);
 sg_status sg_profile_read(sg_problem* prob, int kind, int64_t* launches, double* ms);
 
-/* Number of kernel launches this library has made in the process so far
- * (all handles); differences bracket a region of interest. */
+/* Plumbing.  Number of kernel launches this library has made in the process
+ * so far (all handles, kernels inside recorded graphs included);
+ * differences bracket a region of interest.  Errors: SG_ERR_ARG for NULL. */
 sg_status sg_launch_count(int64_t* count);
 
+/* Message of the last failure on this host thread ("" when none); the
+ * pointer stays valid until the thread's next failing call. */
 const char* sg_last_error(void);
 
 #ifdef __cplusplus
