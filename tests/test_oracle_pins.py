@@ -386,3 +386,32 @@ def test_monte_carlo_mean_variance():
     assert np.all(np.abs(mc_var - var_sg) <= 4 * se_var + trunc_v + 1e-18)
     # and the variance is genuinely resolved (not trivially inside the band)
     assert np.max(var_sg) > 10 * np.max(se_var)
+
+
+def test_paper_verification_setting_against_collocation():
+    """The paper's verification setting for the linear problem (Sec. 5,
+    Fig. mcs_verify_poisson: three random variables, input order 2, output
+    order 3, sigma = 0.1), checked against a 6^3-point Gauss-Hermite
+    collocation of the exact lognormal problem instead of Monte Carlo: the
+    SG mean and standard deviation agree (the input truncation at order 2
+    is the only difference)."""
+    import itertools
+    import scipy.sparse.linalg as spla
+    from numpy.polynomial import hermite_e as H
+    N = 20
+    prob = galerkin.build(N, 3, 3, 2, sigma2=0.01, bx=0.5, by=0.5)
+    U = galerkin.solve_direct(prob)
+    x, w = H.hermegauss(6)
+    w = w / np.sqrt(2.0 * np.pi)
+    b = fem.load_vector(N)
+    m1 = np.zeros(prob.n)
+    m2 = np.zeros(prob.n)
+    for i, j, k in itertools.product(range(6), repeat=3):
+        xi = np.array([x[i], x[j], x[k]])
+        u = spla.spsolve(fem.assemble(N, np.exp(xi @ prob.gfield)).tocsc(), b)
+        m1 += w[i] * w[j] * w[k] * u
+        m2 += w[i] * w[j] * w[k] * u * u
+    std_c = np.sqrt(m2 - m1 ** 2)
+    std_sg = np.sqrt((U[:, 1:] ** 2).sum(1))
+    assert np.linalg.norm(U[:, 0] - m1) / np.linalg.norm(m1) <= 1e-6
+    assert np.linalg.norm(std_sg - std_c) / np.linalg.norm(std_c) <= 1e-3
