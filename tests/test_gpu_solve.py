@@ -234,3 +234,21 @@ def test_new_kernel_shape_after_a_solve(gpu):
     info = sg.sg_solve(prob, Y, rtol=1e-8, mode=1)
     assert info["relres"] <= 1e-8
     assert (X - Y).norm().item() <= 1e-6 * X.norm().item()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_paper_verification_setting(gpu, mode):
+    """The paper's verification setting (three random variables, input
+    order 2 -- a truncated lognormal input -- output order 3, sigma = 0.1)
+    on a 32^2 mesh: the solve matches the oracle's direct solution."""
+    import paper_2310_14649_gb300 as sg
+    c = dict(N=32, L=3, p=3, q=2, sigma2=0.01, b=0.5, sx=2, sy=2, overlap=1)
+    prob = setup(c)
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    X = zeros(prob)
+    info = sg.sg_solve(prob, X, rtol=1e-10, mode=mode)
+    Xh = to_np(X, prob.n)
+    Xd = galerkin.solve_direct(ref)
+    assert prob.P == 20 and prob.K == 10
+    assert info["relres"] <= 1e-10
+    assert np.linalg.norm(Xh - Xd) / np.linalg.norm(Xd) <= 1e-8
