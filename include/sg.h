@@ -565,14 +565,20 @@ sg_status sg_mdot_noalloc(sg_dtype dtype, const void* V, int64_t stride, int nv,
                           int64_t len, double* out_dev, void* stream);
 
 /* Plumbing.  Per-launch timing of the operator-apply and RAS local-solve
- * kernels, for benchmarks.  While enabled, every such launch through this handle (outside
- * recorded graphs) is bracketed by CUDA events on its stream (a few
- * microseconds of overhead per launch).  Enabling (or disabling) clears the
- * records.  sg_profile_read waits for the recorded events and returns the
- * number of launches and their summed device time in ms for one kind:
- * 0 fine apply FP32, 1 fine apply FP64, 2 coarse apply FP32, 3 coarse apply
- * FP64, 4 RAS local solve FP32, 5 RAS local solve FP64.
- * Errors: SG_ERR_ARG for a kind outside 0..5. */
+ * kernels and of the phases of a host-driven solve, for benchmarks.  While
+ * enabled, every such launch or phase through this handle (outside recorded
+ * graphs) is bracketed by CUDA events on its stream (a few microseconds of
+ * overhead each, so time the headline with the profiler off).  Enabling (or
+ * disabling) clears the records.  sg_profile_read waits for the recorded
+ * events and returns the number of launches and their summed device time in
+ * ms for one kind: 0 fine apply FP32, 1 fine apply FP64, 2 coarse apply
+ * FP32, 3 coarse apply FP64, 4 RAS local solve FP32, 5 RAS local solve FP64;
+ * phases (each holds the kernels it launches; 4 and 5 lie inside 6):
+ * 6 smoother, 7 coarse correction (restriction, the coarse GMRES graph,
+ * interpolation), 8 Arnoldi step (Gram-Schmidt, Givens rotation,
+ * normalisation), 9 refinement bookkeeping (FP64 residual norm, conversion
+ * to FP32, the update of x).
+ * Errors: SG_ERR_ARG for a kind outside 0..9. */
 sg_status sg_profile(sg_problem* prob, int enable);
 sg_status sg_profile_read(sg_problem* prob, int kind, int64_t* launches, double* ms);
 

@@ -231,8 +231,10 @@ def sg_profile(prob, enable):
 
 
 def sg_profile_read(prob, kind):
-    """(launches, total ms) of one apply kind: 0 fine FP32, 1 fine FP64,
-    2 coarse FP32, 3 coarse FP64."""
+    """(launches, total ms) of one kind: kernels 0 fine apply FP32, 1 fine
+    apply FP64, 2 coarse apply FP32, 3 coarse apply FP64, 4/5 RAS local
+    solve FP32/FP64; phases 6 smoother, 7 coarse correction, 8 Arnoldi
+    step, 9 refinement bookkeeping."""
     cnt, ms = ctypes.c_int64(), ctypes.c_double()
     call("sg_profile_read", prob.handle, kind, ctypes.byref(cnt), ctypes.byref(ms))
     return cnt.value, ms.value

@@ -28,6 +28,7 @@ struct KrylovWork {
   DevBuf V, Z, w, tmp, tmp2, state, partial, counter;
   GmresState s{};
   double* host = nullptr;  // pinned: [0] est, [1] h_{j+1,j}, [2] bad, [4..] scalars
+  Profiler* prof = nullptr;  // times the Arnoldi steps (phase kind 8) when on
 
   sg_status init(int64_t len_, int m_, bool flexible_) {
     len = len_;
@@ -144,6 +145,7 @@ inline sg_status gmres_run(KrylovWork<T>& W, const Op<T>& A, const Op<T>& M, con
       T* zj = W.flexible ? W.Zj(j) : dp<T>(W.tmp);
       SG_TRY(M(W.Vj(j), zj));
       SG_TRY(A(zj, dp<T>(W.w)));
+      ProfScope arnoldi(W.prof, 8, st);
       double* h1 = W.s.hsum;
       double* h2 = W.s.hsum + (W.m + 1);
       SG_TRY(vec_mdot<T>(dp<T>(W.V), len, j + 1, dp<T>(W.w), len, h1, dp<double>(W.partial),
@@ -160,6 +162,7 @@ inline sg_status gmres_run(KrylovWork<T>& W, const Op<T>& A, const Op<T>& M, con
       }
       SG_TRY(gmres_givens(W.s, W.m, j, W.host, st));
       SG_TRY(vec_scale_by<T>(dp<T>(W.w), W.Vj(j + 1), len, W.s.scal + 1, false, st));
+      arnoldi.stop();
       SG_CUDA(cudaStreamSynchronize(st));
       res.its++;
       k = j + 1;
@@ -269,6 +272,7 @@ struct SolverCtx {
     ldc = pc->co.ldc;
     lenc = int64_t(pr->P) * ldc;
     SG_TRY(fine.init(len, restart, true));
+    fine.prof = &pr->prof;
     // flexible storage: the update x += M (V y) reuses Z_j = M V_j
     SG_TRY(coarse.init(lenc, pc->inner_restart, true));
     coarse.passes = pc->inner_passes;
@@ -476,6 +480,7 @@ struct SolverCtx {
   }
   // Q r = R_0^T A_c^{-1} R_0 r
   sg_status coarse_correction(const T* R, T* Z, bool add, cudaStream_t st) {
+    ProfScope phase(&pr->prof, 7, st);
     SG_TRY(spmm<T>(pc->co.R, R, ld, nullptr, 0, dp<T>(rc), ldc, pr->P, 0, st));
     if (pc->device_loops) {
       SG_TRY(coarse_solve_graph(st));
@@ -491,6 +496,7 @@ struct SolverCtx {
   // the learned smoother is active; FP32 inputs are recorded while a
   // harvest for training is on
   sg_status smooth(const T* R, T* Z, cudaStream_t st) {
+    ProfScope phase(&pr->prof, 6, st);
     Harvest& h = pc->harvest;
     if (sizeof(T) == 4 && h.on && h.count < h.cap) {
       SG_CUDA(cudaMemcpyAsync(dp<float>(h.pool) + h.count * len, R, len * sizeof(T), cudaMemcpyDeviceToDevice, st));
@@ -527,6 +533,8 @@ struct SolverState {
   bool dirty = false;                        // the last solve ended on an error
   double* host = nullptr;                    // pinned scalars
   uint64_t serial;                           // distinguishes successive preconditioner setups
+  uint64_t ctx_gen = 0;                      // bumped whenever c64 or c32 is dropped or re-created:
+                                             // recorded graphs hold their buffers by address
   SolverState() {
     static std::atomic<uint64_t> next{1};
     serial = next++;
@@ -545,6 +553,7 @@ inline sg_status get_ctx(sg_problem* pr, SolverCtx<T>*& out) {
   SolverState& S = *pr->solver;
   auto& c = ctx_of<T>(S);
   if (!c || !c->ready || c->fine.m != S.restart) {
+    ++S.ctx_gen;
     c.reset(new SolverCtx<T>());
     SG_TRY(c->init(pr, &S.pc, S.restart));
   }

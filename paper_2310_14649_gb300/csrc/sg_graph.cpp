@@ -233,7 +233,8 @@ static sg_status capture_fine(SolverCtx<T>& c, const T* b, T* x, double rtol, bo
 struct GraphSystem {
   sg_problem* pr = nullptr;
   uint64_t serial = 0;
-  const void* ctx64 = nullptr;  // the workspaces the graph was recorded with
+  uint64_t ctx_gen = 0;         // generation of the workspaces the graph was recorded with
+  const void* ctx64 = nullptr;
   const void* ctx32 = nullptr;
   RegionCounts ir;              // refinement loop: fixed, -, per step
   CapStreams streams;
@@ -334,6 +335,7 @@ static sg_status prepare_system(GraphSystem& gs, const sg_solve_opts& o) {
   S.pc.use_cnn = S.pc.smoother == 1 && pr->cnn && pr->cnn->trained;
   S.pc.harvest.on = false;
   gs.serial = S.serial;
+  gs.ctx_gen = S.ctx_gen;
   gs.ctx64 = c64;
   gs.ctx32 = c32;
   return gs.streams.create();
@@ -434,8 +436,8 @@ sg_status sg_batch_solve(sg_batch* B, const double* const* F, const int64_t* ldf
   auto t0 = std::chrono::steady_clock::now();
   for (size_t i = 0; i < n; ++i) {
     sg_problem* pr = B->sys[i].pr;
-    SG_ARG(pr->solver && pr->solver->serial == B->sys[i].serial && pr->solver->c64.get() == B->sys[i].ctx64 &&
-               pr->solver->c32.get() == B->sys[i].ctx32,
+    SG_ARG(pr->solver && pr->solver->serial == B->sys[i].serial && pr->solver->ctx_gen == B->sys[i].ctx_gen &&
+               pr->solver->c64.get() == B->sys[i].ctx64 && pr->solver->c32.get() == B->sys[i].ctx32,
            "sg_batch_solve: a problem's preconditioner or solver workspace changed after sg_batch_create");
     SG_ARG(X[i] && ldx[i] >= pr->n && (!F || !F[i] || (ldf && ldf[i] >= pr->n)),
            "sg_batch_solve: bad block or leading dimension");

@@ -108,9 +108,16 @@ struct TripleTables {
   DevBuf off;      // int32 P x (nchunk + 1)
 };
 
-// Optional per-launch timing of the operator-apply kernels (bench mode):
-// CUDA events bracket each launch on its stream; read() sums the elapsed
-// times per kind (0 fine FP32, 1 fine FP64, 2 coarse FP32, 3 coarse FP64).
+// Optional per-launch timing (bench mode): CUDA events bracket each launch
+// or phase on its stream; read() sums the elapsed times per kind.  Kernel
+// kinds: 0 fine apply FP32, 1 fine apply FP64, 2 coarse apply FP32, 3
+// coarse apply FP64, 4 RAS local solve FP32, 5 RAS local solve FP64.
+// Phase kinds of the host-driven solve (a phase holds the kernels it
+// launches, so kinds 4 and 5 lie inside kind 6): 6 smoother, 7 coarse
+// correction (restriction, coarse GMRES graph, interpolation), 8 Arnoldi
+// step (Gram-Schmidt, Givens rotation, normalisation), 9 refinement step
+// bookkeeping (FP64 residual norm, conversion to FP32, the update of x).
+constexpr int kProfKinds = 10;
 struct Profiler {
   bool on = false;
   struct Rec {
@@ -124,6 +131,23 @@ struct Profiler {
   sg_status read(int kind, int64_t* launches, double* ms);
   void reset() { used = 0; }
   ~Profiler();
+};
+
+// Brackets a phase with profiler events when the profiler is on (errors of
+// the event calls are ignored: timing never fails a solve).
+struct ProfScope {
+  Profiler* p;
+  cudaStream_t st;
+  size_t slot = 0;
+  bool on;
+  ProfScope(Profiler* p_, int kind, cudaStream_t st_) : p(p_), st(st_), on(p_ && p_->on) {
+    if (on && p->begin(kind, st, slot) != SG_OK) on = false;
+  }
+  void stop() {
+    if (on) p->end(slot, st);
+    on = false;
+  }
+  ~ProfScope() { stop(); }
 };
 
 // Register-specialised apply compiled at setup time (sg_jit.cpp).  Four

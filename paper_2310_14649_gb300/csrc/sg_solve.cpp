@@ -25,6 +25,7 @@ void drop_recorded(sg_problem* pr) {
   cudaDeviceSynchronize();
   pr->solver->c64.reset();
   pr->solver->c32.reset();
+  ++pr->solver->ctx_gen;  // a new context may reuse a freed one's address
 }
 
 
@@ -300,7 +301,7 @@ sg_status sg_profile(sg_problem* pr, int enable) {
 }
 
 sg_status sg_profile_read(sg_problem* pr, int kind, int64_t* launches, double* ms) {
-  SG_ARG(pr && kind >= 0 && kind < 6, "sg_profile_read: bad argument");
+  SG_ARG(pr && kind >= 0 && kind < kProfKinds, "sg_profile_read: bad argument");
   return pr->prof.read(kind, launches, ms);
 }
 
@@ -504,9 +505,12 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
       else
         SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
       x_is_zero = false;
-      SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 1, dp<double>(c64->fine.partial),
-                               dp<unsigned>(c64->fine.counter), st));
-      SG_CUDA(cudaMemcpyAsync(S.host + 1, scal + 1, 8, cudaMemcpyDeviceToHost, st));
+      {
+        ProfScope phase(&pr->prof, 9, st);
+        SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 1, dp<double>(c64->fine.partial),
+                                 dp<unsigned>(c64->fine.counter), st));
+        SG_CUDA(cudaMemcpyAsync(S.host + 1, scal + 1, 8, cudaMemcpyDeviceToHost, st));
+      }
       SG_CUDA(cudaStreamSynchronize(st));
       const double rr = std::sqrt(S.host[1]) / nF;
       if (!std::isfinite(rr)) {
@@ -526,8 +530,11 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
       }
       rr_prev = rr;
       inf.ir_steps++;
-      SG_TRY((vec_convert<double, float>(dp<double>(S.r64), r32, len, nullptr, scal + 1, st)));
-      SG_CUDA(cudaMemsetAsync(d32, 0, len * 4, st));
+      {
+        ProfScope phase(&pr->prof, 9, st);
+        SG_TRY((vec_convert<double, float>(dp<double>(S.r64), r32, len, nullptr, scal + 1, st)));
+        SG_CUDA(cudaMemsetAsync(d32, 0, len * 4, st));
+      }
       GmresResult res;
       // the FP32 correction solve stops on its Arnoldi estimate: its true FP32
       // residual cannot fall much below u_32 * cond(A), the FP64 loop
@@ -542,6 +549,7 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
         if (gs != SG_OK) continue;  // the correction is not usable
       }
       SG_TRY(gs);
+      ProfScope phase(&pr->prof, 9, st);
       SG_TRY(vec_add_scaled_f32(x64, d32, len, scal + 1, st));
     }
   }

@@ -112,6 +112,30 @@ def test_batch_rejects_changed_problem(gpu):
         sg.sg_batch_create([p, p])
 
 
+@pytest.mark.parametrize("change", ["config", "kernel"])
+def test_batch_rejects_reconfigured_apply(gpu, change):
+    """A change of apply kernel frees the solver workspaces the batch was
+    recorded with; a solve then re-creates them, possibly at the same
+    addresses.  The recorded batch must refuse to run (SG_ERR_ARG) without
+    launching its graph."""
+    import paper_2310_14649_gb300 as sg
+    p = make(SMALL[0])
+    B = sg.sg_batch_create([p], rtol=1e-8)
+    if change == "config":
+        sg.sg_apply_config(p, rows=1, groups=1, prefetch=4)
+    else:
+        sg.sg_set_apply_kernel(p, 1)
+    X = zeros(p)
+    assert sg.sg_solve(p, X, rtol=1e-8, mode=1)["relres"] <= 1e-8
+    l0 = sg.sg_launch_count()
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_batch_solve(B, [zeros(p)])
+    assert e.value.status == -1
+    assert sg.sg_launch_count() == l0
+    B.close()
+    p.close()
+
+
 def test_twelve_uneven_systems(gpu):
     """The batch of twelve seeded systems (meshes 64^2..384^2, L 2..5,
     p 2..4) in one recorded graph: every system reaches relres 1e-8, and

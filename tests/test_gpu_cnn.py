@@ -18,6 +18,9 @@ CASES = [
     # N, L, p, q: 23 x 23 and 35 x 35 images (several 8 x 16 tiles with a ragged edge)
     (24, 2, 2, 4),
     (36, 2, 1, 2),
+    # 259 x 259 images, three of them: the tcgen05 kernel's 128-pixel row
+    # tiles at x0 = 0 and 128 and the ragged tile at 256, against the oracle
+    (260, 1, 2, 4),
 ]
 
 
@@ -185,20 +188,26 @@ def test_energy_gradient_matches_oracle(pair):
 
 
 def test_adam_step_matches_oracle(pair):
-    """One update: the new weights follow the oracle's Adam from the
-    gradient the kernels produced (FP32 arithmetic)."""
+    """Four consecutive updates: after each, the new weights follow the
+    oracle's Adam (moments carried across steps, bias corrections at
+    t = 1..4) from the previous weights and the gradient the kernels
+    produced (FP32 arithmetic)."""
     import paper_2310_14649_gb300 as sg
     prob, ref = pair
     params = params_for(10)
     sg.sg_cnn_set_weights(prob, params)
     R = random_block(ref.n, 2, seed=73).astype(np.float32).astype(np.float64)
     Zs = random_block(ref.n, 2, seed=74).astype(np.float32).astype(np.float64)
-    sg.sg_cnn_train_step(prob, dev_rows(R), dev_rows(Zs), lr=1e-3, update=True)
-    g = sg.cnn_unflatten(sg.sg_cnn_get_weights(prob, gradient=True))
-    w1 = sg.sg_cnn_get_weights(prob)
-    p32 = sg.cnn_unflatten(sg.cnn_flatten(params))
-    ref_new, _ = cnn.adam_step(p32, g, cnn.adam_init(p32), lr=1e-3)
-    np.testing.assert_allclose(w1, sg.cnn_flatten(ref_new), rtol=1e-5, atol=1e-8)
+    prev = sg.cnn_unflatten(sg.cnn_flatten(params))
+    state = cnn.adam_init(prev)
+    for t in range(1, 5):
+        sg.sg_cnn_train_step(prob, dev_rows(R), dev_rows(Zs), lr=1e-3, update=True)
+        g = sg.cnn_unflatten(sg.sg_cnn_get_weights(prob, gradient=True))
+        w1 = sg.sg_cnn_get_weights(prob)
+        ref_new, state = cnn.adam_step(prev, g, state, lr=1e-3)
+        assert state[0] == t
+        np.testing.assert_allclose(w1, sg.cnn_flatten(ref_new), rtol=1e-5, atol=1e-8, err_msg="step %d" % t)
+        prev = sg.cnn_unflatten(w1)
 
 
 def test_mean_solve_matches_sparse_direct(pair):

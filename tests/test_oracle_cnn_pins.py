@@ -2,6 +2,7 @@
 direct 2D correlation, gradients against central differences, the Adam step
 against its closed form on a quadratic."""
 import numpy as np
+import pytest
 import scipy.signal
 
 from oracle import cnn
@@ -59,6 +60,53 @@ def test_adam_first_step_closed_form():
     new, state = cnn.adam_step(params, g, cnn.adam_init(params), lr=1e-2)
     assert np.allclose(new[0][0], 1.0 - 1e-2, atol=1e-9)
     assert np.allclose(new[0][1], 1e-2, atol=1e-9)
+
+
+@pytest.mark.parametrize("b1,b2", [(0.9, 0.999), (0.5, 0.75)])
+def test_adam_several_steps_closed_form(b1, b2):
+    """Steps t = 1..5 with gradients that change from step to step: the
+    moments are the bias-corrected exponentially weighted sums
+    m_t = (1-b1) sum_s b1^(t-s) g_s / (1-b1^t) and
+    v_t = (1-b2) sum_s b2^(t-s) g_s^2 / (1-b2^t) (Kingma and Ba, Alg. 1 in
+    closed form), and the parameter after t steps is
+    theta_0 - lr sum_{s<=t} m_s / (sqrt(v_s) + eps).  With two different
+    (b1, b2) pairs a swapped decay rate, a wrong bias-correction power or a
+    missing correction fails."""
+    lr, eps = 1e-2, 1e-8
+    theta0 = np.array([0.7, -1.3, 2.0])
+    gs = [np.array([0.3, -2.0, 0.05]) * (1 + 0.5 * s) * (-1) ** s for s in range(5)]
+    gs = [gs[s] + np.array([0.1, 0.2, -0.3]) * s * s for s in range(5)]
+    params = [(theta0.reshape(3, 1, 1, 1), np.array([0.25]))]
+    state = cnn.adam_init(params)
+    expect = theta0.copy()
+    expect_b = 0.25
+    for t in range(1, 6):
+        grads = [(gs[t - 1].reshape(3, 1, 1, 1), np.array([gs[t - 1][0] - 1.0]))]
+        params, state = cnn.adam_step(params, grads, state, lr=lr, b1=b1, b2=b2, eps=eps)
+        w1 = np.array([(1 - b1) * b1 ** (t - s) for s in range(1, t + 1)]) / (1 - b1 ** t)
+        w2 = np.array([(1 - b2) * b2 ** (t - s) for s in range(1, t + 1)]) / (1 - b2 ** t)
+        G = np.array(gs[:t])
+        mh = w1 @ G
+        vh = w2 @ (G * G)
+        expect = expect - lr * mh / (np.sqrt(vh) + eps)
+        gb = G[:, 0] - 1.0
+        expect_b = expect_b - lr * (w1 @ gb) / (np.sqrt(w2 @ (gb * gb)) + eps)
+        assert state[0] == t
+        np.testing.assert_allclose(params[0][0].ravel(), expect, rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(params[0][1], [expect_b], rtol=1e-13, atol=1e-15)
+
+
+def test_adam_minimises_a_quadratic():
+    """On f(theta) = 0.5 sum a_i theta_i^2 Adam with a small step reaches
+    the minimiser: after 3000 steps of lr 1e-2 every |theta_i| is below
+    a few lr (its steps are about lr in size near the optimum)."""
+    a = np.array([1.0, 10.0, 0.1])
+    params = [(np.array([1.0, -2.0, 3.0]).reshape(3, 1, 1, 1), np.zeros(1))]
+    state = cnn.adam_init(params)
+    for _ in range(3000):
+        th = params[0][0].ravel()
+        params, state = cnn.adam_step(params, [((a * th).reshape(3, 1, 1, 1), np.zeros(1))], state, lr=1e-2)
+    assert np.all(np.abs(params[0][0]) < 5e-2)
 
 
 def test_he_init_scale():

@@ -1,5 +1,6 @@
 """The allocation-free multi-dot entry point (sg_mdot_noalloc) against the
-handle-based sg_mdot, through the C ABI (GPU).
+handle-based sg_mdot and against the host FP64 product, through the C ABI
+(GPU).
 
 sg_mdot_noalloc is for callers that cannot call cudaMalloc (a framework's
 caching allocator holds the free memory, or the loop cannot afford the
@@ -9,6 +10,7 @@ two calls in a row must each give the right answer: the second must not see
 the first one's partial sums or counter.  This file is collected last.
 """
 import ctypes
+import math
 
 import numpy as np
 import pytest
@@ -51,9 +53,17 @@ def test_noalloc_matches_mdot_on_two_calls(gpu, dt):
         sg.sg_mdot(prob, V, w, ref)
         torch.cuda.synchronize()
         g, r = got.cpu().numpy(), ref.cpu().numpy()
-        bound = (V.double().abs().cpu().numpy() @ w.double().abs().cpu().numpy())
+        Vh, wh = V.double().cpu().numpy(), w.double().cpu().numpy()
+        bound = np.abs(Vh) @ np.abs(wh)
         m = 11 if dt == "f32" else 4
         assert np.all(np.abs(g - r) <= 2 * m * u * bound), (g, r)
+        # the host FP64 product, each sum correctly rounded (math.fsum; FP32
+        # inputs multiply exactly in FP64): the device result may differ by
+        # the rounding of its summation tree, whose depth is at most the
+        # elements one thread adds, plus the block and last-block reductions
+        exact = np.array([math.fsum(Vh[i] * wh) for i in range(nv)])
+        depth = 11 if dt == "f32" else -(-length // (304 * 256)) + 8 + 304
+        assert np.all(np.abs(g - exact) <= 2 * depth * u * bound + U64 * np.abs(exact)), (g, exact)
     prob.close()
 
 
