@@ -30,6 +30,13 @@ nonlinear  the nonlinear problem (Sec. 2.2, Eqs. NLP_StrongPDE,
            stonlp_system, AjkTkl): fourfold products t_ijkl, the linearised
            operator A + T(U) and the Picard iteration; the deterministic
            problem for collocation pins
+newton     the nonlinear problem with conductivity k (1 + u^2) (Sec. 2.2 with
+           u^2 in place of alpha u): the projected square, the element
+           Galerkin matrices, the residual, the exact Jacobian and Newton's
+           method
+par        multi-core operator apply, mean-block preconditioner and GMRES
+           (plain C loops in sgo.c over all host cores), for full-size
+           reference solutions and the timed CPU baseline
 cnn        FP64 convolutional smoother forward/backward (not in the paper:
            parity unpinned against the paper, gradients pinned by
            central differences)
