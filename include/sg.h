@@ -350,12 +350,58 @@ typedef struct {
 sg_status sg_solve(sg_problem* prob, const double* F_dev, int64_t ldf, double* X_dev, int64_t ldx,
                    const sg_solve_opts* opts, sg_solve_info* info, void* stream);
 
-/* Newton iteration for the nonlinear stochastic Poisson problem of Sec. 2.2
- * (Eqs. NLP_StrongPDE, stonlp_system; stop at a relative update of
- * tol_update).  Not built in this library: after the argument checks
- * (SG_ERR_ARG) it returns SG_ERR_UNSUPPORTED and leaves X unchanged. */
+/* ------------------------------------------------------------------------
+ * Nonlinear problem (Sec. 2.2, Eqs. NLP_StrongPDE, stonlp_system,
+ * vectorvalPDENL, AjkTkl, with the conductivity (1 + u^2) in place of the
+ * paper's (1 + alpha u)):
+ *     -div( c(x, xi) (1 + u^2) grad u ) = 1,   u = 0 on the boundary,
+ * c the lognormal field of sg_setup.  Inside triangle e the solution enters
+ * the conductivity through its element average ubar_e (mean of the three
+ * vertex values, zero at Dirichlet vertices); its square is projected onto
+ * the output chaos by the triple products,
+ *     w_{e,f} = sum_{a,b} ubar_{e,a} ubar_{e,b} <psi_a psi_b psi_f>,
+ * so the element Galerkin matrix is
+ *     sum_i cbar_i(e) <psi_i psi_l psi_m> + sum_{i,f} cbar_i(e) w_{e,f} <psi_i psi_f psi_l psi_m>.
+ * The fourfold products are formed through the input chaos, which needs
+ * q_in >= 2 p_out (SG_ERR_ARG otherwise).  Nonlinear operator A(U), residual
+ * F - A(U) U, Jacobian J(U) = A(U) + d(A(U)) U / dU (non-symmetric).  The
+ * first call builds the nonlinear work (coefficients of every input term
+ * at every triangle, the triple lists, two operator value arrays:
+ * about 2 (K E + 3 K n) doubles).  SG_ERR_UNSUPPORTED when (3 P + K) x 256
+ * bytes exceed the 227 KB of shared memory a CTA may use.
+ * ------------------------------------------------------------------------ */
+
+/* Newton's method from the initial guess in X (FP64 mode-major device
+ * block; the solution on return): each step solves J(U) dU = F - A(U) U
+ * (F = the load vector) by flexible GMRES preconditioned by the two-level
+ * cycle of sg_precond_setup (set up for the linear problem; the learned
+ * smoother when it is selected) to the relative tolerance opts->inner_rtol
+ * (<= 0: 1e-4), with at most opts->max_it iterations a step; mode 1: the
+ * Jacobian applies and the preconditioner in FP32 (the Newton residual and
+ * the update in FP64), mode 0: all in FP64.  Stops when
+ * ||dU|| / ||U|| <= tol_update.  info: outer_it = GMRES iterations summed,
+ * inner_it = coarse GMRES iterations, ir_steps = Newton steps, relres =
+ * ||F - A(U) U|| / ||F|| of the returned U, hist_host = the relative
+ * updates.  Needs sg_precond_setup.
+ * Returns SG_OK, SG_NOT_CONVERGED (max_newton steps taken; X = last
+ * iterate), SG_ERR_BREAKDOWN (non-finite residual or update), SG_ERR_ARG,
+ * SG_ERR_UNSUPPORTED (see above). */
 sg_status sg_newton(sg_problem* prob, double* X_dev, int64_t ldx, double tol_update, int max_newton,
                     const sg_solve_opts* opts, sg_solve_info* info, void* stream);
+
+/* R = F - A(X) X in FP64 (F = NULL: the load vector), mode-major device
+ * blocks; R must not overlap X or F.  Errors as for sg_apply, plus those of
+ * the nonlinear setup above. */
+sg_status sg_nonlinear_residual(sg_problem* prob, const double* F_dev, int64_t ldf, const double* X_dev,
+                                int64_t ldx, double* R_dev, int64_t ldr, void* stream);
+
+/* Y = J(U) dU, the Jacobian of the nonlinear residual's operator part at U
+ * applied to dU: dtype FP64 (double blocks, FP64 arithmetic) or FP32
+ * (float blocks; the operator A(U) is formed from U in FP64, everything
+ * else in FP32).  Y must not overlap U or dU.  Errors as for
+ * sg_nonlinear_residual. */
+sg_status sg_nonlinear_jacobian_apply(sg_problem* prob, sg_dtype dtype, const void* U_dev, int64_t ldu,
+                                      const void* dU_dev, int64_t lddu, void* Y_dev, int64_t ldy, void* stream);
 
 /* ------------------------------------------------------------------------
  * Learned smoother.  The method statement replaces the mean-based local

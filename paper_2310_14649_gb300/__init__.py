@@ -17,6 +17,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel", "sg_set_apply_fp64",
            "sg_apply_fp64_info", "sg_precond_save", "sg_precond_load", "sg_fourfold_products",
+           "sg_newton", "sg_nonlinear_residual", "sg_nonlinear_jacobian_apply",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
@@ -224,6 +225,49 @@ def sg_solve(prob, X, F=None, rtol=1e-8, max_it=500, restart=30, mode=0, inner_r
     out["hist"] = hist[:info.hist_len].copy()
     out["status"] = st
     return out
+
+
+def sg_newton(prob, X, tol_update=1e-8, max_newton=20, max_it=500, restart=30, mode=1, inner_rtol=0.0,
+              hist_cap=64, stream=None, allow_not_converged=False, orth_passes=0):
+    """Newton's method for -div(c (1 + u^2) grad u) = 1 from the initial
+    guess in X (FP64, [P, ld]; the solution on return).  Returns a dict of
+    the solve info (ir_steps = Newton steps, hist = relative updates)."""
+    import torch
+    _check_block(prob, X, "X")
+    if X.dtype != torch.float64:
+        raise TypeError("sg_newton works on FP64 blocks")
+    hist = np.zeros(max(hist_cap, 1), dtype=np.float64)
+    opts = _lib.SolveOpts(1e-8, max_it, restart, mode, inner_rtol, 0,
+                          hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), hist_cap, 0, orth_passes)
+    info = _lib.SolveInfo()
+    allow = (0, 1) if allow_not_converged else (0,)
+    st = call("sg_newton", prob.handle, dev_ptr(X), X.stride(0), ctypes.c_double(tol_update), max_newton,
+              ctypes.byref(opts), ctypes.byref(info), stream_handle(stream), allow=allow)
+    out = {f: getattr(info, f) for f, _ in _lib.SolveInfo._fields_}
+    out["hist"] = hist[:info.hist_len].copy()
+    out["status"] = st
+    return out
+
+
+def sg_nonlinear_residual(prob, X, R, F=None, stream=None):
+    """R = F - A(X) X of the nonlinear problem (FP64 blocks; F None: the
+    load vector)."""
+    _check_block(prob, X, "X")
+    _check_block(prob, R, "R")
+    call("sg_nonlinear_residual", prob.handle, dev_ptr(F) if F is not None else None,
+         F.stride(0) if F is not None else 0, dev_ptr(X), X.stride(0), dev_ptr(R), R.stride(0),
+         stream_handle(stream))
+
+
+def sg_nonlinear_jacobian_apply(prob, U, dU, Y, stream=None):
+    """Y = J(U) dU of the nonlinear problem (FP32 or FP64 blocks of one
+    dtype)."""
+    for t, nm in ((U, "U"), (dU, "dU"), (Y, "Y")):
+        _check_block(prob, t, nm)
+    if not (U.dtype == dU.dtype == Y.dtype):
+        raise TypeError("U, dU and Y must have one dtype")
+    call("sg_nonlinear_jacobian_apply", prob.handle, _dtype_code(U), dev_ptr(U), U.stride(0), dev_ptr(dU),
+         dU.stride(0), dev_ptr(Y), Y.stride(0), stream_handle(stream))
 
 
 def sg_profile(prob, enable):

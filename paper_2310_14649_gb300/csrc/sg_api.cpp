@@ -69,6 +69,7 @@ sg_status sg_destroy(sg_problem* pr) {
   if (!pr) return SG_OK;
   solver_free(pr);
   cnn_free(pr);
+  newton_free(pr);
   for (int w = 0; w < kJitFamilies; ++w) jit_free(pr, w);
   pr->mdot_partial.free_();
   pr->mdot_counter.free_();

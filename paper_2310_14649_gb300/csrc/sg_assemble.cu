@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "sg_internal.h"
+#include "sg_stencil.h"
 
 namespace sg {
 
@@ -69,15 +70,8 @@ __global__ void k_fine_ell(const double* __restrict__ cb, int N, int64_t n, int6
     int64_t r = t - int64_t(kl) * n;
     int i = int(r % m) + 1, j = int(r / m) + 1;
     const double* c = cb + int64_t(kl) * E;
-    auto lo = [&](int ci, int cj) { return c[2LL * (int64_t(cj) * N + ci)]; };
-    auto up = [&](int ci, int cj) { return c[2LL * (int64_t(cj) * N + ci) + 1]; };
     double v[5];
-    v[0] = (j > 1) ? -0.5 * (up(i, j - 1) + lo(i - 1, j - 1)) : 0.0;
-    v[1] = (i > 1) ? -0.5 * (lo(i - 1, j) + up(i - 1, j - 1)) : 0.0;
-    v[2] = 0.5 * lo(i, j) + 0.5 * up(i, j) + lo(i - 1, j) + up(i, j - 1) + 0.5 * lo(i - 1, j - 1) +
-           0.5 * up(i - 1, j - 1);
-    v[3] = (i < m) ? -0.5 * (lo(i, j) + up(i, j - 1)) : 0.0;
-    v[4] = (j < m) ? -0.5 * (up(i, j) + lo(i - 1, j)) : 0.0;
+    p1_stencil<double>(c, N, i, j, v);
     int k = k0 + kl;
     for (int s = 0; s < 5; ++s) {
       int64_t idx = (int64_t(k) * 5 + s) * ldr + r;
@@ -116,8 +110,24 @@ sg_status assemble_fine(sg_problem* pr) {
   SG_TRY(A.v64.alloc(size_t(K) * S * ldr * sizeof(double)));
   SG_TRY(A.v32.alloc(size_t(K) * S * ldr * sizeof(float)));
 
-  // inputs of the coefficient kernel
-  DevBuf dg, dmi, disf, dcb;
+  const int KC = 32;
+  DevBuf dcb;
+  SG_TRY(dcb.alloc(size_t(KC) * E * sizeof(double)));
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    int kn = std::min(KC, K - k0);
+    SG_TRY(element_coefficients(pr, k0, kn, dcb.as<double>(), nullptr));
+    k_fine_ell<<<4 * 152, 256>>>(dcb.as<double>(), N, n, ldr, k0, kn, A.v64.as<double>(),
+                                 A.v32.as<float>()); note_launch();
+    SG_CUDA(cudaGetLastError());
+  }
+  SG_CUDA(cudaDeviceSynchronize());
+  return SG_OK;
+}
+
+sg_status element_coefficients(sg_problem* pr, int k0, int kn, double* out, cudaStream_t st) {
+  const int K = pr->K, L = pr->L;
+  const int64_t E = pr->E;
+  DevBuf dg, dmi, disf;
   std::vector<double> isf(K, 1.0);
   std::vector<int32_t> mi = pr->mi_in;
   if (L == 0) mi.assign(1, 0);
@@ -135,22 +145,10 @@ sg_status assemble_fine(sg_problem* pr) {
   SG_CUDA(cudaMemcpy(dmi.ptr, mi.data(), mi.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   SG_TRY(disf.alloc(isf.size() * sizeof(double)));
   SG_CUDA(cudaMemcpy(disf.ptr, isf.data(), isf.size() * sizeof(double), cudaMemcpyHostToDevice));
-  const int KC = 32;
-  SG_TRY(dcb.alloc(size_t(KC) * E * sizeof(double)));
-  for (int k0 = 0; k0 < K; k0 += KC) {
-    int kn = std::min(KC, K - k0);
-    k_cbar<<<4 * 152, 256>>>(dg.as<double>(), dmi.as<int>(), disf.as<double>(), L, E, pr->g0, k0, kn,
-                             dcb.as<double>()); note_launch();
-    SG_CUDA(cudaGetLastError());
-    k_fine_ell<<<4 * 152, 256>>>(dcb.as<double>(), N, n, ldr, k0, kn, A.v64.as<double>(),
-                                 A.v32.as<float>()); note_launch();
-    SG_CUDA(cudaGetLastError());
-  }
-  SG_CUDA(cudaDeviceSynchronize());
-  dg.free_();
-  dmi.free_();
-  disf.free_();
-  dcb.free_();
+  k_cbar<<<4 * 152, 256, 0, st>>>(dg.as<double>(), dmi.as<int>(), disf.as<double>(), L, E, pr->g0, k0, kn, out);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  SG_CUDA(cudaStreamSynchronize(st));
   return SG_OK;
 }
 

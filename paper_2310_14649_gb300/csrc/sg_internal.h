@@ -96,6 +96,8 @@ struct AsmBlocks {
 
 struct SolverState;
 void solver_free(sg_problem* pr);
+struct NewtonWork;
+void newton_free(sg_problem* pr);
 struct Cnn;
 void cnn_free(sg_problem* pr);
 
@@ -197,6 +199,7 @@ struct sg_problem {
   int64_t ld = 0;                      // internal leading dimension of blocks
   sg::SolverState* solver = nullptr;   // preconditioner + solver workspaces
   sg::Cnn* cnn = nullptr;              // learned smoother network
+  sg::NewtonWork* nl = nullptr;        // nonlinear problem: coefficients, operators, triple lists
   sg::Profiler prof;
   sg::JitApply* jit[sg::kJitFamilies] = {};     // specialised apply per family (fine/coarse x f32/f64)
   sg::JitConfig jit_cfg[sg::kJitFamilies];
@@ -210,9 +213,14 @@ struct sg_problem {
 namespace sg {
 // setup helpers (sg_setup.cpp)
 std::vector<int32_t> multi_indices(int L, int p);
+// <He_a He_b He_c> (integer, textbook linearisation formula)
+int64_t he_triple_1d(int a, int b, int c);
 sg_status build_host(sg_problem* pr, const sg_kl_desc* kl);
 // device assembly (sg_assemble.cu)
 sg_status assemble_fine(sg_problem* pr);
+// lognormal input coefficients c_bar_k(e) of terms [k0, k0 + kn) at every
+// element, written as out[(k - k0) E + e] (FP64 device array); synchronous
+sg_status element_coefficients(sg_problem* pr, int k0, int kn, double* out, cudaStream_t st);
 sg_status build_triple_tables(sg_problem* pr, TripleTables& t, int S);
 // apply (sg_apply.cu)
 template <typename T>

@@ -95,6 +95,8 @@ double alpha_fact(const int32_t* alpha, int L) {
 
 // Total-degree multi-index set, degree ascending and lexicographically
 // descending within one degree (compositions of d generated largest-first).
+int64_t he_triple_1d(int a, int b, int c) { return he_triple(a, b, c); }
+
 std::vector<int32_t> multi_indices(int L, int p) {
   std::vector<int32_t> out;
   std::vector<int32_t> cur(std::max(L, 1), 0);

@@ -378,17 +378,6 @@ sg_status sg_precond_apply(sg_problem* pr, sg_dtype dtype, int which, const void
 static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double* X, int64_t ldx,
                             const sg_solve_opts* o, sg_solve_info* info, void* stream);
 
-sg_status sg_newton(sg_problem* pr, double* X, int64_t ldx, double tol_update, int max_newton,
-                    const sg_solve_opts* o, sg_solve_info* info, void* stream) {
-  (void)ldx;
-  (void)stream;
-  (void)info;
-  SG_ARG(pr && X && o, "sg_newton: NULL argument");
-  SG_ARG(tol_update > 0 && max_newton > 0, "sg_newton: tol_update and max_newton must be > 0");
-  set_error("sg_newton: the nonlinear stochastic problem (Sec. 2.2) is not built in this library");
-  return SG_ERR_UNSUPPORTED;
-}
-
 sg_status sg_solve(sg_problem* pr, const double* F, int64_t ldf, double* X, int64_t ldx, const sg_solve_opts* o,
                    sg_solve_info* info, void* stream) {
   const sg_status s = solve_impl(pr, F, ldf, X, ldx, o, info, stream);

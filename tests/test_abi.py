@@ -63,6 +63,8 @@ def test_argument_errors_without_gpu(libsg):
     assert libsg.sg_precond_save(None, None, ctypes.byref(n)) == -1
     assert libsg.sg_precond_load(None, b"x" * 64, 64) == -1
     assert libsg.sg_newton(None, None, 0, ctypes.c_double(1e-8), 10, None, None, None) == -1
+    assert libsg.sg_nonlinear_residual(None, None, 0, None, 0, None, 0, None) == -1
+    assert libsg.sg_nonlinear_jacobian_apply(None, 0, None, 0, None, 0, None, 0, None) == -1
     assert libsg.sg_apply_fp64_info(None, None, None, None) == -1
     assert libsg.sg_apply_config(None, 0, 1, 1, 1, 1, 8, 1, 0, 1, 4) == -1
 
