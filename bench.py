@@ -192,8 +192,9 @@ def oracle_measure(cfg, reps_apply=3):
     """The FP64 oracle on every host core: its Kronecker apply (median of
     `reps_apply`, in GB/s with the apply's algorithmic bytes at 8 B per
     value) and one complete GMRES solve to relres 1e-8 (I kron A_0^{-1}
-    preconditioner), then continued to 1e-12 (untimed) as the reference
-    solution the GPU's solutions are compared with."""
+    preconditioner), then continued to 1e-11 (untimed) as the reference
+    solution the GPU's solutions are compared with (1e-12 is below the
+    rounding floor of the FP64 residual on this system)."""
     import numpy as np
     from oracle import par
     prob, op, t_setup = oracle_setup(cfg)
@@ -208,7 +209,7 @@ def oracle_measure(cfg, reps_apply=3):
     t_apply = statistics.median(ts)
     bytes64 = K * nnz * 8 + nnz * 4 + (n + 1) * 4 + 2 * n * P * 8
     X8, its8, hist8, t_solve = par.solve(prob, tol=1e-8, op=op)
-    X12, its12, _, _ = par.solve(prob, tol=1e-12, op=op, X0=X8)
+    X12, its12, _, _ = par.solve(prob, tol=1e-11, max_it=300, op=op, X0=X8)
     return {"t_setup": t_setup, "t_apply": t_apply, "apply_gbs": bytes64 / t_apply / 1e9,
             "apply_bytes": bytes64, "t_solve": t_solve, "its": its8, "relres_est": hist8[-1] if hist8 else 0.0,
             "cores": par.threads(), "X_ref": X12, "ref_its": its8 + its12}
@@ -521,7 +522,7 @@ def main():
                "apply_ms": round(o["t_apply"] * 1e3, 2), "apply_gbs": round(o["apply_gbs"], 2),
                "apply_bytes_f64": o["apply_bytes"], "setup_s": round(o["t_setup"], 2)}
         oracle_err = {"mixed": err_vs(X_mixed, o["X_ref"]), "plain_fp64": err_vs(X64_sol, o["X_ref"]),
-                      "reference": "oracle GMRES to relres 1e-12 (%d iterations)" % o["ref_its"]}
+                      "reference": "oracle GMRES to relres 1e-11 (%d iterations)" % o["ref_its"]}
 
     line = {
         "metric": METRIC, "value": round(ms_all, 3), "unit": "ms", "n_gpus": world,

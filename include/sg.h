@@ -403,6 +403,25 @@ sg_status sg_nonlinear_residual(sg_problem* prob, const double* F_dev, int64_t l
 sg_status sg_nonlinear_jacobian_apply(sg_problem* prob, sg_dtype dtype, const void* U_dev, int64_t ldu,
                                       const void* dU_dev, int64_t lddu, void* Y_dev, int64_t ldy, void* stream);
 
+/* Monte Carlo verification (Sec. 4.1, Fig. mcs_verify_poisson: the SG
+ * mean, standard deviation and pdf against Monte Carlo samples of the
+ * deterministic problem).  For each of S samples xi_s (FP64 device array,
+ * S x L row-major, drawn by the caller) solves
+ *     -div( c_s grad u_s ) = 1,  u_s = 0 on the boundary,
+ *     c_s(e) = exp( g0 + sum_i g_i(e) xi_{s,i} )
+ * (the exact lognormal field with this problem's KL modes at the element
+ * centroids) with the P1 discretisation of the SG system, by
+ * Jacobi-preconditioned conjugate gradients in FP32 to ||r|| <= rtol ||b||
+ * or max_it iterations, one CTA per sample with its vectors in shared
+ * memory.  u_s is written to U + s * ldu (n values, dtype FP32 or FP64).
+ * its_max (host, may be NULL) receives the largest iteration count.
+ * Synchronous.  Limits: 1 <= L <= 16 and N <= 102 (the sample's system
+ * must fit one CTA: about 16 (N-1)^2 bytes of shared memory).
+ * Returns SG_NOT_CONVERGED when a sample reached max_it (all are written),
+ * SG_ERR_ARG for the limits or bad arguments. */
+sg_status sg_sample_solve(sg_problem* prob, const double* xi_dev, int64_t S, sg_dtype dtype, void* U_dev,
+                          int64_t ldu, double rtol, int max_it, int* its_max, void* stream);
+
 /* ------------------------------------------------------------------------
  * Learned smoother.  The method statement replaces the mean-based local
  * solve (I (x) A_0)^{-1} inside the smoother by a small convolutional

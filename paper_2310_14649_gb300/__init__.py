@@ -17,7 +17,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel", "sg_set_apply_fp64",
            "sg_apply_fp64_info", "sg_precond_save", "sg_precond_load", "sg_fourfold_products",
-           "sg_newton", "sg_nonlinear_residual", "sg_nonlinear_jacobian_apply",
+           "sg_newton", "sg_nonlinear_residual", "sg_nonlinear_jacobian_apply", "sg_sample_solve",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
@@ -268,6 +268,22 @@ def sg_nonlinear_jacobian_apply(prob, U, dU, Y, stream=None):
         raise TypeError("U, dU and Y must have one dtype")
     call("sg_nonlinear_jacobian_apply", prob.handle, _dtype_code(U), dev_ptr(U), U.stride(0), dev_ptr(dU),
          dU.stride(0), dev_ptr(Y), Y.stride(0), stream_handle(stream))
+
+
+def sg_sample_solve(prob, xi, U, rtol=1e-6, max_it=2000, stream=None, allow_not_converged=False):
+    """Deterministic solves for Monte Carlo samples: xi (CUDA float64
+    [S, L]) -> U (CUDA float32 or float64 [S, ld >= n], row s = u_s).
+    Returns the largest CG iteration count."""
+    import torch
+    if xi.dtype != torch.float64 or not xi.is_contiguous() or xi.dim() != 2 or xi.shape[1] != prob.L:
+        raise TypeError("xi must be a contiguous float64 [S, L] tensor")
+    if U.dim() != 2 or U.shape[0] != xi.shape[0] or U.shape[1] < prob.n or U.stride(1) != 1:
+        raise ValueError("U must be [S, ld >= n] with unit column stride")
+    its = ctypes.c_int(0)
+    allow = (0, 1) if allow_not_converged else (0,)
+    call("sg_sample_solve", prob.handle, dev_ptr(xi), xi.shape[0], _dtype_code(U), dev_ptr(U), U.stride(0),
+         ctypes.c_double(rtol), max_it, ctypes.byref(its), stream_handle(stream), allow=allow)
+    return its.value
 
 
 def sg_profile(prob, enable):

@@ -105,6 +105,8 @@ SIGNATURES = {
     "sg_precond_save": [vp, vp, P_i64],
     "sg_newton": [vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, vp, vp, vp],
     "sg_nonlinear_residual": [vp, vp, i64, vp, i64, vp, i64, vp],
+    "sg_sample_solve": [vp, vp, i64, ctypes.c_int, vp, i64, ctypes.c_double, ctypes.c_int,
+                        ctypes.POINTER(ctypes.c_int), vp],
     "sg_nonlinear_jacobian_apply": [vp, ctypes.c_int, vp, i64, vp, i64, vp, i64, vp],
     "sg_fourfold_products": [ctypes.c_int, ctypes.c_int, ctypes.c_int, P_i64, P_i32, P_i64, P_f64],
     "sg_precond_load": [vp, vp, ctypes.c_int64],

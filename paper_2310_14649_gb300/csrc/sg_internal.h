@@ -200,6 +200,7 @@ struct sg_problem {
   sg::SolverState* solver = nullptr;   // preconditioner + solver workspaces
   sg::Cnn* cnn = nullptr;              // learned smoother network
   sg::NewtonWork* nl = nullptr;        // nonlinear problem: coefficients, operators, triple lists
+  sg::DevBuf gfield_dev;               // KL modes at the element centroids (sampled solves)
   sg::Profiler prof;
   sg::JitApply* jit[sg::kJitFamilies] = {};     // specialised apply per family (fine/coarse x f32/f64)
   sg::JitConfig jit_cfg[sg::kJitFamilies];

@@ -237,7 +237,7 @@ def test_network_operators_in_precond_apply(pair):
     import torch
     import paper_2310_14649_gb300 as sg
     prob, ref = pair
-    sx = 2
+    sx = max(2, -(-(ref.N - 1) // 33))   # boxes of at most 33 x 33 nodes
     sg.sg_precond_setup(prob, sx, sx, 1)
     params = params_for(11)
     sg.sg_cnn_set_weights(prob, params)

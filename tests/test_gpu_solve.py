@@ -115,15 +115,16 @@ def test_not_converged_and_breakdown(gpu):
 def test_solve_full_256_matches_oracle(gpu):
     """The 256x256 mesh, L=4, p=3 (2.3M unknowns), solved as the benchmark
     does: both modes reach the true FP64 relres 1e-8 and the oracle's
-    solution (multi-core FP64 GMRES to relres 1e-12) to relative L2 error
-    1e-7 (Appendix A, Eq. relerror)."""
+    solution (multi-core FP64 GMRES to relres 1e-11, about the floor its
+    rounding allows here) to relative L2 error 1e-7 (Appendix A, Eq.
+    relerror)."""
     import paper_2310_14649_gb300 as sg
     from oracle import par
     c = CONFIGS["poisson256_L4_p3"]
     prob = setup(c, inner_rtol=0.3)
     ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
-    Xo, its, hist, _ = par.solve(ref, tol=1e-12)
-    assert hist[-1] <= 1e-12
+    Xo, its, hist, _ = par.solve(ref, tol=1e-11, max_it=300)
+    assert hist[-1] <= 1e-11
     sols = []
     for mode in (0, 1):
         X = zeros(prob)
