@@ -362,6 +362,141 @@ def extra_measurements(sg, torch, prob, stream):
     return out
 
 
+def ev_time(torch, stream, fn):
+    """(ms, result) of fn() between CUDA events on `stream`."""
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), r
+
+
+def large_workload(sg, torch, stream, reps=3):
+    """The 512x512 mesh, L=6, p=3 (P=84, K=924, 21.9M unknowns): mixed and
+    plain FP64 solves, the apply's roofline (per-launch events in a separate
+    profiled solve) and the learned smoother against RAS."""
+    from sg_inputs import CONFIGS
+    c = CONFIGS["poisson512_L6_p3"]
+    t0 = time.perf_counter()
+    prob = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    sg.sg_apply_autotune(prob)
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL)
+    for which in (1, 2, 3):
+        sg.sg_apply_autotune(prob, which=which)
+    n, P, K, nnz = prob.n, prob.P, prob.K, prob.nnzA
+    X = torch.zeros((P, n), dtype=torch.float64, device="cuda")
+
+    def solve(mode):
+        X.zero_()
+        return sg.sg_solve(prob, X, rtol=1e-8, mode=mode, max_it=600)
+
+    solve(1)
+    runs = [ev_time(torch, stream, lambda: solve(1)) for _ in range(reps)]
+    ms32 = statistics.median(r[0] for r in runs)
+    info32 = runs[-1][1]
+    ms64, info64 = ev_time(torch, stream, lambda: solve(0))
+    sg.sg_profile(prob, True)
+    solve(1)
+    cnt, kms = sg.sg_profile_read(prob, 0)
+    rcnt, rms = sg.sg_profile_read(prob, 4)
+    sg.sg_profile(prob, False)
+    bytes_f32 = K * nnz * 4 + nnz * 4 + (n + 1) * 4 + 2 * n * P * 4
+    avg = kms / max(cnt, 1)
+    peak, peak_kind = peaks()
+    out = {"workload": "poisson512_L6_p3", "N": c["N"], "L": c["L"], "P": P, "K": K, "unknowns": n * P,
+           "setup_s": round(t_setup, 2),
+           "mixed_ms": round(ms32, 2), "mixed_outer_it": info32["outer_it"], "mixed_relres": info32["relres"],
+           "plain_fp64_ms": round(ms64, 2), "plain_fp64_outer_it": info64["outer_it"],
+           "speedup_mixed": round(ms64 / ms32, 3),
+           "roofline": {"kernel": "sg_apply FP32 (fine Galerkin operator)", "bound": "hbm",
+                        "achieved": round(bytes_f32 / (avg * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(bytes_f32 / (avg * 1e-3) / 1e9 / peak, 4), "peak_source": peak_kind,
+                        "bytes_per_launch": bytes_f32, "avg_launch_ms": avg, "launches": cnt},
+           "ras_local_ms_per_launch": rms / max(rcnt, 1), "apply_shape": sg.sg_apply_info(prob)}
+    # learned smoother trained on this system, against RAS
+    info = sg.sg_train_precond(prob, n_pairs=4096, epochs=4, batch=32, lr=1e-3, seed=0, loss=0)
+    solve(1)
+    msl, infol = ev_time(torch, stream, lambda: solve(1))
+    sg.sg_precond_set_smoother(prob, 0)
+    out["learned"] = {"t_train": round(info["t_train"], 2), "loss_last": float("%.4g" % info["loss_last"]),
+                      "mixed_ms": round(msl, 2), "mixed_outer_it": infol["outer_it"],
+                      "fallback": infol["fallback_used"], "relres": infol["relres"],
+                      "vs_ras_mixed": round(msl / ms32, 3)}
+    prob.close()
+    return out
+
+
+def nonlinear_workload(sg, torch, stream):
+    """The nonlinear problem -div(c (1 + u^2) grad u) = 1 on the 384x384
+    mesh, L=4, p=4 (P=70, K=495, 10.3M unknowns): Newton to a relative update
+    of 1e-8, each step by FGMRES with the two-level preconditioner, FP32
+    inside the FP64 Newton residual (mixed) and all FP64 (plain)."""
+    from sg_inputs import CONFIGS
+    c = CONFIGS["poisson384_L4_p4"]
+    prob = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
+    sg.sg_apply_autotune(prob)
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL)
+    for which in (1, 2, 3):
+        sg.sg_apply_autotune(prob, which=which)
+    X = torch.zeros((prob.P, prob.n), dtype=torch.float64, device="cuda")
+
+    def newton(mode):
+        X.zero_()
+        return sg.sg_newton(prob, X, tol_update=1e-8, mode=mode)
+
+    newton(1)
+    ms32, i32 = ev_time(torch, stream, lambda: newton(1))
+    ms64, i64 = ev_time(torch, stream, lambda: newton(0))
+    out = {"workload": "poisson384_L4_p4 nonlinear (1 + u^2)", "P": prob.P, "K": prob.K,
+           "unknowns": prob.n * prob.P, "mixed_ms": round(ms32, 2), "newton_steps": i32["ir_steps"],
+           "gmres_its": i32["outer_it"], "relres": i32["relres"], "last_update": float(i32["hist"][-1]),
+           "plain_fp64_ms": round(ms64, 2), "plain_newton_steps": i64["ir_steps"], "plain_gmres_its": i64["outer_it"],
+           "speedup_mixed": round(ms64 / ms32, 3)}
+    prob.close()
+    return out
+
+
+def verification_workload(sg, torch, stream, S=40000):
+    """The paper's verification setting (Sec. 4.1: 101 x 101 vertices, three
+    random variables, input order 2, output order 3, sigma = 0.1, four
+    subdomains): the SG solve and 40,000 Monte Carlo samples, both on the
+    GPU, and their mean and standard deviation at (0.5, 0.5) and (0.3, 0.7)."""
+    import numpy as np
+    N, L, p, q = 100, 3, 3, 2
+    prob = sg.sg_setup(N, L, p, q, sigma2=0.01, bx=0.5, by=0.5)
+    sg.sg_precond_setup(prob, 2, 2, 1)
+    X = torch.zeros((prob.P, prob.n), dtype=torch.float64, device="cuda")
+    sg.sg_solve(prob, X, rtol=1e-10, mode=1)
+    X.zero_()
+    ms_sg, info = ev_time(torch, stream, lambda: sg.sg_solve(prob, X, rtol=1e-10, mode=1))
+    xi = torch.from_numpy(np.random.default_rng(2023).standard_normal((S, L))).cuda()
+    U = torch.empty((S, prob.n), dtype=torch.float32, device="cuda")
+    sg.sg_sample_solve(prob, xi[:64], U[:64])
+    ms_mc, its = ev_time(torch, stream, lambda: sg.sg_sample_solve(prob, xi, U, rtol=1e-6))
+    Ud = U.double()
+    mean_mc, std_mc = Ud.mean(0), Ud.std(0)
+    mean_sg = X[0]
+    std_sg = X[1:].pow(2).sum(0).sqrt()
+    m = N - 1
+    pts = {}
+    for (px, py) in ((0.5, 0.5), (0.3, 0.7)):
+        r = (round(py * N) - 1) * m + (round(px * N) - 1)
+        pts["%.1f,%.1f" % (px, py)] = {"mean_sg": float(mean_sg[r]), "mean_mc": float(mean_mc[r]),
+                                       "std_sg": float(std_sg[r]), "std_mc": float(std_mc[r]),
+                                       "se_mean": float(std_mc[r]) / S ** 0.5}
+    out = {"setting": "N=100 (10,201 vertices), L=3, p=3, q=2, sigma=0.1, 2x2 boxes", "sg_ms": round(ms_sg, 3),
+           "sg_outer_it": info["outer_it"], "mc_samples": S, "mc_ms": round(ms_mc, 1),
+           "mc_samples_per_s": round(S / ms_mc * 1e3, 1), "mc_max_cg_its": its,
+           "mean_rel_diff": float((mean_sg - mean_mc).norm() / mean_sg.norm()),
+           "std_rel_diff": float((std_sg - std_mc).norm() / std_sg.norm()), "points": pts}
+    prob.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -510,6 +645,10 @@ def main():
     e2e_ms = max_over_ranks(world, g0.elapsed_time(g1) / args.steps)
 
     extras = {} if (args.no_extras or rank != 0) else extra_measurements(sg, torch, prob, stream)
+    if not args.no_extras and rank == 0:
+        extras["poisson512"] = large_workload(sg, torch, stream)
+        extras["nonlinear"] = nonlinear_workload(sg, torch, stream)
+        extras["verification"] = verification_workload(sg, torch, stream)
 
     cpu = None
     oracle_err = None

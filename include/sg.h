@@ -479,6 +479,15 @@ sg_status sg_cnn_train_step(sg_problem* prob, const float* R_dev, int64_t ldr, c
  * SG_ERR_TIMEOUT if a tcgen05 completion wait ran out (no output then). */
 sg_status sg_cnn_set_kernel(sg_problem* prob, int kind);
 
+/* Plumbing.  Polls of the mbarrier on which a tcgen05 forward-convolution
+ * CTA waits for its MMAs before it gives up (limit < 0: the default,
+ * 4,194,304 polls).  A CTA whose wait runs out stores nothing, sets an
+ * error flag that sg_cnn_apply returns as SG_ERR_TIMEOUT, and then waits
+ * again (bounded) for the MMAs it issued before it frees their tensor
+ * memory, so the context stays usable.  limit = 0 makes every wait run out
+ * at once (for tests of that path). */
+sg_status sg_cnn_set_wait_limit(sg_problem* prob, int limit);
+
 /* Loss of sg_cnn_train_step: 0 (default) sum_a (e_a^T A_0 e_a) /
  * (z*_a^T A_0 z*_a), e_a = y_a - z*_a / rms(r_a): the error in the energy
  * norm of A_0, which weights the oscillatory error a smoother must remove;

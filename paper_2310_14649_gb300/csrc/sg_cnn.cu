@@ -8,6 +8,10 @@
 // to 16 or 32); weights are [tap][Cout][Cin] (Cin contiguous), FP32 master
 // copies with BF16 copies for the tensor cores; accumulation is FP32.
 //
+// With the tcgen05 kernels selected (default), the forward convolutions and
+// the input gradients run on the fifth-generation tensor cores
+// (sg_conv_tc.cu); the weight gradients, and everything with the legacy
+// kernels selected, run on the kernels below.
 // Convolutions are implicit GEMMs on the tensor cores (BF16 mma.sync
 // m16n8k16, FP32 accumulators): a CTA of 4 warps owns an 8 x 16 pixel tile,
 // the input tile with its 1-pixel halo and all 9 taps of the weights sit in
@@ -439,6 +443,7 @@ sg_status Cnn::init(const std::vector<double>& logdiag, int H_, int W_, const st
     SG_TRY(wf[l].alloc(size_t(9) * kCoPad[l] * kCiPad[l] * 2));
     SG_TRY(wr[l].alloc(size_t(9) * kCoPad[l] * kCiPad[l] * 2));
     SG_TRY(wtc[l].alloc(size_t(9) * kCoPad[l] * kCiPad[l] * 2));
+    SG_TRY(wtcr[l].alloc(size_t(9) * kCoPad[l] * kCiPad[l] * 2));
   }
   std::vector<float> ld(logdiag.begin(), logdiag.end());
   SG_TRY(logd.alloc(ld.size() * 4));
@@ -512,7 +517,8 @@ sg_status Cnn::pack(cudaStream_t st) {
     k_pack_weights<<<64, 256, 0, st>>>(dp<float>(params) + woff[l], kCiPad[l], kCoPad[l], dp<bf16>(wf[l]),
                                       dp<bf16>(wr[l])); note_launch();
     SG_CUDA(cudaGetLastError());
-    SG_TRY(conv_tc_pack(dp<float>(params) + woff[l], kCiPad[l], kCoPad[l], wtc[l].ptr, st));
+    SG_TRY(conv_tc_pack(dp<float>(params) + woff[l], kCiPad[l], kCoPad[l], wtc[l].ptr, false, st));
+    if (l > 0) SG_TRY(conv_tc_pack(dp<float>(params) + woff[l], kCiPad[l], kCoPad[l], wtcr[l].ptr, true, st));
   }
   return SG_OK;
 }
@@ -525,7 +531,7 @@ sg_status Cnn::forward(int nimg, cudaStream_t st) {
   if (use_tc) {
     for (int l = 0; l < 5; ++l)
       SG_TRY(conv_tc_layer(l, act[l].ptr, wtc[l].ptr, b[l], l < 4 ? act[l + 1].ptr : nullptr,
-                           l == 4 ? dp<float>(out) : nullptr, H, W, nimg, dp<int>(tcerr), st));
+                           l == 4 ? dp<float>(out) : nullptr, H, W, nimg, dp<int>(tcerr), wait_limit, st));
     return SG_OK;
   }
   k_conv<16, 32, 0><<<grid, 128, 0, st>>>(dp<bf16>(act[0]), dp<bf16>(wf[0]), b[0], nullptr, dp<bf16>(act[1]), nullptr, H,
@@ -562,6 +568,11 @@ sg_status Cnn::backward(int nimg, cudaStream_t st) {
     if (l == 0) break;
     // dL/d(input of layer l) masked by the ReLU that produced it
     bf16* Gn = dp<bf16>(gbuf[cur ^ 1]);
+    if (use_tc) {
+      SG_TRY(conv_tc_dgrad(l, G, wtcr[l].ptr, X, Gn, H, W, nimg, dp<int>(tcerr), wait_limit, st));
+      cur ^= 1;
+      continue;
+    }
     if (l == 4)
       k_conv<16, 32, 2><<<grid, 128, 0, st>>>(G, dp<bf16>(wr[l]), nullptr, X, Gn, nullptr, H, W);
     else

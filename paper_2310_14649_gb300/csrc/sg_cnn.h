@@ -7,6 +7,8 @@ namespace sg {
 
 struct MeanSolver;
 
+constexpr int kTcWaitDefault = 1 << 22;  // mbarrier polls before a tcgen05 kernel reports a timeout
+
 int64_t cnn_param_count();          // parameters in the oracle layout
 int64_t cnn_param_count_padded();   // parameters in the padded kernel layout
 
@@ -23,7 +25,9 @@ struct Cnn {
   int loss_kind = 0;                     // 0 energy norm of A_0, 1 relative L2 error
   bool use_tc = true;                    // forward on tcgen05 (false: mma.sync)
   DevBuf wtc[5];                         // BF16 weights in the tcgen05 plane layout
+  DevBuf wtcr[5];                        // flipped, transposed weights (input gradient), same layout
   DevBuf tcerr;                          // set by a tcgen05 kernel whose wait timed out
+  int wait_limit = kTcWaitDefault;       // mbarrier polls of a tcgen05 completion wait
   DevCsr A0;                             // fine mean matrix (energy loss)
   DevBuf ebuf, aebuf, azbuf;             // error, A_0 error, A_0 target (energy loss)
   Cnn() = default;
@@ -58,9 +62,11 @@ sg_status cnn_smooth(sg_problem* pr, const Precond& pc, const T* R, int64_t ld, 
 Precond& precond_of(sg_problem* pr);
 // tcgen05 forward convolution (sg_conv_tc.cu)
 sg_status conv_tc_attrs();
-sg_status conv_tc_pack(const float* Wsrc, int ci_pad, int co_pad, void* out, cudaStream_t st);
+sg_status conv_tc_pack(const float* Wsrc, int ci_pad, int co_pad, void* out, bool rev, cudaStream_t st);
+sg_status conv_tc_dgrad(int l, const void* G, const void* Wr, const void* mask, void* Yb, int H, int W, int nimg,
+                        int* err, int wait_limit, cudaStream_t st);
 sg_status conv_tc_layer(int l, const void* X, const void* Wp, const float* b, void* Yb, float* Yf, int H, int W,
-                        int nimg, int* err, cudaStream_t st);
+                        int nimg, int* err, int wait_limit, cudaStream_t st);
 // selects the learned smoother with damping omega (estimated when <= 0)
 sg_status learned_smoother_enable(sg_problem* pr, double omega, cudaStream_t st);
 // He-normal weights (std sqrt(2 / fan_in)), zero biases, in the oracle

@@ -29,7 +29,7 @@ using bf16 = __nv_bfloat16;
 
 constexpr int kHalo = 130;  // halo pixels per row: 128 outputs + 2
 constexpr int kRows = 4;    // output rows per CTA (TMEM: 32 columns each)
-constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before the error exit
+constexpr int kDrainLimit = 1 << 24;  // polls of the wait that follows a timed-out one
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -72,11 +72,16 @@ struct TcShape {
 };
 
 // EPI 0: bias + ReLU, BF16 out (CO = 32 channels); EPI 1: bias, FP32 out of
-// channel 0 (CO = 16)
+// channel 0 (CO = 16); EPI 2: times (mask > 0), the derivative of the ReLU
+// that produced the layer input, BF16 out (CO = 32): the input gradient
+// (the same convolution of the output gradient with the flipped,
+// transposed weights)
 template <int CI, int CO, int EPI>
 __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ X, const bf16* __restrict__ Wp,
-                                                 const float* __restrict__ bias, bf16* __restrict__ Yb,
-                                                 float* __restrict__ Yf, int H, int W, int* __restrict__ err) {
+                                                 const float* __restrict__ bias, const bf16* __restrict__ mask,
+                                                 bf16* __restrict__ Yb,
+                                                 float* __restrict__ Yf, int H, int W, int* __restrict__ err,
+                                                 int wait_limit) {
   using S = TcShape<CI, CO>;
   extern __shared__ __align__(128) uint8_t sm[];
   uint8_t* sB = sm;
@@ -142,19 +147,24 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ X, con
                      smem_u32(mbar))
                  : "memory");
   }
-  // accumulator complete (bounded wait; on a timeout the error flag is set
-  // and nothing is stored)
-  uint32_t done = 0;
-  for (int it = 0; it < kWaitLimit && !done; ++it)
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(mbar))
-        : "memory");
+  // accumulator complete (bounded wait of wait_limit polls; on a timeout
+  // the error flag is set and nothing is stored, and a second bounded wait
+  // lets the MMAs already issued finish before their tensor memory is freed)
+  auto poll = [&](int limit, uint32_t done) {
+    for (int it = 0; it < limit && !done; ++it)
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(smem_u32(mbar))
+          : "memory");
+    return done;
+  };
+  uint32_t done = poll(wait_limit, 0u);
   const bool ok = __all_sync(0xffffffffu, done != 0);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (!ok) {
     if (lane == 0) atomicExch(err, 1);
+    poll(kDrainLimit, done);
   } else {
     const int x = x0 + warp * 32 + lane;
 #pragma unroll 1
@@ -178,10 +188,27 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ X, con
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         if (store) {
           uint32_t o[16];
+          if (EPI == 0) {
 #pragma unroll
-          for (int c = 0; c < 16; ++c)
-            o[c] = pack_bf2(relu_nan(__uint_as_float(r[2 * c]) + bias[2 * c]),
-                            relu_nan(__uint_as_float(r[2 * c + 1]) + bias[2 * c + 1]));
+            for (int c = 0; c < 16; ++c)
+              o[c] = pack_bf2(relu_nan(__uint_as_float(r[2 * c]) + bias[2 * c]),
+                              relu_nan(__uint_as_float(r[2 * c + 1]) + bias[2 * c + 1]));
+          } else {
+            const uint4* mk = reinterpret_cast<const uint4*>(mask + pix * 32);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint4 mv = mk[q];
+              const uint32_t mw[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                const int c = 4 * q + h;
+                const float m0 = __bfloat162float(__ushort_as_bfloat16(uint16_t(mw[h] & 0xffffu)));
+                const float m1 = __bfloat162float(__ushort_as_bfloat16(uint16_t(mw[h] >> 16)));
+                o[c] = pack_bf2(m0 > 0.f ? __uint_as_float(r[2 * c]) : 0.f,
+                                m1 > 0.f ? __uint_as_float(r[2 * c + 1]) : 0.f);
+              }
+            }
+          }
           uint4* dst = reinterpret_cast<uint4*>(Yb + pix * 32);
 #pragma unroll
           for (int q = 0; q < 4; ++q) dst[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
@@ -206,22 +233,26 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ X, con
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(32 * kRows) : "memory");
 }
 
-// FP32 padded weights [tap][co][ci] -> BF16 planes [tap][ci / 8][co][8]
-__global__ void k_pack_planes(const float* __restrict__ Wsrc, int ci_pad, int co_pad, bf16* __restrict__ out) {
+// FP32 padded weights [tap][co][ci] -> BF16 planes [tap][ci / 8][co][8];
+// with rev, the flipped, transposed weights of the input gradient,
+// W'[8 - tap][ci][co] = W[tap][co][ci], as planes [tap'][co / 8][ci][8]
+__global__ void k_pack_planes(const float* __restrict__ Wsrc, int ci_pad, int co_pad, bf16* __restrict__ out,
+                              int rev) {
   const int total = 9 * co_pad * ci_pad;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int t = e / (co_pad * ci_pad), rem = e - t * co_pad * ci_pad;
     const int co = rem / ci_pad, ci = rem - co * ci_pad;
-    const size_t dst = ((size_t(t) * (ci_pad / 8) + ci / 8) * co_pad + co) * 8 + (ci % 8);
+    const size_t dst = rev ? ((size_t(8 - t) * (co_pad / 8) + co / 8) * ci_pad + ci) * 8 + (co % 8)
+                           : ((size_t(t) * (ci_pad / 8) + ci / 8) * co_pad + co) * 8 + (ci % 8);
     out[dst] = __float2bfloat16(Wsrc[e]);
   }
 }
 
 template <int CI, int CO, int EPI>
-sg_status launch_tc(const bf16* X, const bf16* Wp, const float* b, bf16* Yb, float* Yf, int H, int W, int nimg,
-                    int* err, cudaStream_t st) {
+sg_status launch_tc(const bf16* X, const bf16* Wp, const float* b, const bf16* mask, bf16* Yb, float* Yf, int H,
+                    int W, int nimg, int* err, int wait_limit, cudaStream_t st) {
   dim3 grid(unsigned((W + 127) / 128), unsigned((H + kRows - 1) / kRows), unsigned(nimg));
-  k_conv_tc<CI, CO, EPI><<<grid, 128, TcShape<CI, CO>::SMEM, st>>>(X, Wp, b, Yb, Yf, H, W, err);
+  k_conv_tc<CI, CO, EPI><<<grid, 128, TcShape<CI, CO>::SMEM, st>>>(X, Wp, b, mask, Yb, Yf, H, W, err, wait_limit);
   note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
@@ -238,12 +269,16 @@ sg_status conv_tc_attrs() {
                                TcShape<32, 32>::SMEM));
   SG_CUDA(cudaFuncSetAttribute(k_conv_tc<32, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                TcShape<32, 16>::SMEM));
+  SG_CUDA(cudaFuncSetAttribute(k_conv_tc<16, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcShape<16, 32>::SMEM));
+  SG_CUDA(cudaFuncSetAttribute(k_conv_tc<32, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcShape<32, 32>::SMEM));
   done = true;
   return SG_OK;
 }
 
-sg_status conv_tc_pack(const float* Wsrc, int ci_pad, int co_pad, void* out, cudaStream_t st) {
-  k_pack_planes<<<64, 256, 0, st>>>(Wsrc, ci_pad, co_pad, static_cast<bf16*>(out));
+sg_status conv_tc_pack(const float* Wsrc, int ci_pad, int co_pad, void* out, bool rev, cudaStream_t st) {
+  k_pack_planes<<<64, 256, 0, st>>>(Wsrc, ci_pad, co_pad, static_cast<bf16*>(out), rev ? 1 : 0);
   note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
@@ -251,12 +286,26 @@ sg_status conv_tc_pack(const float* Wsrc, int ci_pad, int co_pad, void* out, cud
 
 // layer l of the network: 0 (16 -> 32), 1..3 (32 -> 32), 4 (32 -> 16, FP32 out)
 sg_status conv_tc_layer(int l, const void* X, const void* Wp, const float* b, void* Yb, float* Yf, int H, int W,
-                        int nimg, int* err, cudaStream_t st) {
+                        int nimg, int* err, int wait_limit, cudaStream_t st) {
   const bf16* x = static_cast<const bf16*>(X);
   const bf16* w = static_cast<const bf16*>(Wp);
-  if (l == 0) return launch_tc<16, 32, 0>(x, w, b, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, st);
-  if (l == 4) return launch_tc<32, 16, 1>(x, w, b, nullptr, Yf, H, W, nimg, err, st);
-  return launch_tc<32, 32, 0>(x, w, b, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, st);
+  if (l == 0)
+    return launch_tc<16, 32, 0>(x, w, b, nullptr, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, wait_limit, st);
+  if (l == 4) return launch_tc<32, 16, 1>(x, w, b, nullptr, nullptr, Yf, H, W, nimg, err, wait_limit, st);
+  return launch_tc<32, 32, 0>(x, w, b, nullptr, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, wait_limit, st);
+}
+
+// input gradient of layer l (1..4): G (the output gradient, C_out(l)
+// channels) convolved with the flipped, transposed weights Wr, times the
+// ReLU derivative of the layer input (mask), into Yb (C_in(l) = 32 channels)
+sg_status conv_tc_dgrad(int l, const void* G, const void* Wr, const void* mask, void* Yb, int H, int W, int nimg,
+                        int* err, int wait_limit, cudaStream_t st) {
+  const bf16* g = static_cast<const bf16*>(G);
+  const bf16* w = static_cast<const bf16*>(Wr);
+  const bf16* mk = static_cast<const bf16*>(mask);
+  if (l == 4)
+    return launch_tc<16, 32, 2>(g, w, nullptr, mk, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, wait_limit, st);
+  return launch_tc<32, 32, 2>(g, w, nullptr, mk, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, wait_limit, st);
 }
 
 }  // namespace sg

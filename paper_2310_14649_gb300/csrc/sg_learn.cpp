@@ -115,6 +115,13 @@ sg_status sg_cnn_apply(sg_problem* pr, const float* R, int64_t ldr, float* Z, in
   return SG_OK;
 }
 
+sg_status sg_cnn_set_wait_limit(sg_problem* pr, int limit) {
+  SG_ARG(pr, "sg_cnn_set_wait_limit: NULL handle");
+  SG_TRY(ensure_cnn(pr));
+  pr->cnn->wait_limit = limit < 0 ? kTcWaitDefault : limit;
+  return SG_OK;
+}
+
 sg_status sg_cnn_set_kernel(sg_problem* pr, int kind) {
   SG_ARG(pr, "sg_cnn_set_kernel: NULL handle");
   SG_ARG(kind == 0 || kind == 1, "sg_cnn_set_kernel: kind must be 0 (mma.sync) or 1 (tcgen05)");

@@ -91,6 +91,33 @@ def test_forward_matches_oracle(pair, kernel):
     sg.sg_cnn_set_kernel(prob, 1)
 
 
+def test_tcgen05_wait_timeout_is_reported_and_recovers(pair):
+    """With a wait limit of 0 every tcgen05 CTA gives up on its completion
+    wait at once: sg_cnn_apply returns SG_ERR_TIMEOUT (the CTAs still wait,
+    bounded, for the MMAs they issued before freeing tensor memory), and the
+    next apply with the default limit gives the same output as before."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = pair
+    sg.sg_cnn_set_kernel(prob, 1)
+    sg.sg_cnn_set_weights(prob, params_for(7))
+    R = random_block(ref.n, ref.P, seed=79).astype(np.float32).astype(np.float64)
+    Rd = dev_rows(R)
+    Z1 = dev_rows(np.zeros((ref.n, ref.P)))
+    sg.sg_cnn_apply(prob, Rd, Z1)
+    try:
+        sg.sg_cnn_set_wait_limit(prob, 0)
+        with pytest.raises(sg.SgError) as e:
+            sg.sg_cnn_apply(prob, Rd, dev_rows(np.zeros((ref.n, ref.P))))
+        assert e.value.status == -5
+    finally:
+        sg.sg_cnn_set_wait_limit(prob, -1)
+    Z2 = dev_rows(np.zeros((ref.n, ref.P)))
+    sg.sg_cnn_apply(prob, Rd, Z2)
+    torch.cuda.synchronize()
+    assert torch.equal(Z1, Z2)
+
+
 def test_tcgen05_and_mma_sync_agree_on_large_images(gpu):
     """255 x 255 images (two 128-pixel row tiles, ragged last tile and row
     group) through both kernels: the FP32 sums of BF16 products agree."""

@@ -62,7 +62,10 @@ def test_learned_solve_matches_oracle(trained, mode):
 def test_trained_network_gains_over_untrained(trained):
     """Outer iterations to 1e-8 with the trained network against the same
     network at its He initialisation (no fallback in either), and against
-    the RAS smoother for reference."""
+    the method without the network (the RAS smoother): the network gains
+    over its untrained state, and its gap to RAS stays within a factor 2 of
+    the RAS iteration count (the measured gap, not a gain: a 3 x 3 network of
+    receptive field 11 replaces exact local solves on 36 x 36 boxes)."""
     import paper_2310_14649_gb300 as sg
     prob, c, _ = trained
     w_trained = sg.sg_cnn_get_weights(prob)
@@ -84,6 +87,7 @@ def test_trained_network_gains_over_untrained(trained):
     sg.sg_precond_set_smoother(prob, 1)
     assert its["trained"]["relres"] <= 1e-8
     assert its["trained"]["outer_it"] < its["untrained"]["outer_it"]
+    assert its["ras"]["outer_it"] <= its["trained"]["outer_it"] <= 2 * its["ras"]["outer_it"]
 
 
 def test_fallback_on_nan_weights(gpu):
