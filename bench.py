@@ -412,7 +412,9 @@ def large_workload(sg, torch, stream, reps=3):
            "mixed_ms": round(ms32, 2), "mixed_outer_it": info32["outer_it"], "mixed_relres": info32["relres"],
            "plain_fp64_ms": round(ms64, 2), "plain_fp64_outer_it": info64["outer_it"],
            "speedup_mixed": round(ms64 / ms32, 3),
-           "roofline": {"kernel": "sg_apply FP32 (fine Galerkin operator)", "bound": "hbm",
+           "apply_forms": apply_forms,
+        "roofline": {"kernel": "sg_apply FP32 (fine Galerkin operator, %s form)" % ("edge-flux" if flux_on else
+                                                                                    "five-slot"), "bound": "hbm",
                         "achieved": round(bytes_f32 / (avg * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(bytes_f32 / (avg * 1e-3) / 1e9 / peak, 4), "peak_source": peak_kind,
                         "bytes_per_launch": bytes_f32, "avg_launch_ms": avg, "launches": cnt},
@@ -584,8 +586,14 @@ def main():
     sg.sg_profile(prob, False)
 
     # roofline of the fine FP32 operator apply: algorithmic bytes per launch
+    # (five-slot form: values, pattern and blocks read once; edge-flux form:
+    # one conductance per edge and term, two indices per edge slot of a row)
     K, nnz = prob.K, prob.nnzA
-    bytes_f32 = K * nnz * 4 + nnz * 4 + (n + 1) * 4 + 2 * n * P * 4
+    flux_on = sg.sg_apply_flux(prob, -1)
+    N_ = c["N"]
+    bytes_slot = K * nnz * 4 + nnz * 4 + (n + 1) * 4 + 2 * n * P * 4
+    bytes_flux = K * 2 * N_ * (N_ - 1) * 4 + 4 * 2 * 4 * n + 2 * n * P * 4
+    bytes_f32 = bytes_flux if flux_on else bytes_slot
     cnt, kms = kinds["apply_fine_f32"]
     avg_ms = kms / max(cnt, 1)
     achieved = bytes_f32 / (avg_ms * 1e-3) / 1e9 if cnt else None
@@ -644,6 +652,22 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(world, g0.elapsed_time(g1) / args.steps)
 
+    # both storage forms of the fine FP32 apply, timed alone (20 launches
+    # after 3, CUDA events; values exceed L2, so no flush)
+    apply_forms = {}
+    Xa = torch.randn((P, n), dtype=torch.float32, device="cuda")
+    Ya = torch.empty_like(Xa)
+    chosen = sg.sg_apply_flux(prob, -1)
+    for form, mode in (("five_slot", 0), ("edge_flux", 1)):
+        sg.sg_apply_flux(prob, mode)
+        for _ in range(3):
+            sg.sg_apply(prob, Xa, Ya)
+        ms_a, _ = ev_time(torch, stream, lambda: [sg.sg_apply(prob, Xa, Ya) for _ in range(20)])
+        byt = bytes_flux if mode else bytes_slot
+        apply_forms[form] = {"ms": round(ms_a / 20, 5), "bytes": byt, "gbs": round(byt / (ms_a / 20 * 1e-3) / 1e9, 1)}
+    sg.sg_apply_flux(prob, 2)
+    sg.sg_apply_autotune(prob)                 # the tuned choice again (cached)
+    assert sg.sg_apply_flux(prob, -1) == chosen
     extras = {} if (args.no_extras or rank != 0) else extra_measurements(sg, torch, prob, stream)
     if not args.no_extras and rank == 0:
         extras["poisson512"] = large_workload(sg, torch, stream)
@@ -682,7 +706,9 @@ def main():
                              "mixed_ms": round(ms_paper32, 3), "mixed_outer_it": info_paper32["outer_it"],
                              "mixed_inner_it": info_paper32["inner_it"],
                              "plain_fp64_ms": round(ms_paper64, 3), "plain_fp64_outer_it": info_paper64["outer_it"]},
-        "roofline": {"kernel": "sg_apply FP32 (fine Galerkin operator)", "bound": "hbm",
+        "apply_forms": apply_forms,
+        "roofline": {"kernel": "sg_apply FP32 (fine Galerkin operator, %s form)" % ("edge-flux" if flux_on else
+                                                                                    "five-slot"), "bound": "hbm",
                      "achieved": round(achieved, 1) if achieved else None, "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
                      "peak_source": peak_kind, "bytes_per_launch": bytes_f32, "avg_launch_ms": avg_ms,

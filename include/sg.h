@@ -198,6 +198,26 @@ sg_status sg_apply_fp64_info(const sg_problem* prob, int* fine, int* coarse, int
 sg_status sg_apply_config(sg_problem* prob, int which, int rows, int groups, int igroups, int sgroups,
                           int prefetch, int min_blocks, int stages, int cgroups, int warps);
 
+/* Edge-flux form of the fine FP32 operator (Sec. 2.1, Eq. Galerkin_L_exp
+ * in Kronecker form, the stiffness written edge by edge): on this mesh the
+ * rows of every A_k are
+ *     (A_k x)_r = sum over the four edges (r, r') of w_k(r, r') (x_r - x_r'),
+ * x_r' = 0 at a Dirichlet node, with one conductance w_k per edge (half the
+ * sum of c_k over the two triangles sharing it).  Storing the K
+ * conductances of the 2 N (N - 1) edges instead of the K values of five
+ * stencil slots per node reads 2.5 times fewer matrix bytes per apply, and
+ * four edge passes replace five slot passes.  mode 0: the five-slot form
+ * (the autotuner may not choose the edge form); 1: the edge form now (its
+ * K x 2 N (N - 1) FP32 conductances are built on first use); 2 (default):
+ * the autotuner (sg_apply_autotune, fine FP32 family) times both forms and
+ * keeps the faster; -1: no change.  on (may be NULL) receives 1 when fine
+ * FP32 applies use the edge form.  sg_apply_config selects the slot form.
+ * Coarse and FP64 applies are unaffected.  A change drops recorded
+ * coarse-solve graphs; recorded batches of this problem then refuse to run.
+ * Errors: SG_ERR_ARG (mode out of range; mode 1 without the specialised
+ * kernel), SG_ERR_NOMEM, SG_ERR_CUDA. */
+sg_status sg_apply_flux(sg_problem* prob, int mode, int* on);
+
 /* Autotuner: compiles the candidate tile shapes, times each on this
  * problem's operator of family `which` (as for sg_apply_config; the
  * coarse families after sg_precond_setup) with CUDA events, keeps the fastest and stores

@@ -114,6 +114,7 @@ SIGNATURES = {
     "sg_apply_fp64_info": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), P_i64],
     "sg_apply_config": [vp] + [ctypes.c_int] * 10,
     "sg_apply_autotune": [vp, ctypes.c_int, ctypes.c_int, P_f64],
+    "sg_apply_flux": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "sg_apply_info": [vp, ctypes.c_int, P_i32, P_f64],
     "sg_launch_count": [P_i64],
     "sg_profile_read": [vp, ctypes.c_int, P_i64, P_f64],

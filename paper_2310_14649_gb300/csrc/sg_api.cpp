@@ -1,3 +1,4 @@
+#include <algorithm>
 // C ABI of libsg: argument checking and dispatch (declared in sg.h).
 #include <atomic>
 #include <cstring>
@@ -112,6 +113,25 @@ sg_status sg_apply_config(sg_problem* pr, int which, int rows, int groups, int i
   c.cgroups = cgroups;
   c.warps = warps;
   return jit_configure(pr, which, c);
+}
+
+sg_status sg_apply_flux(sg_problem* pr, int mode, int* on) {
+  SG_ARG(pr && mode >= -1 && mode <= 2, "sg_apply_flux: NULL handle or mode not in [-1, 2]");
+  if (mode >= 0) pr->flux_allowed = mode != 0;
+  if (mode == 0 || mode == 1) {
+    SG_ARG(jit_eligible(pr) || mode == 0, "sg_apply_flux: the edge-flux form needs the specialised kernel");
+    JitConfig c = pr->jit_cfg_set[0] ? pr->jit_cfg[0] : jit_default_config(pr, 0);
+    if (mode == 1 && (c.rows != 1 || c.stages != 0 || c.cgroups != 1)) {
+      c.rows = 1;
+      c.stages = 0;
+      c.cgroups = 1;
+      c.prefetch = std::max(c.prefetch, 8);
+    }
+    c.flux = mode;
+    if (pr->flux_on != c.flux || !pr->jit_cfg_set[0]) SG_TRY(jit_configure(pr, 0, c));
+  }
+  if (on) *on = pr->flux_on;
+  return SG_OK;
 }
 
 sg_status sg_apply_autotune(sg_problem* pr, int which, int force, double* best_ms) {

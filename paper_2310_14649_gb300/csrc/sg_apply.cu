@@ -306,8 +306,12 @@ sg_status apply_any(sg_problem* pr, bool coarse, const T* X, int64_t ldx, const 
       return apply_asm64(pr, A, B, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<const double*>(F),
                          ldf, reinterpret_cast<double*>(Y), ldy, st);
   }
-  if (pr->apply_mode != 1 && jit_eligible(pr))
-    return jit_apply_launch(pr, (coarse ? 1 : 0) + (sizeof(T) == 8 ? 2 : 0), A, X, ldx, F, ldf, Y, ldy, st);
+  if (pr->apply_mode != 1 && jit_eligible(pr)) {
+    // the edge-flux form of the fine FP32 operator when the family is configured for it
+    const bool flux = !coarse && sizeof(T) == 4 && pr->flux_on;
+    return jit_apply_launch(pr, (coarse ? 1 : 0) + (sizeof(T) == 8 ? 2 : 0), flux ? pr->flux : A, X, ldx, F, ldf, Y,
+                            ldy, st);
+  }
   return apply_ell<T>(A, coarse ? coarse_tri(pr) : pr->tri, pr->P, pr->K, X, ldx, F, ldf, Y, ldy, st);
 }
 

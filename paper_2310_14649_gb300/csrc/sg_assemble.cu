@@ -81,7 +81,82 @@ __global__ void k_fine_ell(const double* __restrict__ cb, int N, int64_t n, int6
   }
 }
 
+// Conductances of the edge-flux form for input terms [k0, k0 + kn): the
+// horizontal edge (i,j)-(i+1,j) (i = 0..N-1, j = 1..N-1) at (j-1) N + i,
+// half the sum of the lower triangle of cell (i,j) and the upper one of
+// cell (i,j-1); the vertical edge (i,j)-(i,j+1) (i = 1..N-1, j = 0..N-1) at
+// N (N-1) + j (N-1) + i - 1, half the sum of the upper triangle of cell
+// (i,j) and the lower one of cell (i-1,j).  A row of A_k is then the sum
+// over its four edges of w (x_r - x_neighbour) (the rows of the P1 element
+// matrices sum to zero).  Thread per (term, edge).
+__global__ void k_flux_values(const double* __restrict__ cb, int N, int64_t vkst, int k0, int kn,
+                              float* __restrict__ v32) {
+  const int m = N - 1;
+  const int64_t E = 2LL * N * N, ne = 2LL * N * m, total = int64_t(kn) * ne;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int kl = int(t / ne);
+    const int64_t e = t - int64_t(kl) * ne;
+    const double* c = cb + int64_t(kl) * E;
+    auto lo = [&](int ci, int cj) { return c[2LL * (int64_t(cj) * N + ci)]; };
+    auto up = [&](int ci, int cj) { return c[2LL * (int64_t(cj) * N + ci) + 1]; };
+    double v;
+    if (e < int64_t(N) * m) {
+      const int i = int(e % N), j = int(e / N) + 1;
+      v = 0.5 * (lo(i, j) + up(i, j - 1));
+    } else {
+      const int64_t e2 = e - int64_t(N) * m;
+      const int i = int(e2 % m) + 1, j = int(e2 / m);
+      v = 0.5 * (up(i, j) + lo(i - 1, j));
+    }
+    v32[int64_t(k0 + kl) * vkst + e] = float(v);
+  }
+}
+
 }  // namespace
+
+sg_status flux_build(sg_problem* pr) {
+  Ell& A = pr->flux;
+  if (A.v32.ptr) return SG_OK;
+  const int S = 4, K = pr->K, N = pr->N, m = N - 1;
+  const int64_t n = pr->n, E = pr->E, ldr = pr->fine.ldr, ne = 2LL * N * m;
+  A.S = S;
+  A.n = n;
+  A.ldr = ldr;
+  A.vkst = round_up(ne, 64);
+  std::vector<int32_t> col(size_t(S) * ldr, -1), vidx(size_t(S) * ldr, 0);
+  for (int64_t r = 0; r < n; ++r) {
+    const int i = int(r % m) + 1, j = int(r / m) + 1;
+    col[0 * ldr + r] = int32_t(i < m ? r + 1 : -1);
+    vidx[0 * ldr + r] = int32_t(int64_t(j - 1) * N + i);
+    col[1 * ldr + r] = int32_t(i > 1 ? r - 1 : -1);
+    vidx[1 * ldr + r] = int32_t(int64_t(j - 1) * N + i - 1);
+    col[2 * ldr + r] = int32_t(j < m ? r + m : -1);
+    vidx[2 * ldr + r] = int32_t(int64_t(N) * m + int64_t(j) * m + i - 1);
+    col[3 * ldr + r] = int32_t(j > 1 ? r - m : -1);
+    vidx[3 * ldr + r] = int32_t(int64_t(N) * m + int64_t(j - 1) * m + i - 1);
+  }
+  SG_TRY(A.col.alloc(col.size() * 4));
+  SG_TRY(A.vidx.alloc(vidx.size() * 4));
+  SG_CUDA(cudaMemcpy(A.col.ptr, col.data(), col.size() * 4, cudaMemcpyHostToDevice));
+  SG_CUDA(cudaMemcpy(A.vidx.ptr, vidx.data(), vidx.size() * 4, cudaMemcpyHostToDevice));
+  DevBuf v;
+  SG_TRY(v.alloc(size_t(K) * A.vkst * 4));
+  SG_CUDA(cudaMemset(v.ptr, 0, size_t(K) * A.vkst * 4));
+  const int KC = 32;
+  DevBuf dcb;
+  SG_TRY(dcb.alloc(size_t(KC) * E * sizeof(double)));
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    const int kn = std::min(KC, K - k0);
+    SG_TRY(element_coefficients(pr, k0, kn, dcb.as<double>(), nullptr));
+    k_flux_values<<<4 * 152, 256>>>(dcb.as<double>(), N, A.vkst, k0, kn, v.as<float>());
+    note_launch();
+    SG_CUDA(cudaGetLastError());
+  }
+  SG_CUDA(cudaDeviceSynchronize());
+  A.v32 = std::move(v);
+  return SG_OK;
+}
 
 sg_status assemble_fine(sg_problem* pr) {
   const int S = 5, K = pr->K, L = pr->L, N = pr->N;

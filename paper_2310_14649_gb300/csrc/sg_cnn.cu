@@ -8,10 +8,10 @@
 // to 16 or 32); weights are [tap][Cout][Cin] (Cin contiguous), FP32 master
 // copies with BF16 copies for the tensor cores; accumulation is FP32.
 //
-// With the tcgen05 kernels selected (default), the forward convolutions and
-// the input gradients run on the fifth-generation tensor cores
-// (sg_conv_tc.cu); the weight gradients, and everything with the legacy
-// kernels selected, run on the kernels below.
+// With the tcgen05 kernels selected (default), the forward convolutions,
+// the input gradients and the weight gradients run on the fifth-generation
+// tensor cores (sg_conv_tc.cu); with the legacy kernels selected they run on
+// the kernels below.
 // Convolutions are implicit GEMMs on the tensor cores (BF16 mma.sync
 // m16n8k16, FP32 accumulators): a CTA of 4 warps owns an 8 x 16 pixel tile,
 // the input tile with its 1-pixel halo and all 9 taps of the weights sit in
@@ -557,13 +557,15 @@ sg_status Cnn::backward(int nimg, cudaStream_t st) {
     float* db = dp<float>(grads) + boff[l];
     const bf16* X = dp<bf16>(act[l]);
     const bf16* G = dp<bf16>(gbuf[cur]);
-    if (l == 4)
+    if (use_tc)
+      SG_TRY(conv_tc_wgrad(l, X, G, dW, db, H, W, nimg, dp<int>(tcerr), wait_limit, st));
+    else if (l == 4)
       k_conv_wgrad<32, 16><<<wg_blocks, 128, 0, st>>>(X, G, dW, db, H, W, nimg);
     else if (l == 0)
       k_conv_wgrad<16, 32><<<wg_blocks, 128, 0, st>>>(X, G, dW, db, H, W, nimg);
     else
       k_conv_wgrad<32, 32><<<wg_blocks, 128, 0, st>>>(X, G, dW, db, H, W, nimg);
-    note_launch();
+    if (!use_tc) note_launch();
     SG_CUDA(cudaGetLastError());
     if (l == 0) break;
     // dL/d(input of layer l) masked by the ReLU that produced it

@@ -63,6 +63,8 @@ Precond& precond_of(sg_problem* pr);
 // tcgen05 forward convolution (sg_conv_tc.cu)
 sg_status conv_tc_attrs();
 sg_status conv_tc_pack(const float* Wsrc, int ci_pad, int co_pad, void* out, bool rev, cudaStream_t st);
+sg_status conv_tc_wgrad(int l, const void* X, const void* G, float* dW, float* db, int H, int W, int nimg, int* err,
+                        int wait_limit, cudaStream_t st);
 sg_status conv_tc_dgrad(int l, const void* G, const void* Wr, const void* mask, void* Yb, int H, int W, int nimg,
                         int* err, int wait_limit, cudaStream_t st);
 sg_status conv_tc_layer(int l, const void* X, const void* Wp, const float* b, void* Yb, float* Yf, int H, int W,

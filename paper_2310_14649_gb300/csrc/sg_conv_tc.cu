@@ -19,6 +19,8 @@
 // planes per tap.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "sg_cnn.h"
 
 namespace sg {
@@ -233,6 +235,203 @@ __global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ X, con
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(32 * kRows) : "memory");
 }
 
+// Weight gradient of a 3x3 convolution on the tensor cores:
+//     dW[dy dx][co][ci] = sum_pixels G[y][x][co] X[y + dy - 1][x + dx - 1][ci],
+//     db[co] = sum_pixels G[y][x][co],
+// as one implicit GEMM per tap row dy: D_dy[(dx, ci)][co] = sum_x A[(dx, ci)][x]
+// B[co][x], M = 3 C_in shifted input channels (+ a row of ones that yields
+// the bias gradient, the rest zero) padded to 128, N = C_out, K = the 128
+// pixels of one image-row segment.  A CTA walks down a strip of rows of one
+// 128-pixel column segment: input row y + 1 is transposed into one of three
+// rolling shared-memory slots (pixels along K, three copies shifted by dx),
+// so the rows y - 1, y and y + 1 that output row y needs are resident, and
+// the output-gradient row y is transposed into B.  The three accumulators
+// (one per dy) stay in tensor memory over the whole strip; the epilogue adds
+// them to the FP32 gradient with atomics.  Shared-memory operands are
+// K-major in the canonical layout (8-row x 16-byte core matrices; planes of
+// 8 pixels, rows 16 bytes apart).
+constexpr int kWgRows = 128;       // M rows of the A operand (padded)
+constexpr int kWgPix = 128;        // pixels per chunk (K)
+
+template <int CI, int CO>
+struct WgShape {
+  static constexpr int PLANE_A = kWgRows * 16;            // bytes per 8-pixel plane of A
+  static constexpr int SLOT = (kWgPix / 8) * PLANE_A;     // bytes per rolling input slot
+  static constexpr int PLANE_B = CO * 16;
+  static constexpr int SB = (kWgPix / 8) * PLANE_B;
+  static constexpr int ONES = 3 * CI;                     // the row of ones (bias gradient)
+  static constexpr int SMEM = 3 * SLOT + SB + 16;
+};
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) k_wgrad_tc(const bf16* __restrict__ X, const bf16* __restrict__ G,
+                                                  float* __restrict__ dW, float* __restrict__ db, int H, int W,
+                                                  int rows_per_cta, int* __restrict__ err, int wait_limit) {
+  using S = WgShape<CI, CO>;
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint8_t* sA = sm;
+  uint8_t* sB = sm + 3 * S::SLOT;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + S::SB);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * kWgPix, img = blockIdx.z;
+  const int ya = blockIdx.y * rows_per_cta, yb = min(H, ya + rows_per_cta);
+  const bf16* Ximg = X + size_t(img) * H * W * CI;
+  const bf16* Gimg = G + size_t(img) * H * W * CO;
+  // element (row m, pixel k) of slot s / of B (row co, pixel k)
+  auto a_off = [&](int s, int m, int k) { return s * S::SLOT + (k >> 3) * S::PLANE_A + (m >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2; };
+  auto b_off = [&](int co, int k) { return (k >> 3) * S::PLANE_B + (co >> 3) * 128 + (co & 7) * 16 + (k & 7) * 2; };
+  // zero every slot, then the row of ones
+  for (int e = tid; e < 3 * S::SLOT / 16; e += 128) reinterpret_cast<uint4*>(sA)[e] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  const bf16 one = __float2bfloat16(1.0f);
+  for (int e = tid; e < 3 * kWgPix; e += 128)
+    *reinterpret_cast<bf16*>(sA + a_off(e / kWgPix, S::ONES, e % kWgPix)) = one;
+  // input row r (zero outside the image) into slot (r + 3) % 3: position q
+  // (x = x0 + q - 1) feeds copies dx with pixel k = q - dx
+  auto stage_x = [&](int r) {
+    const int s = (r + 3) % 3;
+    for (int e = tid; e < (kWgPix + 2) * (CI / 8); e += 128) {
+      const int q = e / (CI / 8), c8 = e % (CI / 8);
+      const int x = x0 + q - 1;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (r >= 0 && r < H && x >= 0 && x < W) v = *reinterpret_cast<const uint4*>(Ximg + (size_t(r) * W + x) * CI + 8 * c8);
+      const bf16* hv = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int k = q - dx;
+        if (k < 0 || k >= kWgPix) continue;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) *reinterpret_cast<bf16*>(sA + a_off(s, dx * CI + 8 * c8 + c, k)) = hv[c];
+      }
+    }
+  };
+  auto stage_g = [&](int y) {
+    for (int e = tid; e < kWgPix * (CO / 8); e += 128) {
+      const int k = e / (CO / 8), c8 = e % (CO / 8);
+      const int x = x0 + k;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (x < W) v = *reinterpret_cast<const uint4*>(Gimg + (size_t(y) * W + x) * CO + 8 * c8);
+      const bf16* hv = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) *reinterpret_cast<bf16*>(sB + b_off(8 * c8 + c, k)) = hv[c];
+    }
+  };
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "n"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (ya < yb) {
+    stage_x(ya - 1);
+    stage_x(ya);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+  constexpr uint32_t idesc = inst_desc(128, CO);
+  auto poll = [&](int limit, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < limit && !done; ++it)
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(smem_u32(mbar)), "r"(parity)
+          : "memory");
+    return done;
+  };
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int y = ya; y < yb; ++y) {
+    stage_x(y + 1);
+    stage_g(y);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (tid == 0) {
+#pragma unroll 1
+      for (int dy = 0; dy < 3; ++dy) {
+        const int s = (y + dy - 1 + 3) % 3;
+#pragma unroll
+        for (int kc = 0; kc < kWgPix / 16; ++kc) {
+          const uint64_t ad = mat_desc(a0 + uint32_t(s * S::SLOT + 2 * kc * S::PLANE_A), S::PLANE_A, 128);
+          const uint64_t bd = mat_desc(b0 + uint32_t(2 * kc * S::PLANE_B), S::PLANE_B, 128);
+          const uint32_t acc = (y > ya || kc > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + uint32_t(dy * CO)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(mbar))
+                   : "memory");
+    }
+    // the MMAs read the slots and B: wait before the next staging
+    const uint32_t done = poll(wait_limit, phase);
+    ok = __syncthreads_and(done != 0) != 0;
+    phase ^= 1u;
+    if (!ok) {
+      if (tid == 0) atomicExch(err, 1);
+      poll(kDrainLimit, phase ^ 1u);   // the MMAs of this chunk, before tensor memory is freed
+      break;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (ok && ya < yb) {
+    // lanes = A rows m = dx C_in + ci (and the row of ones), columns = co
+    const int m = warp * 32 + lane;
+#pragma unroll 1
+    for (int dy = 0; dy < 3; ++dy) {
+      uint32_t r[CO];
+      const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16) + uint32_t(dy * CO);
+      if (CO == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16 % CO]), "=r"(r[17 % CO]), "=r"(r[18 % CO]), "=r"(r[19 % CO]), "=r"(r[20 % CO]),
+              "=r"(r[21 % CO]), "=r"(r[22 % CO]), "=r"(r[23 % CO]), "=r"(r[24 % CO]), "=r"(r[25 % CO]),
+              "=r"(r[26 % CO]), "=r"(r[27 % CO]), "=r"(r[28 % CO]), "=r"(r[29 % CO]), "=r"(r[30 % CO]),
+              "=r"(r[31 % CO])
+            : "r"(taddr)
+            : "memory");
+      } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (m < 3 * CI) {
+        const int dx = m / CI, ci = m % CI, t = dy * 3 + dx;
+#pragma unroll
+        for (int co = 0; co < CO; ++co) atomicAdd(dW + (size_t(t) * CO + co) * CI + ci, __uint_as_float(r[co]));
+      } else if (m == S::ONES && dy == 1) {
+#pragma unroll
+        for (int co = 0; co < CO; ++co) atomicAdd(db + co, __uint_as_float(r[co]));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(128) : "memory");
+}
+
 // FP32 padded weights [tap][co][ci] -> BF16 planes [tap][ci / 8][co][8];
 // with rev, the flipped, transposed weights of the input gradient,
 // W'[8 - tap][ci][co] = W[tap][co][ci], as planes [tap'][co / 8][ci][8]
@@ -273,6 +472,12 @@ sg_status conv_tc_attrs() {
                                TcShape<16, 32>::SMEM));
   SG_CUDA(cudaFuncSetAttribute(k_conv_tc<32, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                TcShape<32, 32>::SMEM));
+  SG_CUDA(cudaFuncSetAttribute(k_wgrad_tc<16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               WgShape<16, 32>::SMEM));
+  SG_CUDA(cudaFuncSetAttribute(k_wgrad_tc<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               WgShape<32, 32>::SMEM));
+  SG_CUDA(cudaFuncSetAttribute(k_wgrad_tc<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               WgShape<32, 16>::SMEM));
   done = true;
   return SG_OK;
 }
@@ -293,6 +498,32 @@ sg_status conv_tc_layer(int l, const void* X, const void* Wp, const float* b, vo
     return launch_tc<16, 32, 0>(x, w, b, nullptr, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, wait_limit, st);
   if (l == 4) return launch_tc<32, 16, 1>(x, w, b, nullptr, nullptr, Yf, H, W, nimg, err, wait_limit, st);
   return launch_tc<32, 32, 0>(x, w, b, nullptr, static_cast<bf16*>(Yb), nullptr, H, W, nimg, err, wait_limit, st);
+}
+
+template <int CI, int CO>
+sg_status launch_wgrad(const bf16* X, const bf16* G, float* dW, float* db, int H, int W, int nimg, int* err,
+                       int wait_limit, cudaStream_t st) {
+  const int xs = (W + kWgPix - 1) / kWgPix;
+  // about two CTAs per SM over the (column segment, row strip, image) grid
+  const int64_t strips = int64_t(xs) * nimg;
+  int rows = int(std::max<int64_t>(4, (int64_t(H) * strips + 2 * 152 - 1) / (2 * 152)));
+  rows = std::min(rows, H);
+  dim3 grid(unsigned(xs), unsigned((H + rows - 1) / rows), unsigned(nimg));
+  k_wgrad_tc<CI, CO><<<grid, 128, WgShape<CI, CO>::SMEM, st>>>(X, G, dW, db, H, W, rows, err, wait_limit);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+// weight and bias gradients of layer l, added to dW [tap][C_out][C_in] and
+// db (FP32, padded channel counts): X the layer input, G its output gradient
+sg_status conv_tc_wgrad(int l, const void* X, const void* G, float* dW, float* db, int H, int W, int nimg, int* err,
+                        int wait_limit, cudaStream_t st) {
+  const bf16* x = static_cast<const bf16*>(X);
+  const bf16* g = static_cast<const bf16*>(G);
+  if (l == 0) return launch_wgrad<16, 32>(x, g, dW, db, H, W, nimg, err, wait_limit, st);
+  if (l == 4) return launch_wgrad<32, 16>(x, g, dW, db, H, W, nimg, err, wait_limit, st);
+  return launch_wgrad<32, 32>(x, g, dW, db, H, W, nimg, err, wait_limit, st);
 }
 
 // input gradient of layer l (1..4): G (the output gradient, C_out(l)

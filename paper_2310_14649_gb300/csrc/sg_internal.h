@@ -83,6 +83,12 @@ struct Ell {
   DevBuf col;      // int32 S x ldr
   DevBuf v64;      // double K x S x ldr
   DevBuf v32;      // float  K x S x ldr
+  // edge-flux form (fine FP32 operator only): col[s * ldr + r] is the
+  // neighbour across edge s of row r or -1 (a Dirichlet node), vidx[s * ldr
+  // + r] the offset of that edge's conductance within a term's block, the
+  // conductances of term k at v32[k * vkst + vidx]
+  DevBuf vidx;     // int32 S x ldr
+  int64_t vkst = 0;
 };
 
 // The Galerkin operator summed per stencil edge into its P x P block (FP64),
@@ -156,7 +162,7 @@ struct ProfScope {
 // families: which = 0 fine FP32, 1 coarse FP32, 2 fine FP64, 3 coarse FP64.
 constexpr int kJitFamilies = 4;
 constexpr int kJitMaxP = 128;
-constexpr int kJitGeneratorVersion = 9;  // bump when the generated code changes
+constexpr int kJitGeneratorVersion = 10;  // bump when the generated code changes
 constexpr int64_t kJitMaxT = 40000;
 struct JitConfig {
   int rows = 1;        // rows per thread (2: paired FP32 FMA)
@@ -170,6 +176,8 @@ struct JitConfig {
   int cgroups = 1;     // output groups as separate 128-thread CTAs (no register cap from wide CTAs)
   int warps = 4;       // warps per group (rows per group = 32 x warps x rows): narrow groups keep
                        // several slot or input groups within one register-rich CTA
+  int flux = 0;        // 1: edge-flux form (fine FP32 family): y_r = sum over the four edges of
+                       // sum_k w_k G_k (x_r - x_neighbour), conductances stored once per edge
 };
 struct JitApply {
   cudaLibrary_t lib = nullptr;
@@ -208,6 +216,9 @@ struct sg_problem {
   sg::DevBuf mdot_partial, mdot_counter;  // scratch of sg_mdot
   int apply_mode = 0;                  // 0 auto, 1 shared-memory kernel, 2 specialised
   sg::AsmBlocks asm_fine;              // assembled FP64 blocks of the fine operator
+  sg::Ell flux;                        // edge-flux form of the fine operator (FP32 conductances)
+  int flux_on = 0;                     // fine FP32 applies use the edge-flux form
+  bool flux_allowed = true;            // the autotuner may choose the edge-flux form
   int asm_mode = 0;                    // FP64 applies: 0 auto, 1 never assembled, 2 always
 };
 
@@ -222,6 +233,9 @@ sg_status assemble_fine(sg_problem* pr);
 // lognormal input coefficients c_bar_k(e) of terms [k0, k0 + kn) at every
 // element, written as out[(k - k0) E + e] (FP64 device array); synchronous
 sg_status element_coefficients(sg_problem* pr, int k0, int kn, double* out, cudaStream_t st);
+// edge-flux form of the fine operator: neighbours, offsets and the FP32
+// conductances of every input term on every edge (allocated on first use)
+sg_status flux_build(sg_problem* pr);
 sg_status build_triple_tables(sg_problem* pr, TripleTables& t, int S);
 // apply (sg_apply.cu)
 template <typename T>

@@ -119,6 +119,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
   // coefficients as exact double immediates
   const char* T = fp64 ? "double" : "float";
   const std::string Ts = T;
+  const bool flux = c.flux != 0 && !fp64;
   const int mb = c.min_blocks, NG = HO * HI * SG, NPART = HI * SG, W = csplit ? 4 : c.warps;
   const std::vector<int> cut = output_split(pr, HO);
   std::vector<int> icut(HI + 1);
@@ -182,19 +183,29 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
       if (has_a[a]) body << "    " << ty << " y" << a << (R == 2 ? " = make_float2(0.f, 0.f);\n" : (fp64 ? " = 0.0;\n" : " = 0.f;\n"));
     body << "#pragma unroll 1\n"
             "    for (int s = " << (slot_only ? std::string("grp") : std::to_string(sgi)) << "; s < S; s += " << SG
-         << ") {\n"
-            "      const " << Ts << "* xp0 = X + col[(long long)s * ldr + rr];\n";
+         << ") {\n";
+    if (flux)
+      body << "      const int cn = col[(long long)s * ldr + rr];\n"
+              "      const float mk = cn >= 0 ? 1.f : 0.f;\n"
+              "      const float* xp0 = X + (cn >= 0 ? cn : rr);\n"
+              "      const float* xr0 = X + rr;\n";
+    else
+      body << "      const " << Ts << "* xp0 = X + col[(long long)s * ldr + rr];\n";
     if (R == 2) body << "      const float* xp1 = X + col[(long long)s * ldr + rr + 1];\n";
     for (int b = 0; b < P; ++b) {
       if (!need_b[b]) continue;
       if (R == 2)
         body << "      const float2 x" << b << " = make_float2(__ldg(xp0 + (long long)" << b
              << " * ldx), __ldg(xp1 + (long long)" << b << " * ldx));\n";
+      else if (flux)  // the difference across the edge: x_r - x_neighbour (0 at a Dirichlet node)
+        body << "      const float x" << b << " = fmaf(-mk, __ldg(xp0 + (long long)" << b
+             << " * ldx), __ldg(xr0 + (long long)" << b << " * ldx));\n";
       else
         body << "      const " << Ts << " x" << b << " = __ldg(xp0 + (long long)" << b << " * ldx);\n";
     }
     const bool staged = c.stages >= 2;
-    if (!staged) body << "      const " << Ts << "* vp = V + (long long)s * ldr + rr;\n";
+    if (!staged && flux) body << "      const float* vp = V + vidx[(long long)s * ldr + rr];\n";
+    else if (!staged) body << "      const " << Ts << "* vp = V + (long long)s * ldr + rr;\n";
     auto load = [&](int k) {
       if (R == 2)
         body << "      const float2 v" << k << " = __ldg(reinterpret_cast<const float2*>(vp + (long long)" << k
@@ -278,7 +289,8 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
   }
   std::ostringstream os;
   os << "// generated: Galerkin apply, P=" << P << " K=" << K << " T=" << pr->T << " R=" << R << " groups=" << HO
-     << "x" << HI << "x" << SG << " pf=" << pf << " mb=" << mb << (fp64 ? " fp64" : "") << "\n";
+     << "x" << HI << "x" << SG << " pf=" << pf << " mb=" << mb << (fp64 ? " fp64" : "") << (flux ? " flux" : "")
+     << "\n";
   os << (fp64 ? "#define GD(h) __longlong_as_double(h)\n" : "#define G(h) __int_as_float(h)\n");
   if (c.stages >= 2) {
     const int KB = std::max(1, pf);
@@ -318,11 +330,11 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
        << "(\n"
           "    const " << Ts << "* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
           "    const " << Ts << "* __restrict__ X, long long ldx, const " << Ts << "* __restrict__ F, long long ldf,\n"
-          "    " << Ts << "* __restrict__ Y, long long ldy) {\n"
+          "    " << Ts << "* __restrict__ Y, long long ldy, const int* __restrict__ vidx, long long vkst) {\n"
           "  const int grp = blockIdx.x % " << HO << ";\n"
           "  const int r = (blockIdx.x / " << HO << ") * 128 + threadIdx.x;\n"
           "  const int rr = r < n ? r : n - 1;\n"
-          "  const long long kst = (long long)S * ldr;\n";
+          "  const long long kst = vkst > 0 ? vkst : (long long)S * ldr;\n";
     os << body.str();
     os << "}\n";
     return os.str();
@@ -331,7 +343,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
      << (fp64 ? "sg_k1_f64" : "sg_k1") << "(\n"
         "    const " << Ts << "* __restrict__ V, const int* __restrict__ col, long long ldr, int n, int S,\n"
         "    const " << Ts << "* __restrict__ X, long long ldx, const " << Ts << "* __restrict__ F, long long ldf,\n"
-        "    " << Ts << "* __restrict__ Y, long long ldy) {\n"
+        "    " << Ts << "* __restrict__ Y, long long ldy, const int* __restrict__ vidx, long long vkst) {\n"
         "  extern __shared__ " << Ts << " smem[];\n"
         "  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
         "  const int grp = warp / " << W << ";\n"
@@ -339,7 +351,7 @@ std::string jit_apply_source(const sg_problem* pr, const JitConfig& c, bool fp64
      << 32 * R << " + lane * " << R << ";\n"
      << "  const int r = blockIdx.x * " << rows_cta << " + lrow;\n"
      << "  const int rr = r < n ? r : (n - 1) & ~" << (R - 1) << ";\n"
-     << "  const long long kst = (long long)S * ldr;\n";
+     << "  const long long kst = vkst > 0 ? vkst : (long long)S * ldr;\n";
   if (NG == 1) {
     os << "  " << Ts << "* part = smem;\n  (void)part;\n";
     if (c.stages >= 2)
@@ -482,23 +494,28 @@ sg_status jit_configure(sg_problem* pr, int which, const JitConfig& c) {
       (c.stages >= 2 && (c.rows != 1 || c.groups * c.igroups * c.sgroups != 1 || c.prefetch < 1)) ||
       c.cgroups < 1 || c.cgroups > 16 ||
       (c.cgroups > 1 && (c.rows != 1 || c.groups * c.igroups * c.sgroups != 1 || c.stages != 0)) ||
-      (c.warps != 1 && c.warps != 2 && c.warps != 4) || (c.warps != 4 && (c.stages != 0 || c.cgroups > 1))) {
+      (c.warps != 1 && c.warps != 2 && c.warps != 4) || (c.warps != 4 && (c.stages != 0 || c.cgroups > 1)) ||
+      (c.flux != 0 && c.flux != 1) ||
+      (c.flux == 1 && (which != 0 || c.rows != 1 || c.stages != 0 || c.cgroups != 1))) {
     set_error("sg_apply_config: rows in {1,2}; groups, igroups in [1,4]; sgroups in [1,8]; "
               "groups*igroups*sgroups <= 8; prefetch in [0,64]; min_blocks in [1,8]; FP64 families: rows 1; "
               "stages 0 or 2..8, staged only with one row and one group and prefetch >= 1; "
               "cgroups 1..16, split only with one row, one group and no staging; warps per group 1, 2 or 4, "
-              "fewer than 4 only without staging or separate CTAs");
+              "fewer than 4 only without staging or separate CTAs; flux (fine FP32 family only) with one row, "
+              "no staging and no separate CTAs");
     return SG_ERR_ARG;
   }
   if (jit_smem_bytes(pr, c, which >= 2) > 200 * 1024) {
     set_error("sg_apply_config: the input-group hand-off does not fit in shared memory");
     return SG_ERR_ARG;
   }
+  if (c.flux) SG_TRY(flux_build(pr));
   // recorded coarse-solve graphs reference the kernel about to be unloaded
-  if (pr->jit[which]) drop_recorded(pr);
+  if (pr->jit[which] || (which == 0 && pr->flux_on != c.flux)) drop_recorded(pr);
   jit_free(pr, which);
   pr->jit_cfg[which] = c;
   pr->jit_cfg_set[which] = true;
+  if (which == 0) pr->flux_on = c.flux;
   if (!jit_eligible(pr)) return SG_OK;
   return jit_apply_build(pr, which);
 }
@@ -518,9 +535,11 @@ static sg_status launch_kernel(cudaKernel_t kern, const JitConfig& c, size_t sme
   if (A.n == 0) return SG_OK;
   const T* V = sizeof(T) == 8 ? reinterpret_cast<const T*>(A.v64.ptr) : reinterpret_cast<const T*>(A.v32.ptr);
   const int* col = dp<int>(A.col);
-  long long ldr = A.ldr, lx = ldx, lf = ldf, ly = ldy;
+  const int* vidx = dp<int>(A.vidx);
+  long long ldr = A.ldr, lx = ldx, lf = ldf, ly = ldy, vkst = A.vkst;
   int n = int(A.n), S = A.S;
-  void* args[] = {(void*)&V, (void*)&col, &ldr, &n, &S, (void*)&X, &lx, (void*)&F, &lf, (void*)&Y, &ly};
+  void* args[] = {(void*)&V, (void*)&col, &ldr, &n, &S, (void*)&X, &lx, (void*)&F, &lf, (void*)&Y, &ly,
+                  (void*)&vidx, &vkst};
   const bool cs = c.cgroups > 1;
   const int64_t rows_per_cta = 32LL * (cs ? 4 : c.warps) * c.rows;
   dim3 grid(unsigned((A.n + rows_per_cta - 1) / rows_per_cta * (cs ? c.cgroups : 1))),
@@ -606,6 +625,17 @@ static std::vector<JitConfig> candidates(const sg_problem* pr, int which) {
     if (jit_smem_bytes(pr, c, fp64) > 200 * 1024) continue;
     out.push_back(c);
   }
+  // the fine FP32 family also in the edge-flux form (one row per thread,
+  // no staging, no separate CTAs)
+  if (which == 0 && !fp64 && pr->flux_allowed) {
+    const size_t nslot = out.size();
+    for (size_t i = 0; i < nslot; ++i) {
+      JitConfig c = out[i];
+      if (c.rows != 1 || c.stages != 0 || c.cgroups != 1) continue;
+      c.flux = 1;
+      out.push_back(c);
+    }
+  }
   if (out.empty()) out.push_back(jit_default_config(pr, which));
   return out;
 }
@@ -633,13 +663,13 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
     return SG_ERR_ARG;
   }
   const Ell& A = coarse ? coarse_ell(pr) : pr->fine;
-  const std::string path = cache_dir() + "/tune_" + tune_key(pr, A, fp64) + ".txt";
+  const std::string path = cache_dir() + "/tune_" + tune_key(pr, A, fp64) + (pr->flux_allowed ? "_fx" : "") + ".txt";
   if (!force) {
     std::ifstream in(path);
     JitConfig c;
     double ms = 0;
     if (in >> c.rows >> c.groups >> c.igroups >> c.sgroups >> c.prefetch >> c.min_blocks >> c.stages >> c.cgroups >>
-        c.warps >> ms) {
+        c.warps >> c.flux >> ms) {
       if (best_ms) *best_ms = ms;
       return jit_configure(pr, which, c);
     }
@@ -660,11 +690,13 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
   for (const JitConfig& c : candidates(pr, which)) {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
+    if (c.flux && flux_build(pr) != SG_OK) continue;
     if (jit_compile(jit_apply_source(pr, c, fp64), &lib, &kern, nullptr, nullptr, pr->device, fp64) != SG_OK) continue;
     const size_t sm = jit_smem_bytes(pr, c, fp64);
+    const Ell& Ac = c.flux ? pr->flux : A;
     auto run = [&]() {
-      return fp64 ? launch_kernel<double>(kern, c, sm, A, dp<double>(X), A.ldr, nullptr, 0, dp<double>(Y), A.ldr, st)
-                  : launch_kernel<float>(kern, c, sm, A, dp<float>(X), A.ldr, nullptr, 0, dp<float>(Y), A.ldr, st);
+      return fp64 ? launch_kernel<double>(kern, c, sm, Ac, dp<double>(X), A.ldr, nullptr, 0, dp<double>(Y), A.ldr, st)
+                  : launch_kernel<float>(kern, c, sm, Ac, dp<float>(X), A.ldr, nullptr, 0, dp<float>(Y), A.ldr, st);
     };
     std::vector<float> ts;
     for (int rep = 0; rep < 7 && status == SG_OK; ++rep) {
@@ -697,8 +729,8 @@ sg_status jit_autotune(sg_problem* pr, int which, int force, double* best_ms) {
   std::ofstream out(path);
   if (out)
     out << best.rows << " " << best.groups << " " << best.igroups << " " << best.sgroups << " " << best.prefetch
-        << " " << best.min_blocks << " " << best.stages << " " << best.cgroups << " " << best.warps << " " << best_t
-        << "\n";
+        << " " << best.min_blocks << " " << best.stages << " " << best.cgroups << " " << best.warps << " " << best.flux
+        << " " << best_t << "\n";
   return jit_configure(pr, which, best);
 }
 

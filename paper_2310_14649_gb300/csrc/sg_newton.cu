@@ -321,7 +321,9 @@ sg_status nl_ell(sg_problem* pr, const Tc* coef, Ell& A, cudaStream_t st) {
 template <typename T>
 sg_status nl_apply(sg_problem* pr, const Ell& A, const T* X, const T* F, T* Y, cudaStream_t st) {
   const int64_t ld = pr->ld;
-  if (pr->apply_mode != 1 && jit_eligible(pr))
+  // the fine FP32 family may be generated for the edge-flux storage, which
+  // these per-step value arrays do not have: the shared-memory kernel then
+  if (pr->apply_mode != 1 && jit_eligible(pr) && !(sizeof(T) == 4 && pr->flux_on))
     return jit_apply_launch(pr, sizeof(T) == 8 ? 2 : 0, A, X, ld, F, ld, Y, ld, st);
   return apply_ell<T>(A, pr->tri, pr->P, pr->K, X, ld, F, ld, Y, ld, st);
 }

@@ -233,7 +233,10 @@ def test_autotune_picks_a_valid_shape(gpu):
     ms = sg.sg_apply_autotune(prob, force=True)
     info = sg.sg_apply_info(prob)
     assert ms > 0 and info["rows"] in (1, 2) and 1 <= info["groups"] <= 4
-    check_apply(prob, ref, random_block(ref.n, ref.P, seed=14), torch.float32, kernel=2)
+    if sg.sg_apply_flux(prob, -1):     # the tuner chose the edge-flux form
+        check_flux(prob, ref, random_block(ref.n, ref.P, seed=14).astype(np.float32).astype(np.float64))
+    else:
+        check_apply(prob, ref, random_block(ref.n, ref.P, seed=14), torch.float32, kernel=2)
     ms64 = sg.sg_apply_autotune(prob, force=True, which=2)
     assert ms64 > 0 and sg.sg_apply_info(prob, which=2)["rows"] == 1
     check_apply(prob, ref, random_block(ref.n, ref.P, seed=17), torch.float64, kernel=2)
@@ -259,3 +262,65 @@ def test_mdot(gpu, dt, nv, length):
     bound = np.abs(Vh) @ np.abs(wh)
     u = U64 if dt == "f64" else U32
     assert np.all(np.abs(out.cpu().numpy() - refv) <= gamma(8 if dt == "f32" else 1, u) * bound + 1e-12 * bound)
+
+
+def flux_bound(ref, X):
+    """Rounding scale of the edge-flux form: sum over the four edges of
+    sum_k |w_k| |G_k| (|x_r| + |x_neighbour|), the conductances w_k of the
+    oracle's element coefficients (half the sum over the two triangles of
+    each edge), and the largest number of products summed into one output."""
+    N, m, n = ref.N, ref.N - 1, ref.n
+    c = ref.cbar                                              # [K, E]
+    lo = c[:, 0::2].reshape(ref.K, N, N)                      # [k, j, i] lower triangle of cell (i, j)
+    up = c[:, 1::2].reshape(ref.K, N, N)
+    i = np.tile(np.arange(1, N), m)
+    j = np.repeat(np.arange(1, N), m)
+    east = 0.5 * (lo[:, j, i] + up[:, j - 1, i])
+    west = 0.5 * (lo[:, j, i - 1] + up[:, j - 1, i - 1])
+    north = 0.5 * (up[:, j, i] + lo[:, j, i - 1])
+    south = 0.5 * (up[:, j - 1, i] + lo[:, j - 1, i - 1])
+    r = np.arange(n)
+    Xa = np.abs(X)
+    zero = np.zeros((1, ref.P))
+    Xp = np.vstack([Xa, zero])
+    nb = {"e": np.where(i < m, r + 1, n), "w": np.where(i > 1, r - 1, n),
+          "n": np.where(j < m, r + m, n), "s": np.where(j > 1, r - m, n)}
+    G = np.abs(ref.G())
+    bound = np.zeros((n, ref.P))
+    for key, w in (("e", east), ("w", west), ("n", north), ("s", south)):
+        D = Xa + Xp[nb[key]]
+        for k in range(ref.K):
+            bound += np.abs(w[k])[:, None] * (D @ G[k].T)
+    per_a = np.bincount(ref.kab[:, 1], minlength=ref.P).max()
+    return bound, int(4 * 2 * per_a)
+
+
+@pytest.mark.parametrize("N,L,p,q", [(32, 2, 2, 4), (64, 4, 3, 6), (29, 3, 2, 4)])
+def test_flux_apply_matches_oracle(gpu, N, L, p, q):
+    """The edge-flux form of the fine FP32 operator (conductances per edge,
+    y_r = sum over edges of sum_k w_k G_k (x_r - x_neighbour)) against the
+    oracle's operator, elementwise within its rounding bound; switching back
+    restores the five-slot form."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(N, L, p, q)
+    X = random_block(ref.n, ref.P, seed=55).astype(np.float32).astype(np.float64)
+    try:
+        assert sg.sg_apply_flux(prob, 1) == 1
+        check_flux(prob, ref, X)
+    finally:
+        assert sg.sg_apply_flux(prob, 0) == 0
+    prob.close()
+
+
+def check_flux(prob, ref, X):
+    import torch
+    import paper_2310_14649_gb300 as sg
+    Yr = galerkin.apply(ref, X)
+    Xd = to_dev(X, torch.float32, ref.n + 7)
+    Yd = torch.full((ref.P, ref.n + 3), float("nan"), dtype=torch.float32, device="cuda")
+    sg.sg_apply(prob, Xd, Yd)
+    Y = from_dev(Yd, ref.n)
+    bound, m = flux_bound(ref, X)
+    assert np.all(np.abs(Y - Yr) <= gamma(m, U32) * bound + 1e-30)
+    assert np.linalg.norm(Y - Yr) <= 1e-5 * np.linalg.norm(Yr)

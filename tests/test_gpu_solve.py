@@ -260,3 +260,22 @@ def test_paper_verification_setting(gpu, mode):
     assert prob.P == 20 and prob.K == 10
     assert info["relres"] <= 1e-10
     assert np.linalg.norm(Xh - Xd) / np.linalg.norm(Xd) <= 1e-8
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_solve_with_flux_apply(gpu, mode):
+    """Solves with the edge-flux form of the fine FP32 operator reach the
+    same relres and the oracle's solution (the FP64 residual of the
+    refinement keeps its own form)."""
+    import paper_2310_14649_gb300 as sg
+    c = dict(N=64, L=4, p=3, q=6, sigma2=0.3, b=0.5, sx=2, sy=2, overlap=2)
+    prob = setup(c)
+    ref = galerkin.build(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"], c["b"])
+    Xo, _, _ = galerkin.solve_gmres(ref, tol=1e-12)
+    assert sg.sg_apply_flux(prob, 1) == 1
+    X = zeros(prob)
+    info = sg.sg_solve(prob, X, rtol=1e-8, mode=mode)
+    Xh = to_np(X, prob.n)
+    assert info["relres"] <= 1e-8
+    assert np.linalg.norm(Xh - Xo) / np.linalg.norm(Xo) <= 1e-7
+    prob.close()
