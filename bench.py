@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and learned-smoother measurements")
     ap.add_argument("--only-timed", action="store_true",
                     help="the timed mixed solves only (no comparison solves, e2e or extras): for launch lists")
+    ap.add_argument("--kernel-case", default=None,
+                    choices=["apply_slot", "apply_flux", "cnn_train", "nl_coef", "sample", "ras"],
+                    help="run a few launches of one kernel on a small case and exit (for profiler captures)")
     return ap.parse_args()
 
 
@@ -499,8 +502,57 @@ def verification_workload(sg, torch, stream, S=40000):
     return out
 
 
+def kernel_case(name):
+    """A few launches of one kernel family on a case small enough for a
+    full profiler capture (inputs still larger than L2 where that matters)."""
+    import numpy as np
+    import torch
+    import paper_2310_14649_gb300 as sg
+    from sg_inputs import CONFIGS
+    torch.cuda.set_device(0)
+    c = CONFIGS[WORKLOAD]
+    if name in ("apply_slot", "apply_flux", "ras"):
+        prob = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
+        sg.sg_apply_autotune(prob)
+        X = torch.randn((prob.P, prob.n), dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(X)
+        if name == "ras":
+            sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL)
+            for _ in range(3):
+                sg.sg_precond_apply(prob, sg.PC_RAS_LOCAL, X, Y)
+        else:
+            sg.sg_apply_flux(prob, 1 if name == "apply_flux" else 0)
+            for _ in range(3):
+                sg.sg_apply(prob, X, Y)
+    elif name == "cnn_train":
+        prob = sg.sg_setup(256, 2, 1, 2)
+        sg.sg_cnn_init(prob, seed=1)
+        R = torch.randn((32, prob.n), dtype=torch.float32, device="cuda")
+        Z = torch.randn_like(R)
+        for _ in range(2):
+            sg.sg_cnn_train_step(prob, R, Z, lr=1e-3, update=True)
+    elif name == "nl_coef":
+        c5 = CONFIGS["poisson384_L4_p4"]
+        prob = sg.sg_setup(128, c5["L"], c5["p"], c5["q"], sigma2=c5["sigma2"], bx=c5["b"], by=c5["b"])
+        U = 0.05 * torch.randn((prob.P, prob.n), dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(U)
+        for _ in range(3):
+            sg.sg_nonlinear_jacobian_apply(prob, U, U, Y)
+    elif name == "sample":
+        prob = sg.sg_setup(100, 3, 3, 2, sigma2=0.01, bx=0.5, by=0.5)
+        xi = torch.from_numpy(np.random.default_rng(1).standard_normal((304, 3))).cuda()
+        U = torch.empty((304, prob.n), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            sg.sg_sample_solve(prob, xi, U)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": name, "ok": True}))
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        kernel_case(args.kernel_case)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

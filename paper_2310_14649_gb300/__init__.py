@@ -17,7 +17,8 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel", "sg_set_apply_fp64",
            "sg_apply_fp64_info", "sg_precond_save", "sg_precond_load", "sg_fourfold_products",
-           "sg_newton", "sg_nonlinear_residual", "sg_nonlinear_jacobian_apply", "sg_sample_solve", "sg_cnn_set_wait_limit", "sg_apply_flux",
+           "sg_newton", "sg_nonlinear_residual", "sg_nonlinear_jacobian_apply", "sg_sample_solve",
+           "sg_cnn_set_wait_limit", "sg_apply_flux",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
@@ -281,7 +282,7 @@ def sg_sample_solve(prob, xi, U, rtol=1e-6, max_it=2000, stream=None, allow_not_
         raise ValueError("U must be [S, ld >= n] with unit column stride")
     its = ctypes.c_int(0)
     allow = (0, 1) if allow_not_converged else (0,)
-    call("sg_sample_solve", "sg_cnn_set_wait_limit", "sg_apply_flux", prob.handle, dev_ptr(xi), xi.shape[0], _dtype_code(U), dev_ptr(U), U.stride(0),
+    call("sg_sample_solve", prob.handle, dev_ptr(xi), xi.shape[0], _dtype_code(U), dev_ptr(U), U.stride(0),
          ctypes.c_double(rtol), max_it, ctypes.byref(its), stream_handle(stream), allow=allow)
     return its.value
 
