@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and learned-smoother measurements")
     ap.add_argument("--only-timed", action="store_true",
                     help="the timed mixed solves only (no comparison solves, e2e or extras): for launch lists")
+    ap.add_argument("--host-loops", action="store_true",
+                    help="coarse GMRES driven from the host (every kernel a separate launch): for launch lists")
     ap.add_argument("--kernel-case", default=None,
                     choices=["apply_slot", "apply_flux", "cnn_train", "nl_coef", "sample", "ras"],
                     help="run a few launches of one kernel on a small case and exit (for profiler captures)")
@@ -54,25 +56,27 @@ def parse():
 
 
 def measured_traffic(shape):
-    """DRAM bytes per launch of the fine apply from the committed ncu
-    summary, when it was taken on the same generated kernel (same tile shape
-    and code-generator version); otherwise None."""
-    path = os.path.join(ROOT, "profiles", "sg_k1_poisson256_L4_p3.md")
-    try:
-        text = open(path).read()
-    except OSError:
-        return None
-    vals = {}
-    for line in text.splitlines():
-        if line.startswith("traffic-key:"):
-            for kv in line.split(":", 1)[1].split():
-                k, v = kv.split("=")
-                vals[k] = v
-    key = {k: str(shape[k]) for k in ("rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "stages",
-                                      "cgroups", "warps", "generator")}
-    if not vals or any(vals.get(k) != v for k, v in key.items()):
-        return None
-    return int(vals["bytes"])
+    """DRAM bytes per launch of the fine apply from a committed ncu summary
+    (profiles/sg_k1*_poisson256_L4_p3.md) taken on the same generated kernel
+    (tile shape, storage form and code-generator version); otherwise None."""
+    import glob
+    keys = ("rows", "groups", "igroups", "sgroups", "prefetch", "min_blocks", "stages", "cgroups", "warps",
+            "generator", "flux")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "sg_k1*_poisson256_L4_p3.md"))):
+        try:
+            text = open(path).read()
+        except OSError:
+            continue
+        vals = {}
+        for line in text.splitlines():
+            if line.startswith("traffic-key:"):
+                for kv in line.split(":", 1)[1].split():
+                    k, v = kv.split("=")
+                    vals[k] = v
+        vals.setdefault("flux", "0")
+        if vals and all(vals.get(k) == str(shape.get(k, 0)) for k in keys):
+            return int(vals["bytes"])
+    return None
 
 
 def peaks():
@@ -415,9 +419,7 @@ def large_workload(sg, torch, stream, reps=3):
            "mixed_ms": round(ms32, 2), "mixed_outer_it": info32["outer_it"], "mixed_relres": info32["relres"],
            "plain_fp64_ms": round(ms64, 2), "plain_fp64_outer_it": info64["outer_it"],
            "speedup_mixed": round(ms64 / ms32, 3),
-           "apply_forms": apply_forms,
-        "roofline": {"kernel": "sg_apply FP32 (fine Galerkin operator, %s form)" % ("edge-flux" if flux_on else
-                                                                                    "five-slot"), "bound": "hbm",
+           "roofline": {"kernel": "sg_apply FP32 (fine Galerkin operator, five-slot form)", "bound": "hbm",
                         "achieved": round(bytes_f32 / (avg * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(bytes_f32 / (avg * 1e-3) / 1e9 / peak, 4), "peak_source": peak_kind,
                         "bytes_per_launch": bytes_f32, "avg_launch_ms": avg, "launches": cnt},
@@ -573,7 +575,7 @@ def main():
     tune_ms = sg.sg_apply_autotune(prob)       # cached after the first run
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
-    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL)
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL, host_loops=args.host_loops)
     torch.cuda.synchronize()
     t_pc = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -612,7 +614,8 @@ def main():
         line = {"metric": METRIC, "value": round(ms_all, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_all, 3), "higher_is_better": False,
                 "scaling": "weak", "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "coarse_inner_rtol": INNER_RTOL, "only_timed": True},
+                "config": {"workload": WORKLOAD, "coarse_inner_rtol": INNER_RTOL, "only_timed": True,
+                           "coarse_loops": "host" if args.host_loops else "graph"},
                 "gpu_launches": int(launches)}
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -764,7 +767,8 @@ def main():
                      "achieved": round(achieved, 1) if achieved else None, "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
                      "peak_source": peak_kind, "bytes_per_launch": bytes_f32, "avg_launch_ms": avg_ms,
-                     "launches": cnt, "traffic": measured_traffic(sg.sg_apply_info(prob))},
+                     "launches": cnt,
+                     "traffic": measured_traffic(dict(sg.sg_apply_info(prob), flux=flux_on))},
         "roofline_top_kernel": {"kernel": "k_ras_local FP32 (RAS line solves, %d boxes, line width %d)"
                                           % (ras_boxes, ras_w),
                                 "bound": "alu", "achieved": round(ras_tflops, 2) if ras_tflops else None,
