@@ -281,7 +281,15 @@ typedef struct {
                           1 = tensor cores (m16n8k8 TF32 MMA with operands
                           split into high and remainder parts, FP32
                           accumulation; 8 modes per CTA unless ras_modes
-                          is given).  FP64 data always use the FMA kernel. */
+                          is given); 2 = explicit local inverses: the owned
+                          rows of each (I (x) A_{0,i})^{-1}, formed at setup
+                          in FP64 from the line factors and stored in FP32
+                          (boxes wider than twice the overlap, P <= 96),
+                          applied as dense products on the tcgen05 tensor
+                          cores (kind::tf32, operands split into high and
+                          remainder parts, FP32 accumulation in tensor
+                          memory) with the Kronecker factor fused.  FP64
+                          data always use the FMA kernel. */
 } sg_precond_opts;
 
 /* Builds partitions, local factors, the coarse space, the AMG hierarchy,
@@ -499,14 +507,15 @@ sg_status sg_cnn_train_step(sg_problem* prob, const float* R_dev, int64_t ldr, c
  * SG_ERR_TIMEOUT if a tcgen05 completion wait ran out (no output then). */
 sg_status sg_cnn_set_kernel(sg_problem* prob, int kind);
 
-/* Plumbing.  Polls of the mbarrier on which a tcgen05 forward-convolution
- * CTA waits for its MMAs before it gives up (limit < 0: the default,
+/* Plumbing.  Polls of the mbarrier on which a tcgen05 CTA of this handle
+ * (the network's convolutions, the RAS products with explicit local
+ * inverses) waits for its MMAs before it gives up (limit < 0: the default,
  * 4,194,304 polls).  A CTA whose wait runs out stores nothing, sets an
- * error flag that sg_cnn_apply returns as SG_ERR_TIMEOUT, and then waits
- * again (bounded) for the MMAs it issued before it frees their tensor
- * memory, so the context stays usable.  limit = 0 makes every wait run out
- * at once (for tests of that path). */
-sg_status sg_cnn_set_wait_limit(sg_problem* prob, int limit);
+ * error flag that sg_cnn_apply, sg_precond_apply and sg_solve return as
+ * SG_ERR_TIMEOUT, and then waits again (bounded) for the MMAs it issued
+ * before it frees their tensor memory, so the context stays usable.
+ * limit = 0 makes every such wait run out at once (for tests of that path). */
+sg_status sg_set_wait_limit(sg_problem* prob, int limit);
 
 /* Loss of sg_cnn_train_step: 0 (default) sum_a (e_a^T A_0 e_a) /
  * (z*_a^T A_0 z*_a), e_a = y_a - z*_a / rms(r_a): the error in the energy

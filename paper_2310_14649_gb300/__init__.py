@@ -18,7 +18,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel", "sg_set_apply_fp64",
            "sg_apply_fp64_info", "sg_precond_save", "sg_precond_load", "sg_fourfold_products",
            "sg_newton", "sg_nonlinear_residual", "sg_nonlinear_jacobian_apply", "sg_sample_solve",
-           "sg_cnn_set_wait_limit", "sg_apply_flux",
+           "sg_set_wait_limit", "sg_apply_flux",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
            "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
@@ -481,10 +481,11 @@ def sg_cnn_set_kernel(prob, kind):
     call("sg_cnn_set_kernel", prob.handle, kind)
 
 
-def sg_cnn_set_wait_limit(prob, limit=-1):
-    """Polls of a tcgen05 completion wait before SG_ERR_TIMEOUT (-1:
-    default; 0: every wait runs out at once)."""
-    call("sg_cnn_set_wait_limit", prob.handle, limit)
+def sg_set_wait_limit(prob, limit=-1):
+    """Polls of a tcgen05 completion wait (network convolutions, RAS
+    inverse products) before SG_ERR_TIMEOUT (-1: default; 0: every wait
+    runs out at once)."""
+    call("sg_set_wait_limit", prob.handle, limit)
 
 
 def sg_cnn_set_loss(prob, kind):

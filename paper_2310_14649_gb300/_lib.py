@@ -103,7 +103,7 @@ SIGNATURES = {
     "sg_set_apply_kernel": [vp, ctypes.c_int],
     "sg_set_apply_fp64": [vp, ctypes.c_int],
     "sg_precond_save": [vp, vp, P_i64],
-    "sg_cnn_set_wait_limit": [vp, ctypes.c_int],
+    "sg_set_wait_limit": [vp, ctypes.c_int],
     "sg_newton": [vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, vp, vp, vp],
     "sg_nonlinear_residual": [vp, vp, i64, vp, i64, vp, i64, vp],
     "sg_sample_solve": [vp, vp, i64, ctypes.c_int, vp, i64, ctypes.c_double, ctypes.c_int,

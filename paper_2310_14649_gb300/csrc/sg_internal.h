@@ -219,6 +219,7 @@ struct sg_problem {
   sg::Ell flux;                        // edge-flux form of the fine operator (FP32 conductances)
   int flux_on = 0;                     // fine FP32 applies use the edge-flux form
   bool flux_allowed = true;            // the autotuner may choose the edge-flux form
+  int wait_limit = 1 << 22;            // mbarrier polls of a tcgen05 completion wait
   int asm_mode = 0;                    // FP64 applies: 0 auto, 1 never assembled, 2 always
 };
 

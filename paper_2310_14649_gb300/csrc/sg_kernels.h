@@ -25,6 +25,14 @@ template <typename T>
 // (slot stride stride2, the same leading dimension)
 sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st, T* Z2 = nullptr,
                          int64_t stride2 = 0, const int* j2 = nullptr);
+// RAS local solves by explicit local inverses on tcgen05 (sg_ras_tc.cu):
+// built at setup for ras_kernel 2 (FP32 data; P <= 96), applied with the
+// Kronecker factor M fused when transform
+bool ras_inverse_supported(int P);
+sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st);
+sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld, float* Z, const float* M,
+                            bool transform, int wait_limit, cudaStream_t st);
+sg_status ras_inverse_check(const Precond& pc, cudaStream_t st);
 template <typename T>
 sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T* out = nullptr, int64_t ldo = 0);
 sg_status frobenius_weights(sg_problem* pr, std::vector<double>& w);

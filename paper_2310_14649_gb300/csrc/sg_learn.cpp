@@ -33,6 +33,7 @@ sg_status ensure_cnn(sg_problem* pr) {
     delete c;
     return s;
   }
+  c->wait_limit = pr->wait_limit;
   pr->cnn = c;
   return SG_OK;
 }
@@ -115,10 +116,11 @@ sg_status sg_cnn_apply(sg_problem* pr, const float* R, int64_t ldr, float* Z, in
   return SG_OK;
 }
 
-sg_status sg_cnn_set_wait_limit(sg_problem* pr, int limit) {
-  SG_ARG(pr, "sg_cnn_set_wait_limit: NULL handle");
-  SG_TRY(ensure_cnn(pr));
-  pr->cnn->wait_limit = limit < 0 ? kTcWaitDefault : limit;
+sg_status sg_set_wait_limit(sg_problem* pr, int limit) {
+  SG_ARG(pr, "sg_set_wait_limit: NULL handle");
+  pr->wait_limit = limit < 0 ? kTcWaitDefault : limit;
+  if (pr->cnn) pr->cnn->wait_limit = pr->wait_limit;
+  if (pr->solver) precond_of(pr).wait_limit = pr->wait_limit;
   return SG_OK;
 }
 

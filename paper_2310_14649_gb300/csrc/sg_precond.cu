@@ -699,6 +699,16 @@ template <typename T>
 sg_status ras_apply(const Precond& pc, int64_t n, int P, const T* R, int64_t ld, T* Z, cudaStream_t st,
                     bool transform, Profiler* prof) {
   const RasData& D = pc.ras;
+  if (sizeof(T) == 4 && pc.ras_kernel == 2 && D.d_inv.ptr) {
+    // explicit local inverses on tcgen05, the Kronecker factor fused
+    size_t slot = 0;
+    const bool timed = prof && prof->on;
+    if (timed) SG_TRY(prof->begin(4, st, slot));
+    SG_TRY(ras_inverse_apply(pc, P, reinterpret_cast<const float*>(R), ld, reinterpret_cast<float*>(Z),
+                             reinterpret_cast<const float*>(pc.gtinv32.ptr), transform, pc.wait_limit, st));
+    if (timed) SG_TRY(prof->end(slot, st));
+    return SG_OK;
+  }
   if (sizeof(T) == 4 && pc.ras_kernel == 1) {
     // tensor-core kernel: 8 modes per CTA by default (one 8-wide MMA tile;
     // 64 boxes x 5 chunks of a 35-mode problem are 320 CTAs of 73 KB, all

@@ -227,7 +227,9 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
          "sg_precond_setup: subdomain counts must be in [1, N-1]");
   SG_ARG(o->overlap >= 0 && o->overlap <= 8, "sg_precond_setup: overlap must be in [0, 8]");
   SG_ARG(o->amg_kernel == 0 || o->amg_kernel == 1, "sg_precond_setup: amg_kernel must be 0 or 1");
-  SG_ARG(o->ras_kernel == 0 || o->ras_kernel == 1, "sg_precond_setup: ras_kernel must be 0 or 1");
+  SG_ARG(o->ras_kernel >= 0 && o->ras_kernel <= 2, "sg_precond_setup: ras_kernel must be 0, 1 or 2");
+  SG_ARG(o->ras_kernel != 2 || ras_inverse_supported(pr->P),
+         "sg_precond_setup: ras_kernel 2 (explicit local inverses) needs P <= 96");
   SG_ARG(o->ras_stages == 0 || (o->ras_stages >= 2 && o->ras_stages <= 8),
          "sg_precond_setup: ras_stages must be 0 (automatic) or in [2, 8]");
   SG_ARG(o->inner_orth_passes >= 0 && o->inner_orth_passes <= 2,
@@ -254,6 +256,8 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   SG_TRY(kernel_attrs_init());
   sg_status s = precond_setup_host(pr, pc);
   pc.amg.fused = o->amg_kernel == 0;
+  pc.wait_limit = pr->wait_limit;
+  if (s == SG_OK && pc.ras_kernel == 2) s = ras_inverse_build(pr, pc, st);
   std::vector<double> ginv;
   if (s == SG_OK) s = kronecker_factor(pr, pc, ginv);
   pc.omega = 1.0;
@@ -372,6 +376,7 @@ sg_status sg_precond_apply(sg_problem* pr, sg_dtype dtype, int which, const void
           ? precond_apply_t<double>(pr, which, static_cast<const double*>(R), ldr, static_cast<double*>(Z), ldz, st)
           : precond_apply_t<float>(pr, which, static_cast<const float*>(R), ldr, static_cast<float*>(Z), ldz, st);
   if (s < 0) pr->solver->dirty = true;
+  if (s == SG_OK && pr->solver->pc.ras_kernel == 2) return ras_inverse_check(pr->solver->pc, st);
   return s;
 }
 
@@ -580,6 +585,7 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
     inf.hist_len = cnt;
   }
   if (info) *info = inf;
+  if (S.pc.ras_kernel == 2) SG_TRY(ras_inverse_check(S.pc, st));
   status = inf.relres <= o->rtol ? SG_OK : SG_NOT_CONVERGED;
   if (status == SG_NOT_CONVERGED) set_error("sg_solve: max_it reached before rtol");
   return status;

@@ -51,6 +51,12 @@ struct RasData {
   DevBuf d_nlines;                         // int32 nbox
   DevBuf d_gidx;                           // int32 nbox x lmax x wmax (-1 pad, owned | 1<<30)
   DevBuf linv64, loff64, linv32, loff32;   // nbox x lmax x wmax x wmax
+  // explicit local inverses (ras_kernel 2): owned rows of A_{0,i}^{-1}, FP32
+  // [nbox][inv_mpad][inv_kp]; owned global indices [nbox][inv_mpad] (-1 pad),
+  // overlapped global indices [nbox][inv_kp], overlapped counts, the
+  // (box, 128-row tile) work items and a timeout flag
+  int inv_kp = 0, inv_mpad = 0, inv_items = 0;
+  DevBuf d_inv, d_inv_owned, d_inv_idx, d_inv_nov, d_inv_items, d_inv_err;
 };
 
 // Coarse 2h space: interpolation R_0^T and the coarse Galerkin operator.
@@ -81,7 +87,9 @@ struct Precond {
   int inner_passes = 1;  // Gram-Schmidt passes of the coarse GMRES
   int ras_modes = 0;                       // modes per CTA of the RAS kernel (0 automatic)
   int ras_stages = 0;                      // depth of its ring of line matrices (0 automatic)
-  int ras_kernel = 0;                      // 0: FMA kernel; 1: tensor cores for FP32 data
+  int ras_kernel = 0;                      // 0: FMA kernel; 1: tensor cores for FP32 data (line
+                                           // recurrence); 2: explicit local inverses on tcgen05
+  int wait_limit = 1 << 22;                // mbarrier polls of a tcgen05 completion wait
   RasData ras;
   CoarseData co;
   AmgHier amg;                             // on the coarse mean operator

@@ -106,12 +106,12 @@ def test_tcgen05_wait_timeout_is_reported_and_recovers(pair):
     Z1 = dev_rows(np.zeros((ref.n, ref.P)))
     sg.sg_cnn_apply(prob, Rd, Z1)
     try:
-        sg.sg_cnn_set_wait_limit(prob, 0)
+        sg.sg_set_wait_limit(prob, 0)
         with pytest.raises(sg.SgError) as e:
             sg.sg_cnn_apply(prob, Rd, dev_rows(np.zeros((ref.n, ref.P))))
         assert e.value.status == -5
     finally:
-        sg.sg_cnn_set_wait_limit(prob, -1)
+        sg.sg_set_wait_limit(prob, -1)
     Z2 = dev_rows(np.zeros((ref.n, ref.P)))
     sg.sg_cnn_apply(prob, Rd, Z2)
     torch.cuda.synchronize()

@@ -283,3 +283,43 @@ def test_amg_vcycle_kernels_multilevel(multilevel, dt):
     with pytest.raises(sg.SgError) as e:
         sg.sg_precond_setup(prob, 4, 4, 1, amg_kernel=2)
     assert e.value.status == -1
+
+
+def test_ras_explicit_inverses(pair):
+    """RAS local solves by explicit local inverses on tcgen05 (ras_kernel 2:
+    FP32 owned rows of each local inverse, TF32 products with operands split
+    into high and remainder parts): the local solves, the smoother with its
+    fused Kronecker factor, and the two-level cycle against the oracle; a
+    wait limit of 0 is reported as SG_ERR_TIMEOUT and the next apply agrees
+    with the first."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, (sx, sy, ov) = pair
+    X = random_block(ref.n, ref.P, seed=39)
+    try:
+        sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200, ras_kernel=2)
+        Y, Xq = run(prob, sg.PC_RAS_LOCAL, X, ref.n, torch.float32)
+        Yr = ras.apply_ras(tl.parts, tl.solvers, Xq)
+        assert np.max(np.abs(Y - Yr)) <= 1e-4 * np.max(np.abs(Yr))
+        assert np.linalg.norm(Y - Yr) <= 2e-6 * np.linalg.norm(Yr)
+        omega = sg.sg_precond_info(prob)[0]
+        Y, Xq = run(prob, sg.PC_SMOOTH, X, ref.n, torch.float32)
+        Gt = ras.kronecker_factor(ref)
+        Yr = omega * np.linalg.solve(Gt, ras.apply_ras(tl.parts, tl.solvers, Xq).T).T
+        assert np.max(np.abs(Y - Yr)) <= 1e-4 * np.max(np.abs(Yr))
+        try:
+            sg.sg_set_wait_limit(prob, 0)
+            with pytest.raises(sg.SgError) as e:
+                run(prob, sg.PC_RAS_LOCAL, X, ref.n, torch.float32)
+            assert e.value.status == -5
+        finally:
+            sg.sg_set_wait_limit(prob, -1)
+        Y2, _ = run(prob, sg.PC_RAS_LOCAL, X, ref.n, torch.float32)
+        Y1, _ = run(prob, sg.PC_RAS_LOCAL, X, ref.n, torch.float32)
+        assert np.array_equal(Y1, Y2)
+        # FP64 data keep the line kernel
+        Y, Xq = run(prob, sg.PC_RAS_LOCAL, X, ref.n, torch.float64)
+        Yr = ras.apply_ras(tl.parts, tl.solvers, Xq)
+        assert np.max(np.abs(Y - Yr)) <= 1e-11 * np.max(np.abs(Yr))
+    finally:
+        sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200)
