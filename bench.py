@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--host-loops", action="store_true",
                     help="coarse GMRES driven from the host (every kernel a separate launch): for launch lists")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["apply_slot", "apply_flux", "cnn_train", "nl_coef", "sample", "ras"],
+                    choices=["apply_slot", "apply_flux", "cnn_train", "nl_coef", "sample", "ras", "ras_inv"],
                     help="run a few launches of one kernel on a small case and exit (for profiler captures)")
     return ap.parse_args()
 
@@ -513,15 +513,19 @@ def kernel_case(name):
     from sg_inputs import CONFIGS
     torch.cuda.set_device(0)
     c = CONFIGS[WORKLOAD]
-    if name in ("apply_slot", "apply_flux", "ras"):
+    if name in ("apply_slot", "apply_flux", "ras", "ras_inv"):
         prob = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
         sg.sg_apply_autotune(prob)
         X = torch.randn((prob.P, prob.n), dtype=torch.float32, device="cuda")
         Y = torch.empty_like(X)
-        if name == "ras":
-            sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL)
+        if name in ("ras", "ras_inv"):
+            sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL,
+                                ras_kernel=2 if name == "ras_inv" else 0)
             for _ in range(3):
-                sg.sg_precond_apply(prob, sg.PC_RAS_LOCAL, X, Y)
+                sg.sg_precond_apply(prob, sg.PC_SMOOTH, X, Y)
+            stream = torch.cuda.current_stream()
+            ms, _ = ev_time(torch, stream, lambda: [sg.sg_precond_apply(prob, sg.PC_SMOOTH, X, Y) for _ in range(20)])
+            print(json.dumps({"kernel_case": name, "smoother_ms": ms / 20}))
         else:
             sg.sg_apply_flux(prob, 1 if name == "apply_flux" else 0)
             for _ in range(3):

@@ -27,7 +27,8 @@ namespace sg {
 
 namespace {
 
-constexpr int kInvKC = 32;           // overlapped nodes per chunk (K)
+constexpr int kInvKC = 16;           // overlapped nodes per chunk (K)
+constexpr int kInvStages = 4;        // chunks in flight
 constexpr int kInvDrain = 1 << 24;   // polls of the wait that follows a timed-out one
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -52,9 +53,23 @@ __device__ __forceinline__ int tile_off(int rows, int m, int k) {
   return (k >> 2) * (rows * 16) + (m >> 3) * 128 + (m & 7) * 16 + (k & 3) * 4;
 }
 
-// One CTA per (box, 128-row tile of its owned nodes); 128 threads.
-// smem: two stages of {A hi, A lo (128 x 32), B hi, B lo (N x 32)}, the
-// transform matrix [P][P], two mbarriers, the tensor-memory address.
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+// 4-byte copy; src_bytes 0 fills zero
+__device__ __forceinline__ void cp4(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+// One CTA per (box, 128-row tile of its owned nodes); 128 threads.  The
+// inverse rows and the gathered residual stream through kInvStages stages
+// of shared memory by asynchronous copies, kInvStages - 1 chunks ahead;
+// each thread splits the values it copied into a TF32 high part (in place)
+// and the remainder, so no barrier separates a chunk's arrival from its
+// split.  smem: stages of {A (128 x KC), A remainder, B (N x KC), B
+// remainder}, the transform matrix [P][P], one mbarrier per stage, the
+// tensor-memory address.
 __global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R, int64_t ld, float* __restrict__ Z,
                                                     int P, int N, int Kp, int Mpad, const int2* __restrict__ items,
                                                     const float* __restrict__ ainv, const int* __restrict__ owned,
@@ -63,9 +78,9 @@ __global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R,
                                                     int* __restrict__ err, int wait_limit) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int SA = 128 * kInvKC * 4, SB = N * kInvKC * 4, STAGE = 2 * SA + 2 * SB;
-  float* Ms = reinterpret_cast<float*>(sm + 2 * STAGE);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * STAGE + ((P * P * 4 + 15) & ~15));
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  float* Ms = reinterpret_cast<float*>(sm + kInvStages * STAGE);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kInvStages * STAGE + ((P * P * 4 + 15) & ~15));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kInvStages);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int2 it = items[blockIdx.x];
   const int box = it.x, row0 = it.y * 128;
@@ -81,14 +96,29 @@ __global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(mbar + s)) : "memory");
+    for (int s = 0; s < kInvStages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(mbar + s)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  const uint32_t tmem = *tslot;
-  const uint32_t idesc = tf32_desc(128, N);
+  // copies of chunk c into its stage: A rows by 16-byte pieces (thread =
+  // row, one piece per 4-column plane), B gathered by 4-byte words with the
+  // mode rows of a plane contiguous across the threads
+  auto issue = [&](int c) {
+    if (c < nchunk) {
+      unsigned char* st = sm + (c % kInvStages) * STAGE;
+      const int k0 = c * kInvKC;
+#pragma unroll
+      for (int q = 0; q < kInvKC / 4; ++q) cp16(st + q * 2048 + tid * 16, A + size_t(tid) * Kp + k0 + 4 * q);
+      float* Bs = reinterpret_cast<float*>(st + 2 * SA);
+      for (int e = tid; e < N * kInvKC; e += 128) {
+        const int kk = e & 3, n = (e >> 2) % N, q = (e >> 2) / N;
+        const int j = k0 + 4 * q + kk;
+        const bool in = n < P && j < nb;
+        cp4(Bs + e, in ? R + int64_t(n) * ld + ix[j] : R, in ? 4 : 0);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
   auto poll = [&](int s, uint32_t parity, int limit) {
     uint32_t done = 0;
     for (int i = 0; i < limit && !done; ++i)
@@ -99,50 +129,45 @@ __global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R,
           : "memory");
     return done;
   };
+  for (int c = 0; c < kInvStages - 1; ++c) issue(c);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = tf32_desc(128, N);
   bool ok = true;
   int issued = 0;  // chunks whose MMAs were committed
   for (int c = 0; c < nchunk; ++c) {
-    const int s = c & 1;
+    const int s = c % kInvStages;
     unsigned char* st = sm + s * STAGE;
-    if (c >= 2) {  // the MMAs of chunk c - 2 read this stage
-      const uint32_t done = poll(s, uint32_t(((c - 2) >> 1) & 1), wait_limit);
-      if (!__syncthreads_and(done != 0)) {
-        ok = false;
-        break;
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kInvStages - 2) : "memory");
+    // split this thread's copies: high part in place, remainder beside it
+    {
+      float* Ar = reinterpret_cast<float*>(st);
+      float* Al = reinterpret_cast<float*>(st + SA);
+#pragma unroll
+      for (int q = 0; q < kInvKC / 4; ++q) {
+        const int off = (q * 2048 + tid * 16) / 4;
+        const float4 v = *reinterpret_cast<const float4*>(Ar + off);
+        const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+        *reinterpret_cast<float4*>(Ar + off) = h;
+        *reinterpret_cast<float4*>(Al + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
       }
-    }
-    float* Ah = reinterpret_cast<float*>(st);
-    float* Al = reinterpret_cast<float*>(st + SA);
-    float* Bh = reinterpret_cast<float*>(st + 2 * SA);
-    float* Bl = reinterpret_cast<float*>(st + 2 * SA + SB);
-    const int k0 = c * kInvKC;
-    // A: 128 rows x 32 columns of the inverse, 16-byte loads
-    for (int e = tid; e < 128 * (kInvKC / 4); e += 128) {
-      const int m = e / (kInvKC / 4), q = e % (kInvKC / 4);
-      const float4 v = *reinterpret_cast<const float4*>(A + size_t(m) * Kp + k0 + 4 * q);
-      const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-      const float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-      const int off = tile_off(128, m, 4 * q) / 4;
-      *reinterpret_cast<float4*>(Ah + off) = h;
-      *reinterpret_cast<float4*>(Al + off) = l;
-    }
-    // B: the restricted residual, modes as rows (zero past P and past the
-    // box's overlapped nodes)
-    for (int e = tid; e < N * kInvKC; e += 128) {
-      const int n = e / kInvKC, k = e % kInvKC, j = k0 + k;
-      float v = 0.f;
-      if (n < P && j < nb) v = R[int64_t(n) * ld + ix[j]];
-      const float h = tf32_hi(v);
-      const int off = tile_off(N, n, k) / 4;
-      Bh[off] = h;
-      Bl[off] = v - h;
+      float* Br = reinterpret_cast<float*>(st + 2 * SA);
+      float* Bl = reinterpret_cast<float*>(st + 2 * SA + SB);
+      for (int e = tid; e < N * kInvKC; e += 128) {
+        const float v = Br[e], h = tf32_hi(v);
+        Br[e] = h;
+        Bl[e] = v - h;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (tid == 0) {
-      const uint32_t ah = smem_addr(Ah), al = smem_addr(Al), bh = smem_addr(Bh), bl = smem_addr(Bl);
+      const uint32_t ah = smem_addr(st), al = smem_addr(st + SA), bh = smem_addr(st + 2 * SA),
+                     bl = smem_addr(st + 2 * SA + SB);
       const uint32_t PLA = 128 * 16, PLB = uint32_t(N) * 16;
 #pragma unroll
       for (int k8 = 0; k8 < kInvKC / 8; ++k8) {
@@ -165,20 +190,34 @@ __global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R,
                    : "memory");
     }
     issued = c + 1;
+    // the stage of chunk c + kInvStages - 1 was read by the MMAs of chunk c - 1
+    if (c >= 1) {
+      const int cp = c - 1;
+      const uint32_t done = poll(cp % kInvStages, uint32_t((cp / kInvStages) & 1), wait_limit);
+      if (!__syncthreads_and(done != 0)) {
+        ok = false;
+        break;
+      }
+    }
+    issue(c + kInvStages - 1);
   }
-  // the last chunk (and the one before) complete before the accumulator is read
+  // the last commit arrives when every MMA of this CTA has completed
   if (ok && issued > 0) {
-    const int c = issued - 1;
-    uint32_t done = poll(c & 1, uint32_t((c >> 1) & 1), wait_limit);
-    if (issued > 1) done &= poll((c - 1) & 1, uint32_t(((c - 1) >> 1) & 1), wait_limit);
+    const int cl = issued - 1;
+    const uint32_t done = poll(cl % kInvStages, uint32_t((cl / kInvStages) & 1), wait_limit);
     ok = __syncthreads_and(done != 0) != 0;
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
     // MMAs already issued must finish before their tensor memory is freed
-    for (int c = max(0, issued - 2); c < issued; ++c) poll(c & 1, uint32_t((c >> 1) & 1), kInvDrain);
+    if (issued > 0) {
+      const int cl = issued - 1;
+      poll(cl % kInvStages, uint32_t((cl / kInvStages) & 1), kInvDrain);
+    }
   }
+  __syncthreads();
   if (ok && issued > 0) {
     // accumulator rows to shared memory (the stages are free now), row
     // stride odd so that the per-row reads of a warp hit distinct banks
@@ -255,7 +294,7 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
 
 size_t inv_smem(int P, int N) {
   const size_t stage = 2 * size_t(128) * kInvKC * 4 + 2 * size_t(N) * kInvKC * 4;
-  return 2 * stage + ((size_t(P) * P * 4 + 15) & ~size_t(15)) + 2 * 8 + 16;
+  return kInvStages * stage + ((size_t(P) * P * 4 + 15) & ~size_t(15)) + kInvStages * 8 + 16;
 }
 
 }  // namespace
@@ -287,7 +326,7 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
     set_error("RAS explicit inverses: boxes must be wider than twice the overlap");
     return SG_ERR_UNSUPPORTED;
   }
-  const int Kp = (nmax + kInvKC - 1) / kInvKC * kInvKC;
+  const int Kp = (nmax + 31) / 32 * 32;
   const int Mpad = (omax + 127) / 128 * 128;
   std::vector<int32_t> hidx(size_t(nbox) * Kp, 0), hown(size_t(nbox) * Mpad, -1);
   std::vector<int2> items;

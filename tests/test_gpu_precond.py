@@ -196,7 +196,7 @@ def test_ras_kernels(pair, kernel, modes):
         assert np.max(np.abs(Y - Yr)) <= 1e-4 * np.max(np.abs(Yr))
         assert np.linalg.norm(Y - Yr) <= 2e-6 * np.linalg.norm(Yr)
         with pytest.raises(sg.SgError):
-            sg.sg_precond_setup(prob, sx, sy, ov, ras_kernel=2)
+            sg.sg_precond_setup(prob, sx, sy, ov, ras_kernel=3)
     finally:
         sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200)
 
