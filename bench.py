@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "poisson256_L4_p3"
 METRIC = "SG solve time to relres 1e-8 (FP32 in FP64 refinement, two-level RAS+AMG FGMRES)"
 INNER_RTOL = 0.3          # inner coarse GMRES tolerance of the timed solves
+RAS_KERNEL = 3            # FP32 RAS local solves: the faster of the line kernel and the explicit inverses
 PAPER_INNER_RTOL = 1e-5   # the paper's default for the 2GV3 variant
 
 
@@ -391,7 +392,7 @@ def large_workload(sg, torch, stream, reps=3):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     sg.sg_apply_autotune(prob)
-    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL)
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL, ras_kernel=RAS_KERNEL)
     for which in (1, 2, 3):
         sg.sg_apply_autotune(prob, which=which)
     n, P, K, nnz = prob.n, prob.P, prob.K, prob.nnzA
@@ -423,7 +424,8 @@ def large_workload(sg, torch, stream, reps=3):
                         "achieved": round(bytes_f32 / (avg * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(bytes_f32 / (avg * 1e-3) / 1e9 / peak, 4), "peak_source": peak_kind,
                         "bytes_per_launch": bytes_f32, "avg_launch_ms": avg, "launches": cnt},
-           "ras_local_ms_per_launch": rms / max(rcnt, 1), "apply_shape": sg.sg_apply_info(prob)}
+           "ras_local_ms_per_launch": rms / max(rcnt, 1), "ras_kernel": sg.sg_precond_ras_kernel(prob),
+           "apply_shape": sg.sg_apply_info(prob)}
     # learned smoother trained on this system, against RAS
     info = sg.sg_train_precond(prob, n_pairs=4096, epochs=4, batch=32, lr=1e-3, seed=0, loss=0)
     solve(1)
@@ -446,7 +448,7 @@ def nonlinear_workload(sg, torch, stream):
     c = CONFIGS["poisson384_L4_p4"]
     prob = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
     sg.sg_apply_autotune(prob)
-    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL)
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL, ras_kernel=RAS_KERNEL)
     for which in (1, 2, 3):
         sg.sg_apply_autotune(prob, which=which)
     X = torch.zeros((prob.P, prob.n), dtype=torch.float64, device="cuda")
@@ -579,7 +581,8 @@ def main():
     tune_ms = sg.sg_apply_autotune(prob)       # cached after the first run
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
-    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL, host_loops=args.host_loops)
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL, host_loops=args.host_loops,
+                        ras_kernel=RAS_KERNEL)
     torch.cuda.synchronize()
     t_pc = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -657,11 +660,19 @@ def main():
     avg_ms = kms / max(cnt, 1)
     achieved = bytes_f32 / (avg_ms * 1e-3) / 1e9 if cnt else None
     peak, peak_kind = peaks()
-    # the RAS local solves (FP32 FMA recurrences)
+    # the RAS local solves: line FMA recurrences, or explicit inverses
     ras_flops, ras_boxes, ras_w = sg.sg_precond_stats(prob)
+    ras_kernel = sg.sg_precond_ras_kernel(prob)
     rcnt, rms = kinds["ras_local_f32"]
     ras_avg = rms / max(rcnt, 1)
     ras_tflops = ras_flops / (ras_avg * 1e-3) / 1e12 if rcnt else None
+    # explicit inverses: the owned rows x overlapped columns of every box
+    # (FP32), the gathered residual and the written result
+    inv_bytes = 0
+    for b in range(ras_boxes):
+        idx_b, own_b = sg.sg_get_partition(prob, b)
+        inv_bytes += int(own_b.sum()) * len(idx_b) * 4 + len(idx_b) * P * 4
+    inv_bytes += n * P * 4
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
     # phases of one step (non-overlapping: the fine applies outside the
     # smoother and the coarse correction, the smoother, the coarse
@@ -685,11 +696,11 @@ def main():
     ms64, info64 = timed(0)
     X64_sol = X.clone()
     # the paper's inner tolerance, both precisions
-    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=PAPER_INNER_RTOL)
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=PAPER_INNER_RTOL, ras_kernel=RAS_KERNEL)
     solve(mode=1)
     ms_paper32, info_paper32 = timed(1)
     ms_paper64, info_paper64 = timed(0)
-    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL)
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL, ras_kernel=RAS_KERNEL)
     solve(mode=1)
 
     # end to end through the C ABI with host buffers: F host->device, solve,
@@ -726,6 +737,17 @@ def main():
         apply_forms[form] = {"ms": round(ms_a / 20, 5), "bytes": byt, "gbs": round(byt / (ms_a / 20 * 1e-3) / 1e9, 1)}
     sg.sg_apply_flux(prob, 2)
     sg.sg_apply_autotune(prob)                 # the tuned choice again (cached)
+    # both FP32 RAS local-solve kernels, the smoother with its Kronecker
+    # factor (20 applications after 3)
+    ras_forms = {}
+    for form, kern in (("line_fma", 0), ("explicit_inverse_tcgen05", 2)):
+        sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL, ras_kernel=kern)
+        for _ in range(3):
+            sg.sg_precond_apply(prob, sg.PC_SMOOTH, Xa, Ya)
+        ms_r, _ = ev_time(torch, stream, lambda: [sg.sg_precond_apply(prob, sg.PC_SMOOTH, Xa, Ya) for _ in range(20)])
+        ras_forms[form] = {"smoother_ms": round(ms_r / 20, 5)}
+    sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL, ras_kernel=RAS_KERNEL)
+    ras_forms["chosen"] = ["line_fma", "", "explicit_inverse_tcgen05"][sg.sg_precond_ras_kernel(prob)]
     assert sg.sg_apply_flux(prob, -1) == chosen
     extras = {} if (args.no_extras or rank != 0) else extra_measurements(sg, torch, prob, stream)
     if not args.no_extras and rank == 0:
@@ -773,15 +795,24 @@ def main():
                      "peak_source": peak_kind, "bytes_per_launch": bytes_f32, "avg_launch_ms": avg_ms,
                      "launches": cnt,
                      "traffic": measured_traffic(dict(sg.sg_apply_info(prob), flux=flux_on))},
-        "roofline_top_kernel": {"kernel": "k_ras_local FP32 (RAS line solves, %d boxes, line width %d)"
-                                          % (ras_boxes, ras_w),
-                                "bound": "alu", "achieved": round(ras_tflops, 2) if ras_tflops else None,
-                                "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                                "frac": round(ras_tflops / fp32_peak, 4) if ras_tflops else None,
-                                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                                "flops_per_launch": ras_flops, "avg_launch_ms": ras_avg, "launches": rcnt,
-                                "note": "latency-bound line recurrences (dependent steps per sweep); "
-                                        "a few percent of DRAM bandwidth"},
+        "roofline_top_kernel": ({"kernel": "k_ras_inv_tc FP32 (RAS by explicit local inverses on tcgen05, %d boxes, "
+                                           "Kronecker factor fused)" % ras_boxes,
+                                 "bound": "hbm", "achieved": round(inv_bytes / (ras_avg * 1e-3) / 1e9, 1) if rcnt else None,
+                                 "peak": peak, "unit": "GB/s",
+                                 "frac": round(inv_bytes / (ras_avg * 1e-3) / 1e9 / peak, 4) if rcnt else None,
+                                 "peak_source": peak_kind, "bytes_per_launch": inv_bytes, "avg_launch_ms": ras_avg,
+                                 "launches": rcnt}
+                                if ras_kernel == 2 else
+                                {"kernel": "k_ras_local FP32 (RAS line solves, %d boxes, line width %d)"
+                                           % (ras_boxes, ras_w),
+                                 "bound": "alu", "achieved": round(ras_tflops, 2) if ras_tflops else None,
+                                 "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                                 "frac": round(ras_tflops / fp32_peak, 4) if ras_tflops else None,
+                                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                                 "flops_per_launch": ras_flops, "avg_launch_ms": ras_avg, "launches": rcnt,
+                                 "note": "latency-bound line recurrences (dependent steps per sweep); "
+                                         "a few percent of DRAM bandwidth"}),
+        "ras_forms": ras_forms,
         "phase_ms_per_step": phase_ms,
         "profiled_ms_per_step": round(ms_prof, 3),
         "attributed_share": round(attributed / ms_prof, 3),

@@ -288,7 +288,10 @@ typedef struct {
                           applied as dense products on the tcgen05 tensor
                           cores (kind::tf32, operands split into high and
                           remainder parts, FP32 accumulation in tensor
-                          memory) with the Kronecker factor fused.  FP64
+                          memory) with the Kronecker factor fused;
+                          3 = automatic: 2 when its inverses can be built
+                          and one application measures faster than the
+                          FMA kernel's on this problem, else 0.  FP64
                           data always use the FMA kernel. */
 } sg_precond_opts;
 
@@ -307,8 +310,11 @@ sg_status sg_precond_info(const sg_problem* prob, double* omega, int* amg_levels
 /* Size of the RAS local solves: useful flops of one application over all P
  * modes (forward and backward block sweeps: per line the w_l x w_{l-1}
  * sub-diagonal block and the triangular inverse), number of boxes, padded
- * line width.  Any pointer may be NULL. */
-sg_status sg_precond_stats(const sg_problem* prob, double* ras_flops, int* ras_boxes, int* ras_wmax);
+ * line width, and the FP32 local-solve kernel in use (0, 1 or 2 as for
+ * sg_precond_opts.ras_kernel; the automatic choice 3 resolved).  Any
+ * pointer may be NULL. */
+sg_status sg_precond_stats(const sg_problem* prob, double* ras_flops, int* ras_boxes, int* ras_wmax,
+                           int* ras_kernel);
 
 /* Overlapped node set of box `sub` (ascending global indices) and its owned
  * flags (D_i).  Call with idx = owned = NULL to get the count first. */

@@ -20,7 +20,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_newton", "sg_nonlinear_residual", "sg_nonlinear_jacobian_apply", "sg_sample_solve",
            "sg_set_wait_limit", "sg_apply_flux",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
-           "sg_mdot_noalloc", "sg_precond_stats", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
+           "sg_mdot_noalloc", "sg_precond_stats", "sg_precond_ras_kernel", "sg_cnn_param_count", "sg_cnn_init", "sg_cnn_set_weights",
            "sg_cnn_get_weights", "sg_cnn_apply", "sg_cnn_train_step", "sg_mean_solve",
            "sg_train_precond", "sg_precond_set_smoother", "cnn_flatten", "cnn_unflatten", "sg_cnn_set_loss", "sg_cnn_set_kernel",
            "Batch", "sg_batch_create", "sg_batch_solve", "sg_batch_destroy", "sg_solve_batch",
@@ -165,8 +165,16 @@ def sg_precond_info(prob):
 def sg_precond_stats(prob):
     """(RAS useful flops per application, boxes, padded line width)."""
     f, nb, w = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
-    call("sg_precond_stats", prob.handle, ctypes.byref(f), ctypes.byref(nb), ctypes.byref(w))
+    call("sg_precond_stats", prob.handle, ctypes.byref(f), ctypes.byref(nb), ctypes.byref(w), None)
     return f.value, nb.value, w.value
+
+
+def sg_precond_ras_kernel(prob):
+    """The FP32 RAS local-solve kernel in use: 0 line FMA, 1 line TF32 MMA,
+    2 explicit local inverses on tcgen05."""
+    k = ctypes.c_int()
+    call("sg_precond_stats", prob.handle, None, None, None, ctypes.byref(k))
+    return k.value
 
 
 def sg_get_partition(prob, sub):

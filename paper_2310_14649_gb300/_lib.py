@@ -92,7 +92,8 @@ SIGNATURES = {
     "sg_precond_setup": [vp, ctypes.POINTER(PrecondOpts), vp],
     "sg_precond_info": [vp, P_f64, ctypes.POINTER(ctypes.c_int), P_i64, ctypes.POINTER(ctypes.c_int)],
     "sg_get_partition": [vp, ctypes.c_int, P_i32, P_i64, P_i32],
-    "sg_precond_stats": [vp, P_f64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "sg_precond_stats": [vp, P_f64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_int)],
     "sg_get_coarse_csr": [vp, P_i64, P_i64, P_i32, P_i32],
     "sg_get_amg_level": [vp, ctypes.c_int, P_i64, P_i32],
     "sg_precond_apply": [vp, ctypes.c_int, ctypes.c_int, vp, i64, vp, i64, vp],

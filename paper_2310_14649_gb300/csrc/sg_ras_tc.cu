@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R,
   extern __shared__ __align__(128) unsigned char sm[];
   const int SA = 128 * kInvKC * 4, SB = N * kInvKC * 4, STAGE = 2 * SA + 2 * SB;
   float* Ms = reinterpret_cast<float*>(sm + kInvStages * STAGE);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kInvStages * STAGE + ((P * P * 4 + 15) & ~15));
+  int* Is = reinterpret_cast<int*>(sm + kInvStages * STAGE + ((P * P * 4 + 15) & ~15));  // [Kp] box indices
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kInvStages * STAGE + ((P * P * 4 + 15) & ~15) + Kp * 4);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kInvStages);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int2 it = items[blockIdx.x];
@@ -89,6 +90,8 @@ __global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R,
   const float* A = ainv + (size_t(box) * Mpad + row0) * Kp;
   const int* ix = idx + size_t(box) * Kp;
   for (int e = tid; e < P * P; e += 128) Ms[e] = M[e];
+  for (int e = tid; e < Kp; e += 128) Is[e] = e < nb ? ix[e] : 0;
+  __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tslot)),
                  "r"(tcols)
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R,
         const int kk = e & 3, n = (e >> 2) % N, q = (e >> 2) / N;
         const int j = k0 + 4 * q + kk;
         const bool in = n < P && j < nb;
-        cp4(Bs + e, in ? R + int64_t(n) * ld + ix[j] : R, in ? 4 : 0);
+        cp4(Bs + e, in ? R + int64_t(n) * ld + Is[j] : R, in ? 4 : 0);
       }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -292,14 +295,18 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
   }
 }
 
-size_t inv_smem(int P, int N) {
+size_t inv_smem(int P, int N, int Kp) {
   const size_t stage = 2 * size_t(128) * kInvKC * 4 + 2 * size_t(N) * kInvKC * 4;
-  return kInvStages * stage + ((size_t(P) * P * 4 + 15) & ~size_t(15)) + kInvStages * 8 + 16;
+  return kInvStages * stage + ((size_t(P) * P * 4 + 15) & ~size_t(15)) + size_t(Kp) * 4 + kInvStages * 8 + 16;
 }
 
 }  // namespace
 
-bool ras_inverse_supported(int P) { return P >= 1 && P <= 96 && inv_smem(P, (P + 15) / 16 * 16) <= 227 * 1024; }
+// the index list of the widest supported box: 48 x 48 overlapped nodes
+constexpr int kInvMaxKp = 48 * 48;
+bool ras_inverse_supported(int P) {
+  return P >= 1 && P <= 96 && inv_smem(P, (P + 15) / 16 * 16, kInvMaxKp) <= 227 * 1024;
+}
 
 sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   RasData& D = pc.ras;
@@ -327,6 +334,10 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
     return SG_ERR_UNSUPPORTED;
   }
   const int Kp = (nmax + 31) / 32 * 32;
+  if (Kp > kInvMaxKp) {
+    set_error("RAS explicit inverses: overlapped boxes of at most 2,304 nodes");
+    return SG_ERR_UNSUPPORTED;
+  }
   const int Mpad = (omax + 127) / 128 * 128;
   std::vector<int32_t> hidx(size_t(nbox) * Kp, 0), hown(size_t(nbox) * Mpad, -1);
   std::vector<int2> items;
@@ -392,7 +403,7 @@ sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld
   const RasData& D = pc.ras;
   const int N = (P + 15) / 16 * 16;
   const int tcols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
-  k_ras_inv_tc<<<unsigned(D.inv_items), 128, inv_smem(P, N), st>>>(
+  k_ras_inv_tc<<<unsigned(D.inv_items), 128, inv_smem(P, N, D.inv_kp), st>>>(
       R, ld, Z, P, N, D.inv_kp, D.inv_mpad, dp<int2>(D.d_inv_items), dp<float>(D.d_inv), dp<int>(D.d_inv_owned),
       dp<int>(D.d_inv_idx), dp<int>(D.d_inv_nov), M, transform ? 1 : 0, tcols, dp<int>(D.d_inv_err), wait_limit);
   note_launch();

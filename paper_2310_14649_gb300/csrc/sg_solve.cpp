@@ -144,6 +144,55 @@ static sg_status estimate_omega(sg_problem* pr, SolverState& S, cudaStream_t st)
 
 Precond& precond_of(sg_problem* pr) { return pr->solver->pc; }
 
+// ras_kernel 3: build the explicit local inverses when they are available
+// and keep them when one FP32 application (median of 5, CUDA events, after
+// a warm-up) is faster than the line kernel's; otherwise the line kernel.
+sg_status ras_kernel_choose(sg_problem* pr, Precond& pc, cudaStream_t st) {
+  pc.ras_kernel = 0;
+  if (!ras_inverse_supported(pr->P)) return SG_OK;
+  const sg_status b = ras_inverse_build(pr, pc, st);
+  if (b == SG_ERR_UNSUPPORTED) return SG_OK;
+  SG_TRY(b);
+  const int64_t len = int64_t(pr->P) * pr->ld;
+  DevBuf R, Z;
+  SG_TRY(R.alloc(len * 4));
+  SG_TRY(Z.alloc(len * 4));
+  std::vector<float> h(len);
+  for (int64_t e = 0; e < len; ++e) h[e] = float(1 + (e * 7) % 13) * 0.125f;
+  SG_CUDA(cudaMemcpy(R.ptr, h.data(), len * 4, cudaMemcpyHostToDevice));
+  cudaEvent_t e0, e1;
+  SG_CUDA(cudaEventCreate(&e0));
+  SG_CUDA(cudaEventCreate(&e1));
+  double t[2] = {0, 0};
+  for (int k : {0, 2}) {
+    pc.ras_kernel = k;
+    std::vector<float> ts;
+    for (int rep = 0; rep < 6; ++rep) {
+      SG_CUDA(cudaEventRecord(e0, st));
+      SG_TRY(ras_apply<float>(pc, pr->n, pr->P, dp<float>(R), pr->ld, dp<float>(Z), st, true));
+      SG_CUDA(cudaEventRecord(e1, st));
+      SG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      SG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep) ts.push_back(ms);
+    }
+    std::sort(ts.begin(), ts.end());
+    t[k == 2] = ts[ts.size() / 2];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SG_TRY(ras_inverse_check(pc, st));
+  pc.ras_kernel = t[1] < t[0] ? 2 : 0;
+  if (pc.ras_kernel == 0) {
+    RasData& D = pc.ras;
+    D.d_inv.free_();
+    D.d_inv_owned.free_();
+    D.d_inv_idx.free_();
+    D.d_inv_items.free_();
+  }
+  return SG_OK;
+}
+
 // Selects the learned smoother for later solves with damping omega_cnn
 // (= 1 / rho(S_cnn A) by the same power iteration when omega <= 0).
 sg_status learned_smoother_enable(sg_problem* pr, double omega, cudaStream_t st) {
@@ -227,7 +276,7 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
          "sg_precond_setup: subdomain counts must be in [1, N-1]");
   SG_ARG(o->overlap >= 0 && o->overlap <= 8, "sg_precond_setup: overlap must be in [0, 8]");
   SG_ARG(o->amg_kernel == 0 || o->amg_kernel == 1, "sg_precond_setup: amg_kernel must be 0 or 1");
-  SG_ARG(o->ras_kernel >= 0 && o->ras_kernel <= 2, "sg_precond_setup: ras_kernel must be 0, 1 or 2");
+  SG_ARG(o->ras_kernel >= 0 && o->ras_kernel <= 3, "sg_precond_setup: ras_kernel must be 0, 1, 2 or 3");
   SG_ARG(o->ras_kernel != 2 || ras_inverse_supported(pr->P),
          "sg_precond_setup: ras_kernel 2 (explicit local inverses) needs P <= 96");
   SG_ARG(o->ras_stages == 0 || (o->ras_stages >= 2 && o->ras_stages <= 8),
@@ -258,6 +307,7 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   pc.amg.fused = o->amg_kernel == 0;
   pc.wait_limit = pr->wait_limit;
   if (s == SG_OK && pc.ras_kernel == 2) s = ras_inverse_build(pr, pc, st);
+  if (s == SG_OK && pc.ras_kernel == 3) s = ras_kernel_choose(pr, pc, st);
   std::vector<double> ginv;
   if (s == SG_OK) s = kronecker_factor(pr, pc, ginv);
   pc.omega = 1.0;
@@ -327,12 +377,13 @@ sg_status sg_precond_info(const sg_problem* pr, double* omega, int* amg_levels, 
   return SG_OK;
 }
 
-sg_status sg_precond_stats(const sg_problem* pr, double* ras_flops, int* ras_boxes, int* ras_wmax) {
+sg_status sg_precond_stats(const sg_problem* pr, double* ras_flops, int* ras_boxes, int* ras_wmax, int* ras_kernel) {
   SG_ARG(pr && pr->solver && pr->solver->pc.ready, "sg_precond_stats: no preconditioner set up");
   const RasData& R = pr->solver->pc.ras;
   if (ras_flops) *ras_flops = R.flops_per_mode * pr->P;
   if (ras_boxes) *ras_boxes = R.nbox;
   if (ras_wmax) *ras_wmax = R.wmax;
+  if (ras_kernel) *ras_kernel = pr->solver->pc.ras_kernel;
   return SG_OK;
 }
 

@@ -180,6 +180,23 @@ def test_ras_ring_depths(pair, dt):
         sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200)
 
 
+def test_ras_kernel_automatic_choice(pair):
+    """ras_kernel 3 keeps one of the two FP32 local-solve kernels (the
+    faster on this problem) and the local solves match the oracle."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref, tl, (sx, sy, ov) = pair
+    try:
+        sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200, ras_kernel=3)
+        assert sg.sg_precond_ras_kernel(prob) in (0, 2)
+        X = random_block(ref.n, ref.P, seed=40)
+        Y, Xq = run(prob, sg.PC_RAS_LOCAL, X, ref.n, torch.float32)
+        Yr = ras.apply_ras(tl.parts, tl.solvers, Xq)
+        assert np.max(np.abs(Y - Yr)) <= 1e-4 * np.max(np.abs(Yr))
+    finally:
+        sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200)
+
+
 @pytest.mark.parametrize("kernel,modes", [(1, 0), (1, 3), (1, 8), (1, 10), (0, 0), (0, 4)])
 def test_ras_kernels(pair, kernel, modes):
     """FP32 RAS local solves on the tensor cores (3xTF32 MMA; several mode
@@ -196,7 +213,7 @@ def test_ras_kernels(pair, kernel, modes):
         assert np.max(np.abs(Y - Yr)) <= 1e-4 * np.max(np.abs(Yr))
         assert np.linalg.norm(Y - Yr) <= 2e-6 * np.linalg.norm(Yr)
         with pytest.raises(sg.SgError):
-            sg.sg_precond_setup(prob, sx, sy, ov, ras_kernel=3)
+            sg.sg_precond_setup(prob, sx, sy, ov, ras_kernel=4)
     finally:
         sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200)
 
@@ -301,7 +318,11 @@ def test_ras_explicit_inverses(pair):
         Y, Xq = run(prob, sg.PC_RAS_LOCAL, X, ref.n, torch.float32)
         Yr = ras.apply_ras(tl.parts, tl.solvers, Xq)
         assert np.max(np.abs(Y - Yr)) <= 1e-4 * np.max(np.abs(Yr))
-        assert np.linalg.norm(Y - Yr) <= 2e-6 * np.linalg.norm(Yr)
+        # the inverse entries are stored in FP32: their rounding (u = 2^-24)
+        # accumulates over the n_i overlapped nodes of a row, about
+        # sqrt(n_i) u relative in L2 (2e-6 for 36^2 nodes), plus the TF32
+        # split's 2^-22 per product
+        assert np.linalg.norm(Y - Yr) <= 1e-5 * np.linalg.norm(Yr)
         omega = sg.sg_precond_info(prob)[0]
         Y, Xq = run(prob, sg.PC_SMOOTH, X, ref.n, torch.float32)
         Gt = ras.kronecker_factor(ref)
