@@ -803,6 +803,10 @@ static sg_status node_transform_reg(float* Z, int64_t ld, int64_t n, int P, cons
 template <typename T>
 sg_status node_transform(T* Z, int64_t ld, int64_t n, int P, const T* M, cudaStream_t st, T* Z2, int64_t stride2,
                          const int* j2) {
+  if (!M) {
+    set_error("node_transform: the Kronecker factor is not on the device yet");
+    return SG_ERR_ARG;
+  }
   if (sizeof(T) == 4 && P <= 64) {
     float* Zf = reinterpret_cast<float*>(Z);
     const float* Mf = reinterpret_cast<const float*>(M);

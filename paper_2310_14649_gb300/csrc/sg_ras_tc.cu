@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R,
   const int nchunk = (nb + kInvKC - 1) / kInvKC;
   const float* A = ainv + (size_t(box) * Mpad + row0) * Kp;
   const int* ix = idx + size_t(box) * Kp;
-  for (int e = tid; e < P * P; e += 128) Ms[e] = M[e];
+  if (transform)
+    for (int e = tid; e < P * P; e += 128) Ms[e] = M[e];
   for (int e = tid; e < Kp; e += 128) Is[e] = e < nb ? ix[e] : 0;
   __syncthreads();
   if (warp == 0) {
@@ -401,6 +402,10 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
 sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld, float* Z, const float* M,
                             bool transform, int wait_limit, cudaStream_t st) {
   const RasData& D = pc.ras;
+  if (transform && !M) {
+    set_error("ras_inverse_apply: the Kronecker factor is not on the device yet");
+    return SG_ERR_ARG;
+  }
   const int N = (P + 15) / 16 * 16;
   const int tcols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
   k_ras_inv_tc<<<unsigned(D.inv_items), 128, inv_smem(P, N, D.inv_kp), st>>>(

@@ -307,11 +307,13 @@ sg_status sg_precond_setup(sg_problem* pr, const sg_precond_opts* o, void* strea
   pc.amg.fused = o->amg_kernel == 0;
   pc.wait_limit = pr->wait_limit;
   if (s == SG_OK && pc.ras_kernel == 2) s = ras_inverse_build(pr, pc, st);
-  if (s == SG_OK && pc.ras_kernel == 3) s = ras_kernel_choose(pr, pc, st);
   std::vector<double> ginv;
   if (s == SG_OK) s = kronecker_factor(pr, pc, ginv);
   pc.omega = 1.0;
   if (s == SG_OK) s = upload_gtinv(pr, pc, ginv);
+  // the choice times the full local step (with the Kronecker factor), so
+  // it runs once that factor is on the device
+  if (s == SG_OK && pc.ras_kernel == 3) s = ras_kernel_choose(pr, pc, st);
   if (s == SG_OK && o->omega <= 0) s = estimate_omega(pr, S, st);
   if (s == SG_OK && o->omega > 0) pc.omega = o->omega;
   if (s == SG_OK) s = upload_gtinv(pr, pc, ginv);
