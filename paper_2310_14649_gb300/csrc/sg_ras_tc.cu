@@ -4,13 +4,25 @@
 // where D_i keeps the owned nodes, so box i needs only the owned rows of
 // A_{0,i}^{-1}: Zowned_i[m][a] = sum_j Ainv_i[m][j] r[idx_i[j]][a] — a
 // product of an (owned x overlapped) matrix with the (overlapped x P)
-// restricted residual.  The rows are tiled by 128 (M), the P modes padded
-// to N (a multiple of 16), the overlapped nodes (K) streamed in chunks of 32.
-// The operands are FP32 split into a TF32 high part and the remainder,
-// D += Ah Bh + Ah Bl + Al Bh (kind::tf32, FP32 accumulation in tensor
-// memory), which keeps FP32 accuracy.  The epilogue applies the smoother's
-// Kronecker factor (omega G~^{-1} across the modes of a node) before the
-// store, so no separate node transform follows.
+// restricted residual.
+//
+// Work: the owned rows of every box are cut into tiles of 128 rows (the
+// MMA's M), the overlapped nodes into chunks of 32 (K), the P modes padded
+// to N (a multiple of 16).  The inverse is stored chunk by chunk in the
+// operand layout of the tensor cores, so one bulk copy moves a 16 KB chunk
+// from HBM to shared memory; the sequence of all (tile, chunk) pairs is cut
+// into one contiguous range per SM (a persistent grid), so every SM streams
+// the same number of bytes and a tile is shared by at most two CTAs.
+//
+// Precision: FP32 operands split into a TF32 high part and the remainder,
+// x = xh + xl.  The residual is split once per apply into the stacked
+// operand [rh; rl] (2N rows), the inverse chunk in shared memory after its
+// arrival; then per k-step
+//     D[:, 0:2N] += Ah [rh; rl]^T,   D[:, 0:N] += Al rh^T
+// (kind::tf32, FP32 accumulation in tensor memory) and the epilogue sums
+// the two column halves: Ah rh + Ah rl + Al rh, the product to FP32
+// accuracy.  The epilogue applies the smoother's Kronecker factor (omega
+// G~^{-1} across the modes of a node) before the store.
 //
 // The inverses are formed once at setup in FP64 from the line-block
 // Cholesky factors: the local solve applied to unit right-hand sides, four
@@ -27,9 +39,26 @@ namespace sg {
 
 namespace {
 
-constexpr int kInvKC = 16;           // overlapped nodes per chunk (K)
-constexpr int kInvStages = 4;        // chunks in flight
-constexpr int kInvDrain = 1 << 24;   // polls of the wait that follows a timed-out one
+constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
+constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
+constexpr int kInvMaxStages = 4;           // chunks in flight
+constexpr int kInvThreads = 320;           // copy warp, MMA warp, 4 split warps, 4 epilogue warps
+constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
+constexpr size_t kSmemLimit = 227 * 1024;
+
+// index tables of the explicit-inverse data, in ints, in this order
+enum InvMeta {
+  kTileStart,   // [ntiles + 1]: first chunk of each tile in the global sequence
+  kTileBox,     // [ntiles]
+  kTileOwned,   // [ntiles][128]: global node of each tile row, -1 for padding
+  kBoxChunk0,   // [nbox]: first chunk of the box in the packed residual
+  kBoxTile0,    // [nbox]: first tile of the box
+  kChunkBox,    // [bchunks]: box of each packed residual chunk
+  kSplitTile,   // [nsplit]: tiles two CTAs accumulate into
+  kIdx,         // [nbox][Kp]: overlapped global nodes
+  kNov,         // [nbox]: overlapped node counts
+  kMetaCount
+};
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -47,232 +76,406 @@ __host__ __device__ constexpr uint32_t tf32_desc(int M, int N) {
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// (row m, k) of a K-major operand tile with `rows` rows and 32 k: planes of
-// 4 k (16 bytes per row), rows 16 bytes apart, 8-row core matrices 128 bytes
-__device__ __forceinline__ int tile_off(int rows, int m, int k) {
-  return (k >> 2) * (rows * 16) + (m >> 3) * 128 + (m & 7) * 16 + (k & 3) * 4;
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(b)), "r"(count) : "memory");
 }
-
-__device__ __forceinline__ void cp16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(b)) : "memory");
 }
-// 4-byte copy; src_bytes 0 fills zero
-__device__ __forceinline__ void cp4(void* dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+// polls the phase of parity `parity`; gives up after `limit` polls or when
+// another role of the CTA has given up
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int limit, volatile int* abort) {
+  for (int i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (abort && *abort) return false;
+  }
+  return false;
+}
+// bulk copy global -> shared, completion counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+__device__ __forceinline__ void bulk_load_stream(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                 uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_addr(b))
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
 
-// One CTA per (box, 128-row tile of its owned nodes); 128 threads.  The
-// inverse rows and the gathered residual stream through kInvStages stages
-// of shared memory by asynchronous copies, kInvStages - 1 chunks ahead;
-// each thread splits the values it copied into a TF32 high part (in place)
-// and the remainder, so no barrier separates a chunk's arrival from its
-// split.  smem: stages of {A (128 x KC), A remainder, B (N x KC), B
-// remainder}, the transform matrix [P][P], one mbarrier per stage, the
-// tensor-memory address.
-__global__ void __launch_bounds__(128) k_ras_inv_tc(const float* __restrict__ R, int64_t ld, float* __restrict__ Z,
-                                                    int P, int N, int Kp, int Mpad, const int2* __restrict__ items,
-                                                    const float* __restrict__ ainv, const int* __restrict__ owned,
-                                                    const int* __restrict__ idx, const int* __restrict__ nov,
-                                                    const float* __restrict__ M, int transform, int tcols,
-                                                    int* __restrict__ err, int wait_limit) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  const int SA = 128 * kInvKC * 4, SB = N * kInvKC * 4, STAGE = 2 * SA + 2 * SB;
-  float* Ms = reinterpret_cast<float*>(sm + kInvStages * STAGE);
-  int* Is = reinterpret_cast<int*>(sm + kInvStages * STAGE + ((P * P * 4 + 15) & ~15));  // [Kp] box indices
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kInvStages * STAGE + ((P * P * 4 + 15) & ~15) + Kp * 4);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kInvStages);
+struct InvArgs {
+  float* Z;
+  int64_t ld;
+  const float* ainv;   // [chunks][kInvChunk]
+  const float* bpack;  // [bchunks][2N x kInvKC]
+  const int* meta;
+  int64_t off[kMetaCount];
+  const float* M;      // P x P Kronecker factor (row a: coefficients of output mode a)
+  int transform;
+  int P, stages, ntiles, tcols, acc_cols;
+  int64_t chunks;
+  int* err;
+  int wait_limit;
+};
+
+// the pieces of this CTA's chunk range: (tile t, chunks [cb, ce) of it)
+struct PieceIter {
+  const int* ts;
+  int64_t g, g1;
+  int t;
+  __device__ PieceIter(const int* tile_start, int ntiles, int64_t g0, int64_t g1_) : ts(tile_start), g(g0), g1(g1_) {
+    int lo = 0, hi = ntiles - 1;  // the last tile starting at or before g0
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ts[mid] <= g0) lo = mid;
+      else hi = mid - 1;
+    }
+    t = lo;
+  }
+  __device__ bool next(int& tile, int& cb, int& ce, bool& split) {
+    if (g >= g1) return false;
+    const int64_t a = ts[t], e = ts[t + 1];
+    tile = t;
+    cb = int(g - a);
+    ce = int(min(g1, e) - a);
+    split = cb > 0 || a + ce < e;
+    g = a + ce;
+    ++t;
+    return true;
+  }
+};
+
+// Persistent kernel, one CTA per SM, chunk range [blockIdx.x * chunks /
+// grid, ...).  Roles: warp 0 lane 0 issues the bulk copies of a stage
+// (inverse chunk + packed residual chunk); warps 2-5 split the inverse
+// chunk in place (high part) and beside it (remainder); warp 1 lane 0 issues
+// the MMAs of a stage and commits them to the stage's "empty" barrier and,
+// at the end of a tile piece, to the accumulator's "full" barrier; warps
+// 6-9 read the accumulator (two in tensor memory, alternating by piece),
+// apply the Kronecker factor and store (atomically adding when the tile is
+// shared with the neighbouring CTA, whose rows were zeroed by the pack
+// kernel; two addends onto zero give the same sum in either order).
+// shared memory: stages of {A (raw, then high part) 16 KB | A remainder
+// 16 KB | packed residual 2N x 32 x 4 B}, the N x N factor, barriers.
+template <int NB>
+__global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
+  constexpr int N = 16 * NB;
+  constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4, STAGE = 2 * SA + SB;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int S = a.stages;
+  float* Ms = reinterpret_cast<float*>(sm + S * STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S * STAGE + N * N * 4);
+  uint64_t* full = bars;                      // [S] copies landed
+  uint64_t* split = bars + kInvMaxStages;     // [S] split done (128 arrivals)
+  uint64_t* empty = bars + 2 * kInvMaxStages; // [S] MMAs of the stage done
+  uint64_t* accf = bars + 3 * kInvMaxStages;  // [2] accumulator complete
+  uint64_t* acce = accf + 2;                  // [2] accumulator read (128 arrivals)
+  uint64_t* fin = acce + 2;                   // last MMA done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int2 it = items[blockIdx.x];
-  const int box = it.x, row0 = it.y * 128;
-  const int nb = nov[box];
-  const int nchunk = (nb + kInvKC - 1) / kInvKC;
-  const float* A = ainv + (size_t(box) * Mpad + row0) * Kp;
-  const int* ix = idx + size_t(box) * Kp;
-  if (transform)
-    for (int e = tid; e < P * P; e += 128) Ms[e] = M[e];
-  for (int e = tid; e < Kp; e += 128) Is[e] = e < nb ? ix[e] : 0;
-  __syncthreads();
-  if (warp == 0) {
+  const int* meta = a.meta;
+  const int* tile_start = meta + a.off[kTileStart];
+  const int64_t g0 = int64_t(blockIdx.x) * a.chunks / gridDim.x;
+  const int64_t g1 = int64_t(blockIdx.x + 1) * a.chunks / gridDim.x;
+
+  if (a.transform)
+    for (int e = tid; e < N * N; e += kInvThreads) {
+      const int r = e / N, c = e % N;
+      Ms[e] = (r < a.P && c < a.P) ? a.M[r * a.P + c] : 0.f;
+    }
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tslot)),
-                 "r"(tcols)
+                 "r"(a.tcols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < kInvStages; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(mbar + s)) : "memory");
+    for (int s = 0; s < kInvMaxStages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(split + s, 128);
+      mbar_init(empty + s, 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(accf + k, 1);
+      mbar_init(acce + k, 128);
+    }
+    mbar_init(fin, 1);
+    *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  // copies of chunk c into its stage: A rows by 16-byte pieces (thread =
-  // row, one piece per 4-column plane), B gathered by 4-byte words with the
-  // mode rows of a plane contiguous across the threads
-  auto issue = [&](int c) {
-    if (c < nchunk) {
-      unsigned char* st = sm + (c % kInvStages) * STAGE;
-      const int k0 = c * kInvKC;
-#pragma unroll
-      for (int q = 0; q < kInvKC / 4; ++q) cp16(st + q * 2048 + tid * 16, A + size_t(tid) * Kp + k0 + 4 * q);
-      float* Bs = reinterpret_cast<float*>(st + 2 * SA);
-      for (int e = tid; e < N * kInvKC; e += 128) {
-        const int kk = e & 3, n = (e >> 2) % N, q = (e >> 2) / N;
-        const int j = k0 + 4 * q + kk;
-        const bool in = n < P && j < nb;
-        cp4(Bs + e, in ? R + int64_t(n) * ld + Is[j] : R, in ? 4 : 0);
-      }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  };
-  auto poll = [&](int s, uint32_t parity, int limit) {
-    uint32_t done = 0;
-    for (int i = 0; i < limit && !done; ++i)
-      asm volatile(
-          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-          : "=r"(done)
-          : "r"(smem_addr(mbar + s)), "r"(parity)
-          : "memory");
-    return done;
-  };
-  for (int c = 0; c < kInvStages - 1; ++c) issue(c);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = tf32_desc(128, N);
-  bool ok = true;
-  int issued = 0;  // chunks whose MMAs were committed
-  for (int c = 0; c < nchunk; ++c) {
-    const int s = c % kInvStages;
-    unsigned char* st = sm + s * STAGE;
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kInvStages - 2) : "memory");
-    // split this thread's copies: high part in place, remainder beside it
-    {
-      float* Ar = reinterpret_cast<float*>(st);
-      float* Al = reinterpret_cast<float*>(st + SA);
-#pragma unroll
-      for (int q = 0; q < kInvKC / 4; ++q) {
-        const int off = (q * 2048 + tid * 16) / 4;
-        const float4 v = *reinterpret_cast<const float4*>(Ar + off);
-        const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-        *reinterpret_cast<float4*>(Ar + off) = h;
-        *reinterpret_cast<float4*>(Al + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-      }
-      float* Br = reinterpret_cast<float*>(st + 2 * SA);
-      float* Bl = reinterpret_cast<float*>(st + 2 * SA + SB);
-      for (int e = tid; e < N * kInvKC; e += 128) {
-        const float v = Br[e], h = tf32_hi(v);
-        Br[e] = h;
-        Bl[e] = v - h;
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (tid == 0) {
-      const uint32_t ah = smem_addr(st), al = smem_addr(st + SA), bh = smem_addr(st + 2 * SA),
-                     bl = smem_addr(st + 2 * SA + SB);
-      const uint32_t PLA = 128 * 16, PLB = uint32_t(N) * 16;
-#pragma unroll
-      for (int k8 = 0; k8 < kInvKC / 8; ++k8) {
-        const uint32_t oa = 2 * k8 * PLA, ob = 2 * k8 * PLB;
-        const uint64_t dah = smem_desc(ah + oa, PLA, 128), dal = smem_desc(al + oa, PLA, 128);
-        const uint64_t dbh = smem_desc(bh + ob, PLB, 128), dbl = smem_desc(bl + ob, PLB, 128);
-        const uint64_t da[3] = {dah, dah, dal}, db[3] = {dbh, dbl, dbh};
-#pragma unroll
-        for (int pass = 0; pass < 3; ++pass) {
-          const uint32_t acc = (c > 0 || k8 > 0 || pass > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(da[pass]), "l"(db[pass]), "r"(idesc), "r"(acc)
-              : "memory");
+  auto fail = [&]() {
+    *abort = 1;
+    atomicExch(a.err, 1);
+  };
+
+  if (warp == 0) {
+    // ---- copies ----
+    if (lane == 0) {
+      uint64_t pol;
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+      const int* tile_box = meta + a.off[kTileBox];
+      const int* box_chunk0 = meta + a.off[kBoxChunk0];
+      PieceIter pi(tile_start, a.ntiles, g0, g1);
+      int t, cb, ce;
+      bool sp;
+      int it = 0;
+      bool ok = true;
+      while (ok && pi.next(t, cb, ce, sp)) {
+        const int64_t gt = tile_start[t];
+        const int64_t gb = box_chunk0[tile_box[t]];
+        for (int c = cb; c < ce; ++c, ++it) {
+          const int s = it % S;
+          if (it >= S && !mbar_wait(empty + s, uint32_t((it / S - 1) & 1), a.wait_limit, abort)) {
+            fail();
+            ok = false;
+            break;
+          }
+          unsigned char* st = sm + s * STAGE;
+          mbar_expect_tx(full + s, SA + SB);
+          bulk_load_stream(st, a.ainv + (gt + c) * kInvChunk, SA, full + s, pol);
+          bulk_load(st + 2 * SA, a.bpack + (gb + c) * (2 * N * kInvKC), SB, full + s);
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                       smem_addr(mbar + s))
-                   : "memory");
+      // every copy lands before the CTA's shared memory is released
+      for (int s = 0; s < S && s < it; ++s) {
+        const int u = s + S * ((it - 1 - s) / S);  // last use of stage s
+        mbar_wait(full + s, uint32_t((u / S) & 1), kInvDrain, nullptr);
+      }
     }
-    issued = c + 1;
-    // the stage of chunk c + kInvStages - 1 was read by the MMAs of chunk c - 1
-    if (c >= 1) {
-      const int cp = c - 1;
-      const uint32_t done = poll(cp % kInvStages, uint32_t((cp / kInvStages) & 1), wait_limit);
-      if (!__syncthreads_and(done != 0)) {
-        ok = false;
+  } else if (warp == 1) {
+    // ---- MMAs ----
+    if (lane == 0) {
+      PieceIter pi(tile_start, a.ntiles, g0, g1);
+      int t, cb, ce;
+      bool sp;
+      int it = 0, pc = 0;
+      bool ok = true, any = false;
+      const uint32_t id2 = tf32_desc(128, 2 * N), id1 = tf32_desc(128, N);
+      constexpr uint32_t PLA = 128 * 16, PLB = 2 * N * 16;
+      while (ok && pi.next(t, cb, ce, sp)) {
+        const int acc = pc & 1;
+        if (pc >= 2 && !mbar_wait(acce + acc, uint32_t((pc / 2 - 1) & 1), a.wait_limit, abort)) {
+          fail();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t d = tmem + uint32_t(acc * a.acc_cols);
+        for (int c = cb; c < ce; ++c, ++it) {
+          const int s = it % S;
+          if (!mbar_wait(split + s, uint32_t((it / S) & 1), a.wait_limit, abort)) {
+            fail();
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t ah = smem_addr(sm + s * STAGE), al = ah + SA, bb = ah + 2 * SA;
+#pragma unroll
+          for (int k8 = 0; k8 < kInvKC / 8; ++k8) {
+            const uint64_t dah = smem_desc(ah + 2 * k8 * PLA, PLA, 128);
+            const uint64_t dal = smem_desc(al + 2 * k8 * PLA, PLA, 128);
+            const uint64_t db = smem_desc(bb + 2 * k8 * PLB, PLB, 128);
+            tc_mma(d, dah, db, id2, (c > cb || k8 > 0) ? 1u : 0u);
+            tc_mma(d, dal, db, id1, 1u);
+          }
+          any = true;
+          tc_commit(empty + s);
+        }
+        if (!ok) break;
+        tc_commit(accf + acc);
+        ++pc;
+      }
+      // every MMA completes before tensor memory is freed
+      if (any) {
+        tc_commit(fin);
+        mbar_wait(fin, 0u, kInvDrain, nullptr);
+      }
+    }
+  } else if (warp < 6) {
+    // ---- split of the inverse chunk: high part in place, remainder beside it ----
+    const int sid = tid - 64;
+    PieceIter pi(tile_start, a.ntiles, g0, g1);
+    int t, cb, ce;
+    bool sp;
+    int it = 0;
+    bool ok = true;
+    while (ok && pi.next(t, cb, ce, sp)) {
+      for (int c = cb; c < ce; ++c, ++it) {
+        const int s = it % S;
+        if (!mbar_wait(full + s, uint32_t((it / S) & 1), a.wait_limit, abort)) {
+          fail();
+          ok = false;
+          break;
+        }
+        float4* ar = reinterpret_cast<float4*>(sm + s * STAGE);
+        float4* al = reinterpret_cast<float4*>(sm + s * STAGE + SA);
+#pragma unroll
+        for (int q = 0; q < kInvChunk / 4 / 128; ++q) {
+          const int e = sid + 128 * q;
+          const float4 v = ar[e];
+          const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+          ar[e] = h;
+          al[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive(split + s);
+      }
+    }
+  } else {
+    // ---- epilogue: rows 32 (warp % 4) + lane of the accumulator ----
+    const int lg = warp & 3, m = 32 * lg + lane;
+    const int* tile_owned = meta + a.off[kTileOwned];
+    PieceIter pi(tile_start, a.ntiles, g0, g1);
+    int t, cb, ce;
+    bool sp;
+    int pc = 0;
+    while (pi.next(t, cb, ce, sp)) {
+      const int acc = pc & 1;
+      // the warp converges before the aligned tensor-memory loads
+      const bool got = mbar_wait(accf + acc, uint32_t((pc / 2) & 1), a.wait_limit, abort);
+      if (!__all_sync(0xffffffffu, got)) {
+        fail();
         break;
       }
-    }
-    issue(c + kInvStages - 1);
-  }
-  // the last commit arrives when every MMA of this CTA has completed
-  if (ok && issued > 0) {
-    const int cl = issued - 1;
-    const uint32_t done = poll(cl % kInvStages, uint32_t((cl / kInvStages) & 1), wait_limit);
-    ok = __syncthreads_and(done != 0) != 0;
-  }
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-    // MMAs already issued must finish before their tensor memory is freed
-    if (issued > 0) {
-      const int cl = issued - 1;
-      poll(cl % kInvStages, uint32_t((cl / kInvStages) & 1), kInvDrain);
-    }
-  }
-  __syncthreads();
-  if (ok && issued > 0) {
-    // accumulator rows to shared memory (the stages are free now), row
-    // stride odd so that the per-row reads of a warp hit distinct banks
-    const int ys = P | 1;
-    float* Ys = reinterpret_cast<float*>(sm);
-    const int m = warp * 32 + lane;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      float y[N];
+      const uint32_t base = tmem + (uint32_t(32 * lg) << 16) + uint32_t(acc * a.acc_cols);
 #pragma unroll
-    for (int c16 = 0; c16 < 8; ++c16) {
-      if (c16 * 16 >= N) break;
-      uint32_t r[16];
-      const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16) + uint32_t(16 * c16);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-          "%14, %15}, [%16];\n"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      for (int j = 0; j < NB; ++j) {
+        float lo[16];
+        tc_ld16(base + 16 * j, y + 16 * j);
+        tc_ld16(base + N + 16 * j, lo);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (c16 * 16 + q < P) Ys[m * ys + c16 * 16 + q] = __uint_as_float(r[q]);
-    }
-    __syncwarp();
-    const int g = owned[size_t(box) * Mpad + row0 + m];
-    if (g >= 0) {
-      const float* yr = Ys + m * ys;
-      for (int a = 0; a < P; ++a) {
-        float v;
-        if (transform) {
-          v = 0.f;
-          const float* ma = Ms + a * P;
-#pragma unroll 5
-          for (int b = 0; b < P; ++b) v = fmaf(ma[b], yr[b], v);
-        } else {
-          v = yr[a];
+        for (int q = 0; q < 16; ++q) y[16 * j + q] += lo[q];
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      mbar_arrive(acce + acc);
+      ++pc;
+      const int g = tile_owned[int64_t(t) * 128 + m];
+      if (g < 0) continue;
+      float* zr = a.Z + g;
+      if (a.transform) {
+        for (int r = 0; r < a.P; ++r) {
+          const float4* mr = reinterpret_cast<const float4*>(Ms + r * N);
+          float v = 0.f;
+#pragma unroll
+          for (int b4 = 0; b4 < N / 4; ++b4) {
+            const float4 w = mr[b4];
+            v = fmaf(w.x, y[4 * b4], v);
+            v = fmaf(w.y, y[4 * b4 + 1], v);
+            v = fmaf(w.z, y[4 * b4 + 2], v);
+            v = fmaf(w.w, y[4 * b4 + 3], v);
+          }
+          if (sp) atomicAdd(zr + int64_t(r) * a.ld, v);
+          else zr[int64_t(r) * a.ld] = v;
         }
-        Z[int64_t(a) * ld + g] = v;
+      } else {
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+          if (r < a.P) {
+            if (sp) atomicAdd(zr + int64_t(r) * a.ld, y[r]);
+            else zr[int64_t(r) * a.ld] = y[r];
+          }
+        }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tcols) : "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(a.tcols) : "memory");
+}
+
+// The residual of every box in the operand layout of its chunks: chunk
+// (box b, c) holds, for the overlapped nodes j = 32 c .. 32 c + 31, the
+// rows n < N (high parts of r[n][idx_b[j]]) and N + n (remainders), planes
+// of 4 nodes (16 bytes per row).  Also zeroes the output rows of the tiles
+// that two CTAs accumulate into.
+__global__ void k_ras_inv_pack(const float* __restrict__ R, int64_t ld, int P, int N, int64_t nb4,
+                               const int* __restrict__ meta, InvArgs a, float* __restrict__ bpack, int nsplit,
+                               int Kp) {
+  const int* chunk_box = meta + a.off[kChunkBox];
+  const int* box_chunk0 = meta + a.off[kBoxChunk0];
+  const int* idx = meta + a.off[kIdx];
+  const int* nov = meta + a.off[kNov];
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  for (int64_t f = t0; f < nb4; f += stride) {
+    const int n = int(f % N);
+    const int64_t r = f / N;
+    const int q = int(r % (kInvKC / 4));
+    const int64_t gc = r / (kInvKC / 4);
+    const int b = chunk_box[gc];
+    const int j0 = int(gc - box_chunk0[b]) * kInvKC + 4 * q;
+    const int nb = nov[b];
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int j = j0 + k;
+      v[k] = (n < P && j < nb) ? R[int64_t(n) * ld + idx[int64_t(b) * Kp + j]] : 0.f;
+    }
+    const float4 h = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
+    float4* out = reinterpret_cast<float4*>(bpack + gc * (2 * N * kInvKC)) + q * 2 * N;
+    out[n] = h;
+    out[N + n] = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
+  }
+  const int* split_tile = meta + a.off[kSplitTile];
+  const int* tile_owned = meta + a.off[kTileOwned];
+  const int64_t nz = int64_t(nsplit) * 128 * P;
+  for (int64_t e = t0; e < nz; e += stride) {
+    const int c = int(e % P);
+    const int64_t r = e / P;
+    const int g = tile_owned[int64_t(split_tile[r / 128]) * 128 + int(r % 128)];
+    if (g >= 0) a.Z[int64_t(c) * ld + g] = 0.f;
+  }
 }
 
 // unit right-hand sides of one colour class: R[j][idx_b[j]] = 1 for the
 // boxes b of that class (their overlapped sets are disjoint)
-__global__ void k_inv_unit_rhs(double* __restrict__ R, int64_t ld, const int* __restrict__ idx, const int* __restrict__ nov,
-                               const int* __restrict__ color, int cls, int Kp, int nbox) {
+__global__ void k_inv_unit_rhs(double* __restrict__ R, int64_t ld, const int* __restrict__ idx,
+                               const int* __restrict__ nov, const int* __restrict__ color, int cls, int Kp, int nbox) {
   const int64_t total = int64_t(nbox) * Kp;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
     const int b = int(t / Kp), j = int(t % Kp);
@@ -281,33 +484,67 @@ __global__ void k_inv_unit_rhs(double* __restrict__ R, int64_t ld, const int* __
   }
 }
 
-// Ainv_b[m][j] = Z[j][owned_b[m]] for the boxes of one colour class
+// Ainv_b[m][j] = Z[j][owned_b[m]] for the boxes of one colour class, into
+// the chunk layout: tile box_tile0[b] + m / 128, chunk j / 32, plane
+// (j % 32) / 4, row m % 128, word j % 4
 __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* __restrict__ ainv,
-                              const int* __restrict__ owned, const int* __restrict__ nov,
-                              const int* __restrict__ color, int cls, int Mpad, int Kp, int nbox) {
+                              const int* __restrict__ meta, InvArgs a, const int* __restrict__ color, int cls,
+                              int Mpad, int Kp, int nbox) {
+  const int* nov = meta + a.off[kNov];
+  const int* box_tile0 = meta + a.off[kBoxTile0];
+  const int* tile_start = meta + a.off[kTileStart];
+  const int* tile_owned = meta + a.off[kTileOwned];
   const int64_t total = int64_t(nbox) * Mpad * Kp;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
     const int b = int(t / (int64_t(Mpad) * Kp));
     if (color[b] != cls) continue;
     const int64_t rem = t - int64_t(b) * Mpad * Kp;
     const int m = int(rem / Kp), j = int(rem % Kp);
-    const int g = owned[size_t(b) * Mpad + m];
-    ainv[t] = (g >= 0 && j < nov[b]) ? float(Zs[int64_t(j) * ld + g]) : 0.f;
+    const int tile = box_tile0[b] + m / 128;
+    if (tile >= box_tile0[b + 1]) continue;                 // past the box's last tile
+    const int64_t c0 = tile_start[tile];
+    if (j >= (tile_start[tile + 1] - c0) * kInvKC) continue;  // past the box's last chunk
+    const int g = tile_owned[int64_t(tile) * 128 + m % 128];
+    const float v = (g >= 0 && j < nov[b]) ? float(Zs[int64_t(j) * ld + g]) : 0.f;
+    ainv[(c0 + j / kInvKC) * kInvChunk + ((j % kInvKC) / 4) * 512 + (m % 128) * 4 + (j % 4)] = v;
   }
 }
 
-size_t inv_smem(int P, int N, int Kp) {
-  const size_t stage = 2 * size_t(128) * kInvKC * 4 + 2 * size_t(N) * kInvKC * 4;
-  return kInvStages * stage + ((size_t(P) * P * 4 + 15) & ~size_t(15)) + size_t(Kp) * 4 + kInvStages * 8 + 16;
+size_t inv_stage_bytes(int N) { return 2 * size_t(kInvChunk) * 4 + 2 * size_t(N) * kInvKC * 4; }
+size_t inv_fixed_bytes(int N) { return size_t(N) * N * 4 + (3 * kInvMaxStages + 5) * 8 + 16; }
+
+int inv_stages(int P) {
+  const int N = (P + 15) / 16 * 16;
+  const size_t room = kSmemLimit - inv_fixed_bytes(N);
+  return int(std::min<size_t>(kInvMaxStages, room / inv_stage_bytes(N)));
+}
+
+template <int NB>
+sg_status inv_launch(const InvArgs& args, int grid, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    SG_CUDA(cudaFuncSetAttribute(k_ras_inv_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemLimit)));
+    attr = true;
+  }
+  const size_t smem = args.stages * inv_stage_bytes(16 * NB) + inv_fixed_bytes(16 * NB);
+  k_ras_inv_tc<NB><<<unsigned(grid), kInvThreads, smem, st>>>(args);
+  note_launch();
+  SG_CUDA(cudaGetLastError());
+  return SG_OK;
+}
+
+InvArgs inv_args(const RasData& D) {
+  InvArgs a{};
+  a.meta = dp<int>(D.d_inv_meta);
+  for (int k = 0; k < kMetaCount; ++k) a.off[k] = D.inv_off[k];
+  return a;
 }
 
 }  // namespace
 
 // the index list of the widest supported box: 48 x 48 overlapped nodes
 constexpr int kInvMaxKp = 48 * 48;
-bool ras_inverse_supported(int P) {
-  return P >= 1 && P <= 96 && inv_smem(P, (P + 15) / 16 * 16, kInvMaxKp) <= 227 * 1024;
-}
+bool ras_inverse_supported(int P) { return P >= 1 && P <= 96 && inv_stages(P) >= 2; }
 
 sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   RasData& D = pc.ras;
@@ -315,14 +552,16 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
     set_error("RAS explicit inverses on tensor cores: P must be in [1, 96]");
     return SG_ERR_UNSUPPORTED;
   }
+  D.inv_free();
   const int nbox = D.nbox;
   int nmax = 0, omax = 0;
-  std::vector<int> nov(nbox), color(nbox);
+  std::vector<int> nov(nbox), nown(nbox), color(nbox);
   for (int b = 0; b < nbox; ++b) {
     nov[b] = int(D.idx[b].size());
     nmax = std::max(nmax, nov[b]);
     int o = 0;
     for (int32_t f : D.owned[b]) o += f ? 1 : 0;
+    nown[b] = o;
     omax = std::max(omax, o);
     const int bx = b % pc.sx, by = b / pc.sx;
     color[b] = (bx & 1) + 2 * (by & 1);
@@ -334,34 +573,81 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
     set_error("RAS explicit inverses: boxes must be wider than twice the overlap");
     return SG_ERR_UNSUPPORTED;
   }
-  const int Kp = (nmax + 31) / 32 * 32;
+  const int Kp = (nmax + kInvKC - 1) / kInvKC * kInvKC;
   if (Kp > kInvMaxKp) {
     set_error("RAS explicit inverses: overlapped boxes of at most 2,304 nodes");
     return SG_ERR_UNSUPPORTED;
   }
   const int Mpad = (omax + 127) / 128 * 128;
-  std::vector<int32_t> hidx(size_t(nbox) * Kp, 0), hown(size_t(nbox) * Mpad, -1);
-  std::vector<int2> items;
+  const int P = pr->P, N = (P + 15) / 16 * 16;
+  // tiles (128 owned rows of a box) and chunks (32 overlapped nodes)
+  std::vector<int> tile_start{0}, tile_box, tile_owned, box_chunk0(nbox), box_tile0(nbox + 1), chunk_box, hidx(
+      size_t(nbox) * Kp, 0);
+  int64_t bchunks = 0;
+  int maxlen = 1;
   for (int b = 0; b < nbox; ++b) {
-    int o = 0;
+    const int nch = (nov[b] + kInvKC - 1) / kInvKC;
+    maxlen = std::max(maxlen, nch);
+    box_chunk0[b] = int(bchunks);
+    for (int c = 0; c < nch; ++c) chunk_box.push_back(b);
+    bchunks += nch;
+    box_tile0[b] = int(tile_box.size());
+    std::vector<int> own;
     for (int j = 0; j < nov[b]; ++j) {
       hidx[size_t(b) * Kp + j] = D.idx[b][j];
-      if (D.owned[b][j]) hown[size_t(b) * Mpad + o++] = D.idx[b][j];
+      if (D.owned[b][j]) own.push_back(D.idx[b][j]);
     }
-    for (int t = 0; t * 128 < o; ++t) items.push_back(make_int2(b, t));
+    for (int t = 0; t * 128 < nown[b]; ++t) {
+      tile_box.push_back(b);
+      tile_start.push_back(tile_start.back() + nch);
+      for (int r = 0; r < 128; ++r) tile_owned.push_back(t * 128 + r < nown[b] ? own[t * 128 + r] : -1);
+    }
   }
-  DevBuf didx, down, dnov, dcol, ditems, dainv;
-  SG_TRY(didx.alloc(hidx.size() * 4));
-  SG_TRY(down.alloc(hown.size() * 4));
-  SG_TRY(dnov.alloc(nov.size() * 4));
+  box_tile0[nbox] = int(tile_box.size());
+  const int ntiles = int(tile_box.size());
+  const int64_t chunks = tile_start.back();
+  // one CTA per SM; each range at least as long as the longest tile, so a
+  // tile meets at most two ranges
+  int dev = 0, sms = 0;
+  SG_CUDA(cudaGetDevice(&dev));
+  SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(sms, chunks / maxlen)));
+  std::vector<int> split_tile;
+  {
+    std::vector<int> pieces(ntiles, 0);
+    int t = 0;
+    for (int i = 0; i < grid; ++i) {
+      const int64_t g0 = int64_t(i) * chunks / grid, g1 = int64_t(i + 1) * chunks / grid;
+      while (tile_start[t + 1] <= g0) ++t;
+      for (int u = t; u < ntiles && tile_start[u] < g1; ++u) ++pieces[u];
+    }
+    for (int u = 0; u < ntiles; ++u) {
+      if (pieces[u] > 2) {
+        set_error("RAS explicit inverses: a tile met more than two chunk ranges");
+        return SG_ERR_UNSUPPORTED;
+      }
+      if (pieces[u] == 2) split_tile.push_back(u);
+    }
+  }
+  // the index tables in one buffer
+  std::vector<int> meta;
+  const std::vector<int>* parts[kMetaCount] = {&tile_start, &tile_box, &tile_owned, &box_chunk0, &box_tile0,
+                                               &chunk_box,  &split_tile, &hidx, &nov};
+  for (int k = 0; k < kMetaCount; ++k) {
+    D.inv_off[k] = int64_t(meta.size());
+    meta.insert(meta.end(), parts[k]->begin(), parts[k]->end());
+    meta.resize((meta.size() + 3) / 4 * 4, 0);
+  }
+  DevBuf dmeta, dcol, dainv, dbpack;
+  SG_TRY(dmeta.alloc(meta.size() * 4));
   SG_TRY(dcol.alloc(color.size() * 4));
-  SG_TRY(ditems.alloc(items.size() * sizeof(int2)));
-  SG_CUDA(cudaMemcpy(didx.ptr, hidx.data(), hidx.size() * 4, cudaMemcpyHostToDevice));
-  SG_CUDA(cudaMemcpy(down.ptr, hown.data(), hown.size() * 4, cudaMemcpyHostToDevice));
-  SG_CUDA(cudaMemcpy(dnov.ptr, nov.data(), nov.size() * 4, cudaMemcpyHostToDevice));
+  SG_CUDA(cudaMemcpy(dmeta.ptr, meta.data(), meta.size() * 4, cudaMemcpyHostToDevice));
   SG_CUDA(cudaMemcpy(dcol.ptr, color.data(), color.size() * 4, cudaMemcpyHostToDevice));
-  SG_CUDA(cudaMemcpy(ditems.ptr, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
-  SG_TRY(dainv.alloc(size_t(nbox) * Mpad * Kp * 4));
+  SG_TRY(dainv.alloc(size_t(chunks) * kInvChunk * 4));
+  SG_TRY(dbpack.alloc(size_t(bchunks) * 2 * N * kInvKC * 4));
+  D.d_inv_meta = std::move(dmeta);
+  InvArgs ia = inv_args(D);
+  const int* dm = dp<int>(D.d_inv_meta);
   // the local solves (FP64, no Kronecker factor) of the unit right-hand sides
   const int64_t ld = pr->ld;
   DevBuf Rs, Zs;
@@ -370,32 +656,30 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   for (int cls = 0; cls < 4; ++cls) {
     SG_CUDA(cudaMemsetAsync(Rs.ptr, 0, Rs.bytes, st));
     SG_CUDA(cudaMemsetAsync(Zs.ptr, 0, Zs.bytes, st));
-    k_inv_unit_rhs<<<4 * 152, 256, 0, st>>>(dp<double>(Rs), ld, dp<int>(didx), dp<int>(dnov), dp<int>(dcol), cls, Kp,
-                                            nbox);
+    k_inv_unit_rhs<<<4 * 152, 256, 0, st>>>(dp<double>(Rs), ld, dm + D.inv_off[kIdx], dm + D.inv_off[kNov],
+                                            dp<int>(dcol), cls, Kp, nbox);
     note_launch();
     SG_CUDA(cudaGetLastError());
     SG_TRY(ras_apply<double>(pc, pr->n, nmax, dp<double>(Rs), ld, dp<double>(Zs), st, false));
-    k_inv_extract<<<4 * 152, 256, 0, st>>>(dp<double>(Zs), ld, dp<float>(dainv), dp<int>(down), dp<int>(dnov),
-                                           dp<int>(dcol), cls, Mpad, Kp, nbox);
+    k_inv_extract<<<4 * 152, 256, 0, st>>>(dp<double>(Zs), ld, dp<float>(dainv), dm, ia, dp<int>(dcol), cls, Mpad,
+                                           Kp, nbox);
     note_launch();
     SG_CUDA(cudaGetLastError());
   }
   SG_CUDA(cudaStreamSynchronize(st));
   D.inv_kp = Kp;
-  D.inv_mpad = Mpad;
-  D.inv_items = int(items.size());
+  D.inv_n = N;
+  D.inv_p = P;
+  D.inv_ntiles = ntiles;
+  D.inv_grid = grid;
+  D.inv_nsplit = int(split_tile.size());
+  D.inv_stages = inv_stages(P);
+  D.inv_chunks = chunks;
+  D.inv_bchunks = bchunks;
   D.d_inv = std::move(dainv);
-  D.d_inv_idx = std::move(didx);
-  D.d_inv_owned = std::move(down);
-  D.d_inv_nov = std::move(dnov);
-  D.d_inv_items = std::move(ditems);
+  D.d_inv_bpack = std::move(dbpack);
   if (!D.d_inv_err.ptr) SG_TRY(D.d_inv_err.alloc(16));
   SG_CUDA(cudaMemset(D.d_inv_err.ptr, 0, 16));
-  static bool attr = false;
-  if (!attr) {
-    SG_CUDA(cudaFuncSetAttribute(k_ras_inv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr = true;
-  }
   return SG_OK;
 }
 
@@ -406,14 +690,48 @@ sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld
     set_error("ras_inverse_apply: the Kronecker factor is not on the device yet");
     return SG_ERR_ARG;
   }
-  const int N = (P + 15) / 16 * 16;
-  const int tcols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
-  k_ras_inv_tc<<<unsigned(D.inv_items), 128, inv_smem(P, N, D.inv_kp), st>>>(
-      R, ld, Z, P, N, D.inv_kp, D.inv_mpad, dp<int2>(D.d_inv_items), dp<float>(D.d_inv), dp<int>(D.d_inv_owned),
-      dp<int>(D.d_inv_idx), dp<int>(D.d_inv_nov), M, transform ? 1 : 0, tcols, dp<int>(D.d_inv_err), wait_limit);
+  if (P != D.inv_p || !D.d_inv.ptr) {
+    set_error("ras_inverse_apply: the local inverses were built for another number of modes");
+    return SG_ERR_ARG;
+  }
+  // the pack kernel reads R while it zeroes rows of Z
+  const float *r0 = R, *r1 = R + int64_t(P) * ld, *z0 = Z, *z1 = Z + int64_t(P) * ld;
+  if (r0 < z1 && z0 < r1) {
+    set_error("ras_inverse_apply: input and output overlap");
+    return SG_ERR_ARG;
+  }
+  const int N = D.inv_n;
+  InvArgs a = inv_args(D);
+  a.Z = Z;
+  a.ld = ld;
+  a.ainv = dp<float>(D.d_inv);
+  a.bpack = dp<float>(D.d_inv_bpack);
+  a.M = M;
+  a.transform = transform ? 1 : 0;
+  a.P = P;
+  a.stages = D.inv_stages;
+  a.ntiles = D.inv_ntiles;
+  a.acc_cols = 32;  // a power of two >= 2N: the accumulators start at columns 0 and acc_cols
+  while (a.acc_cols < 2 * N) a.acc_cols *= 2;
+  a.tcols = 2 * a.acc_cols;
+  a.chunks = D.inv_chunks;
+  a.err = dp<int>(D.d_inv_err);
+  a.wait_limit = wait_limit;
+  const int64_t nb4 = D.inv_bchunks * (kInvKC / 4) * N;
+  const int pgrid = int(std::min<int64_t>(8 * 152, (nb4 + 255) / 256));
+  k_ras_inv_pack<<<unsigned(std::max(pgrid, 1)), 256, 0, st>>>(R, ld, P, N, nb4, a.meta, a, dp<float>(D.d_inv_bpack),
+                                                              D.inv_nsplit, D.inv_kp);
   note_launch();
   SG_CUDA(cudaGetLastError());
-  return SG_OK;
+  switch (N / 16) {
+    case 1: return inv_launch<1>(a, D.inv_grid, st);
+    case 2: return inv_launch<2>(a, D.inv_grid, st);
+    case 3: return inv_launch<3>(a, D.inv_grid, st);
+    case 4: return inv_launch<4>(a, D.inv_grid, st);
+    case 5: return inv_launch<5>(a, D.inv_grid, st);
+    case 6: return inv_launch<6>(a, D.inv_grid, st);
+    default: set_error("ras_inverse_apply: P > 96"); return SG_ERR_ARG;
+  }
 }
 
 // SG_ERR_TIMEOUT (and the flag cleared) when a completion wait of the

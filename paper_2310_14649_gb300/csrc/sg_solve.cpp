@@ -184,11 +184,7 @@ sg_status ras_kernel_choose(sg_problem* pr, Precond& pc, cudaStream_t st) {
   SG_TRY(ras_inverse_check(pc, st));
   pc.ras_kernel = t[1] < t[0] ? 2 : 0;
   if (pc.ras_kernel == 0) {
-    RasData& D = pc.ras;
-    D.d_inv.free_();
-    D.d_inv_owned.free_();
-    D.d_inv_idx.free_();
-    D.d_inv_items.free_();
+    pc.ras.inv_free();
   }
   return SG_OK;
 }

@@ -51,12 +51,21 @@ struct RasData {
   DevBuf d_nlines;                         // int32 nbox
   DevBuf d_gidx;                           // int32 nbox x lmax x wmax (-1 pad, owned | 1<<30)
   DevBuf linv64, loff64, linv32, loff32;   // nbox x lmax x wmax x wmax
-  // explicit local inverses (ras_kernel 2): owned rows of A_{0,i}^{-1}, FP32
-  // [nbox][inv_mpad][inv_kp]; owned global indices [nbox][inv_mpad] (-1 pad),
-  // overlapped global indices [nbox][inv_kp], overlapped counts, the
-  // (box, 128-row tile) work items and a timeout flag
-  int inv_kp = 0, inv_mpad = 0, inv_items = 0;
-  DevBuf d_inv, d_inv_owned, d_inv_idx, d_inv_nov, d_inv_items, d_inv_err;
+  // explicit local inverses (ras_kernel 2): the owned rows of A_{0,i}^{-1}
+  // in FP32 as chunks of 128 rows x 32 overlapped nodes in the tensor-core
+  // operand layout (tiles of 128 owned rows in box order, chunks in node
+  // order), the buffer of the packed residual, the index tables (offsets in
+  // ints into d_inv_meta, InvMeta order) and a timeout flag
+  int inv_kp = 0, inv_n = 0, inv_p = 0, inv_ntiles = 0, inv_grid = 0, inv_nsplit = 0, inv_stages = 0;
+  int64_t inv_chunks = 0, inv_bchunks = 0;
+  int64_t inv_off[10] = {};
+  DevBuf d_inv, d_inv_meta, d_inv_bpack, d_inv_err;
+  void inv_free() {
+    d_inv.free_();
+    d_inv_meta.free_();
+    d_inv_bpack.free_();
+    inv_chunks = 0;
+  }
 };
 
 // Coarse 2h space: interpolation R_0^T and the coarse Galerkin operator.
