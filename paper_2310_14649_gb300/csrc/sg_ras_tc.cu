@@ -41,7 +41,9 @@ namespace {
 
 constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
 constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
-constexpr int kInvMaxStages = 4;           // chunks in flight
+constexpr int kInvMaxStages = 6;           // chunks in flight
+constexpr int kInvLoSlots = 2;             // ring of inverse remainders
+constexpr int kInvPrefetch = 8;            // chunks prefetched into L2 ahead of the copies
 constexpr int kInvThreads = 320;           // copy warp, MMA warp, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
 constexpr size_t kSmemLimit = 227 * 1024;
@@ -191,16 +193,20 @@ struct PieceIter {
 // apply the Kronecker factor and store (atomically adding when the tile is
 // shared with the neighbouring CTA, whose rows were zeroed by the pack
 // kernel; two addends onto zero give the same sum in either order).
-// shared memory: stages of {A (raw, then high part) 16 KB | A remainder
-// 16 KB | packed residual 2N x 32 x 4 B}, the N x N factor, barriers.
+// The CTA's inverse chunks are one contiguous range of memory, prefetched
+// into L2 kInvPrefetch chunks ahead of the bulk copies.  Shared memory:
+// stages of {A (raw, then high part) 16 KB | packed residual 2N x 32 x 4 B},
+// a ring of two A remainders (chunk c's slot is free once the MMAs of chunk
+// c - 2 completed), the N x N factor, barriers.
 template <int NB>
 __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   constexpr int N = 16 * NB;
-  constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4, STAGE = 2 * SA + SB;
+  constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4, STAGE = SA + SB;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int S = a.stages;
-  float* Ms = reinterpret_cast<float*>(sm + S * STAGE);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S * STAGE + N * N * 4);
+  unsigned char* lo_ring = sm + S * STAGE;
+  float* Ms = reinterpret_cast<float*>(lo_ring + kInvLoSlots * SA);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(lo_ring + kInvLoSlots * SA + N * N * 4);
   uint64_t* full = bars;                      // [S] copies landed
   uint64_t* split = bars + kInvMaxStages;     // [S] split done (128 arrivals)
   uint64_t* empty = bars + 2 * kInvMaxStages; // [S] MMAs of the stage done
@@ -261,6 +267,8 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       bool sp;
       int it = 0;
       bool ok = true;
+      for (int64_t g = g0; g < g1 && g < g0 + kInvPrefetch; ++g)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a.ainv + g * kInvChunk), "r"(SA) : "memory");
       while (ok && pi.next(t, cb, ce, sp)) {
         const int64_t gt = tile_start[t];
         const int64_t gb = box_chunk0[tile_box[t]];
@@ -274,7 +282,13 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
           unsigned char* st = sm + s * STAGE;
           mbar_expect_tx(full + s, SA + SB);
           bulk_load_stream(st, a.ainv + (gt + c) * kInvChunk, SA, full + s, pol);
-          bulk_load(st + 2 * SA, a.bpack + (gb + c) * (2 * N * kInvKC), SB, full + s);
+          bulk_load(st + SA, a.bpack + (gb + c) * (2 * N * kInvKC), SB, full + s);
+          // the CTA's chunks are consecutive: chunk `it` is g0 + it
+          if (g0 + it + kInvPrefetch < g1)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a.ainv + (g0 + it + kInvPrefetch) *
+                                                                                      kInvChunk),
+                         "r"(SA)
+                         : "memory");
         }
       }
       // every copy lands before the CTA's shared memory is released
@@ -309,7 +323,8 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const uint32_t ah = smem_addr(sm + s * STAGE), al = ah + SA, bb = ah + 2 * SA;
+          const uint32_t ah = smem_addr(sm + s * STAGE), bb = ah + SA;
+          const uint32_t al = smem_addr(lo_ring + (it % kInvLoSlots) * SA);
 #pragma unroll
           for (int k8 = 0; k8 < kInvKC / 8; ++k8) {
             const uint64_t dah = smem_desc(ah + 2 * k8 * PLA, PLA, 128);
@@ -347,8 +362,17 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
           ok = false;
           break;
         }
+        // the remainder slot of chunk it - 2 is free once its MMAs completed
+        if (it >= kInvLoSlots) {
+          const int u = it - kInvLoSlots;
+          if (!mbar_wait(empty + u % S, uint32_t((u / S) & 1), a.wait_limit, abort)) {
+            fail();
+            ok = false;
+            break;
+          }
+        }
         float4* ar = reinterpret_cast<float4*>(sm + s * STAGE);
-        float4* al = reinterpret_cast<float4*>(sm + s * STAGE + SA);
+        float4* al = reinterpret_cast<float4*>(lo_ring + (it % kInvLoSlots) * SA);
 #pragma unroll
         for (int q = 0; q < kInvChunk / 4 / 128; ++q) {
           const int e = sid + 128 * q;
@@ -510,8 +534,10 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
   }
 }
 
-size_t inv_stage_bytes(int N) { return 2 * size_t(kInvChunk) * 4 + 2 * size_t(N) * kInvKC * 4; }
-size_t inv_fixed_bytes(int N) { return size_t(N) * N * 4 + (3 * kInvMaxStages + 5) * 8 + 16; }
+size_t inv_stage_bytes(int N) { return size_t(kInvChunk) * 4 + 2 * size_t(N) * kInvKC * 4; }
+size_t inv_fixed_bytes(int N) {
+  return kInvLoSlots * size_t(kInvChunk) * 4 + size_t(N) * N * 4 + (3 * kInvMaxStages + 5) * 8 + 16;
+}
 
 int inv_stages(int P) {
   const int N = (P + 15) / 16 * 16;
