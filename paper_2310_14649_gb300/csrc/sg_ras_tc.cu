@@ -16,8 +16,9 @@
 //
 // Precision: FP32 operands split into a TF32 high part and the remainder,
 // x = xh + xl.  The residual is split once per apply into the stacked
-// operand [rh; rl] (2N rows), the inverse chunk in shared memory after its
-// arrival; then per k-step
+// operand [rh; rl] (2N rows, shared memory), the inverse chunk after its
+// arrival, row by row, into tensor memory (the MMA's A operand there, so
+// the tensor cores read only the residual from shared memory); per k-step
 //     D[:, 0:2N] += Ah [rh; rl]^T,   D[:, 0:N] += Al rh^T
 // (kind::tf32, FP32 accumulation in tensor memory) and the epilogue sums
 // the two column halves: Ah rh + Ah rl + Al rh, the product to FP32
@@ -42,7 +43,6 @@ namespace {
 constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
 constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
 constexpr int kInvMaxStages = 6;           // chunks in flight
-constexpr int kInvLoSlots = 2;             // ring of inverse remainders
 constexpr int kInvPrefetch = 8;            // chunks prefetched into L2 ahead of the copies
 constexpr int kInvThreads = 320;           // copy warp, MMA warp, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
@@ -121,11 +121,23 @@ __device__ __forceinline__ void tc_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_addr(b))
                : "memory");
 }
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// A operand in tensor memory (row m in lane m, k along the columns)
+__device__ __forceinline__ void tc_mma_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// 32 consecutive columns of this thread's lane
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]),
+      "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]),
+      "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
       : "memory");
 }
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
@@ -150,7 +162,10 @@ struct InvArgs {
   int64_t off[kMetaCount];
   const float* M;      // P x P Kronecker factor (row a: coefficients of output mode a)
   int transform;
-  int P, stages, ntiles, tcols, acc_cols;
+  int P, stages, ntiles, tcols;
+  int aslots;    // tensor-memory slots of split inverse chunks (64 columns each, from column 0)
+  int acc_base;  // first column of the accumulators (acc_cols columns each)
+  int acc_cols;
   int64_t chunks;
   int* err;
   int wait_limit;
@@ -186,7 +201,9 @@ struct PieceIter {
 // Persistent kernel, one CTA per SM, chunk range [blockIdx.x * chunks /
 // grid, ...).  Roles: warp 0 lane 0 issues the bulk copies of a stage
 // (inverse chunk + packed residual chunk); warps 2-5 split the inverse
-// chunk in place (high part) and beside it (remainder); warp 1 lane 0 issues
+// chunk, one row per thread, into a tensor-memory slot (high part in
+// columns 0-31, remainder in 32-63; the slot of chunk c is free once the
+// MMAs of chunk c - aslots completed); warp 1 lane 0 issues
 // the MMAs of a stage and commits them to the stage's "empty" barrier and,
 // at the end of a tile piece, to the accumulator's "full" barrier; warps
 // 6-9 read the accumulator (two in tensor memory, alternating by piece),
@@ -195,18 +212,16 @@ struct PieceIter {
 // kernel; two addends onto zero give the same sum in either order).
 // The CTA's inverse chunks are one contiguous range of memory, prefetched
 // into L2 kInvPrefetch chunks ahead of the bulk copies.  Shared memory:
-// stages of {A (raw, then high part) 16 KB | packed residual 2N x 32 x 4 B},
-// a ring of two A remainders (chunk c's slot is free once the MMAs of chunk
-// c - 2 completed), the N x N factor, barriers.
+// stages of {A (raw) 16 KB | packed residual 2N x 32 x 4 B}, the N x N
+// factor, barriers.
 template <int NB>
 __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   constexpr int N = 16 * NB;
   constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4, STAGE = SA + SB;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int S = a.stages;
-  unsigned char* lo_ring = sm + S * STAGE;
-  float* Ms = reinterpret_cast<float*>(lo_ring + kInvLoSlots * SA);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(lo_ring + kInvLoSlots * SA + N * N * 4);
+  float* Ms = reinterpret_cast<float*>(sm + S * STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S * STAGE + N * N * 4);
   uint64_t* full = bars;                      // [S] copies landed
   uint64_t* split = bars + kInvMaxStages;     // [S] split done (128 arrivals)
   uint64_t* empty = bars + 2 * kInvMaxStages; // [S] MMAs of the stage done
@@ -306,7 +321,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       int it = 0, pc = 0;
       bool ok = true, any = false;
       const uint32_t id2 = tf32_desc(128, 2 * N), id1 = tf32_desc(128, N);
-      constexpr uint32_t PLA = 128 * 16, PLB = 2 * N * 16;
+      constexpr uint32_t PLB = 2 * N * 16;
       while (ok && pi.next(t, cb, ce, sp)) {
         const int acc = pc & 1;
         if (pc >= 2 && !mbar_wait(acce + acc, uint32_t((pc / 2 - 1) & 1), a.wait_limit, abort)) {
@@ -314,7 +329,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t d = tmem + uint32_t(acc * a.acc_cols);
+        const uint32_t d = tmem + uint32_t(a.acc_base + acc * a.acc_cols);
         for (int c = cb; c < ce; ++c, ++it) {
           const int s = it % S;
           if (!mbar_wait(split + s, uint32_t((it / S) & 1), a.wait_limit, abort)) {
@@ -323,15 +338,13 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const uint32_t ah = smem_addr(sm + s * STAGE), bb = ah + SA;
-          const uint32_t al = smem_addr(lo_ring + (it % kInvLoSlots) * SA);
+          const uint32_t bb = smem_addr(sm + s * STAGE) + SA;
+          const uint32_t ta = tmem + uint32_t(64 * (it % a.aslots));
 #pragma unroll
           for (int k8 = 0; k8 < kInvKC / 8; ++k8) {
-            const uint64_t dah = smem_desc(ah + 2 * k8 * PLA, PLA, 128);
-            const uint64_t dal = smem_desc(al + 2 * k8 * PLA, PLA, 128);
             const uint64_t db = smem_desc(bb + 2 * k8 * PLB, PLB, 128);
-            tc_mma(d, dah, db, id2, (c > cb || k8 > 0) ? 1u : 0u);
-            tc_mma(d, dal, db, id1, 1u);
+            tc_mma_ta(d, ta + 8 * k8, db, id2, (c > cb || k8 > 0) ? 1u : 0u);
+            tc_mma_ta(d, ta + 32 + 8 * k8, db, id1, 1u);
           }
           any = true;
           tc_commit(empty + s);
@@ -347,8 +360,9 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       }
     }
   } else if (warp < 6) {
-    // ---- split of the inverse chunk: high part in place, remainder beside it ----
-    const int sid = tid - 64;
+    // ---- split of the inverse chunk: row m of the chunk into lane m ----
+    const int m = 32 * (warp & 3) + lane;
+    const uint32_t trow = tmem + (uint32_t(32 * (warp & 3)) << 16);
     PieceIter pi(tile_start, a.ntiles, g0, g1);
     int t, cb, ce;
     bool sp;
@@ -357,31 +371,38 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     while (ok && pi.next(t, cb, ce, sp)) {
       for (int c = cb; c < ce; ++c, ++it) {
         const int s = it % S;
-        if (!mbar_wait(full + s, uint32_t((it / S) & 1), a.wait_limit, abort)) {
+        bool got = mbar_wait(full + s, uint32_t((it / S) & 1), a.wait_limit, abort);
+        // the slot of chunk it - aslots is free once its MMAs completed
+        if (got && it >= a.aslots) {
+          const int u = it - a.aslots;
+          got = mbar_wait(empty + u % S, uint32_t((u / S) & 1), a.wait_limit, abort);
+        }
+        // the warp converges before the aligned tensor-memory stores
+        if (!__all_sync(0xffffffffu, got)) {
           fail();
           ok = false;
           break;
         }
-        // the remainder slot of chunk it - 2 is free once its MMAs completed
-        if (it >= kInvLoSlots) {
-          const int u = it - kInvLoSlots;
-          if (!mbar_wait(empty + u % S, uint32_t((u / S) & 1), a.wait_limit, abort)) {
-            fail();
-            ok = false;
-            break;
-          }
-        }
-        float4* ar = reinterpret_cast<float4*>(sm + s * STAGE);
-        float4* al = reinterpret_cast<float4*>(lo_ring + (it % kInvLoSlots) * SA);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const unsigned char* ar = sm + s * STAGE;
+        float hi[kInvKC], lo[kInvKC];
 #pragma unroll
-        for (int q = 0; q < kInvChunk / 4 / 128; ++q) {
-          const int e = sid + 128 * q;
-          const float4 v = ar[e];
-          const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-          ar[e] = h;
-          al[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        for (int q = 0; q < kInvKC / 4; ++q) {
+          const float4 v = *reinterpret_cast<const float4*>(ar + q * 2048 + m * 16);
+          hi[4 * q] = tf32_hi(v.x);
+          hi[4 * q + 1] = tf32_hi(v.y);
+          hi[4 * q + 2] = tf32_hi(v.z);
+          hi[4 * q + 3] = tf32_hi(v.w);
+          lo[4 * q] = v.x - hi[4 * q];
+          lo[4 * q + 1] = v.y - hi[4 * q + 1];
+          lo[4 * q + 2] = v.z - hi[4 * q + 2];
+          lo[4 * q + 3] = v.w - hi[4 * q + 3];
         }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const uint32_t ta = trow + uint32_t(64 * (it % a.aslots));
+        tc_st32(ta, hi);
+        tc_st32(ta + 32, lo);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         mbar_arrive(split + s);
       }
     }
@@ -403,7 +424,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       float y[N];
-      const uint32_t base = tmem + (uint32_t(32 * lg) << 16) + uint32_t(acc * a.acc_cols);
+      const uint32_t base = tmem + (uint32_t(32 * lg) << 16) + uint32_t(a.acc_base + acc * a.acc_cols);
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
         float lo[16];
@@ -455,40 +476,46 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
 // The residual of every box in the operand layout of its chunks: chunk
 // (box b, c) holds, for the overlapped nodes j = 32 c .. 32 c + 31, the
 // rows n < N (high parts of r[n][idx_b[j]]) and N + n (remainders), planes
-// of 4 nodes (16 bytes per row).  Also zeroes the output rows of the tiles
-// that two CTAs accumulate into.
-__global__ void k_ras_inv_pack(const float* __restrict__ R, int64_t ld, int P, int N, int64_t nb4,
-                               const int* __restrict__ meta, InvArgs a, float* __restrict__ bpack, int nsplit,
-                               int Kp) {
+// of 4 nodes (16 bytes per row).  One block per chunk: the gather reads
+// runs of consecutive nodes of a mode row into shared memory, the writes
+// are whole 16-byte rows of a plane.  The remaining blocks' threads zero
+// the output rows of the tiles that two CTAs accumulate into.
+constexpr int kPackThreads = 256;
+__global__ void __launch_bounds__(kPackThreads) k_ras_inv_pack(const float* __restrict__ R, int64_t ld, int P, int N,
+                                                               int64_t bchunks, InvArgs a, float* __restrict__ bpack,
+                                                               int nsplit, int Kp) {
+  __shared__ float tile[96][kInvKC + 1];
+  const int* meta = a.meta;
   const int* chunk_box = meta + a.off[kChunkBox];
   const int* box_chunk0 = meta + a.off[kBoxChunk0];
   const int* idx = meta + a.off[kIdx];
   const int* nov = meta + a.off[kNov];
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  const int64_t t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  for (int64_t f = t0; f < nb4; f += stride) {
-    const int n = int(f % N);
-    const int64_t r = f / N;
-    const int q = int(r % (kInvKC / 4));
-    const int64_t gc = r / (kInvKC / 4);
+  const int tid = threadIdx.x;
+  for (int64_t gc = blockIdx.x; gc < bchunks; gc += gridDim.x) {
     const int b = chunk_box[gc];
-    const int j0 = int(gc - box_chunk0[b]) * kInvKC + 4 * q;
+    const int j0 = int(gc - box_chunk0[b]) * kInvKC;
     const int nb = nov[b];
-    float v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int j = j0 + k;
-      v[k] = (n < P && j < nb) ? R[int64_t(n) * ld + idx[int64_t(b) * Kp + j]] : 0.f;
+    const int* ib = idx + int64_t(b) * Kp;
+    for (int e = tid; e < N * kInvKC; e += kPackThreads) {
+      const int n = e / kInvKC, k = e % kInvKC, j = j0 + k;
+      tile[n][k] = (n < P && j < nb) ? R[int64_t(n) * ld + ib[j]] : 0.f;
     }
-    const float4 h = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
-    float4* out = reinterpret_cast<float4*>(bpack + gc * (2 * N * kInvKC)) + q * 2 * N;
-    out[n] = h;
-    out[N + n] = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
+    __syncthreads();
+    float4* out = reinterpret_cast<float4*>(bpack + gc * (2 * N * kInvKC));
+    for (int e = tid; e < (kInvKC / 4) * N; e += kPackThreads) {
+      const int q = e / N, n = e % N;
+      const float v0 = tile[n][4 * q], v1 = tile[n][4 * q + 1], v2 = tile[n][4 * q + 2], v3 = tile[n][4 * q + 3];
+      const float4 h = make_float4(tf32_hi(v0), tf32_hi(v1), tf32_hi(v2), tf32_hi(v3));
+      out[q * 2 * N + n] = h;
+      out[q * 2 * N + N + n] = make_float4(v0 - h.x, v1 - h.y, v2 - h.z, v3 - h.w);
+    }
+    __syncthreads();
   }
   const int* split_tile = meta + a.off[kSplitTile];
   const int* tile_owned = meta + a.off[kTileOwned];
   const int64_t nz = int64_t(nsplit) * 128 * P;
-  for (int64_t e = t0; e < nz; e += stride) {
+  const int64_t stride = int64_t(gridDim.x) * kPackThreads;
+  for (int64_t e = blockIdx.x * int64_t(kPackThreads) + tid; e < nz; e += stride) {
     const int c = int(e % P);
     const int64_t r = e / P;
     const int g = tile_owned[int64_t(split_tile[r / 128]) * 128 + int(r % 128)];
@@ -535,9 +562,7 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
 }
 
 size_t inv_stage_bytes(int N) { return size_t(kInvChunk) * 4 + 2 * size_t(N) * kInvKC * 4; }
-size_t inv_fixed_bytes(int N) {
-  return kInvLoSlots * size_t(kInvChunk) * 4 + size_t(N) * N * 4 + (3 * kInvMaxStages + 5) * 8 + 16;
-}
+size_t inv_fixed_bytes(int N) { return size_t(N) * N * 4 + (3 * kInvMaxStages + 5) * 8 + 16; }
 
 int inv_stages(int P) {
   const int N = (P + 15) / 16 * 16;
@@ -737,16 +762,20 @@ sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld
   a.P = P;
   a.stages = D.inv_stages;
   a.ntiles = D.inv_ntiles;
-  a.acc_cols = 32;  // a power of two >= 2N: the accumulators start at columns 0 and acc_cols
-  while (a.acc_cols < 2 * N) a.acc_cols *= 2;
-  a.tcols = 2 * a.acc_cols;
+  // tensor memory (512 columns): the split inverse chunks in slots of 64
+  // columns from column 0, then two accumulators of 2N columns (rounded to
+  // 64); four slots when they fit, else two
+  a.acc_cols = (2 * N + 63) / 64 * 64;
+  a.aslots = 2 * a.acc_cols <= 256 ? 4 : 2;
+  a.acc_base = 64 * a.aslots;
+  a.tcols = 512;
   a.chunks = D.inv_chunks;
   a.err = dp<int>(D.d_inv_err);
   a.wait_limit = wait_limit;
-  const int64_t nb4 = D.inv_bchunks * (kInvKC / 4) * N;
-  const int pgrid = int(std::min<int64_t>(8 * 152, (nb4 + 255) / 256));
-  k_ras_inv_pack<<<unsigned(std::max(pgrid, 1)), 256, 0, st>>>(R, ld, P, N, nb4, a.meta, a, dp<float>(D.d_inv_bpack),
-                                                              D.inv_nsplit, D.inv_kp);
+  const int pgrid = int(std::min<int64_t>(D.inv_bchunks, 8 * 152));
+  k_ras_inv_pack<<<unsigned(std::max(pgrid, 1)), kPackThreads, 0, st>>>(R, ld, P, N, D.inv_bchunks, a,
+                                                                       dp<float>(D.d_inv_bpack), D.inv_nsplit,
+                                                                       D.inv_kp);
   note_launch();
   SG_CUDA(cudaGetLastError());
   switch (N / 16) {
