@@ -42,8 +42,14 @@ namespace {
 
 constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
 constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
-constexpr int kInvMaxStages = 6;           // chunks in flight
-constexpr int kInvPrefetch = 8;            // chunks prefetched into L2 ahead of the copies
+#ifndef SG_INV_MAX_STAGES
+#define SG_INV_MAX_STAGES 6
+#endif
+#ifndef SG_INV_PREFETCH
+#define SG_INV_PREFETCH 8
+#endif
+constexpr int kInvMaxStages = SG_INV_MAX_STAGES;  // chunks in flight
+constexpr int kInvPrefetch = SG_INV_PREFETCH;  // chunks prefetched into L2 ahead of the copies
 constexpr int kInvThreads = 320;           // copy warp, MMA warp, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
 constexpr size_t kSmemLimit = 227 * 1024;
@@ -495,11 +501,14 @@ __global__ void __launch_bounds__(kPackThreads) k_ras_inv_pack(const float* __re
     const int b = chunk_box[gc];
     const int j0 = int(gc - box_chunk0[b]) * kInvKC;
     const int nb = nov[b];
-    const int* ib = idx + int64_t(b) * Kp;
-    for (int e = tid; e < N * kInvKC; e += kPackThreads) {
-      const int n = e / kInvKC, k = e % kInvKC, j = j0 + k;
-      tile[n][k] = (n < P && j < nb) ? R[int64_t(n) * ld + ib[j]] : 0.f;
-    }
+    // thread (k, n0): node j0 + k of every eighth mode row from n0, the
+    // node index loaded once and the rows' loads independent
+    const int k = tid % kInvKC, n0 = tid / kInvKC;
+    const int j = j0 + k;
+    const int gi = j < nb ? idx[int64_t(b) * Kp + j] : -1;
+#pragma unroll 4
+    for (int n = n0; n < N; n += kPackThreads / kInvKC)
+      tile[n][k] = (n < P && gi >= 0) ? R[int64_t(n) * ld + gi] : 0.f;
     __syncthreads();
     float4* out = reinterpret_cast<float4*>(bpack + gc * (2 * N * kInvKC));
     for (int e = tid; e < (kInvKC / 4) * N; e += kPackThreads) {
