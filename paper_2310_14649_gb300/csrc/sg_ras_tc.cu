@@ -170,8 +170,10 @@ struct InvArgs {
   int transform;
   int P, stages, ntiles, tcols;
   int aslots;    // tensor-memory slots of split inverse chunks (64 columns each, from column 0)
-  int acc_base;  // first column of the accumulators (acc_cols columns each)
-  int acc_cols;
+  int acc_base;  // first column of the accumulators
+  int kch;       // independent accumulation chains per accumulator (k-steps alternate between them)
+  int nbuf;      // accumulators (alternating by tile piece)
+  int chain_cols;  // columns of one chain: [Ah rh | Ah rl | Al rh], 3N rounded up to 32
   int64_t chunks;
   int* err;
   int wait_limit;
@@ -329,13 +331,16 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       const uint32_t id2 = tf32_desc(128, 2 * N), id1 = tf32_desc(128, N);
       constexpr uint32_t PLB = 2 * N * 16;
       while (ok && pi.next(t, cb, ce, sp)) {
-        const int acc = pc & 1;
-        if (pc >= 2 && !mbar_wait(acce + acc, uint32_t((pc / 2 - 1) & 1), a.wait_limit, abort)) {
+        const int acc = pc % a.nbuf;
+        if (pc >= a.nbuf && !mbar_wait(acce + acc, uint32_t((pc / a.nbuf - 1) & 1), a.wait_limit, abort)) {
           fail();
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t d = tmem + uint32_t(a.acc_base + acc * a.acc_cols);
+        // back-to-back MMAs into one accumulator wait for each other: the
+        // high and remainder products, and the k-steps of alternate chains,
+        // go to separate columns
+        const uint32_t d = tmem + uint32_t(a.acc_base + acc * a.kch * a.chain_cols);
         for (int c = cb; c < ce; ++c, ++it) {
           const int s = it % S;
           if (!mbar_wait(split + s, uint32_t((it / S) & 1), a.wait_limit, abort)) {
@@ -349,8 +354,10 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
 #pragma unroll
           for (int k8 = 0; k8 < kInvKC / 8; ++k8) {
             const uint64_t db = smem_desc(bb + 2 * k8 * PLB, PLB, 128);
-            tc_mma_ta(d, ta + 8 * k8, db, id2, (c > cb || k8 > 0) ? 1u : 0u);
-            tc_mma_ta(d, ta + 32 + 8 * k8, db, id1, 1u);
+            const uint32_t dc = d + uint32_t((k8 % a.kch) * a.chain_cols);
+            const uint32_t first = (c == cb && k8 < a.kch) ? 0u : 1u;
+            tc_mma_ta(dc, ta + 8 * k8, db, id2, first);
+            tc_mma_ta(dc + 2 * N, ta + 32 + 8 * k8, db, id1, first);
           }
           any = true;
           tc_commit(empty + s);
@@ -421,24 +428,31 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     bool sp;
     int pc = 0;
     while (pi.next(t, cb, ce, sp)) {
-      const int acc = pc & 1;
+      const int acc = pc % a.nbuf;
       // the warp converges before the aligned tensor-memory loads
-      const bool got = mbar_wait(accf + acc, uint32_t((pc / 2) & 1), a.wait_limit, abort);
+      const bool got = mbar_wait(accf + acc, uint32_t((pc / a.nbuf) & 1), a.wait_limit, abort);
       if (!__all_sync(0xffffffffu, got)) {
         fail();
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       float y[N];
-      const uint32_t base = tmem + (uint32_t(32 * lg) << 16) + uint32_t(a.acc_base + acc * a.acc_cols);
+      const uint32_t base =
+          tmem + (uint32_t(32 * lg) << 16) + uint32_t(a.acc_base + acc * a.kch * a.chain_cols);
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
-        float lo[16];
-        tc_ld16(base + 16 * j, y + 16 * j);
-        tc_ld16(base + N + 16 * j, lo);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < 16; ++q) y[16 * j + q] += lo[q];
+        for (int q = 0; q < 16; ++q) y[16 * j + q] = 0.f;
+        for (int ch = 0; ch < a.kch; ++ch) {
+          float p0[16], p1[16], p2[16];
+          const uint32_t cbase = base + uint32_t(ch * a.chain_cols + 16 * j);
+          tc_ld16(cbase, p0);
+          tc_ld16(cbase + N, p1);
+          tc_ld16(cbase + 2 * N, p2);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 16; ++q) y[16 * j + q] += (p0[q] + p2[q]) + p1[q];
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       mbar_arrive(acce + acc);
@@ -772,12 +786,26 @@ sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld
   a.stages = D.inv_stages;
   a.ntiles = D.inv_ntiles;
   // tensor memory (512 columns): the split inverse chunks in slots of 64
-  // columns from column 0, then two accumulators of 2N columns (rounded to
-  // 64); four slots when they fit, else two
-  a.acc_cols = (2 * N + 63) / 64 * 64;
-  a.aslots = 2 * a.acc_cols <= 256 ? 4 : 2;
-  a.acc_base = 64 * a.aslots;
+  // columns from column 0, then the accumulators, each of kch chains of
+  // chain_cols columns.  Preferred: two chains, two accumulators, four
+  // slots; fewer where 512 columns do not hold them (two chains count more
+  // than a second accumulator: a tile piece is 40 chunks of MMAs).
+  a.chain_cols = (3 * N + 31) / 32 * 32;
   a.tcols = 512;
+  const int shapes[6][3] = {{2, 2, 4}, {2, 2, 2}, {2, 1, 3}, {2, 1, 2}, {1, 1, 4}, {1, 1, 2}};
+  a.kch = 0;
+  for (const auto& sh : shapes)
+    if (64 * sh[2] + sh[0] * sh[1] * a.chain_cols <= 512) {
+      a.kch = sh[0];
+      a.nbuf = sh[1];
+      a.aslots = sh[2];
+      break;
+    }
+  if (!a.kch) {
+    set_error("ras_inverse_apply: tensor memory too small for P modes");
+    return SG_ERR_UNSUPPORTED;
+  }
+  a.acc_base = 64 * a.aslots;
   a.chunks = D.inv_chunks;
   a.err = dp<int>(D.d_inv_err);
   a.wait_limit = wait_limit;
