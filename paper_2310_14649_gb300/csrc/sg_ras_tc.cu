@@ -50,7 +50,7 @@ constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB
 #endif
 constexpr int kInvMaxStages = SG_INV_MAX_STAGES;  // chunks in flight
 constexpr int kInvPrefetch = SG_INV_PREFETCH;  // chunks prefetched into L2 ahead of the copies
-constexpr int kInvThreads = 320;           // copy warp, MMA warp, 4 split warps, 4 epilogue warps
+constexpr int kInvThreads = 352;           // copy warp, 2 MMA warps, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -211,9 +211,11 @@ struct PieceIter {
 // (inverse chunk + packed residual chunk); warps 2-5 split the inverse
 // chunk, one row per thread, into a tensor-memory slot (high part in
 // columns 0-31, remainder in 32-63; the slot of chunk c is free once the
-// MMAs of chunk c - aslots completed); warp 1 lane 0 issues
-// the MMAs of a stage and commits them to the stage's "empty" barrier and,
-// at the end of a tile piece, to the accumulator's "full" barrier; warps
+// MMAs of chunk c - aslots completed); lane 0 of warp 1 (and of warp 10
+// when there are two chains: each warp issues the k-steps of its chain, so
+// the issue of small MMAs runs on two threads) issues the MMAs of a stage
+// and commits them to the stage's "empty" barrier and, at the end of a
+// tile piece, to the accumulator's "full" barrier; warps
 // 6-9 read the accumulator (two in tensor memory, alternating by piece),
 // apply the Kronecker factor and store (atomically adding when the tile is
 // shared with the neighbouring CTA, whose rows were zeroed by the pack
@@ -235,8 +237,8 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   uint64_t* empty = bars + 2 * kInvMaxStages; // [S] MMAs of the stage done
   uint64_t* accf = bars + 3 * kInvMaxStages;  // [2] accumulator complete
   uint64_t* acce = accf + 2;                  // [2] accumulator read (128 arrivals)
-  uint64_t* fin = acce + 2;                   // last MMA done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+  uint64_t* fin = acce + 2;                   // [2] last MMA of each issuer done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int* meta = a.meta;
@@ -259,13 +261,14 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     for (int s = 0; s < kInvMaxStages; ++s) {
       mbar_init(full + s, 1);
       mbar_init(split + s, 128);
-      mbar_init(empty + s, 1);
+      mbar_init(empty + s, a.kch);
     }
     for (int k = 0; k < 2; ++k) {
-      mbar_init(accf + k, 1);
+      mbar_init(accf + k, a.kch);
       mbar_init(acce + k, 128);
     }
     mbar_init(fin, 1);
+    mbar_init(fin + 1, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -320,9 +323,11 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
         mbar_wait(full + s, uint32_t((u / S) & 1), kInvDrain, nullptr);
       }
     }
-  } else if (warp == 1) {
-    // ---- MMAs ----
-    if (lane == 0) {
+  } else if (warp == 1 || warp == 10) {
+    // ---- MMAs: issuer q, k-steps of chain q (all k-steps with one chain) ----
+    const int q = warp == 10 ? 1 : 0;
+    const int k0 = a.kch == 2 ? 2 * q : 0, k1 = a.kch == 2 ? k0 + 2 : kInvKC / 8;
+    if (lane == 0 && q < a.kch) {
       PieceIter pi(tile_start, a.ntiles, g0, g1);
       int t, cb, ce;
       bool sp;
@@ -351,11 +356,10 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const uint32_t bb = smem_addr(sm + s * STAGE) + SA;
           const uint32_t ta = tmem + uint32_t(64 * (it % a.aslots));
-#pragma unroll
-          for (int k8 = 0; k8 < kInvKC / 8; ++k8) {
+          const uint32_t dc = d + uint32_t(q * a.chain_cols);
+          for (int k8 = k0; k8 < k1; ++k8) {
             const uint64_t db = smem_desc(bb + 2 * k8 * PLB, PLB, 128);
-            const uint32_t dc = d + uint32_t((k8 % a.kch) * a.chain_cols);
-            const uint32_t first = (c == cb && k8 < a.kch) ? 0u : 1u;
+            const uint32_t first = (c == cb && k8 == k0) ? 0u : 1u;
             tc_mma_ta(dc, ta + 8 * k8, db, id2, first);
             tc_mma_ta(dc + 2 * N, ta + 32 + 8 * k8, db, id1, first);
           }
@@ -368,8 +372,8 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       }
       // every MMA completes before tensor memory is freed
       if (any) {
-        tc_commit(fin);
-        mbar_wait(fin, 0u, kInvDrain, nullptr);
+        tc_commit(fin + q);
+        mbar_wait(fin + q, 0u, kInvDrain, nullptr);
       }
     }
   } else if (warp < 6) {
@@ -585,7 +589,7 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
 }
 
 size_t inv_stage_bytes(int N) { return size_t(kInvChunk) * 4 + 2 * size_t(N) * kInvKC * 4; }
-size_t inv_fixed_bytes(int N) { return size_t(N) * N * 4 + (3 * kInvMaxStages + 5) * 8 + 16; }
+size_t inv_fixed_bytes(int N) { return size_t(N) * N * 4 + (3 * kInvMaxStages + 6) * 8 + 16; }
 
 int inv_stages(int P) {
   const int N = (P + 15) / 16 * 16;
