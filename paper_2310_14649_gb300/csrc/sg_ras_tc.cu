@@ -42,15 +42,10 @@ namespace {
 
 constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
 constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
-#ifndef SG_INV_MAX_STAGES
-#define SG_INV_MAX_STAGES 6
-#endif
-#ifndef SG_INV_PREFETCH
-#define SG_INV_PREFETCH 8
-#endif
-constexpr int kInvMaxStages = SG_INV_MAX_STAGES;  // chunks in flight
-constexpr int kInvPrefetch = SG_INV_PREFETCH;  // chunks prefetched into L2 ahead of the copies
-constexpr int kInvThreads = 352;           // copy warp, 2 MMA warps, 4 split warps, 4 epilogue warps
+constexpr int kInvMaxA = 12;               // inverse chunks in flight (ring freed by the split)
+constexpr int kInvMaxB = 4;                // packed residual chunks in flight (ring freed by the MMAs)
+constexpr int kInvMaxSlots = 4;            // tensor-memory slots of split chunks
+constexpr int kInvThreads = 384;           // 2 copy warps, 2 MMA warps, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -168,7 +163,7 @@ struct InvArgs {
   int64_t off[kMetaCount];
   const float* M;      // P x P Kronecker factor (row a: coefficients of output mode a)
   int transform;
-  int P, stages, ntiles, tcols;
+  int P, astages, bstages, ntiles, tcols;
   int aslots;    // tensor-memory slots of split inverse chunks (64 columns each, from column 0)
   int acc_base;  // first column of the accumulators
   int kch;       // independent accumulation chains per accumulator (k-steps alternate between them)
@@ -207,35 +202,44 @@ struct PieceIter {
 };
 
 // Persistent kernel, one CTA per SM, chunk range [blockIdx.x * chunks /
-// grid, ...).  Roles: warp 0 lane 0 issues the bulk copies of a stage
-// (inverse chunk + packed residual chunk); warps 2-5 split the inverse
-// chunk, one row per thread, into a tensor-memory slot (high part in
-// columns 0-31, remainder in 32-63; the slot of chunk c is free once the
-// MMAs of chunk c - aslots completed); lane 0 of warp 1 (and of warp 10
-// when there are two chains: each warp issues the k-steps of its chain, so
-// the issue of small MMAs runs on two threads) issues the MMAs of a stage
-// and commits them to the stage's "empty" barrier and, at the end of a
-// tile piece, to the accumulator's "full" barrier; warps
-// 6-9 read the accumulator (two in tensor memory, alternating by piece),
-// apply the Kronecker factor and store (atomically adding when the tile is
-// shared with the neighbouring CTA, whose rows were zeroed by the pack
-// kernel; two addends onto zero give the same sum in either order).
-// The CTA's inverse chunks are one contiguous range of memory, prefetched
-// into L2 kInvPrefetch chunks ahead of the bulk copies.  Shared memory:
-// stages of {A (raw) 16 KB | packed residual 2N x 32 x 4 B}, the N x N
-// factor, barriers.
+// grid, ...): chunk `it` of the CTA is global chunk g0 + it, so its
+// inverse chunks are one contiguous range of memory.  Roles (lane 0 where
+// one thread acts):
+//  * warp 0 copies inverse chunks into ring A (16 KB stages, freed as soon
+//    as the split threads have read them);
+//  * warp 11 copies packed residual chunks into ring B (2N x 32 x 4 B
+//    stages, freed when the MMAs reading them completed);
+//  * warps 2-5 split an inverse chunk, one row per thread, into a
+//    tensor-memory slot (high part in columns 0-31, remainder in 32-63; the
+//    slot of chunk c is free once the MMAs of chunk c - aslots completed);
+//  * warps 1 and 10 issue the MMAs (with two chains each warp issues the
+//    k-steps of its chain, so the issue of these small MMAs runs on two
+//    threads) and commit them to the B stage's and the slot's barriers and,
+//    at the end of a tile piece, to the accumulator's "full" barrier;
+//  * warps 6-9 read the accumulator (alternating by piece when there are
+//    two), apply the Kronecker factor and store (atomically adding when the
+//    tile is shared with the neighbouring CTA, whose rows were zeroed by the
+//    pack kernel; two addends onto zero give the same sum in either order).
+// Separate rings keep the inverse stream deep: its stages turn over after
+// the copy latency and the split, not after the MMAs.  Shared memory: ring
+// A, ring B, the N x N factor, barriers.
 template <int NB>
 __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   constexpr int N = 16 * NB;
-  constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4, STAGE = SA + SB;
+  constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4;
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int S = a.stages;
-  float* Ms = reinterpret_cast<float*>(sm + S * STAGE);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S * STAGE + N * N * 4);
-  uint64_t* full = bars;                      // [S] copies landed
-  uint64_t* split = bars + kInvMaxStages;     // [S] split done (128 arrivals)
-  uint64_t* empty = bars + 2 * kInvMaxStages; // [S] MMAs of the stage done
-  uint64_t* accf = bars + 3 * kInvMaxStages;  // [2] accumulator complete
+  const int QA = a.astages, QB = a.bstages, NS = a.aslots;
+  unsigned char* ring_a = sm;
+  unsigned char* ring_b = sm + QA * SA;
+  float* Ms = reinterpret_cast<float*>(ring_b + QB * SB);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring_b + QB * SB + N * N * 4);
+  uint64_t* afull = bars;                     // [QA] inverse chunk landed
+  uint64_t* aempty = afull + kInvMaxA;        // [QA] inverse chunk read (128 arrivals)
+  uint64_t* bfull = aempty + kInvMaxA;        // [QB] residual chunk landed
+  uint64_t* bempty = bfull + kInvMaxB;        // [QB] its MMAs done (kch commits)
+  uint64_t* split = bempty + kInvMaxB;        // [NS] slot written (128 arrivals)
+  uint64_t* tfree = split + kInvMaxSlots;     // [NS] slot's MMAs done (kch commits)
+  uint64_t* accf = tfree + kInvMaxSlots;      // [2] accumulator complete (kch commits)
   uint64_t* acce = accf + 2;                  // [2] accumulator read (128 arrivals)
   uint64_t* fin = acce + 2;                   // [2] last MMA of each issuer done
   uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 2);
@@ -245,6 +249,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   const int* tile_start = meta + a.off[kTileStart];
   const int64_t g0 = int64_t(blockIdx.x) * a.chunks / gridDim.x;
   const int64_t g1 = int64_t(blockIdx.x + 1) * a.chunks / gridDim.x;
+  const int nch = int(g1 - g0);
 
   if (a.transform)
     for (int e = tid; e < N * N; e += kInvThreads) {
@@ -258,17 +263,23 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < kInvMaxStages; ++s) {
-      mbar_init(full + s, 1);
+    for (int s = 0; s < kInvMaxA; ++s) {
+      mbar_init(afull + s, 1);
+      mbar_init(aempty + s, 128);
+    }
+    for (int s = 0; s < kInvMaxB; ++s) {
+      mbar_init(bfull + s, 1);
+      mbar_init(bempty + s, a.kch);
+    }
+    for (int s = 0; s < kInvMaxSlots; ++s) {
       mbar_init(split + s, 128);
-      mbar_init(empty + s, a.kch);
+      mbar_init(tfree + s, a.kch);
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(accf + k, a.kch);
       mbar_init(acce + k, 128);
+      mbar_init(fin + k, 1);
     }
-    mbar_init(fin, 1);
-    mbar_init(fin + 1, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -282,10 +293,27 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   };
 
   if (warp == 0) {
-    // ---- copies ----
+    // ---- inverse chunks into ring A ----
     if (lane == 0) {
       uint64_t pol;
       asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+      int it = 0;
+      for (; it < nch; ++it) {
+        const int s = it % QA;
+        if (it >= QA && !mbar_wait(aempty + s, uint32_t((it / QA - 1) & 1), a.wait_limit, abort)) {
+          fail();
+          break;
+        }
+        mbar_expect_tx(afull + s, SA);
+        bulk_load_stream(ring_a + s * SA, a.ainv + (g0 + it) * kInvChunk, SA, afull + s, pol);
+      }
+      // every copy lands before the CTA's shared memory is released
+      for (int s = 0; s < QA && s < it; ++s)
+        mbar_wait(afull + s, uint32_t(((s + QA * ((it - 1 - s) / QA)) / QA) & 1), kInvDrain, nullptr);
+    }
+  } else if (warp == 11) {
+    // ---- packed residual chunks into ring B ----
+    if (lane == 0) {
       const int* tile_box = meta + a.off[kTileBox];
       const int* box_chunk0 = meta + a.off[kBoxChunk0];
       PieceIter pi(tile_start, a.ntiles, g0, g1);
@@ -293,35 +321,21 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       bool sp;
       int it = 0;
       bool ok = true;
-      for (int64_t g = g0; g < g1 && g < g0 + kInvPrefetch; ++g)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a.ainv + g * kInvChunk), "r"(SA) : "memory");
       while (ok && pi.next(t, cb, ce, sp)) {
-        const int64_t gt = tile_start[t];
         const int64_t gb = box_chunk0[tile_box[t]];
         for (int c = cb; c < ce; ++c, ++it) {
-          const int s = it % S;
-          if (it >= S && !mbar_wait(empty + s, uint32_t((it / S - 1) & 1), a.wait_limit, abort)) {
+          const int s = it % QB;
+          if (it >= QB && !mbar_wait(bempty + s, uint32_t((it / QB - 1) & 1), a.wait_limit, abort)) {
             fail();
             ok = false;
             break;
           }
-          unsigned char* st = sm + s * STAGE;
-          mbar_expect_tx(full + s, SA + SB);
-          bulk_load_stream(st, a.ainv + (gt + c) * kInvChunk, SA, full + s, pol);
-          bulk_load(st + SA, a.bpack + (gb + c) * (2 * N * kInvKC), SB, full + s);
-          // the CTA's chunks are consecutive: chunk `it` is g0 + it
-          if (g0 + it + kInvPrefetch < g1)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a.ainv + (g0 + it + kInvPrefetch) *
-                                                                                      kInvChunk),
-                         "r"(SA)
-                         : "memory");
+          mbar_expect_tx(bfull + s, SB);
+          bulk_load(ring_b + s * SB, a.bpack + (gb + c) * (2 * N * kInvKC), SB, bfull + s);
         }
       }
-      // every copy lands before the CTA's shared memory is released
-      for (int s = 0; s < S && s < it; ++s) {
-        const int u = s + S * ((it - 1 - s) / S);  // last use of stage s
-        mbar_wait(full + s, uint32_t((u / S) & 1), kInvDrain, nullptr);
-      }
+      for (int s = 0; s < QB && s < it; ++s)
+        mbar_wait(bfull + s, uint32_t(((s + QB * ((it - 1 - s) / QB)) / QB) & 1), kInvDrain, nullptr);
     }
   } else if (warp == 1 || warp == 10) {
     // ---- MMAs: issuer q, k-steps of chain q (all k-steps with one chain) ----
@@ -343,19 +357,20 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         // back-to-back MMAs into one accumulator wait for each other: the
-        // high and remainder products, and the k-steps of alternate chains,
+        // high and remainder products, and the k-steps of the two chains,
         // go to separate columns
         const uint32_t d = tmem + uint32_t(a.acc_base + acc * a.kch * a.chain_cols);
         for (int c = cb; c < ce; ++c, ++it) {
-          const int s = it % S;
-          if (!mbar_wait(split + s, uint32_t((it / S) & 1), a.wait_limit, abort)) {
+          const int sb = it % QB, sl = it % NS;
+          if (!mbar_wait(split + sl, uint32_t((it / NS) & 1), a.wait_limit, abort) ||
+              !mbar_wait(bfull + sb, uint32_t((it / QB) & 1), a.wait_limit, abort)) {
             fail();
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const uint32_t bb = smem_addr(sm + s * STAGE) + SA;
-          const uint32_t ta = tmem + uint32_t(64 * (it % a.aslots));
+          const uint32_t bb = smem_addr(ring_b + sb * SB);
+          const uint32_t ta = tmem + uint32_t(64 * sl);
           const uint32_t dc = d + uint32_t(q * a.chain_cols);
           for (int k8 = k0; k8 < k1; ++k8) {
             const uint64_t db = smem_desc(bb + 2 * k8 * PLB, PLB, 128);
@@ -364,7 +379,8 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
             tc_mma_ta(dc + 2 * N, ta + 32 + 8 * k8, db, id1, first);
           }
           any = true;
-          tc_commit(empty + s);
+          tc_commit(bempty + sb);
+          tc_commit(tfree + sl);
         }
         if (!ok) break;
         tc_commit(accf + acc);
@@ -380,48 +396,40 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     // ---- split of the inverse chunk: row m of the chunk into lane m ----
     const int m = 32 * (warp & 3) + lane;
     const uint32_t trow = tmem + (uint32_t(32 * (warp & 3)) << 16);
-    PieceIter pi(tile_start, a.ntiles, g0, g1);
-    int t, cb, ce;
-    bool sp;
-    int it = 0;
-    bool ok = true;
-    while (ok && pi.next(t, cb, ce, sp)) {
-      for (int c = cb; c < ce; ++c, ++it) {
-        const int s = it % S;
-        bool got = mbar_wait(full + s, uint32_t((it / S) & 1), a.wait_limit, abort);
-        // the slot of chunk it - aslots is free once its MMAs completed
-        if (got && it >= a.aslots) {
-          const int u = it - a.aslots;
-          got = mbar_wait(empty + u % S, uint32_t((u / S) & 1), a.wait_limit, abort);
-        }
-        // the warp converges before the aligned tensor-memory stores
-        if (!__all_sync(0xffffffffu, got)) {
-          fail();
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const unsigned char* ar = sm + s * STAGE;
-        float hi[kInvKC], lo[kInvKC];
-#pragma unroll
-        for (int q = 0; q < kInvKC / 4; ++q) {
-          const float4 v = *reinterpret_cast<const float4*>(ar + q * 2048 + m * 16);
-          hi[4 * q] = tf32_hi(v.x);
-          hi[4 * q + 1] = tf32_hi(v.y);
-          hi[4 * q + 2] = tf32_hi(v.z);
-          hi[4 * q + 3] = tf32_hi(v.w);
-          lo[4 * q] = v.x - hi[4 * q];
-          lo[4 * q + 1] = v.y - hi[4 * q + 1];
-          lo[4 * q + 2] = v.z - hi[4 * q + 2];
-          lo[4 * q + 3] = v.w - hi[4 * q + 3];
-        }
-        const uint32_t ta = trow + uint32_t(64 * (it % a.aslots));
-        tc_st32(ta, hi);
-        tc_st32(ta + 32, lo);
-        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        mbar_arrive(split + s);
+    for (int it = 0; it < nch; ++it) {
+      const int sa = it % QA, sl = it % NS;
+      bool got = mbar_wait(afull + sa, uint32_t((it / QA) & 1), a.wait_limit, abort);
+      // the slot of chunk it - aslots is free once its MMAs completed
+      if (got && it >= NS) got = mbar_wait(tfree + sl, uint32_t((it / NS - 1) & 1), a.wait_limit, abort);
+      // the warp converges before the aligned tensor-memory stores
+      if (!__all_sync(0xffffffffu, got)) {
+        fail();
+        break;
       }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const unsigned char* ar = ring_a + sa * SA;
+      float4 v[kInvKC / 4];
+#pragma unroll
+      for (int q = 0; q < kInvKC / 4; ++q) v[q] = *reinterpret_cast<const float4*>(ar + q * 2048 + m * 16);
+      mbar_arrive(aempty + sa);  // the stage is read: the copy of chunk it + QA may start
+      float hi[kInvKC], lo[kInvKC];
+#pragma unroll
+      for (int q = 0; q < kInvKC / 4; ++q) {
+        hi[4 * q] = tf32_hi(v[q].x);
+        hi[4 * q + 1] = tf32_hi(v[q].y);
+        hi[4 * q + 2] = tf32_hi(v[q].z);
+        hi[4 * q + 3] = tf32_hi(v[q].w);
+        lo[4 * q] = v[q].x - hi[4 * q];
+        lo[4 * q + 1] = v[q].y - hi[4 * q + 1];
+        lo[4 * q + 2] = v[q].z - hi[4 * q + 2];
+        lo[4 * q + 3] = v[q].w - hi[4 * q + 3];
+      }
+      const uint32_t ta = trow + uint32_t(64 * sl);
+      tc_st32(ta, hi);
+      tc_st32(ta + 32, lo);
+      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      mbar_arrive(split + sl);
     }
   } else {
     // ---- epilogue: rows 32 (warp % 4) + lane of the accumulator ----
@@ -588,13 +596,25 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
   }
 }
 
-size_t inv_stage_bytes(int N) { return size_t(kInvChunk) * 4 + 2 * size_t(N) * kInvKC * 4; }
-size_t inv_fixed_bytes(int N) { return size_t(N) * N * 4 + (3 * kInvMaxStages + 6) * 8 + 16; }
-
-int inv_stages(int P) {
+// ring depths for N padded modes: ring B of 4 (3) stages, ring A of the
+// rest of the shared memory (at most kInvMaxA)
+struct InvRings {
+  int qa, qb;
+  size_t smem;
+};
+InvRings inv_rings(int P) {
   const int N = (P + 15) / 16 * 16;
-  const size_t room = kSmemLimit - inv_fixed_bytes(N);
-  return int(std::min<size_t>(kInvMaxStages, room / inv_stage_bytes(N)));
+  const size_t sa = size_t(kInvChunk) * 4, sb = 2 * size_t(N) * kInvKC * 4;
+  const size_t fixed = size_t(N) * N * 4 + (2 * kInvMaxA + 2 * kInvMaxB + 2 * kInvMaxSlots + 6) * 8 + 16;
+  InvRings r{0, 0, 0};
+  for (int qb = kInvMaxB; qb >= 2; --qb) {
+    if (fixed + qb * sb + 2 * sa > kSmemLimit) continue;
+    r.qb = qb;
+    r.qa = int(std::min<size_t>(kInvMaxA, (kSmemLimit - fixed - qb * sb) / sa));
+    r.smem = fixed + qb * sb + r.qa * sa;
+    break;
+  }
+  return r;
 }
 
 template <int NB>
@@ -604,7 +624,7 @@ sg_status inv_launch(const InvArgs& args, int grid, cudaStream_t st) {
     SG_CUDA(cudaFuncSetAttribute(k_ras_inv_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemLimit)));
     attr = true;
   }
-  const size_t smem = args.stages * inv_stage_bytes(16 * NB) + inv_fixed_bytes(16 * NB);
+  const size_t smem = inv_rings(args.P).smem;
   k_ras_inv_tc<NB><<<unsigned(grid), kInvThreads, smem, st>>>(args);
   note_launch();
   SG_CUDA(cudaGetLastError());
@@ -622,7 +642,7 @@ InvArgs inv_args(const RasData& D) {
 
 // the index list of the widest supported box: 48 x 48 overlapped nodes
 constexpr int kInvMaxKp = 48 * 48;
-bool ras_inverse_supported(int P) { return P >= 1 && P <= 96 && inv_stages(P) >= 2; }
+bool ras_inverse_supported(int P) { return P >= 1 && P <= 96 && inv_rings(P).qa >= 2; }
 
 sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   RasData& D = pc.ras;
@@ -751,7 +771,6 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   D.inv_ntiles = ntiles;
   D.inv_grid = grid;
   D.inv_nsplit = int(split_tile.size());
-  D.inv_stages = inv_stages(P);
   D.inv_chunks = chunks;
   D.inv_bchunks = bchunks;
   D.d_inv = std::move(dainv);
@@ -787,7 +806,8 @@ sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld
   a.M = M;
   a.transform = transform ? 1 : 0;
   a.P = P;
-  a.stages = D.inv_stages;
+  a.astages = inv_rings(P).qa;
+  a.bstages = inv_rings(P).qb;
   a.ntiles = D.inv_ntiles;
   // tensor memory (512 columns): the split inverse chunks in slots of 64
   // columns from column 0, then the accumulators, each of kch chains of
