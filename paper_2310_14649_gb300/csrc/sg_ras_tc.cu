@@ -42,8 +42,8 @@ namespace {
 
 constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
 constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
-constexpr int kInvMaxA = 12;               // inverse chunks in flight (ring freed by the split)
-constexpr int kInvMaxB = 4;                // packed residual chunks in flight (ring freed by the MMAs)
+constexpr int kInvMaxA = 8;                // inverse chunk pairs in flight (ring freed by the split)
+constexpr int kInvMaxB = 4;                // packed residual chunk pairs in flight (ring freed by the MMAs)
 constexpr int kInvMaxSlots = 4;            // tensor-memory slots of split chunks
 constexpr int kInvThreads = 384;           // 2 copy warps, 2 MMA warps, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
@@ -203,12 +203,16 @@ struct PieceIter {
 
 // Persistent kernel, one CTA per SM, chunk range [blockIdx.x * chunks /
 // grid, ...): chunk `it` of the CTA is global chunk g0 + it, so its
-// inverse chunks are one contiguous range of memory.  Roles (lane 0 where
-// one thread acts):
-//  * warp 0 copies inverse chunks into ring A (16 KB stages, freed as soon
-//    as the split threads have read them);
-//  * warp 11 copies packed residual chunks into ring B (2N x 32 x 4 B
-//    stages, freed when the MMAs reading them completed);
+// inverse chunks are one contiguous range of memory.  The rings hold
+// chunk pairs: one bulk copy moves a pair (a copy's fixed cost is then
+// spread over 32 KB; single 16 KB copies left an SM's copy engine well
+// short of its share of the memory bandwidth).  Roles (lane 0 where one
+// thread acts):
+//  * warp 0 copies inverse chunk pairs into ring A (32 KB stages, freed as
+//    soon as the split threads have read both chunks);
+//  * warp 11 copies packed residual chunk pairs into ring B (2 x 2N x 32 x
+//    4 B stages, one copy when the pair is contiguous, freed when the MMAs
+//    reading both chunks completed);
 //  * warps 2-5 split an inverse chunk, one row per thread, into a
 //    tensor-memory slot (high part in columns 0-31, remainder in 32-63; the
 //    slot of chunk c is free once the MMAs of chunk c - aslots completed);
@@ -229,14 +233,14 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int QA = a.astages, QB = a.bstages, NS = a.aslots;
-  unsigned char* ring_a = sm;
-  unsigned char* ring_b = sm + QA * SA;
-  float* Ms = reinterpret_cast<float*>(ring_b + QB * SB);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(ring_b + QB * SB + N * N * 4);
-  uint64_t* afull = bars;                     // [QA] inverse chunk landed
-  uint64_t* aempty = afull + kInvMaxA;        // [QA] inverse chunk read (128 arrivals)
-  uint64_t* bfull = aempty + kInvMaxA;        // [QB] residual chunk landed
-  uint64_t* bempty = bfull + kInvMaxB;        // [QB] its MMAs done (kch commits)
+  unsigned char* ring_a = sm;                 // [QA][2][SA]
+  unsigned char* ring_b = sm + QA * 2 * SA;   // [QB][2][SB]
+  float* Ms = reinterpret_cast<float*>(ring_b + QB * 2 * SB);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring_b + QB * 2 * SB + N * N * 4);
+  uint64_t* afull = bars;                     // [QA] inverse chunk pair landed
+  uint64_t* aempty = afull + kInvMaxA;        // [QA] pair read (128 arrivals per chunk)
+  uint64_t* bfull = aempty + kInvMaxA;        // [QB] residual chunk pair landed
+  uint64_t* bempty = bfull + kInvMaxB;        // [QB] its MMAs done (kch commits per chunk)
   uint64_t* split = bempty + kInvMaxB;        // [NS] slot written (128 arrivals)
   uint64_t* tfree = split + kInvMaxSlots;     // [NS] slot's MMAs done (kch commits)
   uint64_t* accf = tfree + kInvMaxSlots;      // [2] accumulator complete (kch commits)
@@ -265,11 +269,11 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   if (tid == 0) {
     for (int s = 0; s < kInvMaxA; ++s) {
       mbar_init(afull + s, 1);
-      mbar_init(aempty + s, 128);
+      mbar_init(aempty + s, 256);
     }
     for (int s = 0; s < kInvMaxB; ++s) {
       mbar_init(bfull + s, 1);
-      mbar_init(bempty + s, a.kch);
+      mbar_init(bempty + s, 2 * a.kch);
     }
     for (int s = 0; s < kInvMaxSlots; ++s) {
       mbar_init(split + s, 128);
@@ -297,45 +301,61 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     if (lane == 0) {
       uint64_t pol;
       asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
-      int it = 0;
-      for (; it < nch; ++it) {
-        const int s = it % QA;
-        if (it >= QA && !mbar_wait(aempty + s, uint32_t((it / QA - 1) & 1), a.wait_limit, abort)) {
+      // pair u holds chunks 2u and 2u + 1 (the last pair of an odd range
+      // one chunk: its stage is never waited for again)
+      const int npair = (nch + 1) / 2;
+      int u = 0;
+      for (; u < npair; ++u) {
+        const int s = u % QA;
+        if (u >= QA && !mbar_wait(aempty + s, uint32_t((u / QA - 1) & 1), a.wait_limit, abort)) {
           fail();
           break;
         }
-        mbar_expect_tx(afull + s, SA);
-        bulk_load_stream(ring_a + s * SA, a.ainv + (g0 + it) * kInvChunk, SA, afull + s, pol);
+        const uint32_t bytes = SA * uint32_t(min(2, nch - 2 * u));
+        mbar_expect_tx(afull + s, bytes);
+        bulk_load_stream(ring_a + s * 2 * SA, a.ainv + (g0 + 2 * u) * kInvChunk, bytes, afull + s, pol);
       }
       // every copy lands before the CTA's shared memory is released
-      for (int s = 0; s < QA && s < it; ++s)
-        mbar_wait(afull + s, uint32_t(((s + QA * ((it - 1 - s) / QA)) / QA) & 1), kInvDrain, nullptr);
+      for (int s = 0; s < QA && s < u; ++s)
+        mbar_wait(afull + s, uint32_t(((s + QA * ((u - 1 - s) / QA)) / QA) & 1), kInvDrain, nullptr);
     }
   } else if (warp == 11) {
     // ---- packed residual chunks into ring B ----
     if (lane == 0) {
       const int* tile_box = meta + a.off[kTileBox];
       const int* box_chunk0 = meta + a.off[kBoxChunk0];
+      // the packed-residual chunk of each CTA chunk in order
       PieceIter pi(tile_start, a.ntiles, g0, g1);
-      int t, cb, ce;
+      int t = 0, cb = 0, ce = 0, c = 0;
       bool sp;
-      int it = 0;
-      bool ok = true;
-      while (ok && pi.next(t, cb, ce, sp)) {
-        const int64_t gb = box_chunk0[tile_box[t]];
-        for (int c = cb; c < ce; ++c, ++it) {
-          const int s = it % QB;
-          if (it >= QB && !mbar_wait(bempty + s, uint32_t((it / QB - 1) & 1), a.wait_limit, abort)) {
-            fail();
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(bfull + s, SB);
-          bulk_load(ring_b + s * SB, a.bpack + (gb + c) * (2 * N * kInvKC), SB, bfull + s);
+      auto next_src = [&]() -> const float* {
+        if (c >= ce) {
+          pi.next(t, cb, ce, sp);
+          c = cb;
+        }
+        return a.bpack + (int64_t(box_chunk0[tile_box[t]]) + c++) * (2 * N * kInvKC);
+      };
+      const int npair = (nch + 1) / 2;
+      int u = 0;
+      for (; u < npair; ++u) {
+        const int s = u % QB;
+        if (u >= QB && !mbar_wait(bempty + s, uint32_t((u / QB - 1) & 1), a.wait_limit, abort)) {
+          fail();
+          break;
+        }
+        const float* p0 = next_src();
+        const float* p1 = 2 * u + 1 < nch ? next_src() : nullptr;
+        unsigned char* dst = ring_b + s * 2 * SB;
+        mbar_expect_tx(bfull + s, p1 ? 2 * SB : SB);
+        if (p1 == p0 + 2 * N * kInvKC) {
+          bulk_load(dst, p0, 2 * SB, bfull + s);
+        } else {
+          bulk_load(dst, p0, SB, bfull + s);
+          if (p1) bulk_load(dst + SB, p1, SB, bfull + s);
         }
       }
-      for (int s = 0; s < QB && s < it; ++s)
-        mbar_wait(bfull + s, uint32_t(((s + QB * ((it - 1 - s) / QB)) / QB) & 1), kInvDrain, nullptr);
+      for (int s = 0; s < QB && s < u; ++s)
+        mbar_wait(bfull + s, uint32_t(((s + QB * ((u - 1 - s) / QB)) / QB) & 1), kInvDrain, nullptr);
     }
   } else if (warp == 1 || warp == 10) {
     // ---- MMAs: issuer q, k-steps of chain q (all k-steps with one chain) ----
@@ -361,15 +381,15 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
         // go to separate columns
         const uint32_t d = tmem + uint32_t(a.acc_base + acc * a.kch * a.chain_cols);
         for (int c = cb; c < ce; ++c, ++it) {
-          const int sb = it % QB, sl = it % NS;
+          const int sb = (it / 2) % QB, sl = it % NS;
           if (!mbar_wait(split + sl, uint32_t((it / NS) & 1), a.wait_limit, abort) ||
-              !mbar_wait(bfull + sb, uint32_t((it / QB) & 1), a.wait_limit, abort)) {
+              !mbar_wait(bfull + sb, uint32_t((it / 2 / QB) & 1), a.wait_limit, abort)) {
             fail();
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const uint32_t bb = smem_addr(ring_b + sb * SB);
+          const uint32_t bb = smem_addr(ring_b + (sb * 2 + (it & 1)) * SB);
           const uint32_t ta = tmem + uint32_t(64 * sl);
           const uint32_t dc = d + uint32_t(q * a.chain_cols);
           for (int k8 = k0; k8 < k1; ++k8) {
@@ -397,8 +417,8 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     const int m = 32 * (warp & 3) + lane;
     const uint32_t trow = tmem + (uint32_t(32 * (warp & 3)) << 16);
     for (int it = 0; it < nch; ++it) {
-      const int sa = it % QA, sl = it % NS;
-      bool got = mbar_wait(afull + sa, uint32_t((it / QA) & 1), a.wait_limit, abort);
+      const int sa = (it / 2) % QA, sl = it % NS;
+      bool got = mbar_wait(afull + sa, uint32_t((it / 2 / QA) & 1), a.wait_limit, abort);
       // the slot of chunk it - aslots is free once its MMAs completed
       if (got && it >= NS) got = mbar_wait(tfree + sl, uint32_t((it / NS - 1) & 1), a.wait_limit, abort);
       // the warp converges before the aligned tensor-memory stores
@@ -407,11 +427,11 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const unsigned char* ar = ring_a + sa * SA;
+      const unsigned char* ar = ring_a + (sa * 2 + (it & 1)) * SA;
       float4 v[kInvKC / 4];
 #pragma unroll
       for (int q = 0; q < kInvKC / 4; ++q) v[q] = *reinterpret_cast<const float4*>(ar + q * 2048 + m * 16);
-      mbar_arrive(aempty + sa);  // the stage is read: the copy of chunk it + QA may start
+      mbar_arrive(aempty + sa);  // read: once both chunks are, the copy of pair it / 2 + QA may start
       float hi[kInvKC], lo[kInvKC];
 #pragma unroll
       for (int q = 0; q < kInvKC / 4; ++q) {
@@ -596,8 +616,8 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
   }
 }
 
-// ring depths for N padded modes: ring B of 4 (3) stages, ring A of the
-// rest of the shared memory (at most kInvMaxA)
+// ring depths (chunk pairs) for N padded modes: ring B of 2 pairs, ring A
+// of the rest of the shared memory (at most kInvMaxA pairs)
 struct InvRings {
   int qa, qb;
   size_t smem;
@@ -607,12 +627,11 @@ InvRings inv_rings(int P) {
   const size_t sa = size_t(kInvChunk) * 4, sb = 2 * size_t(N) * kInvKC * 4;
   const size_t fixed = size_t(N) * N * 4 + (2 * kInvMaxA + 2 * kInvMaxB + 2 * kInvMaxSlots + 6) * 8 + 16;
   InvRings r{0, 0, 0};
-  for (int qb = kInvMaxB; qb >= 2; --qb) {
-    if (fixed + qb * sb + 2 * sa > kSmemLimit) continue;
+  const int qb = 2;
+  if (fixed + qb * 2 * sb + 2 * 2 * sa <= kSmemLimit) {
     r.qb = qb;
-    r.qa = int(std::min<size_t>(kInvMaxA, (kSmemLimit - fixed - qb * sb) / sa));
-    r.smem = fixed + qb * sb + r.qa * sa;
-    break;
+    r.qa = int(std::min<size_t>(kInvMaxA, (kSmemLimit - fixed - qb * 2 * sb) / (2 * sa)));
+    r.smem = fixed + qb * 2 * sb + r.qa * 2 * sa;
   }
   return r;
 }
