@@ -43,7 +43,7 @@ namespace {
 constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
 constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
 constexpr int kInvMaxA = 8;                // inverse chunk pairs in flight (ring freed by the split)
-constexpr int kInvMaxB = 4;                // packed residual chunk pairs in flight (ring freed by the MMAs)
+constexpr int kInvMaxB = 6;                // packed residual chunk pairs in flight (ring freed by the MMAs)
 constexpr int kInvMaxSlots = 4;            // tensor-memory slots of split chunks
 constexpr int kInvThreads = 384;           // 2 copy warps, 2 MMA warps, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
@@ -616,8 +616,11 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
   }
 }
 
-// ring depths (chunk pairs) for N padded modes: ring B of 2 pairs, ring A
-// of the rest of the shared memory (at most kInvMaxA pairs)
+// ring depths (chunk pairs) for N padded modes.  A stage of ring A turns
+// over after the copy latency and the split, one of ring B only after the
+// MMAs of both its chunks as well (the residual pairs come from L2 but
+// wait for their MMAs): ring A of 3 pairs, ring B of the rest of the
+// shared memory (at most kInvMaxB pairs), each at least 2.
 struct InvRings {
   int qa, qb;
   size_t smem;
@@ -627,11 +630,12 @@ InvRings inv_rings(int P) {
   const size_t sa = size_t(kInvChunk) * 4, sb = 2 * size_t(N) * kInvKC * 4;
   const size_t fixed = size_t(N) * N * 4 + (2 * kInvMaxA + 2 * kInvMaxB + 2 * kInvMaxSlots + 6) * 8 + 16;
   InvRings r{0, 0, 0};
-  const int qb = 2;
-  if (fixed + qb * 2 * sb + 2 * 2 * sa <= kSmemLimit) {
-    r.qb = qb;
-    r.qa = int(std::min<size_t>(kInvMaxA, (kSmemLimit - fixed - qb * 2 * sb) / (2 * sa)));
-    r.smem = fixed + qb * 2 * sb + r.qa * 2 * sa;
+  for (int qa = 3; qa >= 2; --qa) {
+    if (fixed + qa * 2 * sa + 2 * 2 * sb > kSmemLimit) continue;
+    r.qa = qa;
+    r.qb = int(std::min<size_t>(kInvMaxB, (kSmemLimit - fixed - qa * 2 * sa) / (2 * sb)));
+    r.smem = fixed + qa * 2 * sa + r.qb * 2 * sb;
+    break;
   }
   return r;
 }
