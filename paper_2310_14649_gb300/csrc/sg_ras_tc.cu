@@ -42,10 +42,8 @@ namespace {
 
 constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
 constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
-constexpr int kInvMaxA = 8;                // inverse chunk pairs in flight (ring freed by the split)
-constexpr int kInvMaxB = 6;                // packed residual chunk pairs in flight (ring freed by the MMAs)
-constexpr int kInvMaxSlots = 4;            // tensor-memory slots of split chunks
-constexpr int kInvThreads = 384;           // 2 copy warps, 2 MMA warps, 4 split warps, 4 epilogue warps
+constexpr int kInvMaxStages = 6;           // chunks in flight
+constexpr int kInvThreads = 352;           // copy warp, 2 MMA warps, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -163,7 +161,7 @@ struct InvArgs {
   int64_t off[kMetaCount];
   const float* M;      // P x P Kronecker factor (row a: coefficients of output mode a)
   int transform;
-  int P, astages, bstages, ntiles, tcols;
+  int P, stages, ntiles, tcols;
   int aslots;    // tensor-memory slots of split inverse chunks (64 columns each, from column 0)
   int acc_base;  // first column of the accumulators
   int kch;       // independent accumulation chains per accumulator (k-steps alternate between them)
@@ -202,48 +200,34 @@ struct PieceIter {
 };
 
 // Persistent kernel, one CTA per SM, chunk range [blockIdx.x * chunks /
-// grid, ...): chunk `it` of the CTA is global chunk g0 + it, so its
-// inverse chunks are one contiguous range of memory.  The rings hold
-// chunk pairs: one bulk copy moves a pair (a copy's fixed cost is then
-// spread over 32 KB; single 16 KB copies left an SM's copy engine well
-// short of its share of the memory bandwidth).  Roles (lane 0 where one
-// thread acts):
-//  * warp 0 copies inverse chunk pairs into ring A (32 KB stages, freed as
-//    soon as the split threads have read both chunks);
-//  * warp 11 copies packed residual chunk pairs into ring B (2 x 2N x 32 x
-//    4 B stages, one copy when the pair is contiguous, freed when the MMAs
-//    reading both chunks completed);
-//  * warps 2-5 split an inverse chunk, one row per thread, into a
-//    tensor-memory slot (high part in columns 0-31, remainder in 32-63; the
-//    slot of chunk c is free once the MMAs of chunk c - aslots completed);
-//  * warps 1 and 10 issue the MMAs (with two chains each warp issues the
-//    k-steps of its chain, so the issue of these small MMAs runs on two
-//    threads) and commit them to the B stage's and the slot's barriers and,
-//    at the end of a tile piece, to the accumulator's "full" barrier;
-//  * warps 6-9 read the accumulator (alternating by piece when there are
-//    two), apply the Kronecker factor and store (atomically adding when the
-//    tile is shared with the neighbouring CTA, whose rows were zeroed by the
-//    pack kernel; two addends onto zero give the same sum in either order).
-// Separate rings keep the inverse stream deep: its stages turn over after
-// the copy latency and the split, not after the MMAs.  Shared memory: ring
-// A, ring B, the N x N factor, barriers.
+// grid, ...).  Roles: warp 0 lane 0 issues the bulk copies of a stage
+// (inverse chunk + packed residual chunk); warps 2-5 split the inverse
+// chunk, one row per thread, into a tensor-memory slot (high part in
+// columns 0-31, remainder in 32-63; the slot of chunk c is free once the
+// MMAs of chunk c - aslots completed); lane 0 of warp 1 (and of warp 10
+// when there are two chains: each warp issues the k-steps of its chain, so
+// the issue of small MMAs runs on two threads) issues the MMAs of a stage
+// and commits them to the stage's "empty" barrier and, at the end of a
+// tile piece, to the accumulator's "full" barrier; warps
+// 6-9 read the accumulator (two in tensor memory, alternating by piece),
+// apply the Kronecker factor and store (atomically adding when the tile is
+// shared with the neighbouring CTA, whose rows were zeroed by the pack
+// kernel; two addends onto zero give the same sum in either order).
+// Shared memory:
+// stages of {A (raw) 16 KB | packed residual 2N x 32 x 4 B}, the N x N
+// factor, barriers.
 template <int NB>
 __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   constexpr int N = 16 * NB;
-  constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4;
+  constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4, STAGE = SA + SB;
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int QA = a.astages, QB = a.bstages, NS = a.aslots;
-  unsigned char* ring_a = sm;                 // [QA][2][SA]
-  unsigned char* ring_b = sm + QA * 2 * SA;   // [QB][2][SB]
-  float* Ms = reinterpret_cast<float*>(ring_b + QB * 2 * SB);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(ring_b + QB * 2 * SB + N * N * 4);
-  uint64_t* afull = bars;                     // [QA] inverse chunk pair landed
-  uint64_t* aempty = afull + kInvMaxA;        // [QA] pair read (128 arrivals per chunk)
-  uint64_t* bfull = aempty + kInvMaxA;        // [QB] residual chunk pair landed
-  uint64_t* bempty = bfull + kInvMaxB;        // [QB] its MMAs done (kch commits per chunk)
-  uint64_t* split = bempty + kInvMaxB;        // [NS] slot written (128 arrivals)
-  uint64_t* tfree = split + kInvMaxSlots;     // [NS] slot's MMAs done (kch commits)
-  uint64_t* accf = tfree + kInvMaxSlots;      // [2] accumulator complete (kch commits)
+  const int S = a.stages;
+  float* Ms = reinterpret_cast<float*>(sm + S * STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S * STAGE + N * N * 4);
+  uint64_t* full = bars;                      // [S] copies landed
+  uint64_t* split = bars + kInvMaxStages;     // [S] split done (128 arrivals)
+  uint64_t* empty = bars + 2 * kInvMaxStages; // [S] MMAs of the stage done
+  uint64_t* accf = bars + 3 * kInvMaxStages;  // [2] accumulator complete
   uint64_t* acce = accf + 2;                  // [2] accumulator read (128 arrivals)
   uint64_t* fin = acce + 2;                   // [2] last MMA of each issuer done
   uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 2);
@@ -253,7 +237,6 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   const int* tile_start = meta + a.off[kTileStart];
   const int64_t g0 = int64_t(blockIdx.x) * a.chunks / gridDim.x;
   const int64_t g1 = int64_t(blockIdx.x + 1) * a.chunks / gridDim.x;
-  const int nch = int(g1 - g0);
 
   if (a.transform)
     for (int e = tid; e < N * N; e += kInvThreads) {
@@ -267,23 +250,17 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < kInvMaxA; ++s) {
-      mbar_init(afull + s, 1);
-      mbar_init(aempty + s, 256);
-    }
-    for (int s = 0; s < kInvMaxB; ++s) {
-      mbar_init(bfull + s, 1);
-      mbar_init(bempty + s, 2 * a.kch);
-    }
-    for (int s = 0; s < kInvMaxSlots; ++s) {
+    for (int s = 0; s < kInvMaxStages; ++s) {
+      mbar_init(full + s, 1);
       mbar_init(split + s, 128);
-      mbar_init(tfree + s, a.kch);
+      mbar_init(empty + s, a.kch);
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(accf + k, a.kch);
       mbar_init(acce + k, 128);
-      mbar_init(fin + k, 1);
     }
+    mbar_init(fin, 1);
+    mbar_init(fin + 1, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -297,65 +274,38 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
   };
 
   if (warp == 0) {
-    // ---- inverse chunks into ring A ----
+    // ---- copies ----
     if (lane == 0) {
       uint64_t pol;
       asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
-      // pair u holds chunks 2u and 2u + 1 (the last pair of an odd range
-      // one chunk: its stage is never waited for again)
-      const int npair = (nch + 1) / 2;
-      int u = 0;
-      for (; u < npair; ++u) {
-        const int s = u % QA;
-        if (u >= QA && !mbar_wait(aempty + s, uint32_t((u / QA - 1) & 1), a.wait_limit, abort)) {
-          fail();
-          break;
-        }
-        const uint32_t bytes = SA * uint32_t(min(2, nch - 2 * u));
-        mbar_expect_tx(afull + s, bytes);
-        bulk_load_stream(ring_a + s * 2 * SA, a.ainv + (g0 + 2 * u) * kInvChunk, bytes, afull + s, pol);
-      }
-      // every copy lands before the CTA's shared memory is released
-      for (int s = 0; s < QA && s < u; ++s)
-        mbar_wait(afull + s, uint32_t(((s + QA * ((u - 1 - s) / QA)) / QA) & 1), kInvDrain, nullptr);
-    }
-  } else if (warp == 11) {
-    // ---- packed residual chunks into ring B ----
-    if (lane == 0) {
       const int* tile_box = meta + a.off[kTileBox];
       const int* box_chunk0 = meta + a.off[kBoxChunk0];
-      // the packed-residual chunk of each CTA chunk in order
       PieceIter pi(tile_start, a.ntiles, g0, g1);
-      int t = 0, cb = 0, ce = 0, c = 0;
+      int t, cb, ce;
       bool sp;
-      auto next_src = [&]() -> const float* {
-        if (c >= ce) {
-          pi.next(t, cb, ce, sp);
-          c = cb;
-        }
-        return a.bpack + (int64_t(box_chunk0[tile_box[t]]) + c++) * (2 * N * kInvKC);
-      };
-      const int npair = (nch + 1) / 2;
-      int u = 0;
-      for (; u < npair; ++u) {
-        const int s = u % QB;
-        if (u >= QB && !mbar_wait(bempty + s, uint32_t((u / QB - 1) & 1), a.wait_limit, abort)) {
-          fail();
-          break;
-        }
-        const float* p0 = next_src();
-        const float* p1 = 2 * u + 1 < nch ? next_src() : nullptr;
-        unsigned char* dst = ring_b + s * 2 * SB;
-        mbar_expect_tx(bfull + s, p1 ? 2 * SB : SB);
-        if (p1 == p0 + 2 * N * kInvKC) {
-          bulk_load(dst, p0, 2 * SB, bfull + s);
-        } else {
-          bulk_load(dst, p0, SB, bfull + s);
-          if (p1) bulk_load(dst + SB, p1, SB, bfull + s);
+      int it = 0;
+      bool ok = true;
+      while (ok && pi.next(t, cb, ce, sp)) {
+        const int64_t gt = tile_start[t];
+        const int64_t gb = box_chunk0[tile_box[t]];
+        for (int c = cb; c < ce; ++c, ++it) {
+          const int s = it % S;
+          if (it >= S && !mbar_wait(empty + s, uint32_t((it / S - 1) & 1), a.wait_limit, abort)) {
+            fail();
+            ok = false;
+            break;
+          }
+          unsigned char* st = sm + s * STAGE;
+          mbar_expect_tx(full + s, SA + SB);
+          bulk_load_stream(st, a.ainv + (gt + c) * kInvChunk, SA, full + s, pol);
+          bulk_load(st + SA, a.bpack + (gb + c) * (2 * N * kInvKC), SB, full + s);
         }
       }
-      for (int s = 0; s < QB && s < u; ++s)
-        mbar_wait(bfull + s, uint32_t(((s + QB * ((u - 1 - s) / QB)) / QB) & 1), kInvDrain, nullptr);
+      // every copy lands before the CTA's shared memory is released
+      for (int s = 0; s < S && s < it; ++s) {
+        const int u = s + S * ((it - 1 - s) / S);  // last use of stage s
+        mbar_wait(full + s, uint32_t((u / S) & 1), kInvDrain, nullptr);
+      }
     }
   } else if (warp == 1 || warp == 10) {
     // ---- MMAs: issuer q, k-steps of chain q (all k-steps with one chain) ----
@@ -377,20 +327,19 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         // back-to-back MMAs into one accumulator wait for each other: the
-        // high and remainder products, and the k-steps of the two chains,
+        // high and remainder products, and the k-steps of alternate chains,
         // go to separate columns
         const uint32_t d = tmem + uint32_t(a.acc_base + acc * a.kch * a.chain_cols);
         for (int c = cb; c < ce; ++c, ++it) {
-          const int sb = (it / 2) % QB, sl = it % NS;
-          if (!mbar_wait(split + sl, uint32_t((it / NS) & 1), a.wait_limit, abort) ||
-              !mbar_wait(bfull + sb, uint32_t((it / 2 / QB) & 1), a.wait_limit, abort)) {
+          const int s = it % S;
+          if (!mbar_wait(split + s, uint32_t((it / S) & 1), a.wait_limit, abort)) {
             fail();
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const uint32_t bb = smem_addr(ring_b + (sb * 2 + (it & 1)) * SB);
-          const uint32_t ta = tmem + uint32_t(64 * sl);
+          const uint32_t bb = smem_addr(sm + s * STAGE) + SA;
+          const uint32_t ta = tmem + uint32_t(64 * (it % a.aslots));
           const uint32_t dc = d + uint32_t(q * a.chain_cols);
           for (int k8 = k0; k8 < k1; ++k8) {
             const uint64_t db = smem_desc(bb + 2 * k8 * PLB, PLB, 128);
@@ -399,8 +348,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
             tc_mma_ta(dc + 2 * N, ta + 32 + 8 * k8, db, id1, first);
           }
           any = true;
-          tc_commit(bempty + sb);
-          tc_commit(tfree + sl);
+          tc_commit(empty + s);
         }
         if (!ok) break;
         tc_commit(accf + acc);
@@ -416,40 +364,48 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     // ---- split of the inverse chunk: row m of the chunk into lane m ----
     const int m = 32 * (warp & 3) + lane;
     const uint32_t trow = tmem + (uint32_t(32 * (warp & 3)) << 16);
-    for (int it = 0; it < nch; ++it) {
-      const int sa = (it / 2) % QA, sl = it % NS;
-      bool got = mbar_wait(afull + sa, uint32_t((it / 2 / QA) & 1), a.wait_limit, abort);
-      // the slot of chunk it - aslots is free once its MMAs completed
-      if (got && it >= NS) got = mbar_wait(tfree + sl, uint32_t((it / NS - 1) & 1), a.wait_limit, abort);
-      // the warp converges before the aligned tensor-memory stores
-      if (!__all_sync(0xffffffffu, got)) {
-        fail();
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const unsigned char* ar = ring_a + (sa * 2 + (it & 1)) * SA;
-      float4 v[kInvKC / 4];
+    PieceIter pi(tile_start, a.ntiles, g0, g1);
+    int t, cb, ce;
+    bool sp;
+    int it = 0;
+    bool ok = true;
+    while (ok && pi.next(t, cb, ce, sp)) {
+      for (int c = cb; c < ce; ++c, ++it) {
+        const int s = it % S;
+        bool got = mbar_wait(full + s, uint32_t((it / S) & 1), a.wait_limit, abort);
+        // the slot of chunk it - aslots is free once its MMAs completed
+        if (got && it >= a.aslots) {
+          const int u = it - a.aslots;
+          got = mbar_wait(empty + u % S, uint32_t((u / S) & 1), a.wait_limit, abort);
+        }
+        // the warp converges before the aligned tensor-memory stores
+        if (!__all_sync(0xffffffffu, got)) {
+          fail();
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const unsigned char* ar = sm + s * STAGE;
+        float hi[kInvKC], lo[kInvKC];
 #pragma unroll
-      for (int q = 0; q < kInvKC / 4; ++q) v[q] = *reinterpret_cast<const float4*>(ar + q * 2048 + m * 16);
-      mbar_arrive(aempty + sa);  // read: once both chunks are, the copy of pair it / 2 + QA may start
-      float hi[kInvKC], lo[kInvKC];
-#pragma unroll
-      for (int q = 0; q < kInvKC / 4; ++q) {
-        hi[4 * q] = tf32_hi(v[q].x);
-        hi[4 * q + 1] = tf32_hi(v[q].y);
-        hi[4 * q + 2] = tf32_hi(v[q].z);
-        hi[4 * q + 3] = tf32_hi(v[q].w);
-        lo[4 * q] = v[q].x - hi[4 * q];
-        lo[4 * q + 1] = v[q].y - hi[4 * q + 1];
-        lo[4 * q + 2] = v[q].z - hi[4 * q + 2];
-        lo[4 * q + 3] = v[q].w - hi[4 * q + 3];
+        for (int q = 0; q < kInvKC / 4; ++q) {
+          const float4 v = *reinterpret_cast<const float4*>(ar + q * 2048 + m * 16);
+          hi[4 * q] = tf32_hi(v.x);
+          hi[4 * q + 1] = tf32_hi(v.y);
+          hi[4 * q + 2] = tf32_hi(v.z);
+          hi[4 * q + 3] = tf32_hi(v.w);
+          lo[4 * q] = v.x - hi[4 * q];
+          lo[4 * q + 1] = v.y - hi[4 * q + 1];
+          lo[4 * q + 2] = v.z - hi[4 * q + 2];
+          lo[4 * q + 3] = v.w - hi[4 * q + 3];
+        }
+        const uint32_t ta = trow + uint32_t(64 * (it % a.aslots));
+        tc_st32(ta, hi);
+        tc_st32(ta + 32, lo);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        mbar_arrive(split + s);
       }
-      const uint32_t ta = trow + uint32_t(64 * sl);
-      tc_st32(ta, hi);
-      tc_st32(ta + 32, lo);
-      asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      mbar_arrive(split + sl);
     }
   } else {
     // ---- epilogue: rows 32 (warp % 4) + lane of the accumulator ----
@@ -616,28 +572,13 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
   }
 }
 
-// ring depths (chunk pairs) for N padded modes.  A stage of ring A turns
-// over after the copy latency and the split, one of ring B only after the
-// MMAs of both its chunks as well (the residual pairs come from L2 but
-// wait for their MMAs): ring A of 3 pairs, ring B of the rest of the
-// shared memory (at most kInvMaxB pairs), each at least 2.
-struct InvRings {
-  int qa, qb;
-  size_t smem;
-};
-InvRings inv_rings(int P) {
+size_t inv_stage_bytes(int N) { return size_t(kInvChunk) * 4 + 2 * size_t(N) * kInvKC * 4; }
+size_t inv_fixed_bytes(int N) { return size_t(N) * N * 4 + (3 * kInvMaxStages + 6) * 8 + 16; }
+
+int inv_stages(int P) {
   const int N = (P + 15) / 16 * 16;
-  const size_t sa = size_t(kInvChunk) * 4, sb = 2 * size_t(N) * kInvKC * 4;
-  const size_t fixed = size_t(N) * N * 4 + (2 * kInvMaxA + 2 * kInvMaxB + 2 * kInvMaxSlots + 6) * 8 + 16;
-  InvRings r{0, 0, 0};
-  for (int qa = 3; qa >= 2; --qa) {
-    if (fixed + qa * 2 * sa + 2 * 2 * sb > kSmemLimit) continue;
-    r.qa = qa;
-    r.qb = int(std::min<size_t>(kInvMaxB, (kSmemLimit - fixed - qa * 2 * sa) / (2 * sb)));
-    r.smem = fixed + qa * 2 * sa + r.qb * 2 * sb;
-    break;
-  }
-  return r;
+  const size_t room = kSmemLimit - inv_fixed_bytes(N);
+  return int(std::min<size_t>(kInvMaxStages, room / inv_stage_bytes(N)));
 }
 
 template <int NB>
@@ -647,7 +588,7 @@ sg_status inv_launch(const InvArgs& args, int grid, cudaStream_t st) {
     SG_CUDA(cudaFuncSetAttribute(k_ras_inv_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemLimit)));
     attr = true;
   }
-  const size_t smem = inv_rings(args.P).smem;
+  const size_t smem = args.stages * inv_stage_bytes(16 * NB) + inv_fixed_bytes(16 * NB);
   k_ras_inv_tc<NB><<<unsigned(grid), kInvThreads, smem, st>>>(args);
   note_launch();
   SG_CUDA(cudaGetLastError());
@@ -665,7 +606,7 @@ InvArgs inv_args(const RasData& D) {
 
 // the index list of the widest supported box: 48 x 48 overlapped nodes
 constexpr int kInvMaxKp = 48 * 48;
-bool ras_inverse_supported(int P) { return P >= 1 && P <= 96 && inv_rings(P).qa >= 2; }
+bool ras_inverse_supported(int P) { return P >= 1 && P <= 96 && inv_stages(P) >= 2; }
 
 sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   RasData& D = pc.ras;
@@ -794,6 +735,7 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   D.inv_ntiles = ntiles;
   D.inv_grid = grid;
   D.inv_nsplit = int(split_tile.size());
+  D.inv_stages = inv_stages(P);
   D.inv_chunks = chunks;
   D.inv_bchunks = bchunks;
   D.d_inv = std::move(dainv);
@@ -829,8 +771,7 @@ sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld
   a.M = M;
   a.transform = transform ? 1 : 0;
   a.P = P;
-  a.astages = inv_rings(P).qa;
-  a.bstages = inv_rings(P).qb;
+  a.stages = D.inv_stages;
   a.ntiles = D.inv_ntiles;
   // tensor memory (512 columns): the split inverse chunks in slots of 64
   // columns from column 0, then the accumulators, each of kch chains of
