@@ -80,6 +80,26 @@ def measured_traffic(shape):
     return None
 
 
+def ras_inv_traffic():
+    """DRAM bytes per launch of k_ras_inv_tc from the committed ncu summary
+    (profiles/k_ras_inv_tc_poisson256_L4_p3.md), if that summary was taken on
+    the current kernel source (its sha1 recorded there); otherwise None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2310_14649_gb300", "csrc", "sg_ras_tc.cu")
+    prof = os.path.join(ROOT, "profiles", "k_ras_inv_tc_poisson256_L4_p3.md")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        vals = {}
+        for line in open(prof).read().splitlines():
+            if line.startswith("traffic-key:"):
+                for kv in line.split(":", 1)[1].split():
+                    k, v = kv.split("=")
+                    vals[k] = v
+        return int(vals["bytes"]) if vals.get("source-sha1") == sha else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -795,13 +815,14 @@ def main():
                      "peak_source": peak_kind, "bytes_per_launch": bytes_f32, "avg_launch_ms": avg_ms,
                      "launches": cnt,
                      "traffic": measured_traffic(dict(sg.sg_apply_info(prob), flux=flux_on))},
-        "roofline_top_kernel": ({"kernel": "k_ras_inv_tc FP32 (RAS by explicit local inverses on tcgen05, %d boxes, "
-                                           "Kronecker factor fused)" % ras_boxes,
+        "roofline_top_kernel": ({"kernel": "k_ras_inv_pack + k_ras_inv_tc FP32 (RAS by explicit local inverses on "
+                                           "tcgen05, %d boxes, Kronecker factor fused; the timed span holds both "
+                                           "launches)" % ras_boxes,
                                  "bound": "hbm", "achieved": round(inv_bytes / (ras_avg * 1e-3) / 1e9, 1) if rcnt else None,
                                  "peak": peak, "unit": "GB/s",
                                  "frac": round(inv_bytes / (ras_avg * 1e-3) / 1e9 / peak, 4) if rcnt else None,
                                  "peak_source": peak_kind, "bytes_per_launch": inv_bytes, "avg_launch_ms": ras_avg,
-                                 "launches": rcnt}
+                                 "launches": rcnt, "traffic": ras_inv_traffic()}
                                 if ras_kernel == 2 else
                                 {"kernel": "k_ras_local FP32 (RAS line solves, %d boxes, line width %d)"
                                            % (ras_boxes, ras_w),
