@@ -54,7 +54,7 @@ enum InvMeta {
   kTileOwned,   // [ntiles][128]: global node of each tile row, -1 for padding
   kBoxChunk0,   // [nbox]: first chunk of the box in the packed residual
   kBoxTile0,    // [nbox]: first tile of the box
-  kChunkBox,    // [bchunks]: box of each packed residual chunk
+  kChunkIdx,    // [bchunks][32]: global nodes of each packed residual chunk, -1 for padding
   kSplitTile,   // [nsplit]: tiles two CTAs accumulate into
   kIdx,         // [nbox][Kp]: overlapped global nodes
   kNov,         // [nbox]: overlapped node counts
@@ -485,32 +485,33 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
 // (box b, c) holds, for the overlapped nodes j = 32 c .. 32 c + 31, the
 // rows n < N (high parts of r[n][idx_b[j]]) and N + n (remainders), planes
 // of 4 nodes (16 bytes per row).  One block per chunk: the gather reads
-// runs of consecutive nodes of a mode row into shared memory, the writes
-// are whole 16-byte rows of a plane.  The remaining blocks' threads zero
-// the output rows of the tiles that two CTAs accumulate into.
+// runs of consecutive nodes of a mode row into shared memory (one index
+// load, then independent loads of the rows), the writes are whole 16-byte
+// rows of a plane.  The threads also zero the output rows of the tiles that
+// two CTAs accumulate into.
 constexpr int kPackThreads = 256;
 __global__ void __launch_bounds__(kPackThreads) k_ras_inv_pack(const float* __restrict__ R, int64_t ld, int P, int N,
                                                                int64_t bchunks, InvArgs a, float* __restrict__ bpack,
-                                                               int nsplit, int Kp) {
+                                                               int nsplit) {
   __shared__ float tile[96][kInvKC + 1];
   const int* meta = a.meta;
-  const int* chunk_box = meta + a.off[kChunkBox];
-  const int* box_chunk0 = meta + a.off[kBoxChunk0];
-  const int* idx = meta + a.off[kIdx];
-  const int* nov = meta + a.off[kNov];
+  const int* chunk_idx = meta + a.off[kChunkIdx];
   const int tid = threadIdx.x;
   for (int64_t gc = blockIdx.x; gc < bchunks; gc += gridDim.x) {
-    const int b = chunk_box[gc];
-    const int j0 = int(gc - box_chunk0[b]) * kInvKC;
-    const int nb = nov[b];
-    // thread (k, n0): node j0 + k of every eighth mode row from n0, the
-    // node index loaded once and the rows' loads independent
+    // thread (k, n0): node k of the chunk in every eighth mode row from n0
     const int k = tid % kInvKC, n0 = tid / kInvKC;
-    const int j = j0 + k;
-    const int gi = j < nb ? idx[int64_t(b) * Kp + j] : -1;
-#pragma unroll 4
-    for (int n = n0; n < N; n += kPackThreads / kInvKC)
-      tile[n][k] = (n < P && gi >= 0) ? R[int64_t(n) * ld + gi] : 0.f;
+    const int gi = chunk_idx[gc * kInvKC + k];
+    float v[96 / (kPackThreads / kInvKC)];
+#pragma unroll
+    for (int i = 0; i < 96 / (kPackThreads / kInvKC); ++i) {
+      const int n = n0 + i * (kPackThreads / kInvKC);
+      v[i] = (n < P && gi >= 0) ? R[int64_t(n) * ld + gi] : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 96 / (kPackThreads / kInvKC); ++i) {
+      const int n = n0 + i * (kPackThreads / kInvKC);
+      if (n < N) tile[n][k] = v[i];
+    }
     __syncthreads();
     float4* out = reinterpret_cast<float4*>(bpack + gc * (2 * N * kInvKC));
     for (int e = tid; e < (kInvKC / 4) * N; e += kPackThreads) {
@@ -643,7 +644,7 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   const int Mpad = (omax + 127) / 128 * 128;
   const int P = pr->P, N = (P + 15) / 16 * 16;
   // tiles (128 owned rows of a box) and chunks (32 overlapped nodes)
-  std::vector<int> tile_start{0}, tile_box, tile_owned, box_chunk0(nbox), box_tile0(nbox + 1), chunk_box, hidx(
+  std::vector<int> tile_start{0}, tile_box, tile_owned, box_chunk0(nbox), box_tile0(nbox + 1), chunk_idx, hidx(
       size_t(nbox) * Kp, 0);
   int64_t bchunks = 0;
   int maxlen = 1;
@@ -651,7 +652,7 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
     const int nch = (nov[b] + kInvKC - 1) / kInvKC;
     maxlen = std::max(maxlen, nch);
     box_chunk0[b] = int(bchunks);
-    for (int c = 0; c < nch; ++c) chunk_box.push_back(b);
+    for (int j = 0; j < nch * kInvKC; ++j) chunk_idx.push_back(j < nov[b] ? D.idx[b][j] : -1);
     bchunks += nch;
     box_tile0[b] = int(tile_box.size());
     std::vector<int> own;
@@ -694,7 +695,7 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   // the index tables in one buffer
   std::vector<int> meta;
   const std::vector<int>* parts[kMetaCount] = {&tile_start, &tile_box, &tile_owned, &box_chunk0, &box_tile0,
-                                               &chunk_box,  &split_tile, &hidx, &nov};
+                                               &chunk_idx,  &split_tile, &hidx, &nov};
   for (int k = 0; k < kMetaCount; ++k) {
     D.inv_off[k] = int64_t(meta.size());
     meta.insert(meta.end(), parts[k]->begin(), parts[k]->end());
@@ -797,10 +798,10 @@ sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld
   a.chunks = D.inv_chunks;
   a.err = dp<int>(D.d_inv_err);
   a.wait_limit = wait_limit;
-  const int pgrid = int(std::min<int64_t>(D.inv_bchunks, 8 * 152));
-  k_ras_inv_pack<<<unsigned(std::max(pgrid, 1)), kPackThreads, 0, st>>>(R, ld, P, N, D.inv_bchunks, a,
-                                                                       dp<float>(D.d_inv_bpack), D.inv_nsplit,
-                                                                       D.inv_kp);
+  // one block per packed chunk (every chunk's loads in flight at once)
+  const int pgrid = int(std::max<int64_t>(1, std::min<int64_t>(D.inv_bchunks, 1 << 30)));
+  k_ras_inv_pack<<<unsigned(pgrid), kPackThreads, 0, st>>>(R, ld, P, N, D.inv_bchunks, a, dp<float>(D.d_inv_bpack),
+                                                           D.inv_nsplit);
   note_launch();
   SG_CUDA(cudaGetLastError());
   switch (N / 16) {
