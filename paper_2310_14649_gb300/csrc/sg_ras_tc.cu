@@ -43,7 +43,7 @@ namespace {
 constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
 constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
 constexpr int kInvMaxStages = 6;           // chunks in flight
-constexpr int kInvThreads = 352;           // copy warp, 2 MMA warps, 4 split warps, 4 epilogue warps
+constexpr int kInvThreads = 384;           // 2 copy warps, 2 MMA warps, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -273,8 +273,11 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     atomicExch(a.err, 1);
   };
 
-  if (warp == 0) {
-    // ---- copies ----
+  if (warp == 0 || warp == 11) {
+    // ---- copies: warp 0 the even chunks, warp 11 the odd ones (a thread
+    // has about one bulk copy in issue at a time, so two threads double the
+    // copy rate; the stage count is even, so a stage keeps its parity) ----
+    const int p = warp == 0 ? 0 : 1;
     if (lane == 0) {
       uint64_t pol;
       asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
@@ -289,6 +292,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
         const int64_t gt = tile_start[t];
         const int64_t gb = box_chunk0[tile_box[t]];
         for (int c = cb; c < ce; ++c, ++it) {
+          if ((it & 1) != p) continue;
           const int s = it % S;
           if (it >= S && !mbar_wait(empty + s, uint32_t((it / S - 1) & 1), a.wait_limit, abort)) {
             fail();
@@ -301,8 +305,9 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
           bulk_load(st + SA, a.bpack + (gb + c) * (2 * N * kInvKC), SB, full + s);
         }
       }
-      // every copy lands before the CTA's shared memory is released
-      for (int s = 0; s < S && s < it; ++s) {
+      // every copy lands before the CTA's shared memory is released (it
+      // counts the chunks up to the last one issued, of either parity)
+      for (int s = p; s < S && s < it; s += 2) {
         const int u = s + S * ((it - 1 - s) / S);  // last use of stage s
         mbar_wait(full + s, uint32_t((u / S) & 1), kInvDrain, nullptr);
       }
@@ -579,7 +584,7 @@ size_t inv_fixed_bytes(int N) { return size_t(N) * N * 4 + (3 * kInvMaxStages + 
 int inv_stages(int P) {
   const int N = (P + 15) / 16 * 16;
   const size_t room = kSmemLimit - inv_fixed_bytes(N);
-  return int(std::min<size_t>(kInvMaxStages, room / inv_stage_bytes(N)));
+  return int(std::min<size_t>(kInvMaxStages, room / inv_stage_bytes(N))) & ~1;  // even: two copy warps
 }
 
 template <int NB>
