@@ -6,28 +6,24 @@
 // product of an (owned x overlapped) matrix with the (overlapped x P)
 // restricted residual.
 //
-// Shape.  One tcgen05.mma costs an SM about the same time for any N up to
-// 256 (about 140 cycles for M = 128, K = 8 TF32), so the long dimension
-// goes into N: the owned rows of a box are cut into tiles of 256 rows (the
-// MMA's N, operand B: the inverse), the residual's modes are the MMA's M
-// (operand A, 128 rows), the overlapped nodes are K, in chunks of 16.  The
-// inverse is stored chunk by chunk in the operand layout, so one bulk copy
-// moves a 16 KB chunk from HBM to shared memory; the sequence of all
-// (tile, chunk) pairs is cut into one contiguous range per SM (a persistent
-// grid), so every SM streams the same number of bytes and a tile is shared
-// by at most two CTAs.
+// Work: the owned rows of every box are cut into tiles of 128 rows (the
+// MMA's M), the overlapped nodes into chunks of 32 (K), the P modes padded
+// to N (a multiple of 16).  The inverse is stored chunk by chunk in the
+// operand layout of the tensor cores, so one bulk copy moves a 16 KB chunk
+// from HBM to shared memory; the sequence of all (tile, chunk) pairs is cut
+// into one contiguous range per SM (a persistent grid), so every SM streams
+// the same number of bytes and a tile is shared by at most two CTAs.
 //
 // Precision: FP32 operands split into a TF32 high part and the remainder,
-// x = xh + xl.  The residual is split once per apply: with 2N <= 128 padded
-// modes one operand [rh; rl] (rows a and N + a), else two operands rh, rl.
-// The inverse chunk is split in shared memory after its arrival (high part
-// in place, remainder in a ring beside it).  Per k-step
-//     D += [rh; rl] Ah^T + [rh; rl] Al^T          (2N <= 128)
-//     D1 += rh Ah^T + rh Al^T,  D2 += rl Ah^T      (otherwise)
-// (kind::tf32, FP32 accumulation in tensor memory, lanes = modes, columns
-// = rows of the inverse); the epilogue adds the two halves (rh A + rl A,
-// the product to FP32 accuracy), applies the smoother's Kronecker factor
-// (omega G~^{-1} across the modes of a node) and stores.
+// x = xh + xl.  The residual is split once per apply into the stacked
+// operand [rh; rl] (2N rows, shared memory), the inverse chunk after its
+// arrival, row by row, into tensor memory (the MMA's A operand there, so
+// the tensor cores read only the residual from shared memory); per k-step
+//     D[:, 0:2N] += Ah [rh; rl]^T,   D[:, 0:N] += Al rh^T
+// (kind::tf32, FP32 accumulation in tensor memory) and the epilogue sums
+// the two column halves: Ah rh + Ah rl + Al rh, the product to FP32
+// accuracy.  The epilogue applies the smoother's Kronecker factor (omega
+// G~^{-1} across the modes of a node) before the store.
 //
 // The inverses are formed once at setup in FP64 from the line-block
 // Cholesky factors: the local solve applied to unit right-hand sides, four
@@ -44,13 +40,10 @@ namespace sg {
 
 namespace {
 
-constexpr int kInvRows = 256;              // owned rows per tile: the MMA's N
-constexpr int kInvKC = 16;                 // overlapped nodes per chunk (K)
-constexpr int kInvChunk = kInvRows * kInvKC;  // floats of one inverse chunk (16 KB)
-constexpr int kInvAop = 128 * kInvKC;      // floats of one residual operand tile (8 KB)
+constexpr int kInvKC = 32;                 // overlapped nodes per chunk (K)
+constexpr int kInvChunk = 128 * kInvKC;    // floats of one inverse chunk (16 KB)
 constexpr int kInvMaxStages = 6;           // chunks in flight
-constexpr int kInvMaxLo = 3;               // ring of inverse remainders
-constexpr int kInvThreads = 352;           // 2 copy warps, MMA warp, 4 split warps, 4 epilogue warps
+constexpr int kInvThreads = 384;           // 2 copy warps, 2 MMA warps, 4 split warps, 4 epilogue warps
 constexpr int kInvDrain = 1 << 24;         // polls of a wait that follows a timed-out one
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -58,10 +51,10 @@ constexpr size_t kSmemLimit = 227 * 1024;
 enum InvMeta {
   kTileStart,   // [ntiles + 1]: first chunk of each tile in the global sequence
   kTileBox,     // [ntiles]
-  kTileOwned,   // [ntiles][256]: global node of each tile row, -1 for padding
+  kTileOwned,   // [ntiles][128]: global node of each tile row, -1 for padding
   kBoxChunk0,   // [nbox]: first chunk of the box in the packed residual
   kBoxTile0,    // [nbox]: first tile of the box
-  kChunkIdx,    // [bchunks][16]: global nodes of each packed residual chunk, -1 for padding
+  kChunkIdx,    // [bchunks][32]: global nodes of each packed residual chunk, -1 for padding
   kSplitTile,   // [nsplit]: tiles two CTAs accumulate into
   kIdx,         // [nbox][Kp]: overlapped global nodes
   kNov,         // [nbox]: overlapped node counts
@@ -94,11 +87,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
 }
 // polls the phase of parity `parity`; gives up after `limit` polls or when
-// another role of the CTA has given up.  sleep_ns > 0 backs off between
-// polls: for long waits off the critical path, whose polling would take
-// issue slots from the warps that share the scheduler.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int limit, volatile int* abort,
-                                          unsigned sleep_ns = 0) {
+// another role of the CTA has given up
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int limit, volatile int* abort) {
   for (int i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
@@ -108,7 +98,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int limi
         : "memory");
     if (done) return true;
     if (abort && *abort) return false;
-    if (sleep_ns) __nanosleep(sleep_ns);
   }
   return false;
 }
@@ -131,11 +120,23 @@ __device__ __forceinline__ void tc_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_addr(b))
                : "memory");
 }
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// A operand in tensor memory (row m in lane m, k along the columns)
+__device__ __forceinline__ void tc_mma_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// 32 consecutive columns of this thread's lane
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]),
+      "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]),
+      "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
       : "memory");
 }
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
@@ -155,12 +156,17 @@ struct InvArgs {
   float* Z;
   int64_t ld;
   const float* ainv;   // [chunks][kInvChunk]
-  const float* apack;  // [bchunks][nop][kInvAop]: the residual operand tiles
+  const float* bpack;  // [bchunks][2N x kInvKC]
   const int* meta;
   int64_t off[kMetaCount];
   const float* M;      // P x P Kronecker factor (row a: coefficients of output mode a)
   int transform;
-  int P, stages, nlo, ntiles;
+  int P, stages, ntiles, tcols;
+  int aslots;    // tensor-memory slots of split inverse chunks (64 columns each, from column 0)
+  int acc_base;  // first column of the accumulators
+  int kch;       // independent accumulation chains per accumulator (k-steps alternate between them)
+  int nbuf;      // accumulators (alternating by tile piece)
+  int chain_cols;  // columns of one chain: [Ah rh | Ah rl | Al rh], 3N rounded up to 32
   int64_t chunks;
   int* err;
   int wait_limit;
@@ -194,56 +200,43 @@ struct PieceIter {
 };
 
 // Persistent kernel, one CTA per SM, chunk range [blockIdx.x * chunks /
-// grid, ...): chunk `it` of the CTA is global chunk g0 + it.  Roles (lane 0
-// where one thread acts):
-//  * warps 0 and 10 copy the even and the odd chunks (a thread keeps about
-//    one bulk copy in issue at a time): the inverse chunk and the residual
-//    operand tile(s) of its box chunk into a stage;
-//  * warps 2-5 split the inverse chunk, high part in place, remainder into
-//    the ring slot of the chunk (free once the MMAs of chunk it - nlo
-//    completed);
-//  * warp 1 issues the MMAs of a chunk and commits them to the stage's and
-//    the slot's barriers and, at the end of a tile piece, to the
-//    accumulator's "full" barrier;
-//  * warps 6-9 read the accumulator 32 rows at a time (lane = mode, column
-//    = row), pass it through shared memory so that a thread holds a row's
-//    modes, apply the Kronecker factor and store (atomically adding when
-//    the tile is shared with the neighbouring CTA, whose rows were zeroed
-//    by the pack kernel; two addends onto zero give the same sum in either
-//    order).
-// Shared memory: stages of {inverse chunk (raw, then high part) 16 KB |
-// residual operand(s) 8 or 16 KB}, the remainder ring, the N x N factor,
-// the 2 x 32 x (N + 1) epilogue staging, barriers.
+// grid, ...).  Roles: warp 0 lane 0 issues the bulk copies of a stage
+// (inverse chunk + packed residual chunk); warps 2-5 split the inverse
+// chunk, one row per thread, into a tensor-memory slot (high part in
+// columns 0-31, remainder in 32-63; the slot of chunk c is free once the
+// MMAs of chunk c - aslots completed); lane 0 of warp 1 (and of warp 10
+// when there are two chains: each warp issues the k-steps of its chain, so
+// the issue of small MMAs runs on two threads) issues the MMAs of a stage
+// and commits them to the stage's "empty" barrier and, at the end of a
+// tile piece, to the accumulator's "full" barrier; warps
+// 6-9 read the accumulator (two in tensor memory, alternating by piece),
+// apply the Kronecker factor and store (atomically adding when the tile is
+// shared with the neighbouring CTA, whose rows were zeroed by the pack
+// kernel; two addends onto zero give the same sum in either order).
+// Shared memory:
+// stages of {A (raw) 16 KB | packed residual 2N x 32 x 4 B}, the N x N
+// factor, barriers.
 template <int NB>
 __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
-  constexpr int N = 16 * NB;                 // padded modes
-  constexpr bool STACK = 2 * N <= 128;       // [rh; rl] in one operand
-  constexpr int NOP = STACK ? 1 : 2;         // residual operand tiles per chunk
-  constexpr uint32_t SI = kInvChunk * 4, SAOP = NOP * kInvAop * 4, STAGE = SI + SAOP;
-  constexpr int YS = N + 1;                  // epilogue staging row stride
+  constexpr int N = 16 * NB;
+  constexpr uint32_t SA = kInvChunk * 4, SB = 2 * N * kInvKC * 4, STAGE = SA + SB;
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int S = a.stages, NL = a.nlo;
-  unsigned char* lo_ring = sm + S * STAGE;
-  float* Ms = reinterpret_cast<float*>(lo_ring + NL * SI);
-  float* Ys = Ms + N * N;                    // [2][32][YS]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Ys + 2 * 32 * YS + ((2 * 32 * YS) & 1));
-  uint64_t* full = bars;                     // [S] copies landed
-  uint64_t* empty = full + kInvMaxStages;    // [S] MMAs of the stage done
-  uint64_t* split = empty + kInvMaxStages;   // [NL] remainder written (128 arrivals)
-  uint64_t* lofree = split + kInvMaxLo;      // [NL] MMAs reading the slot done
-  uint64_t* accf = lofree + kInvMaxLo;       // [2] accumulator complete
-  uint64_t* acce = accf + 2;                 // [2] accumulator read (128 arrivals)
-  uint64_t* fin = acce + 2;                  // last MMA done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+  const int S = a.stages;
+  float* Ms = reinterpret_cast<float*>(sm + S * STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S * STAGE + N * N * 4);
+  uint64_t* full = bars;                      // [S] copies landed
+  uint64_t* split = bars + kInvMaxStages;     // [S] split done (128 arrivals)
+  uint64_t* empty = bars + 2 * kInvMaxStages; // [S] MMAs of the stage done
+  uint64_t* accf = bars + 3 * kInvMaxStages;  // [2] accumulator complete
+  uint64_t* acce = accf + 2;                  // [2] accumulator read (128 arrivals)
+  uint64_t* fin = acce + 2;                   // [2] last MMA of each issuer done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-  volatile int* ewait = abort + 1;           // [4] per epilogue warp: its wait succeeded
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int* meta = a.meta;
   const int* tile_start = meta + a.off[kTileStart];
   const int64_t g0 = int64_t(blockIdx.x) * a.chunks / gridDim.x;
   const int64_t g1 = int64_t(blockIdx.x + 1) * a.chunks / gridDim.x;
-  const int nch = int(g1 - g0);
-  const int nbuf = STACK ? 2 : 1;            // accumulators: 256 columns each, or D1 and D2 of one
 
   if (a.transform)
     for (int e = tid; e < N * N; e += kInvThreads) {
@@ -251,24 +244,23 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       Ms[e] = (r < a.P && c < a.P) ? a.M[r * a.P + c] : 0.f;
     }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_addr(tslot))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tslot)),
+                 "r"(a.tcols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
     for (int s = 0; s < kInvMaxStages; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(empty + s, 1);
-    }
-    for (int s = 0; s < kInvMaxLo; ++s) {
       mbar_init(split + s, 128);
-      mbar_init(lofree + s, 1);
+      mbar_init(empty + s, a.kch);
     }
     for (int k = 0; k < 2; ++k) {
-      mbar_init(accf + k, 1);
+      mbar_init(accf + k, a.kch);
       mbar_init(acce + k, 128);
     }
     mbar_init(fin, 1);
+    mbar_init(fin + 1, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -281,9 +273,10 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
     atomicExch(a.err, 1);
   };
 
-  if (warp == 0 || warp == 10) {
-    // ---- copies of the even (warp 0) or odd (warp 10) chunks; S is even,
-    // so a stage keeps its parity ----
+  if (warp == 0 || warp == 11) {
+    // ---- copies: warp 0 the even chunks, warp 11 the odd ones (a thread
+    // has about one bulk copy in issue at a time, so two threads double the
+    // copy rate; the stage count is even, so a stage keeps its parity) ----
     const int p = warp == 0 ? 0 : 1;
     if (lane == 0) {
       uint64_t pol;
@@ -296,6 +289,7 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       int it = 0;
       bool ok = true;
       while (ok && pi.next(t, cb, ce, sp)) {
+        const int64_t gt = tile_start[t];
         const int64_t gb = box_chunk0[tile_box[t]];
         for (int c = cb; c < ce; ++c, ++it) {
           if ((it & 1) != p) continue;
@@ -306,9 +300,9 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
             break;
           }
           unsigned char* st = sm + s * STAGE;
-          mbar_expect_tx(full + s, STAGE);
-          bulk_load_stream(st, a.ainv + (g0 + it) * kInvChunk, SI, full + s, pol);
-          bulk_load(st + SI, a.apack + (gb + c) * (NOP * kInvAop), SAOP, full + s);
+          mbar_expect_tx(full + s, SA + SB);
+          bulk_load_stream(st, a.ainv + (gt + c) * kInvChunk, SA, full + s, pol);
+          bulk_load(st + SA, a.bpack + (gb + c) * (2 * N * kInvKC), SB, full + s);
         }
       }
       // every copy lands before the CTA's shared memory is released (it
@@ -318,47 +312,48 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
         mbar_wait(full + s, uint32_t((u / S) & 1), kInvDrain, nullptr);
       }
     }
-  } else if (warp == 1) {
-    // ---- MMAs ----
-    if (lane == 0) {
+  } else if (warp == 1 || warp == 10) {
+    // ---- MMAs: issuer q, k-steps of chain q (all k-steps with one chain) ----
+    const int q = warp == 10 ? 1 : 0;
+    const int k0 = a.kch == 2 ? 2 * q : 0, k1 = a.kch == 2 ? k0 + 2 : kInvKC / 8;
+    if (lane == 0 && q < a.kch) {
       PieceIter pi(tile_start, a.ntiles, g0, g1);
       int t, cb, ce;
       bool sp;
       int it = 0, pc = 0;
       bool ok = true, any = false;
-      const uint32_t idesc = tf32_desc(128, kInvRows);
-      constexpr uint32_t PLA = 128 * 16, PLB = kInvRows * 16;
+      const uint32_t id2 = tf32_desc(128, 2 * N), id1 = tf32_desc(128, N);
+      constexpr uint32_t PLB = 2 * N * 16;
       while (ok && pi.next(t, cb, ce, sp)) {
-        const int acc = pc % nbuf;
-        if (pc >= nbuf && !mbar_wait(acce + acc, uint32_t((pc / nbuf - 1) & 1), a.wait_limit, abort)) {
+        const int acc = pc % a.nbuf;
+        if (pc >= a.nbuf && !mbar_wait(acce + acc, uint32_t((pc / a.nbuf - 1) & 1), a.wait_limit, abort)) {
           fail();
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t d1 = tmem + uint32_t(256 * acc), d2 = tmem + 256u;
+        // back-to-back MMAs into one accumulator wait for each other: the
+        // high and remainder products, and the k-steps of alternate chains,
+        // go to separate columns
+        const uint32_t d = tmem + uint32_t(a.acc_base + acc * a.kch * a.chain_cols);
         for (int c = cb; c < ce; ++c, ++it) {
-          const int s = it % S, l = it % NL;
-          // the split of chunk it follows the arrival of its stage
-          if (!mbar_wait(split + l, uint32_t((it / NL) & 1), a.wait_limit, abort)) {
+          const int s = it % S;
+          if (!mbar_wait(split + s, uint32_t((it / S) & 1), a.wait_limit, abort)) {
             fail();
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-          const uint32_t bh = smem_addr(sm + s * STAGE), ap = bh + SI, bl = smem_addr(lo_ring + l * SI);
-#pragma unroll
-          for (int k8 = 0; k8 < kInvKC / 8; ++k8) {
-            const uint64_t dbh = smem_desc(bh + 2 * k8 * PLB, PLB, 128);
-            const uint64_t dbl = smem_desc(bl + 2 * k8 * PLB, PLB, 128);
-            const uint64_t da = smem_desc(ap + 2 * k8 * PLA, PLA, 128);
-            const uint32_t first = (c == cb && k8 == 0) ? 0u : 1u;
-            tc_mma(d1, da, dbh, idesc, first);
-            tc_mma(d1, da, dbl, idesc, 1u);
-            if (!STACK) tc_mma(d2, da + ((kInvAop * 4) >> 4), dbh, idesc, first);
+          const uint32_t bb = smem_addr(sm + s * STAGE) + SA;
+          const uint32_t ta = tmem + uint32_t(64 * (it % a.aslots));
+          const uint32_t dc = d + uint32_t(q * a.chain_cols);
+          for (int k8 = k0; k8 < k1; ++k8) {
+            const uint64_t db = smem_desc(bb + 2 * k8 * PLB, PLB, 128);
+            const uint32_t first = (c == cb && k8 == k0) ? 0u : 1u;
+            tc_mma_ta(dc, ta + 8 * k8, db, id2, first);
+            tc_mma_ta(dc + 2 * N, ta + 32 + 8 * k8, db, id1, first);
           }
           any = true;
           tc_commit(empty + s);
-          tc_commit(lofree + l);
         }
         if (!ok) break;
         tc_commit(accf + acc);
@@ -366,148 +361,149 @@ __global__ void __launch_bounds__(kInvThreads, 1) k_ras_inv_tc(InvArgs a) {
       }
       // every MMA completes before tensor memory is freed
       if (any) {
-        tc_commit(fin);
-        mbar_wait(fin, 0u, kInvDrain, nullptr);
+        tc_commit(fin + q);
+        mbar_wait(fin + q, 0u, kInvDrain, nullptr);
       }
     }
   } else if (warp < 6) {
-    // ---- split of the inverse chunk: high part in place, remainder in the ring ----
-    const int sid = tid - 64;
-    for (int it = 0; it < nch; ++it) {
-      const int s = it % S, l = it % NL;
-      bool got = mbar_wait(full + s, uint32_t((it / S) & 1), a.wait_limit, abort);
-      if (got && it >= NL) got = mbar_wait(lofree + l, uint32_t((it / NL - 1) & 1), a.wait_limit, abort);
-      if (!got) {
-        fail();
-        break;
-      }
-      float4* ar = reinterpret_cast<float4*>(sm + s * STAGE);
-      float4* al = reinterpret_cast<float4*>(lo_ring + l * SI);
+    // ---- split of the inverse chunk: row m of the chunk into lane m ----
+    const int m = 32 * (warp & 3) + lane;
+    const uint32_t trow = tmem + (uint32_t(32 * (warp & 3)) << 16);
+    PieceIter pi(tile_start, a.ntiles, g0, g1);
+    int t, cb, ce;
+    bool sp;
+    int it = 0;
+    bool ok = true;
+    while (ok && pi.next(t, cb, ce, sp)) {
+      for (int c = cb; c < ce; ++c, ++it) {
+        const int s = it % S;
+        bool got = mbar_wait(full + s, uint32_t((it / S) & 1), a.wait_limit, abort);
+        // the slot of chunk it - aslots is free once its MMAs completed
+        if (got && it >= a.aslots) {
+          const int u = it - a.aslots;
+          got = mbar_wait(empty + u % S, uint32_t((u / S) & 1), a.wait_limit, abort);
+        }
+        // the warp converges before the aligned tensor-memory stores
+        if (!__all_sync(0xffffffffu, got)) {
+          fail();
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const unsigned char* ar = sm + s * STAGE;
+        float hi[kInvKC], lo[kInvKC];
 #pragma unroll
-      for (int q = 0; q < kInvChunk / 4 / 128; ++q) {
-        const int e = sid + 128 * q;
-        const float4 v = ar[e];
-        const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-        ar[e] = h;
-        al[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        for (int q = 0; q < kInvKC / 4; ++q) {
+          const float4 v = *reinterpret_cast<const float4*>(ar + q * 2048 + m * 16);
+          hi[4 * q] = tf32_hi(v.x);
+          hi[4 * q + 1] = tf32_hi(v.y);
+          hi[4 * q + 2] = tf32_hi(v.z);
+          hi[4 * q + 3] = tf32_hi(v.w);
+          lo[4 * q] = v.x - hi[4 * q];
+          lo[4 * q + 1] = v.y - hi[4 * q + 1];
+          lo[4 * q + 2] = v.z - hi[4 * q + 2];
+          lo[4 * q + 3] = v.w - hi[4 * q + 3];
+        }
+        const uint32_t ta = trow + uint32_t(64 * (it % a.aslots));
+        tc_st32(ta, hi);
+        tc_st32(ta + 32, lo);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        mbar_arrive(split + s);
       }
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      mbar_arrive(split + l);
     }
   } else {
-    // ---- epilogue: lane l of the accumulator = mode part l ----
-    const int et = tid - 192;                  // 0..127
-    const int l = 32 * (warp & 3) + lane;      // this thread's tensor-memory lane
-    const int part = STACK ? (l < N ? 0 : (l < 2 * N ? 1 : 2)) : (l < N ? 0 : 2);
-    const int am = part == 1 ? l - N : l;      // mode of the lane
-    const int r = et & 31, gq = et >> 5;       // row within a block of 32, output group
+    // ---- epilogue: rows 32 (warp % 4) + lane of the accumulator ----
+    const int lg = warp & 3, m = 32 * lg + lane;
     const int* tile_owned = meta + a.off[kTileOwned];
     PieceIter pi(tile_start, a.ntiles, g0, g1);
     int t, cb, ce;
     bool sp;
     int pc = 0;
     while (pi.next(t, cb, ce, sp)) {
-      const int acc = pc % nbuf;
-      const bool got = mbar_wait(accf + acc, uint32_t((pc / nbuf) & 1), a.wait_limit, abort, 256);
-      // the four warps agree before the aligned tensor-memory loads and the
-      // named barriers below: all go on or all stop
-      const bool wok = __all_sync(0xffffffffu, got);
-      if (lane == 0) ewait[warp & 3] = wok ? 1 : 0;
-      asm volatile("bar.sync 1, 128;\n" ::: "memory");
-      if (!(ewait[0] && ewait[1] && ewait[2] && ewait[3])) {
+      const int acc = pc % a.nbuf;
+      // the warp converges before the aligned tensor-memory loads
+      const bool got = mbar_wait(accf + acc, uint32_t((pc / a.nbuf) & 1), a.wait_limit, abort);
+      if (!__all_sync(0xffffffffu, got)) {
         fail();
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t base = tmem + (uint32_t(32 * (warp & 3)) << 16);
-      for (int blk = 0; blk < kInvRows / 32; ++blk) {
-        float v[32];
-        tc_ld16(base + uint32_t(256 * acc + 32 * blk), v);
-        tc_ld16(base + uint32_t(256 * acc + 32 * blk + 16), v + 16);
-        if (!STACK) {
-          float w[32];
-          tc_ld16(base + uint32_t(256 + 32 * blk), w);
-          tc_ld16(base + uint32_t(256 + 32 * blk + 16), w + 16);
+      float y[N];
+      const uint32_t base =
+          tmem + (uint32_t(32 * lg) << 16) + uint32_t(a.acc_base + acc * a.kch * a.chain_cols);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) y[16 * j + q] = 0.f;
+        for (int ch = 0; ch < a.kch; ++ch) {
+          float p0[16], p1[16], p2[16];
+          const uint32_t cbase = base + uint32_t(ch * a.chain_cols + 16 * j);
+          tc_ld16(cbase, p0);
+          tc_ld16(cbase + N, p1);
+          tc_ld16(cbase + 2 * N, p2);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] += w[q];
-        } else {
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          for (int q = 0; q < 16; ++q) y[16 * j + q] += (p0[q] + p2[q]) + p1[q];
         }
-        if (blk == kInvRows / 32 - 1) {
-          asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-          mbar_arrive(acce + acc);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      mbar_arrive(acce + acc);
+      ++pc;
+      const int g = tile_owned[int64_t(t) * 128 + m];
+      if (g < 0) continue;
+      float* zr = a.Z + g;
+      if (a.transform) {
+        for (int r = 0; r < a.P; ++r) {
+          const float4* mr = reinterpret_cast<const float4*>(Ms + r * N);
+          float v = 0.f;
+#pragma unroll
+          for (int b4 = 0; b4 < N / 4; ++b4) {
+            const float4 w = mr[b4];
+            v = fmaf(w.x, y[4 * b4], v);
+            v = fmaf(w.y, y[4 * b4 + 1], v);
+            v = fmaf(w.z, y[4 * b4 + 2], v);
+            v = fmaf(w.w, y[4 * b4 + 3], v);
+          }
+          if (sp) atomicAdd(zr + int64_t(r) * a.ld, v);
+          else zr[int64_t(r) * a.ld] = v;
         }
-        if (part < 2) {
-          float* y = Ys + part * 32 * YS + am;
+      } else {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) y[q * YS] = v[q];
-        }
-        asm volatile("bar.sync 1, 128;\n" ::: "memory");
-        // thread (r, gq): row blk * 32 + r, outputs gq, gq + 4, ...
-        const int g = tile_owned[int64_t(t) * kInvRows + blk * 32 + r];
-        if (g >= 0) {
-          float yr[N];
-#pragma unroll
-          for (int b = 0; b < N; ++b) yr[b] = STACK ? Ys[r * YS + b] + Ys[32 * YS + r * YS + b] : Ys[r * YS + b];
-          float* zr = a.Z + g;
-          if (a.transform) {
-            for (int o = gq; o < a.P; o += 4) {
-              const float4* mr = reinterpret_cast<const float4*>(Ms + o * N);
-              float x = 0.f;
-#pragma unroll
-              for (int b4 = 0; b4 < N / 4; ++b4) {
-                const float4 m4 = mr[b4];
-                x = fmaf(m4.x, yr[4 * b4], x);
-                x = fmaf(m4.y, yr[4 * b4 + 1], x);
-                x = fmaf(m4.z, yr[4 * b4 + 2], x);
-                x = fmaf(m4.w, yr[4 * b4 + 3], x);
-              }
-              if (sp) atomicAdd(zr + int64_t(o) * a.ld, x);
-              else zr[int64_t(o) * a.ld] = x;
-            }
-          } else {
-#pragma unroll
-            for (int o = 0; o < N; ++o) {
-              if ((o & 3) == gq && o < a.P) {
-                if (sp) atomicAdd(zr + int64_t(o) * a.ld, yr[o]);
-                else zr[int64_t(o) * a.ld] = yr[o];
-              }
-            }
+        for (int r = 0; r < N; ++r) {
+          if (r < a.P) {
+            if (sp) atomicAdd(zr + int64_t(r) * a.ld, y[r]);
+            else zr[int64_t(r) * a.ld] = y[r];
           }
         }
-        asm volatile("bar.sync 1, 128;\n" ::: "memory");
       }
-      ++pc;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(a.tcols) : "memory");
 }
 
-// The residual operand tiles of every box chunk: chunk (box b, c) covers
-// the overlapped nodes j = 16 c .. 16 c + 15; tile rows are modes (with
-// 2N <= 128: rows n < P the high parts of r[n][idx_b[j]], rows N + n the
-// remainders; else tile 0 the high parts, tile 1 the remainders), planes
-// of 4 nodes (16 bytes per row); the padding rows stay zero from setup.
-// One block per chunk: the gather reads runs of consecutive nodes of a mode
-// row into shared memory, the writes are whole 16-byte rows of a plane.
-// The threads also zero the output rows of the tiles that two CTAs
-// accumulate into.
+// The residual of every box in the operand layout of its chunks: chunk
+// (box b, c) holds, for the overlapped nodes j = 32 c .. 32 c + 31, the
+// rows n < N (high parts of r[n][idx_b[j]]) and N + n (remainders), planes
+// of 4 nodes (16 bytes per row).  One block per chunk: the gather reads
+// runs of consecutive nodes of a mode row into shared memory (one index
+// load, then independent loads of the rows), the writes are whole 16-byte
+// rows of a plane.  The threads also zero the output rows of the tiles that
+// two CTAs accumulate into.
 constexpr int kPackThreads = 256;
 __global__ void __launch_bounds__(kPackThreads) k_ras_inv_pack(const float* __restrict__ R, int64_t ld, int P, int N,
-                                                               int64_t bchunks, InvArgs a, float* __restrict__ apack,
+                                                               int64_t bchunks, InvArgs a, float* __restrict__ bpack,
                                                                int nsplit) {
   __shared__ float tile[96][kInvKC + 1];
   const int* meta = a.meta;
   const int* chunk_idx = meta + a.off[kChunkIdx];
   const int tid = threadIdx.x;
-  const bool stack = 2 * N <= 128;
-  const int nop = stack ? 1 : 2;
   for (int64_t gc = blockIdx.x; gc < bchunks; gc += gridDim.x) {
-    // thread (k, n0): node k of the chunk in every 16th mode row from n0
+    // thread (k, n0): node k of the chunk in every eighth mode row from n0
     const int k = tid % kInvKC, n0 = tid / kInvKC;
     const int gi = chunk_idx[gc * kInvKC + k];
     float v[96 / (kPackThreads / kInvKC)];
@@ -522,26 +518,24 @@ __global__ void __launch_bounds__(kPackThreads) k_ras_inv_pack(const float* __re
       if (n < N) tile[n][k] = v[i];
     }
     __syncthreads();
-    float4* out = reinterpret_cast<float4*>(apack + gc * (nop * kInvAop));
+    float4* out = reinterpret_cast<float4*>(bpack + gc * (2 * N * kInvKC));
     for (int e = tid; e < (kInvKC / 4) * N; e += kPackThreads) {
       const int q = e / N, n = e % N;
       const float v0 = tile[n][4 * q], v1 = tile[n][4 * q + 1], v2 = tile[n][4 * q + 2], v3 = tile[n][4 * q + 3];
       const float4 h = make_float4(tf32_hi(v0), tf32_hi(v1), tf32_hi(v2), tf32_hi(v3));
-      const float4 lo = make_float4(v0 - h.x, v1 - h.y, v2 - h.z, v3 - h.w);
-      out[q * 128 + n] = h;
-      if (stack) out[q * 128 + N + n] = lo;
-      else out[kInvAop / 4 + q * 128 + n] = lo;
+      out[q * 2 * N + n] = h;
+      out[q * 2 * N + N + n] = make_float4(v0 - h.x, v1 - h.y, v2 - h.z, v3 - h.w);
     }
     __syncthreads();
   }
   const int* split_tile = meta + a.off[kSplitTile];
   const int* tile_owned = meta + a.off[kTileOwned];
-  const int64_t nz = int64_t(nsplit) * kInvRows * P;
+  const int64_t nz = int64_t(nsplit) * 128 * P;
   const int64_t stride = int64_t(gridDim.x) * kPackThreads;
   for (int64_t e = blockIdx.x * int64_t(kPackThreads) + tid; e < nz; e += stride) {
     const int c = int(e % P);
     const int64_t r = e / P;
-    const int g = tile_owned[int64_t(split_tile[r / kInvRows]) * kInvRows + int(r % kInvRows)];
+    const int g = tile_owned[int64_t(split_tile[r / 128]) * 128 + int(r % 128)];
     if (g >= 0) a.Z[int64_t(c) * ld + g] = 0.f;
   }
 }
@@ -559,8 +553,8 @@ __global__ void k_inv_unit_rhs(double* __restrict__ R, int64_t ld, const int* __
 }
 
 // Ainv_b[m][j] = Z[j][owned_b[m]] for the boxes of one colour class, into
-// the chunk layout: tile box_tile0[b] + m / 256, chunk j / 16, plane
-// (j % 16) / 4, row m % 256, word j % 4
+// the chunk layout: tile box_tile0[b] + m / 128, chunk j / 32, plane
+// (j % 32) / 4, row m % 128, word j % 4
 __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* __restrict__ ainv,
                               const int* __restrict__ meta, InvArgs a, const int* __restrict__ color, int cls,
                               int Mpad, int Kp, int nbox) {
@@ -574,42 +568,33 @@ __global__ void k_inv_extract(const double* __restrict__ Zs, int64_t ld, float* 
     if (color[b] != cls) continue;
     const int64_t rem = t - int64_t(b) * Mpad * Kp;
     const int m = int(rem / Kp), j = int(rem % Kp);
-    const int tile = box_tile0[b] + m / kInvRows;
+    const int tile = box_tile0[b] + m / 128;
     if (tile >= box_tile0[b + 1]) continue;                 // past the box's last tile
     const int64_t c0 = tile_start[tile];
     if (j >= (tile_start[tile + 1] - c0) * kInvKC) continue;  // past the box's last chunk
-    const int g = tile_owned[int64_t(tile) * kInvRows + m % kInvRows];
+    const int g = tile_owned[int64_t(tile) * 128 + m % 128];
     const float v = (g >= 0 && j < nov[b]) ? float(Zs[int64_t(j) * ld + g]) : 0.f;
-    ainv[(c0 + j / kInvKC) * kInvChunk + ((j % kInvKC) / 4) * (kInvRows * 4) + (m % kInvRows) * 4 + (j % 4)] = v;
+    ainv[(c0 + j / kInvKC) * kInvChunk + ((j % kInvKC) / 4) * 512 + (m % 128) * 4 + (j % 4)] = v;
   }
 }
 
-// stage depth (even: two copy warps) and remainder ring for N padded modes
-struct InvShape {
-  int stages, nlo;
-  size_t smem;
-};
-InvShape inv_shape(int P) {
+size_t inv_stage_bytes(int N) { return size_t(kInvChunk) * 4 + 2 * size_t(N) * kInvKC * 4; }
+size_t inv_fixed_bytes(int N) { return size_t(N) * N * 4 + (3 * kInvMaxStages + 6) * 8 + 16; }
+
+int inv_stages(int P) {
   const int N = (P + 15) / 16 * 16;
-  const int nop = 2 * N <= 128 ? 1 : 2;
-  const size_t si = size_t(kInvChunk) * 4, stage = si + size_t(nop) * kInvAop * 4;
-  const size_t fixed = size_t(N) * N * 4 + (2 * 32 * (N + 1) + 1) * 4 +
-                       (2 * kInvMaxStages + 2 * kInvMaxLo + 5) * 8 + 32;
-  for (int nlo = kInvMaxLo; nlo >= 2; --nlo) {
-    if (fixed + nlo * si > kSmemLimit) continue;
-    const int s = int(std::min<size_t>(kInvMaxStages, (kSmemLimit - fixed - nlo * si) / stage)) & ~1;
-    if (s >= 4 || (nlo == 2 && s >= 2)) return InvShape{s, nlo, fixed + nlo * si + s * stage};
-  }
-  return InvShape{0, 0, 0};
+  const size_t room = kSmemLimit - inv_fixed_bytes(N);
+  return int(std::min<size_t>(kInvMaxStages, room / inv_stage_bytes(N))) & ~1;  // even: two copy warps
 }
 
 template <int NB>
-sg_status inv_launch(const InvArgs& args, int grid, size_t smem, cudaStream_t st) {
+sg_status inv_launch(const InvArgs& args, int grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     SG_CUDA(cudaFuncSetAttribute(k_ras_inv_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemLimit)));
     attr = true;
   }
+  const size_t smem = args.stages * inv_stage_bytes(16 * NB) + inv_fixed_bytes(16 * NB);
   k_ras_inv_tc<NB><<<unsigned(grid), kInvThreads, smem, st>>>(args);
   note_launch();
   SG_CUDA(cudaGetLastError());
@@ -627,7 +612,7 @@ InvArgs inv_args(const RasData& D) {
 
 // the index list of the widest supported box: 48 x 48 overlapped nodes
 constexpr int kInvMaxKp = 48 * 48;
-bool ras_inverse_supported(int P) { return P >= 1 && P <= 96 && inv_shape(P).stages >= 2; }
+bool ras_inverse_supported(int P) { return P >= 1 && P <= 96 && inv_stages(P) >= 2; }
 
 sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   RasData& D = pc.ras;
@@ -661,9 +646,9 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
     set_error("RAS explicit inverses: overlapped boxes of at most 2,304 nodes");
     return SG_ERR_UNSUPPORTED;
   }
-  const int Mpad = (omax + kInvRows - 1) / kInvRows * kInvRows;
-  const int P = pr->P, N = (P + 15) / 16 * 16, nop = 2 * N <= 128 ? 1 : 2;
-  // tiles (256 owned rows of a box) and chunks (16 overlapped nodes)
+  const int Mpad = (omax + 127) / 128 * 128;
+  const int P = pr->P, N = (P + 15) / 16 * 16;
+  // tiles (128 owned rows of a box) and chunks (32 overlapped nodes)
   std::vector<int> tile_start{0}, tile_box, tile_owned, box_chunk0(nbox), box_tile0(nbox + 1), chunk_idx, hidx(
       size_t(nbox) * Kp, 0);
   int64_t bchunks = 0;
@@ -680,11 +665,10 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
       hidx[size_t(b) * Kp + j] = D.idx[b][j];
       if (D.owned[b][j]) own.push_back(D.idx[b][j]);
     }
-    for (int t = 0; t * kInvRows < nown[b]; ++t) {
+    for (int t = 0; t * 128 < nown[b]; ++t) {
       tile_box.push_back(b);
       tile_start.push_back(tile_start.back() + nch);
-      for (int r = 0; r < kInvRows; ++r)
-        tile_owned.push_back(t * kInvRows + r < nown[b] ? own[t * kInvRows + r] : -1);
+      for (int r = 0; r < 128; ++r) tile_owned.push_back(t * 128 + r < nown[b] ? own[t * 128 + r] : -1);
     }
   }
   box_tile0[nbox] = int(tile_box.size());
@@ -722,15 +706,13 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
     meta.insert(meta.end(), parts[k]->begin(), parts[k]->end());
     meta.resize((meta.size() + 3) / 4 * 4, 0);
   }
-  DevBuf dmeta, dcol, dainv, dapack;
+  DevBuf dmeta, dcol, dainv, dbpack;
   SG_TRY(dmeta.alloc(meta.size() * 4));
   SG_TRY(dcol.alloc(color.size() * 4));
   SG_CUDA(cudaMemcpy(dmeta.ptr, meta.data(), meta.size() * 4, cudaMemcpyHostToDevice));
   SG_CUDA(cudaMemcpy(dcol.ptr, color.data(), color.size() * 4, cudaMemcpyHostToDevice));
   SG_TRY(dainv.alloc(size_t(chunks) * kInvChunk * 4));
-  SG_TRY(dapack.alloc(size_t(bchunks) * nop * kInvAop * 4));
-  // the operand rows past the modes stay zero; the pack writes the others
-  SG_CUDA(cudaMemsetAsync(dapack.ptr, 0, dapack.bytes, st));
+  SG_TRY(dbpack.alloc(size_t(bchunks) * 2 * N * kInvKC * 4));
   D.d_inv_meta = std::move(dmeta);
   InvArgs ia = inv_args(D);
   const int* dm = dp<int>(D.d_inv_meta);
@@ -759,10 +741,11 @@ sg_status ras_inverse_build(sg_problem* pr, Precond& pc, cudaStream_t st) {
   D.inv_ntiles = ntiles;
   D.inv_grid = grid;
   D.inv_nsplit = int(split_tile.size());
+  D.inv_stages = inv_stages(P);
   D.inv_chunks = chunks;
   D.inv_bchunks = bchunks;
   D.d_inv = std::move(dainv);
-  D.d_inv_bpack = std::move(dapack);
+  D.d_inv_bpack = std::move(dbpack);
   if (!D.d_inv_err.ptr) SG_TRY(D.d_inv_err.alloc(16));
   SG_CUDA(cudaMemset(D.d_inv_err.ptr, 0, 16));
   return SG_OK;
@@ -786,18 +769,37 @@ sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld
     return SG_ERR_ARG;
   }
   const int N = D.inv_n;
-  const InvShape sh = inv_shape(P);
   InvArgs a = inv_args(D);
   a.Z = Z;
   a.ld = ld;
   a.ainv = dp<float>(D.d_inv);
-  a.apack = dp<float>(D.d_inv_bpack);
+  a.bpack = dp<float>(D.d_inv_bpack);
   a.M = M;
   a.transform = transform ? 1 : 0;
   a.P = P;
-  a.stages = sh.stages;
-  a.nlo = sh.nlo;
+  a.stages = D.inv_stages;
   a.ntiles = D.inv_ntiles;
+  // tensor memory (512 columns): the split inverse chunks in slots of 64
+  // columns from column 0, then the accumulators, each of kch chains of
+  // chain_cols columns.  Preferred: two chains, two accumulators, four
+  // slots; fewer where 512 columns do not hold them (two chains count more
+  // than a second accumulator: a tile piece is 40 chunks of MMAs).
+  a.chain_cols = (3 * N + 31) / 32 * 32;
+  a.tcols = 512;
+  const int shapes[6][3] = {{2, 2, 4}, {2, 2, 2}, {2, 1, 3}, {2, 1, 2}, {1, 1, 4}, {1, 1, 2}};
+  a.kch = 0;
+  for (const auto& sh : shapes)
+    if (64 * sh[2] + sh[0] * sh[1] * a.chain_cols <= 512) {
+      a.kch = sh[0];
+      a.nbuf = sh[1];
+      a.aslots = sh[2];
+      break;
+    }
+  if (!a.kch) {
+    set_error("ras_inverse_apply: tensor memory too small for P modes");
+    return SG_ERR_UNSUPPORTED;
+  }
+  a.acc_base = 64 * a.aslots;
   a.chunks = D.inv_chunks;
   a.err = dp<int>(D.d_inv_err);
   a.wait_limit = wait_limit;
@@ -808,12 +810,12 @@ sg_status ras_inverse_apply(const Precond& pc, int P, const float* R, int64_t ld
   note_launch();
   SG_CUDA(cudaGetLastError());
   switch (N / 16) {
-    case 1: return inv_launch<1>(a, D.inv_grid, sh.smem, st);
-    case 2: return inv_launch<2>(a, D.inv_grid, sh.smem, st);
-    case 3: return inv_launch<3>(a, D.inv_grid, sh.smem, st);
-    case 4: return inv_launch<4>(a, D.inv_grid, sh.smem, st);
-    case 5: return inv_launch<5>(a, D.inv_grid, sh.smem, st);
-    case 6: return inv_launch<6>(a, D.inv_grid, sh.smem, st);
+    case 1: return inv_launch<1>(a, D.inv_grid, st);
+    case 2: return inv_launch<2>(a, D.inv_grid, st);
+    case 3: return inv_launch<3>(a, D.inv_grid, st);
+    case 4: return inv_launch<4>(a, D.inv_grid, st);
+    case 5: return inv_launch<5>(a, D.inv_grid, st);
+    case 6: return inv_launch<6>(a, D.inv_grid, st);
     default: set_error("ras_inverse_apply: P > 96"); return SG_ERR_ARG;
   }
 }

@@ -56,7 +56,7 @@ struct RasData {
   // operand layout (tiles of 128 owned rows in box order, chunks in node
   // order), the buffer of the packed residual, the index tables (offsets in
   // ints into d_inv_meta, InvMeta order) and a timeout flag
-  int inv_kp = 0, inv_n = 0, inv_p = 0, inv_ntiles = 0, inv_grid = 0, inv_nsplit = 0;
+  int inv_kp = 0, inv_n = 0, inv_p = 0, inv_ntiles = 0, inv_grid = 0, inv_nsplit = 0, inv_stages = 0;
   int64_t inv_chunks = 0, inv_bchunks = 0;
   int64_t inv_off[10] = {};
   DevBuf d_inv, d_inv_meta, d_inv_bpack, d_inv_err;
