@@ -600,7 +600,7 @@ enum AmgOp { kDown, kRestrict, kProlong, kResid, kFinal };
 
 template <typename T>
 struct AmgPhase {
-  int n = 0, G = 1;
+  int n = 0, G = 1, P = 1;
   const int* rp = nullptr;
   const int* ci = nullptr;
   const T* v = nullptr;
@@ -616,45 +616,85 @@ struct AmgPhase {
   T* Y2 = nullptr;        // kDown: x = D^{-1} b (ld ldy)
 };
 
-template <typename T, int OP>
+// MB modes per thread group: the row's pattern and values are read once
+// for MB right-hand sides (blockIdx.y covers modes MB y .. MB y + MB - 1)
+template <typename T, int OP, int MB>
 __global__ void __launch_bounds__(128) k_amg_phase(const __grid_constant__ AmgPhase<T> p) {
   const int G = p.G;
   const int grp = threadIdx.x / G, lane = threadIdx.x - grp * G;
   const int i = blockIdx.x * (128 / G) + grp;
-  const int64_t a = blockIdx.y;
+  const int64_t a0 = int64_t(blockIdx.y) * MB;
+  const int nm = int(min(int64_t(MB), int64_t(p.P) - a0));
   const bool live = i < p.n;
-  const T* X = p.X + a * p.ldx;
-  T acc = T(0);
+  T acc[MB];
+#pragma unroll
+  for (int m = 0; m < MB; ++m) acc[m] = T(0);
   if (live) {
     const int e1 = p.rp[i + 1];
     for (int e = p.rp[i] + lane; e < e1; e += G) {
       const int j = p.ci[e];
-      T g;
-      if (OP == kDown)
-        g = p.d[j] * X[j];
-      else if (OP == kProlong)
-        g = p.Xd ? X[j] + p.Xd[j] * p.Xt[a * p.ldx + j] : X[j];
-      else
-        g = X[j];
-      acc += p.v[e] * g;
+      const T v = p.v[e];
+      T dj = T(0);
+      if (OP == kDown || (OP == kProlong && p.Xd)) dj = OP == kDown ? p.d[j] : p.Xd[j];
+#pragma unroll
+      for (int m = 0; m < MB; ++m) {
+        if (m < nm) {
+          const T* X = p.X + (a0 + m) * p.ldx;
+          T g;
+          if (OP == kDown)
+            g = dj * X[j];
+          else if (OP == kProlong)
+            g = p.Xd ? X[j] + dj * p.Xt[(a0 + m) * p.ldx + j] : X[j];
+          else
+            g = X[j];
+          acc[m] += v * g;
+        }
+      }
     }
   }
-  for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+#pragma unroll
+  for (int m = 0; m < MB; ++m)
+    for (int o = G >> 1; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
   if (!live || lane != 0) return;
-  T* y = p.Y + a * p.ldy + i;
-  if (OP == kDown) {
-    const T bi = p.B[a * p.ldb + i];
-    *y = bi - acc;
-    p.Y2[a * p.ldy + i] = p.d[i] * bi;
-  } else if (OP == kRestrict) {
-    *y = acc;
-  } else if (OP == kProlong) {
-    *y += acc;
-  } else if (OP == kResid) {
-    *y = p.B[a * p.ldb + i] - acc;
-  } else {
-    *y = X[i] + p.d[i] * (p.B[a * p.ldb + i] - acc);
+#pragma unroll
+  for (int m = 0; m < MB; ++m) {
+    if (m >= nm) break;
+    const int64_t a = a0 + m;
+    T* y = p.Y + a * p.ldy + i;
+    if (OP == kDown) {
+      const T bi = p.B[a * p.ldb + i];
+      *y = bi - acc[m];
+      p.Y2[a * p.ldy + i] = p.d[i] * bi;
+    } else if (OP == kRestrict) {
+      *y = acc[m];
+    } else if (OP == kProlong) {
+      *y += acc[m];
+    } else if (OP == kResid) {
+      *y = p.B[a * p.ldb + i] - acc[m];
+    } else {
+      *y = p.X[a * p.ldx + i] + p.d[i] * (p.B[a * p.ldb + i] - acc[m]);
+    }
   }
+}
+
+// the phase kernel with the largest MB in {1, 2, 4, 8} that still leaves
+// about one wave of resident threads (152 SMs x 2048) of (row, mode group)
+// lane groups
+template <typename T, int OP>
+cudaError_t amg_phase_launch(const AmgPhase<T>& p, cudaStream_t st) {
+  const int rows = 128 / p.G;
+  const int64_t lanes_per_mode_group = int64_t(p.n) * p.G;
+  int MB = 8;
+  while (MB > 1 && lanes_per_mode_group * ((p.P + MB - 1) / MB) < 152 * 2048) MB >>= 1;
+  const dim3 grid(unsigned((p.n + rows - 1) / rows), unsigned((p.P + MB - 1) / MB));
+  switch (MB) {
+    case 8: k_amg_phase<T, OP, 8><<<grid, 128, 0, st>>>(p); break;
+    case 4: k_amg_phase<T, OP, 4><<<grid, 128, 0, st>>>(p); break;
+    case 2: k_amg_phase<T, OP, 2><<<grid, 128, 0, st>>>(p); break;
+    default: k_amg_phase<T, OP, 1><<<grid, 128, 0, st>>>(p); break;
+  }
+  note_launch();
+  return cudaGetLastError();
 }
 
 // Coarsest level with a warp per row: x = A_c^{-1} b (explicit FP64 inverse)
@@ -845,15 +885,10 @@ sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T*
       while (G < 32 && 2 * G < avg && M.n * int64_t(P) * (2 * G) <= 2 * 152 * 2048) G <<= 1;
       return G;
     };
-    auto launch = [&](auto kern, AmgPhase<T> p) -> sg_status {
-      const int rows = 128 / p.G;
-      kern<<<dim3(unsigned((p.n + rows - 1) / rows), unsigned(P)), 128, 0, st>>>(p); note_launch();
-      SG_CUDA(cudaGetLastError());
-      return SG_OK;
-    };
     auto phase = [&](const DevCsr& M) {
       AmgPhase<T> p;
       p.n = int(M.n);
+      p.P = P;
       p.G = lanes(M);
       p.rp = M.rowptr.as<int>();
       p.ci = M.col.as<int>();
@@ -871,13 +906,13 @@ sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T*
       p.Y = w.t[l];
       p.Y2 = w.x[l];
       p.ldy = L.ld;
-      SG_TRY(launch(k_amg_phase<T, kDown>, p));
+      SG_CUDA((amg_phase_launch<T, kDown>(p, st)));
       AmgPhase<T> q = phase(L.R);
       q.X = w.t[l];
       q.ldx = L.ld;
       q.Y = w.b[l + 1];
       q.ldy = H[l + 1].ld;
-      SG_TRY(launch(k_amg_phase<T, kRestrict>, q));
+      SG_CUDA((amg_phase_launch<T, kRestrict>(q, st)));
     }
     {
       const AmgLevel& L = H[nl - 1];
@@ -898,7 +933,7 @@ sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T*
       }
       p.Y = w.x[l];
       p.ldy = L.ld;
-      SG_TRY(launch(k_amg_phase<T, kProlong>, p));
+      SG_CUDA((amg_phase_launch<T, kProlong>(p, st)));
       AmgPhase<T> q = phase(L.A);
       q.X = w.x[l];
       q.ldx = L.ld;
@@ -908,11 +943,11 @@ sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T*
       if (l > 0 || out == w.x[0]) {
         q.Y = w.t[l];
         q.ldy = L.ld;
-        SG_TRY(launch(k_amg_phase<T, kResid>, q));
+        SG_CUDA((amg_phase_launch<T, kResid>(q, st)));
       } else {
         q.Y = out;
         q.ldy = ldo;
-        SG_TRY(launch(k_amg_phase<T, kFinal>, q));
+        SG_CUDA((amg_phase_launch<T, kFinal>(q, st)));
       }
     }
     if (out == w.x[0]) {
