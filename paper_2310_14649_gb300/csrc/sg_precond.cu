@@ -697,101 +697,6 @@ cudaError_t amg_phase_launch(const AmgPhase<T>& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// The levels below the first of the V-cycle in one launch: a cluster of
-// kAmgCl CTAs per PCE mode (modes are independent), the rows of a level
-// split over the cluster's CTAs, a cluster barrier (hardware, no polling)
-// between the phases: per level l = 1 .. nl-2 the down phase and the
-// restriction, the coarsest dense solve, then per level the prolongation
-// (post-smoothing of the level below folded in) and the residual.  The
-// same arithmetic as the per-phase kernels, one thread per row (a warp per
-// row for the dense solve); the first level's phases run GPU-wide around
-// it.
-constexpr int kAmgCl = 8, kAmgClThreads = 256, kAmgMaxLev = 12;
-template <typename T>
-struct AmgCoarseArgs {
-  int nl = 0, nc = 0;
-  const double* cinv = nullptr;  // coarsest inverse, nc x nc
-  struct Lev {
-    int n = 0;
-    int64_t ld = 0;
-    const int *arp = nullptr, *aci = nullptr, *rrp = nullptr, *rci = nullptr, *prp = nullptr, *pci = nullptr;
-    const T *av = nullptr, *rv = nullptr, *pv = nullptr, *d = nullptr;
-    T *b = nullptr, *t = nullptr, *x = nullptr;
-  } lev[kAmgMaxLev];
-};
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-
-template <typename T>
-__global__ void __cluster_dims__(kAmgCl, 1, 1) __launch_bounds__(kAmgClThreads)
-    k_amg_coarse(const __grid_constant__ AmgCoarseArgs<T> c) {
-  unsigned rank;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(rank));
-  const int64_t a = blockIdx.y;
-  const int t0 = int(rank) * kAmgClThreads + threadIdx.x, stride = kAmgCl * kAmgClThreads;
-  const int nl = c.nl;
-  for (int l = 1; l < nl - 1; ++l) {
-    const auto& L = c.lev[l];
-    const T* b = L.b + a * L.ld;
-    for (int i = t0; i < L.n; i += stride) {
-      T acc = T(0);
-      for (int e = L.arp[i]; e < L.arp[i + 1]; ++e) {
-        const int j = L.aci[e];
-        acc += L.av[e] * (L.d[j] * b[j]);
-      }
-      L.t[a * L.ld + i] = b[i] - acc;
-      L.x[a * L.ld + i] = L.d[i] * b[i];
-    }
-    cluster_sync_all();
-    const auto& Ln = c.lev[l + 1];
-    const T* t = L.t + a * L.ld;
-    for (int i = t0; i < Ln.n; i += stride) {
-      T acc = T(0);
-      for (int e = L.rrp[i]; e < L.rrp[i + 1]; ++e) acc += L.rv[e] * t[L.rci[e]];
-      Ln.b[a * Ln.ld + i] = acc;
-    }
-    cluster_sync_all();
-  }
-  {
-    // coarsest: x = A_c^{-1} b, a warp per row, FP64 sums
-    const auto& L = c.lev[nl - 1];
-    const int warp = t0 >> 5, lane = threadIdx.x & 31, nwarps = stride >> 5;
-    const T* b = L.b + a * L.ld;
-    for (int i = warp; i < c.nc; i += nwarps) {
-      double acc = 0.0;
-      for (int j = lane; j < c.nc; j += 32) acc += c.cinv[int64_t(i) * c.nc + j] * double(b[j]);
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) L.x[a * L.ld + i] = T(acc);
-    }
-    cluster_sync_all();
-  }
-  for (int l = nl - 2; l >= 1; --l) {
-    const auto& L = c.lev[l];
-    const auto& Ln = c.lev[l + 1];
-    const bool smooth = l + 1 < nl - 1;
-    const T* xn = Ln.x + a * Ln.ld;
-    const T* tn = Ln.t + a * Ln.ld;
-    for (int i = t0; i < L.n; i += stride) {
-      T acc = T(0);
-      for (int e = L.prp[i]; e < L.prp[i + 1]; ++e) {
-        const int j = L.pci[e];
-        acc += L.pv[e] * (smooth ? xn[j] + Ln.d[j] * tn[j] : xn[j]);
-      }
-      L.x[a * L.ld + i] += acc;
-    }
-    cluster_sync_all();
-    const T* x = L.x + a * L.ld;
-    for (int i = t0; i < L.n; i += stride) {
-      T acc = T(0);
-      for (int e = L.arp[i]; e < L.arp[i + 1]; ++e) acc += L.av[e] * x[L.aci[e]];
-      L.t[a * L.ld + i] = L.b[a * L.ld + i] - acc;
-    }
-    cluster_sync_all();
-  }
-}
-
 // Coarsest level with a warp per row: x = A_c^{-1} b (explicit FP64 inverse)
 template <typename T>
 __global__ void k_dense_solve_warp(int n, const double* __restrict__ Ainv, const T* __restrict__ B, int64_t ldb,
@@ -990,10 +895,7 @@ sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T*
       p.v = dv<T>(M.v64, M.v32);
       return p;
     };
-    // levels 1 .. nl-1 in one cluster launch when the hierarchy has them
-    const bool clustered = nl >= 3 && nl <= kAmgMaxLev;
-    const int ldown = clustered ? 1 : nl - 1;
-    for (int l = 0; l < ldown; ++l) {
+    for (int l = 0; l < nl - 1; ++l) {
       const AmgLevel& L = H[l];
       AmgPhase<T> p = phase(L.A);
       p.X = w.b[l];
@@ -1012,42 +914,14 @@ sg_status amg_vcycle(const AmgHier& H, AmgWork<T>& w, int P, cudaStream_t st, T*
       q.ldy = H[l + 1].ld;
       SG_CUDA((amg_phase_launch<T, kRestrict>(q, st)));
     }
-    if (clustered) {
-      AmgCoarseArgs<T> ca;
-      ca.nl = nl;
-      ca.nc = int(H[nl - 1].n);
-      ca.cinv = H.coarsest_inv64.as<double>();
-      for (int l = 1; l < nl; ++l) {
-        const AmgLevel& L = H[l];
-        auto& cl = ca.lev[l];
-        cl.n = int(L.n);
-        cl.ld = L.ld;
-        cl.arp = L.A.rowptr.as<int>();
-        cl.aci = L.A.col.as<int>();
-        cl.av = dv<T>(L.A.v64, L.A.v32);
-        cl.d = dv<T>(L.dinv64, L.dinv32);
-        if (l + 1 < nl) {
-          cl.rrp = L.R.rowptr.as<int>();
-          cl.rci = L.R.col.as<int>();
-          cl.rv = dv<T>(L.R.v64, L.R.v32);
-          cl.prp = L.Pm.rowptr.as<int>();
-          cl.pci = L.Pm.col.as<int>();
-          cl.pv = dv<T>(L.Pm.v64, L.Pm.v32);
-        }
-        cl.b = w.b[l];
-        cl.t = w.t[l];
-        cl.x = w.x[l];
-      }
-      k_amg_coarse<T><<<dim3(kAmgCl, unsigned(P)), kAmgClThreads, 0, st>>>(ca); note_launch();
-      SG_CUDA(cudaGetLastError());
-    } else {
+    {
       const AmgLevel& L = H[nl - 1];
       dim3 g(unsigned((L.n + 3) / 4), unsigned(P));
       k_dense_solve_warp<T><<<g, 128, 0, st>>>(int(L.n), H.coarsest_inv64.as<double>(), w.b[nl - 1], L.ld,
                                                w.x[nl - 1], L.ld); note_launch();
       SG_CUDA(cudaGetLastError());
     }
-    for (int l = clustered ? 0 : nl - 2; l >= 0; --l) {
+    for (int l = nl - 2; l >= 0; --l) {
       const AmgLevel& L = H[l];
       const AmgLevel& Ln = H[l + 1];
       AmgPhase<T> p = phase(L.Pm);
