@@ -353,7 +353,10 @@ typedef struct {
   int mode;           /* 0: FP64 FGMRES with FP64 preconditioner;
                          1: FP32 FGMRES + FP32 preconditioner inside FP64
                             iterative refinement (FP64 residuals)              */
-  double inner_rtol;  /* mode 1: tolerance of each FP32 solve; <= 0 = 1e-4      */
+  double inner_rtol;  /* mode 1: tolerance of each FP32 solve (relative to the
+                          step's residual; a step whose residual is within a
+                          factor of the target stops at half of rtol / rr,
+                          at most 0.5); <= 0 = 1e-4                         */
   int max_ir;         /* mode 1: refinement steps cap; <= 0 = 20               */
   double* hist_host;  /* optional host buffer for the residual history         */
   int hist_cap;

@@ -581,8 +581,12 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
       GmresResult res;
       // the FP32 correction solve stops on its Arnoldi estimate: its true FP32
       // residual cannot fall much below u_32 * cond(A), the FP64 loop
-      // measures the real progress
-      const sg_status gs = gmres_run<float>(c32->fine, A, M, r32, d32, true, inner, o->max_it - inf.outer_it, res,
+      // measures the real progress.  It needs to reduce the residual only by
+      // the factor left to the target: at most `inner`, at least half of
+      // rtol / rr (capped at 0.5), so a last step just above the target is
+      // one or two iterations instead of a full 1e-4 reduction.
+      const double inner_k = std::max(inner, std::min(0.5, 0.5 * o->rtol / rr));
+      const sg_status gs = gmres_run<float>(c32->fine, A, M, r32, d32, true, inner_k, o->max_it - inf.outer_it, res,
                                             nullptr, 1.0, st, true, stall_test && S.pc.use_cnn);
       inf.outer_it += res.its;
       if (stall_test && S.pc.use_cnn && (gs == SG_ERR_BREAKDOWN || res.stalled)) {
