@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "poisson256_L4_p3"
 METRIC = "SG solve time to relres 1e-8 (FP32 in FP64 refinement, two-level RAS+AMG FGMRES)"
-INNER_RTOL = 0.3          # inner coarse GMRES tolerance of the timed solves
+INNER_RTOL = 0.5          # inner coarse GMRES tolerance of the timed solves
 RAS_KERNEL = 3            # FP32 RAS local solves: the faster of the line kernel and the explicit inverses
 PAPER_INNER_RTOL = 1e-5   # the paper's default for the 2GV3 variant
 
