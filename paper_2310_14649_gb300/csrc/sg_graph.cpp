@@ -157,7 +157,8 @@ static sg_status capture_twolevel(SolverCtx<T>& c, const T* R, T* Z, cudaStream_
 // the iteration cap stored in fdg.iv[2].
 template <typename T>
 static sg_status capture_fine(SolverCtx<T>& c, const T* b, T* x, double rtol, bool trust, const CapStreams& S,
-                              cudaStream_t top) {
+                              cudaStream_t top, const double* rr2 = nullptr, const double* nf2 = nullptr,
+                              double target = 0.0) {
   KrylovWork<T>& W = c.fine;
   const int m = W.m;
   const int64_t len = c.len;
@@ -181,7 +182,7 @@ static sg_status capture_fine(SolverCtx<T>& c, const T* b, T* x, double rtol, bo
   SG_CUDA(cudaStreamGetCaptureInfo(top, &cs, nullptr, &g, nullptr, nullptr, nullptr));
   cudaGraphConditionalHandle hout, hin;
   SG_CUDA(cudaGraphConditionalHandleCreate(&hout, g, 0, 0));
-  SG_TRY(dg_init(c.fdg, W.s.scal + 5, rtol, hout, top));
+  SG_TRY(dg_init(c.fdg, W.s.scal + 5, rtol, hout, top, rr2, nf2, target));
   const int64_t k1 = launch_count();
   int64_t k2 = 0, k3 = 0;
   cudaGraph_t body_out;
@@ -295,7 +296,9 @@ static sg_status capture_system_nodes(GraphSystem& gs, const sg_solve_opts& o, c
   SG_CUDA(cudaStreamBeginCaptureToGraph(i2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   SG_TRY((vec_convert<double, float>(r64, r32, len, nullptr, ird, i2)));
   SG_CUDA(cudaMemsetAsync(d32, 0, len * 4, i2));
-  SG_TRY(capture_fine<float>(*c32, r32, d32, inner, true, gs.streams, i2));
+  // the FP32 correction stops at the reduction left to the target when
+  // that is looser than `inner` (the host-driven refinement's rule)
+  SG_TRY(capture_fine<float>(*c32, r32, d32, inner, true, gs.streams, i2, ird, ird + 1, o.rtol));
   SG_TRY(vec_add_scaled_f32(x64, d32, len, ird, i2));
   SG_TRY(c64->apply_raw_fine(x64, r64, F64, i2));
   SG_TRY(vec_norm2<double>(r64, len, ird, part, cnt, i2));

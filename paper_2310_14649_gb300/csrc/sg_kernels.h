@@ -107,7 +107,11 @@ sg_status dg_scale_next(const T* w, T* V, int64_t stride, int64_t len, DevGmres 
 template <typename T>
 sg_status dg_copy_vj(const T* V, int64_t stride, int64_t lds, T* dst, int64_t ldd, int64_t n, int P, DevGmres d,
                      cudaStream_t st);
-sg_status dg_init(DevGmres d, const double* rnorm2, double rtol, cudaGraphConditionalHandle outer, cudaStream_t st);
+// rr2, nf2 (device, may be NULL): squared FP64 residual and right-hand-side
+// norms of the enclosing refinement step; with them the tolerance is
+// max(rtol, min(0.5, 0.5 target / (||r|| / ||F||)))
+sg_status dg_init(DevGmres d, const double* rnorm2, double rtol, cudaGraphConditionalHandle outer, cudaStream_t st,
+                  const double* rr2 = nullptr, const double* nf2 = nullptr, double target = 0.0);
 sg_status dg_start(DevGmres d, GmresState s, int m, const double* beta2, cudaGraphConditionalHandle inner,
                    cudaStream_t st);
 sg_status dg_givens(DevGmres d, GmresState s, int m, cudaGraphConditionalHandle inner, cudaStream_t st);

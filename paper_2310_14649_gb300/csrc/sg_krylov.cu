@@ -324,9 +324,14 @@ sg_status gmres_backsolve(GmresState s, int m, int k, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 namespace {
 
-__global__ void k_dg_init(DevGmres d, const double* __restrict__ rnorm2, double rtol, cudaGraphConditionalHandle outer) {
+__global__ void k_dg_init(DevGmres d, const double* __restrict__ rnorm2, double rtol, cudaGraphConditionalHandle outer,
+                          const double* __restrict__ rr2, const double* __restrict__ nf2, double target) {
   const double nr = sqrt(*rnorm2);
-  d.dtol[0] = rtol * nr;
+  double tol = rtol;
+  // a refinement step within a factor of its target: the reduction still
+  // needed, with a factor two of margin (at most 0.5)
+  if (rr2 && nf2 && *rr2 > 0.0 && *nf2 > 0.0) tol = fmax(rtol, fmin(0.5, 0.5 * target / sqrt(*rr2 / *nf2)));
+  d.dtol[0] = tol * nr;
   d.iv[1] = 0;  // iterations
   d.iv[3] = 0;  // stop
   d.iv[5] = 0;  // breakdown
@@ -505,8 +510,9 @@ sg_status dg_copy_vj(const T* V, int64_t stride, int64_t lds, T* dst, int64_t ld
   return SG_OK;
 }
 
-sg_status dg_init(DevGmres d, const double* rnorm2, double rtol, cudaGraphConditionalHandle outer, cudaStream_t st) {
-  k_dg_init<<<1, 1, 0, st>>>(d, rnorm2, rtol, outer);
+sg_status dg_init(DevGmres d, const double* rnorm2, double rtol, cudaGraphConditionalHandle outer, cudaStream_t st,
+                  const double* rr2, const double* nf2, double target) {
+  k_dg_init<<<1, 1, 0, st>>>(d, rnorm2, rtol, outer, rr2, nf2, target);
   note_launch();
   SG_CUDA(cudaGetLastError());
   return SG_OK;
