@@ -356,7 +356,7 @@ typedef struct {
   double inner_rtol;  /* mode 1: tolerance of each FP32 solve (relative to the
                           step's residual; a step whose residual is within a
                           factor of the target stops at half of rtol / rr,
-                          at most 0.5); <= 0 = 1e-4                         */
+                          at most 0.5); <= 0 = 3e-4                         */
   int max_ir;         /* mode 1: refinement steps cap; <= 0 = 20               */
   double* hist_host;  /* optional host buffer for the residual history         */
   int hist_cap;

@@ -277,7 +277,7 @@ static sg_status capture_system_nodes(GraphSystem& gs, const sg_solve_opts& o, c
   double* r64 = dp<double>(S.r64);
   double* part = dp<double>(c64->fine.partial);
   unsigned* cnt = dp<unsigned>(c64->fine.counter);
-  const double inner = o.inner_rtol > 0 ? o.inner_rtol : 1e-4;
+  const double inner = o.inner_rtol > 0 ? o.inner_rtol : 3e-4;  // the host-driven refinement's default
   const int max_ir = o.max_ir > 0 ? o.max_ir : 20;
   const cudaStream_t i2 = gs.streams.s[1];
   const int64_t k0 = launch_count();
