@@ -344,3 +344,35 @@ def test_ras_explicit_inverses(pair):
         assert np.max(np.abs(Y - Yr)) <= 1e-11 * np.max(np.abs(Yr))
     finally:
         sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200)
+
+
+@pytest.mark.parametrize("L,p", [(4, 3), (4, 4), (6, 3)], ids=["P35", "P70", "P84"])
+def test_ras_explicit_inverses_wide_modes(gpu, L, p):
+    """Explicit-inverse local solves and the smoother with its fused
+    Kronecker factor at P = 35, 70 and 84 (48, 80 and 96 padded modes: two
+    accumulation chains with two accumulators, one chain with four slots,
+    one chain with two slots) against the oracle, on a 24^2 mesh whose boxes
+    have a ragged 128-row tile (144 owned rows) and a ragged node chunk (168
+    overlapped nodes)."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    N, q, sx, sy, ov = 24, 2, 2, 2, 1
+    prob = sg.sg_setup(N, L, p, q, sigma2=0.3, bx=0.5, by=0.5)
+    try:
+        sg.sg_precond_setup(prob, sx, sy, ov, inner_rtol=1e-13, inner_max=200, ras_kernel=2)
+        assert sg.sg_precond_ras_kernel(prob) == 2
+        ref = galerkin.build(N, L, p, q, sigma2=0.3, bx=0.5, by=0.5)
+        parts = ras.partitions(ref.A(0), N, sx, sy, ov)
+        solvers = ras.local_solvers(ref.A(0), parts)
+        X = random_block(ref.n, ref.P, seed=43)
+        Y, Xq = run(prob, sg.PC_RAS_LOCAL, X, ref.n, torch.float32)
+        Yr = ras.apply_ras(parts, solvers, Xq)
+        assert np.max(np.abs(Y - Yr)) <= 1e-4 * np.max(np.abs(Yr))
+        assert np.linalg.norm(Y - Yr) <= 1e-5 * np.linalg.norm(Yr)
+        omega = sg.sg_precond_info(prob)[0]
+        Y, Xq = run(prob, sg.PC_SMOOTH, X, ref.n, torch.float32)
+        Gt = ras.kronecker_factor(ref)
+        Yr = omega * np.linalg.solve(Gt, ras.apply_ras(parts, solvers, Xq).T).T
+        assert np.max(np.abs(Y - Yr)) <= 1e-4 * np.max(np.abs(Yr))
+    finally:
+        prob.close()
