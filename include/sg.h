@@ -176,6 +176,37 @@ sg_status sg_set_apply_fp64(sg_problem* prob, int mode);
  * and the device bytes the blocks hold.  Any pointer may be NULL. */
 sg_status sg_apply_fp64_info(const sg_problem* prob, int* fine, int* coarse, int64_t* bytes);
 
+/* How the FP64 residuals of the mixed-precision refinement (sg_solve mode
+ * 1, recorded solves and batches of mode 1, sg_residual_refine) are formed
+ * (Sec. 2.1, Eq. Galerkin_L_exp, in the edge form: a row of A_k is the sum
+ * over the four edges of its node of w_k(e) (x_r - x_neighbour), so
+ *     R_r = F_r - sum_e B^e (x_r - x_c(e)),   B^e_ab = sum_k g_kab w_k(e)).
+ * mode 0 (default): in double-FP32 arithmetic over the edge blocks B^e,
+ * summed once in FP64 and stored as pairs of FP32 numbers (P (P + 1) / 2
+ * pairs per edge, built on first use when they take at most a quarter of
+ * the free device memory, else the FP64 apply); 1: the FP64 apply
+ * (sg_residual); 2: always the edge blocks, built now (SG_ERR_NOMEM when
+ * they do not fit, SG_ERR_ARG for P > 128).  Double-FP32: 48-bit
+ * significands, exact products of the high words (FMA), error-free sums,
+ * rounding errors gathered in the low word; the residual entries agree with
+ * FP64 to about 1e-13 of sum |A||X|, and the differences x_r - x_c are
+ * formed before any product, so the cancellation of the stencil costs no
+ * accuracy.  It runs on the FP32 units: GB300's FP64 rate is about 1/64 of
+ * its FP32 rate.  A change drops the recorded graphs, as sg_set_apply_fp64. */
+sg_status sg_set_refine_residual(sg_problem* prob, int mode);
+
+/* Whether the double-FP32 edge blocks are in use (0/1) and their device
+ * bytes (blocks and the split iterate).  Either pointer may be NULL. */
+sg_status sg_refine_residual_info(const sg_problem* prob, int* built, int64_t* bytes);
+
+/* R = F - sum_k A_k X G_k^T as the refinement computes it (see
+ * sg_set_refine_residual): FP64 arrays, layout as sg_residual (F may equal
+ * R; X must not overlap R).  Asynchronous on `stream` once the edge blocks
+ * exist (the first call builds them, synchronously).  Errors: SG_ERR_ARG
+ * for NULL pointers, leading dimensions < n or overlaps; SG_ERR_CUDA. */
+sg_status sg_residual_refine(sg_problem* prob, const double* F_dev, int64_t ldf, const double* X_dev, int64_t ldx,
+                             double* R_dev, int64_t ldr, void* stream);
+
 /* Tile shape of the register-specialised kernel of one family: which = 0
  * fine FP32, 1 coarse FP32, 2 fine FP64, 3 coarse FP64 (the FP64 kernels
  * carry the triple products as exact double immediates): rows per thread

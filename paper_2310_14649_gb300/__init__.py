@@ -16,7 +16,7 @@ __all__ = ["Problem", "sg_setup", "sg_destroy", "sg_get_sizes", "sg_get_multi_in
            "sg_residual", "sg_precond_setup", "sg_precond_info", "sg_get_partition",
            "sg_get_coarse_csr", "sg_get_amg_level", "sg_precond_apply", "sg_solve",
            "sg_profile", "sg_profile_read", "sg_launch_count", "sg_set_apply_kernel", "sg_set_apply_fp64",
-           "sg_apply_fp64_info", "sg_precond_save", "sg_precond_load", "sg_fourfold_products",
+           "sg_apply_fp64_info", "sg_set_refine_residual", "sg_refine_residual_info", "sg_residual_refine", "sg_precond_save", "sg_precond_load", "sg_fourfold_products",
            "sg_newton", "sg_nonlinear_residual", "sg_nonlinear_jacobian_apply", "sg_sample_solve",
            "sg_set_wait_limit", "sg_apply_flux",
            "sg_apply_config", "sg_apply_autotune", "sg_apply_info", "sg_mdot",
@@ -352,6 +352,28 @@ def sg_fourfold_products(L, p, q):
     call("sg_fourfold_products", L, p, q, ctypes.byref(n), _lib.ptr(ijkl, ctypes.c_int32),
          _lib.ptr(num, ctypes.c_int64), _lib.ptr(t, ctypes.c_double))
     return ijkl, num, t
+
+
+def sg_set_refine_residual(prob, mode):
+    """Refinement residuals: 0 auto (double-FP32 edge blocks, memory
+    permitting), 1 FP64 apply, 2 always double-FP32."""
+    call("sg_set_refine_residual", prob.handle, mode)
+
+
+def sg_refine_residual_info(prob):
+    b, nb = ctypes.c_int(), ctypes.c_int64()
+    call("sg_refine_residual_info", prob.handle, ctypes.byref(b), ctypes.byref(nb))
+    return {"built": b.value, "bytes": nb.value}
+
+
+def sg_residual_refine(prob, F, X, R, stream=None):
+    """R = F - sum_k A_k X G_k^T as the refinement forms it (FP64 blocks)."""
+    for t, nm in ((F, "F"), (X, "X"), (R, "R")):
+        _check_block(prob, t, nm)
+    if any(_dtype_code(t) != SG_F64 for t in (F, X, R)):
+        raise TypeError("sg_residual_refine: FP64 blocks only")
+    call("sg_residual_refine", prob.handle, dev_ptr(F), F.stride(0), dev_ptr(X), X.stride(0), dev_ptr(R),
+         R.stride(0), stream_handle(stream))
 
 
 def sg_apply_fp64_info(prob):

@@ -113,6 +113,9 @@ SIGNATURES = {
     "sg_fourfold_products": [ctypes.c_int, ctypes.c_int, ctypes.c_int, P_i64, P_i32, P_i64, P_f64],
     "sg_precond_load": [vp, vp, ctypes.c_int64],
     "sg_apply_fp64_info": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), P_i64],
+    "sg_set_refine_residual": [vp, ctypes.c_int],
+    "sg_refine_residual_info": [vp, ctypes.POINTER(ctypes.c_int), P_i64],
+    "sg_residual_refine": [vp, vp, i64, vp, i64, vp, i64, vp],
     "sg_apply_config": [vp] + [ctypes.c_int] * 10,
     "sg_apply_autotune": [vp, ctypes.c_int, ctypes.c_int, P_f64],
     "sg_apply_flux": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],

@@ -263,6 +263,16 @@ sg_status sg_residual(sg_problem* pr, sg_dtype dtype, const void* F, int64_t ldf
                          static_cast<float*>(R), ldr, st);
 }
 
+sg_status sg_residual_refine(sg_problem* pr, const double* F, int64_t ldf, const double* X, int64_t ldx, double* R,
+                             int64_t ldr, void* stream) {
+  SG_ARG(pr && F && X && R, "sg_residual_refine: NULL argument");
+  SG_ARG(ldx >= pr->n && ldr >= pr->n && ldf >= pr->n, "sg_residual_refine: leading dimension < n");
+  SG_ARG(!overlaps(X, 8 * size_t(ldx) * pr->P, R, 8 * size_t(ldr) * pr->P), "sg_residual_refine: X and R overlap");
+  SG_ARG(F == R ? ldf == ldr : !overlaps(F, 8 * size_t(ldf) * pr->P, R, 8 * size_t(ldr) * pr->P),
+         "sg_residual_refine: F and R overlap with different layouts");
+  return refine_residual(pr, F, ldf, X, ldx, R, ldr, static_cast<cudaStream_t>(stream));
+}
+
 sg_status sg_mdot(sg_problem* pr, sg_dtype dtype, const void* V, int64_t stride, int nv, const void* w, int64_t len,
                   double* out, void* stream) {
   SG_ARG(pr && V && w && out, "sg_mdot: NULL argument");

@@ -234,6 +234,28 @@ sg_status Profiler::read(int kind, int64_t* launches, double* ms) {
   return SG_OK;
 }
 
+void pair_lists(const sg_problem* pr, std::vector<int>& pptr, std::vector<int>& pk, std::vector<double>& pg) {
+  const int P = pr->P;
+  const int npair = P * (P + 1) / 2;
+  // (k, g) list of every packed pair a <= b
+  std::vector<std::vector<std::pair<int, double>>> lst(npair);
+  for (int64_t t = 0; t < pr->T; ++t) {
+    const int k = pr->kab[3 * t], a = pr->kab[3 * t + 1], b = pr->kab[3 * t + 2];
+    if (a > b) continue;
+    lst[size_t(a) * P - size_t(a) * (a - 1) / 2 + (b - a)].push_back({k, pr->g[t]});
+  }
+  pptr.assign(npair + 1, 0);
+  pk.clear();
+  pg.clear();
+  for (int q = 0; q < npair; ++q) {
+    for (const auto& e : lst[q]) {
+      pk.push_back(e.first);
+      pg.push_back(e.second);
+    }
+    pptr[q + 1] = int(pk.size());
+  }
+}
+
 sg_status asm_prepare(sg_problem* pr, const Ell& A, AsmBlocks& B, cudaStream_t st) {
   if (B.tried || pr->asm_mode == 1) return SG_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -249,22 +271,9 @@ sg_status asm_prepare(sg_problem* pr, const Ell& A, AsmBlocks& B, cudaStream_t s
     SG_CUDA(cudaMemGetInfo(&fr, &tot));
     if (bytes > fr / 4) return SG_OK;
   }
-  // (k, g) list of every packed pair a <= b
-  std::vector<std::vector<std::pair<int, double>>> lst(npair);
-  for (int64_t t = 0; t < pr->T; ++t) {
-    const int k = pr->kab[3 * t], a = pr->kab[3 * t + 1], b = pr->kab[3 * t + 2];
-    if (a > b) continue;
-    lst[size_t(a) * P - size_t(a) * (a - 1) / 2 + (b - a)].push_back({k, pr->g[t]});
-  }
-  std::vector<int> pptr(npair + 1, 0), pk;
+  std::vector<int> pptr, pk;
   std::vector<double> pg;
-  for (int q = 0; q < npair; ++q) {
-    for (const auto& e : lst[q]) {
-      pk.push_back(e.first);
-      pg.push_back(e.second);
-    }
-    pptr[q + 1] = int(pk.size());
-  }
+  pair_lists(pr, pptr, pk, pg);
   DevBuf dptr, dk, dg, c;
   SG_TRY(c.alloc(bytes));
   SG_TRY(dptr.alloc(pptr.size() * 4));

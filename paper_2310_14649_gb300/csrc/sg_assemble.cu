@@ -89,8 +89,9 @@ __global__ void k_fine_ell(const double* __restrict__ cb, int N, int64_t n, int6
 // (i,j) and the lower one of cell (i-1,j).  A row of A_k is then the sum
 // over its four edges of w (x_r - x_neighbour) (the rows of the P1 element
 // matrices sum to zero).  Thread per (term, edge).
+template <typename T>
 __global__ void k_flux_values(const double* __restrict__ cb, int N, int64_t vkst, int k0, int kn,
-                              float* __restrict__ v32) {
+                              T* __restrict__ v32) {
   const int m = N - 1;
   const int64_t E = 2LL * N * N, ne = 2LL * N * m, total = int64_t(kn) * ne;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
@@ -109,7 +110,7 @@ __global__ void k_flux_values(const double* __restrict__ cb, int N, int64_t vkst
       const int i = int(e2 % m) + 1, j = int(e2 / m);
       v = 0.5 * (up(i, j) + lo(i - 1, j));
     }
-    v32[int64_t(k0 + kl) * vkst + e] = float(v);
+    v32[int64_t(k0 + kl) * vkst + e] = T(v);
   }
 }
 
@@ -149,12 +150,27 @@ sg_status flux_build(sg_problem* pr) {
   for (int k0 = 0; k0 < K; k0 += KC) {
     const int kn = std::min(KC, K - k0);
     SG_TRY(element_coefficients(pr, k0, kn, dcb.as<double>(), nullptr));
-    k_flux_values<<<4 * 152, 256>>>(dcb.as<double>(), N, A.vkst, k0, kn, v.as<float>());
+    k_flux_values<float><<<4 * 152, 256>>>(dcb.as<double>(), N, A.vkst, k0, kn, v.as<float>());
     note_launch();
     SG_CUDA(cudaGetLastError());
   }
   SG_CUDA(cudaDeviceSynchronize());
   A.v32 = std::move(v);
+  return SG_OK;
+}
+
+sg_status flux_values64(sg_problem* pr, double* w, int64_t vkst) {
+  const int K = pr->K, N = pr->N, KC = 32;
+  DevBuf dcb;
+  SG_TRY(dcb.alloc(size_t(KC) * pr->E * sizeof(double)));
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    const int kn = std::min(KC, K - k0);
+    SG_TRY(element_coefficients(pr, k0, kn, dcb.as<double>(), nullptr));
+    k_flux_values<double><<<4 * 152, 256>>>(dcb.as<double>(), N, vkst, k0, kn, w);
+    note_launch();
+    SG_CUDA(cudaGetLastError());
+  }
+  SG_CUDA(cudaDeviceSynchronize());
   return SG_OK;
 }
 

@@ -437,6 +437,7 @@ struct SolverCtx {
     if (sizeof(T) == 8) {
       SG_TRY(asm_prepare(pr, pr->fine, pr->asm_fine, nullptr));
       SG_TRY(asm_prepare(pr, pc->co.ell, pc->co.asm_c, nullptr));
+      SG_TRY(resid_prepare(pr, nullptr));
     }
     if (pr->apply_mode != 1 && jit_eligible(pr)) {
       SG_TRY(jit_apply_build(pr, sizeof(T) == 8 ? 2 : 0));

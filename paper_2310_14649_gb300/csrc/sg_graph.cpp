@@ -282,7 +282,7 @@ static sg_status capture_system_nodes(GraphSystem& gs, const sg_solve_opts& o, c
   const cudaStream_t i2 = gs.streams.s[1];
   const int64_t k0 = launch_count();
   SG_TRY(vec_norm2<double>(F64, len, ird + 1, part, cnt, top));
-  SG_TRY(c64->apply_raw_fine(x64, r64, F64, top));
+  SG_TRY(refine_residual(pr, F64, pr->ld, x64, pr->ld, r64, pr->ld, top));
   SG_TRY(vec_norm2<double>(r64, len, ird, part, cnt, top));
   cudaGraphConditionalHandle hir;
   cudaStreamCaptureStatus cs;
@@ -300,7 +300,7 @@ static sg_status capture_system_nodes(GraphSystem& gs, const sg_solve_opts& o, c
   // that is looser than `inner` (the host-driven refinement's rule)
   SG_TRY(capture_fine<float>(*c32, r32, d32, inner, true, gs.streams, i2, ird, ird + 1, o.rtol));
   SG_TRY(vec_add_scaled_f32(x64, d32, len, ird, i2));
-  SG_TRY(c64->apply_raw_fine(x64, r64, F64, i2));
+  SG_TRY(refine_residual(pr, F64, pr->ld, x64, pr->ld, r64, pr->ld, i2));
   SG_TRY(vec_norm2<double>(r64, len, ird, part, cnt, i2));
   SG_TRY(ir_decide(ird, ird + 1, iri, o.rtol, max_ir, c32->fdg.iv + 4, o.max_it, hir, i2));
   SG_CUDA(cudaStreamEndCapture(i2, &body));
@@ -481,7 +481,10 @@ sg_status sg_batch_solve(sg_batch* B, const double* const* F, const int64_t* ldf
     double* F64 = dp<double>(S.io);
     double* ird = dp<double>(S.ir_d);
     SolverCtx<double>* c64 = S.c64.get();
-    SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+    if (B->opts.mode == 1)
+      SG_TRY(refine_residual(pr, F64, ld, x64, ld, dp<double>(S.r64), ld, st));
+    else
+      SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
     SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, ird + 2, dp<double>(c64->fine.partial),
                              dp<unsigned>(c64->fine.counter), st));
     SG_TRY(vec_norm2<double>(F64, len, ird + 3, dp<double>(c64->fine.partial), dp<unsigned>(c64->fine.counter), st));

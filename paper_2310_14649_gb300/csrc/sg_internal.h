@@ -100,6 +100,20 @@ struct AsmBlocks {
   DevBuf c;
 };
 
+// The fine operator in the edge-flux form with each edge's P x P block
+// summed once, B_ab^e = sum_k g_kab w_k(e) (symmetric: a <= b stored,
+// packed row by row), each entry split into two FP32 numbers hi + lo;
+// layout [npair][lde].  A row of the operator is sum over its four edges of
+// B^e (x_r - x_neighbour), the neighbour's term dropped on the Dirichlet
+// boundary.  Built on demand for the refinement residuals.
+struct FluxDf {
+  int npair = 0;
+  int64_t lde = 0;
+  bool tried = false;  // the policy was applied (built or declined)
+  DevBuf b;            // float2 [npair][lde]
+  DevBuf xs;           // float2 [P][ldr]: the split iterate
+};
+
 struct SolverState;
 void solver_free(sg_problem* pr);
 struct NewtonWork;
@@ -221,6 +235,8 @@ struct sg_problem {
   bool flux_allowed = true;            // the autotuner may choose the edge-flux form
   int wait_limit = 1 << 22;            // mbarrier polls of a tcgen05 completion wait
   int asm_mode = 0;                    // FP64 applies: 0 auto, 1 never assembled, 2 always
+  sg::FluxDf fdf;                      // double-FP32 edge blocks of the fine operator
+  int res_mode = 0;                    // refinement residuals: 0 auto, 1 FP64 applies, 2 double-FP32 edge blocks
 };
 
 namespace sg {
@@ -237,6 +253,9 @@ sg_status element_coefficients(sg_problem* pr, int k0, int kn, double* out, cuda
 // edge-flux form of the fine operator: neighbours, offsets and the FP32
 // conductances of every input term on every edge (allocated on first use)
 sg_status flux_build(sg_problem* pr);
+// the edge conductances of every input term in FP64, w[k * vkst + e] (the
+// edge numbering of the edge-flux form); synchronous
+sg_status flux_values64(sg_problem* pr, double* w, int64_t vkst);
 sg_status build_triple_tables(sg_problem* pr, TripleTables& t, int S);
 // apply (sg_apply.cu)
 template <typename T>
@@ -257,6 +276,18 @@ sg_status jit_apply_launch(sg_problem* pr, int which, const Ell& A, const float*
 // assembled FP64 blocks (sg_apply.cu): build per the problem's policy (no-op
 // once tried; never while `st` is capturing), and the apply over them
 sg_status asm_prepare(sg_problem* pr, const Ell& A, AsmBlocks& B, cudaStream_t st);
+// (k, g_kab) list of every packed pair a <= b (pair index a P - a (a - 1) / 2
+// + b - a): pair q owns entries [pptr[q], pptr[q + 1]) of pk, pg
+void pair_lists(const sg_problem* pr, std::vector<int>& pptr, std::vector<int>& pk, std::vector<double>& pg);
+// refinement residuals (sg_resid_df.cu): the double-FP32 edge blocks built
+// per the problem's policy (no-op once tried; never while `st` is
+// capturing), and R = F - A X (FP64 in and out) over them, or with the FP64
+// apply when they are not built
+sg_status resid_prepare(sg_problem* pr, cudaStream_t st);
+sg_status resid_df(sg_problem* pr, const double* F, int64_t ldf, const double* X, int64_t ldx, double* R,
+                   int64_t ldr, cudaStream_t st);
+sg_status refine_residual(sg_problem* pr, const double* F, int64_t ldf, const double* X, int64_t ldx, double* R,
+                          int64_t ldr, cudaStream_t st);
 sg_status apply_asm64(const sg_problem* pr, const Ell& A, const AsmBlocks& B, const double* X, int64_t ldx,
                       const double* F, int64_t ldf, double* Y, int64_t ldy, cudaStream_t st);
 // the operator apply without timing: assembled blocks (FP64, when built),

@@ -335,6 +335,23 @@ sg_status sg_set_apply_fp64(sg_problem* pr, int mode) {
   return SG_OK;
 }
 
+sg_status sg_set_refine_residual(sg_problem* pr, int mode) {
+  SG_ARG(pr && mode >= 0 && mode <= 2, "sg_set_refine_residual: mode must be 0, 1 or 2");
+  drop_recorded(pr);
+  pr->res_mode = mode;
+  pr->fdf = FluxDf();
+  if (mode == 2) SG_TRY(resid_prepare(pr, nullptr));
+  return SG_OK;
+}
+
+sg_status sg_refine_residual_info(const sg_problem* pr, int* built, int64_t* bytes) {
+  SG_ARG(pr, "sg_refine_residual_info: NULL handle");
+  const bool b = pr->fdf.b.ptr != nullptr && pr->res_mode != 1;
+  if (built) *built = b;
+  if (bytes) *bytes = b ? int64_t(pr->fdf.b.bytes + pr->fdf.xs.bytes) : 0;
+  return SG_OK;
+}
+
 sg_status sg_apply_fp64_info(const sg_problem* pr, int* fine, int* coarse, int64_t* bytes) {
   SG_ARG(pr, "sg_apply_fp64_info: NULL handle");
   const bool f = pr->asm_fine.c.ptr != nullptr;
@@ -549,7 +566,7 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
       if (x_is_zero)
         SG_CUDA(cudaMemcpyAsync(dp<double>(S.r64), F64, len * 8, cudaMemcpyDeviceToDevice, st));
       else
-        SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+        SG_TRY(refine_residual(pr, F64, ld, x64, ld, dp<double>(S.r64), ld, st));
       x_is_zero = false;
       {
         ProfScope phase(&pr->prof, 9, st);
@@ -605,7 +622,10 @@ static sg_status solve_impl(sg_problem* pr, const double* F, int64_t ldf, double
   }
   // true FP64 residual of the returned iterate
   if (final_r2 < 0.0) {
-    SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
+    if (o->mode == 1)
+      SG_TRY(refine_residual(pr, F64, ld, x64, ld, dp<double>(S.r64), ld, st));
+    else
+      SG_TRY(apply_op<double>(pr, false, x64, ld, F64, ld, dp<double>(S.r64), ld, st));
     SG_TRY(vec_norm2<double>(dp<double>(S.r64), len, scal + 2, dp<double>(c64->fine.partial),
                              dp<unsigned>(c64->fine.counter), st));
     SG_CUDA(cudaMemcpyAsync(S.host + 2, scal + 2, 8, cudaMemcpyDeviceToHost, st));

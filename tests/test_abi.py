@@ -66,6 +66,9 @@ def test_argument_errors_without_gpu(libsg):
     assert libsg.sg_nonlinear_residual(None, None, 0, None, 0, None, 0, None) == -1
     assert libsg.sg_nonlinear_jacobian_apply(None, 0, None, 0, None, 0, None, 0, None) == -1
     assert libsg.sg_apply_fp64_info(None, None, None, None) == -1
+    assert libsg.sg_set_refine_residual(None, 0) == -1
+    assert libsg.sg_refine_residual_info(None, None, None) == -1
+    assert libsg.sg_residual_refine(None, None, 0, None, 0, None, 0, None) == -1
     assert libsg.sg_apply_config(None, 0, 1, 1, 1, 1, 8, 1, 0, 1, 4) == -1
 
 

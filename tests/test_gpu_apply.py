@@ -133,6 +133,72 @@ def test_residual_in_place(gpu, fp64):
     assert np.all(np.abs(R - Rref) <= gamma(m + 1, U64) * (Yb + np.abs(F)))
 
 
+@pytest.mark.parametrize("N,L,p,q", [(32, 2, 2, 4), (33, 3, 3, 6), (2, 2, 1, 2), (9, 0, 0, 0), (40, 1, 5, 10)])
+def test_refine_residual_double_fp32(gpu, N, L, p, q):
+    """The refinement residual over the double-FP32 edge blocks against the
+    FP64 oracle: within 2^-40 of |A||X| + |F| (FP32 alone gives 2^-24),
+    ragged leading dimension, F == R in place, and the policy switch back
+    to the FP64 apply."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    prob, ref = setup_pair(N, L, p, q)
+    sg.sg_set_refine_residual(prob, 2)
+    info = sg.sg_refine_residual_info(prob)
+    npair = ref.P * (ref.P + 1) // 2
+    assert info["built"] == 1 and info["bytes"] >= npair * 2 * N * (N - 1) * 8
+    X = random_block(ref.n, ref.P, seed=5)
+    F = random_block(ref.n, ref.P, seed=6)
+    Rref = F - galerkin.apply(ref, X)
+    Yb, m = bound_and_terms(ref, X)
+    bound = (2.0 ** -40 + gamma(m + 1, U64)) * (Yb + np.abs(F))
+    for ld in (ref.n, ref.n + 37):
+        Xd, Fd = to_dev(X, torch.float64, ld), to_dev(F, torch.float64, ld)
+        Rd = torch.full_like(Fd, 7.0)
+        sg.sg_residual_refine(prob, Fd, Xd, Rd)
+        torch.cuda.synchronize()
+        R = from_dev(Rd, ref.n)
+        assert np.all(np.abs(R - Rref) <= bound)
+        assert torch.all(Rd[:, ref.n:] == 7.0)  # padding rows untouched
+        sg.sg_residual_refine(prob, Fd, Xd, Fd)
+        torch.cuda.synchronize()
+        assert np.array_equal(from_dev(Fd, ref.n), R)
+    sg.sg_set_refine_residual(prob, 1)
+    assert sg.sg_refine_residual_info(prob)["built"] == 0
+    Xd, Fd = to_dev(X, torch.float64), to_dev(F, torch.float64)
+    sg.sg_residual_refine(prob, Fd, Xd, Fd)
+    torch.cuda.synchronize()
+    assert np.all(np.abs(from_dev(Fd, ref.n) - Rref) <= gamma(m + 1, U64) * (Yb + np.abs(F)))
+
+
+def test_refine_residual_full_size_sampled_rows(gpu):
+    """256x256 mesh, L=4, p=3 (P=35), q=6 (K=210), the bench's launch:
+    sampled rows of the double-FP32 refinement residual against the
+    entrywise oracle definition, for a random iterate and for a smooth one
+    (the FP64 solution of the mean problem) whose residual is small."""
+    import torch
+    import paper_2310_14649_gb300 as sg
+    c = CONFIGS["poisson256_L4_p3"]
+    prob, ref = setup_pair(c["N"], c["L"], c["p"], c["q"], c["sigma2"], c["b"])
+    rows = np.unique(np.concatenate([[0, 1, ref.n - 1, ref.n // 2],
+                                     np.random.default_rng(1).integers(0, ref.n, 60)]))
+    absref = galerkin.Problem(**{**ref.__dict__, "vals": np.abs(ref.vals), "g": np.abs(ref.g)})
+    m = int(np.bincount(ref.kab[:, 1]).max() * 5)
+    import scipy.sparse.linalg as spla
+    smooth = np.zeros((ref.n, ref.P))
+    smooth[:, 0] = spla.spsolve(ref.A(0).tocsc(), ref.b)
+    F = ref.rhs()
+    for X in (random_block(ref.n, ref.P, seed=22), smooth):
+        Xd, Fd = to_dev(X, torch.float64), to_dev(F, torch.float64)
+        Rd = torch.empty_like(Xd)
+        sg.sg_residual_refine(prob, Fd, Xd, Rd)
+        torch.cuda.synchronize()
+        R = from_dev(Rd, ref.n)[rows]
+        Rref = F[rows] - galerkin.apply_rows(ref, X, rows)
+        Yb = galerkin.apply_rows(absref, np.abs(X), rows) + np.abs(F[rows])
+        assert np.all(np.abs(R - Rref) <= (2.0 ** -40 + gamma(m, U64)) * Yb)
+    assert sg.sg_refine_residual_info(prob)["built"] == 1
+
+
 def test_rhs(gpu):
     import torch
     import paper_2310_14649_gb300 as sg
