@@ -36,6 +36,9 @@ namespace sg {
 namespace {
 
 constexpr int kDfWarps = 8;
+constexpr int kDfAhead = 8;  // block entries loaded ahead of their products
+constexpr int kDfTileRows = 4;  // node rows of a tile (32 node columns)
+constexpr size_t kSmemMax = 227 * 1024;
 
 // x - y for two double-FP32 values, normalised (|lo| <= ulp(hi) / 2)
 __device__ __forceinline__ float2 df_sub(float2 x, float2 y) {
@@ -97,71 +100,176 @@ __global__ void k_edge_blocks_df(int64_t ne, int64_t lde, int64_t vkst, const in
   B[int64_t(q) * lde + e] = df_split(c);
 }
 
-// R = F - A X over the edge blocks (R = A X when F is null).  Warp w owns
-// outputs a = w + 8 j, j < J.
+// Flux of one edge group: f[a] = sum_b B_ab d_b for the outputs a = w +
+// 8 j of this warp (lane = edge), d in shared memory, the block entries of
+// pair (a, b) at index off(min) + max, off(b) = b P - b (b - 1) / 2 - b
 template <int J>
-__global__ void __launch_bounds__(32 * kDfWarps) k_resid_flux_df(int64_t n, int64_t ldr, int P, int64_t lde,
-                                                                 const int* __restrict__ col,
-                                                                 const int* __restrict__ vidx,
+__device__ __forceinline__ void edge_flux(const float2* __restrict__ Be, int64_t lde, int P, int w, int lane,
+                                          const float2* ds, float (&fh)[J], float (&fl)[J]) {
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int a = w + j * kDfWarps;
+    float h = 0.f, l = 0.f;
+    if (a < P) {
+      // pairs (b, a) for b < a: consecutive b are P - b - 1 pairs apart;
+      // eight loads in flight ahead of their products
+      const float2* pp = Be + int64_t(a) * lde;
+      int b = 0;
+      for (; b + kDfAhead <= a; b += kDfAhead) {
+        float2 cv[kDfAhead];
+#pragma unroll
+        for (int u = 0; u < kDfAhead; ++u) {
+          cv[u] = __ldg(pp);
+          pp += int64_t(P - (b + u) - 1) * lde;
+        }
+#pragma unroll
+        for (int u = 0; u < kDfAhead; ++u) df_fma(h, l, cv[u], ds[(b + u) * 32 + lane]);
+      }
+      for (; b < a; ++b) {
+        df_fma(h, l, __ldg(pp), ds[b * 32 + lane]);
+        pp += int64_t(P - b - 1) * lde;
+      }
+      // pairs (a, b) for b >= a: consecutive from off(a) + a
+      for (; b + kDfAhead <= P; b += kDfAhead) {
+        float2 cv[kDfAhead];
+#pragma unroll
+        for (int u = 0; u < kDfAhead; ++u) cv[u] = __ldg(pp + int64_t(u) * lde);
+        pp += int64_t(kDfAhead) * lde;
+#pragma unroll
+        for (int u = 0; u < kDfAhead; ++u) df_fma(h, l, cv[u], ds[(b + u) * 32 + lane]);
+      }
+      for (; b < P; ++b) {
+        df_fma(h, l, __ldg(pp), ds[b * 32 + lane]);
+        pp += lde;
+      }
+      df_renorm(h, l);
+    }
+    fh[j] = h;
+    fl[j] = l;
+  }
+}
+
+// (y.x, y.y) += sign (h, l) in double-FP32
+__device__ __forceinline__ void df_acc(float2* y, float h, float l) {
+  float2 v = *y;
+  const float s = __fadd_rn(v.x, h);
+  const float bb = __fsub_rn(s, v.x);
+  const float e = __fadd_rn(__fsub_rn(v.x, __fsub_rn(s, bb)), __fsub_rn(h, bb));
+  *y = make_float2(s, __fadd_rn(v.y, __fadd_rn(l, e)));
+}
+
+// R = F - A X (R = A X when F is null) on a tile of 32 x TY interior nodes
+// (I = i0 + 1 .. i0 + 32, J = j0 + 1 .. j0 + TY; row (J - 1) m + I - 1,
+// m = N - 1).  The tile's edges are taken in groups of up to 32 (lane =
+// edge): TY rows of horizontal edges (the one west of each node), the
+// column of edges east of the tile's last node column, TY + 1 rows of
+// vertical edges.  Each edge's flux f = B^e (x_hi - x_lo) is formed once
+// and added to the node above or right of it (+f) and subtracted from the
+// node below or left (-f) where that node is in the tile, in double-FP32
+// accumulators in shared memory.
+template <int J, int TY>
+__global__ void __launch_bounds__(32 * kDfWarps) k_resid_tile_df(int N, int P, int64_t lde, int64_t ldr,
                                                                  const float2* __restrict__ B,
                                                                  const float2* __restrict__ Xs,
                                                                  const double* __restrict__ F, int64_t ldf,
                                                                  double* __restrict__ R, int64_t ldR) {
-  extern __shared__ float2 ds[];  // [P][32]: x_r - x_c across the current edge
+  extern __shared__ float2 sm[];
+  float2* ds = sm;            // [P][32]: x_hi - x_lo across the group's edges
+  float2* y = sm + P * 32;    // [P][TY][32]: the tile's outputs
+  const int m = N - 1;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t r = int64_t(blockIdx.x) * 32 + lane;
-  const bool valid = r < n;
-  float sh[J], sl[J];
-#pragma unroll
-  for (int j = 0; j < J; ++j) sh[j] = sl[j] = 0.f;
-  for (int s = 0; s < 4; ++s) {
-    const int c = valid ? col[int64_t(s) * ldr + r] : -1;
-    const int64_t e = valid ? vidx[int64_t(s) * ldr + r] : 0;
-    __syncthreads();  // the previous edge's differences are consumed
+  for (int idx = threadIdx.x; idx < P * TY * 32; idx += 32 * kDfWarps) y[idx] = make_float2(0.f, 0.f);
+  auto xrow = [&](int I, int Jr) { return (I >= 1 && I <= m && Jr >= 1 && Jr <= m) ? (Jr - 1) * m + I - 1 : -1; };
+  for (int g = 0; g < 2 * TY + 2; ++g) {
+    int64_t e = 0;
+    int rlo = -1, rhi = -1, tlo = -1, thi = -1;
+    if (g < TY) {
+      // horizontal edge between (I - 1, Jr) and (I, Jr)
+      const int I = i0 + lane + 1, Jr = j0 + g + 1;
+      if (Jr <= m && I <= N) {
+        e = int64_t(Jr - 1) * N + I - 1;
+        rlo = xrow(I - 1, Jr);
+        rhi = xrow(I, Jr);
+        if (rhi >= 0) thi = g * 32 + lane;
+        if (rlo >= 0 && lane >= 1) tlo = g * 32 + lane - 1;
+      }
+    } else if (g == TY) {
+      // horizontal edge east of the last node column: (I, Jr) - (I + 1, Jr)
+      const int I = i0 + 32, Jr = j0 + lane + 1;
+      if (lane < TY && Jr <= m && I <= m) {
+        e = int64_t(Jr - 1) * N + I;
+        rlo = xrow(I, Jr);
+        rhi = xrow(I + 1, Jr);
+        tlo = lane * 32 + 31;
+      }
+    } else {
+      // vertical edge between (I, Jl) and (I, Jl + 1)
+      const int t = g - TY - 1, I = i0 + lane + 1, Jl = j0 + t;
+      if (I <= m && Jl + 1 <= N) {
+        e = int64_t(N) * m + int64_t(Jl) * m + I - 1;
+        rlo = xrow(I, Jl);
+        rhi = xrow(I, Jl + 1);
+        if (rhi >= 0 && t <= TY - 1) thi = t * 32 + lane;
+        if (rlo >= 0 && t >= 1) tlo = (t - 1) * 32 + lane;
+      }
+    }
+    const bool active = thi >= 0 || tlo >= 0;
+    if (!active) e = 0;
+    __syncthreads();  // the previous group's differences are consumed
     for (int b = w; b < P; b += kDfWarps) {
       float2 d = make_float2(0.f, 0.f);
-      if (valid) {
-        const float2 xr = Xs[int64_t(b) * ldr + r];
-        d = c >= 0 ? df_sub(xr, Xs[int64_t(b) * ldr + c]) : xr;
+      if (active) {
+        const float2 xh = rhi >= 0 ? Xs[int64_t(b) * ldr + rhi] : make_float2(0.f, 0.f);
+        const float2 xl = rlo >= 0 ? Xs[int64_t(b) * ldr + rlo] : make_float2(0.f, 0.f);
+        d = df_sub(xh, xl);
       }
       ds[b * 32 + lane] = d;
     }
     __syncthreads();
-    const float2* Be = B + e;
+    float fh[J], fl[J];
+    edge_flux<J>(B + e, lde, P, w, lane, ds, fh, fl);
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       const int a = w + j * kDfWarps;
       if (a < P) {
-        float h = sh[j], l = sl[j];
-        // pairs (b, a) for b < a: index off(b) + a, off(b) = b P - b (b - 1) / 2 - b
-        int64_t q = a;
-        for (int b = 0; b < a; ++b) {
-          df_fma(h, l, Be[q * lde], ds[b * 32 + lane]);
-          q += P - b - 1;
-        }
-        // pairs (a, b) for b >= a: consecutive from off(a) + a
-        const float2* Ba = Be + q * lde;
-        for (int b = a; b < P; ++b) df_fma(h, l, Ba[int64_t(b - a) * lde], ds[b * 32 + lane]);
-        df_renorm(h, l);
-        sh[j] = h;
-        sl[j] = l;
+        float2* ya = y + a * TY * 32;
+        if (thi >= 0) df_acc(ya + thi, fh[j], fl[j]);
+        __syncwarp();
+        if (tlo >= 0) df_acc(ya + tlo, -fh[j], -fl[j]);
+        __syncwarp();
       }
     }
   }
-  if (!valid) return;
-#pragma unroll
-  for (int j = 0; j < J; ++j) {
-    const int a = w + j * kDfWarps;
-    if (a < P) {
-      const double y = double(sh[j]) + double(sl[j]);
-      R[int64_t(a) * ldR + r] = F ? F[int64_t(a) * ldf + r] - y : y;
-    }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < P * TY * 32; idx += 32 * kDfWarps) {
+    const int a = idx / (TY * 32), t = (idx / 32) % TY, l = idx % 32;
+    const int r = xrow(i0 + l + 1, j0 + t + 1);
+    if (r < 0) continue;
+    const float2 v = y[idx];
+    const double yv = double(v.x) + double(v.y);
+    R[int64_t(a) * ldR + r] = F ? F[int64_t(a) * ldf + r] - yv : yv;
   }
 }
 
 }  // namespace
 
 constexpr int kDfMaxP = 16 * kDfWarps;
+
+// the tile kernels' shared memory ((1 + TY) P 32 float2, up to 164 KB)
+// above the default 48 KB; set once, before any capture
+sg_status df_kernel_attrs() {
+  static bool done = false;
+  if (done) return SG_OK;
+  const int lim = int(kSmemMax);
+  SG_CUDA(cudaFuncSetAttribute(k_resid_tile_df<2, kDfTileRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  SG_CUDA(cudaFuncSetAttribute(k_resid_tile_df<5, kDfTileRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  SG_CUDA(cudaFuncSetAttribute(k_resid_tile_df<8, kDfTileRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  SG_CUDA(cudaFuncSetAttribute(k_resid_tile_df<11, kDfTileRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  SG_CUDA(cudaFuncSetAttribute(k_resid_tile_df<16, kDfTileRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  done = true;
+  return SG_OK;
+}
 
 sg_status resid_prepare(sg_problem* pr, cudaStream_t st) {
   FluxDf& D = pr->fdf;
@@ -189,7 +297,6 @@ sg_status resid_prepare(sg_problem* pr, cudaStream_t st) {
     SG_CUDA(cudaMemGetInfo(&fr, &tot));
     if (keep + temp > fr / 4) return SG_OK;
   }
-  SG_TRY(flux_build(pr));  // neighbours and edge numbers of every row
   DevBuf w, dptr, dk, dg, b, xs;
   SG_TRY(w.alloc(temp));
   SG_TRY(flux_values64(pr, w.as<double>(), lde));
@@ -211,6 +318,7 @@ sg_status resid_prepare(sg_problem* pr, cudaStream_t st) {
   note_launch();
   SG_CUDA(cudaGetLastError());
   SG_CUDA(cudaDeviceSynchronize());
+  SG_TRY(df_kernel_attrs());
   D.npair = npair;
   D.lde = lde;
   D.b = std::move(b);
@@ -232,14 +340,13 @@ sg_status resid_df(sg_problem* pr, const double* F, int64_t ldf, const double* X
   note_launch();
   SG_CUDA(cudaGetLastError());
   const int need = (P + kDfWarps - 1) / kDfWarps;
-  const size_t smem = size_t(P) * 32 * sizeof(float2);
-  const unsigned grid = unsigned((n + 31) / 32);
-  const int* col = pr->flux.col.as<int>();
-  const int* vidx = pr->flux.vidx.as<int>();
+  const size_t smem = size_t(P) * 32 * (1 + kDfTileRows) * sizeof(float2);
+  const int m = pr->N - 1;
+  const dim3 grid(unsigned((m + 31) / 32), unsigned((m + kDfTileRows - 1) / kDfTileRows));
   const float2* B = D.b.as<float2>();
   const float2* Xs = D.xs.as<float2>();
-#define SG_DF_LAUNCH(JJ)                                                                                       \
-  k_resid_flux_df<JJ><<<grid, 32 * kDfWarps, smem, st>>>(n, ldr, P, D.lde, col, vidx, B, Xs, F, ldf, R, ldR)
+#define SG_DF_LAUNCH(JJ) \
+  k_resid_tile_df<JJ, kDfTileRows><<<grid, 32 * kDfWarps, smem, st>>>(pr->N, P, D.lde, ldr, B, Xs, F, ldf, R, ldR)
   if (need <= 2)
     SG_DF_LAUNCH(2);
   else if (need <= 5)
