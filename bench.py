@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--host-loops", action="store_true",
                     help="coarse GMRES driven from the host (every kernel a separate launch): for launch lists")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["apply_slot", "apply_flux", "cnn_train", "nl_coef", "sample", "ras", "ras_inv"],
+                    choices=["apply_slot", "apply_flux", "cnn_train", "nl_coef", "sample", "ras", "ras_inv",
+                             "refine_residual"],
                     help="run a few launches of one kernel on a small case and exit (for profiler captures)")
     return ap.parse_args()
 
@@ -80,13 +81,13 @@ def measured_traffic(shape):
     return None
 
 
-def ras_inv_traffic():
-    """DRAM bytes per launch of k_ras_inv_tc from the committed ncu summary
-    (profiles/k_ras_inv_tc_poisson256_L4_p3.md), if that summary was taken on
-    the current kernel source (its sha1 recorded there); otherwise None."""
+def ras_inv_traffic(source="sg_ras_tc.cu", summary="k_ras_inv_tc_poisson256_L4_p3.md"):
+    """DRAM bytes per launch of a kernel from its committed ncu summary under
+    profiles/ (by default k_ras_inv_tc), if that summary was taken on the
+    current kernel source (its sha1 recorded there); otherwise None."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2310_14649_gb300", "csrc", "sg_ras_tc.cu")
-    prof = os.path.join(ROOT, "profiles", "k_ras_inv_tc_poisson256_L4_p3.md")
+    src = os.path.join(ROOT, "paper_2310_14649_gb300", "csrc", source)
+    prof = os.path.join(ROOT, "profiles", summary)
     try:
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
         vals = {}
@@ -552,6 +553,17 @@ def kernel_case(name):
             sg.sg_apply_flux(prob, 1 if name == "apply_flux" else 0)
             for _ in range(3):
                 sg.sg_apply(prob, X, Y)
+    elif name == "refine_residual":
+        prob = sg.sg_setup(c["N"], c["L"], c["p"], c["q"], sigma2=c["sigma2"], bx=c["b"], by=c["b"])
+        sg.sg_set_refine_residual(prob, 2)
+        X = torch.randn((prob.P, prob.n), dtype=torch.float64, device="cuda")
+        F = torch.randn_like(X)
+        R = torch.empty_like(X)
+        for _ in range(3):
+            sg.sg_residual_refine(prob, F, X, R)
+        stream = torch.cuda.current_stream()
+        ms, _ = ev_time(torch, stream, lambda: [sg.sg_residual_refine(prob, F, X, R) for _ in range(20)])
+        print(json.dumps({"kernel_case": name, "residual_ms": ms / 20}))
     elif name == "cnn_train":
         prob = sg.sg_setup(256, 2, 1, 2)
         sg.sg_cnn_init(prob, seed=1)
@@ -660,7 +672,7 @@ def main():
     torch.cuda.synchronize()
     ms_prof = p0.elapsed_time(p1) / prof_steps
     kinds = {}
-    for kind, name in ((0, "apply_fine_f32"), (1, "apply_fine_f64"), (2, "apply_coarse_f32"), (3, "apply_coarse_f64"),
+    for kind, name in ((0, "apply_fine_f32"), (1, "refine_residual"), (2, "apply_coarse_f32"), (3, "apply_coarse_f64"),
                        (4, "ras_local_f32"), (6, "smoother"), (7, "coarse_correction"), (8, "arnoldi"),
                        (9, "refinement")):
         cnt, kms = sg.sg_profile_read(prob, kind)
@@ -694,12 +706,17 @@ def main():
         inv_bytes += int(own_b.sum()) * len(idx_b) * 4 + len(idx_b) * P * 4
     inv_bytes += n * P * 4
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+    # refinement residual: the edge blocks (P (P + 1) / 2 pairs of FP32 per
+    # edge) read once, X and F read, R written (FP64)
+    res_cnt, res_ms = kinds["refine_residual"]
+    res_avg = res_ms / max(res_cnt, 1)
+    res_bytes = (P * (P + 1) // 2) * 2 * N_ * (N_ - 1) * 8 + 3 * n * P * 8
     # phases of one step (non-overlapping: the fine applies outside the
     # smoother and the coarse correction, the smoother, the coarse
     # correction, the Arnoldi steps, the refinement bookkeeping); the rest
     # is host synchronisation and small copies
     phase_ms = {k: round(kinds[k][1] / prof_steps, 3) for k in
-                ("apply_fine_f32", "apply_fine_f64", "smoother", "coarse_correction", "arnoldi", "refinement")}
+                ("apply_fine_f32", "refine_residual", "smoother", "coarse_correction", "arnoldi", "refinement")}
     phase_ms["ras_local_f32 (inside smoother)"] = round(kinds["ras_local_f32"][1] / prof_steps, 3)
     attributed = sum(v for k, v in phase_ms.items() if "inside" not in k)
 
@@ -833,6 +850,17 @@ def main():
                                  "flops_per_launch": ras_flops, "avg_launch_ms": ras_avg, "launches": rcnt,
                                  "note": "latency-bound line recurrences (dependent steps per sweep); "
                                          "a few percent of DRAM bandwidth"}),
+        "roofline_refine_residual": ({"kernel": "k_split_df + k_resid_tile_df (FP64 refinement residual in "
+                                                "double-FP32 over the edge blocks; the timed span holds both "
+                                                "launches)",
+                                      "bound": "hbm", "achieved": round(res_bytes / (res_avg * 1e-3) / 1e9, 1),
+                                      "peak": peak, "unit": "GB/s",
+                                      "frac": round(res_bytes / (res_avg * 1e-3) / 1e9 / peak, 4),
+                                      "peak_source": peak_kind, "bytes_per_launch": res_bytes,
+                                      "avg_launch_ms": res_avg, "launches": res_cnt,
+                                      "traffic": ras_inv_traffic("sg_resid_df.cu",
+                                                                 "k_resid_tile_df_poisson256_L4_p3.md")}
+                                     if res_cnt and sg.sg_refine_residual_info(prob)["built"] else None),
         "ras_forms": ras_forms,
         "phase_ms_per_step": phase_ms,
         "profiled_ms_per_step": round(ms_prof, 3),
