@@ -50,6 +50,10 @@ def parse():
                     help="the timed mixed solves only (no comparison solves, e2e or extras): for launch lists")
     ap.add_argument("--host-loops", action="store_true",
                     help="coarse GMRES driven from the host (every kernel a separate launch): for launch lists")
+    ap.add_argument("--ras-kernel", type=int, default=RAS_KERNEL, choices=[0, 2, 3],
+                    help="RAS local solves of the timed solve: 0 line kernel, 2 explicit inverses, 3 the faster "
+                         "(timed at setup; pin it for launch lists, where the profiler's serialisation skews "
+                         "the timing)")
     ap.add_argument("--kernel-case", default=None,
                     choices=["apply_slot", "apply_flux", "cnn_train", "nl_coef", "sample", "ras", "ras_inv",
                              "refine_residual"],
@@ -614,7 +618,7 @@ def main():
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
     sg.sg_precond_setup(prob, c["sx"], c["sy"], c["overlap"], inner_rtol=INNER_RTOL, host_loops=args.host_loops,
-                        ras_kernel=RAS_KERNEL)
+                        ras_kernel=args.ras_kernel)
     torch.cuda.synchronize()
     t_pc = time.perf_counter() - t0
     t0 = time.perf_counter()
