@@ -133,12 +133,14 @@ def test_residual_in_place(gpu, fp64):
     assert np.all(np.abs(R - Rref) <= gamma(m + 1, U64) * (Yb + np.abs(F)))
 
 
-@pytest.mark.parametrize("N,L,p,q", [(32, 2, 2, 4), (33, 3, 3, 6), (2, 2, 1, 2), (9, 0, 0, 0), (40, 1, 5, 10)])
+@pytest.mark.parametrize("N,L,p,q", [(32, 2, 2, 4), (33, 3, 3, 6), (2, 2, 1, 2), (9, 0, 0, 0), (40, 1, 5, 10),
+                                     (12, 5, 3, 2), (12, 4, 4, 2), (10, 3, 7, 2)])
 def test_refine_residual_double_fp32(gpu, N, L, p, q):
     """The refinement residual over the double-FP32 edge blocks against the
     FP64 oracle: within 2^-40 of |A||X| + |F| (FP32 alone gives 2^-24),
     ragged leading dimension, F == R in place, and the policy switch back
-    to the FP64 apply."""
+    to the FP64 apply.  P = 56, 70 and 120 take the kernels with 8, 11 and
+    16 outputs per warp (P up to 64, 88 and 128)."""
     import torch
     import paper_2310_14649_gb300 as sg
     prob, ref = setup_pair(N, L, p, q)
