@@ -342,6 +342,52 @@ def test_apply_three_ways_and_symmetry():
     assert ev.min() > 0
 
 
+def edge_form_apply(prob, X):
+    """The operator written edge by edge (the P1 "/" mesh: the diagonal
+    couplings vanish, rows sum to zero with their Dirichlet neighbours):
+    y_r = sum over the four edges e of r of B^e (x_r - x_c), B^e = sum_k
+    w_k(e) G_k, w_k(e) half the sum of c_k over the two triangles that
+    share e; x = 0 on the boundary."""
+    N = prob.N
+    G = prob.G()
+    cb = prob.cbar
+    Y = np.zeros_like(X)
+
+    def flux(w, ra, rb):
+        xa = X[ra] if ra >= 0 else 0.0
+        xb = X[rb] if rb >= 0 else 0.0
+        f = np.tensordot(w, G, axes=1) @ (xa - xb)
+        if ra >= 0:
+            Y[ra] += f
+        if rb >= 0:
+            Y[rb] -= f
+
+    for j in range(1, N):
+        for i in range(N):
+            # (i, j)-(i+1, j): lower triangle of cell (i, j), upper of (i, j-1)
+            w = 0.5 * (cb[:, 2 * (j * N + i)] + cb[:, 2 * ((j - 1) * N + i) + 1])
+            flux(w, int(fem.interior_index(N, i, j)), int(fem.interior_index(N, i + 1, j)))
+    for j in range(N):
+        for i in range(1, N):
+            # (i, j)-(i, j+1): upper triangle of cell (i, j), lower of (i-1, j)
+            w = 0.5 * (cb[:, 2 * (j * N + i) + 1] + cb[:, 2 * (j * N + i - 1)])
+            flux(w, int(fem.interior_index(N, i, j)), int(fem.interior_index(N, i, j + 1)))
+    return Y
+
+
+def test_edge_form_equals_kronecker_apply():
+    """The edge form of the operator (summed P x P block per edge, applied
+    to the difference of the end nodes), which the refinement residual
+    uses, against the Kronecker apply sum_k A_k X G_k^T of the assembled
+    stiffness matrices (Sec. 2.1, Eq. Galerkin_L_exp)."""
+    for args in ((8, 2, 2, 4), (9, 3, 1, 2), (2, 1, 2, 4)):
+        prob = galerkin.build(*args, sigma2=0.3, bx=0.5, by=0.5)
+        X = np.random.default_rng(3).standard_normal((prob.n, prob.P))
+        Y = galerkin.apply(prob, X)
+        Ye = edge_form_apply(prob, X)
+        assert np.max(np.abs(Ye - Y)) < 1e-12 * np.max(np.abs(Y))
+
+
 def test_gmres_matches_direct():
     prob = galerkin.build(32, 2, 2, 4, sigma2=0.3, bx=0.5, by=0.5)
     Xd = galerkin.solve_direct(prob)
